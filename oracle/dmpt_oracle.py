@@ -1,0 +1,316 @@
+"""FP64 CPU oracle for canonical density matrix perturbation theory.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this module:
+only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it. It shares no code with the CUDA library.
+
+What it computes (Niklasson, Rubensson, Rudberg, Cawkwell, "Canonical density
+matrix perturbation theory"):
+
+* P0, the finite-temperature density matrix of an orthogonal Hamiltonian H0,
+  Eq. (Rec_F_1): P0 = [exp(beta (H0 - mu I)) + I]^-1, with mu fixed by the
+  canonical condition Tr P0 = N_occ (Sec. II, text after Eq. Rec_F_2).
+* P1, its first-order canonical response to H(lambda) = H0 + lambda H1
+  (Eqs. P_resp, H_prt), with the first-order chemical potential mu1 chosen so
+  that Tr P1 = 0 (Sec. II, condition after Eq. P_resp).
+* The free energy Omega = Tr[P H] - T_e S[P] (Eqs. FreeE, SED, k_B = 1) and
+  the polarizability alpha = -2 Tr[P1 H1], i.e. -4 Omega^(2) by the n+1 rule
+  (Eq. Resp_0 with H^(2) = 0).
+
+Two reference functions are provided, both evaluated exactly in the
+eigenbasis of H0 (LAPACK ``dsyevd`` via ``numpy.linalg.eigh``):
+
+* ``kind="fd"``: the Fermi-Dirac function itself, Eq. (Rec_F_1).
+* ``kind="rec"``: the function that the recursion of Eq. (Rec_F_2) applies
+  exactly after M steps. Appendix A shows the M-fold composition of
+  f_2(x) = x^2 / (x^2 + (1-x)^2) equals f_{2^M}(x) = x^(2^M) / (x^(2^M) +
+  (1-x)^(2^M)). With x = 1/2 + z/2 this is 1/2 [1 + tanh(2^M atanh z)], and
+  X0 of Eq. (Rec_F_2) gives z0 = -beta (eps - mu) / 2^(M+1).
+
+The response uses the Daleckii-Krein divided-difference formula: in the
+eigenbasis, (P1)_ij = f[eps_i, eps_j] (h_ij - mu1 delta_ij) with h = V^T H1 V,
+and mu1 = sum_i f'_i h_ii / sum_i f'_i from Tr P1 = 0.
+
+``literal_recursion`` and ``literal_canonical`` restate Algorithm 1 (first
+order) in the paper's X-notation with dense linear solves. They exist to pin
+the closed forms above against the iteration the paper prints.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import numpy as np
+
+LN2 = math.log(2.0)
+
+
+# ----------------------------------------------------------------------------
+# scalar building blocks
+# ----------------------------------------------------------------------------
+
+def logcosh(x):
+    """log cosh(x) without overflow."""
+    a = np.abs(x)
+    return a + np.log1p(np.exp(-2.0 * a)) - LN2
+
+
+def log_sinhc(y):
+    """log(sinh(y)/y) for real y (even function, 0 at y = 0)."""
+    a = np.abs(np.asarray(y, dtype=np.float64))
+    out = np.empty_like(a)
+    small = a < 1e-2
+    s = a[small]
+    # series of log(sinh(y)/y) = y^2/6 - y^4/180 + y^6/2835
+    out[small] = s * s / 6.0 - s ** 4 / 180.0 + s ** 6 / 2835.0
+    b = a[~small]
+    out[~small] = b + np.log1p(-np.exp(-2.0 * b)) - LN2 - np.log(b)
+    return out
+
+
+def atanhc(w):
+    """atanh(w)/w for |w| < 1 (1 at w = 0)."""
+    w = np.asarray(w, dtype=np.float64)
+    out = np.empty_like(w)
+    small = np.abs(w) < 1e-3
+    s = w[small]
+    out[small] = 1.0 + s * s / 3.0 + s ** 4 / 5.0
+    b = w[~small]
+    out[~small] = np.arctanh(b) / b
+    return out
+
+
+def z0_of(eps, mu, beta, n):
+    """z0 = 2 x0 - 1 = -beta (eps - mu) / 2^(n+1), from X0 of Eq. (Rec_F_2)."""
+    return -beta * (np.asarray(eps) - mu) / 2.0 ** (n + 1)
+
+
+# ----------------------------------------------------------------------------
+# occupation functions (eigenvalue -> occupation)
+# ----------------------------------------------------------------------------
+
+def occupation(eps, mu, beta, n: Optional[int] = None):
+    """Occupation of levels eps.
+
+    n is None: Fermi-Dirac 1/(exp(beta (eps - mu)) + 1), Eq. (Rec_F_1).
+    n given:   the closed form of n steps of Eq. (Rec_F_2) (Appendix A),
+               1/2 [1 + tanh(2^n atanh z0)].
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    if n is None:
+        return 0.5 * (1.0 - np.tanh(0.5 * beta * (eps - mu)))
+    z0 = z0_of(eps, mu, beta, n)
+    if np.any(np.abs(z0) >= 1.0):
+        raise ValueError("|z0| >= 1: beta * spread too large for this number of steps")
+    return 0.5 * (1.0 + np.tanh(2.0 ** n * np.arctanh(z0)))
+
+
+def occupation_derivative(eps, mu, beta, n: Optional[int] = None):
+    """d occupation / d eps.
+
+    Fermi-Dirac: -beta f (1 - f). Recursion (n steps): -beta g (1 - g) / (1 - z0^2),
+    the chain rule through atanh of the closed form.
+    """
+    f = occupation(eps, mu, beta, n)
+    d = -beta * f * (1.0 - f)
+    if n is not None:
+        z0 = z0_of(eps, mu, beta, n)
+        d = d / (1.0 - z0 * z0)
+    return d
+
+
+def divided_differences(eps, mu, beta, n: Optional[int] = None):
+    """Matrix F_ij = (f(e_i) - f(e_j)) / (e_i - e_j), with F_ii = f'(e_i).
+
+    Evaluated in closed form, never as a raw quotient, so that degenerate and
+    nearly degenerate levels are exact:
+
+    * Fermi-Dirac, x = beta (e - mu)/2:  tanh(x_a) - tanh(x_b) =
+      sinh(x_a - x_b) / (cosh x_a cosh x_b), hence
+      F = -(beta/4) sinhc(y) sech(x_a) sech(x_b),  y = beta (a - b)/2.
+    * Recursion, u = 2^n atanh(z):  with w = (z_a - z_b)/(1 - z_a z_b),
+      u_a - u_b = 2^n atanh(w), hence
+      F = -(beta/4) sinhc(u_a - u_b) atanhc(w) / (1 - z_a z_b) sech(u_a) sech(u_b).
+    """
+    e = np.asarray(eps, dtype=np.float64)
+    a = e[:, None]
+    b = e[None, :]
+    if n is None:
+        xa = 0.5 * beta * (a - mu)
+        xb = 0.5 * beta * (b - mu)
+        y = 0.5 * beta * (a - b)
+        logv = log_sinhc(y) - logcosh(xa) - logcosh(xb)
+        return -0.25 * beta * np.exp(logv)
+    za = z0_of(a, mu, beta, n)
+    zb = z0_of(b, mu, beta, n)
+    ua = 2.0 ** n * np.arctanh(za)
+    ub = 2.0 ** n * np.arctanh(zb)
+    den = 1.0 - za * zb
+    w = (za - zb) / den
+    du = 2.0 ** n * np.arctanh(w)
+    logv = log_sinhc(du) - logcosh(ua) - logcosh(ub)
+    return -0.25 * beta * atanhc(w) / den * np.exp(logv)
+
+
+# ----------------------------------------------------------------------------
+# chemical potential
+# ----------------------------------------------------------------------------
+
+def mu_bracket(eps, beta, n: Optional[int] = None):
+    lo, hi = float(np.min(eps)), float(np.max(eps))
+    if n is None:
+        pad = 40.0 / beta
+    else:
+        # keep |z0| < 1 over the whole spectrum for every mu in the bracket
+        room = 2.0 ** (n + 1) / beta - (hi - lo)
+        if room <= 0:
+            raise ValueError("beta * spectral width exceeds 2^(n+1): X0 leaves [0, 1]")
+        pad = min(40.0 / beta, 0.49 * room)
+    return lo - pad, hi + pad
+
+
+def find_mu(eps, nocc, beta, n: Optional[int] = None, iters: int = 200):
+    """mu with sum_i occupation(e_i) = nocc, by bisection (Tr P0 rises with mu)."""
+    lo, hi = mu_bracket(eps, beta, n)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if np.sum(occupation(eps, mid, beta, n)) > nocc:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+# ----------------------------------------------------------------------------
+# free energy, Eqs. (FreeE), (SED)
+# ----------------------------------------------------------------------------
+
+def free_energy_levels(eps, occ, beta):
+    """Omega = sum_i occ_i eps_i + (1/beta) sum_i [occ ln occ + (1-occ) ln(1-occ)]."""
+    occ = np.asarray(occ, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = np.where(occ > 0, occ * np.log(np.where(occ > 0, occ, 1.0)), 0.0)
+        t2 = np.where(occ < 1, (1 - occ) * np.log1p(-np.where(occ < 1, occ, 0.0)), 0.0)
+    return float(np.sum(occ * eps) + (t1 + t2).sum() / beta)
+
+
+# ----------------------------------------------------------------------------
+# full reference solve
+# ----------------------------------------------------------------------------
+
+def solve(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec",
+          canonical: bool = True, mu: Optional[float] = None):
+    """Exact P0, P1, mu, mu1, alpha and Omega.
+
+    H0: (N, N) symmetric. H1: (D, N, N) or (N, N) symmetric; P1 is always
+    returned as (D, N, N). kind "rec" uses
+    the n-step recursion function (requires n), "fd" the Fermi-Dirac function.
+    canonical=False keeps mu1 = 0 (grand-canonical response). mu may be given
+    to skip the occupation search.
+    """
+    H0 = np.asarray(H0, dtype=np.float64)
+    H1 = np.asarray(H1, dtype=np.float64)
+    if H1.ndim == 2:
+        H1 = H1[None]
+    nn = n if kind == "rec" else None
+    if kind == "rec" and n is None:
+        raise ValueError("kind='rec' needs n")
+    eps, V = np.linalg.eigh(H0)
+    if mu is None:
+        mu = find_mu(eps, nocc, beta, nn)
+    occ = occupation(eps, mu, beta, nn)
+    P0 = (V * occ) @ V.T
+    F = divided_differences(eps, mu, beta, nn)
+    fprime = np.diag(F).copy()
+    P1 = np.empty_like(H1)
+    mu1 = np.zeros(H1.shape[0])
+    alpha = np.zeros(H1.shape[0])
+    for d in range(H1.shape[0]):
+        h = V.T @ H1[d] @ V
+        if canonical:
+            mu1[d] = float(np.dot(fprime, np.diag(h)) / np.sum(fprime))
+        he = h - mu1[d] * np.eye(h.shape[0])
+        P1[d] = V @ (F * he) @ V.T
+        alpha[d] = -2.0 * float(np.sum(P1[d] * H1[d]))
+    # Q = dP0/dmu (exact for the chosen function): V diag(-f') V^T
+    Q = (V * (-fprime)) @ V.T
+    out = dict(P0=P0, P1=P1, mu=float(mu), mu1=mu1, alpha=alpha, eps=eps, occ=occ,
+               Q=Q, omega=free_energy_levels(eps, occ, beta))
+    return out
+
+
+def rel_frobenius(A, B):
+    """||A - B||_F / ||B||_F (the error measure used for every parity check)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    nb = np.linalg.norm(B)
+    return float(np.linalg.norm(A - B) / (nb if nb > 0 else 1.0))
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1 restated in the paper's X-notation (first order), dense solves
+# ----------------------------------------------------------------------------
+
+def literal_recursion(H0, H1, beta, mu, mu1, M):
+    """One pass of the inner loop of Algorithm 1 for orders 0 and 1.
+
+    X_0^(0) = I/2 - 2^-(M+2) beta (H0 - mu I);  X_0^(1) = -2^-(M+2) beta (H1 - mu1 I).
+    For n = 1..M:  T X_n^(0) = C^(0),  T X_n^(1) = C^(1) + B^(1) X_n^(0), with
+    T = 2 X^(0) (X^(0) - I) + I,  C^(0) = X^(0) X^(0),
+    C^(1) = X^(0) X^(1) + X^(1) X^(0),  B^(1) = 2 (X^(1) - C^(1)),
+    all taken at step n-1. Returns (X_M^(0), X_M^(1), condition numbers of T).
+    """
+    N = H0.shape[0]
+    I = np.eye(N)
+    s = 2.0 ** (-(M + 2)) * beta
+    X0 = 0.5 * I - s * (H0 - mu * I)
+    X1 = -s * (H1 - mu1 * I)
+    conds = []
+    for _ in range(M):
+        T = 2.0 * X0 @ (X0 - I) + I
+        C0 = X0 @ X0
+        C1 = X0 @ X1 + X1 @ X0
+        B1 = 2.0 * (X1 - C1)
+        ev = np.linalg.eigvalsh(0.5 * (T + T.T))
+        conds.append(float(ev[-1] / ev[0]))
+        X0n = np.linalg.solve(T, C0)
+        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
+        X0, X1 = X0n, X1n
+    return X0, X1, conds
+
+
+def literal_canonical(H0, H1, beta, nocc, M, mu0=0.0, tol=1e-9, maxit=100):
+    """The outer loop of Algorithm 1 (orders 0 and 1) with P_mu = beta P0 (I - P0).
+
+    mu  <- mu  + (N_occ - Tr P0) / Tr P_mu
+    mu1 <- mu1 - Tr P1 / Tr P_mu
+    until |Tr P0 - N_occ| + |Tr P1| <= tol.
+    """
+    mu, mu1 = float(mu0), 0.0
+    for it in range(maxit):
+        P0, P1, _ = literal_recursion(H0, H1, beta, mu, mu1, M)
+        tr0 = np.trace(P0)
+        tr1 = np.trace(P1)
+        err = abs(tr0 - nocc) + abs(tr1)
+        if err <= tol:
+            return P0, P1, mu, mu1, it
+        trPmu = beta * np.trace(P0 @ (np.eye(P0.shape[0]) - P0))
+        mu = mu + (nocc - tr0) / trPmu
+        mu1 = mu1 - tr1 / trPmu
+    raise RuntimeError("Algorithm 1 occupation loop did not converge")
+
+
+def pade_f(x, m):
+    """f_m(x) = x^m / (x^m + (1 - x)^m), Appendix A."""
+    return x ** m / (x ** m + (1.0 - x) ** m)
+
+
+def entropy_coefficients():
+    """Table 1 (Eq. S_Approx) coefficients c_i(m) for m = 1, 2, 4, as printed."""
+    return {
+        1: [4 * LN2],
+        2: [8 * LN2 - 2, 16 * LN2 - 8],
+        4: [16 * LN2 - 34 / 5, 96 * LN2 - 844 / 15, 256 * LN2 - 2336 / 15, 256 * LN2 - 2368 / 15],
+    }

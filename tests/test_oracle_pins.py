@@ -1,0 +1,322 @@
+"""Pins for the FP64 oracle: checks against things other than the oracle itself.
+
+Each test ties one oracle function to an independent fact: a different
+algorithm (matrix exponential, Algorithm 1 with dense solves, finite
+differences), an identity stated or implied by the paper, or a printed
+constant. A dropped term, a wrong sign or index, or a transposed operand in
+the oracle fails at least one of these.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as o
+import synthetic as syn
+
+GOLDEN = __file__.rsplit("/", 1)[0] + "/golden"
+
+
+def _rand_sym(N, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(N, N)) * scale
+    return 0.5 * (A + A.T)
+
+
+def _dimer_chain(N=16, t1=-1.0, t2=-0.4):
+    """Gapped chain (alternating hopping), gap ~ 2|t1 - t2| at half filling."""
+    H = np.zeros((N, N))
+    for i in range(N - 1):
+        H[i, i + 1] = H[i + 1, i] = t1 if i % 2 == 0 else t2
+    x = np.arange(N) - (N - 1) / 2.0
+    return H, np.diag(x)
+
+
+# --------------------------------------------------------------------------
+# P0 and mu: Eq. (Rec_F_1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("beta", [0.7, 3.0, 8.0])
+def test_p0_fd_equals_matrix_exponential(beta):
+    """Fermi-Dirac P0 from eigenvalues == [expm(beta(H - mu I)) + I]^-1 (no eigensolver)."""
+    H = _rand_sym(9, 11, 0.4)
+    r = o.solve(H, H, beta, 4.0, kind="fd")
+    N = H.shape[0]
+    E = scipy.linalg.expm(beta * (H - r["mu"] * np.eye(N)))
+    P_ref = np.linalg.inv(E + np.eye(N))
+    assert o.rel_frobenius(r["P0"], P_ref) < 1e-11
+
+
+def test_p0_rec_equals_matrix_power_pade():
+    """Recursion P0 == f_{2^n}(X0) evaluated with matrix powers and one inverse (App. A)."""
+    H = _rand_sym(7, 5, 0.5)
+    beta, n, mu = 4.0, 4, 0.1
+    X0 = 0.5 * np.eye(7) - 2.0 ** (-(n + 2)) * beta * (H - mu * np.eye(7))
+    m = 2 ** n
+    Xm = np.linalg.matrix_power(X0, m)
+    Ym = np.linalg.matrix_power(np.eye(7) - X0, m)
+    P_ref = np.linalg.solve(Xm + Ym, Xm)
+    r = o.solve(H, H, beta, 3.5, n=n, kind="rec", mu=mu)
+    assert o.rel_frobenius(r["P0"], P_ref) < 1e-11
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 12)])
+def test_trace_symmetry_spectrum(kind, n):
+    p = syn.workload("chain64")
+    r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=n, kind=kind)
+    assert abs(np.trace(r["P0"]) - p.nocc) < 1e-10
+    assert np.allclose(r["P0"], r["P0"].T, atol=1e-14)
+    ev = np.linalg.eigvalsh(r["P0"])
+    assert ev.min() > -1e-12 and ev.max() < 1 + 1e-12
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1, first order: closed form vs the printed iteration
+# --------------------------------------------------------------------------
+
+def test_closed_form_equals_literal_recursion():
+    """P0, P1 of kind='rec' == Algorithm 1 (X-notation, dense solves) at the same mu, mu1."""
+    p = syn.workload("chain64")
+    r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    X0, X1, conds = o.literal_recursion(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], p.n)
+    assert o.rel_frobenius(X0, r["P0"]) < 1e-12
+    assert o.rel_frobenius(X1, r["P1"][0]) < 1e-11
+    # T is SPD with spectral condition number <= 2 at every step (Sec. II)
+    assert max(conds) <= 2.0 + 1e-12 and min(conds) >= 1.0
+
+
+def test_literal_canonical_loop_fixed_point():
+    """Algorithm 1's Newton loop with P_mu = beta P(I-P) reaches the closed-form mu, mu1."""
+    H0, H1 = _dimer_chain(24)
+    beta, nocc, n = 6.0, 12.0, 8
+    r = o.solve(H0, H1, beta, nocc, n=n, kind="rec")
+    P0, P1, mu, mu1, it = o.literal_canonical(H0, H1, beta, nocc, n, mu0=0.3)
+    assert abs(mu - r["mu"]) < 1e-11
+    assert abs(mu1 - r["mu1"][0]) < 1e-9
+    assert o.rel_frobenius(P1, r["P1"][0]) < 1e-10
+
+
+def test_composition_rule_scalars():
+    """f_{m n} = f_m o f_n (App. A) and n steps of f_2 == the tanh/atanh closed form."""
+    x = np.linspace(0.02, 0.98, 41)
+    for m, k in ((2, 3), (3, 2), (2, 2)):
+        assert np.allclose(o.pade_f(o.pade_f(x, k), m), o.pade_f(x, m * k), rtol=1e-12, atol=1e-15)
+    beta, n, mu = 10.0, 5, 0.0
+    eps = np.linspace(-2.0, 2.0, 33)
+    x0 = 0.5 - beta * (eps - mu) / 2.0 ** (n + 2)
+    y = x0.copy()
+    for _ in range(n):
+        y = o.pade_f(y, 2)
+    assert np.allclose(o.occupation(eps, mu, beta, n), y, rtol=1e-13, atol=1e-15)
+
+
+def test_truncation_gap_follows_effective_exponent():
+    """g_n(t) = FD(t + t^3/(12 4^n) + O(t^5/4^2n)): the linear X0 stretches the exponent."""
+    beta, n = 20.0, 8
+    eps = np.linspace(-1.0, 1.0, 51)
+    t = beta * eps
+    g = o.occupation(eps, 0.0, beta, n)
+    f_plain = o.occupation(eps, 0.0, beta, None)
+    t_eff = t + t ** 3 / (12.0 * 4.0 ** n)
+    f_eff = 0.5 * (1.0 - np.tanh(0.5 * t_eff))
+    gap = np.max(np.abs(g - f_plain))
+    assert gap > 1e-6
+    assert np.max(np.abs(g - f_eff)) < 1e-3 * gap
+
+
+# --------------------------------------------------------------------------
+# P1, mu1: canonical response (Eqs. P_resp, H_prt, NewtRaphs)
+# --------------------------------------------------------------------------
+
+def _canonical_P0(H0, H1, lam, beta, nocc, n, kind):
+    return o.solve(H0 + lam * H1, H1, beta, nocc, n=n, kind=kind)
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_p1_equals_five_point_finite_difference(kind, n):
+    """P1 == dP0/dlambda of P0(H0 + lambda H1) with mu(lambda) re-fitted (5-point stencil)."""
+    H0 = _rand_sym(10, 3)
+    H1 = np.diag(np.arange(10) - 4.5)
+    beta, nocc, h = 2.0, 5.0, 1e-3
+    r = o.solve(H0, H1, beta, nocc, n=n, kind=kind)
+    P = {k: _canonical_P0(H0, H1, k * h, beta, nocc, n, kind)["P0"] for k in (-2, -1, 1, 2)}
+    fd = (P[-2] - 8 * P[-1] + 8 * P[1] - P[2]) / (12 * h)
+    assert o.rel_frobenius(r["P1"][0], fd) < 1e-8
+    mus = {k: _canonical_P0(H0, H1, k * h, beta, nocc, n, kind)["mu"] for k in (-2, -1, 1, 2)}
+    dmu = (mus[-2] - 8 * mus[-1] + 8 * mus[1] - mus[2]) / (12 * h)
+    assert abs(r["mu1"][0] - dmu) < 1e-8 * max(1.0, abs(dmu))
+
+
+def test_p1_traceless_symmetric_and_shift_invariant():
+    p = syn.workload("chain64")
+    r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    P1 = r["P1"][0]
+    assert abs(np.trace(P1)) < 1e-10 * np.abs(P1).max() * p.N
+    assert np.allclose(P1, P1.T, atol=1e-13 * np.abs(P1).max())
+    r2 = o.solve(p.H0, p.H1 + 3.7 * np.eye(p.N), p.beta, p.nocc, n=p.n, kind="rec")
+    assert o.rel_frobenius(r2["P1"][0], P1) < 1e-12
+    # alpha = -2 Tr(P1 H1) is unchanged by the shift since Tr P1 = 0
+    assert abs(r2["alpha"][0] - r["alpha"][0]) < 1e-9 * abs(r["alpha"][0])
+
+
+def test_alpha_positive_and_canonical_below_grand_canonical():
+    p = syn.workload("chain64")
+    c = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    g = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", canonical=False)
+    assert c["alpha"][0] > 0
+    assert c["alpha"][0] <= g["alpha"][0] + 1e-9
+
+
+def test_Q_equals_dP0_dmu():
+    """Q returned by the oracle == central difference of P0 in mu (rec kind, exact at finite n)."""
+    H0 = _rand_sym(8, 21)
+    beta, n, mu, h = 3.0, 6, 0.2, 1e-4
+    r = o.solve(H0, H0, beta, 4.0, n=n, kind="rec", mu=mu)
+    Pp = o.solve(H0, H0, beta, 4.0, n=n, kind="rec", mu=mu + h)["P0"]
+    Pm = o.solve(H0, H0, beta, 4.0, n=n, kind="rec", mu=mu - h)["P0"]
+    assert o.rel_frobenius(r["Q"], (Pp - Pm) / (2 * h)) < 1e-7
+
+
+def test_zero_temperature_limit():
+    """beta -> infinity on a gapped chain: P0 idempotent and P1 = P0 P1 + P1 P0."""
+    H0, H1 = _dimer_chain(16)
+    r = o.solve(H0, H1, 400.0, 8.0, kind="fd")
+    P0, P1 = r["P0"], r["P1"][0]
+    assert np.abs(P0 @ P0 - P0).max() < 1e-12
+    assert o.rel_frobenius(P0 @ P1 + P1 @ P0, P1) < 1e-10
+
+
+def test_degenerate_levels_are_finite():
+    """Clean periodic lattice (highly degenerate spectrum): divided differences stay exact."""
+    p = syn.cubic_lattice((4, 4, 4), seed=7, onsite_sigma=0.0, bond_disorder=0.0, beta=5.0, n=10)
+    r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    assert np.all(np.isfinite(r["P1"]))
+    h = 1e-4
+    Pp = o.solve(p.H0 + h * p.H1[0], p.H1, p.beta, p.nocc, n=p.n, kind="rec")["P0"]
+    Pm = o.solve(p.H0 - h * p.H1[0], p.H1, p.beta, p.nocc, n=p.n, kind="rec")["P0"]
+    assert o.rel_frobenius(r["P1"][0], (Pp - Pm) / (2 * h)) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# free energy: Eqs. (FreeE), (SED), (Resp_0), (EntDer)
+# --------------------------------------------------------------------------
+
+def _omega(H0, H1, lam, beta, nocc):
+    return o.solve(H0 + lam * H1, H1, beta, nocc, kind="fd")["omega"]
+
+
+def test_n_plus_one_rule_first_and_second_order():
+    """Omega^(1) = Tr[H1 P0] and Omega^(2) = 1/2 Tr[H1 P1] (Eq. Resp_0, H^(2) = 0)."""
+    H0 = _rand_sym(10, 8)
+    H1 = _rand_sym(10, 9, 0.3)
+    beta, nocc, h = 3.0, 4.0, 1e-3
+    r = o.solve(H0, H1, beta, nocc, kind="fd")
+    w = {k: _omega(H0, H1, k * h, beta, nocc) for k in (-2, -1, 0, 1, 2)}
+    d1 = (w[-2] - 8 * w[-1] + 8 * w[1] - w[2]) / (12 * h)
+    d2 = (-w[-2] + 16 * w[-1] - 30 * w[0] + 16 * w[1] - w[2]) / (12 * h * h)
+    assert abs(d1 - np.sum(H1 * r["P0"])) < 1e-9
+    omega2 = 0.5 * np.sum(H1 * r["P1"][0])
+    assert abs(0.5 * d2 - omega2) < 1e-5 * abs(omega2)
+
+
+def test_free_energy_gradient_is_P0():
+    """dOmega/dH0 along any symmetric direction E is Tr[P0 E] (App. B, canonical)."""
+    H0 = _rand_sym(9, 31)
+    beta, nocc, h = 5.0, 3.0, 1e-4
+    r = o.solve(H0, H0, beta, nocc, kind="fd")
+    for s in range(3):
+        E = _rand_sym(9, 100 + s)
+        d = (_omega(H0, E, h, beta, nocc) - _omega(H0, E, -h, beta, nocc)) / (2 * h)
+        assert abs(d - np.sum(r["P0"] * E)) < 1e-7
+
+
+def test_entropy_derivative_identity():
+    """Eq. (EntDer): ln(P (I-P)^-1) = -beta (H - mu I) for the Fermi-Dirac P0."""
+    H0 = _rand_sym(8, 41)
+    beta = 2.5
+    r = o.solve(H0, H0, beta, 3.0, kind="fd")
+    P = r["P0"]
+    L = scipy.linalg.logm(P @ np.linalg.inv(np.eye(8) - P)).real
+    assert o.rel_frobenius(L, -beta * (H0 - r["mu"] * np.eye(8))) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Table 1 constants (Eq. S_Approx, exponent i; see the readings)
+# --------------------------------------------------------------------------
+
+def _golden_tab1():
+    rows = {}
+    for line in open(f"{GOLDEN}/tab1_entropy_coefficients.txt"):
+        if line.startswith("#") or not line.strip():
+            continue
+        m, i, a, b = line.split()
+        rows.setdefault(int(m), []).append((int(a), Fraction(b)))
+    return rows
+
+
+def test_table1_coefficients_match_golden():
+    gold = _golden_tab1()
+    coef = o.entropy_coefficients()
+    for m, lst in gold.items():
+        for (a, b), c in zip(lst, coef[m]):
+            assert abs(c - (a * math.log(2) + float(b))) < 1e-13
+
+
+def test_table1_coefficients_match_entropy_at_half():
+    """s_m(x) = -sum_i c_i (x(x-1))^i matches s(x) = -x ln x - (1-x) ln(1-x) and its even
+    derivatives at x = 1/2 up to order 2(m-1): the construction stated in Table 1's caption."""
+    sp = pytest.importorskip("sympy")
+    x = sp.symbols("x")
+    s = -x * sp.log(x) - (1 - x) * sp.log(1 - x)
+    for m, lst in _golden_tab1().items():
+        c = [a * sp.log(2) + sp.Rational(b.numerator, b.denominator) for a, b in lst]
+        sm = -sum(ci * (x * (x - 1)) ** (i + 1) for i, ci in enumerate(c))
+        for k in range(0, 2 * m - 1, 2):
+            lhs = sp.diff(sm, x, k).subs(x, sp.Rational(1, 2))
+            rhs = sp.diff(s, x, k).subs(x, sp.Rational(1, 2))
+            assert sp.simplify(lhs - rhs) == 0, (m, k)
+
+
+def test_chain64_golden_regression():
+    """The oracle still reproduces the stored chain64 values written by make_golden.py."""
+    import json
+    g = json.load(open(f"{GOLDEN}/chain64_oracle.json"))
+    p = syn.workload("chain64")
+    for kind, n in (("rec", p.n), ("fd", None)):
+        r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=n, kind=kind)
+        ref = g[kind]
+        assert abs(r["mu"] - ref["mu"]) < 1e-12
+        assert abs(r["mu1"][0] - ref["mu1"]) < 1e-10 * max(1, abs(ref["mu1"]))
+        assert abs(r["alpha"][0] - ref["alpha"]) < 1e-10 * abs(ref["alpha"])
+        assert np.allclose(np.diag(r["P0"])[:8], ref["P0_diag_head"], rtol=0, atol=1e-12)
+
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Plant typical slips in the oracle (CPU only) and check a pin notices each one."""
+    H0 = _rand_sym(10, 3)
+    H1 = np.diag(np.arange(10) - 4.5)
+    beta, nocc, h = 2.0, 5.0, 1e-3
+
+    def fd_error():
+        r = o.solve(H0, H1, beta, nocc, kind="fd")
+        P = {k: o.solve(H0 + k * h * H1, H1, beta, nocc, kind="fd")["P0"] for k in (-2, -1, 1, 2)}
+        fd = (P[-2] - 8 * P[-1] + 8 * P[1] - P[2]) / (12 * h)
+        return o.rel_frobenius(r["P1"][0], fd)
+
+    assert fd_error() < 1e-8
+    real_dd = o.dmpt_oracle.divided_differences
+    # wrong sign of the divided differences
+    monkeypatch.setattr(o.dmpt_oracle, "divided_differences", lambda *a, **k: -real_dd(*a, **k))
+    assert fd_error() > 1e-3
+    # dropped off-diagonal (only the diagonal f' kept)
+    monkeypatch.setattr(o.dmpt_oracle, "divided_differences",
+                        lambda *a, **k: np.diag(np.diag(real_dd(*a, **k))))
+    assert fd_error() > 1e-3
+    monkeypatch.setattr(o.dmpt_oracle, "divided_differences", real_dd)
+    # wrong temperature scaling in the occupation (beta/2 slip)
+    real_occ = o.dmpt_oracle.occupation
+    monkeypatch.setattr(o.dmpt_oracle, "occupation",
+                        lambda e, mu, b, n=None: real_occ(e, mu, 0.5 * b, n))
+    assert fd_error() > 1e-3
