@@ -1,0 +1,197 @@
+/*
+ * cdmpt.h - C ABI of the GB300 (sm_103a) canonical density matrix
+ * perturbation theory library (libcdmpt.so).
+ *
+ * The library evaluates, on one GPU, the hot path of canonical density
+ * matrix perturbation theory (Niklasson, Rubensson, Rudberg, Cawkwell):
+ *
+ *   - the recursive Fermi-operator expansion, Eq. (Rec_F_2):
+ *       X_0 = I/2 - 2^-(n+2) beta (H0 - mu I),
+ *       X_k = X_{k-1}^2 [X_{k-1}^2 + (I - X_{k-1})^2]^-1,  k = 1..n,
+ *     each step a linear solve T X_k = X_{k-1}^2 with
+ *     T = 2 X_{k-1}(X_{k-1} - I) + I, by conjugate gradients warm-started
+ *     from the previous iterate (Sec. II, Algorithm 1);
+ *   - the first-order response X^(1) carried through every step with the
+ *     same system matrix T (Algorithm 1, order 1);
+ *   - the canonical constraint Tr P0 = N_occ on mu (Newton steps on the
+ *     occupation, Eq. NewtRaphs) and Tr P1 = 0 on mu1 (Sec. II);
+ *   - the polarizability alpha = -2 Tr[P1 H1] (the n+1 rule, Eq. Resp_0).
+ *
+ * Internally the recursion runs on the deviation Z = 2X - I, for which a
+ * step is Z_{k+1} = 2 (I + Z_k^2)^-1 Z_k; P0 = (I + Z_n)/2, P1 = Z^(1)_n / 2.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense, row-major, symmetric, N x N with leading
+ *     dimension N unless an ld argument says otherwise. Stacks of D
+ *     matrices are contiguous, D * N * N.
+ *   - Device pointers are CUDA global-memory addresses on the current
+ *     device. Host pointers are ordinary CPU memory.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps. The handle owns its device workspace and frees it in
+ *     cdmpt_destroy.
+ *   - Every call returns a cdmpt_status; no C++ exception crosses the ABI.
+ *     On failure cdmpt_last_error() describes the cause.
+ *   - A handle is not thread-safe: use it from one host thread and one
+ *     CUDA stream at a time.
+ */
+#ifndef CDMPT_H
+#define CDMPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDMPT_VERSION_MAJOR 0
+#define CDMPT_VERSION_MINOR 1
+
+typedef enum {
+    CDMPT_OK = 0,
+    CDMPT_ERR_ARG = 1,            /* invalid argument (size, pointer, symmetry) */
+    CDMPT_ERR_RANGE = 2,          /* beta * spectral width / 2^(n+1) >= 1: X_0 leaves [0,1] */
+    CDMPT_ERR_NO_CONVERGENCE = 3, /* occupation (mu) loop did not converge */
+    CDMPT_ERR_CG_MAXITER = 4,     /* a conjugate-gradient solve hit its iteration cap */
+    CDMPT_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    CDMPT_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+    CDMPT_ERR_OOM = 7,            /* device allocation failed */
+    CDMPT_ERR_UNSUPPORTED = 8     /* feature not available on this device / build */
+} cdmpt_status;
+
+typedef enum {
+    CDMPT_FP64 = 0,       /* FP64 storage, FP64 products (CUDA-core DFMA) */
+    CDMPT_FP32 = 1,       /* FP32 storage, FP32-accurate products (3xTF32 on tcgen05 by default) */
+    CDMPT_MIXED_TF32 = 2, /* TF32 products for the occupation sweeps and response,
+                             FP32-accurate residual refinement of the trajectory */
+    CDMPT_MIXED_BF16 = 3  /* reserved: BF16 products + refinement */
+} cdmpt_precision;
+
+typedef enum {
+    CDMPT_GEMM_AUTO = 0,      /* engine chosen from the precision */
+    CDMPT_GEMM_SIMT = 1,      /* CUDA-core FFMA/DFMA tiles */
+    CDMPT_GEMM_TC_TF32 = 2,   /* tcgen05 kind::tf32, one pass, FP32 accumulate in TMEM */
+    CDMPT_GEMM_TC_3XTF32 = 3  /* tcgen05 kind::tf32, hi/lo split, three passes */
+} cdmpt_gemm_engine;
+
+typedef struct {
+    int precision;      /* cdmpt_precision */
+    int gemm_engine;    /* cdmpt_gemm_engine for FP32 storage; ignored for FP64 */
+    double cg_tol;      /* CG stop: ||R||_F <= cg_tol * ||RHS||_F; <= 0 selects the default */
+    int cg_maxit;       /* CG iteration cap per solve */
+    int refine_rounds;  /* residual-refinement rounds (MIXED_* only) */
+    double occ_tol;     /* stop when |Tr P0 - N_occ| <= occ_tol; <= 0 selects N * 1e-12 (FP64)
+                           or N * 1e-7 (otherwise) */
+    int mu_maxit;       /* cap on occupation sweeps */
+    int have_mu_guess;  /* 1: start Newton from mu_guess; 0: start from Tr(H0)/N */
+    double mu_guess;
+    int profile;        /* 1: time every GEMM launch with CUDA events (see cdmpt_stats) */
+    void* stream;       /* cudaStream_t for all work of this handle; NULL = default stream */
+} cdmpt_opts;
+
+typedef struct {
+    int N, D, n;                   /* sizes of the last solve */
+    int mu_iterations;             /* occupation sweeps (0th-order recursions) */
+    int cg_iterations_sweeps;      /* CG iterations summed over all sweeps */
+    int cg_iterations_last_sweep;  /* CG iterations of the final sweep */
+    int cg_iterations_response;    /* CG iterations of the response pass */
+    int cg_iterations_q;           /* CG iterations of the dP/dmu solve */
+    int cg_iterations_refine;      /* CG iterations of the refinement */
+    int gemm_launches;             /* GEMM kernel launches */
+    int kernel_launches;           /* all kernel launches of this library */
+    double gemm_flops;             /* algorithmic GEMM flops, sum of 2 M N K */
+    double tensor_flops;           /* flops issued to the tensor pipe (split passes counted) */
+    double gemm_ms;                /* summed GEMM device time (profile = 1 only) */
+    int gemm_timed;                /* GEMM launches that were timed */
+    double mu, trace_P0, trace_Q;  /* final mu, Tr P0, Tr dP0/dmu */
+    double occupation_error;       /* |Tr P0 - N_occ| + sum_d |Tr P1_d| */
+    double seconds;                /* host wall time of the last solve */
+} cdmpt_stats;
+
+typedef struct cdmpt_handle cdmpt_handle;
+
+/* Library version as (major << 16) | minor. */
+int cdmpt_version(void);
+
+/* Fill *opts with defaults: FP32 precision, automatic engine, cg_tol 1e-7
+ * (FP32) / 1e-13 (FP64), cg_maxit 200, refine_rounds 2, mu_maxit 60,
+ * profile 0, default stream. Returns CDMPT_ERR_ARG if opts is NULL. */
+cdmpt_status cdmpt_default_opts(cdmpt_opts* opts);
+
+/* Create a handle bound to the current CUDA device. opts may be NULL for
+ * defaults; the struct is copied. *out receives the handle.
+ * Errors: ERR_ARG (out NULL, bad precision/engine), ERR_UNSUPPORTED (a
+ * tcgen05 engine on a device that is not sm_103), ERR_CUDA. */
+cdmpt_status cdmpt_create(const cdmpt_opts* opts, cdmpt_handle** out);
+
+/* Replace the options of an existing handle (stream, tolerances, precision). */
+cdmpt_status cdmpt_set_opts(cdmpt_handle* h, const cdmpt_opts* opts);
+
+/* Load the unperturbed Hamiltonian H0 (N x N) and D >= 0 perturbations H1
+ * (D x N x N), Eq. (H_prt) with H^(1) = H1, in an orthogonal basis (Sec. II).
+ * on_device = 0: host pointers; 1: device pointers. Both are copied into
+ * handle-owned FP64 device storage, so the caller may free them afterwards.
+ * Spectral bounds of H0 (Gershgorin discs) are computed on the device here.
+ * Errors: ERR_ARG (N < 1, D < 0, H0 NULL, H1 NULL with D > 0), ERR_OOM,
+ * ERR_CUDA. */
+cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const double* H1,
+                         int on_device);
+
+/* Canonical solve, Algorithm 1 to first order.
+ * beta > 0: inverse temperature; nocc in (0, N): occupation; n >= 1:
+ * recursion steps (M in the paper).
+ * Outputs (any may be NULL to skip): P0 (N x N), P1 (D x N x N) as FP64,
+ * host or device memory according to out_on_device; mu (1 double, host) and
+ * mu1 (D doubles, host). With D = 0 only P0 and mu are produced.
+ * Errors: ERR_ARG, ERR_RANGE (beta (lambda_max - lambda_min) / 2^(n+1) >= 1
+ * for the Gershgorin bounds), ERR_NO_CONVERGENCE (occupation not reached in
+ * mu_maxit sweeps), ERR_CG_MAXITER, ERR_TIMEOUT, ERR_CUDA, ERR_OOM. */
+cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, double* P0,
+                         double* P1, double* mu, double* mu1, int out_on_device);
+
+/* Polarizability alpha_d = -2 Tr[P1_d H1_d] of the last solve, for d < D,
+ * written to alpha (D doubles, host). This is -4 Omega^(2) of Eq. (Resp_0)
+ * with H^(2) = 0. Errors: ERR_ARG if no solve has completed. */
+cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
+
+/* Statistics of the last solve (copied into *st). */
+cdmpt_status cdmpt_get_stats(const cdmpt_handle* h, cdmpt_stats* st);
+
+/* Human-readable description of the last error of this handle ("" if none). */
+const char* cdmpt_last_error(const cdmpt_handle* h);
+
+/* Free the handle and all device memory it owns. NULL is ignored. */
+void cdmpt_destroy(cdmpt_handle* h);
+
+/*
+ * Dense building block exposed for testing and benchmarking: the product of
+ * one recursion step (Algorithm 1 forms every product X Y with Y symmetric).
+ *
+ *   D[m][n] = alpha * sum_k X[m][k] Y[n][k] + beta * C[m][n] + gamma * [m % diag_block == n]
+ *
+ * i.e. D = alpha X Y^T + beta C + gamma I_blocks, X: M x K, Y: Ncols x K, all
+ * row-major device arrays (leading dimensions in elements; for the tcgen05
+ * engines ldx and ldy must be multiples of 4 and X, Y 16-byte aligned).
+ * trans_block > 0 writes (and reads C at) the transposed position inside
+ * consecutive row blocks of height trans_block (requires Ncols == trans_block).
+ * dot != NULL accumulates sum_{m,n} D[m][n] * E[m][n] into *dot (device
+ * double; E NULL means E = D). C may alias D. Asynchronous on stream.
+ * engine: cdmpt_gemm_engine (AUTO = 3xTF32).
+ * Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA. */
+cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X, int ldx,
+                            const float* Y, int ldy, float* D, int ldd, double alpha,
+                            double beta, const float* C, int ldc, double gamma, int diag_block,
+                            int trans_block, double* dot, const float* E, int lde, void* stream);
+
+/* FP64 counterpart of cdmpt_gemm_f32 on CUDA cores (no alignment rule). */
+cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,
+                            int ldy, double* D, int ldd, double alpha, double beta,
+                            const double* C, int ldc, double gamma, int diag_block,
+                            int trans_block, double* dot, const double* E, int lde,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDMPT_H */

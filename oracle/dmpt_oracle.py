@@ -201,14 +201,15 @@ def free_energy_levels(eps, occ, beta):
 # ----------------------------------------------------------------------------
 
 def solve(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec",
-          canonical: bool = True, mu: Optional[float] = None):
+          canonical: bool = True, mu: Optional[float] = None, eig=None):
     """Exact P0, P1, mu, mu1, alpha and Omega.
 
     H0: (N, N) symmetric. H1: (D, N, N) or (N, N) symmetric; P1 is always
     returned as (D, N, N). kind "rec" uses
     the n-step recursion function (requires n), "fd" the Fermi-Dirac function.
     canonical=False keeps mu1 = 0 (grand-canonical response). mu may be given
-    to skip the occupation search.
+    to skip the occupation search. eig = (eps, V) reuses an eigendecomposition
+    of H0 computed by ``numpy.linalg.eigh``.
     """
     H0 = np.asarray(H0, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
@@ -217,7 +218,7 @@ def solve(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec",
     nn = n if kind == "rec" else None
     if kind == "rec" and n is None:
         raise ValueError("kind='rec' needs n")
-    eps, V = np.linalg.eigh(H0)
+    eps, V = np.linalg.eigh(H0) if eig is None else eig
     if mu is None:
         mu = find_mu(eps, nocc, beta, nn)
     occ = occupation(eps, mu, beta, nn)

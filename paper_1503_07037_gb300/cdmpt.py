@@ -1,0 +1,310 @@
+"""Thin ctypes binding of libcdmpt.so (include/cdmpt.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. PyTorch provides device memory (output tensors) and the current
+stream. The functions keep the C names without the ``cdmpt_`` prefix;
+``Handle`` and ``solve`` wrap them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcdmpt.so")
+
+FP64, FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
+GEMM_AUTO, GEMM_SIMT, GEMM_TC_TF32, GEMM_TC_3XTF32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_TF32, "mixed_tf32": MIXED_TF32,
+              "mixed_bf16": MIXED_BF16}
+ENGINES = {"auto": GEMM_AUTO, "simt": GEMM_SIMT, "tf32": GEMM_TC_TF32, "3xtf32": GEMM_TC_3XTF32}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_RANGE", 3: "ERR_NO_CONVERGENCE", 4: "ERR_CG_MAXITER",
+          5: "ERR_TIMEOUT", 6: "ERR_CUDA", 7: "ERR_OOM", 8: "ERR_UNSUPPORTED"}
+
+
+class CdmptError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("gemm_engine", ctypes.c_int),
+        ("cg_tol", ctypes.c_double),
+        ("cg_maxit", ctypes.c_int),
+        ("refine_rounds", ctypes.c_int),
+        ("occ_tol", ctypes.c_double),
+        ("mu_maxit", ctypes.c_int),
+        ("have_mu_guess", ctypes.c_int),
+        ("mu_guess", ctypes.c_double),
+        ("profile", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int), ("D", ctypes.c_int), ("n", ctypes.c_int),
+        ("mu_iterations", ctypes.c_int),
+        ("cg_iterations_sweeps", ctypes.c_int),
+        ("cg_iterations_last_sweep", ctypes.c_int),
+        ("cg_iterations_response", ctypes.c_int),
+        ("cg_iterations_q", ctypes.c_int),
+        ("cg_iterations_refine", ctypes.c_int),
+        ("gemm_launches", ctypes.c_int),
+        ("kernel_launches", ctypes.c_int),
+        ("gemm_flops", ctypes.c_double),
+        ("tensor_flops", ctypes.c_double),
+        ("gemm_ms", ctypes.c_double),
+        ("gemm_timed", ctypes.c_int),
+        ("mu", ctypes.c_double), ("trace_P0", ctypes.c_double), ("trace_Q", ctypes.c_double),
+        ("occupation_error", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opts", "cdmpt_set_H",
+           "cdmpt_solve", "cdmpt_polarizability", "cdmpt_get_stats", "cdmpt_last_error",
+           "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64"]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcdmpt.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1503_07037_gb300.build` (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    sig = {
+        "cdmpt_version": (I, []),
+        "cdmpt_default_opts": (I, [ctypes.POINTER(Opts)]),
+        "cdmpt_create": (I, [ctypes.POINTER(Opts), ctypes.POINTER(P)]),
+        "cdmpt_set_opts": (I, [P, ctypes.POINTER(Opts)]),
+        "cdmpt_set_H": (I, [P, I, P, I, P, I]),
+        "cdmpt_solve": (I, [P, D, D, I, P, P, P, P, I]),
+        "cdmpt_polarizability": (I, [P, P]),
+        "cdmpt_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+        "cdmpt_last_error": (ctypes.c_char_p, [P]),
+        "cdmpt_destroy": (V, [P]),
+        "cdmpt_gemm_f32": (I, [I, I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
+        "cdmpt_gemm_f64": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, h=None):
+    if status != 0:
+        msg = lib().cdmpt_last_error(h)
+        raise CdmptError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        if not torch.cuda.is_available():
+            return 0
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------- C-named wrappers
+
+def version() -> int:
+    return lib().cdmpt_version()
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    _check(lib().cdmpt_default_opts(ctypes.byref(o)))
+    return o
+
+
+def create(opts: Opts) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().cdmpt_create(ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def set_opts(h: int, opts: Opts):
+    _check(lib().cdmpt_set_opts(h, ctypes.byref(opts)), h)
+
+
+def set_H(h: int, N: int, H0_ptr: int, D: int, H1_ptr: Optional[int], on_device: int):
+    _check(lib().cdmpt_set_H(h, N, H0_ptr, D, H1_ptr, on_device), h)
+
+
+def solve_raw(h: int, beta, nocc, n, P0_ptr, P1_ptr, mu_ptr, mu1_ptr, out_on_device: int):
+    _check(lib().cdmpt_solve(h, float(beta), float(nocc), int(n), P0_ptr, P1_ptr, mu_ptr,
+                             mu1_ptr, out_on_device), h)
+
+
+def polarizability(h: int, D: int) -> np.ndarray:
+    a = np.zeros(max(D, 1))
+    _check(lib().cdmpt_polarizability(h, a.ctypes.data), h)
+    return a[:D]
+
+
+def get_stats(h: int) -> dict:
+    s = Stats()
+    _check(lib().cdmpt_get_stats(h, ctypes.byref(s)), h)
+    return s.as_dict()
+
+
+def last_error(h: int) -> str:
+    m = lib().cdmpt_last_error(h)
+    return m.decode() if m else ""
+
+
+def destroy(h: int):
+    lib().cdmpt_destroy(h)
+
+
+def gemm_f32(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, trans_block=0,
+             dot=None, E=None, engine="auto", M=None, Ncols=None, K=None, stream=None):
+    """D = alpha X Y^T + beta C + gamma I on torch CUDA float32 tensors (row-major)."""
+    M = X.shape[0] if M is None else M
+    K = X.shape[1] if K is None else K
+    Ncols = Y.shape[0] if Ncols is None else Ncols
+    eng = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    _check(lib().cdmpt_gemm_f32(eng, M, Ncols, K, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                                _ptr(D), D.stride(0), float(alpha), float(beta), _ptr(C),
+                                C.stride(0) if C is not None else 0, float(gamma), diag_block,
+                                trans_block, _ptr(dot), _ptr(E),
+                                E.stride(0) if E is not None else 0, _stream_ptr(stream)))
+
+
+def gemm_f64(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, trans_block=0,
+             dot=None, E=None, M=None, Ncols=None, K=None, stream=None):
+    """FP64 counterpart of gemm_f32 (CUDA cores)."""
+    M = X.shape[0] if M is None else M
+    K = X.shape[1] if K is None else K
+    Ncols = Y.shape[0] if Ncols is None else Ncols
+    _check(lib().cdmpt_gemm_f64(M, Ncols, K, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                                _ptr(D), D.stride(0), float(alpha), float(beta), _ptr(C),
+                                C.stride(0) if C is not None else 0, float(gamma), diag_block,
+                                trans_block, _ptr(dot), _ptr(E),
+                                E.stride(0) if E is not None else 0, _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------- convenience
+
+class Handle:
+    """Owns one cdmpt_handle. Inputs may be numpy arrays (host) or torch CUDA tensors."""
+
+    def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
+                 refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
+                 stream=None):
+        o = default_opts()
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.gemm_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+        o.cg_tol = cg_tol
+        o.cg_maxit = cg_maxit
+        o.refine_rounds = refine_rounds
+        o.occ_tol = occ_tol
+        o.mu_maxit = mu_maxit
+        o.have_mu_guess = 0 if mu_guess is None else 1
+        o.mu_guess = 0.0 if mu_guess is None else float(mu_guess)
+        o.profile = 1 if profile else 0
+        o.stream = _stream_ptr(stream)
+        self.opts = o
+        self.h = create(o)
+        self.N = 0
+        self.D = 0
+        self._keep = None
+
+    def set_H(self, H0, H1=None):
+        import torch
+        if H1 is None:
+            D = 0
+        else:
+            D = 1 if H1.ndim == 2 else H1.shape[0]
+        N = H0.shape[0]
+        if isinstance(H0, torch.Tensor):
+            H0c = H0.detach().to(torch.float64).contiguous()
+            H1c = None if H1 is None else H1.detach().to(torch.float64).contiguous()
+            on_dev = 1 if H0c.is_cuda else 0
+            if on_dev and H1c is not None and not H1c.is_cuda:
+                H1c = H1c.cuda()
+            p0 = H0c.data_ptr()
+            p1 = None if H1c is None else H1c.data_ptr()
+            self._keep = (H0c, H1c)
+        else:
+            H0c = np.ascontiguousarray(H0, dtype=np.float64)
+            H1c = None if H1 is None else np.ascontiguousarray(H1, dtype=np.float64)
+            on_dev = 0
+            p0 = H0c.ctypes.data
+            p1 = None if H1c is None else H1c.ctypes.data
+            self._keep = (H0c, H1c)
+        set_H(self.h, N, p0, D, p1, on_dev)
+        self._keep = None
+        self.N, self.D = N, D
+
+    def solve(self, beta, nocc, n, want_P0=True, want_P1=True, device="cuda"):
+        """Returns dict(P0, P1, mu, mu1) with P0/P1 float64 torch tensors on `device`."""
+        import torch
+        N, D = self.N, self.D
+        dev = torch.device(device)
+        on_dev = 1 if dev.type == "cuda" else 0
+        P0 = torch.empty((N, N), dtype=torch.float64, device=dev) if want_P0 else None
+        P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev) if (want_P1 and D) else None
+        mu = ctypes.c_double(0.0)
+        mu1 = np.zeros(max(D, 1))
+        solve_raw(self.h, beta, nocc, n, _ptr(P0), _ptr(P1), ctypes.addressof(mu),
+                  mu1.ctypes.data, on_dev)
+        return {"P0": P0, "P1": P1, "mu": mu.value, "mu1": mu1[:D].copy()}
+
+    def polarizability(self):
+        return polarizability(self.h, self.D)
+
+    def stats(self):
+        return get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def solve(H0, H1, beta, nocc, n, precision="fp32", **kw):
+    """One-shot canonical solve: returns (P0, P1, mu, mu1) with P0/P1 on the GPU."""
+    with Handle(precision=precision, **kw) as h:
+        h.set_H(H0, H1)
+        r = h.solve(beta, nocc, n)
+        return r["P0"], r["P1"], r["mu"], r["mu1"]

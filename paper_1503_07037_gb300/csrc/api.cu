@@ -1,0 +1,372 @@
+// C ABI of libcdmpt.so (declared in include/cdmpt.h).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cdmpt.h"
+#include "solver.cuh"
+
+namespace cdmpt {
+
+namespace {
+thread_local std::string g_err;
+std::mutex g_err_word_mu;
+int* g_err_word[64] = {nullptr};
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+const std::string& get_error() { return g_err; }
+
+int* device_error_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_err_word_mu);
+    if (!g_err_word[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemset(p, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        g_err_word[dev] = p;
+    }
+    return g_err_word[dev];
+}
+
+cdmpt_status check_device_error(cudaStream_t s) {
+    int* w = device_error_word();
+    if (!w) return CDMPT_OK;
+    int host = 0;
+    CDMPT_CUDA_TRY(cudaMemcpyAsync(&host, w, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (host != DEV_OK) {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(int), s));
+        set_error("a bounded device wait gave up (code " + std::to_string(host) + ")");
+        return CDMPT_ERR_TIMEOUT;
+    }
+    return CDMPT_OK;
+}
+
+}  // namespace cdmpt
+
+using namespace cdmpt;
+
+struct cdmpt_handle {
+    cdmpt_opts opts;
+    int device = 0;
+    int N = 0, D = 0, ld = 0;
+    double* H0 = nullptr;     // N x ld, FP64, zero padding
+    double* H1 = nullptr;     // D x N x ld
+    double* dscal = nullptr;  // device scalars for set_H (bounds, trace)
+    double gmin = 0, gmax = 0, trH0 = 0;
+    Solver<float>* sf = nullptr;
+    Solver<double>* sd = nullptr;
+    Context cx;
+    cdmpt_stats st;
+    std::string err;
+    bool solved = false;
+    std::vector<double> alpha;
+};
+
+namespace {
+
+cdmpt_status fail(cdmpt_handle* h, cdmpt_status s) {
+    if (h) h->err = get_error();
+    return s;
+}
+
+cdmpt_status fail_msg(cdmpt_handle* h, cdmpt_status s, const std::string& m) {
+    set_error(m);
+    return fail(h, s);
+}
+
+bool valid_opts(const cdmpt_opts* o) {
+    if (o->precision < CDMPT_FP64 || o->precision > CDMPT_MIXED_BF16) return false;
+    if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_3XTF32) return false;
+    if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
+    return true;
+}
+
+void normalise(cdmpt_opts* o) {
+    if (!(o->cg_tol > 0)) o->cg_tol = o->precision == CDMPT_FP64 ? 1e-13 : 1e-7;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdmpt_version(void) { return (CDMPT_VERSION_MAJOR << 16) | CDMPT_VERSION_MINOR; }
+
+cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
+    if (!o) return CDMPT_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = CDMPT_FP32;
+    o->gemm_engine = CDMPT_GEMM_AUTO;
+    o->cg_tol = 0.0;
+    o->cg_maxit = 200;
+    o->refine_rounds = 2;
+    o->occ_tol = 0.0;
+    o->mu_maxit = 60;
+    o->have_mu_guess = 0;
+    o->mu_guess = 0.0;
+    o->profile = 0;
+    o->stream = nullptr;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_set_opts(cdmpt_handle* h, const cdmpt_opts* opts) {
+    if (!h || !opts) return CDMPT_ERR_ARG;
+    if (!valid_opts(opts)) return fail_msg(h, CDMPT_ERR_ARG, "invalid options");
+    if (opts->precision == CDMPT_MIXED_BF16)
+        return fail_msg(h, CDMPT_ERR_UNSUPPORTED, "MIXED_BF16 is not available");
+    const bool needs_tc =
+        opts->precision != CDMPT_FP64 &&
+        (opts->gemm_engine == CDMPT_GEMM_AUTO || opts->gemm_engine >= CDMPT_GEMM_TC_TF32);
+    if (needs_tc && !tc_supported())
+        return fail_msg(h, CDMPT_ERR_UNSUPPORTED,
+                        "tcgen05 engines need an sm_103 GPU; choose CDMPT_GEMM_SIMT or FP64");
+    h->opts = *opts;
+    normalise(&h->opts);
+    h->cx.stream = (cudaStream_t)h->opts.stream;
+    h->cx.engine = h->opts.gemm_engine;
+    h->cx.profile = h->opts.profile != 0;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_create(const cdmpt_opts* opts, cdmpt_handle** out) {
+    if (!out) return CDMPT_ERR_ARG;
+    *out = nullptr;
+    cdmpt_opts o;
+    if (opts)
+        o = *opts;
+    else
+        cdmpt_default_opts(&o);
+    cdmpt_handle* h = new (std::nothrow) cdmpt_handle();
+    if (!h) return CDMPT_ERR_OOM;
+    std::memset(&h->st, 0, sizeof(h->st));
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("no CUDA device");
+        return CDMPT_ERR_CUDA;
+    }
+    cdmpt_status s = cdmpt_set_opts(h, &o);
+    if (s != CDMPT_OK) {
+        delete h;
+        return s;
+    }
+    if (cudaMallocHost((void**)&h->cx.pinned, 64 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&h->dscal, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("allocation of handle scalars failed");
+        cdmpt_destroy(h);
+        return CDMPT_ERR_OOM;
+    }
+    *out = h;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const double* H1,
+                         int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (N < 1 || D < 0 || !H0 || (D > 0 && !H1))
+        return fail_msg(h, CDMPT_ERR_ARG, "set_H: need N >= 1, D >= 0, H0 and (D > 0) H1");
+    if (D > 16) return fail_msg(h, CDMPT_ERR_ARG, "set_H: at most 16 perturbation directions");
+    cudaStream_t s = h->cx.stream;
+    const int ld = (N + 31) / 32 * 32;
+    const size_t blk = (size_t)N * ld;
+    if (N != h->N || D != h->D || ld != h->ld) {
+        cudaFree(h->H0);
+        cudaFree(h->H1);
+        h->H0 = h->H1 = nullptr;
+        if (cudaMalloc((void**)&h->H0, blk * sizeof(double)) != cudaSuccess ||
+            (D > 0 && cudaMalloc((void**)&h->H1, D * blk * sizeof(double)) != cudaSuccess)) {
+            cudaGetLastError();
+            h->N = 0;
+            return fail_msg(h, CDMPT_ERR_OOM, "set_H: device allocation failed");
+        }
+        h->N = N;
+        h->D = D;
+        h->ld = ld;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CDMPT_CUDA_TRY(cudaMemsetAsync(h->H0, 0, blk * sizeof(double), s));
+    CDMPT_CUDA_TRY(cudaMemcpy2DAsync(h->H0, ld * sizeof(double), H0, N * sizeof(double),
+                                     N * sizeof(double), N, kind, s));
+    if (D > 0) {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(h->H1, 0, D * blk * sizeof(double), s));
+        CDMPT_CUDA_TRY(cudaMemcpy2DAsync(h->H1, ld * sizeof(double), H1, N * sizeof(double),
+                                         N * sizeof(double), (size_t)D * N, kind, s));
+    }
+    CDMPT_CUDA_TRY(cudaMemsetAsync(h->dscal, 0, 8 * sizeof(double), s));
+    cdmpt_status st = gershgorin(h->H0, N, ld, h->dscal, s);
+    if (st != CDMPT_OK) return fail(h, st);
+    st = Ew<double>::trace(h->H0, N, ld, 1, h->dscal + 2, s);
+    if (st != CDMPT_OK) return fail(h, st);
+    double host[3];
+    CDMPT_CUDA_TRY(cudaMemcpyAsync(host, h->dscal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+    h->gmin = host[0];
+    h->gmax = host[1];
+    h->trH0 = host[2];
+    h->solved = false;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, double* P0,
+                         double* P1, double* mu, double* mu1, int out_on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (h->N < 1) return fail_msg(h, CDMPT_ERR_ARG, "solve: call cdmpt_set_H first");
+    if (!(beta > 0) || !(nocc > 0) || !(nocc < h->N) || n < 1 || n > 60)
+        return fail_msg(h, CDMPT_ERR_ARG, "solve: need beta > 0, 0 < nocc < N, 1 <= n <= 60");
+    std::memset(&h->st, 0, sizeof(h->st));
+    h->st.N = h->N;
+    h->st.D = h->D;
+    h->st.n = n;
+    h->cx.st = &h->st;
+    h->cx.ev_used = 0;
+    h->solved = false;
+    h->alpha.assign(h->D, 0.0);
+    const long long launches0 = launch_count();
+    const auto t0 = std::chrono::steady_clock::now();
+    cdmpt_status s;
+    if (h->opts.precision == CDMPT_FP64) {
+        if (!h->sd) h->sd = new (std::nothrow) Solver<double>();
+        if (!h->sd) return fail_msg(h, CDMPT_ERR_OOM, "solver allocation");
+        s = h->sd->solve(h->cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts,
+                         beta, nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
+    } else {
+        if (!h->sf) h->sf = new (std::nothrow) Solver<float>();
+        if (!h->sf) return fail_msg(h, CDMPT_ERR_OOM, "solver allocation");
+        Context& cx = h->cx;
+        const int saved = cx.engine;
+        if (h->opts.precision == CDMPT_MIXED_TF32 && cx.engine == CDMPT_GEMM_AUTO)
+            cx.engine = CDMPT_GEMM_TC_TF32;
+        s = h->sf->solve(cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts, beta,
+                         nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
+        cx.engine = saved;
+    }
+    h->st.kernel_launches = (int)(launch_count() - launches0);
+    h->st.seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (h->cx.profile && s == CDMPT_OK) {
+        double ms = 0;
+        int timed = 0;
+        for (size_t i = 0; i < h->cx.ev_used; ++i) {
+            if (!h->cx.ev_ok[i]) continue;
+            float e = 0;
+            if (cudaEventElapsedTime(&e, h->cx.ev[2 * i], h->cx.ev[2 * i + 1]) == cudaSuccess) {
+                ms += e;
+                ++timed;
+            }
+        }
+        h->st.gemm_ms = ms;
+        h->st.gemm_timed = timed;
+    }
+    if (s != CDMPT_OK) return fail(h, s);
+    h->solved = true;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha) {
+    if (!h || !alpha) return CDMPT_ERR_ARG;
+    if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "polarizability: no completed solve");
+    for (int d = 0; d < h->D; ++d) alpha[d] = h->alpha[d];
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_get_stats(const cdmpt_handle* h, cdmpt_stats* st) {
+    if (!h || !st) return CDMPT_ERR_ARG;
+    *st = h->st;
+    return CDMPT_OK;
+}
+
+const char* cdmpt_last_error(const cdmpt_handle* h) {
+    if (!h) return get_error().c_str();
+    return h->err.c_str();
+}
+
+void cdmpt_destroy(cdmpt_handle* h) {
+    if (!h) return;
+    delete h->sf;
+    delete h->sd;
+    for (cudaEvent_t e : h->cx.ev) cudaEventDestroy(e);
+    cudaFree(h->H0);
+    cudaFree(h->H1);
+    cudaFree(h->dscal);
+    if (h->cx.pinned) cudaFreeHost(h->cx.pinned);
+    delete h;
+}
+
+cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X, int ldx,
+                            const float* Y, int ldy, float* D, int ldd, double alpha,
+                            double beta, const float* C, int ldc, double gamma, int diag_block,
+                            int trans_block, double* dot, const float* E, int lde,
+                            void* stream) {
+    if (M < 0 || Ncols < 0 || K < 0 || !X || !Y || !D || (beta != 0.0 && !C)) {
+        set_error("gemm_f32: bad arguments");
+        return CDMPT_ERR_ARG;
+    }
+    if (trans_block > 0 && (Ncols != trans_block || M % trans_block)) {
+        set_error("gemm_f32: trans_block needs Ncols == trans_block and M a multiple of it");
+        return CDMPT_ERR_ARG;
+    }
+    Epilogue<float> ep;
+    ep.alpha = alpha;
+    ep.beta = beta;
+    ep.C = C;
+    ep.ldc = ldc;
+    ep.gamma = gamma;
+    ep.diag_block = diag_block;
+    ep.trans_block = trans_block;
+    ep.dot = dot;
+    ep.E = E;
+    ep.lde = lde;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (engine == CDMPT_GEMM_SIMT) return gemm_simt<float>(M, Ncols, K, X, ldx, Y, ldy, D, ldd, ep,
+                                                           nullptr, s);
+    if (engine != CDMPT_GEMM_AUTO && engine != CDMPT_GEMM_TC_TF32 && engine != CDMPT_GEMM_TC_3XTF32) {
+        set_error("gemm_f32: unknown engine");
+        return CDMPT_ERR_ARG;
+    }
+    return gemm_tc_f32(engine == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : engine, M, Ncols, K, X,
+                       ldx, Y, ldy, D, ldd, ep, nullptr, s);
+}
+
+cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,
+                            int ldy, double* D, int ldd, double alpha, double beta,
+                            const double* C, int ldc, double gamma, int diag_block,
+                            int trans_block, double* dot, const double* E, int lde,
+                            void* stream) {
+    if (M < 0 || Ncols < 0 || K < 0 || !X || !Y || !D || (beta != 0.0 && !C)) {
+        set_error("gemm_f64: bad arguments");
+        return CDMPT_ERR_ARG;
+    }
+    if (trans_block > 0 && (Ncols != trans_block || M % trans_block)) {
+        set_error("gemm_f64: trans_block needs Ncols == trans_block and M a multiple of it");
+        return CDMPT_ERR_ARG;
+    }
+    Epilogue<double> ep;
+    ep.alpha = alpha;
+    ep.beta = beta;
+    ep.C = C;
+    ep.ldc = ldc;
+    ep.gamma = gamma;
+    ep.diag_block = diag_block;
+    ep.trans_block = trans_block;
+    ep.dot = dot;
+    ep.E = E;
+    ep.lde = lde;
+    return gemm_simt<double>(M, Ncols, K, X, ldx, Y, ldy, D, ldd, ep, nullptr,
+                             (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,566 @@
+// Persistent tcgen05 GEMM for sm_103a: D = alpha X Y^T + beta C + gamma I.
+//
+// Every product of the recursion has the form X Y^T with Y symmetric (the
+// right factor is Z_k, A_k = I + Z_k^2, or the symmetrised response), so both
+// operands are read K-major straight from row-major storage.
+//
+// Roles per CTA (one CTA per SM, persistent over output tiles):
+//   warp 0      TMA producer: 128 x 32 and BN x 32 FP32 tiles, 128-byte
+//               swizzle, into a STAGES-deep shared-memory ring;
+//   warp 1      TMEM allocator and single-thread tcgen05.mma issuer
+//               (kind::tf32, M = 128, N = BN, K = 8 per instruction) into
+//               one of two TMEM accumulators (2 x BN columns);
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32 (w % 4) ...), alpha/beta/gamma, transposed
+//               placement, fused Frobenius dot, global stores;
+//   warps 6..9  (3xTF32 only) split each landed FP32 tile in place into
+//               hi = rna_tf32(x) and, in a second buffer, lo = rna_tf32(x - hi),
+//               so the MMA can form lo*hi + hi*lo + hi*hi (Ootomo & Yokota's
+//               split-TF32 scheme) with FP32 accumulation in TMEM.
+//
+// Every mbarrier wait is bounded (about 2 s of %globaltimer). On timeout a
+// thread records the error, raises a shared abort flag that ends the other
+// roles' loops, in-flight TMA/MMA work is drained with bounded waits, and the
+// CTA frees its TMEM before returning.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <string>
+
+#include "epilogue.cuh"
+#include "internal.cuh"
+
+namespace cdmpt {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;        // FP32 elements per 128-byte swizzle row
+constexpr int UMMA_K = 8;     // K of one kind::tf32 instruction
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+template <int BN, int STAGES, int SPLIT>
+struct Cfg {
+    static constexpr int A_BYTES = BM * BK * 4;
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int TX_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGE_BYTES = TX_BYTES * (SPLIT == 3 ? 2 : 1);
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int THREADS = SPLIT == 3 ? 320 : 192;
+    static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN");
+    static_assert(TMEM_COLS <= 512, "TMEM");
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase of the given parity completed; false when
+// the abort flag is raised or the time limit passed (then the flag is raised
+// and the error recorded).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          volatile int* abort_flag, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag (used while draining).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitNs / 4) return;
+    }
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(holder)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row core groups 1024 bytes apart (stride byte offset),
+// descriptor version 1 at bits 46-47, swizzle mode 2 (128 B) at bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_tf32() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t rna_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int BN, int STAGES, int SPLIT>
+__global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+              int K, EpiParams<float> p, const double* skip, int* err) {
+    using C = Cfg<BN, STAGES, SPLIT>;
+    if (skip != nullptr && *skip != 0.0) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* conv = empty + STAGES;
+    uint64_t* tfull = conv + STAGES;    // [2]
+    uint64_t* tempty = tfull + 2;       // [2]
+    uint64_t* drain = tempty + 2;       // [1]
+    uint32_t* tmem_holder = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_mt = (p.M + BM - 1) / BM;
+    const int num_nt = (p.N + BN - 1) / BN;
+    const int num_tiles = num_mt * num_nt;
+    const int num_k = (K + BK - 1) / BK;
+
+    auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
+    auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::TX_BYTES; };
+    auto stage_blo = [&](int s) {
+        return smem + s * C::STAGE_BYTES + C::TX_BYTES + C::A_BYTES;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&conv[s], 128);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    if (warp == 1) tmem_alloc(tmem_holder, C::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            prefetch_map(&tmX);
+            prefetch_map(&tmY);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                const int mt = t % num_mt, nt = t / num_mt;
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], C::TX_BYTES);
+                    tma_load_2d(stage_a(s), &tmX, kb * BK, mt * BM, &full[s]);
+                    tma_load_2d(stage_b(s), &tmY, kb * BK, nt * BN, &full[s]);
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0;
+                for (uint32_t j = first; j < it; ++j) mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32<BN>();
+            uint32_t it = 0;
+            int lt = 0;
+            bool ok = true, issued = false;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++lt) {
+                const int acc = lt & 1;
+                if (!mbar_wait(&tempty[acc], ((lt >> 1) & 1) ^ 1, abort_flag, err,
+                               DEV_TIMEOUT_ACCUM)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tmem_d = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    uint64_t* ready = SPLIT == 3 ? &conv[s] : &full[s];
+                    if (!mbar_wait(ready, ph, abort_flag, err,
+                                   SPLIT == 3 ? DEV_TIMEOUT_CONV : DEV_TIMEOUT_FULL)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        const uint32_t off = kk * UMMA_K * 4;
+                        const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
+                        const uint32_t first = (kb | kk) != 0 ? 1u : 0u;
+                        if constexpr (SPLIT == 3) {
+                            const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
+                            const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
+                            mma_tf32(tmem_d, al, bh, idesc, first);
+                            mma_tf32(tmem_d, ah, bl, idesc, 1u);
+                            mma_tf32(tmem_d, ah, bh, idesc, 1u);
+                        } else {
+                            mma_tf32(tmem_d, ah, bh, idesc, first);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+            }
+            if (!ok && issued) {
+                mma_commit(drain);
+                mbar_drain(drain, 0);
+            }
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;     // TMEM lane quarter this warp may read
+        double dsum = 0.0;
+        int lt = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            int ok = 1;
+            if (lane == 0)
+                ok = mbar_wait(&tfull[acc], (lt >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int mt = t % num_mt, nt = t / num_mt;
+            const int m = mt * BM + 32 * q + lane;
+            const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tbase + c0, r);
+                if (m < p.M) {
+                    float local = 0.f;
+                    const int nb = nt * BN + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = nb + j;
+                        if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(r[j]));
+                    }
+                    dsum += (double)local;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[acc]);
+        }
+        if (p.dot) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+            if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
+        }
+    } else {
+        // ------------------------------------------------ hi/lo split (3xTF32)
+        if constexpr (SPLIT == 3) {
+            const int ct = threadIdx.x - 192;   // 0..127
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+                bool ok = true;
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    int w_ok = 1;
+                    if (lane == 0)
+                        w_ok = mbar_wait(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL);
+                    w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+                    if (!w_ok) {
+                        ok = false;
+                        break;
+                    }
+                    // A and B hi tiles are contiguous, as are the lo tiles
+                    float4* hi = (float4*)stage_a(s);
+                    float4* lo = (float4*)stage_alo(s);
+                    constexpr int NV = C::TX_BYTES / 16;
+#pragma unroll 4
+                    for (int v = ct; v < NV; v += 128) {
+                        float4 x = hi[v];
+                        uint32_t h0 = rna_tf32(x.x), h1 = rna_tf32(x.y), h2 = rna_tf32(x.z),
+                                 h3 = rna_tf32(x.w);
+                        float4 hv = make_float4(__uint_as_float(h0), __uint_as_float(h1),
+                                                __uint_as_float(h2), __uint_as_float(h3));
+                        float4 lv = make_float4(__uint_as_float(rna_tf32(x.x - hv.x)),
+                                                __uint_as_float(rna_tf32(x.y - hv.y)),
+                                                __uint_as_float(rna_tf32(x.z - hv.z)),
+                                                __uint_as_float(rna_tf32(x.w - hv.w)));
+                        hi[v] = hv;
+                        lo[v] = lv;
+                    }
+                    fence_proxy_async();
+                    mbar_arrive(&conv[s]);
+                }
+                if (!ok) break;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* base, int rows, int cols, int ld, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+template <int BN, int STAGES, int SPLIT>
+cdmpt_status launch(int M, int N, int K, const float* X, int ldx, const float* Y, int ldy,
+                    const EpiParams<float>& p, const double* skip, cudaStream_t s) {
+    using C = Cfg<BN, STAGES, SPLIT>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) {
+            set_error(std::string("tcgen05 GEMM smem attribute: ") + cudaGetErrorString(e));
+            return CDMPT_ERR_CUDA;
+        }
+        attr_set = true;
+    }
+    CUtensorMap mx, my;
+    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, BN)) {
+        set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
+        return CDMPT_ERR_ARG;
+    }
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    k_gemm_tc<BN, STAGES, SPLIT>
+        <<<grid, C::THREADS, C::SMEM, s>>>(mx, my, K, p, skip, device_error_word());
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("tcgen05 GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
+}  // namespace
+
+bool tc_supported() {
+    static int cached = -1;
+    if (cached < 0) {
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        cached = (major == 10 && minor == 3) ? 1 : 0;
+    }
+    return cached == 1;
+}
+
+cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ldx,
+                         const float* Y, int ldy, float* D, int ldd, const Epilogue<float>& ep,
+                         const double* skip, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return CDMPT_OK;
+    if (!tc_supported()) {
+        set_error("tcgen05 GEMM needs an sm_103 device");
+        return CDMPT_ERR_UNSUPPORTED;
+    }
+    if ((ldx & 3) || (ldy & 3) || (((uintptr_t)X) & 15) || (((uintptr_t)Y) & 15) || K < 1) {
+        set_error("tcgen05 GEMM: X/Y must be 16-byte aligned with ld a multiple of 4, K >= 1");
+        return CDMPT_ERR_ARG;
+    }
+    EpiParams<float> p;
+    p.alpha = (float)ep.alpha;
+    p.beta = (float)ep.beta;
+    p.gamma = (float)ep.gamma;
+    p.C = ep.C;
+    p.ldc = ep.ldc;
+    p.D = D;
+    p.ldd = ldd;
+    p.M = M;
+    p.N = N;
+    p.diag_block = ep.diag_block > 0 ? ep.diag_block : M;
+    p.trans_block = ep.trans_block;
+    p.dot = ep.dot;
+    p.E = ep.E;
+    p.lde = ep.lde;
+    if (engine == CDMPT_GEMM_TC_TF32) return launch<256, 4, 1>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+    return launch<128, 3, 3>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+}
+
+}  // namespace cdmpt

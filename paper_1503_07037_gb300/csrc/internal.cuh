@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libcdmpt.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "cdmpt.h"
+
+namespace cdmpt {
+
+// Status-returning CUDA check; records the failing call in the thread's last error.
+void set_error(const std::string& msg);
+const std::string& get_error();
+
+#define CDMPT_CUDA_TRY(expr)                                                            \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            ::cdmpt::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e) +     \
+                               " (" __FILE__ ":" + std::to_string(__LINE__) + ")");     \
+            return CDMPT_ERR_CUDA;                                                      \
+        }                                                                               \
+    } while (0)
+
+#define CDMPT_TRY(expr)                   \
+    do {                                  \
+        cdmpt_status _s = (expr);         \
+        if (_s != CDMPT_OK) return _s;    \
+    } while (0)
+
+// Epilogue of every GEMM: D = alpha * X Y^T + beta * C + gamma * I_blocks, with
+// optional transposed placement inside row blocks and an optional fused dot.
+template <typename T>
+struct Epilogue {
+    double alpha = 1.0;
+    double beta = 0.0;
+    const T* C = nullptr;
+    int ldc = 0;
+    double gamma = 0.0;
+    int diag_block = 0;    // identity on (m % diag_block) == n; 0 -> diag_block = M
+    int trans_block = 0;   // > 0: write at the transposed position inside row blocks
+    double* dot = nullptr; // accumulate sum D * E
+    const T* E = nullptr;  // nullptr with dot -> E = D
+    int lde = 0;
+};
+
+// Device-side CG scalars (one block of doubles per solve).
+enum CgSlot {
+    CG_RR = 0,      // <R, R> of the current iterate
+    CG_PQ = 1,      // <P, A P>
+    CG_RRNEW = 2,   // <R, R> after the update
+    CG_BB = 3,      // <RHS, RHS>
+    CG_DONE = 4,    // 1.0 once converged (kernels then return at once)
+    CG_ITERS = 5,   // iterations taken (as double)
+    CG_TOL2 = 6,    // tol^2
+    CG_NSLOTS = 8
+};
+
+// Error word written by kernels whose bounded waits give up.
+enum DeviceError {
+    DEV_OK = 0,
+    DEV_TIMEOUT_FULL = 1,
+    DEV_TIMEOUT_EMPTY = 2,
+    DEV_TIMEOUT_CONV = 3,
+    DEV_TIMEOUT_ACCUM = 4,
+};
+
+int* device_error_word();   // per-device word, zeroed at first use
+cdmpt_status check_device_error(cudaStream_t s);
+
+// GEMM launchers (asynchronous).
+template <typename T>
+cdmpt_status gemm_simt(int M, int N, int K, const T* X, int ldx, const T* Y, int ldy, T* D,
+                       int ldd, const Epilogue<T>& ep, const double* skip, cudaStream_t s);
+
+cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ldx,
+                         const float* Y, int ldy, float* D, int ldd, const Epilogue<float>& ep,
+                         const double* skip, cudaStream_t s);
+bool tc_supported();   // device is sm_103 (tcgen05 kernels built for sm_103a)
+
+// Elementwise / reduction launchers (T = float or double). "count" is the
+// number of elements of a contiguous rows x ld block; padding columns hold 0.
+template <typename T>
+struct Ew {
+    static cdmpt_status init_z(T* Z, const double* H, int N, int ld, int ldh, int blocks,
+                               double scale, double shift, cudaStream_t s);
+    static cdmpt_status cg_update(T* X, T* R, const T* P, const T* Q, size_t count,
+                                  double* sc, cudaStream_t s);
+    static cdmpt_status cg_direction(T* P, const T* R, size_t count, const double* sc,
+                                     cudaStream_t s);
+    static cdmpt_status dot(const T* A, const T* B, size_t count, double* out, const double* skip,
+                            cudaStream_t s);
+    static cdmpt_status axpby(T* Y, const T* X, size_t count, double a, double b,
+                              const double* skip, cudaStream_t s);
+    static cdmpt_status trace(const T* A, int N, int ld, int blocks, double* out, cudaStream_t s);
+    static cdmpt_status transpose_add(T* out, const T* S, int N, int ld, int blocks,
+                                      cudaStream_t s);
+    static cdmpt_status symmetrize(T* Z, int N, int ld, int blocks, cudaStream_t s);
+    static cdmpt_status to_f64(double* out, int ldo, const T* in, int ldi, int N, int rows,
+                               double a, double b_diag, cudaStream_t s);
+    static cdmpt_status diag_dot(const T* A, const double* H, int N, int ld, int ldh,
+                                 double* out, cudaStream_t s);
+};
+
+cdmpt_status cg_scalar_step(double* sc, cudaStream_t s);
+cdmpt_status cg_scalar_init(double* sc, double tol2, cudaStream_t s);
+cdmpt_status gershgorin(const double* H, int N, int ld, double* out2, cudaStream_t s);
+cdmpt_status frob_dot_f64_full(const double* A, const double* B, size_t count, double* out,
+                               cudaStream_t s);
+
+// Count of kernel launches issued by this thread (for statistics).
+void count_launch(int k = 1);
+long long launch_count();
+
+}  // namespace cdmpt

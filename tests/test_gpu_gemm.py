@@ -1,0 +1,125 @@
+"""GPU tests of the product building block D = alpha X Y^T + beta C + gamma I (C ABI).
+
+Reference: the same FP32/FP64 inputs multiplied in FP64 by NumPy on the host.
+Shapes span several 128 x 256 tiles with ragged M, N and K tails.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+# relative Frobenius bounds for K <= 4096 with O(1) entries:
+#  3xTF32 / FFMA carry FP32 rounding (~ sqrt(K) 2^-24), 1xTF32 carries 2^-11 per operand
+TOL = {"simt": 2e-6, "3xtf32": 4e-6, "tf32": 3e-3, "auto": 4e-6}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _mat(rng, rows, cols, ld=None, dtype=np.float32):
+    ld = cols if ld is None else ld
+    A = np.zeros((rows, ld), dtype=dtype)
+    A[:, :cols] = rng.standard_normal((rows, cols))
+    return A
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+@pytest.mark.parametrize("engine", ["simt", "3xtf32", "tf32"])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 32), (300, 200, 130), (1024, 1024, 1024),
+                                   (777, 513, 2049)])
+def test_gemm_f32_plain(cuda, cdmpt_lib, engine, M, N, K):
+    import torch
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    ld = (K + 3) // 4 * 4
+    X = _mat(rng, M, K, ld)
+    Y = _mat(rng, N, K, ld)
+    D = torch.zeros((M, (N + 3) // 4 * 4), dtype=torch.float32, device=cuda)
+    cdmpt_lib.gemm_f32(_t(X, cuda), _t(Y, cuda), D, engine=engine, M=M, Ncols=N, K=K)
+    torch.cuda.synchronize()
+    ref = X[:, :K].astype(np.float64) @ Y[:, :K].astype(np.float64).T
+    assert _rel(D.cpu().numpy()[:, :N].astype(np.float64), ref) < TOL[engine]
+
+
+@pytest.mark.parametrize("engine", ["simt", "3xtf32", "tf32"])
+def test_gemm_f32_epilogue(cuda, cdmpt_lib, engine):
+    """alpha, beta C, gamma on block diagonals, transposed block placement and the fused dot."""
+    import torch
+    rng = np.random.default_rng(5)
+    Nb, blocks = 160, 2
+    M, N, K = Nb * blocks, Nb, Nb
+    X = _mat(rng, M, K)
+    Y = _mat(rng, N, K)
+    C = _mat(rng, M, N)
+    E = _mat(rng, M, N)
+    alpha, beta, gamma = -1.25, 2.0, 0.75
+    acc = X.astype(np.float64) @ Y.astype(np.float64).T
+    for trans in (0, Nb):
+        ref = np.empty((M, N))
+        for b in range(blocks):
+            blk = alpha * acc[b * Nb:(b + 1) * Nb] + gamma * np.eye(Nb)
+            if trans:
+                ref[b * Nb:(b + 1) * Nb] = blk.T + beta * C[b * Nb:(b + 1) * Nb]
+            else:
+                ref[b * Nb:(b + 1) * Nb] = blk + beta * C[b * Nb:(b + 1) * Nb]
+        D = torch.zeros((M, N), dtype=torch.float32, device=cuda)
+        dot = torch.zeros(1, dtype=torch.float64, device=cuda)
+        cdmpt_lib.gemm_f32(_t(X, cuda), _t(Y, cuda), D, alpha=alpha, beta=beta, C=_t(C, cuda),
+                           gamma=gamma, diag_block=Nb, trans_block=trans, dot=dot, E=_t(E, cuda),
+                           engine=engine)
+        torch.cuda.synchronize()
+        got = D.cpu().numpy().astype(np.float64)
+        assert _rel(got, ref) < TOL[engine], trans
+        assert abs(dot.item() - np.sum(got * E)) < 1e-5 * np.sum(np.abs(got * E))
+        # self dot (E = D)
+        dot.zero_()
+        cdmpt_lib.gemm_f32(_t(X, cuda), _t(Y, cuda), D, alpha=alpha, beta=beta, C=_t(C, cuda),
+                           gamma=gamma, diag_block=Nb, trans_block=trans, dot=dot, engine=engine)
+        torch.cuda.synchronize()
+        got = D.cpu().numpy().astype(np.float64)
+        assert abs(dot.item() - np.sum(got * got)) < 1e-5 * np.sum(got * got)
+
+
+def test_gemm_f32_in_place_accumulate(cuda, cdmpt_lib):
+    """C may alias D: D = X Y^T + D."""
+    import torch
+    rng = np.random.default_rng(9)
+    X = _mat(rng, 256, 256)
+    Y = _mat(rng, 256, 256)
+    C = _mat(rng, 256, 256)
+    D = _t(C, cuda).clone()
+    cdmpt_lib.gemm_f32(_t(X, cuda), _t(Y, cuda), D, beta=1.0, C=D, engine="3xtf32")
+    torch.cuda.synchronize()
+    ref = X.astype(np.float64) @ Y.astype(np.float64).T + C
+    assert _rel(D.cpu().numpy().astype(np.float64), ref) < TOL["3xtf32"]
+
+
+def test_gemm_f64(cuda, cdmpt_lib):
+    import torch
+    rng = np.random.default_rng(3)
+    M, N, K = 100, 70, 90
+    X = _mat(rng, M, K, dtype=np.float64)
+    Y = _mat(rng, N, K, dtype=np.float64)
+    C = _mat(rng, M, N, dtype=np.float64)
+    D = torch.zeros((M, N), dtype=torch.float64, device=cuda)
+    dot = torch.zeros(1, dtype=torch.float64, device=cuda)
+    cdmpt_lib.gemm_f64(_t(X, cuda), _t(Y, cuda), D, alpha=0.5, beta=-1.0, C=_t(C, cuda),
+                       gamma=3.0, dot=dot)
+    torch.cuda.synchronize()
+    ref = 0.5 * X @ Y.T - C
+    ref[np.arange(N), np.arange(N)] += 3.0
+    got = D.cpu().numpy()
+    assert _rel(got, ref) < 1e-14
+    assert abs(dot.item() - np.sum(got * got)) < 1e-12 * np.sum(got * got)
+
+
+def test_gemm_rejects_misaligned_ld(cuda, cdmpt_lib):
+    import torch
+    X = torch.zeros((64, 66), dtype=torch.float32, device=cuda)
+    D = torch.zeros((64, 64), dtype=torch.float32, device=cuda)
+    with pytest.raises(cdmpt_lib.CdmptError):
+        cdmpt_lib.gemm_f32(X, X, D, engine="tf32", K=66)
