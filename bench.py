@@ -1,0 +1,366 @@
+"""Throughput of canonical DMPT solves on GB300 (one JSON line on rank 0).
+
+Workload (one step): the 16 x 16 x 16 periodic simple-cubic tight-binding
+lattice (N = 4096, on-site N(0, 0.3^2), hopping -1 +- 10 %, seed 1002), dipole
+perturbation along x, N_occ = N/2, n = 14 recursion steps, solved canonically
+at beta = 5, 20 and 80: three full solves (occupation loop, first-order
+response, mu1, polarizability) per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|mixed]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (exact diagonalisation) on the
+host cores, one solve of the same workload per step.
+Under torchrun every rank solves its own copy (weak scaling, no collective on
+the data path); times are max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("DMPT response solves/sec and tensor TFLOP/s vs peak, mixed vs FP32 at "
+          "≤1e-6 err")
+BETAS = (5.0, 20.0, 80.0)
+LATTICE = (16, 16, 16)
+NSTEPS_REC = 14
+WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {5,20,80}"
+TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16": d["bf16_tflops"],
+                "bf16_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+def problems():
+    import synthetic
+    return [synthetic.cubic_lattice(LATTICE, seed=1002, beta=b, n=NSTEPS_REC) for b in BETAS]
+
+
+# --------------------------------------------------------------------------- oracle timing
+
+def time_oracle(sample_betas, cores_note=True):
+    """Times the FP64 oracle on this host: returns (solves/s, seconds, results)."""
+    import oracle
+    import synthetic
+    res = {}
+    t0 = time.perf_counter()
+    for b in sample_betas:
+        p = synthetic.cubic_lattice(LATTICE, seed=1002, beta=b, n=NSTEPS_REC)
+        res[b] = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    dt = time.perf_counter() - t0
+    return len(sample_betas) / dt, dt, res
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    betas = [BETAS[i % len(BETAS)] for i in range(args.warmup + args.steps)]
+    for b in betas[:args.warmup]:
+        time_oracle([b])
+    t0 = time.perf_counter()
+    for b in betas[args.warmup:]:
+        time_oracle([b])
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 exact diagonalisation (oracle)",
+                   "step": "one solve of the workload (cycling beta 5, 20, 80)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": blas_threads(),
+                         "kind": "oracle",
+                         "sample": "one beta per step: dsyevd N=4096, bisection on mu, "
+                                   "Daleckii-Krein P1, mu1, alpha"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1503_07037_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    probs = problems()
+    N, D = probs[0].N, probs[0].D
+    stream = torch.cuda.current_stream()
+    h = pkg.Handle(precision=args.precision, profile=True, stream=stream)
+    H0 = torch.from_numpy(probs[0].H0).to(dev)
+    H1 = torch.from_numpy(probs[0].H1).to(dev)
+    h.set_H(H0, H1)                 # resident in HBM before the timed region
+    P0 = torch.empty((N, N), dtype=torch.float64, device=dev)
+    P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev)
+    import ctypes
+    mu = ctypes.c_double()
+    mu1 = np.zeros(D)
+
+    def step(stats_acc=None):
+        for p in probs:
+            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0.data_ptr(), P1.data_ptr(),
+                          ctypes.addressof(mu), mu1.ctypes.data, 1)
+            if stats_acc is not None:
+                stats_acc.append(h.stats())
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    st_all = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(st_all)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    barrier()
+    solves = args.steps * len(probs) * world
+    value = solves / (ms / 1000.0)
+
+    # dominant kernel: the GEMM (all launches are N x N x N); events on the library's stream
+    gemm_ms = sum(s["gemm_ms"] for s in st_all)
+    gemm_timed = sum(s["gemm_timed"] for s in st_all)
+    gemm_flops = sum(s["gemm_flops"] for s in st_all)
+    tensor_flops = sum(s["tensor_flops"] for s in st_all)
+    launches = sum(s["kernel_launches"] for s in st_all)
+    avg_gemm_s = gemm_ms / 1000.0 / max(1, gemm_timed)
+    per_launch_flops = 2.0 * N * N * N
+    achieved = per_launch_flops / avg_gemm_s / 1e12
+    pk = peaks()
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25,
+                "unit": "TFLOP/s", "frac": achieved / 1.25, "traffic": None,
+                "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
+    else:
+        peak_tf32 = pk["bf16_sustained"] * TF32_OVER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf32, "traffic": None,
+                "peak_note": f"tf32 = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
+                             f"{TF32_OVER_BF16:.4f} (nominal 1.1/2.25); achieved counts "
+                             "algorithmic 2N^3 flops per GEMM launch",
+                "tensor_pipe_tflops": tensor_flops / gemm_flops * achieved if gemm_flops else None}
+    gemm_share = gemm_ms / (ms / world if world else ms) if ms else None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or True:
+        H0h = torch.from_numpy(probs[0].H0).pin_memory()
+        H1h = torch.from_numpy(probs[0].H1).pin_memory()
+        P0h = torch.empty((N, N), dtype=torch.float64).pin_memory()
+        P1h = torch.empty((D, N, N), dtype=torch.float64).pin_memory()
+        ke = max(1, min(args.steps, 2))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            pkg.set_H(h.h, N, H0h.data_ptr(), D, H1h.data_ptr(), 0)
+            for p in probs:
+                pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0h.data_ptr(), P1h.data_ptr(),
+                              ctypes.addressof(mu), mu1.ctypes.data, 0)
+        torch.cuda.synchronize()
+        dte = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": ke * len(probs) * world / dte, "unit": "solves/s",
+               "h2d_bytes_per_step": (H0h.numel() + H1h.numel()) * 8,
+               "d2h_bytes_per_step": len(probs) * (P0h.numel() + P1h.numel()) * 8,
+               "steps": ke}
+
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # bounded oracle sample: the beta = 20 solve of the workload (one eigendecomposition)
+        v, dt, res = time_oracle([20.0])
+        cpu = {"value": v, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"1 of the 3 solves of a step (beta=20, N=4096), {dt:.1f} s"}
+        # error of our beta = 20 outputs against it
+        with pkg.Handle(precision=args.precision, stream=stream) as h2:
+            h2.set_H(H0, H1)
+            r = h2.solve(20.0, probs[1].nocc, probs[1].n)
+        ref = res[20.0]
+        import oracle
+        err = {"P0": oracle.rel_frobenius(r["P0"].cpu().numpy(), ref["P0"]),
+               "P1": oracle.rel_frobenius(r["P1"][0].cpu().numpy(), ref["P1"][0]),
+               "mu1": abs(r["mu1"][0] - ref["mu1"][0]) / abs(ref["mu1"][0]),
+               "vs": "oracle, recursion-exact function, beta=20"}
+
+    if rank == 0:
+        s_last = st_all[-len(probs):]
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "tf32+f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "gemm": {"fp32": "tcgen05 3xTF32", "fp64": "CUDA-core DFMA",
+                                "mixed": "tcgen05 TF32"}[args.precision],
+                       "l2": "no flush: working set (trajectory of 29 N x N matrices, "
+                             f"{29 * N * N * (8 if args.precision == 'fp64' else 4) / 2**30:.1f}"
+                             " GiB) exceeds the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "error": err,
+            "detail": {
+                "gemm_share_of_step_time": gemm_share,
+                "gemm_avg_ms": avg_gemm_s * 1000,
+                "gemm_launches_per_step": gemm_timed / args.steps,
+                "algorithmic_tflops_per_step": gemm_flops / args.steps / 1e12,
+                "per_beta": [{"beta": p.beta, "mu_iterations": s["mu_iterations"],
+                              "cg_sweeps": s["cg_iterations_sweeps"],
+                              "cg_last_sweep": s["cg_iterations_last_sweep"],
+                              "cg_response": s["cg_iterations_response"],
+                              "cg_q": s["cg_iterations_q"],
+                              "seconds": s["seconds"]} for p, s in zip(probs, s_last)],
+            },
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

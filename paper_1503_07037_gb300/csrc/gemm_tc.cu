@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -40,6 +41,20 @@ constexpr int BM = 128;
 constexpr int BK = 32;        // FP32 elements per 128-byte swizzle row
 constexpr int UMMA_K = 8;     // K of one kind::tf32 instruction
 constexpr unsigned long long kWaitNs = 2000000000ull;
+// k-blocks (of 32) accumulated in TMEM before the partial sum moves to registers
+// in the 3xTF32 engine. The tensor-core FP32 accumulation is not round-to-
+// nearest; short chunks keep its bias at the level of FP32 rounding. The
+// environment variable CDMPT_SPLIT_CHUNK (1, 2, 4 or 0 = whole K) overrides
+// the default of 2 for tuning.
+int split_chunk() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("CDMPT_SPLIT_CHUNK");
+        v = e ? atoi(e) : 2;
+        if (v != 0 && v != 1 && v != 2 && v != 4) v = 2;
+    }
+    return v;
+}
 
 template <int BN, int STAGES, int SPLIT>
 struct Cfg {
@@ -222,7 +237,7 @@ __device__ __forceinline__ uint32_t rna_tf32(float x) {
 
 // ---------------------------------------------------------------- kernel
 
-template <int BN, int STAGES, int SPLIT>
+template <int BN, int STAGES, int SPLIT, int KCH>
 __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               int K, EpiParams<float> p, const double* skip, int* err) {
@@ -245,6 +260,9 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
     const int num_nt = (p.N + BN - 1) / BN;
     const int num_tiles = num_mt * num_nt;
     const int num_k = (K + BK - 1) / BK;
+    // K is accumulated in TMEM in chunks of kc k-blocks (KCH = 0: the whole K)
+    const int kc = KCH > 0 ? KCH : num_k;
+    const int nch = (num_k + kc - 1) / kc;
 
     auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
@@ -305,49 +323,51 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32<BN>();
-            uint32_t it = 0;
-            int lt = 0;
+            uint32_t it = 0, g = 0;
             bool ok = true, issued = false;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++lt) {
-                const int acc = lt & 1;
-                if (!mbar_wait(&tempty[acc], ((lt >> 1) & 1) ^ 1, abort_flag, err,
-                               DEV_TIMEOUT_ACCUM)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t tmem_d = tmem_base + (uint32_t)(acc * BN);
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (it / STAGES) & 1;
-                    uint64_t* ready = SPLIT == 3 ? &conv[s] : &full[s];
-                    if (!mbar_wait(ready, ph, abort_flag, err,
-                                   SPLIT == 3 ? DEV_TIMEOUT_CONV : DEV_TIMEOUT_FULL)) {
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nch && ok; ++c, ++g) {
+                    const int b = g & 1;
+                    if (!mbar_wait(&tempty[b], ((g >> 1) & 1) ^ 1, abort_flag, err,
+                                   DEV_TIMEOUT_ACCUM)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
-#pragma unroll
-                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                        const uint32_t off = kk * UMMA_K * 4;
-                        const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
-                        const uint32_t first = (kb | kk) != 0 ? 1u : 0u;
-                        if constexpr (SPLIT == 3) {
-                            const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
-                            const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
-                            mma_tf32(tmem_d, al, bh, idesc, first);
-                            mma_tf32(tmem_d, ah, bl, idesc, 1u);
-                            mma_tf32(tmem_d, ah, bh, idesc, 1u);
-                        } else {
-                            mma_tf32(tmem_d, ah, bh, idesc, first);
+                    const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
+                    const int kb0 = c * kc, kb1 = min(num_k, kb0 + kc);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        uint64_t* ready = SPLIT == 3 ? &conv[s] : &full[s];
+                        if (!mbar_wait(ready, ph, abort_flag, err,
+                                       SPLIT == 3 ? DEV_TIMEOUT_CONV : DEV_TIMEOUT_FULL)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+#pragma unroll
+                        for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                            const uint32_t off = kk * UMMA_K * 4;
+                            const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
+                            const uint32_t first = ((kb - kb0) | kk) != 0 ? 1u : 0u;
+                            if constexpr (SPLIT == 3) {
+                                const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
+                                const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
+                                mma_tf32(tmem_d, al, bh, idesc, first);
+                                mma_tf32(tmem_d, ah, bl, idesc, 1u);
+                                mma_tf32(tmem_d, ah, bh, idesc, 1u);
+                            } else {
+                                mma_tf32(tmem_d, ah, bh, idesc, first);
+                            }
+                        }
+                        issued = true;
+                        mma_commit(&empty[s]);
                     }
-                    issued = true;
-                    mma_commit(&empty[s]);
+                    if (!ok) break;
+                    mma_commit(&tfull[b]);
                 }
-                if (!ok) break;
-                mma_commit(&tfull[acc]);
             }
             if (!ok && issued) {
                 mma_commit(drain);
@@ -357,36 +377,76 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
     } else if (warp < 6) {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;     // TMEM lane quarter this warp may read
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         double dsum = 0.0;
-        int lt = 0;
-        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++lt) {
-            const int acc = lt & 1;
-            int ok = 1;
-            if (lane == 0)
-                ok = mbar_wait(&tfull[acc], (lt >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
+        uint32_t g = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
             const int mt = t % num_mt, nt = t / num_mt;
             const int m = mt * BM + 32 * q + lane;
-            const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tbase + c0, r);
+            bool ok = true;
+            if constexpr (KCH > 0) {
+                // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
+                float acc[BN];
+#pragma unroll
+                for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+                for (int c = 0; c < nch; ++c, ++g) {
+                    const int b = g & 1;
+                    int w = 1;
+                    if (lane == 0)
+                        w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (!w) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), r);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&tempty[b]);
+                }
+                if (!ok) break;
                 if (m < p.M) {
                     float local = 0.f;
-                    const int nb = nt * BN + c0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int n = nb + j;
-                        if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(r[j]));
+                    for (int j = 0; j < BN; ++j) {
+                        const int n = nt * BN + j;
+                        if (n < p.N) local += epi_apply(p, m, n, acc[j]);
                     }
                     dsum += (double)local;
                 }
+            } else {
+                const int b = g & 1;
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), r);
+                    if (m < p.M) {
+                        float local = 0.f;
+                        const int nb = nt * BN + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int n = nb + j;
+                            if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(r[j]));
+                        }
+                        dsum += (double)local;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&tempty[b]);
+                ++g;
             }
-            tc_fence_before();
-            mbar_arrive(&tempty[acc]);
         }
         if (p.dot) {
 #pragma unroll
@@ -486,13 +546,13 @@ int sm_count() {
     return n;
 }
 
-template <int BN, int STAGES, int SPLIT>
+template <int BN, int STAGES, int SPLIT, int KCH>
 cdmpt_status launch(int M, int N, int K, const float* X, int ldx, const float* Y, int ldy,
                     const EpiParams<float>& p, const double* skip, cudaStream_t s) {
     using C = Cfg<BN, STAGES, SPLIT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT, KCH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) {
             set_error(std::string("tcgen05 GEMM smem attribute: ") + cudaGetErrorString(e));
@@ -507,7 +567,7 @@ cdmpt_status launch(int M, int N, int K, const float* X, int ldx, const float* Y
     }
     const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_tc<BN, STAGES, SPLIT>
+    k_gemm_tc<BN, STAGES, SPLIT, KCH>
         <<<grid, C::THREADS, C::SMEM, s>>>(mx, my, K, p, skip, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -559,8 +619,14 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ld
     p.dot = ep.dot;
     p.E = ep.E;
     p.lde = ep.lde;
-    if (engine == CDMPT_GEMM_TC_TF32) return launch<256, 4, 1>(M, N, K, X, ldx, Y, ldy, p, skip, s);
-    return launch<128, 3, 3>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+    if (engine == CDMPT_GEMM_TC_TF32)
+        return launch<256, 4, 1, 0>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+    switch (split_chunk()) {
+        case 1: return launch<128, 3, 3, 1>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+        case 4: return launch<128, 3, 3, 4>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+        case 0: return launch<128, 3, 3, 0>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+        default: return launch<128, 3, 3, 2>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+    }
 }
 
 }  // namespace cdmpt

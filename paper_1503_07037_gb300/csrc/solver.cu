@@ -172,7 +172,6 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const T* A, const T* rhs_base, dou
     CDMPT_TRY(Ew<T>::axpby(P_, R_, count, 1.0, 0.0, sc + CG_DONE, cx.stream));
 
     int chunk = std::max(1, *iters_out);
-    if (cx.profile) chunk = 1;
     int launched = 0, iters = 0;
     while (true) {
         const size_t ev_first = cx.ev_used;
