@@ -1,0 +1,65 @@
+"""Micro-benchmark of the recursion's product kernel through the C ABI.
+
+  python -m paper_1503_07037_gb300.kernel_bench --n 4096 --engine tf32 --reps 5
+
+Times D = Z Z^T + I (the step's system matrix A_k = I + Z_k^2) on an N x N
+FP32 (or FP64) matrix with CUDA events on the launching stream, after three
+warm-up launches, and prints one JSON line with the duration and the
+algorithmic rate 2 N^3 / t. The input is a seeded symmetric matrix scaled like
+a recursion iterate (spectrum in [-1, 1]).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    import paper_1503_07037_gb300 as pkg
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "f64"])
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args()
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(1234)
+    dt = torch.float64 if a.engine == "f64" else torch.float32
+    Z = torch.randn(a.n, a.n, device=dev, generator=g, dtype=torch.float64)
+    Z = (Z + Z.T) / (2.0 * (2 * a.n) ** 0.5)
+    Z = Z.to(dt).contiguous()
+    D = torch.empty_like(Z)
+
+    def run():
+        if a.engine == "f64":
+            pkg.gemm_f64(Z, Z, D, gamma=1.0)
+        else:
+            pkg.gemm_f32(Z, Z, D, gamma=1.0, engine=a.engine)
+
+    for _ in range(a.warmup):
+        run()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(a.reps):
+        run()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / a.reps / 1e3
+    print(json.dumps({"kernel": "gemm", "engine": a.engine, "n": a.n, "ms": t * 1e3,
+                      "alg_tflops": 2.0 * a.n ** 3 / t / 1e12}))
+
+
+if __name__ == "__main__":
+    main()
