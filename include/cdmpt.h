@@ -154,6 +154,17 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
  * with H^(2) = 0. Errors: ERR_ARG if no solve has completed. */
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
 
+/* Spectral interval of a symmetric matrix from Gershgorin discs:
+ * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).
+ * Every eigenvalue of H lies in [bounds[0], bounds[1]]. cdmpt_solve needs
+ * beta (bounds[1] - bounds[0]) / 2^(n+1) < 1 so that X_0 of Eq. (Rec_F_2) keeps
+ * its spectrum inside [0, 1]; this call lets a caller pick n before solving.
+ * H: N x N FP64 device array with leading dimension ldh >= N. bounds: 2
+ * doubles of device memory. Uses 16 N bytes of temporary device memory
+ * (stream-ordered allocation). Asynchronous on stream.
+ * Errors: ERR_ARG (N < 1, ldh < N, NULL pointers), ERR_CUDA. */
+cdmpt_status cdmpt_spectral_bounds(const double* H, int N, int ldh, double* bounds, void* stream);
+
 /* Statistics of the last solve (copied into *st). */
 cdmpt_status cdmpt_get_stats(const cdmpt_handle* h, cdmpt_stats* st);
 

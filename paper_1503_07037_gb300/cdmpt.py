@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
 _lib = None
 EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opts", "cdmpt_set_H",
            "cdmpt_solve", "cdmpt_polarizability", "cdmpt_get_stats", "cdmpt_last_error",
-           "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64"]
+           "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64", "cdmpt_spectral_bounds"]
 
 
 def lib() -> ctypes.CDLL:
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_destroy": (V, [P]),
         "cdmpt_gemm_f32": (I, [I, I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_gemm_f64": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
+        "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -209,6 +210,16 @@ def gemm_f64(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, tran
                                 C.stride(0) if C is not None else 0, float(gamma), diag_block,
                                 trans_block, _ptr(dot), _ptr(E),
                                 E.stride(0) if E is not None else 0, _stream_ptr(stream)))
+
+
+def spectral_bounds(H, out=None, stream=None):
+    """Gershgorin interval [lo, hi] of a symmetric torch CUDA float64 matrix H (2-element tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=H.device)
+    _check(lib().cdmpt_spectral_bounds(_ptr(H), H.shape[0], H.stride(0), _ptr(out),
+                                       _stream_ptr(stream)))
+    return out
 
 
 # ------------------------------------------------------------- convenience

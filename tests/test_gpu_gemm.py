@@ -123,3 +123,17 @@ def test_gemm_rejects_misaligned_ld(cuda, cdmpt_lib):
     D = torch.zeros((64, 64), dtype=torch.float32, device=cuda)
     with pytest.raises(cdmpt_lib.CdmptError):
         cdmpt_lib.gemm_f32(X, X, D, engine="tf32", K=66)
+
+
+def test_spectral_bounds(cuda, cdmpt_lib):
+    """Gershgorin interval: equals the disc formula and contains every eigenvalue."""
+    import torch
+    import synthetic as syn
+    for p in (syn.workload("chain64"), syn.cubic_lattice((7, 7, 7), seed=2)):
+        H = torch.from_numpy(p.H0).to(cuda)
+        b = cdmpt_lib.spectral_bounds(H).cpu().numpy()
+        rad = np.abs(p.H0).sum(1) - np.abs(np.diag(p.H0))
+        lo, hi = np.min(np.diag(p.H0) - rad), np.max(np.diag(p.H0) + rad)
+        assert abs(b[0] - lo) < 1e-12 and abs(b[1] - hi) < 1e-12
+        ev = np.linalg.eigvalsh(p.H0)
+        assert b[0] <= ev[0] + 1e-12 and ev[-1] <= b[1] + 1e-12
