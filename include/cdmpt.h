@@ -165,6 +165,25 @@ cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
  * Errors: ERR_ARG (N < 1, ldh < N, NULL pointers), ERR_CUDA. */
 cdmpt_status cdmpt_spectral_bounds(const double* H, int N, int ldh, double* bounds, void* stream);
 
+/* Allocation-free cdmpt_spectral_bounds, for callers that must not allocate
+ * device memory: code that runs while a stream is being captured into a CUDA
+ * graph (plain cudaMalloc is not allowed there), code that runs under an
+ * allocator which already owns the whole device memory budget, and latency-
+ * critical loops where cudaFree would synchronize the device. The paper has
+ * no counterpart; this is an interface convenience.
+ * Same arguments, results and asynchrony as cdmpt_spectral_bounds; the caller
+ * still passes H and bounds. The per-row scratch sits in a fixed 512 KiB
+ * array of the library's static device memory, so N may be at most 32768
+ * (larger N returns ERR_ARG). That array is held on every GPU that loads the
+ * library until the process exits, and every call shares it: calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller. The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture begins. No call allocates or frees memory.
+ * Errors: ERR_ARG (N < 1, N > 32768, ldh < N, NULL pointers), ERR_CUDA. */
+cdmpt_status cdmpt_spectral_bounds_noalloc(const double* H, int N, int ldh, double* bounds,
+                                           void* stream);
+
 /* Statistics of the last solve (copied into *st). */
 cdmpt_status cdmpt_get_stats(const cdmpt_handle* h, cdmpt_stats* st);
 

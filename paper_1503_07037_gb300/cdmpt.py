@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
 _lib = None
 EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opts", "cdmpt_set_H",
            "cdmpt_solve", "cdmpt_polarizability", "cdmpt_get_stats", "cdmpt_last_error",
-           "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64", "cdmpt_spectral_bounds"]
+           "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64", "cdmpt_spectral_bounds",
+           "cdmpt_spectral_bounds_noalloc"]
 
 
 def lib() -> ctypes.CDLL:
@@ -101,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_gemm_f32": (I, [I, I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_gemm_f64": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
+        "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -219,6 +221,13 @@ def spectral_bounds(H, out=None, stream=None):
         out = torch.empty(2, dtype=torch.float64, device=H.device)
     _check(lib().cdmpt_spectral_bounds(_ptr(H), H.shape[0], H.stride(0), _ptr(out),
                                        _stream_ptr(stream)))
+    return out
+
+
+def spectral_bounds_noalloc(H, out, stream=None):
+    """spectral_bounds without any device allocation; `out` (2 float64 on the GPU) is required."""
+    _check(lib().cdmpt_spectral_bounds_noalloc(_ptr(H), H.shape[0], H.stride(0), _ptr(out),
+                                               _stream_ptr(stream)))
     return out
 
 

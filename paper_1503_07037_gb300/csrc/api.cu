@@ -284,6 +284,15 @@ cdmpt_status cdmpt_spectral_bounds(const double* H, int N, int ldh, double* boun
     return gershgorin(H, N, ldh, bounds, (cudaStream_t)stream);
 }
 
+cdmpt_status cdmpt_spectral_bounds_noalloc(const double* H, int N, int ldh, double* bounds,
+                                           void* stream) {
+    if (!H || !bounds || N < 1 || ldh < N) {
+        set_error("spectral_bounds_noalloc: need H, bounds, N >= 1 and ldh >= N");
+        return CDMPT_ERR_ARG;
+    }
+    return gershgorin_noalloc(H, N, ldh, bounds, (cudaStream_t)stream);
+}
+
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha) {
     if (!h || !alpha) return CDMPT_ERR_ARG;
     if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "polarizability: no completed solve");

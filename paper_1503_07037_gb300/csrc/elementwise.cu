@@ -354,6 +354,14 @@ __global__ void k_gershgorin_reduce(const double* __restrict__ lohi, int N, doub
 
 thread_local long long g_launches = 0;
 
+// Scratch of cdmpt_spectral_bounds_noalloc: the two disc ends of every row,
+// for at most kNoAllocMaxN rows (2 x 32768 doubles = 512 KiB). It lives in the
+// module's static device memory, so every GPU that loads the library holds it
+// until the process exits. The row pass writes entries 0 .. 2N-1 before the
+// reduction reads them, so no entry has to start at zero.
+constexpr int kNoAllocMaxN = 32768;
+__device__ __align__(256) double g_bounds_scratch[2 * kNoAllocMaxN];
+
 }  // namespace
 
 void count_launch(int k) { g_launches += k; }
@@ -484,6 +492,46 @@ cdmpt_status gershgorin(const double* H, int N, int ld, double* out2, cudaStream
     k_gershgorin_reduce<<<1, 1024, 0, s>>>(lohi, N, out2);
     LAUNCH_CHECK();
     CDMPT_CUDA_TRY(cudaFreeAsync(lohi, s));
+    return CDMPT_OK;
+}
+
+// Allocation-free variant of gershgorin(): same two kernels, with the per-row
+// scratch in g_bounds_scratch instead of a stream-ordered allocation.
+// Host code cannot pass g_bounds_scratch itself to a kernel (on the host the
+// name is a stand-in, not a device address); the device address is looked up
+// with cudaGetSymbolAddress once per device, with that device current, on the
+// first call made on it.
+cdmpt_status gershgorin_noalloc(const double* H, int N, int ld, double* out2, cudaStream_t s) {
+    if (N > kNoAllocMaxN) {
+        set_error("spectral_bounds_noalloc: N = " + std::to_string(N) +
+                  " exceeds the static scratch limit of " + std::to_string(kNoAllocMaxN) +
+                  " rows; use cdmpt_spectral_bounds");
+        return CDMPT_ERR_ARG;
+    }
+    static std::mutex mu;
+    static double* addr[64] = {nullptr};
+    int dev = 0;
+    CDMPT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("spectral_bounds_noalloc: device ordinal out of range");
+        return CDMPT_ERR_ARG;
+    }
+    double* lohi = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!addr[dev]) {
+            void* p = nullptr;
+            CDMPT_CUDA_TRY(cudaGetSymbolAddress(&p, g_bounds_scratch));
+            addr[dev] = (double*)p;
+        }
+        lohi = addr[dev];
+    }
+    const int warps_per_block = kThreads / 32;
+    k_gershgorin_rows<<<(N + warps_per_block - 1) / warps_per_block, kThreads, 0, s>>>(H, N, ld,
+                                                                                        lohi);
+    LAUNCH_CHECK();
+    k_gershgorin_reduce<<<1, 1024, 0, s>>>(lohi, N, out2);
+    LAUNCH_CHECK();
     return CDMPT_OK;
 }
 
