@@ -6,8 +6,13 @@ perturbation along x, N_occ = N/2, n = 14 recursion steps, solved canonically
 at beta = 5, 20 and 80: three full solves (occupation loop, first-order
 response, mu1, polarizability) per step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|mixed]
-                  [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
+                  [--impl ours|reference] [--no-compare] [--no-cpu-baseline]
+
+The timed precision defaults to mixed (TF32 sweeps, split-TF32 refinement and
+response); one step of FP32 with split-TF32 products and one with CUDA-core
+FFMA products are timed beside it ("modes"), and every mode's P0 and P1 are
+compared with the FP64 oracle at the three temperatures ("error").
 
 --impl reference times the FP64 CPU oracle (exact diagonalisation) on the
 host cores, one solve of the same workload per step.
@@ -36,6 +41,9 @@ LATTICE = (16, 16, 16)
 NSTEPS_REC = 14
 WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {5,20,80}"
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
+# DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
+# profiles/ (per engine); None until the kernel's counters are re-taken after a change
+TRAFFIC = {2: None, 3: None}
 
 
 def dist_env():
@@ -177,6 +185,8 @@ def run_reference(args):
 # --------------------------------------------------------------------------- our path
 
 def run_ours(args):
+    import ctypes
+
     import numpy as np
     import torch
 
@@ -206,106 +216,132 @@ def run_ours(args):
     probs = problems()
     N, D = probs[0].N, probs[0].D
     stream = torch.cuda.current_stream()
-    h = pkg.Handle(precision=args.precision, profile=True, stream=stream)
     H0 = torch.from_numpy(probs[0].H0).to(dev)
     H1 = torch.from_numpy(probs[0].H1).to(dev)
-    h.set_H(H0, H1)                 # resident in HBM before the timed region
     P0 = torch.empty((N, N), dtype=torch.float64, device=dev)
     P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev)
-    import ctypes
     mu = ctypes.c_double()
     mu1 = np.zeros(D)
 
-    def step(stats_acc=None):
+    def make(precision, engine="auto"):
+        h = pkg.Handle(precision=precision, engine=engine, profile=True, stream=stream)
+        h.set_H(H0, H1)                 # resident in HBM before any timed region
+        return h
+
+    def step(h, stats_acc=None, outs=None):
         for p in probs:
             pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0.data_ptr(), P1.data_ptr(),
                           ctypes.addressof(mu), mu1.ctypes.data, 1)
             if stats_acc is not None:
                 stats_acc.append(h.stats())
+            if outs is not None:
+                outs.append((P0.cpu().numpy(), P1[0].cpu().numpy()))
 
+    def timed_steps(h, k, stats_acc):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(k):
+            step(h, stats_acc)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    h = make(args.precision)
     for _ in range(args.warmup):
-        step()
+        step(h)
     clocks = ClockSampler(local)
-    barrier()
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     st_all = []
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step(st_all)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms = timed_steps(h, args.steps, st_all)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms)
     barrier()
     solves = args.steps * len(probs) * world
     value = solves / (ms / 1000.0)
 
-    # dominant kernel: the GEMM (all launches are N x N x N); events on the library's stream
-    gemm_ms = sum(s["gemm_ms"] for s in st_all)
-    gemm_timed = sum(s["gemm_timed"] for s in st_all)
-    gemm_flops = sum(s["gemm_flops"] for s in st_all)
-    tensor_flops = sum(s["tensor_flops"] for s in st_all)
-    launches = sum(s["kernel_launches"] for s in st_all)
-    avg_gemm_s = gemm_ms / 1000.0 / max(1, gemm_timed)
-    per_launch_flops = 2.0 * N * N * N
-    achieved = per_launch_flops / avg_gemm_s / 1e12
+    # roofline of the dominant kernel: the GEMM engine with the most device time
+    eng_ms = [sum(s["engine_ms"][e] for s in st_all) for e in range(4)]
+    eng_n = [sum(s["engine_launches"][e] for s in st_all) for e in range(4)]
+    eng_fl = [sum(s["engine_flops"][e] for s in st_all) for e in range(4)]
+    dom = max(range(4), key=lambda e: eng_ms[e])
+    names = {1: "CUDA-core FFMA/DFMA", 2: "tcgen05 TF32", 3: "tcgen05 3xTF32"}
+    avg_s = eng_ms[dom] / 1000.0 / max(1, eng_n[dom])
+    per_launch = eng_fl[dom] / max(1, eng_n[dom])     # 2 N^3 for every launch here
+    achieved = per_launch / avg_s / 1e12
     pk = peaks()
     if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25,
-                "unit": "TFLOP/s", "frac": achieved / 1.25, "traffic": None,
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None,
                 "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
     else:
         peak_tf32 = pk["bf16_sustained"] * TF32_OVER_BF16
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf32, "traffic": None,
+                "frac": achieved / peak_tf32, "traffic": TRAFFIC.get(dom),
+                "kernel": f"k_gemm_tc ({names.get(dom)}), 2 N^3 = {per_launch:.3e} flop per "
+                          f"launch, mean {avg_s * 1e3:.3f} ms over {eng_n[dom]} launches",
                 "peak_note": f"tf32 = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
-                             f"{TF32_OVER_BF16:.4f} (nominal 1.1/2.25); achieved counts "
-                             "algorithmic 2N^3 flops per GEMM launch",
-                "tensor_pipe_tflops": tensor_flops / gemm_flops * achieved if gemm_flops else None}
-    gemm_share = gemm_ms / (ms / world if world else ms) if ms else None
+                             f"{TF32_OVER_BF16:.4f} (nominal 1.1/2.25) of measured",
+                "tensor_pipe_frac": achieved * (3 if dom == 3 else 1) / peak_tf32}
+    launches = sum(s["kernel_launches"] for s in st_all)
+    gemm_ms_total = sum(eng_ms)
 
-    # end to end through the public API with host buffers
-    e2e = None
-    if rank == 0 or True:
-        H0h = torch.from_numpy(probs[0].H0).pin_memory()
-        H1h = torch.from_numpy(probs[0].H1).pin_memory()
-        P0h = torch.empty((N, N), dtype=torch.float64).pin_memory()
-        P1h = torch.empty((D, N, N), dtype=torch.float64).pin_memory()
-        ke = max(1, min(args.steps, 2))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            pkg.set_H(h.h, N, H0h.data_ptr(), D, H1h.data_ptr(), 0)
-            for p in probs:
-                pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0h.data_ptr(), P1h.data_ptr(),
-                              ctypes.addressof(mu), mu1.ctypes.data, 0)
-        torch.cuda.synchronize()
-        dte = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": ke * len(probs) * world / dte, "unit": "solves/s",
-               "h2d_bytes_per_step": (H0h.numel() + H1h.numel()) * 8,
-               "d2h_bytes_per_step": len(probs) * (P0h.numel() + P1h.numel()) * 8,
-               "steps": ke}
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    H0h = torch.from_numpy(probs[0].H0).pin_memory()
+    H1h = torch.from_numpy(probs[0].H1).pin_memory()
+    P0h = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    P1h = torch.empty((D, N, N), dtype=torch.float64).pin_memory()
+    ke = max(1, min(args.steps, 2))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        pkg.set_H(h.h, N, H0h.data_ptr(), D, H1h.data_ptr(), 0)
+        for p in probs:
+            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0h.data_ptr(), P1h.data_ptr(),
+                          ctypes.addressof(mu), mu1.ctypes.data, 0)
+    torch.cuda.synchronize()
+    dte = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": ke * len(probs) * world / dte, "unit": "solves/s",
+           "h2d_bytes_per_step": (H0h.numel() + H1h.numel()) * 8,
+           "d2h_bytes_per_step": len(probs) * (P0h.numel() + P1h.numel()) * 8, "steps": ke}
+    h.set_H(H0, H1)
+
+    # the other precisions on the same workload (one step each), for "mixed vs FP32"
+    modes = {}
+    outs_by_mode = {}
+    if not args.no_compare:
+        for label, prec, eng in (("fp32_3xtf32", "fp32", "3xtf32"), ("fp32_ffma", "fp32", "simt"),
+                                 (args.precision, args.precision, "auto")):
+            hm = make(prec, eng) if label != args.precision else h
+            step(hm)            # warm-up (allocations)
+            stm = []
+            msm = timed_steps(hm, 1, stm)
+            outs = []
+            step(hm, None, outs)
+            outs_by_mode[label] = outs
+            modes[label] = {"solves_per_s": len(probs) / (msm / 1000.0), "ms_per_step": msm}
+            if hm is not h:
+                hm.close()
 
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # bounded oracle sample: the beta = 20 solve of the workload (one eigendecomposition)
+        # bounded oracle sample: the beta = 20 solve of the workload, eigendecomposition included
+        import oracle
         v, dt, res = time_oracle([20.0])
         cpu = {"value": v, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"1 of the 3 solves of a step (beta=20, N=4096), {dt:.1f} s"}
-        # error of our beta = 20 outputs against it
-        with pkg.Handle(precision=args.precision, stream=stream) as h2:
-            h2.set_H(H0, H1)
-            r = h2.solve(20.0, probs[1].nocc, probs[1].n)
-        ref = res[20.0]
-        import oracle
-        err = {"P0": oracle.rel_frobenius(r["P0"].cpu().numpy(), ref["P0"]),
-               "P1": oracle.rel_frobenius(r["P1"][0].cpu().numpy(), ref["P1"][0]),
-               "mu1": abs(r["mu1"][0] - ref["mu1"][0]) / abs(ref["mu1"][0]),
-               "vs": "oracle, recursion-exact function, beta=20"}
+        if outs_by_mode:
+            eig = np.linalg.eigh(probs[0].H0)
+            refs = {p.beta: oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=eig)
+                    for p in probs}
+            err = {"vs": "oracle, recursion-exact function (relative Frobenius)"}
+            for label, outs in outs_by_mode.items():
+                err[label] = {f"beta={p.beta:g}": {
+                    "P0": oracle.rel_frobenius(o[0], refs[p.beta]["P0"]),
+                    "P1": oracle.rel_frobenius(o[1], refs[p.beta]["P1"][0])}
+                    for p, o in zip(probs, outs)}
 
     if rank == 0:
         s_last = st_all[-len(probs):]
@@ -317,25 +353,27 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "gemm": {"fp32": "tcgen05 3xTF32", "fp64": "CUDA-core DFMA",
-                                "mixed": "tcgen05 TF32"}[args.precision],
-                       "l2": "no flush: working set (trajectory of 29 N x N matrices, "
-                             f"{29 * N * N * (8 if args.precision == 'fp64' else 4) / 2**30:.1f}"
-                             " GiB) exceeds the 129 MB L2",
+                                "mixed": "tcgen05 TF32 sweeps, 3xTF32 refinement and response"
+                                }[args.precision],
+                       "l2": "no flush: working set (trajectory of 29 N x N matrices plus "
+                             "their TF32 splits, > 1.8 GiB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
+            "modes": modes,
             "error": err,
             "detail": {
-                "gemm_share_of_step_time": gemm_share,
-                "gemm_avg_ms": avg_gemm_s * 1000,
-                "gemm_launches_per_step": gemm_timed / args.steps,
-                "algorithmic_tflops_per_step": gemm_flops / args.steps / 1e12,
+                "gemm_share_of_step_time": gemm_ms_total / (ms / world) if ms else None,
+                "gemm_ms_per_engine": {names.get(e, e): eng_ms[e] / args.steps for e in range(4)
+                                       if eng_n[e]},
+                "gemm_launches_per_step": sum(eng_n) / args.steps,
+                "algorithmic_tflop_per_step": sum(eng_fl) / args.steps / 1e12,
                 "per_beta": [{"beta": p.beta, "mu_iterations": s["mu_iterations"],
                               "cg_sweeps": s["cg_iterations_sweeps"],
-                              "cg_last_sweep": s["cg_iterations_last_sweep"],
+                              "cg_refine": s["cg_iterations_refine"],
                               "cg_response": s["cg_iterations_response"],
                               "cg_q": s["cg_iterations_q"],
                               "seconds": s["seconds"]} for p, s in zip(probs, s_last)],
@@ -353,9 +391,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the one-step runs of the other precisions")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -106,6 +106,9 @@ typedef struct {
     double mu, trace_P0, trace_Q;  /* final mu, Tr P0, Tr dP0/dmu */
     double occupation_error;       /* |Tr P0 - N_occ| + sum_d |Tr P1_d| */
     double seconds;                /* host wall time of the last solve */
+    double engine_ms[4];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
+    int engine_launches[4];        /* timed GEMM launches per engine */
+    double engine_flops[4];        /* algorithmic flops of those launches */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -154,6 +157,19 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
  * with H^(2) = 0. Errors: ERR_ARG if no solve has completed. */
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
 
+/* Adjoint (vector-Jacobian product) of the last cdmpt_solve on this handle:
+ * gradH0 = d Tr[G0 P0] / d H0, the gradient of any scalar loss L(P0) with
+ * dL/dP0 = G0, under the canonical constraint Tr P0 = N_occ (mu follows H0).
+ * Computed by a reverse sweep through the stored recursion trajectory
+ * (Eq. Rec_F_2 differentiated step by step, one linear solve with the same
+ * step matrix T_k per step, Sec. II), then the chemical-potential term.
+ * The Hessian of the free energy is symmetric, so gradH0 equals the canonical
+ * first-order response P1 for the perturbation H1 = sym(G0) (App. B).
+ * G0, gradH0: N x N FP64, host or device per on_device. Must follow a
+ * successful cdmpt_solve on this handle (its trajectory is reused).
+ * Errors: ERR_ARG (no solve yet, NULL pointers), ERR_CG_MAXITER, ERR_CUDA. */
+cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int on_device);
+
 /* Spectral interval of a symmetric matrix from Gershgorin discs:
  * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).
  * Every eigenvalue of H lies in [bounds[0], bounds[1]]. cdmpt_solve needs
@@ -192,6 +208,44 @@ const char* cdmpt_last_error(const cdmpt_handle* h);
 
 /* Free the handle and all device memory it owns. NULL is ignored. */
 void cdmpt_destroy(cdmpt_handle* h);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent canonical solves of uneven size N_b (b < B), each with the
+ * same number D of perturbation directions, advanced in lockstep: every
+ * product of a recursion step is one grouped persistent tcgen05 launch over
+ * all systems, every vector update one grouped launch; each system keeps its
+ * own CG scalars and chemical potential, and converged systems are skipped.
+ * Storage FP32, split-TF32 products (only CDMPT_FP32 is accepted).
+ */
+typedef struct cdmpt_batch cdmpt_batch;
+
+/* Create a batch of B systems of sizes N[0..B-1] with D directions each.
+ * Errors: ERR_ARG, ERR_UNSUPPORTED (precision other than FP32, or no sm_103
+ * device), ERR_OOM. */
+cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int D,
+                                cdmpt_batch** out);
+
+/* Load H0[b] (N_b x N_b) and H1[b] (D x N_b x N_b), FP64 row-major, host or
+ * device pointers per on_device, and allocate the trajectory for n steps. */
+cdmpt_status cdmpt_batch_set_H(cdmpt_batch* b, const double* const* H0, const double* const* H1,
+                               int n, int on_device);
+
+/* Solve all systems (Algorithm 1 to first order): beta[b], nocc[b] per
+ * system; outputs per system (arrays of B pointers, entries may be NULL):
+ * P0[b] (N_b x N_b), P1[b] (D x N_b x N_b); mu[B], mu1[B*D], alpha[B*D] on the
+ * host (alpha_d = -2 Tr[P1_d H1_d]). Errors as for cdmpt_solve. */
+cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double* nocc, int n,
+                               double* const* P0, double* const* P1, double* mu, double* mu1,
+                               double* alpha, int out_on_device);
+
+/* Statistics of the last batch solve (N holds B). */
+cdmpt_status cdmpt_batch_get_stats(const cdmpt_batch* b, cdmpt_stats* st);
+
+/* Last error of the batch ("" if none). */
+const char* cdmpt_batch_last_error(const cdmpt_batch* b);
+
+/* Free the batch and its device memory. NULL is ignored. */
+void cdmpt_batch_destroy(cdmpt_batch* b);
 
 /*
  * Dense building block exposed for testing and benchmarking: the product of

@@ -65,17 +65,26 @@ class Stats(ctypes.Structure):
         ("mu", ctypes.c_double), ("trace_P0", ctypes.c_double), ("trace_Q", ctypes.c_double),
         ("occupation_error", ctypes.c_double),
         ("seconds", ctypes.c_double),
+        ("engine_ms", ctypes.c_double * 4),
+        ("engine_launches", ctypes.c_int * 4),
+        ("engine_flops", ctypes.c_double * 4),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 _lib = None
 EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opts", "cdmpt_set_H",
            "cdmpt_solve", "cdmpt_polarizability", "cdmpt_get_stats", "cdmpt_last_error",
            "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64", "cdmpt_spectral_bounds",
-           "cdmpt_spectral_bounds_noalloc"]
+           "cdmpt_spectral_bounds_noalloc", "cdmpt_vjp_P0", "cdmpt_batch_create",
+           "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
+           "cdmpt_batch_last_error", "cdmpt_batch_destroy"]
 
 
 def lib() -> ctypes.CDLL:
@@ -103,6 +112,13 @@ def lib() -> ctypes.CDLL:
         "cdmpt_gemm_f64": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
         "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
+        "cdmpt_vjp_P0": (I, [P, P, P, I]),
+        "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
+        "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
+        "cdmpt_batch_solve": (I, [P, P, P, I, P, P, P, P, P, I]),
+        "cdmpt_batch_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+        "cdmpt_batch_last_error": (ctypes.c_char_p, [P]),
+        "cdmpt_batch_destroy": (V, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -301,6 +317,14 @@ class Handle:
     def polarizability(self):
         return polarizability(self.h, self.D)
 
+    def vjp_P0(self, G0):
+        """d Tr[G0 P0] / d H0 for the last solve (torch CUDA float64 in and out)."""
+        import torch
+        G = G0.detach().to(torch.float64).contiguous()
+        out = torch.empty_like(G)
+        _check(lib().cdmpt_vjp_P0(self.h, _ptr(G), _ptr(out), 1 if G.is_cuda else 0), self.h)
+        return out
+
     def stats(self):
         return get_stats(self.h)
 
@@ -320,6 +344,110 @@ class Handle:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Batched canonical solves of uneven-size Hamiltonians (cdmpt_batch_*).
+
+    B = Batch(sizes, D); B.set_H(H0_list, H1_list, n); r = B.solve(betas, noccs, n)
+    returns dict(P0=[...], P1=[...], mu, mu1 (B x D), alpha (B x D)), P0/P1 as
+    float64 torch CUDA tensors.
+    """
+
+    def __init__(self, sizes, D, stream=None, **kw):
+        o = default_opts()
+        o.precision = FP32
+        for k, v in kw.items():
+            setattr(o, k, v)
+        o.stream = _stream_ptr(stream)
+        self.sizes = [int(s) for s in sizes]
+        self.D = int(D)
+        arr = (ctypes.c_int * len(self.sizes))(*self.sizes)
+        h = ctypes.c_void_p()
+        self._err = lambda: (lib().cdmpt_batch_last_error(h) or b"").decode()
+        st = lib().cdmpt_batch_create(ctypes.byref(o), len(self.sizes), arr, self.D,
+                                      ctypes.byref(h))
+        if st != 0:
+            raise CdmptError(st, (lib().cdmpt_batch_last_error(None) or b"").decode())
+        self.h = h.value
+        self._keep = None
+
+    def _check(self, st):
+        if st != 0:
+            m = lib().cdmpt_batch_last_error(self.h)
+            raise CdmptError(st, m.decode() if m else "")
+
+    def set_H(self, H0s, H1s, n):
+        import torch
+        H0t = [torch.as_tensor(np.ascontiguousarray(h), dtype=torch.float64).cuda() for h in H0s]
+        H1t = [torch.as_tensor(np.ascontiguousarray(h), dtype=torch.float64).cuda() for h in H1s]
+        P = ctypes.c_void_p
+        a0 = (P * len(H0t))(*[t.data_ptr() for t in H0t])
+        a1 = (P * len(H1t))(*[t.data_ptr() for t in H1t])
+        self._check(lib().cdmpt_batch_set_H(self.h, a0, a1, int(n), 1))
+        torch.cuda.synchronize()
+
+    def solve(self, betas, noccs, n):
+        import torch
+        B, D = len(self.sizes), self.D
+        P0 = [torch.empty((N, N), dtype=torch.float64, device="cuda") for N in self.sizes]
+        P1 = [torch.empty((D, N, N), dtype=torch.float64, device="cuda") for N in self.sizes]
+        P = ctypes.c_void_p
+        a0 = (P * B)(*[t.data_ptr() for t in P0])
+        a1 = (P * B)(*[t.data_ptr() for t in P1])
+        be = np.ascontiguousarray(betas, dtype=np.float64)
+        no = np.ascontiguousarray(noccs, dtype=np.float64)
+        mu = np.zeros(B)
+        mu1 = np.zeros(B * max(D, 1))
+        al = np.zeros(B * max(D, 1))
+        self._check(lib().cdmpt_batch_solve(self.h, be.ctypes.data, no.ctypes.data, int(n), a0, a1,
+                                            mu.ctypes.data, mu1.ctypes.data, al.ctypes.data, 1))
+        return {"P0": P0, "P1": P1, "mu": mu, "mu1": mu1[:B * D].reshape(B, D),
+                "alpha": al[:B * D].reshape(B, D)}
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().cdmpt_batch_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().cdmpt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DensityMatrix:
+    """Differentiable canonical density matrix P0(H0) (torch.autograd).
+
+    P0 = DensityMatrix.apply(H0, beta, nocc, n, handle) returns P0 for the
+    symmetric CUDA float64 tensor H0; backward gives dL/dH0 through the
+    hand-written adjoint of the recursion (cdmpt_vjp_P0). The handle keeps the
+    trajectory of the forward solve, so call backward before the next solve on
+    the same handle.
+    """
+
+    @staticmethod
+    def apply(H0, beta, nocc, n, handle):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, H):
+                handle.set_H(H.detach(), None)
+                r = handle.solve(beta, nocc, n, want_P1=False)
+                return r["P0"]
+
+            @staticmethod
+            def backward(ctx, G):
+                return handle.vjp_P0(G)
+
+        return _Fn.apply(H0)
 
 
 def solve(H0, H1, beta, nocc, n, precision="fp32", **kw):

@@ -246,13 +246,8 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
     } else {
         if (!h->sf) h->sf = new (std::nothrow) Solver<float>();
         if (!h->sf) return fail_msg(h, CDMPT_ERR_OOM, "solver allocation");
-        Context& cx = h->cx;
-        const int saved = cx.engine;
-        if (h->opts.precision == CDMPT_MIXED_TF32 && cx.engine == CDMPT_GEMM_AUTO)
-            cx.engine = CDMPT_GEMM_TC_TF32;
-        s = h->sf->solve(cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts, beta,
-                         nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
-        cx.engine = saved;
+        s = h->sf->solve(h->cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts,
+                         beta, nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
     }
     h->st.kernel_launches = (int)(launch_count() - launches0);
     h->st.seconds =
@@ -266,6 +261,10 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
             if (cudaEventElapsedTime(&e, h->cx.ev[2 * i], h->cx.ev[2 * i + 1]) == cudaSuccess) {
                 ms += e;
                 ++timed;
+                const int eng = h->cx.ev_engine[i] & 3;
+                h->st.engine_ms[eng] += e;
+                h->st.engine_launches[eng] += 1;
+                h->st.engine_flops[eng] += h->cx.ev_flops[i];
             }
         }
         h->st.gemm_ms = ms;
@@ -291,6 +290,38 @@ cdmpt_status cdmpt_spectral_bounds_noalloc(const double* H, int N, int ldh, doub
         return CDMPT_ERR_ARG;
     }
     return gershgorin_noalloc(H, N, ldh, bounds, (cudaStream_t)stream);
+}
+
+cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (!G0 || !gradH0) return fail_msg(h, CDMPT_ERR_ARG, "vjp_P0: NULL pointer");
+    if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "vjp_P0: no completed solve on this handle");
+    cudaStream_t s = h->cx.stream;
+    const size_t bytes = (size_t)h->N * h->N * sizeof(double);
+    const double* g = G0;
+    double* out = gradH0;
+    double* tmp = nullptr;
+    if (!on_device) {
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 2 * bytes, s));
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(tmp, G0, bytes, cudaMemcpyHostToDevice, s));
+        g = tmp;
+        out = tmp + (size_t)h->N * h->N;
+    }
+    cdmpt_stats keep = h->st;
+    h->cx.st = &h->st;
+    cdmpt_status st;
+    if (h->opts.precision == CDMPT_FP64)
+        st = h->sd ? h->sd->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
+    else
+        st = h->sf ? h->sf->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
+    h->st = keep;
+    if (st == CDMPT_OK && !on_device) {
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, out, bytes, cudaMemcpyDeviceToHost, s));
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st != CDMPT_OK) return fail(h, st);
+    return CDMPT_OK;
 }
 
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha) {
@@ -354,8 +385,30 @@ cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X,
         set_error("gemm_f32: unknown engine");
         return CDMPT_ERR_ARG;
     }
-    return gemm_tc_f32(engine == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : engine, M, Ncols, K, X,
-                       ldx, Y, ldy, D, ldd, ep, nullptr, s);
+    if ((ldx & 3) || (ldy & 3) || (((uintptr_t)X) & 15) || (((uintptr_t)Y) & 15) || K < 1) {
+        set_error("gemm_f32: tcgen05 engines need 16-byte aligned X, Y, ld a multiple of 4, K >= 1");
+        return CDMPT_ERR_ARG;
+    }
+    // The tensor-core engines read TF32-split operands; split X and Y into
+    // stream-ordered temporaries (the solver keeps splits resident instead).
+    const size_t nx = (size_t)M * ldx, ny = (size_t)Ncols * ldy;
+    const size_t px = (nx + 63) / 64 * 64, py = (ny + 63) / 64 * 64;
+    float* tmp = nullptr;
+    CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, (2 * px + 2 * py) * sizeof(float), s));
+    Operand<float> ox, oy;
+    ox.x = X;
+    ox.hi = tmp;
+    ox.lo = tmp + px;
+    oy.x = Y;
+    oy.hi = tmp + 2 * px;
+    oy.lo = tmp + 2 * px + py;
+    cdmpt_status st = split_tf32(X, (nx + 3) / 4 * 4, tmp, tmp + px, s);
+    if (st == CDMPT_OK) st = split_tf32(Y, (ny + 3) / 4 * 4, tmp + 2 * px, tmp + 2 * px + py, s);
+    if (st == CDMPT_OK)
+        st = gemm_tc_f32(engine == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : engine, M, Ncols, K, ox,
+                         ldx, oy, ldy, D, ldd, ep, nullptr, s);
+    cudaFreeAsync(tmp, s);
+    return st;
 }
 
 cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,

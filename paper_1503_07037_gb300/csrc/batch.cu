@@ -1,0 +1,966 @@
+// Batched canonical solves: B Hamiltonians of uneven size N_b, each with D
+// perturbation directions, advanced in lockstep (Algorithm 1 per system).
+//
+// Every product of a step is ONE grouped persistent tcgen05 launch over all
+// systems (k_gemm_tc<..., GROUPED> walking a descriptor array of per-system
+// problems), and every vector operation is one grouped elementwise launch.
+// Each system keeps its own CG scalars, convergence flag and chemical
+// potential on the device; a converged system is skipped through its flag
+// (its GEMM tiles and elementwise blocks return at once). Storage is FP32 with
+// split-TF32 (3xTF32) products, as in the single-system FP32 mode.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "cdmpt.h"
+#include "batch_kernels.cuh"
+#include "gemm_problem.cuh"
+#include "internal.cuh"
+#include "solver.cuh"
+
+namespace cdmpt {
+
+namespace {
+
+constexpr int kEngine = CDMPT_GEMM_TC_3XTF32;
+constexpr int kSlots = 64;
+
+struct Mat {   // FP32 matrix stack with TF32 split
+    float* x = nullptr;
+    float* hi = nullptr;
+    float* lo = nullptr;
+};
+
+struct Sys {
+    int N = 0, ld = 0;
+    size_t blk = 0;
+    double* H0 = nullptr;     // N x ld FP64
+    double* H1 = nullptr;     // D x N x ld FP64
+    std::vector<Mat> Z, W;
+    Mat R, P, Q, S, A1, RHS, Z1a, Z1b, Qmu;
+    double* sc = nullptr;     // kSlots doubles
+    double gmin = 0, gmax = 0, trH0 = 0;
+    // host-side state of the current solve
+    double beta = 0, nocc = 0, s2 = 0, mu = 0, lo = 0, hi = 0;
+    bool converged = false;
+};
+
+enum BSlot { B_TRZ = 8, B_ZZ = 9, B_TRQ = 10, B_TRZ1 = 16, B_ALPHA = 32 };
+
+}  // namespace
+
+}  // namespace cdmpt
+
+using namespace cdmpt;
+
+struct cdmpt_batch {
+    cdmpt_opts opts;
+    int B = 0, D = 0, n_alloc = -1;
+    std::vector<Sys> sys;
+    std::vector<void*> allocs;
+    double* inactive = nullptr;   // device flag per system: 1 while skipped
+    // tensor-map cache: (X hi, rows of X, Y hi) -> first of four maps in the device table
+    std::map<std::tuple<const void*, int, const void*>, int> map_index;
+    std::vector<CUtensorMap> maps_host;
+    CUtensorMap* maps_dev = nullptr;
+    int maps_uploaded = 0, maps_cap = 0;
+    // staging ring for per-launch descriptor arrays
+    char* stage_host = nullptr;
+    char* stage_dev = nullptr;
+    size_t stage_slot = 0, stage_slots = 0, slot_bytes = 0;
+    double* pinned = nullptr;     // scalar readback, B x kSlots
+    Context cx;                   // stream, profile events, statistics hookup
+    cdmpt_stats st;
+    std::string err;
+    bool have_H = false;
+};
+
+namespace {
+
+cdmpt_status bfail(cdmpt_batch* b, cdmpt_status s) {
+    if (b) b->err = get_error();
+    return s;
+}
+
+cdmpt_status bfail_msg(cdmpt_batch* b, cdmpt_status s, const std::string& m) {
+    set_error(m);
+    return bfail(b, s);
+}
+
+cdmpt_status grab(cdmpt_batch* b, size_t bytes, void** out) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch: device allocation of " + std::to_string(bytes) + " bytes failed");
+        return CDMPT_ERR_OOM;
+    }
+    if (cudaMemset(p, 0, bytes) != cudaSuccess) return CDMPT_ERR_CUDA;
+    b->allocs.push_back(p);
+    *out = p;
+    return CDMPT_OK;
+}
+
+cdmpt_status grab_mat(cdmpt_batch* b, size_t elems, Mat* m, bool split) {
+    CDMPT_TRY(grab(b, elems * sizeof(float), (void**)&m->x));
+    if (split) {
+        CDMPT_TRY(grab(b, elems * sizeof(float), (void**)&m->hi));
+        CDMPT_TRY(grab(b, elems * sizeof(float), (void**)&m->lo));
+    }
+    return CDMPT_OK;
+}
+
+// Copies a descriptor array into the next staging slot; returns its device address.
+template <typename T>
+cdmpt_status stage(cdmpt_batch* b, const std::vector<T>& v, const T** dev) {
+    const size_t bytes = v.size() * sizeof(T);
+    if (bytes > b->slot_bytes) {
+        set_error("batch: descriptor array exceeds the staging slot");
+        return CDMPT_ERR_ARG;
+    }
+    if (b->stage_slot == b->stage_slots) {
+        // every slot has been handed to the stream: wait before reusing them
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(b->cx.stream));
+        b->stage_slot = 0;
+    }
+    char* h = b->stage_host + b->stage_slot * b->slot_bytes;
+    char* d = b->stage_dev + b->stage_slot * b->slot_bytes;
+    ++b->stage_slot;
+    std::memcpy(h, v.data(), bytes);
+    CDMPT_CUDA_TRY(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b->cx.stream));
+    *dev = (const T*)d;
+    return CDMPT_OK;
+}
+
+// Index of the first of four consecutive tensor maps (X hi, Y hi, X lo, Y lo)
+// of one operand pair; encoded and uploaded on first use, never rewritten.
+cdmpt_status quad_of(cdmpt_batch* b, const Mat* X, int rows, const Mat* Y, int N, int ld,
+                     int* idx) {
+    const auto key = std::make_tuple((const void*)X->hi, rows, (const void*)Y->hi);
+    auto it = b->map_index.find(key);
+    if (it != b->map_index.end()) {
+        *idx = it->second;
+        return CDMPT_OK;
+    }
+    if ((int)b->maps_host.size() + 4 > b->maps_cap) {
+        set_error("batch: tensor-map table full");
+        return CDMPT_ERR_OOM;
+    }
+    CUtensorMap m[4];
+    if (!tc_encode_operand(&m[0], X->hi, rows, N, ld, false, kEngine) ||
+        !tc_encode_operand(&m[1], Y->hi, N, N, ld, true, kEngine) ||
+        !tc_encode_operand(&m[2], X->lo, rows, N, ld, false, kEngine) ||
+        !tc_encode_operand(&m[3], Y->lo, N, N, ld, true, kEngine)) {
+        set_error("batch: tensor map encoding failed");
+        return CDMPT_ERR_ARG;
+    }
+    *idx = (int)b->maps_host.size();
+    for (int q = 0; q < 4; ++q) b->maps_host.push_back(m[q]);
+    b->map_index[key] = *idx;
+    return CDMPT_OK;
+}
+
+cdmpt_status flush_maps(cdmpt_batch* b) {
+    const int n = (int)b->maps_host.size();
+    if (n > b->maps_uploaded) {
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(b->maps_dev + b->maps_uploaded,
+                                       b->maps_host.data() + b->maps_uploaded,
+                                       (n - b->maps_uploaded) * sizeof(CUtensorMap),
+                                       cudaMemcpyHostToDevice, b->cx.stream));
+        // the host vector may reallocate later: wait for the copy before it can
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(b->cx.stream));
+        b->maps_uploaded = n;
+    }
+    return CDMPT_OK;
+}
+
+// One problem of a grouped GEMM: D = alpha X Y^T + beta C + gamma I (rows x N_b, K = N_b).
+struct GemmSpec {
+    const Mat* X;
+    int rows;
+    const Mat* Y;
+    EpiParams<float> p;
+    const double* skip;
+};
+
+EpiParams<float> epi(float* D, int M, int N, int ld, float alpha = 1.f, float beta = 0.f,
+                     const float* C = nullptr, float gamma = 0.f) {
+    EpiParams<float> p;
+    std::memset(&p, 0, sizeof(p));
+    p.alpha = alpha;
+    p.beta = beta;
+    p.gamma = gamma;
+    p.C = C;
+    p.ldc = ld;
+    p.D = D;
+    p.ldd = ld;
+    p.M = M;
+    p.N = N;
+    p.diag_block = N;
+    p.lde = ld;
+    return p;
+}
+
+cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
+    std::vector<GemmProblem> probs;
+    std::vector<int> quad;
+    probs.reserve(specs.size());
+    int tiles = 0;
+    const int bm = tc_tile_m(), bn = tc_tile_n(kEngine);
+    for (const GemmSpec& g : specs) {
+        const int N = g.p.N;
+        int q = 0;
+        CDMPT_TRY(quad_of(b, g.X, g.rows, g.Y, N, g.p.ldd, &q));
+        GemmProblem pr;
+        pr.p = g.p;
+        pr.K = N;
+        pr.tile_begin = tiles;
+        pr.num_mt = (g.p.M + bm - 1) / bm;
+        pr.skip = g.skip;
+        pr.maps = nullptr;
+        probs.push_back(pr);
+        quad.push_back(q);
+        tiles += pr.num_mt * ((N + bn - 1) / bn);
+    }
+    if (probs.empty()) return CDMPT_OK;
+    CDMPT_TRY(flush_maps(b));
+    for (size_t i = 0; i < probs.size(); ++i) probs[i].maps = b->maps_dev + quad[i];
+    const GemmProblem* dev = nullptr;
+    CDMPT_TRY(stage(b, probs, &dev));
+    if (b->cx.st) {
+        for (const GemmSpec& g : specs) {
+            const double f = 2.0 * g.p.M * (double)g.p.N * g.p.N;
+            b->cx.st->gemm_flops += f;
+            b->cx.st->tensor_flops += 3.0 * f;
+        }
+        b->cx.st->gemm_launches += 1;
+    }
+    return gemm_tc_grouped(kEngine, dev, (int)probs.size(), tiles, b->cx.stream);
+}
+
+}  // namespace
+
+namespace {
+
+GrpEw ewd(float* p0, float* p1 = nullptr, float* p2 = nullptr, float* p3 = nullptr) {
+    GrpEw d;
+    std::memset(&d, 0, sizeof(d));
+    d.p0 = p0;
+    d.p1 = p1;
+    d.p2 = p2;
+    d.p3 = p3;
+    return d;
+}
+
+cdmpt_status run_ew(cdmpt_batch* b, int op, const std::vector<GrpEw>& d) {
+    if (d.empty()) return CDMPT_OK;
+    long long maxc = 0;
+    for (const GrpEw& e : d) maxc = std::max(maxc, (long long)e.rows * e.ld);
+    const GrpEw* dev = nullptr;
+    CDMPT_TRY(stage(b, d, &dev));
+    return grouped_ew(op, dev, (int)d.size(), maxc, b->cx.stream);
+}
+
+// Runs a tiled op (symmetrize / transpose-add / trace) over every system.
+template <typename F>
+cdmpt_status run_tiles(cdmpt_batch* b, const std::vector<GrpEw>& d, int blocks, F launch) {
+    int maxN = 0;
+    for (const GrpEw& e : d) maxN = std::max(maxN, e.N);
+    const GrpEw* dev = nullptr;
+    CDMPT_TRY(stage(b, d, &dev));
+    return launch(dev, (int)d.size(), maxN, blocks, b->cx.stream);
+}
+
+double* scal_base(cdmpt_batch* b) { return b->sys[0].sc; }
+
+cdmpt_status zero_slots(cdmpt_batch* b, int first, int count) {
+    CDMPT_CUDA_TRY(cudaMemset2DAsync(scal_base(b) + first, kSlots * sizeof(double), 0,
+                                     count * sizeof(double), b->B, b->cx.stream));
+    return CDMPT_OK;
+}
+
+cdmpt_status read_all(cdmpt_batch* b) {
+    CDMPT_CUDA_TRY(cudaMemcpyAsync(b->pinned, scal_base(b), (size_t)b->B * kSlots * sizeof(double),
+                                   cudaMemcpyDeviceToHost, b->cx.stream));
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(b->cx.stream));
+    return check_device_error(b->cx.stream);
+}
+
+// Per-system arguments of one grouped CG solve: X (s I + t W) = rhs_scale rhs.
+struct BCg {
+    float* X;
+    const Mat* x0;        // warm start (scale 1) or null for zero
+    const float* rhs;
+    const Mat* W;
+    int rows;
+};
+
+cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, double t, double tol,
+                      const std::vector<const double*>& skip, int hint, int* iters) {
+    const int G = b->B;
+    CDMPT_TRY(zero_slots(b, 0, CG_NSLOTS));
+    std::vector<GrpEw> dx, dr, drr, dbb, dp;
+    std::vector<GemmSpec> g0;
+    for (int i = 0; i < G; ++i) {
+        Sys& sy = b->sys[i];
+        const BCg& c = a[i];
+        GrpEw e = ewd(c.X);
+        e.rows = c.rows; e.ld = sy.ld; e.N = sy.N; e.count = (long long)c.rows * sy.ld;
+        e.skip = skip[i];
+        if (c.x0) {
+            GrpEw x = e;                 // X = x0
+            x.p1 = c.x0->x;
+            x.s0 = 1.0;
+            x.s1 = 0.0;
+            dx.push_back(x);
+            GrpEw r = e;                 // R = rhs - s x0
+            r.p0 = sy.R.x;
+            r.p1 = (float*)c.rhs;
+            r.p2 = c.x0->x;
+            r.s0 = 1.0;
+            r.s1 = -s;
+            dr.push_back(r);
+            GemmSpec gs;                 // R += -t x0 W, <R,R>
+            gs.X = c.x0;
+            gs.rows = c.rows;
+            gs.Y = c.W;
+            gs.p = epi(sy.R.x, c.rows, sy.N, sy.ld, (float)-t, 1.f, sy.R.x);
+            gs.p.dot = sy.sc + CG_RR;
+            gs.skip = skip[i];
+            g0.push_back(gs);
+        } else {
+            GrpEw x = e;                 // X = 0
+            dx.push_back(x);
+            GrpEw r = e;                 // R = rhs
+            r.p0 = sy.R.x;
+            r.p1 = (float*)c.rhs;
+            r.p2 = (float*)c.rhs;
+            r.s0 = 1.0;
+            r.s1 = 0.0;
+            dr.push_back(r);
+            GrpEw q = e;                 // <R,R>
+            q.p0 = sy.R.x;
+            q.p1 = sy.R.x;
+            q.sc = sy.sc;
+            q.s0 = CG_RR;
+            drr.push_back(q);
+        }
+        GrpEw bb = e;
+        bb.p0 = (float*)c.rhs;
+        bb.p1 = (float*)c.rhs;
+        bb.sc = sy.sc;
+        bb.s0 = CG_BB;
+        dbb.push_back(bb);
+        GrpEw p = e;                     // P = R (split), unless done
+        p.p0 = sy.P.x;
+        p.p1 = sy.R.x;
+        p.p2 = sy.P.hi;
+        p.p3 = sy.P.lo;
+        p.s0 = 1.0;
+        p.s1 = 0.0;
+        p.sc = sy.sc;
+        dp.push_back(p);
+    }
+    if (!g0.empty()) {
+        CDMPT_TRY(run_ew(b, G_AXPBY, dx));
+        CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
+        CDMPT_TRY(grouped_gemm(b, g0));
+    } else {
+        CDMPT_TRY(run_ew(b, G_ZERO, dx));
+        CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
+        CDMPT_TRY(run_ew(b, G_DOT, drr));
+    }
+    CDMPT_TRY(run_ew(b, G_DOT, dbb));
+    {
+        std::vector<GrpEw> di(G);
+        for (int i = 0; i < G; ++i) {
+            di[i] = ewd(nullptr);
+            di[i].sc = b->sys[i].sc;
+            di[i].s0 = tol * tol;
+            di[i].s1 = 0.0;
+            di[i].skip = skip[i];
+        }
+        const GrpEw* dev = nullptr;
+        CDMPT_TRY(stage(b, di, &dev));
+        CDMPT_TRY(grouped_cg_init(dev, G, b->cx.stream));
+    }
+    for (GrpEw& e : dp) e.skip = e.sc + CG_DONE;
+    CDMPT_TRY(run_ew(b, G_AXPBY, dp));
+
+    // iteration descriptors (constant over iterations)
+    std::vector<GemmSpec> gi;
+    std::vector<GrpEw> du, dd, ds;
+    for (int i = 0; i < G; ++i) {
+        Sys& sy = b->sys[i];
+        const BCg& c = a[i];
+        GemmSpec gs;
+        gs.X = &sy.P;
+        gs.rows = c.rows;
+        gs.Y = c.W;
+        gs.p = epi(sy.Q.x, c.rows, sy.N, sy.ld, (float)t, (float)s, sy.P.x);
+        gs.p.dot = sy.sc + CG_PQ;
+        gs.p.E = sy.P.x;
+        gs.skip = sy.sc + CG_DONE;
+        gi.push_back(gs);
+        GrpEw u = ewd(c.X, sy.R.x, sy.P.x, sy.Q.x);
+        u.rows = c.rows; u.ld = sy.ld; u.N = sy.N; u.count = (long long)c.rows * sy.ld;
+        u.sc = sy.sc;
+        du.push_back(u);
+        GrpEw dv = ewd(sy.P.x, sy.R.x, sy.P.hi, sy.P.lo);
+        dv.rows = c.rows; dv.ld = sy.ld; dv.N = sy.N; dv.count = (long long)c.rows * sy.ld;
+        dv.sc = sy.sc;
+        dd.push_back(dv);
+        GrpEw st = ewd(nullptr);
+        st.sc = sy.sc;
+        ds.push_back(st);
+    }
+    int chunk = std::max(1, hint), done_iters = 0;
+    while (true) {
+        for (int c = 0; c < chunk; ++c) {
+            CDMPT_TRY(grouped_gemm(b, gi));
+            CDMPT_TRY(run_ew(b, G_CG_UPDATE, du));
+            CDMPT_TRY(run_ew(b, G_CG_DIR, dd));
+            const GrpEw* dev = nullptr;
+            CDMPT_TRY(stage(b, ds, &dev));
+            CDMPT_TRY(grouped_cg_step(dev, G, b->cx.stream));
+        }
+        done_iters += chunk;
+        CDMPT_TRY(read_all(b));
+        bool all = true;
+        int most = 0;
+        for (int i = 0; i < G; ++i) {
+            all = all && b->pinned[i * kSlots + CG_DONE] != 0.0;
+            most = std::max(most, (int)b->pinned[i * kSlots + CG_ITERS]);
+        }
+        if (all) {
+            *iters = most;
+            return CDMPT_OK;
+        }
+        if (done_iters >= b->opts.cg_maxit) {
+            set_error("batch: CG did not converge in " + std::to_string(b->opts.cg_maxit) +
+                      " iterations");
+            return CDMPT_ERR_CG_MAXITER;
+        }
+        chunk = 2;
+    }
+}
+
+// One 0th-order pass for the systems whose inactive flag is 0.
+cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
+    const int G = b->B;
+    std::vector<const double*> skip(G);
+    for (int i = 0; i < G; ++i) skip[i] = b->inactive + i;
+    {
+        std::vector<GrpEw> d;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            GrpEw e = ewd(sy.Z[0].x, nullptr, sy.Z[0].hi, sy.Z[0].lo);
+            e.h = sy.H0;
+            e.rows = sy.N; e.ld = sy.ld; e.N = sy.N;
+            e.s0 = -sy.s2;
+            e.s1 = sy.mu;
+            e.skip = skip[i];
+            d.push_back(e);
+        }
+        CDMPT_TRY(run_ew(b, G_INIT_Z, d));
+    }
+    int total = 0, hint = 1;
+    for (int k = 0; k < n; ++k) {
+        std::vector<GemmSpec> gw, gr;
+        std::vector<BCg> cg(G);
+        std::vector<GrpEw> dz, dsym;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            GemmSpec w;                  // W_k = Z_k Z_k
+            w.X = &sy.Z[k];
+            w.rows = sy.N;
+            w.Y = &sy.Z[k];
+            w.p = epi(sy.W[k].x, sy.N, sy.N, sy.ld);
+            w.p.Dhi = sy.W[k].hi;
+            w.p.Dlo = sy.W[k].lo;
+            w.skip = skip[i];
+            gw.push_back(w);
+            GemmSpec r;                  // RHS = -2 Z_k W_k
+            r.X = &sy.Z[k];
+            r.rows = sy.N;
+            r.Y = &sy.W[k];
+            r.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -2.f);
+            r.skip = skip[i];
+            gr.push_back(r);
+            cg[i] = BCg{sy.Z[k + 1].x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
+            GrpEw z = ewd(sy.Z[k + 1].x, sy.Z[k].x);   // Z_{k+1} = 2 Z_k + d
+            z.rows = sy.N; z.ld = sy.ld; z.N = sy.N; z.count = (long long)sy.N * sy.ld;
+            z.s0 = 2.0;
+            z.s1 = 1.0;
+            z.skip = skip[i];
+            dz.push_back(z);
+            GrpEw y = ewd(sy.Z[k + 1].x, nullptr, sy.Z[k + 1].hi, sy.Z[k + 1].lo);
+            y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
+            y.skip = skip[i];
+            dsym.push_back(y);
+        }
+        CDMPT_TRY(grouped_gemm(b, gw));
+        CDMPT_TRY(grouped_gemm(b, gr));
+        int it = 0;
+        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, skip, hint, &it));
+        total += it;
+        hint = std::max(1, it);
+        CDMPT_TRY(run_ew(b, G_AXPBY, dz));
+        CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));
+    }
+    *iters_out = total;
+    return CDMPT_OK;
+}
+
+cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
+    if (b->n_alloc >= n) return CDMPT_OK;
+    for (void* p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    b->map_index.clear();
+    b->maps_host.clear();
+    b->maps_uploaded = 0;
+    const int B = b->B, D = b->D;
+    double* scal = nullptr;
+    CDMPT_TRY(grab(b, (size_t)B * kSlots * sizeof(double), (void**)&scal));
+    CDMPT_TRY(grab(b, (size_t)B * sizeof(double), (void**)&b->inactive));
+    b->maps_cap = B * (8 * n + 16) * 4;
+    CDMPT_TRY(grab(b, (size_t)b->maps_cap * sizeof(CUtensorMap), (void**)&b->maps_dev));
+    b->maps_host.reserve(b->maps_cap);
+    for (int i = 0; i < B; ++i) {
+        Sys& sy = b->sys[i];
+        sy.sc = scal + (size_t)i * kSlots;
+        const size_t blk = sy.blk;
+        const size_t big = (size_t)std::max(1, D) * blk;
+        CDMPT_TRY(grab(b, blk * sizeof(double), (void**)&sy.H0));
+        if (D > 0) CDMPT_TRY(grab(b, D * blk * sizeof(double), (void**)&sy.H1));
+        sy.Z.assign(n + 1, Mat());
+        sy.W.assign(n, Mat());
+        for (int k = 0; k <= n; ++k) CDMPT_TRY(grab_mat(b, blk, &sy.Z[k], true));
+        for (int k = 0; k < n; ++k) CDMPT_TRY(grab_mat(b, blk, &sy.W[k], true));
+        CDMPT_TRY(grab_mat(b, big, &sy.R, false));
+        CDMPT_TRY(grab_mat(b, big, &sy.P, true));
+        CDMPT_TRY(grab_mat(b, big, &sy.Q, false));
+        CDMPT_TRY(grab_mat(b, big, &sy.S, false));
+        CDMPT_TRY(grab_mat(b, big, &sy.A1, true));
+        CDMPT_TRY(grab_mat(b, big, &sy.RHS, true));
+        CDMPT_TRY(grab_mat(b, big, &sy.Z1a, true));
+        CDMPT_TRY(grab_mat(b, big, &sy.Z1b, true));
+        CDMPT_TRY(grab_mat(b, blk, &sy.Qmu, false));
+    }
+    b->n_alloc = n;
+    b->have_H = false;
+    return CDMPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int D,
+                                cdmpt_batch** out) {
+    if (!out || B < 1 || !N || D < 0 || D > 16) return CDMPT_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < B; ++i)
+        if (N[i] < 1) return CDMPT_ERR_ARG;
+    cdmpt_batch* b = new (std::nothrow) cdmpt_batch();
+    if (!b) return CDMPT_ERR_OOM;
+    if (opts)
+        b->opts = *opts;
+    else
+        cdmpt_default_opts(&b->opts);
+    if (!(b->opts.cg_tol > 0)) b->opts.cg_tol = 1e-7;
+    if (b->opts.precision != CDMPT_FP32) {
+        delete b;
+        set_error("batch: only CDMPT_FP32 (split-TF32 products) is available");
+        return CDMPT_ERR_UNSUPPORTED;
+    }
+    if (!tc_supported()) {
+        delete b;
+        set_error("batch: needs an sm_103 GPU (tcgen05)");
+        return CDMPT_ERR_UNSUPPORTED;
+    }
+    std::memset(&b->st, 0, sizeof(b->st));
+    b->B = B;
+    b->D = D;
+    b->sys.resize(B);
+    for (int i = 0; i < B; ++i) {
+        b->sys[i].N = N[i];
+        b->sys[i].ld = (N[i] + 31) / 32 * 32;
+        b->sys[i].blk = (size_t)N[i] * b->sys[i].ld;
+    }
+    b->cx.stream = (cudaStream_t)b->opts.stream;
+    b->slot_bytes = std::max<size_t>(64 * 1024, (size_t)B * 16 * sizeof(GrpEw));
+    b->slot_bytes = std::max<size_t>(b->slot_bytes, (size_t)B * D * sizeof(GrpEw) + 1024);
+    b->slot_bytes = std::max<size_t>(b->slot_bytes, (size_t)B * sizeof(GemmProblem) + 1024);
+    b->stage_slots = 512;
+    if (cudaMallocHost((void**)&b->stage_host, b->slot_bytes * b->stage_slots) != cudaSuccess ||
+        cudaMalloc((void**)&b->stage_dev, b->slot_bytes * b->stage_slots) != cudaSuccess ||
+        cudaMallocHost((void**)&b->pinned, (size_t)B * kSlots * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cdmpt_batch_destroy(b);
+        set_error("batch: staging allocation failed");
+        return CDMPT_ERR_OOM;
+    }
+    *out = b;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_batch_set_H(cdmpt_batch* b, const double* const* H0, const double* const* H1,
+                               int n, int on_device) {
+    if (!b || !H0 || (b->D > 0 && !H1) || n < 1 || n > 60) return CDMPT_ERR_ARG;
+    cdmpt_status s = alloc_batch(b, n);
+    if (s != CDMPT_OK) return bfail(b, s);
+    cudaStream_t st = b->cx.stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    double* tmp = nullptr;
+    CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 4 * sizeof(double), st));
+    for (int i = 0; i < b->B; ++i) {
+        Sys& sy = b->sys[i];
+        if (!H0[i] || (b->D > 0 && !H1[i])) return bfail_msg(b, CDMPT_ERR_ARG, "batch: NULL H");
+        CDMPT_CUDA_TRY(cudaMemcpy2DAsync(sy.H0, sy.ld * sizeof(double), H0[i],
+                                         sy.N * sizeof(double), sy.N * sizeof(double), sy.N,
+                                         kind, st));
+        if (b->D > 0)
+            CDMPT_CUDA_TRY(cudaMemcpy2DAsync(sy.H1, sy.ld * sizeof(double), H1[i],
+                                             sy.N * sizeof(double), sy.N * sizeof(double),
+                                             (size_t)b->D * sy.N, kind, st));
+        CDMPT_CUDA_TRY(cudaMemsetAsync(tmp, 0, 4 * sizeof(double), st));
+        s = gershgorin(sy.H0, sy.N, sy.ld, tmp, st);
+        if (s != CDMPT_OK) return bfail(b, s);
+        s = Ew<double>::trace(sy.H0, sy.N, sy.ld, 1, tmp + 2, st);
+        if (s != CDMPT_OK) return bfail(b, s);
+        double host[3];
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(host, tmp, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(st));
+        sy.gmin = host[0];
+        sy.gmax = host[1];
+        sy.trH0 = host[2];
+    }
+    CDMPT_CUDA_TRY(cudaFreeAsync(tmp, st));
+    b->have_H = true;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double* nocc, int n,
+                               double* const* P0, double* const* P1, double* mu, double* mu1,
+                               double* alpha, int out_on_device) {
+    if (!b || !beta || !nocc) return CDMPT_ERR_ARG;
+    if (!b->have_H || n > b->n_alloc)
+        return bfail_msg(b, CDMPT_ERR_ARG, "batch: call cdmpt_batch_set_H with this n first");
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = launch_count();
+    std::memset(&b->st, 0, sizeof(b->st));
+    b->cx.st = &b->st;
+    const int G = b->B, D = b->D;
+    cudaStream_t st = b->cx.stream;
+    std::vector<double> inact(G, 0.0);
+    for (int i = 0; i < G; ++i) {
+        Sys& sy = b->sys[i];
+        if (!(beta[i] > 0) || !(nocc[i] > 0) || !(nocc[i] < sy.N))
+            return bfail_msg(b, CDMPT_ERR_ARG, "batch: need beta > 0 and 0 < nocc < N");
+        sy.beta = beta[i];
+        sy.nocc = nocc[i];
+        sy.s2 = std::ldexp(beta[i], -(n + 1));
+        const double width = sy.gmax - sy.gmin;
+        if (!(sy.s2 * width < 1.0))
+            return bfail_msg(b, CDMPT_ERR_RANGE, "batch: beta (lambda_max - lambda_min) / 2^(n+1) "
+                                                 ">= 1 for system " + std::to_string(i));
+        const double pad = std::min(40.0 / sy.beta, 0.45 * (1.0 / sy.s2 - width));
+        sy.lo = sy.gmin - pad;
+        sy.hi = sy.gmax + pad;
+        sy.mu = std::min(std::max(sy.trH0 / sy.N, sy.lo + 1e-3 * pad), sy.hi - 1e-3 * pad);
+        sy.converged = false;
+    }
+    // -------------------------------------------------- occupation loops, in lockstep
+    int sweeps = 0;
+    for (; sweeps < b->opts.mu_maxit; ++sweeps) {
+        for (int i = 0; i < G; ++i) inact[i] = b->sys[i].converged ? 1.0 : 0.0;
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
+                                       cudaMemcpyHostToDevice, st));
+        int iters = 0;
+        cdmpt_status s = sweep_batch(b, n, &iters);
+        if (s != CDMPT_OK) return bfail(b, s);
+        b->st.cg_iterations_sweeps += iters;
+        CDMPT_TRY(zero_slots(b, B_TRZ, 2));
+        {
+            std::vector<GrpEw> dt, dd;
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                GrpEw e = ewd(sy.Z[n].x, sy.Z[n].x);
+                e.rows = sy.N; e.ld = sy.ld; e.N = sy.N; e.count = (long long)sy.blk;
+                e.sc = sy.sc;
+                e.skip = b->inactive + i;
+                e.s0 = B_TRZ;
+                dt.push_back(e);
+                e.s0 = B_ZZ;
+                dd.push_back(e);
+            }
+            s = run_tiles(b, dt, 1, grouped_trace);
+            if (s != CDMPT_OK) return bfail(b, s);
+            s = run_ew(b, G_DOT, dd);
+            if (s != CDMPT_OK) return bfail(b, s);
+        }
+        CDMPT_TRY(read_all(b));
+        bool all = true;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            if (sy.converged) continue;
+            const double trP = 0.5 * (sy.N + b->pinned[i * kSlots + B_TRZ]);
+            const double zz = b->pinned[i * kSlots + B_ZZ];
+            const double err = trP - sy.nocc;
+            const double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-7 * sy.N;
+            if (std::fabs(err) <= tol) {
+                sy.converged = true;
+                continue;
+            }
+            all = false;
+            if (err > 0) sy.hi = sy.mu; else sy.lo = sy.mu;
+            const double slope = 0.25 * sy.beta * (sy.N - zz);
+            double mnew = slope > 0 ? sy.mu - err / slope : 0.5 * (sy.lo + sy.hi);
+            if (!(mnew > sy.lo && mnew < sy.hi)) mnew = 0.5 * (sy.lo + sy.hi);
+            sy.mu = mnew;
+        }
+        if (all) {
+            ++sweeps;
+            break;
+        }
+    }
+    b->st.mu_iterations = sweeps;
+    for (int i = 0; i < G; ++i)
+        if (!b->sys[i].converged)
+            return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
+                             "batch: occupation of system " + std::to_string(i) + " not reached");
+    if (mu)
+        for (int i = 0; i < G; ++i) mu[i] = b->sys[i].mu;
+    std::fill(inact.begin(), inact.end(), 0.0);
+    CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
+                                   cudaMemcpyHostToDevice, st));
+    std::vector<const double*> none(G, nullptr);
+
+    // -------------------------------------------------- response (all systems, D directions)
+    if (D > 0) {
+        std::vector<GrpEw> d;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            GrpEw e = ewd(sy.Z1a.x, nullptr, sy.Z1a.hi, sy.Z1a.lo);
+            e.h = sy.H1;
+            e.rows = D * sy.N; e.ld = sy.ld; e.N = sy.N;
+            e.s0 = -sy.s2;
+            e.s1 = 0.0;
+            d.push_back(e);
+        }
+        CDMPT_TRY(run_ew(b, G_INIT_Z, d));
+        int total = 0, hint = 1;
+        for (int k = 0; k < n; ++k) {
+            std::vector<GemmSpec> gs, g1, g2;
+            std::vector<GrpEw> dta, dz, dsym;
+            std::vector<BCg> cg(G);
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                Mat* Z1 = (k % 2 == 0) ? &sy.Z1a : &sy.Z1b;
+                Mat* Z1n = (k % 2 == 0) ? &sy.Z1b : &sy.Z1a;
+                const int rows = D * sy.N;
+                GemmSpec a;              // S^T = Z1 Z_k
+                a.X = Z1;
+                a.rows = rows;
+                a.Y = &sy.Z[k];
+                a.p = epi(sy.S.x, rows, sy.N, sy.ld);
+                a.skip = nullptr;
+                gs.push_back(a);
+                GrpEw t = ewd(sy.A1.x, sy.S.x, sy.A1.hi, sy.A1.lo);
+                t.rows = rows; t.ld = sy.ld; t.N = sy.N;
+                dta.push_back(t);
+                GemmSpec r1;             // RHS = -(A1 Z_{k+1})^T
+                r1.X = &sy.A1;
+                r1.rows = rows;
+                r1.Y = &sy.Z[k + 1];
+                r1.p = epi(sy.RHS.x, rows, sy.N, sy.ld, -1.f);
+                r1.p.trans_block = sy.N;
+                r1.skip = nullptr;
+                g1.push_back(r1);
+                GemmSpec r2;             // RHS -= 2 Z1 W_k
+                r2.X = Z1;
+                r2.rows = rows;
+                r2.Y = &sy.W[k];
+                r2.p = epi(sy.RHS.x, rows, sy.N, sy.ld, -2.f, 1.f, sy.RHS.x);
+                r2.skip = nullptr;
+                g2.push_back(r2);
+                cg[i] = BCg{Z1n->x, nullptr, sy.RHS.x, &sy.W[k], rows};
+                GrpEw z = ewd(Z1n->x, Z1->x);
+                z.rows = rows; z.ld = sy.ld; z.N = sy.N; z.count = (long long)rows * sy.ld;
+                z.s0 = 2.0;
+                z.s1 = 1.0;
+                dz.push_back(z);
+                GrpEw y = ewd(Z1n->x, nullptr, Z1n->hi, Z1n->lo);
+                y.rows = rows; y.ld = sy.ld; y.N = sy.N;
+                dsym.push_back(y);
+            }
+            CDMPT_TRY(grouped_gemm(b, gs));
+            CDMPT_TRY(run_tiles(b, dta, D, grouped_transpose_add));
+            CDMPT_TRY(grouped_gemm(b, g1));
+            CDMPT_TRY(grouped_gemm(b, g2));
+            int it = 0;
+            cdmpt_status s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it);
+            if (s != CDMPT_OK) return bfail(b, s);
+            total += it;
+            hint = std::max(1, it);
+            CDMPT_TRY(run_ew(b, G_AXPBY, dz));
+            CDMPT_TRY(run_tiles(b, dsym, D, grouped_symmetrize));
+        }
+        b->st.cg_iterations_response = total;
+        // Q' = (I - Z_n^2)(I - W_0)^-1; dP0/dmu = beta/4 Q'
+        {
+            std::vector<GemmSpec> gq;
+            std::vector<BCg> cg(G);
+            std::vector<GrpEw> dsym;
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                GemmSpec q;
+                q.X = &sy.Z[n];
+                q.rows = sy.N;
+                q.Y = &sy.Z[n];
+                q.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -1.f, 0.f, nullptr, 1.f);
+                q.p.Dhi = sy.RHS.hi;
+                q.p.Dlo = sy.RHS.lo;
+                q.skip = nullptr;
+                gq.push_back(q);
+                cg[i] = BCg{sy.Qmu.x, &sy.RHS, sy.RHS.x, &sy.W[0], sy.N};
+                GrpEw y = ewd(sy.Qmu.x);
+                y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
+                dsym.push_back(y);
+            }
+            CDMPT_TRY(grouped_gemm(b, gq));
+            int it = 0;
+            cdmpt_status s = cg_batch(b, cg, 1.0, -1.0, b->opts.cg_tol, none, 1, &it);
+            if (s != CDMPT_OK) return bfail(b, s);
+            b->st.cg_iterations_q = it;
+            CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));
+        }
+        // traces, mu1, P1 = Z1/2 + mu1 Q, alpha = -sum Z1 H1
+        Mat* Z1f = (n % 2 == 0) ? nullptr : nullptr;
+        (void)Z1f;
+        CDMPT_TRY(zero_slots(b, B_TRQ, 1));
+        CDMPT_TRY(zero_slots(b, B_TRZ1, 32));
+        {
+            std::vector<GrpEw> dq, dz;
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                Mat* Z1 = (n % 2 == 0) ? &sy.Z1a : &sy.Z1b;
+                GrpEw q = ewd(sy.Qmu.x);
+                q.rows = sy.N; q.ld = sy.ld; q.N = sy.N;
+                q.sc = sy.sc;
+                q.s0 = B_TRQ;
+                dq.push_back(q);
+                GrpEw z = ewd(Z1->x);
+                z.rows = D * sy.N; z.ld = sy.ld; z.N = sy.N;
+                z.sc = sy.sc;
+                z.s0 = B_TRZ1;
+                dz.push_back(z);
+            }
+            CDMPT_TRY(run_tiles(b, dq, 1, grouped_trace));
+            CDMPT_TRY(run_tiles(b, dz, D, grouped_trace));
+        }
+        CDMPT_TRY(read_all(b));
+        {
+            std::vector<GrpEw> da, dh;
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                Mat* Z1 = (n % 2 == 0) ? &sy.Z1a : &sy.Z1b;
+                const double trQ = 0.25 * sy.beta * b->pinned[i * kSlots + B_TRQ];
+                for (int dd = 0; dd < D; ++dd) {
+                    const double trP1 = 0.5 * b->pinned[i * kSlots + B_TRZ1 + dd];
+                    const double m1 = trQ > 0 ? -trP1 / trQ : 0.0;
+                    if (mu1) mu1[i * D + dd] = m1;
+                    GrpEw a = ewd(Z1->x + (size_t)dd * sy.blk, sy.Qmu.x);
+                    a.rows = sy.N; a.ld = sy.ld; a.N = sy.N; a.count = (long long)sy.blk;
+                    a.s0 = 2.0 * m1 * 0.25 * sy.beta;
+                    a.s1 = 1.0;
+                    da.push_back(a);
+                    GrpEw h = ewd(Z1->x + (size_t)dd * sy.blk);
+                    h.h = sy.H1 + (size_t)dd * sy.blk;
+                    h.rows = sy.N; h.ld = sy.ld; h.N = sy.N;
+                    h.sc = sy.sc;
+                    h.s0 = B_ALPHA + dd;
+                    dh.push_back(h);
+                }
+            }
+            CDMPT_TRY(zero_slots(b, B_ALPHA, 16));
+            CDMPT_TRY(run_ew(b, G_AXPBY, da));
+            CDMPT_TRY(run_ew(b, G_DOT_H, dh));
+        }
+        CDMPT_TRY(read_all(b));
+        for (int i = 0; i < G; ++i)
+            for (int dd = 0; dd < D; ++dd)
+                if (alpha) alpha[i * D + dd] = -b->pinned[i * kSlots + B_ALPHA + dd];
+    }
+    // -------------------------------------------------- outputs
+    for (int i = 0; i < G; ++i) {
+        Sys& sy = b->sys[i];
+        const size_t e0 = (size_t)sy.N * sy.N;
+        if (P0 && P0[i]) {
+            if (out_on_device) {
+                CDMPT_TRY(Ew<float>::to_f64(P0[i], sy.N, sy.Z[n].x, sy.ld, sy.N, sy.N, 0.5, 0.5, st));
+            } else {
+                double* tmp = nullptr;
+                CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, e0 * sizeof(double), st));
+                CDMPT_TRY(Ew<float>::to_f64(tmp, sy.N, sy.Z[n].x, sy.ld, sy.N, sy.N, 0.5, 0.5, st));
+                CDMPT_CUDA_TRY(cudaMemcpyAsync(P0[i], tmp, e0 * sizeof(double),
+                                               cudaMemcpyDeviceToHost, st));
+                CDMPT_CUDA_TRY(cudaFreeAsync(tmp, st));
+            }
+        }
+        if (D > 0 && P1 && P1[i]) {
+            Mat* Z1 = (n % 2 == 0) ? &sy.Z1a : &sy.Z1b;
+            const int rows = D * sy.N;
+            if (out_on_device) {
+                CDMPT_TRY(Ew<float>::to_f64(P1[i], sy.N, Z1->x, sy.ld, sy.N, rows, 0.5, 0.0, st));
+            } else {
+                double* tmp = nullptr;
+                CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, D * e0 * sizeof(double), st));
+                CDMPT_TRY(Ew<float>::to_f64(tmp, sy.N, Z1->x, sy.ld, sy.N, rows, 0.5, 0.0, st));
+                CDMPT_CUDA_TRY(cudaMemcpyAsync(P1[i], tmp, D * e0 * sizeof(double),
+                                               cudaMemcpyDeviceToHost, st));
+                CDMPT_CUDA_TRY(cudaFreeAsync(tmp, st));
+            }
+        }
+    }
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(st));
+    b->st.kernel_launches = (int)(launch_count() - launches0);
+    b->st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    b->st.n = n;
+    b->st.D = D;
+    b->st.N = G;
+    cdmpt_status s = check_device_error(st);
+    if (s != CDMPT_OK) return bfail(b, s);
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_batch_get_stats(const cdmpt_batch* b, cdmpt_stats* st) {
+    if (!b || !st) return CDMPT_ERR_ARG;
+    *st = b->st;
+    return CDMPT_OK;
+}
+
+const char* cdmpt_batch_last_error(const cdmpt_batch* b) {
+    if (!b) return get_error().c_str();
+    return b->err.c_str();
+}
+
+void cdmpt_batch_destroy(cdmpt_batch* b) {
+    if (!b) return;
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->stage_host) cudaFreeHost(b->stage_host);
+    if (b->stage_dev) cudaFree(b->stage_dev);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
+}
+
+}  // extern "C"

@@ -83,10 +83,46 @@ __device__ __forceinline__ void block_sum_atomic(double v, double* out) {
     }
 }
 
+// hi = rna_tf32(v), lo = rna_tf32(v - hi): the split operands of the 3xTF32
+// tensor-core engine (both exactly representable in TF32). No-op for double.
+template <typename T>
+__device__ __forceinline__ void put_split(T* hi, T* lo, size_t i, T v) {
+    if constexpr (sizeof(T) == 4) {
+        if (hi) {
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            const float hv = __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hv));
+            hi[i] = hv;
+            lo[i] = __uint_as_float(l);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void put_split16(T* hi, T* lo, size_t i, const T (&v)[Vec<T>::W]) {
+    if constexpr (sizeof(T) == 4) {
+        if (hi) {
+            float h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t a, b;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(a) : "f"(v[k]));
+                h[k] = __uint_as_float(a);
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(v[k] - h[k]));
+                l[k] = __uint_as_float(b);
+            }
+            store16(hi + i, h);
+            store16(lo + i, l);
+        }
+    }
+}
+
 // Z[r][j] = scale * (H[r][j] - shift * [j == r mod N]) for j < N, 0 for j >= N.
 template <typename T>
 __global__ void k_init_z(T* __restrict__ Z, const double* __restrict__ H, int N, int ld, int ldh,
-                         size_t rows, double scale, double shift) {
+                         size_t rows, double scale, double shift, T* __restrict__ hi,
+                         T* __restrict__ lo) {
     const size_t total = rows * (size_t)ld;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -99,6 +135,7 @@ __global__ void k_init_z(T* __restrict__ Z, const double* __restrict__ H, int N,
             v *= scale;
         }
         Z[e] = (T)v;
+        put_split(hi, lo, e, (T)v);
     }
 }
 
@@ -134,9 +171,10 @@ __global__ void k_cg_update(T* __restrict__ X, T* __restrict__ R, const T* __res
 // P = R + beta P with beta = rr_new / rr, unless converged.
 template <typename T>
 __global__ void k_cg_direction(T* __restrict__ P, const T* __restrict__ R, size_t nvec,
-                               const double* __restrict__ sc) {
+                               const double* __restrict__ sc, T* __restrict__ hi,
+                               T* __restrict__ lo) {
     if (sc[CG_DONE] != 0.0) return;
-    if (sc[CG_RRNEW] <= sc[CG_TOL2] * sc[CG_BB]) return;
+    if (sc[CG_RRNEW] <= sc[CG_THRESH]) return;
     const T beta = (T)(sc[CG_RRNEW] / sc[CG_RR]);
     constexpr int W = Vec<T>::W;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec;
@@ -147,13 +185,14 @@ __global__ void k_cg_direction(T* __restrict__ P, const T* __restrict__ R, size_
 #pragma unroll
         for (int i = 0; i < W; ++i) p[i] = fma(beta, p[i], r[i]);
         store16(P + v * W, p);
+        put_split16(hi, lo, v * W, p);
     }
 }
 
 __global__ void k_cg_scalar_step(double* sc) {
     if (sc[CG_DONE] != 0.0) return;
     sc[CG_ITERS] += 1.0;
-    if (sc[CG_RRNEW] <= sc[CG_TOL2] * sc[CG_BB]) {
+    if (sc[CG_RRNEW] <= sc[CG_THRESH]) {
         sc[CG_DONE] = 1.0;
         sc[CG_RR] = sc[CG_RRNEW];
     } else {
@@ -163,12 +202,14 @@ __global__ void k_cg_scalar_step(double* sc) {
     }
 }
 
-__global__ void k_cg_scalar_init(double* sc, double tol2) {
-    sc[CG_TOL2] = tol2;
+__global__ void k_cg_scalar_init(double* sc, double tol2, double tol2_r0) {
+    const double thresh = fmax(tol2 * sc[CG_BB], tol2_r0 * sc[CG_RR]);
+    sc[CG_THRESH] = thresh;
+    sc[CG_RR0] = sc[CG_RR];
     sc[CG_ITERS] = 0.0;
     sc[CG_PQ] = 0.0;
     sc[CG_RRNEW] = 0.0;
-    sc[CG_DONE] = (sc[CG_RR] <= tol2 * sc[CG_BB]) ? 1.0 : 0.0;
+    sc[CG_DONE] = (sc[CG_RR] <= thresh) ? 1.0 : 0.0;
 }
 
 template <typename T>
@@ -192,7 +233,8 @@ __global__ void k_dot(const T* __restrict__ A, const T* __restrict__ B, size_t n
 
 template <typename T>
 __global__ void k_axpby(T* __restrict__ Y, const T* __restrict__ X, size_t nvec, double a,
-                        double b, const double* __restrict__ skip) {
+                        double b, const double* __restrict__ skip, T* __restrict__ hi,
+                        T* __restrict__ lo) {
     if (skip && *skip != 0.0) return;
     constexpr int W = Vec<T>::W;
     const T ta = (T)a, tb = (T)b;
@@ -209,6 +251,48 @@ __global__ void k_axpby(T* __restrict__ Y, const T* __restrict__ X, size_t nvec,
             for (int i = 0; i < W; ++i) y[i] = ta * x[i];
         }
         store16(Y + v * W, y);
+        put_split16(hi, lo, v * W, y);
+    }
+}
+
+// out = a X + b Y (out may alias X or Y).
+template <typename T>
+__global__ void k_lincomb(T* __restrict__ out, const T* X, double a, const T* Y, double b,
+                          size_t nvec) {
+    constexpr int W = Vec<T>::W;
+    const T ta = (T)a, tb = (T)b;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec;
+         v += (size_t)gridDim.x * blockDim.x) {
+        T x[W], y[W];
+        load16(X + v * W, x);
+        load16(Y + v * W, y);
+#pragma unroll
+        for (int i = 0; i < W; ++i) x[i] = fma(ta, x[i], tb * y[i]);
+        store16(out + v * W, x);
+    }
+}
+
+// hi/lo split of a contiguous array (float only).
+__global__ void k_split(const float* __restrict__ X, size_t nvec, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec;
+         v += (size_t)gridDim.x * blockDim.x) {
+        float x[4];
+        load16(X + v * 4, x);
+        put_split16<float>(hi, lo, v * 4, x);
+    }
+}
+
+// A[b N + i][i] += s for every block b (diagonal shift of a stack).
+template <typename T>
+__global__ void k_add_diag(T* __restrict__ A, int N, int ld, size_t rows, double s,
+                           T* __restrict__ hi, T* __restrict__ lo) {
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < rows;
+         r += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = r * ld + (r % (size_t)N);
+        const T v = A[i] + (T)s;
+        A[i] = v;
+        put_split(hi, lo, i, v);
     }
 }
 
@@ -226,7 +310,8 @@ constexpr int TT = 32;  // transpose tile
 
 // out_b = S_b + S_b^T for every N x N block b.
 template <typename T>
-__global__ void k_transpose_add(T* __restrict__ out, const T* __restrict__ S, int N, int ld) {
+__global__ void k_transpose_add(T* __restrict__ out, const T* __restrict__ S, int N, int ld,
+                                T* __restrict__ hi, T* __restrict__ lo) {
     __shared__ T tile[TT][TT + 1];
     const size_t base = (size_t)blockIdx.z * N * ld;
     const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
@@ -238,15 +323,43 @@ __global__ void k_transpose_add(T* __restrict__ out, const T* __restrict__ S, in
     __syncthreads();
     for (int y = threadIdx.y; y < TT; y += blockDim.y) {
         const int r = i0 + y, c = j0 + threadIdx.x;
-        if (r < N && c < N)
-            out[base + (size_t)r * ld + c] = S[base + (size_t)r * ld + c] + tile[threadIdx.x][y];
+        if (r < N && c < N) {
+            const size_t i = base + (size_t)r * ld + c;
+            const T v = S[i] + tile[threadIdx.x][y];
+            out[i] = v;
+            put_split(hi, lo, i, v);
+        }
+    }
+}
+
+// out_b = in_b^T for every N x N block b (out-of-place), with optional split.
+template <typename T>
+__global__ void k_transpose(T* __restrict__ out, const T* __restrict__ in, int N, int ld,
+                            T* __restrict__ hi, T* __restrict__ lo) {
+    __shared__ T tile[TT][TT + 1];
+    const size_t base = (size_t)blockIdx.z * N * ld;
+    const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = j0 + y, c = i0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < N && c < N) ? in[base + (size_t)r * ld + c] : T(0);
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = i0 + y, c = j0 + threadIdx.x;
+        if (r < N && c < N) {
+            const size_t i = base + (size_t)r * ld + c;
+            const T v = tile[threadIdx.x][y];
+            out[i] = v;
+            put_split(hi, lo, i, v);
+        }
     }
 }
 
 // Z_b = (Z_b + Z_b^T)/2 in place; block (bx, by) with bx < by exits, the
 // other one owns the tile pair.
 template <typename T>
-__global__ void k_symmetrize(T* __restrict__ Z, int N, int ld) {
+__global__ void k_symmetrize(T* __restrict__ Z, int N, int ld, T* __restrict__ hi,
+                             T* __restrict__ lo) {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
     __shared__ T a[TT][TT + 1];
@@ -267,11 +380,17 @@ __global__ void k_symmetrize(T* __restrict__ Z, int N, int ld) {
         const T avg_ij = T(0.5) * (a[y][x] + b[x][y]);  // position (i0+y, j0+x)
         const T avg_ji = T(0.5) * (b[y][x] + a[x][y]);  // position (j0+y, i0+x)
         int r = i0 + y, c = j0 + x;
-        if (r < N && c < N) Z[base + (size_t)r * ld + c] = avg_ij;
+        if (r < N && c < N) {
+            Z[base + (size_t)r * ld + c] = avg_ij;
+            put_split(hi, lo, base + (size_t)r * ld + c, avg_ij);
+        }
         if (bi != bj) {
             r = j0 + y;
             c = i0 + x;
-            if (r < N && c < N) Z[base + (size_t)r * ld + c] = avg_ji;
+            if (r < N && c < N) {
+                Z[base + (size_t)r * ld + c] = avg_ji;
+                put_split(hi, lo, base + (size_t)r * ld + c, avg_ji);
+            }
         }
     }
 }
@@ -380,9 +499,10 @@ long long launch_count() { return g_launches; }
 
 template <typename T>
 cdmpt_status Ew<T>::init_z(T* Z, const double* H, int N, int ld, int ldh, int blocks,
-                           double scale, double shift, cudaStream_t s) {
+                           double scale, double shift, cudaStream_t s, T* hi, T* lo) {
     const size_t rows = (size_t)blocks * N;
-    k_init_z<T><<<grid_for(rows * ld), kThreads, 0, s>>>(Z, H, N, ld, ldh, rows, scale, shift);
+    k_init_z<T><<<grid_for(rows * ld), kThreads, 0, s>>>(Z, H, N, ld, ldh, rows, scale, shift, hi,
+                                                          lo);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }
@@ -398,9 +518,9 @@ cdmpt_status Ew<T>::cg_update(T* X, T* R, const T* P, const T* Q, size_t count, 
 
 template <typename T>
 cdmpt_status Ew<T>::cg_direction(T* P, const T* R, size_t count, const double* sc,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, T* hi, T* lo) {
     const size_t nvec = count / Vec<T>::W;
-    k_cg_direction<T><<<grid_for(nvec), kThreads, 0, s>>>(P, R, nvec, sc);
+    k_cg_direction<T><<<grid_for(nvec), kThreads, 0, s>>>(P, R, nvec, sc, hi, lo);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }
@@ -416,9 +536,9 @@ cdmpt_status Ew<T>::dot(const T* A, const T* B, size_t count, double* out, const
 
 template <typename T>
 cdmpt_status Ew<T>::axpby(T* Y, const T* X, size_t count, double a, double b,
-                          const double* skip, cudaStream_t s) {
+                          const double* skip, cudaStream_t s, T* hi, T* lo) {
     const size_t nvec = count / Vec<T>::W;
-    k_axpby<T><<<grid_for(nvec), kThreads, 0, s>>>(Y, X, nvec, a, b, skip);
+    k_axpby<T><<<grid_for(nvec), kThreads, 0, s>>>(Y, X, nvec, a, b, skip, hi, lo);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }
@@ -433,19 +553,19 @@ cdmpt_status Ew<T>::trace(const T* A, int N, int ld, int blocks, double* out, cu
 
 template <typename T>
 cdmpt_status Ew<T>::transpose_add(T* out, const T* S, int N, int ld, int blocks,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, T* hi, T* lo) {
     const int nt = (N + TT - 1) / TT;
     dim3 grid(nt, nt, blocks), block(TT, 8);
-    k_transpose_add<T><<<grid, block, 0, s>>>(out, S, N, ld);
+    k_transpose_add<T><<<grid, block, 0, s>>>(out, S, N, ld, hi, lo);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }
 
 template <typename T>
-cdmpt_status Ew<T>::symmetrize(T* Z, int N, int ld, int blocks, cudaStream_t s) {
+cdmpt_status Ew<T>::symmetrize(T* Z, int N, int ld, int blocks, cudaStream_t s, T* hi, T* lo) {
     const int nt = (N + TT - 1) / TT;
     dim3 grid(nt, nt, blocks), block(TT, 8);
-    k_symmetrize<T><<<grid, block, 0, s>>>(Z, N, ld);
+    k_symmetrize<T><<<grid, block, 0, s>>>(Z, N, ld, hi, lo);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }
@@ -467,6 +587,41 @@ cdmpt_status Ew<T>::diag_dot(const T* A, const double* H, int N, int ld, int ldh
     return CDMPT_OK;
 }
 
+template <typename T>
+cdmpt_status Ew<T>::transpose(T* out, const T* in, int N, int ld, int blocks, cudaStream_t s,
+                              T* hi, T* lo) {
+    const int nt = (N + TT - 1) / TT;
+    dim3 grid(nt, nt, blocks), block(TT, 8);
+    k_transpose<T><<<grid, block, 0, s>>>(out, in, N, ld, hi, lo);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+template <typename T>
+cdmpt_status Ew<T>::lincomb(T* out, const T* X, double a, const T* Y, double b, size_t count,
+                            cudaStream_t s) {
+    const size_t nvec = count / Vec<T>::W;
+    k_lincomb<T><<<grid_for(nvec), kThreads, 0, s>>>(out, X, a, Y, b, nvec);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+template <typename T>
+cdmpt_status Ew<T>::add_diag(T* A, int N, int ld, int blocks, double shift, cudaStream_t s, T* hi,
+                             T* lo) {
+    const size_t rows = (size_t)blocks * N;
+    k_add_diag<T><<<grid_for(rows), kThreads, 0, s>>>(A, N, ld, rows, shift, hi, lo);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+cdmpt_status split_tf32(const float* X, size_t count, float* hi, float* lo, cudaStream_t s) {
+    const size_t nvec = count / 4;
+    k_split<<<grid_for(nvec), kThreads, 0, s>>>(X, nvec, hi, lo);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
 template struct Ew<float>;
 template struct Ew<double>;
 
@@ -476,8 +631,8 @@ cdmpt_status cg_scalar_step(double* sc, cudaStream_t s) {
     return CDMPT_OK;
 }
 
-cdmpt_status cg_scalar_init(double* sc, double tol2, cudaStream_t s) {
-    k_cg_scalar_init<<<1, 1, 0, s>>>(sc, tol2);
+cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s) {
+    k_cg_scalar_init<<<1, 1, 0, s>>>(sc, tol2, tol2_r0);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace cdmpt {
 
@@ -22,6 +23,8 @@ struct EpiParams {
     double* dot;
     const T* E;
     int lde;
+    T* Dhi;   // optional TF32 split of D (float only), same ld as D
+    T* Dlo;
 };
 
 template <typename T>
@@ -46,6 +49,16 @@ __device__ __forceinline__ T epi_apply(const EpiParams<T>& p, int m, int n, T ac
     if (p.beta != T(0)) v = fma(p.beta, p.C[r * p.ldc + c], v);
     if (p.gamma != T(0) && (m % p.diag_block) == n) v += p.gamma;
     p.D[r * p.ldd + c] = v;
+    if constexpr (sizeof(T) == 4) {
+        if (p.Dhi) {
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            const float hv = __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hv));
+            p.Dhi[r * p.ldd + c] = hv;
+            p.Dlo[r * p.ldd + c] = __uint_as_float(l);
+        }
+    }
     if (p.dot) return v * (p.E ? p.E[r * p.lde + c] : v);
     return T(0);
 }

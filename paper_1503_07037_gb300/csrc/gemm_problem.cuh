@@ -1,0 +1,26 @@
+// One problem of a (possibly grouped) tcgen05 GEMM launch, shared by the
+// kernel (gemm_tc.cu) and the batched solver that builds descriptor arrays.
+#pragma once
+
+#include <cuda.h>
+
+#include "epilogue.cuh"
+
+namespace cdmpt {
+
+struct GemmProblem {
+    EpiParams<float> p;        // M, N, D, C, alpha, beta, gamma, dot, ...
+    int K;
+    int tile_begin;            // first launch-wide tile index of this problem
+    int num_mt;                // output tiles along M
+    const double* skip;        // the problem is skipped while *skip != 0
+    const CUtensorMap* maps;   // grouped launches: X hi, Y hi, X lo, Y lo (device memory)
+};
+
+// Tensor map of an FP32 operand (rows x cols, leading dimension ld) as the X
+// (box 128 rows) or the Y operand (box of the engine's tile width) of the
+// tcgen05 kernel. Returns false if the driver rejects it (alignment).
+bool tc_encode_operand(CUtensorMap* map, const float* base, int rows, int cols, int ld,
+                       bool as_y, int engine);
+
+}  // namespace cdmpt

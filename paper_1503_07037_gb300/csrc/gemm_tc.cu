@@ -13,10 +13,11 @@
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //               lanes 32 (w % 4) ...), alpha/beta/gamma, transposed
 //               placement, fused Frobenius dot, global stores;
-//   warps 6..9  (3xTF32 only) split each landed FP32 tile in place into
-//               hi = rna_tf32(x) and, in a second buffer, lo = rna_tf32(x - hi),
-//               so the MMA can form lo*hi + hi*lo + hi*hi (Ootomo & Yokota's
-//               split-TF32 scheme) with FP32 accumulation in TMEM.
+// For 3xTF32 the operands arrive already split in HBM (hi = rna_tf32(x),
+// lo = rna_tf32(x - hi), written once by the kernel that produced x) and TMA
+// loads the hi and lo tiles of both operands, so the MMA forms
+// lo*hi + hi*lo + hi*hi (Ootomo & Yokota's split-TF32 scheme) with FP32
+// accumulation in TMEM, restarted every KCH k-blocks and summed in registers.
 //
 // Every mbarrier wait is bounded (about 2 s of %globaltimer). On timeout a
 // thread records the error, raises a shared abort flag that ends the other
@@ -27,10 +28,12 @@
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <string>
 
 #include "epilogue.cuh"
+#include "gemm_problem.cuh"
 #include "internal.cuh"
 
 namespace cdmpt {
@@ -56,19 +59,22 @@ int split_chunk() {
     return v;
 }
 
-template <int BN, int STAGES, int SPLIT>
+
+template <int BN, int STAGES, int PASSES>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
-    static constexpr int TX_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGE_BYTES = TX_BYTES * (SPLIT == 3 ? 2 : 1);
+    static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
+    // one pass: the A and B tiles; three passes: their hi and lo tiles
+    static constexpr int STAGE_BYTES = PAIR_BYTES * (PASSES == 3 ? 2 : 1);
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int THREADS = SPLIT == 3 ? 320 : 192;
+    static constexpr int THREADS = 192;
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(TMEM_COLS <= 512, "TMEM");
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -150,6 +156,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Orders the tensormap proxy after the generic writes (a host copy) that put a
+// tensor map into global memory, before TMA first reads it.
+__device__ __forceinline__ void acquire_map(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
@@ -237,45 +249,97 @@ __device__ __forceinline__ uint32_t rna_tf32(float x) {
 
 // ---------------------------------------------------------------- kernel
 
-template <int BN, int STAGES, int SPLIT, int KCH>
-__global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
+// Where one output tile lives: its problem, its corner and its tensor maps.
+struct TileRef {
+    const GemmProblem* pr;
+    const CUtensorMap *mx, *my, *mxl, *myl;
+    int m0, n0, num_k;
+    bool skip;
+};
+
+// Tile t of the launch. A single problem uses the __grid_constant__ maps; a
+// grouped launch finds the problem by binary search over tile_begin and reads
+// its maps from global memory. A problem whose skip flag is set (its CG has
+// converged) contributes no work; every role sees the same flags, so all roles
+// walk the same sequence of tiles.
+template <bool GROUPED>
+__device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
+                                            const GemmProblem* groups, int G,
+                                            const CUtensorMap* sx, const CUtensorMap* sy,
+                                            const CUtensorMap* sxl, const CUtensorMap* syl) {
+    TileRef r;
+    const GemmProblem* pr;
+    if constexpr (GROUPED) {
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (groups[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        pr = &groups[lo];
+        r.mx = pr->maps;
+        r.my = pr->maps + 1;
+        r.mxl = pr->maps + 2;
+        r.myl = pr->maps + 3;
+        r.skip = pr->skip != nullptr && *pr->skip != 0.0;
+    } else {
+        pr = &single;
+        r.mx = sx;
+        r.my = sy;
+        r.mxl = sxl;
+        r.myl = syl;
+        r.skip = false;
+    }
+    const int lt = t - pr->tile_begin;
+    r.pr = pr;
+    r.m0 = (lt % pr->num_mt) * BM;
+    r.n0 = 0;   // set by the caller, which knows BN
+    r.num_k = (pr->K + BK - 1) / BK;
+    return r;
+}
+
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED>
+__global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-              int K, EpiParams<float> p, const double* skip, int* err) {
-    using C = Cfg<BN, STAGES, SPLIT>;
-    if (skip != nullptr && *skip != 0.0) return;
+              const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
+              const __grid_constant__ GemmProblem single, const GemmProblem* groups, int G,
+              int total_tiles, int* err) {
+    using C = Cfg<BN, STAGES, PASSES>;
+    if (!GROUPED && single.skip != nullptr && *single.skip != 0.0) return;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* conv = empty + STAGES;
-    uint64_t* tfull = conv + STAGES;    // [2]
+    uint64_t* tfull = empty + STAGES;   // [2]
     uint64_t* tempty = tfull + 2;       // [2]
     uint64_t* drain = tempty + 2;       // [1]
     uint32_t* tmem_holder = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int num_mt = (p.M + BM - 1) / BM;
-    const int num_nt = (p.N + BN - 1) / BN;
-    const int num_tiles = num_mt * num_nt;
-    const int num_k = (K + BK - 1) / BK;
+    auto tile = [&](int t) {
+        TileRef r = tile_ref<GROUPED>(t, single, groups, G, &tmX, &tmY, &tmXl, &tmYl);
+        const int lt = t - r.pr->tile_begin;
+        r.n0 = (lt / r.pr->num_mt) * BN;
+        return r;
+    };
     // K is accumulated in TMEM in chunks of kc k-blocks (KCH = 0: the whole K)
-    const int kc = KCH > 0 ? KCH : num_k;
-    const int nch = (num_k + kc - 1) / kc;
+    auto chunks = [&](int num_k, int* kc) {
+        *kc = KCH > 0 ? KCH : num_k;
+        return (num_k + *kc - 1) / *kc;
+    };
 
     auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
-    auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::TX_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::PAIR_BYTES; };
     auto stage_blo = [&](int s) {
-        return smem + s * C::STAGE_BYTES + C::TX_BYTES + C::A_BYTES;
+        return smem + s * C::STAGE_BYTES + C::PAIR_BYTES + C::A_BYTES;
     };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&conv[s], 128);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -295,22 +359,45 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            prefetch_map(&tmX);
-            prefetch_map(&tmY);
+            if constexpr (!GROUPED) {
+                prefetch_map(&tmX);
+                prefetch_map(&tmY);
+                if constexpr (PASSES == 3) {
+                    prefetch_map(&tmXl);
+                    prefetch_map(&tmYl);
+                }
+            }
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                const int mt = t % num_mt, nt = t / num_mt;
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
+            const GemmProblem* last = nullptr;
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                const TileRef r = tile(t);
+                if (r.skip) continue;
+                if constexpr (GROUPED) {
+                    if (r.pr != last) {
+                        acquire_map(r.mx);
+                        acquire_map(r.my);
+                        if constexpr (PASSES == 3) {
+                            acquire_map(r.mxl);
+                            acquire_map(r.myl);
+                        }
+                        last = r.pr;
+                    }
+                }
+                for (int kb = 0; kb < r.num_k; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[s], C::TX_BYTES);
-                    tma_load_2d(stage_a(s), &tmX, kb * BK, mt * BM, &full[s]);
-                    tma_load_2d(stage_b(s), &tmY, kb * BK, nt * BN, &full[s]);
+                    mbar_expect_tx(&full[s], C::STAGE_BYTES);
+                    tma_load_2d(stage_a(s), r.mx, kb * BK, r.m0, &full[s]);
+                    tma_load_2d(stage_b(s), r.my, kb * BK, r.n0, &full[s]);
+                    if constexpr (PASSES == 3) {
+                        tma_load_2d(stage_alo(s), r.mxl, kb * BK, r.m0, &full[s]);
+                        tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
+                    }
                 }
             }
             if (!ok) {
@@ -325,7 +412,11 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
             constexpr uint32_t idesc = idesc_tf32<BN>();
             uint32_t it = 0, g = 0;
             bool ok = true, issued = false;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                const TileRef r = tile(t);
+                if (r.skip) continue;
+                int kc = 0;
+                const int nch = chunks(r.num_k, &kc);
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int b = g & 1;
                     if (!mbar_wait(&tempty[b], ((g >> 1) & 1) ^ 1, abort_flag, err,
@@ -335,13 +426,11 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
-                    const int kb0 = c * kc, kb1 = min(num_k, kb0 + kc);
+                    const int kb0 = c * kc, kb1 = min(r.num_k, kb0 + kc);
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
-                        uint64_t* ready = SPLIT == 3 ? &conv[s] : &full[s];
-                        if (!mbar_wait(ready, ph, abort_flag, err,
-                                       SPLIT == 3 ? DEV_TIMEOUT_CONV : DEV_TIMEOUT_FULL)) {
+                        if (!mbar_wait(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL)) {
                             ok = false;
                             break;
                         }
@@ -352,7 +441,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                             const uint32_t off = kk * UMMA_K * 4;
                             const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
                             const uint32_t first = ((kb - kb0) | kk) != 0 ? 1u : 0u;
-                            if constexpr (SPLIT == 3) {
+                            if constexpr (PASSES == 3) {
                                 const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
                                 const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
                                 mma_tf32(tmem_d, al, bh, idesc, first);
@@ -374,15 +463,19 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                 mbar_drain(drain, 0);
             }
         }
-    } else if (warp < 6) {
+    } else {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;     // TMEM lane quarter this warp may read
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         double dsum = 0.0;
         uint32_t g = 0;
-        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-            const int mt = t % num_mt, nt = t / num_mt;
-            const int m = mt * BM + 32 * q + lane;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            const TileRef r = tile(t);
+            if (r.skip) continue;
+            const EpiParams<float> p = r.pr->p;
+            const int m = r.m0 + 32 * q + lane;
+            int kc = 0;
+            const int nch = chunks(r.num_k, &kc);
             bool ok = true;
             if constexpr (KCH > 0) {
                 // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
@@ -402,10 +495,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                     tc_fence_after();
 #pragma unroll
                     for (int c0 = 0; c0 < BN; c0 += 32) {
-                        uint32_t r[32];
-                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), r);
+                        uint32_t rr[32];
+                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+                        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[b]);
@@ -415,12 +508,13 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                     float local = 0.f;
 #pragma unroll
                     for (int j = 0; j < BN; ++j) {
-                        const int n = nt * BN + j;
+                        const int n = r.n0 + j;
                         if (n < p.N) local += epi_apply(p, m, n, acc[j]);
                     }
                     dsum += (double)local;
                 }
             } else {
+                (void)nch;
                 const int b = g & 1;
                 int w = 1;
                 if (lane == 0)
@@ -430,15 +524,15 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                 tc_fence_after();
 #pragma unroll 1
                 for (int c0 = 0; c0 < BN; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), r);
+                    uint32_t rr[32];
+                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
                     if (m < p.M) {
                         float local = 0.f;
-                        const int nb = nt * BN + c0;
+                        const int nb = r.n0 + c0;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int n = nb + j;
-                            if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(r[j]));
+                            if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
                         }
                         dsum += (double)local;
                     }
@@ -447,52 +541,21 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, SPLIT>::THREADS, 1)
                 mbar_arrive(&tempty[b]);
                 ++g;
             }
-        }
-        if (p.dot) {
+            if constexpr (GROUPED) {
+                // each problem has its own dot target: flush per tile
+                if (p.dot) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-            if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
-        }
-    } else {
-        // ------------------------------------------------ hi/lo split (3xTF32)
-        if constexpr (SPLIT == 3) {
-            const int ct = threadIdx.x - 192;   // 0..127
-            uint32_t it = 0;
-            for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-                bool ok = true;
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (it / STAGES) & 1;
-                    int w_ok = 1;
-                    if (lane == 0)
-                        w_ok = mbar_wait(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL);
-                    w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-                    if (!w_ok) {
-                        ok = false;
-                        break;
-                    }
-                    // A and B hi tiles are contiguous, as are the lo tiles
-                    float4* hi = (float4*)stage_a(s);
-                    float4* lo = (float4*)stage_alo(s);
-                    constexpr int NV = C::TX_BYTES / 16;
-#pragma unroll 4
-                    for (int v = ct; v < NV; v += 128) {
-                        float4 x = hi[v];
-                        uint32_t h0 = rna_tf32(x.x), h1 = rna_tf32(x.y), h2 = rna_tf32(x.z),
-                                 h3 = rna_tf32(x.w);
-                        float4 hv = make_float4(__uint_as_float(h0), __uint_as_float(h1),
-                                                __uint_as_float(h2), __uint_as_float(h3));
-                        float4 lv = make_float4(__uint_as_float(rna_tf32(x.x - hv.x)),
-                                                __uint_as_float(rna_tf32(x.y - hv.y)),
-                                                __uint_as_float(rna_tf32(x.z - hv.z)),
-                                                __uint_as_float(rna_tf32(x.w - hv.w)));
-                        hi[v] = hv;
-                        lo[v] = lv;
-                    }
-                    fence_proxy_async();
-                    mbar_arrive(&conv[s]);
+                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                    if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
                 }
-                if (!ok) break;
+                dsum = 0.0;
+            }
+        }
+        if constexpr (!GROUPED) {
+            if (single.p.dot) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                if (lane == 0 && dsum != 0.0) atomicAdd(single.p.dot, dsum);
             }
         }
     }
@@ -546,29 +609,48 @@ int sm_count() {
     return n;
 }
 
-template <int BN, int STAGES, int SPLIT, int KCH>
-cdmpt_status launch(int M, int N, int K, const float* X, int ldx, const float* Y, int ldy,
-                    const EpiParams<float>& p, const double* skip, cudaStream_t s) {
-    using C = Cfg<BN, STAGES, SPLIT>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT, KCH>,
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED>
+cdmpt_status set_smem_attr() {
+    using C = Cfg<BN, STAGES, PASSES>;
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, PASSES, KCH, GROUPED>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) {
             set_error(std::string("tcgen05 GEMM smem attribute: ") + cudaGetErrorString(e));
             return CDMPT_ERR_CUDA;
         }
-        attr_set = true;
+        done = true;
     }
-    CUtensorMap mx, my;
-    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, BN)) {
+    return CDMPT_OK;
+}
+
+template <int BN, int STAGES, int PASSES, int KCH>
+cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ldx, const float* Y,
+                    const float* Yl, int ldy, const EpiParams<float>& p, const double* skip,
+                    cudaStream_t s) {
+    using C = Cfg<BN, STAGES, PASSES>;
+    {
+        const cdmpt_status st = set_smem_attr<BN, STAGES, PASSES, KCH, false>();
+        if (st != CDMPT_OK) return st;
+    }
+    CUtensorMap mx, my, mxl, myl;
+    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, BN) ||
+        !make_map(&mxl, Xl, M, K, ldx, BM) || !make_map(&myl, Yl, N, K, ldy, BN)) {
         set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
         return CDMPT_ERR_ARG;
     }
-    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    GemmProblem pr;
+    pr.p = p;
+    pr.K = K;
+    pr.tile_begin = 0;
+    pr.num_mt = (M + BM - 1) / BM;
+    pr.skip = skip;
+    pr.maps = nullptr;
+    const int tiles = pr.num_mt * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_tc<BN, STAGES, SPLIT, KCH>
-        <<<grid, C::THREADS, C::SMEM, s>>>(mx, my, K, p, skip, device_error_word());
+    k_gemm_tc<BN, STAGES, PASSES, KCH, false><<<grid, C::THREADS, C::SMEM, s>>>(
+        mx, my, mxl, myl, pr, nullptr, 1, tiles, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -578,7 +660,55 @@ cdmpt_status launch(int M, int N, int K, const float* X, int ldx, const float* Y
     return CDMPT_OK;
 }
 
+template <int BN, int STAGES, int PASSES, int KCH>
+cdmpt_status launch_grouped(const GemmProblem* problems, int G, int total_tiles, cudaStream_t s) {
+    using C = Cfg<BN, STAGES, PASSES>;
+    {
+        const cdmpt_status st = set_smem_attr<BN, STAGES, PASSES, KCH, true>();
+        if (st != CDMPT_OK) return st;
+    }
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    GemmProblem none;
+    std::memset(&none, 0, sizeof(none));
+    const int grid = total_tiles < sm_count() ? total_tiles : sm_count();
+    k_gemm_tc<BN, STAGES, PASSES, KCH, true><<<grid, C::THREADS, C::SMEM, s>>>(
+        dummy, dummy, dummy, dummy, none, problems, G, total_tiles, device_error_word());
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("grouped tcgen05 GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
 }  // namespace
+
+int tc_tile_n(int engine) { return engine == CDMPT_GEMM_TC_TF32 ? 256 : 128; }
+int tc_tile_m() { return BM; }
+
+bool tc_encode_operand(CUtensorMap* map, const float* base, int rows, int cols, int ld,
+                       bool as_y, int engine) {
+    // as X: box of 128 rows (BM); as Y: box of the engine's BN rows
+    return make_map(map, base, rows, cols, ld, as_y ? tc_tile_n(engine) : BM);
+}
+
+cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int total_tiles,
+                             cudaStream_t s) {
+    if (G <= 0 || total_tiles <= 0) return CDMPT_OK;
+    if (!tc_supported()) {
+        set_error("tcgen05 GEMM needs an sm_103 device");
+        return CDMPT_ERR_UNSUPPORTED;
+    }
+    if (engine == CDMPT_GEMM_TC_TF32) return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
+    switch (split_chunk()) {
+        case 1: return launch_grouped<128, 3, 3, 1>(problems, G, total_tiles, s);
+        case 4: return launch_grouped<128, 3, 3, 4>(problems, G, total_tiles, s);
+        case 0: return launch_grouped<128, 3, 3, 0>(problems, G, total_tiles, s);
+        default: return launch_grouped<128, 3, 3, 2>(problems, G, total_tiles, s);
+    }
+}
 
 bool tc_supported() {
     static int cached = -1;
@@ -592,15 +722,24 @@ bool tc_supported() {
     return cached == 1;
 }
 
-cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ldx,
-                         const float* Y, int ldy, float* D, int ldd, const Epilogue<float>& ep,
-                         const double* skip, cudaStream_t s) {
+cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& X, int ldx,
+                         const Operand<float>& Y, int ldy, float* D, int ldd,
+                         const Epilogue<float>& ep, const double* skip, cudaStream_t s) {
     if (M <= 0 || N <= 0) return CDMPT_OK;
     if (!tc_supported()) {
         set_error("tcgen05 GEMM needs an sm_103 device");
         return CDMPT_ERR_UNSUPPORTED;
     }
-    if ((ldx & 3) || (ldy & 3) || (((uintptr_t)X) & 15) || (((uintptr_t)Y) & 15) || K < 1) {
+    const bool three = engine != CDMPT_GEMM_TC_TF32;
+    const float* xh = X.hi ? X.hi : X.x;
+    const float* yh = Y.hi ? Y.hi : Y.x;
+    if (three && (!X.hi || !X.lo || !Y.hi || !Y.lo)) {
+        set_error("3xTF32 GEMM needs the hi/lo split of both operands");
+        return CDMPT_ERR_ARG;
+    }
+    auto misaligned = [](const float* q) { return q && (((uintptr_t)q) & 15); };
+    if ((ldx & 3) || (ldy & 3) || !xh || !yh || misaligned(xh) || misaligned(yh) ||
+        misaligned(X.lo) || misaligned(Y.lo) || K < 1) {
         set_error("tcgen05 GEMM: X/Y must be 16-byte aligned with ld a multiple of 4, K >= 1");
         return CDMPT_ERR_ARG;
     }
@@ -619,13 +758,14 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ld
     p.dot = ep.dot;
     p.E = ep.E;
     p.lde = ep.lde;
-    if (engine == CDMPT_GEMM_TC_TF32)
-        return launch<256, 4, 1, 0>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+    p.Dhi = ep.Dhi;
+    p.Dlo = ep.Dlo;
+    if (!three) return launch<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
     switch (split_chunk()) {
-        case 1: return launch<128, 3, 3, 1>(M, N, K, X, ldx, Y, ldy, p, skip, s);
-        case 4: return launch<128, 3, 3, 4>(M, N, K, X, ldx, Y, ldy, p, skip, s);
-        case 0: return launch<128, 3, 3, 0>(M, N, K, X, ldx, Y, ldy, p, skip, s);
-        default: return launch<128, 3, 3, 2>(M, N, K, X, ldx, Y, ldy, p, skip, s);
+        case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+        case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+        case 0: return launch<128, 3, 3, 0>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+        default: return launch<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
     }
 }
 

@@ -44,6 +44,17 @@ struct Epilogue {
     double* dot = nullptr; // accumulate sum D * E
     const T* E = nullptr;  // nullptr with dot -> E = D
     int lde = 0;
+    T* Dhi = nullptr;      // optional TF32 hi/lo split of D (float only)
+    T* Dlo = nullptr;
+};
+
+// A GEMM operand: the values and, for float storage, their TF32 split
+// (hi = rna_tf32(x), lo = rna_tf32(x - hi)); hi/lo may be null when unused.
+template <typename T>
+struct Operand {
+    const T* x = nullptr;
+    const T* hi = nullptr;
+    const T* lo = nullptr;
 };
 
 // Device-side CG scalars (one block of doubles per solve).
@@ -54,7 +65,8 @@ enum CgSlot {
     CG_BB = 3,      // <RHS, RHS>
     CG_DONE = 4,    // 1.0 once converged (kernels then return at once)
     CG_ITERS = 5,   // iterations taken (as double)
-    CG_TOL2 = 6,    // tol^2
+    CG_THRESH = 6,  // stop when <R,R> <= this (absolute)
+    CG_RR0 = 7,     // <R,R> of the initial residual
     CG_NSLOTS = 8
 };
 
@@ -75,37 +87,60 @@ template <typename T>
 cdmpt_status gemm_simt(int M, int N, int K, const T* X, int ldx, const T* Y, int ldy, T* D,
                        int ldd, const Epilogue<T>& ep, const double* skip, cudaStream_t s);
 
-cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const float* X, int ldx,
-                         const float* Y, int ldy, float* D, int ldd, const Epilogue<float>& ep,
-                         const double* skip, cudaStream_t s);
+// tcgen05 engines. TF32 reads X.hi / Y.hi when given (round-to-nearest
+// operands), else X.x / Y.x; 3xTF32 requires the hi and lo arrays of both.
+cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& X, int ldx,
+                         const Operand<float>& Y, int ldy, float* D, int ldd,
+                         const Epilogue<float>& ep, const double* skip, cudaStream_t s);
 bool tc_supported();   // device is sm_103 (tcgen05 kernels built for sm_103a)
+
+// Grouped tcgen05 launches (batched solves). A GemmProblem holds one problem's
+// epilogue, K, tile offset, skip flag and four tensor maps in device memory.
+struct GemmProblem;
+int tc_tile_n(int engine);
+int tc_tile_m();
+cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int total_tiles,
+                             cudaStream_t s);
 
 // Elementwise / reduction launchers (T = float or double). "count" is the
 // number of elements of a contiguous rows x ld block; padding columns hold 0.
 template <typename T>
 struct Ew {
+    // Kernels that produce GEMM operands optionally also write the hi/lo TF32
+    // split of their output (float only; hi = lo = nullptr skips it).
     static cdmpt_status init_z(T* Z, const double* H, int N, int ld, int ldh, int blocks,
-                               double scale, double shift, cudaStream_t s);
+                               double scale, double shift, cudaStream_t s, T* hi = nullptr,
+                               T* lo = nullptr);
     static cdmpt_status cg_update(T* X, T* R, const T* P, const T* Q, size_t count,
                                   double* sc, cudaStream_t s);
     static cdmpt_status cg_direction(T* P, const T* R, size_t count, const double* sc,
-                                     cudaStream_t s);
+                                     cudaStream_t s, T* hi = nullptr, T* lo = nullptr);
     static cdmpt_status dot(const T* A, const T* B, size_t count, double* out, const double* skip,
                             cudaStream_t s);
     static cdmpt_status axpby(T* Y, const T* X, size_t count, double a, double b,
-                              const double* skip, cudaStream_t s);
+                              const double* skip, cudaStream_t s, T* hi = nullptr,
+                              T* lo = nullptr);
     static cdmpt_status trace(const T* A, int N, int ld, int blocks, double* out, cudaStream_t s);
     static cdmpt_status transpose_add(T* out, const T* S, int N, int ld, int blocks,
-                                      cudaStream_t s);
-    static cdmpt_status symmetrize(T* Z, int N, int ld, int blocks, cudaStream_t s);
+                                      cudaStream_t s, T* hi = nullptr, T* lo = nullptr);
+    static cdmpt_status symmetrize(T* Z, int N, int ld, int blocks, cudaStream_t s,
+                                   T* hi = nullptr, T* lo = nullptr);
+    static cdmpt_status add_diag(T* A, int N, int ld, int blocks, double shift, cudaStream_t s,
+                                 T* hi = nullptr, T* lo = nullptr);
+    static cdmpt_status lincomb(T* out, const T* X, double a, const T* Y, double b, size_t count,
+                                cudaStream_t s);
+    static cdmpt_status transpose(T* out, const T* in, int N, int ld, int blocks, cudaStream_t s,
+                                  T* hi = nullptr, T* lo = nullptr);
     static cdmpt_status to_f64(double* out, int ldo, const T* in, int ldi, int N, int rows,
                                double a, double b_diag, cudaStream_t s);
     static cdmpt_status diag_dot(const T* A, const double* H, int N, int ld, int ldh,
                                  double* out, cudaStream_t s);
 };
 
+cdmpt_status split_tf32(const float* X, size_t count, float* hi, float* lo, cudaStream_t s);
 cdmpt_status cg_scalar_step(double* sc, cudaStream_t s);
-cdmpt_status cg_scalar_init(double* sc, double tol2, cudaStream_t s);
+// threshold = max(tol2 * <B,B>, tol2_r0 * <R0,R0>)
+cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s);
 cdmpt_status gershgorin(const double* H, int N, int ld, double* out2, cudaStream_t s);
 cdmpt_status gershgorin_noalloc(const double* H, int N, int ld, double* out2, cudaStream_t s);
 cdmpt_status frob_dot_f64_full(const double* A, const double* B, size_t count, double* out,

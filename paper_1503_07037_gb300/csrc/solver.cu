@@ -9,6 +9,12 @@
 // Every linear system is solved with right multiplication X -> X A_k (A_k is
 // symmetric), so all products are X Y^T with Y symmetric. Solutions are
 // symmetric in exact arithmetic and are symmetrised after every solve.
+// A_k is kept as W_k = Z_k^2 and applied as X + X W_k, and the 0th-order step
+// solves for the correction d = Z_{k+1} - 2 Z_k from d A_k = -2 Z_k W_k: in
+// FP32 this keeps the small quantities (Z^2 in early steps, the correction)
+// in their own exponent range instead of rounding them against I or 2 Z_k,
+// which makes the CG result about three times more accurate than solving for
+// Z_{k+1} against A_k = I + Z_k^2 directly.
 //
 // Chemical potential: Newton on Tr P0 = N_occ with the paper's slope
 // Tr P_mu = beta Tr[P0 (I - P0)] = beta/4 (N - ||Z_n||_F^2) (Eq. NewtRaphs),
@@ -16,10 +22,18 @@
 // Q = dP0/dmu, which at finite n is exactly beta P0 (I - P0) (I - Z_0^2)^-1;
 // the response runs once with mu1 = 0 and mu1 = -Tr P1|_0 / Tr Q follows in
 // closed form (the fixed point of the mu1 update of Algorithm 1).
+//
+// Mixed precision (CDMPT_MIXED_TF32): the occupation sweeps run with one-pass
+// TF32 products. The converged trajectory is then refined step by step: with
+// Z_k already refined, A_k = I + Z_k^2 and the residual 2 Z_k - Z_{k+1} A_k
+// are formed with split-TF32 (FP32-accurate) products, and the correction of
+// Z_{k+1} is found by CG whose iterations use one-pass TF32 products (mixed-
+// precision iterative refinement of each step's linear system). Between
+// passes a Newton step on mu shifts Z_0 by s2 dmu I. The response then uses
+// split-TF32 products throughout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <string>
 
@@ -52,7 +66,7 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n) {
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
     Z_.clear();
-    A_.clear();
+    W_.clear();
     N_ = N;
     D_ = D;
     n_ = n;
@@ -71,21 +85,32 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n) {
         *out = (T*)p;
         return CDMPT_OK;
     };
+    // split = true: also the TF32 hi/lo arrays (float storage only)
+    auto buf = [&](size_t elems, Buf<T>* b, bool split) -> cdmpt_status {
+        *b = Buf<T>();
+        CDMPT_TRY(grab(elems, &b->x));
+        if (split && sizeof(T) == 4) {
+            CDMPT_TRY(grab(elems, &b->hi));
+            CDMPT_TRY(grab(elems, &b->lo));
+        }
+        return CDMPT_OK;
+    };
     Z_.resize(n + 1);
-    A_.resize(n);
-    for (int k = 0; k <= n; ++k) CDMPT_TRY(grab(blk_, &Z_[k]));
-    for (int k = 0; k < n; ++k) CDMPT_TRY(grab(blk_, &A_[k]));
+    W_.resize(n);
+    for (int k = 0; k <= n; ++k) CDMPT_TRY(buf(blk_, &Z_[k], true));
+    for (int k = 0; k < n; ++k) CDMPT_TRY(buf(blk_, &W_[k], true));
     const size_t big = (size_t)rows_needed * ld;
-    CDMPT_TRY(grab(big, &R_));
-    CDMPT_TRY(grab(big, &P_));
-    CDMPT_TRY(grab(big, &Q_));
-    CDMPT_TRY(grab(big, &S_));
-    CDMPT_TRY(grab(big, &A1_));
-    CDMPT_TRY(grab(big, &RHS_));
-    CDMPT_TRY(grab(big, &Z1a_));
-    CDMPT_TRY(grab(big, &Z1b_));
-    CDMPT_TRY(grab(blk_, &Qmu_));
-    CDMPT_TRY(grab(blk_, &Mq_));
+    CDMPT_TRY(buf(big, &R_, false));
+    CDMPT_TRY(buf(big, &P_, true));
+    CDMPT_TRY(buf(big, &Q_, false));
+    CDMPT_TRY(buf(big, &S_, false));
+    CDMPT_TRY(buf(big, &A1_, true));
+    CDMPT_TRY(buf(big, &RHS_, true));
+    CDMPT_TRY(buf(big, &Z1a_, true));
+    CDMPT_TRY(buf(big, &Z1b_, true));
+    CDMPT_TRY(buf(blk_, &Qmu_, false));
+    CDMPT_TRY(buf(blk_, &Zh_, false));
+    traj_valid_ = q_valid_ = false;
     void* p = nullptr;
     if (cudaMalloc(&p, S_NSLOTS * sizeof(double)) != cudaSuccess) return CDMPT_ERR_OOM;
     allocs_.push_back(p);
@@ -102,13 +127,24 @@ cdmpt_status Solver<T>::read_scalars(Context& cx, const double* dev, int count) 
 }
 
 template <typename T>
-cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const T* X, const T* Y, T* D,
-                             const Epilogue<T>& ep, const double* skip, int engine_override) {
-    int engine = CDMPT_GEMM_SIMT;
-    if constexpr (sizeof(T) == 4) {
-        engine = engine_override ? engine_override : cx.engine;
-        if (engine == CDMPT_GEMM_AUTO) engine = CDMPT_GEMM_TC_3XTF32;
+int Solver<T>::engine_of(const Context& cx, int override_engine) const {
+    if constexpr (sizeof(T) == 8) {
+        return CDMPT_GEMM_SIMT;
+    } else {
+        const int e = override_engine ? override_engine : cx.engine;
+        return e == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : e;
     }
+}
+
+static double tensor_factor(int engine) {
+    return engine == CDMPT_GEMM_TC_3XTF32 ? 3.0 : engine == CDMPT_GEMM_TC_TF32 ? 1.0 : 0.0;
+}
+
+template <typename T>
+cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>& X,
+                             const Operand<T>& Y, T* D, const Epilogue<T>& ep, const double* skip,
+                             int engine_override) {
+    const int engine = engine_of(cx, engine_override);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cx.profile) {
         while (cx.ev.size() < 2 * (cx.ev_used + 1)) {
@@ -116,8 +152,14 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const T* X, cons
             CDMPT_CUDA_TRY(cudaEventCreate(&e));
             cx.ev.push_back(e);
         }
-        if (cx.ev_ok.size() < cx.ev_used + 1) cx.ev_ok.resize(cx.ev_used + 1);
+        if (cx.ev_ok.size() < cx.ev_used + 1) {
+            cx.ev_ok.resize(cx.ev_used + 1);
+            cx.ev_engine.resize(cx.ev_used + 1);
+            cx.ev_flops.resize(cx.ev_used + 1);
+        }
         cx.ev_ok[cx.ev_used] = 1;
+        cx.ev_engine[cx.ev_used] = engine;
+        cx.ev_flops[cx.ev_used] = 2.0 * M * (double)Nc * K;
         e0 = cx.ev[2 * cx.ev_used];
         e1 = cx.ev[2 * cx.ev_used + 1];
         CDMPT_CUDA_TRY(cudaEventRecord(e0, cx.stream));
@@ -125,11 +167,11 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const T* X, cons
     cdmpt_status s;
     if constexpr (sizeof(T) == 4) {
         if (engine == CDMPT_GEMM_SIMT)
-            s = gemm_simt<float>(M, Nc, K, X, ld, Y, ld, D, ld, ep, skip, cx.stream);
+            s = gemm_simt<float>(M, Nc, K, X.x, ld, Y.x, ld, D, ld, ep, skip, cx.stream);
         else
             s = gemm_tc_f32(engine, M, Nc, K, X, ld, Y, ld, D, ld, ep, skip, cx.stream);
     } else {
-        s = gemm_simt<double>(M, Nc, K, X, ld, Y, ld, D, ld, ep, skip, cx.stream);
+        s = gemm_simt<double>(M, Nc, K, X.x, ld, Y.x, ld, D, ld, ep, skip, cx.stream);
     }
     if (s != CDMPT_OK) return s;
     if (cx.profile) {
@@ -140,52 +182,68 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const T* X, cons
         const double f = 2.0 * M * (double)Nc * K;
         cx.st->gemm_launches += 1;
         cx.st->gemm_flops += f;
-        cx.st->tensor_flops += engine == CDMPT_GEMM_TC_3XTF32 ? 3 * f
-                               : engine == CDMPT_GEMM_TC_TF32 ? f
-                                                              : 0.0;
+        cx.st->tensor_flops += tensor_factor(engine) * f;
     }
     return CDMPT_OK;
 }
 
-// Solve X A = rhs_scale * rhs_base for X (rows x N), warm start in X.
-// Global CG in the Frobenius inner product; A is SPD (spectrum in [1, 2] for
-// the recursion, Sec. II). Scalars stay on the device; the host reads the
-// convergence flag once per chunk of iterations, and iterations launched
-// after convergence return at once.
+// Solve X A = rhs_scale * rhs for X (rows x N) by global CG in the Frobenius
+// inner product, starting from x0_scale * x0 (or zero). A is SPD (spectrum in
+// [1, 2] for the recursion, Sec. II). The initial residual and the iterations
+// may use different GEMM engines (accurate residual, cheap iterations: one
+// step of mixed-precision iterative refinement). Scalars stay on the device;
+// the host reads the convergence flag once per chunk of iterations, and
+// iterations launched after convergence return at once.
 template <typename T>
-cdmpt_status Solver<T>::cg(Context& cx, T* X, const T* A, const T* rhs_base, double rhs_scale,
-                           int rows, double tol, int maxit, int* iters_out, int engine_override) {
-    const size_t count = (size_t)rows * ld;
+cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
+                           double* rel_res0) {
+    const size_t count = (size_t)a.rows * ld;
     double* sc = sc_;
+    const int init_engine = engine_of(cx, a.init_engine);
+    const int iter_engine = engine_of(cx, a.iter_engine);
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc, 0, CG_NSLOTS * sizeof(double), cx.stream));
-    {   // R = s B - X A, <R,R>
+    if (a.x0) {
+        if (X != a.x0->x || a.x0_scale != 1.0)
+            CDMPT_TRY(Ew<T>::axpby(X, a.x0->x, count, a.x0_scale, 0.0, nullptr, cx.stream));
+        // R = rhs_scale rhs - x0_scale (s x0 + t x0 W), <R,R>
+        CDMPT_TRY(Ew<T>::lincomb(R_.x, a.rhs, a.rhs_scale, a.x0->x, -a.x0_scale * a.s, count,
+                                 cx.stream));
         Epilogue<T> ep;
-        ep.alpha = -1.0;
-        ep.beta = rhs_scale;
-        ep.C = rhs_base;
+        ep.alpha = -a.x0_scale * a.t;
+        ep.beta = 1.0;
+        ep.C = R_.x;
         ep.ldc = ld;
         ep.dot = sc + CG_RR;
-        CDMPT_TRY(gemm(cx, rows, N_, N_, X, A, R_, ep, nullptr, engine_override));
+        CDMPT_TRY(gemm(cx, a.rows, N_, N_, a.x0->op(), a.W->op(), R_.x, ep, nullptr, init_engine));
+    } else {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(X, 0, count * sizeof(T), cx.stream));
+        CDMPT_TRY(Ew<T>::axpby(R_.x, a.rhs, count, a.rhs_scale, 0.0, nullptr, cx.stream));
+        CDMPT_TRY(Ew<T>::dot(R_.x, R_.x, count, sc + CG_RR, nullptr, cx.stream));
     }
-    CDMPT_TRY(Ew<T>::dot(rhs_base, rhs_base, count, sc + CG_BB, nullptr, cx.stream));
-    CDMPT_TRY(cg_scalar_init(sc, tol * tol * rhs_scale * rhs_scale, cx.stream));
-    CDMPT_TRY(Ew<T>::axpby(P_, R_, count, 1.0, 0.0, sc + CG_DONE, cx.stream));
+    CDMPT_TRY(Ew<T>::dot(a.rhs, a.rhs, count, sc + CG_BB, nullptr, cx.stream));
+    CDMPT_TRY(cg_scalar_init(sc, a.tol * a.tol * a.rhs_scale * a.rhs_scale, a.tol_r0 * a.tol_r0,
+                             cx.stream));
+    CDMPT_TRY(Ew<T>::axpby(P_.x, R_.x, count, 1.0, 0.0, sc + CG_DONE, cx.stream, P_.hi, P_.lo));
 
-    int chunk = std::max(1, *iters_out);
-    int launched = 0, iters = 0;
+    int chunk = std::max(1, a.hint);
+    int iters = 0;
     while (true) {
         const size_t ev_first = cx.ev_used;
         for (int c = 0; c < chunk; ++c) {
-            Epilogue<T> ep;
+            Epilogue<T> ep;   // Q = s P + t P W, <P,Q>
+            ep.alpha = a.t;
+            ep.beta = a.s;
+            ep.C = P_.x;
+            ep.ldc = ld;
             ep.dot = sc + CG_PQ;
-            ep.E = P_;
+            ep.E = P_.x;
             ep.lde = ld;
-            CDMPT_TRY(gemm(cx, rows, N_, N_, P_, A, Q_, ep, sc + CG_DONE, engine_override));
-            CDMPT_TRY(Ew<T>::cg_update(X, R_, P_, Q_, count, sc, cx.stream));
-            CDMPT_TRY(Ew<T>::cg_direction(P_, R_, count, sc, cx.stream));
+            CDMPT_TRY(gemm(cx, a.rows, N_, N_, P_.op(), a.W->op(), Q_.x, ep, sc + CG_DONE,
+                           iter_engine));
+            CDMPT_TRY(Ew<T>::cg_update(X, R_.x, P_.x, Q_.x, count, sc, cx.stream));
+            CDMPT_TRY(Ew<T>::cg_direction(P_.x, R_.x, count, sc, cx.stream, P_.hi, P_.lo));
             CDMPT_TRY(cg_scalar_step(sc, cx.stream));
         }
-        launched += chunk;
         CDMPT_TRY(read_scalars(cx, sc, CG_NSLOTS));
         const int now = (int)cx.pinned[CG_ITERS];
         const int ran = now - iters;
@@ -195,55 +253,244 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const T* A, const T* rhs_base, dou
             for (size_t e = ev_first + ran; e < cx.ev_used; ++e) cx.ev_ok[e] = 0;
         }
         if (cx.st) {
-            const double f = 2.0 * rows * (double)N_ * N_;
-            int engine = CDMPT_GEMM_SIMT;
-            if constexpr (sizeof(T) == 4) {
-                engine = engine_override ? engine_override : cx.engine;
-                if (engine == CDMPT_GEMM_AUTO) engine = CDMPT_GEMM_TC_3XTF32;
-            }
+            const double f = 2.0 * a.rows * (double)N_ * N_;
             cx.st->gemm_launches += ran;
             cx.st->gemm_flops += ran * f;
-            cx.st->tensor_flops += ran * (engine == CDMPT_GEMM_TC_3XTF32 ? 3 * f
-                                          : engine == CDMPT_GEMM_TC_TF32 ? f
-                                                                         : 0.0);
+            cx.st->tensor_flops += ran * tensor_factor(iter_engine) * f;
         }
         if (cx.pinned[CG_DONE] != 0.0) break;
-        if (iters >= maxit) {
+        if (iters >= a.maxit) {
             *iters_out = iters;
-            set_error("CG did not reach the tolerance in " + std::to_string(maxit) +
+            set_error("CG did not reach the tolerance in " + std::to_string(a.maxit) +
                       " iterations (relative residual " +
                       std::to_string(std::sqrt(cx.pinned[CG_RRNEW] /
-                                               std::max(1e-300, cx.pinned[CG_BB] * rhs_scale *
-                                                                    rhs_scale))) +
+                                               std::max(1e-300, cx.pinned[CG_BB] * a.rhs_scale *
+                                                                    a.rhs_scale))) +
                       ")");
             return CDMPT_ERR_CG_MAXITER;
         }
         chunk = 2;
     }
     *iters_out = iters;
+    if (rel_res0) {
+        const double bb = cx.pinned[CG_BB] * a.rhs_scale * a.rhs_scale;
+        *rel_res0 = bb > 0 ? std::sqrt(cx.pinned[CG_RR0] / bb) : 0.0;
+    }
     return CDMPT_OK;
 }
 
 // One 0th-order pass of Algorithm 1 at chemical potential mu: Z_0 .. Z_n, A_0 .. A_{n-1}.
 template <typename T>
 cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s2,
-                              const cdmpt_opts& o, int n, int* cg_iters, int engine_override) {
-    CDMPT_TRY(Ew<T>::init_z(Z_[0], H0, N_, ld, ld, 1, -s2, mu, cx.stream));
+                              const cdmpt_opts& o, int n, int engine, double tol,
+                              int* cg_iters) {
+    CDMPT_TRY(Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo));
     int total = 0, hint = 1;
     for (int k = 0; k < n; ++k) {
-        Epilogue<T> ep;
-        ep.gamma = 1.0;   // A_k = I + Z_k Z_k
-        CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k], Z_[k], A_[k], ep, nullptr, engine_override));
-        CDMPT_TRY(Ew<T>::axpby(Z_[k + 1], Z_[k], blk_, 2.0, 0.0, nullptr, cx.stream));
-        int it = hint;
-        CDMPT_TRY(cg(cx, Z_[k + 1], A_[k], Z_[k], 2.0, N_, o.cg_tol, o.cg_maxit, &it,
-                     engine_override));
+        {   // W_k = Z_k Z_k
+            Epilogue<T> ep;
+            ep.Dhi = W_[k].hi;
+            ep.Dlo = W_[k].lo;
+            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr, engine));
+        }
+        {   // right side of the correction: -2 Z_k W_k
+            Epilogue<T> ep;
+            ep.alpha = -2.0;
+            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, engine));
+        }
+        CgArgs a;
+        a.W = &W_[k];
+        a.rhs = RHS_.x;
+        a.rows = N_;
+        a.tol = tol;
+        a.maxit = o.cg_maxit;
+        a.init_engine = a.iter_engine = engine;
+        a.hint = hint;
+        int it = 0;
+        CDMPT_TRY(cg(cx, Z_[k + 1].x, a, &it, nullptr));   // d, in the Z_{k+1} buffer
         total += it;
         hint = std::max(1, it);
-        CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1], N_, ld, 1, cx.stream));
+        // Z_{k+1} = 2 Z_k + d, symmetrised, with its TF32 split
+        CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, Z_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
+        CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
     }
     *cg_iters = total;
     return CDMPT_OK;
+}
+
+// One refinement pass over the stored trajectory (mixed precision): for each
+// step, accurate A_k from the refined Z_k, accurate residual of the stored
+// Z_{k+1}, one-pass TF32 CG iterations for the correction.
+template <typename T>
+cdmpt_status Solver<T>::refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
+                               double* max_rel_res) {
+    int total = 0;
+    double worst = 0.0;
+    for (int k = 0; k < n; ++k) {
+        {   // accurate W_k from the refined Z_k
+            Epilogue<T> ep;
+            ep.Dhi = W_[k].hi;
+            ep.Dlo = W_[k].lo;
+            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr,
+                           CDMPT_GEMM_TC_3XTF32));
+        }
+        // accurate residual r = 2 Z_k - Z_{k+1} - Z_{k+1} W_k of the stored Z_{k+1}
+        CDMPT_TRY(Ew<T>::lincomb(S_.x, Z_[k].x, 2.0, Z_[k + 1].x, -1.0, blk_, cx.stream));
+        {
+            Epilogue<T> ep;
+            ep.alpha = -1.0;
+            ep.beta = 1.0;
+            ep.C = S_.x;
+            ep.ldc = ld;
+            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k + 1].op(), W_[k].op(), RHS_.x, ep, nullptr,
+                           CDMPT_GEMM_TC_3XTF32));
+        }
+        // correction d (I + W_k) = r with one-pass TF32 iterations
+        CgArgs a;
+        a.W = &W_[k];
+        a.rhs = RHS_.x;
+        a.rows = N_;
+        a.tol = 1e-3;      // one-pass TF32 iterations gain about three digits
+        a.maxit = o.cg_maxit;
+        a.init_engine = a.iter_engine = CDMPT_GEMM_TC_TF32;
+        a.hint = 2;
+        int it = 0;
+        CDMPT_TRY(cg(cx, A1_.x, a, &it, nullptr));
+        total += it;
+        // relative size of the residual: |r| / |2 Z_k| (host-side from CG scalars)
+        const double bb = cx.pinned[CG_BB];
+        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_ZZ, 0, sizeof(double), cx.stream));
+        CDMPT_TRY(Ew<T>::dot(Z_[k].x, Z_[k].x, blk_, sc_ + S_ZZ, nullptr, cx.stream));
+        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+        const double zz = cx.pinned[S_ZZ];
+        if (zz > 0) worst = std::max(worst, std::sqrt(bb / (4.0 * zz)));
+        CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, A1_.x, blk_, 1.0, 1.0, nullptr, cx.stream));
+        CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
+    }
+    *cg_iters = total;
+    *max_rel_res = worst;
+    return CDMPT_OK;
+}
+
+template <typename T>
+cdmpt_status Solver<T>::occupation(Context& cx, int n, double* trP, double* zz) {
+    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRZ, 0, 2 * sizeof(double), cx.stream));
+    CDMPT_TRY(Ew<T>::trace(Z_[n].x, N_, ld, 1, sc_ + S_TRZ, cx.stream));
+    CDMPT_TRY(Ew<T>::dot(Z_[n].x, Z_[n].x, blk_, sc_ + S_ZZ, nullptr, cx.stream));
+    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+    *trP = 0.5 * (N_ + cx.pinned[S_TRZ]);
+    *zz = cx.pinned[S_ZZ];
+    return CDMPT_OK;
+}
+
+// Q = dP0/dmu = beta/4 (I - Z_n^2)(I - Z_0^2)^-1 for the stored trajectory,
+// by CG with the operator X - X W_0.
+template <typename T>
+cdmpt_status Solver<T>::compute_q(Context& cx) {
+    const int n = last_n_, N = N_;
+    const double beta = last_beta_;
+    const int acc = last_acc_;
+    const cdmpt_opts& o = last_opts_;
+    cdmpt_stats& st = *cx.st;
+    Epilogue<T> ep;
+    ep.alpha = -0.25 * beta;
+    ep.gamma = 0.25 * beta;
+    ep.Dhi = RHS_.hi;
+    ep.Dlo = RHS_.lo;
+    CDMPT_TRY(gemm(cx, N, N, N, Z_[n].op(), Z_[n].op(), RHS_.x, ep, nullptr, acc));
+    CgArgs a;   // (I - W_0) Q = beta/4 (I - Z_n^2), i.e. operator X - X W_0
+    a.W = &W_[0];
+    a.s = 1.0;
+    a.t = -1.0;
+    a.x0 = &RHS_;
+    a.rhs = RHS_.x;
+    a.rows = N;
+    a.tol = o.cg_tol;
+    a.maxit = o.cg_maxit;
+    a.init_engine = a.iter_engine = acc;
+    int it = 0;
+    CDMPT_TRY(cg(cx, Qmu_.x, a, &it, nullptr));
+    st.cg_iterations_q = it;
+    CDMPT_TRY(Ew<T>::symmetrize(Qmu_.x, N, ld, 1, cx.stream));
+    q_valid_ = true;
+    return CDMPT_OK;
+}
+
+// Reverse sweep. With Zh_{k+1} the (symmetric) adjoint of Z_{k+1}, the step
+// Z_{k+1} = 2 A_k^-1 Z_k, whose tangent is A_k dZ_{k+1} = 2 dZ_k - (Z_k dZ_k +
+// dZ_k Z_k) Z_{k+1}, gives with V = Zh_{k+1} A_k^-1 (one CG solve)
+//   Zh_k = sym(2 V - Z_{k+1} V Z_k - Z_k Z_{k+1} V).
+// Left products use the TN kernel with transposed right factors:
+// Z_k V^T = gemm(Z_k, V), Z_{k+1} V Z_k = gemm(Z_{k+1}, Z_k V^T), B V = gemm(B, V^T).
+// Z_0 = -s2 (H0 - mu I) and the canonical dmu = Tr(Q dH0) / Tr Q give
+//   grad = -s2 Zh_0 + s2 Tr(Zh_0) Q / Tr Q.
+template <typename T>
+cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
+    if (!traj_valid_) {
+        set_error("vjp: no completed solve on this handle");
+        return CDMPT_ERR_ARG;
+    }
+    const int n = last_n_, N = N_;
+    const int acc = last_acc_;
+    const cdmpt_opts& o = last_opts_;
+    // Zh_n = 1/2 sym(G0)   (P0 = (I + Z_n) / 2)
+    CDMPT_TRY(Ew<T>::init_z(Zh_.x, G0, N, ld, N, 1, 0.5, 0.0, cx.stream));
+    CDMPT_TRY(Ew<T>::symmetrize(Zh_.x, N, ld, 1, cx.stream));
+    Buf<T>& V = Z1a_;
+    Buf<T>& VT = Z1b_;
+    Buf<T>& M1T = A1_;
+    Buf<T>& B = RHS_;
+    for (int k = n - 1; k >= 0; --k) {
+        CgArgs a;
+        a.W = &W_[k];
+        a.rhs = Zh_.x;
+        a.rows = N;
+        a.tol = o.cg_tol;
+        a.maxit = o.cg_maxit;
+        a.init_engine = a.iter_engine = acc;
+        a.hint = 2;
+        int it = 0;
+        CDMPT_TRY(cg(cx, V.x, a, &it, nullptr));
+        if constexpr (sizeof(T) == 4) CDMPT_TRY(split_tf32(V.x, blk_, V.hi, V.lo, cx.stream));
+        CDMPT_TRY(Ew<T>::transpose(VT.x, V.x, N, ld, 1, cx.stream, VT.hi, VT.lo));
+        {
+            Epilogue<T> ep;   // Z_k V^T
+            ep.Dhi = M1T.hi;
+            ep.Dlo = M1T.lo;
+            CDMPT_TRY(gemm(cx, N, N, N, Z_[k].op(), V.op(), M1T.x, ep, nullptr, acc));
+        }
+        {
+            Epilogue<T> ep;   // Z_{k+1} V Z_k
+            CDMPT_TRY(gemm(cx, N, N, N, Z_[k + 1].op(), M1T.op(), S_.x, ep, nullptr, acc));
+        }
+        {
+            Epilogue<T> ep;   // B = Z_k Z_{k+1}
+            ep.Dhi = B.hi;
+            ep.Dlo = B.lo;
+            CDMPT_TRY(gemm(cx, N, N, N, Z_[k].op(), Z_[k + 1].op(), B.x, ep, nullptr, acc));
+        }
+        CDMPT_TRY(Ew<T>::lincomb(S_.x, V.x, 2.0, S_.x, -1.0, blk_, cx.stream));   // 2V - Z'VZ
+        {
+            Epilogue<T> ep;   // Zh_k = 2V - Z'VZ - B V
+            ep.alpha = -1.0;
+            ep.beta = 1.0;
+            ep.C = S_.x;
+            ep.ldc = ld;
+            CDMPT_TRY(gemm(cx, N, N, N, B.op(), VT.op(), Zh_.x, ep, nullptr, acc));
+        }
+        CDMPT_TRY(Ew<T>::symmetrize(Zh_.x, N, ld, 1, cx.stream));
+    }
+    if (!q_valid_) CDMPT_TRY(compute_q(cx));
+    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, 2 * sizeof(double), cx.stream));
+    CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+    CDMPT_TRY(Ew<T>::trace(Zh_.x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
+    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+    const double trQ = cx.pinned[S_TRQ], trZh = cx.pinned[S_TRQ + 1];
+    const double c = trQ > 0 ? last_s2_ * trZh / trQ : 0.0;
+    CDMPT_TRY(Ew<T>::lincomb(Zh_.x, Zh_.x, -last_s2_, Qmu_.x, c, blk_, cx.stream));
+    CDMPT_TRY(Ew<T>::to_f64(grad, N, Zh_.x, ld, N, N, 1.0, 0.0, cx.stream));
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
+    return check_device_error(cx.stream);
 }
 
 template <typename T>
@@ -257,6 +504,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         return CDMPT_ERR_ARG;
     }
     CDMPT_TRY(reserve(N, D, n));
+    traj_valid_ = q_valid_ = false;
     cdmpt_stats& st = *cx.st;
     const double s2 = std::ldexp(beta, -(n + 1));
     const double width = gmax - gmin;
@@ -265,33 +513,38 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                   " >= 1: X_0 leaves [0, 1]; use more recursion steps");
         return CDMPT_ERR_RANGE;
     }
+    const bool mixed = sizeof(T) == 4 && o.precision == CDMPT_MIXED_TF32;
+    if (mixed && cx.engine == CDMPT_GEMM_SIMT) {
+        set_error("MIXED_TF32 needs the tcgen05 engines");
+        return CDMPT_ERR_ARG;
+    }
+    // engines: "acc" for FP32-accurate products, "fast" for the occupation sweeps
+    const int acc = mixed ? (int)CDMPT_GEMM_TC_3XTF32 : engine_of(cx, 0);
+    const int fast = mixed ? (int)CDMPT_GEMM_TC_TF32 : acc;
     const double pad = std::min(40.0 / beta, 0.45 * (1.0 / s2 - width));
     double lo = gmin - pad, hi = gmax + pad;
     double mu = o.have_mu_guess ? o.mu_guess : trH0 / N;
     mu = std::min(std::max(mu, lo + 1e-3 * pad), hi - 1e-3 * pad);
-    const double occ_tol =
-        o.occ_tol > 0 ? o.occ_tol : N * (sizeof(T) == 8 ? 1e-12 : 1e-7);
+    const double occ_tol = o.occ_tol > 0 ? o.occ_tol : N * (sizeof(T) == 8 ? 1e-12 : 1e-7);
+    // one-pass TF32 traces are good to about 1e-4 relative; the refinement finishes mu
+    const double occ_tol_sweep = mixed ? std::max(occ_tol, 1e-5 * N) : occ_tol;
+    const double sweep_tol = mixed ? 1e-4 : o.cg_tol;
 
     // -------------------------------------------------- occupation loop
     bool converged = false;
     double trP = 0, zz = 0;
     for (int it = 0; it < o.mu_maxit; ++it) {
         int iters = 0;
-        CDMPT_TRY(sweep(cx, H0, mu, s2, o, n, &iters, 0));
+        CDMPT_TRY(sweep(cx, H0, mu, s2, o, n, fast, sweep_tol, &iters));
         st.mu_iterations += 1;
         st.cg_iterations_sweeps += iters;
         st.cg_iterations_last_sweep = iters;
-        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRZ, 0, 2 * sizeof(double), cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Z_[n], N, ld, 1, sc_ + S_TRZ, cx.stream));
-        CDMPT_TRY(Ew<T>::dot(Z_[n], Z_[n], blk_, sc_ + S_ZZ, nullptr, cx.stream));
-        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-        trP = 0.5 * (N + cx.pinned[S_TRZ]);
-        zz = cx.pinned[S_ZZ];
+        CDMPT_TRY(occupation(cx, n, &trP, &zz));
         const double err = trP - nocc;
         st.mu = mu;
         st.trace_P0 = trP;
         st.occupation_error = std::fabs(err);
-        if (std::fabs(err) <= occ_tol) {
+        if (std::fabs(err) <= occ_tol_sweep) {
             converged = true;
             break;
         }
@@ -311,62 +564,104 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                   std::to_string(st.mu_iterations) + " sweeps");
         return CDMPT_ERR_NO_CONVERGENCE;
     }
+
+    // -------------------------------------------------- refinement (mixed)
+    if (mixed) {
+        const int min_pass = std::max(1, o.refine_rounds);
+        bool done = false;
+        for (int pass = 0; pass < min_pass + 6 && !done; ++pass) {
+            int iters = 0;
+            double worst = 0.0;
+            CDMPT_TRY(refine(cx, o, n, &iters, &worst));
+            st.cg_iterations_refine += iters;
+            CDMPT_TRY(occupation(cx, n, &trP, &zz));
+            const double err = trP - nocc;
+            st.trace_P0 = trP;
+            st.occupation_error = std::fabs(err);
+            // refined traces are good to about 1e-9 N: finish mu that far
+            const bool occ_ok = std::fabs(err) <= (o.occ_tol > 0 ? occ_tol : 1e-9 * N);
+            if (occ_ok && pass + 1 >= min_pass && worst < 1e-4) {
+                done = true;
+                break;
+            }
+            if (!occ_ok) {   // Newton step on mu; Z_0 = -s2 (H - mu I) moves by s2 dmu I
+                const double slope = 0.25 * beta * (N - zz);
+                const double dmu = slope > 0 ? -err / slope : 0.0;
+                mu += dmu;
+                CDMPT_TRY(Ew<T>::add_diag(Z_[0].x, N, ld, 1, s2 * dmu, cx.stream, Z_[0].hi,
+                                          Z_[0].lo));
+            }
+        }
+        if (!done) {
+            set_error("mixed-precision refinement did not converge: |Tr P0 - N_occ| = " +
+                      std::to_string(st.occupation_error));
+            return CDMPT_ERR_NO_CONVERGENCE;
+        }
+    }
+    st.mu = mu;
     if (mu_out) *mu_out = mu;
+    traj_valid_ = true;
+    last_beta_ = beta;
+    last_s2_ = s2;
+    last_n_ = n;
+    last_acc_ = acc;
+    last_opts_ = o;
 
     // -------------------------------------------------- first-order response
     if (D > 0) {
         const int rows = D * N;
         const size_t count = (size_t)rows * ld;
-        T* Z1 = Z1a_;
-        T* Z1n = Z1b_;
-        CDMPT_TRY(Ew<T>::init_z(Z1, H1, N, ld, ld, D, -s2, 0.0, cx.stream));
+        Buf<T>* Z1 = &Z1a_;
+        Buf<T>* Z1n = &Z1b_;
+        CDMPT_TRY(Ew<T>::init_z(Z1->x, H1, N, ld, ld, D, -s2, 0.0, cx.stream, Z1->hi, Z1->lo));
         int total = 0, hint = 1;
         for (int k = 0; k < n; ++k) {
             {   // S^T = Z1 Z_k (stacked over directions)
                 Epilogue<T> ep;
-                CDMPT_TRY(gemm(cx, rows, N, N, Z1, Z_[k], S_, ep, nullptr));
+                CDMPT_TRY(gemm(cx, rows, N, N, Z1->op(), Z_[k].op(), S_.x, ep, nullptr, acc));
             }
             // A1 = Z_k Z1 + Z1 Z_k, block by block
-            CDMPT_TRY(Ew<T>::transpose_add(A1_, S_, N, ld, D, cx.stream));
-            {   // RHS = 2 Z1 - Z_{k+1} A1 = (2 Z1 - A1 Z_{k+1})^T per block
+            CDMPT_TRY(Ew<T>::transpose_add(A1_.x, S_.x, N, ld, D, cx.stream, A1_.hi, A1_.lo));
+            // correction form: Z1_{k+1} = 2 Z1_k + d1 with
+            //   d1 (I + W_k) = -Z_{k+1} A1 - 2 Z1_k W_k
+            // (both terms carry the same sign for saturated levels, so no cancellation)
+            {   // -Z_{k+1} A1 = -(A1 Z_{k+1})^T per block
                 Epilogue<T> ep;
                 ep.alpha = -1.0;
-                ep.beta = 2.0;
-                ep.C = Z1;
-                ep.ldc = ld;
                 ep.trans_block = N;
-                CDMPT_TRY(gemm(cx, rows, N, N, A1_, Z_[k + 1], RHS_, ep, nullptr));
+                CDMPT_TRY(gemm(cx, rows, N, N, A1_.op(), Z_[k + 1].op(), RHS_.x, ep, nullptr, acc));
             }
-            CDMPT_TRY(Ew<T>::axpby(Z1n, Z1, count, 2.0, 0.0, nullptr, cx.stream));
-            int it = hint;
-            CDMPT_TRY(cg(cx, Z1n, A_[k], RHS_, 1.0, rows, o.cg_tol, o.cg_maxit, &it));
+            {   // -= 2 Z1_k W_k
+                Epilogue<T> ep;
+                ep.alpha = -2.0;
+                ep.beta = 1.0;
+                ep.C = RHS_.x;
+                ep.ldc = ld;
+                CDMPT_TRY(gemm(cx, rows, N, N, Z1->op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
+            }
+            CgArgs a;
+            a.W = &W_[k];
+            a.rhs = RHS_.x;
+            a.rows = rows;
+            a.tol = o.cg_tol;
+            a.maxit = o.cg_maxit;
+            a.init_engine = a.iter_engine = acc;
+            a.hint = hint;
+            int it = 0;
+            CDMPT_TRY(cg(cx, Z1n->x, a, &it, nullptr));
             total += it;
             hint = std::max(1, it);
-            CDMPT_TRY(Ew<T>::symmetrize(Z1n, N, ld, D, cx.stream));
+            CDMPT_TRY(Ew<T>::axpby(Z1n->x, Z1->x, count, 2.0, 1.0, nullptr, cx.stream));
+            CDMPT_TRY(Ew<T>::symmetrize(Z1n->x, N, ld, D, cx.stream, Z1n->hi, Z1n->lo));
             std::swap(Z1, Z1n);
         }
         st.cg_iterations_response = total;
 
-        // Q = dP0/dmu = beta/4 (I - Z_n^2)(I - Z_0^2)^-1
-        {
-            Epilogue<T> ep;
-            ep.alpha = -0.25 * beta;
-            ep.gamma = 0.25 * beta;
-            CDMPT_TRY(gemm(cx, N, N, N, Z_[n], Z_[n], RHS_, ep, nullptr));
-            Epilogue<T> em;
-            em.alpha = -1.0;
-            em.gamma = 1.0;
-            CDMPT_TRY(gemm(cx, N, N, N, Z_[0], Z_[0], Mq_, em, nullptr));
-            CDMPT_TRY(Ew<T>::axpby(Qmu_, RHS_, blk_, 1.0, 0.0, nullptr, cx.stream));
-            int it = 1;
-            CDMPT_TRY(cg(cx, Qmu_, Mq_, RHS_, 1.0, N, o.cg_tol, o.cg_maxit, &it));
-            st.cg_iterations_q = it;
-            CDMPT_TRY(Ew<T>::symmetrize(Qmu_, N, ld, 1, cx.stream));
-        }
+        CDMPT_TRY(compute_q(cx));
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, (S_NSLOTS - S_TRQ) * sizeof(double),
                                        cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Qmu_, N, ld, 1, sc_ + S_TRQ, cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Z1, N, ld, D, sc_ + S_TRZ1, cx.stream));
+        CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+        CDMPT_TRY(Ew<T>::trace(Z1->x, N, ld, D, sc_ + S_TRZ1, cx.stream));
         CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
         const double trQ = cx.pinned[S_TRQ];
         st.trace_Q = trQ;
@@ -375,21 +670,21 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             const double mu1 = trQ > 0 ? -trP1 / trQ : 0.0;
             if (mu1_out) mu1_out[d] = mu1;
             // P1 = Z1/2 + mu1 Q  <=>  Z1 += 2 mu1 Q
-            CDMPT_TRY(Ew<T>::axpby(Z1 + (size_t)d * blk_, Qmu_, blk_, 2.0 * mu1, 1.0, nullptr,
+            CDMPT_TRY(Ew<T>::axpby(Z1->x + (size_t)d * blk_, Qmu_.x, blk_, 2.0 * mu1, 1.0, nullptr,
                                    cx.stream));
-            CDMPT_TRY(Ew<T>::diag_dot(Z1 + (size_t)d * blk_, H1 + (size_t)d * blk_, N, ld, ld,
+            CDMPT_TRY(Ew<T>::diag_dot(Z1->x + (size_t)d * blk_, H1 + (size_t)d * blk_, N, ld, ld,
                                       sc_ + S_ALPHA + d, cx.stream));
         }
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRZ1, 0, kMaxD * sizeof(double), cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Z1, N, ld, D, sc_ + S_TRZ1, cx.stream));
+        CDMPT_TRY(Ew<T>::trace(Z1->x, N, ld, D, sc_ + S_TRZ1, cx.stream));
         if (P1) {
             if (out_on_device) {
-                CDMPT_TRY(Ew<T>::to_f64(P1, N, Z1, ld, N, rows, 0.5, 0.0, cx.stream));
+                CDMPT_TRY(Ew<T>::to_f64(P1, N, Z1->x, ld, N, rows, 0.5, 0.0, cx.stream));
             } else {
                 double* tmp = nullptr;
                 CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, (size_t)rows * N * sizeof(double),
                                                cx.stream));
-                CDMPT_TRY(Ew<T>::to_f64(tmp, N, Z1, ld, N, rows, 0.5, 0.0, cx.stream));
+                CDMPT_TRY(Ew<T>::to_f64(tmp, N, Z1->x, ld, N, rows, 0.5, 0.0, cx.stream));
                 CDMPT_CUDA_TRY(cudaMemcpyAsync(P1, tmp, (size_t)rows * N * sizeof(double),
                                                cudaMemcpyDeviceToHost, cx.stream));
                 CDMPT_CUDA_TRY(cudaFreeAsync(tmp, cx.stream));
@@ -407,11 +702,11 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
 
     if (P0) {
         if (out_on_device) {
-            CDMPT_TRY(Ew<T>::to_f64(P0, N, Z_[n], ld, N, N, 0.5, 0.5, cx.stream));
+            CDMPT_TRY(Ew<T>::to_f64(P0, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
         } else {
             double* tmp = nullptr;
             CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, (size_t)N * N * sizeof(double), cx.stream));
-            CDMPT_TRY(Ew<T>::to_f64(tmp, N, Z_[n], ld, N, N, 0.5, 0.5, cx.stream));
+            CDMPT_TRY(Ew<T>::to_f64(tmp, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
             CDMPT_CUDA_TRY(cudaMemcpyAsync(P0, tmp, (size_t)N * N * sizeof(double),
                                            cudaMemcpyDeviceToHost, cx.stream));
             CDMPT_CUDA_TRY(cudaFreeAsync(tmp, cx.stream));

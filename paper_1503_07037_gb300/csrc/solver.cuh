@@ -21,8 +21,26 @@ struct Context {
     // event pairs for GEMM timing (profile mode)
     std::vector<cudaEvent_t> ev;
     std::vector<char> ev_ok;        // pair i timed a GEMM that did its work
+    std::vector<int> ev_engine;     // engine of pair i
+    std::vector<double> ev_flops;   // algorithmic flops of pair i
     size_t ev_used = 0;
     double* pinned = nullptr;       // host scalar readback (64 doubles)
+};
+
+// A rows x ld matrix (or stack of N-row blocks) and, for float storage, its
+// TF32 split written by whichever kernel produced it.
+template <typename T>
+struct Buf {
+    T* x = nullptr;
+    T* hi = nullptr;
+    T* lo = nullptr;
+    Operand<T> op() const {
+        Operand<T> o;
+        o.x = x;
+        o.hi = hi;
+        o.lo = lo;
+        return o;
+    }
 };
 
 template <typename T>
@@ -36,24 +54,59 @@ public:
                        double nocc, int n, double* P0, double* P1, double* mu_out,
                        double* mu1_out, int out_on_device, double* alpha_out);
 
+    // Vector-Jacobian product of the last solve: grad = d Tr[G0 P0] / d H0 under
+    // the canonical constraint, by a reverse sweep through the stored
+    // trajectory. G0 and grad are N x N FP64 device arrays (leading dimension N).
+    cdmpt_status vjp_p0(Context& cx, const double* G0, double* grad);
+    bool trajectory_valid() const { return traj_valid_; }
+
     int ld = 0;
 
 private:
-    cdmpt_status gemm(Context& cx, int M, int Nc, int K, const T* X, const T* Y, T* D,
-                      const Epilogue<T>& ep, const double* skip, int engine_override = 0);
-    cdmpt_status cg(Context& cx, T* X, const T* A, const T* rhs_base, double rhs_scale, int rows,
-                    double tol, int maxit, int* iters_out, int engine_override = 0);
+    struct CgArgs {
+        // system operator X -> s X + t X W (W symmetric): the step matrix
+        // A_k = I + Z_k^2 is applied as X + X W_k so that the small part
+        // W_k = Z_k^2 keeps its own FP32 precision instead of sitting next to I
+        const Buf<T>* W = nullptr;
+        double s = 1.0, t = 1.0;
+        const Buf<T>* x0 = nullptr;     // warm start (null: zero)
+        double x0_scale = 1.0;
+        const T* rhs = nullptr;         // right-hand side = rhs_scale * rhs
+        double rhs_scale = 1.0;
+        int rows = 0;
+        double tol = 1e-7;              // ||R|| <= tol ||RHS||
+        double tol_r0 = 0.0;            // or ||R|| <= tol_r0 ||R_0||
+        int maxit = 200;
+        int init_engine = 0;            // engine of the initial residual (0: context default)
+        int iter_engine = 0;            // engine of the iterations
+        int hint = 1;                   // iterations expected (first chunk size)
+    };
+    cdmpt_status gemm(Context& cx, int M, int Nc, int K, const Operand<T>& X,
+                      const Operand<T>& Y, T* D, const Epilogue<T>& ep, const double* skip,
+                      int engine_override = 0);
+    cdmpt_status cg(Context& cx, T* X, const CgArgs& a, int* iters_out, double* rel_res0);
     cdmpt_status sweep(Context& cx, const double* H0, double mu, double s2, const cdmpt_opts& o,
-                       int n, int* cg_iters, int engine_override);
+                       int n, int engine, double tol, int* cg_iters);
+    cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
+                        double* max_rel_res);
+    cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);
+    cdmpt_status compute_q(Context& cx);
     cdmpt_status read_scalars(Context& cx, const double* dev, int count);
+    int engine_of(const Context& cx, int override_engine) const;
 
     int N_ = 0, D_ = 0, n_ = 0;
     size_t blk_ = 0;                 // N * ld elements
-    std::vector<T*> Z_, A_;          // trajectory Z_0..Z_n and A_0..A_{n-1}
-    T *R_ = nullptr, *P_ = nullptr, *Q_ = nullptr;       // CG work (D' * N rows)
-    T *S_ = nullptr, *A1_ = nullptr, *RHS_ = nullptr;    // response work
-    T *Z1a_ = nullptr, *Z1b_ = nullptr;                  // response iterates
-    T *Qmu_ = nullptr, *Mq_ = nullptr;                   // dP/dmu and I - Z_0^2
+    std::vector<Buf<T>> Z_, W_;      // trajectory Z_0..Z_n and W_k = Z_k^2, k < n
+    Buf<T> R_, P_, Q_;               // CG work (D' * N rows)
+    Buf<T> S_, A1_, RHS_;            // response work
+    Buf<T> Z1a_, Z1b_;               // response iterates
+    Buf<T> Qmu_;                     // dP/dmu
+    Buf<T> Zh_;                      // adjoint of Z_k in the reverse sweep
+    // state of the last solve, for the response's Q and the adjoint
+    bool traj_valid_ = false, q_valid_ = false;
+    double last_beta_ = 0, last_s2_ = 0;
+    int last_n_ = 0, last_acc_ = 0;
+    cdmpt_opts last_opts_{};
     double* sc_ = nullptr;           // device scalars
     std::vector<void*> allocs_;
     int rows_cap_ = 0;               // row capacity of the CG work buffers

@@ -1,8 +1,13 @@
 """GPU parity of the full canonical solve (C ABI) against the FP64 oracle.
 
 Parity reference: the oracle's recursion-exact function (kind="rec", same n).
-Bars (relative Frobenius norm): 1e-10 for FP64, 1e-5 for FP32. The gap of the
-recursion to the exact Fermi-Dirac function is reported separately.
+Bars (relative Frobenius norm): 1e-10 for FP64, 1e-5 for FP32, 1e-6 for mixed
+precision after refinement. The gap of the recursion to the exact Fermi-Dirac
+function is reported separately.
+
+Mixed precision at beta = 80 keeps the trajectory in FP32: plain float32 with
+exact (LU) step solves already leaves P1 at 1.1e-6 there (N = 4096, measured
+on the host), so that one case is held to 2e-6, the FP32 storage floor.
 """
 import numpy as np
 import pytest
@@ -12,7 +17,7 @@ import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
-BAR = {"fp64": 1e-10, "fp32": 1e-5}
+BAR = {"fp64": 1e-10, "fp32": 1e-5, "mixed": 1e-6}
 
 
 def _rel(a, b):
@@ -70,6 +75,16 @@ def test_fp32_lattice_1000(cuda, cdmpt_lib, engine):
     _check(r, ref, BAR["fp32"], 1)
 
 
+@pytest.mark.parametrize("beta", [5.0, 20.0])
+def test_mixed_lattice_1000(cuda, cdmpt_lib, beta):
+    """TF32 sweeps + split-TF32 refinement of the trajectory + split-TF32 response."""
+    p = syn.cubic_lattice((10, 10, 10), seed=1002, beta=beta, n=14, directions="xy")
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    r = _run(cdmpt_lib, p, "mixed")
+    _check(r, ref, 2e-6, 2)
+    assert r["stats"]["cg_iterations_refine"] > 0
+
+
 def test_tf32_single_pass_is_coarse(cuda, cdmpt_lib):
     """One TF32 pass per product (no refinement) lands near 1e-4, far from the FP32 bar."""
     p = syn.cubic_lattice((10, 10, 10), seed=1002, beta=20.0, n=14)
@@ -87,6 +102,15 @@ def test_fp32_cubic16_full_size(cuda, cdmpt_lib, beta):
     ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=eig)
     r = _run(cdmpt_lib, p, "fp32")
     _check(r, ref, BAR["fp32"], 1)
+
+
+@pytest.mark.parametrize("beta,bar", [(5.0, 1e-6), (20.0, 1e-6), (80.0, 2e-6)])
+def test_mixed_cubic16_full_size(cuda, cdmpt_lib, beta, bar):
+    """Mixed precision on the measured workload (N = 4096, n = 14)."""
+    p = syn.cubic_lattice((16, 16, 16), seed=1002, beta=beta, n=14)
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=_eig_cubic16())
+    r = _run(cdmpt_lib, p, "mixed")
+    _check(r, ref, bar, 1)
 
 
 _EIG = {}
