@@ -267,6 +267,23 @@ cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X,
                             double beta, const float* C, int ldc, double gamma, int diag_block,
                             int trans_block, double* dot, const float* E, int lde, void* stream);
 
+/* TF32 split of count FP32 values for the tensor-core engines:
+ * hi = round_to_nearest_tf32(x), lo = round_to_nearest_tf32(x - hi), so that
+ * hi + lo carries x to about 2^-22 relative (split-TF32 products).
+ * count must be a multiple of 4; X, hi, lo 16-byte aligned device arrays. */
+cdmpt_status cdmpt_split_tf32(const float* X, size_t count, float* hi, float* lo, void* stream);
+
+/* cdmpt_gemm_f32 for operands already split by cdmpt_split_tf32 (Xhi/Xlo and
+ * Yhi/Ylo share the leading dimensions ldx / ldy). engine TC_TF32 reads only
+ * the hi arrays; TC_3XTF32 (or AUTO) all four. Lets a caller split an operand
+ * once and reuse it over many products. */
+cdmpt_status cdmpt_gemm_f32_split(int engine, int M, int Ncols, int K, const float* Xhi,
+                                  const float* Xlo, int ldx, const float* Yhi, const float* Ylo,
+                                  int ldy, float* D, int ldd, double alpha, double beta,
+                                  const float* C, int ldc, double gamma, int diag_block,
+                                  int trans_block, double* dot, const float* E, int lde,
+                                  void* stream);
+
 /* FP64 counterpart of cdmpt_gemm_f32 on CUDA cores (no alignment rule). */
 cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,
                             int ldy, double* D, int ldd, double alpha, double beta,

@@ -84,7 +84,8 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_destroy", "cdmpt_gemm_f32", "cdmpt_gemm_f64", "cdmpt_spectral_bounds",
            "cdmpt_spectral_bounds_noalloc", "cdmpt_vjp_P0", "cdmpt_batch_create",
            "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
-           "cdmpt_batch_last_error", "cdmpt_batch_destroy"]
+           "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
+           "cdmpt_gemm_f32_split"]
 
 
 def lib() -> ctypes.CDLL:
@@ -119,6 +120,9 @@ def lib() -> ctypes.CDLL:
         "cdmpt_batch_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "cdmpt_batch_last_error": (ctypes.c_char_p, [P]),
         "cdmpt_batch_destroy": (V, [P]),
+        "cdmpt_split_tf32": (I, [P, ctypes.c_size_t, P, P, P]),
+        "cdmpt_gemm_f32_split": (I, [I, I, I, I, P, P, I, P, P, I, P, I, D, D, P, I, D, I, I, P, P, I,
+                                     P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -215,6 +219,31 @@ def gemm_f32(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, tran
                                 C.stride(0) if C is not None else 0, float(gamma), diag_block,
                                 trans_block, _ptr(dot), _ptr(E),
                                 E.stride(0) if E is not None else 0, _stream_ptr(stream)))
+
+
+def split_tf32(X, hi=None, lo=None, stream=None):
+    """TF32 hi/lo split of a contiguous float32 CUDA tensor (returns (hi, lo))."""
+    import torch
+    hi = torch.empty_like(X) if hi is None else hi
+    lo = torch.empty_like(X) if lo is None else lo
+    _check(lib().cdmpt_split_tf32(_ptr(X), X.numel(), _ptr(hi), _ptr(lo), _stream_ptr(stream)))
+    return hi, lo
+
+
+def gemm_f32_split(Xs, Ys, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, engine="3xtf32", M=None,
+                   Ncols=None, K=None, stream=None):
+    """gemm_f32 on pre-split operands Xs = (hi, lo), Ys = (hi, lo)."""
+    Xh, Xl = Xs
+    Yh, Yl = Ys
+    M = Xh.shape[0] if M is None else M
+    K = Xh.shape[1] if K is None else K
+    Ncols = Yh.shape[0] if Ncols is None else Ncols
+    eng = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    _check(lib().cdmpt_gemm_f32_split(eng, M, Ncols, K, _ptr(Xh), _ptr(Xl), Xh.stride(0),
+                                      _ptr(Yh), _ptr(Yl), Yh.stride(0), _ptr(D), D.stride(0),
+                                      float(alpha), float(beta), _ptr(C),
+                                      C.stride(0) if C is not None else 0, float(gamma), 0, 0,
+                                      None, None, 0, _stream_ptr(stream)))
 
 
 def gemm_f64(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, trans_block=0,

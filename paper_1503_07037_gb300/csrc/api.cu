@@ -411,6 +411,55 @@ cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X,
     return st;
 }
 
+cdmpt_status cdmpt_split_tf32(const float* X, size_t count, float* hi, float* lo, void* stream) {
+    if (!X || !hi || !lo || (count & 3)) {
+        set_error("split_tf32: need X, hi, lo and count a multiple of 4");
+        return CDMPT_ERR_ARG;
+    }
+    return split_tf32(X, count, hi, lo, (cudaStream_t)stream);
+}
+
+cdmpt_status cdmpt_gemm_f32_split(int engine, int M, int Ncols, int K, const float* Xhi,
+                                  const float* Xlo, int ldx, const float* Yhi, const float* Ylo,
+                                  int ldy, float* D, int ldd, double alpha, double beta,
+                                  const float* C, int ldc, double gamma, int diag_block,
+                                  int trans_block, double* dot, const float* E, int lde,
+                                  void* stream) {
+    if (M < 0 || Ncols < 0 || K < 1 || !Xhi || !Yhi || !D || (beta != 0.0 && !C) ||
+        (engine != CDMPT_GEMM_TC_TF32 && (!Xlo || !Ylo))) {
+        set_error("gemm_f32_split: bad arguments");
+        return CDMPT_ERR_ARG;
+    }
+    if (engine != CDMPT_GEMM_AUTO && engine != CDMPT_GEMM_TC_TF32 && engine != CDMPT_GEMM_TC_3XTF32) {
+        set_error("gemm_f32_split: engine must be AUTO, TC_TF32 or TC_3XTF32");
+        return CDMPT_ERR_ARG;
+    }
+    if (trans_block > 0 && (Ncols != trans_block || M % trans_block)) {
+        set_error("gemm_f32_split: trans_block needs Ncols == trans_block and M a multiple of it");
+        return CDMPT_ERR_ARG;
+    }
+    Epilogue<float> ep;
+    ep.alpha = alpha;
+    ep.beta = beta;
+    ep.C = C;
+    ep.ldc = ldc;
+    ep.gamma = gamma;
+    ep.diag_block = diag_block;
+    ep.trans_block = trans_block;
+    ep.dot = dot;
+    ep.E = E;
+    ep.lde = lde;
+    Operand<float> ox, oy;
+    ox.x = Xhi;
+    ox.hi = Xhi;
+    ox.lo = Xlo;
+    oy.x = Yhi;
+    oy.hi = Yhi;
+    oy.lo = Ylo;
+    return gemm_tc_f32(engine == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : engine, M, Ncols, K, ox,
+                       ldx, oy, ldy, D, ldd, ep, nullptr, (cudaStream_t)stream);
+}
+
 cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,
                             int ldy, double* D, int ldd, double alpha, double beta,
                             const double* C, int ldc, double gamma, int diag_block,

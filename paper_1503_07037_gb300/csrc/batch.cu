@@ -183,6 +183,13 @@ cdmpt_status flush_maps(cdmpt_batch* b) {
 }
 
 // One problem of a grouped GEMM: D = alpha X Y^T + beta C + gamma I (rows x N_b, K = N_b).
+void add_flops(cdmpt_batch* b, double f) {
+    if (b->cx.st) {
+        b->cx.st->gemm_flops += f;
+        b->cx.st->tensor_flops += 3.0 * f;
+    }
+}
+
 struct GemmSpec {
     const Mat* X;
     int rows;
@@ -235,14 +242,7 @@ cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
     for (size_t i = 0; i < probs.size(); ++i) probs[i].maps = b->maps_dev + quad[i];
     const GemmProblem* dev = nullptr;
     CDMPT_TRY(stage(b, probs, &dev));
-    if (b->cx.st) {
-        for (const GemmSpec& g : specs) {
-            const double f = 2.0 * g.p.M * (double)g.p.N * g.p.N;
-            b->cx.st->gemm_flops += f;
-            b->cx.st->tensor_flops += 3.0 * f;
-        }
-        b->cx.st->gemm_launches += 1;
-    }
+    if (b->cx.st) b->cx.st->gemm_launches += 1;
     return gemm_tc_grouped(kEngine, dev, (int)probs.size(), tiles, b->cx.stream);
 }
 
@@ -442,6 +442,12 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
         }
         if (all) {
             *iters = most;
+            for (int i = 0; i < G; ++i) {
+                const Sys& sy = b->sys[i];
+                const double f = 2.0 * a[i].rows * (double)sy.N * sy.N;
+                add_flops(b, f * b->pinned[i * kSlots + CG_ITERS]);
+                if (a[i].x0 && !(skip[i] && b->sys[i].converged)) add_flops(b, f);
+            }
             return CDMPT_OK;
         }
         if (done_iters >= b->opts.cg_maxit) {
@@ -509,6 +515,9 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
         }
         CDMPT_TRY(grouped_gemm(b, gw));
         CDMPT_TRY(grouped_gemm(b, gr));
+        for (int i = 0; i < G; ++i)
+            if (!b->sys[i].converged)
+                add_flops(b, 4.0 * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
         int it = 0;
         CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, skip, hint, &it));
         total += it;
@@ -807,6 +816,8 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             CDMPT_TRY(run_tiles(b, dta, D, grouped_transpose_add));
             CDMPT_TRY(grouped_gemm(b, g1));
             CDMPT_TRY(grouped_gemm(b, g2));
+            for (int i = 0; i < G; ++i)
+                add_flops(b, 6.0 * D * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
             int it = 0;
             cdmpt_status s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it);
             if (s != CDMPT_OK) return bfail(b, s);
@@ -838,6 +849,8 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 dsym.push_back(y);
             }
             CDMPT_TRY(grouped_gemm(b, gq));
+            for (int i = 0; i < G; ++i)
+                add_flops(b, 2.0 * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
             int it = 0;
             cdmpt_status s = cg_batch(b, cg, 1.0, -1.0, b->opts.cg_tol, none, 1, &it);
             if (s != CDMPT_OK) return bfail(b, s);

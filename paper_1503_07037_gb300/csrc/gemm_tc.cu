@@ -158,6 +158,29 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of both CTAs of a cluster pair.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                     "memory");
+}
+
+// TMA load of one box into the same shared-memory offset of every CTA in
+// mask, each CTA's mbarrier at the same offset receiving the transaction bytes.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
 // Orders the tensormap proxy after the generic writes (a host copy) that put a
 // tensor map into global memory, before TMA first reads it.
 __device__ __forceinline__ void acquire_map(const CUtensorMap* map) {
@@ -223,6 +246,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
+        : "memory");
+}
+
+// Arrives on the mbarrier at the same offset in every CTA of mask once this
+// thread's prior tcgen05 operations complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
         : "memory");
 }
 
@@ -297,7 +330,11 @@ __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
     return r;
 }
 
-template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED>
+// PAIR: a cluster of two CTAs works on vertically adjacent tiles (same B
+// columns); each CTA loads its own A tile and half of the B tile, multicast to
+// both, so each SM fetches half as many B bytes. Stage reuse then waits for
+// both CTAs' MMAs (empty barriers count two commits).
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool PAIR = false>
 __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
@@ -336,10 +373,14 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         return smem + s * C::STAGE_BYTES + C::PAIR_BYTES + C::A_BYTES;
     };
 
+    const uint32_t rank = PAIR ? cluster_rank() : 0;
+    // tile t of this CTA: single CTAs stride over tiles, pairs over tile pairs
+    const int t_first = PAIR ? (int)(blockIdx.x / 2) * 2 + (int)rank : (int)blockIdx.x;
+    const int t_step = PAIR ? (int)gridDim.x : (int)gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], PAIR ? 2 : 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -353,6 +394,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     if (warp == 1) tmem_alloc(tmem_holder, C::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // peer barriers initialised before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
 
@@ -370,7 +412,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             const GemmProblem* last = nullptr;
-            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            for (int t = t_first; t < total_tiles && ok; t += t_step) {
                 const TileRef r = tile(t);
                 if (r.skip) continue;
                 if constexpr (GROUPED) {
@@ -393,10 +435,21 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     }
                     mbar_expect_tx(&full[s], C::STAGE_BYTES);
                     tma_load_2d(stage_a(s), r.mx, kb * BK, r.m0, &full[s]);
-                    tma_load_2d(stage_b(s), r.my, kb * BK, r.n0, &full[s]);
-                    if constexpr (PASSES == 3) {
+                    if constexpr (PASSES == 3)
                         tma_load_2d(stage_alo(s), r.mxl, kb * BK, r.m0, &full[s]);
-                        tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
+                    if constexpr (PAIR) {
+                        // this CTA's half of the B box, into both CTAs
+                        const int half = BN / 2;
+                        const uint32_t off = rank * (uint32_t)(C::B_BYTES / 2);
+                        tma_load_2d_mc(stage_b(s) + off, r.my, kb * BK, r.n0 + (int)rank * half,
+                                       &full[s], (uint16_t)0x3);
+                        if constexpr (PASSES == 3)
+                            tma_load_2d_mc(stage_blo(s) + off, r.myl, kb * BK,
+                                           r.n0 + (int)rank * half, &full[s], (uint16_t)0x3);
+                    } else {
+                        tma_load_2d(stage_b(s), r.my, kb * BK, r.n0, &full[s]);
+                        if constexpr (PASSES == 3)
+                            tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
                     }
                 }
             }
@@ -412,7 +465,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             constexpr uint32_t idesc = idesc_tf32<BN>();
             uint32_t it = 0, g = 0;
             bool ok = true, issued = false;
-            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            for (int t = t_first; t < total_tiles && ok; t += t_step) {
                 const TileRef r = tile(t);
                 if (r.skip) continue;
                 int kc = 0;
@@ -452,7 +505,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                             }
                         }
                         issued = true;
-                        mma_commit(&empty[s]);
+                        if constexpr (PAIR)
+                            mma_commit_mc(&empty[s], (uint16_t)0x3);
+                        else
+                            mma_commit(&empty[s]);
                     }
                     if (!ok) break;
                     mma_commit(&tfull[b]);
@@ -469,7 +525,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         double dsum = 0.0;
         uint32_t g = 0;
-        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        for (int t = t_first; t < total_tiles; t += t_step) {
             const TileRef r = tile(t);
             if (r.skip) continue;
             const EpiParams<float> p = r.pr->p;
@@ -562,6 +618,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // no CTA leaves while its peer may still signal it
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -658,6 +715,87 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
         return CDMPT_ERR_CUDA;
     }
     return CDMPT_OK;
+}
+
+// Cluster-pair launch (B multicast); needs an even number of M tiles.
+template <int BN, int STAGES, int PASSES, int KCH>
+cdmpt_status launch_pair(int M, int N, int K, const float* X, const float* Xl, int ldx,
+                         const float* Y, const float* Yl, int ldy, const EpiParams<float>& p,
+                         const double* skip, cudaStream_t s) {
+    using C = Cfg<BN, STAGES, PASSES>;
+    auto kern = k_gemm_tc<BN, STAGES, PASSES, KCH, false, true>;
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3(2 * sm_count() / 2);
+        q.blockDim = dim3(C::THREADS);
+        q.dynamicSmemBytes = C::SMEM;
+        cudaLaunchAttribute a;
+        a.id = cudaLaunchAttributeClusterDimension;
+        a.val.clusterDim.x = 2;
+        a.val.clusterDim.y = 1;
+        a.val.clusterDim.z = 1;
+        q.attrs = &a;
+        q.numAttrs = 1;
+        int n = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
+        if (e != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            set_error("tcgen05 pair GEMM: no resident cluster of two");
+            return CDMPT_ERR_UNSUPPORTED;
+        }
+        max_clusters = n;
+    }
+    CUtensorMap mx, my, mxl, myl;
+    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, BN / 2) ||
+        !make_map(&mxl, Xl, M, K, ldx, BM) || !make_map(&myl, Yl, N, K, ldy, BN / 2)) {
+        set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
+        return CDMPT_ERR_ARG;
+    }
+    GemmProblem pr;
+    pr.p = p;
+    pr.K = K;
+    pr.tile_begin = 0;
+    pr.num_mt = (M + BM - 1) / BM;
+    pr.skip = skip;
+    pr.maps = nullptr;
+    const int tiles = pr.num_mt * ((N + BN - 1) / BN);
+    const int pairs = tiles / 2;
+    const int clusters = pairs < max_clusters ? pairs : max_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 2;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, pr,
+                                       (const GemmProblem*)nullptr, 1, tiles, device_error_word());
+    count_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("tcgen05 pair GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
+bool pair_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("CDMPT_PAIR");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 template <int BN, int STAGES, int PASSES, int KCH>
@@ -760,7 +898,13 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     p.lde = ep.lde;
     p.Dhi = ep.Dhi;
     p.Dlo = ep.Dlo;
-    if (!three) return launch<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
+    const bool pair = pair_enabled() && ((M + BM - 1) / BM) % 2 == 0;
+    if (!three) {
+        if (pair) return launch_pair<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
+        return launch<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
+    }
+    if (pair && split_chunk() == 2)
+        return launch_pair<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
     switch (split_chunk()) {
         case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
         case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
