@@ -315,3 +315,154 @@ def entropy_coefficients():
         2: [8 * LN2 - 2, 16 * LN2 - 8],
         4: [16 * LN2 - 34 / 5, 96 * LN2 - 844 / 15, 256 * LN2 - 2336 / 15, 256 * LN2 - 2368 / 15],
     }
+
+
+# ----------------------------------------------------------------------------
+# second order: P2 = (1/2) d^2 P / d lambda^2 (Algorithm 1, order 2, with
+# H^(2) = 0) and the polarizability gradient d alpha / d H0 = -4 P2
+# ----------------------------------------------------------------------------
+
+def occupation_second_derivative(eps, mu, beta, n: Optional[int] = None):
+    """d^2 occupation / d eps^2.
+
+    Fermi-Dirac, x = beta (e - mu)/2, t = tanh x:  (beta^2/4) t (1 - t^2).
+    Recursion (n steps), z = z0(e), T = tanh(2^n atanh z), s = beta / 2^(n+1):
+    2^n s^2 (1 - T^2) (z - 2^n T) / (1 - z^2)^2 (the derivative of
+    -beta/4 (1 - T^2) / (1 - z^2) through the closed form).
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    if n is None:
+        t = np.tanh(0.5 * beta * (eps - mu))
+        return 0.25 * beta * beta * t * (1.0 - t * t)
+    z = z0_of(eps, mu, beta, n)
+    m = 2.0 ** n
+    t = np.tanh(m * np.arctanh(z))
+    s = beta / 2.0 ** (n + 1)
+    return m * s * s * (1.0 - t * t) * (z - m * t) / (1.0 - z * z) ** 2
+
+
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(8)
+_GL_X = 0.5 * (_GL_X + 1.0)
+_GL_W = 0.5 * _GL_W
+
+
+def second_dd_quadrature(a, b, c, mu, beta, n: Optional[int] = None):
+    """f[a, b, c] as the Hermite-Genocchi integral of f'' over the 2-simplex,
+    a + t1 (b - a) + t2 (c - a), t1, t2 >= 0, t1 + t2 <= 1, after the collapse
+    t1 = x, t2 = (1 - x) y (Jacobian 1 - x), with an 8 x 8 Gauss-Legendre rule.
+    Exact to rounding when beta * spread <= 1 (the nearest poles of f lie
+    pi / beta off the real axis)."""
+    a = np.asarray(a, dtype=np.float64)[..., None, None]
+    b = np.asarray(b, dtype=np.float64)[..., None, None]
+    c = np.asarray(c, dtype=np.float64)[..., None, None]
+    x = _GL_X[:, None]
+    y = _GL_X[None, :]
+    pts = a + x * (b - a) + (1.0 - x) * y * (c - a)
+    w = _GL_W[:, None] * _GL_W[None, :] * (1.0 - x)
+    return np.sum(occupation_second_derivative(pts, mu, beta, n) * w, axis=(-2, -1))
+
+
+def _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad):
+    """f[e_i, e_k, e_j] for the pairs (i, j) = (I[p], J[p]) and every k: (len(I), N).
+
+    f[x, y, z] = (f[x, y] - f[y, z]) / (x - z) is taken across the widest of the
+    three pairs; triples whose whole spread is within quad / beta (where that
+    quotient would cancel) use the quadrature instead.
+    """
+    a = eps[I][:, None]
+    c = eps[J][:, None]
+    b = eps[None, :]
+    fac = F[I, J][:, None]                     # f[a, c]
+    fab = F[I, :]                              # f[a, b]
+    fcb = F[J, :]                              # f[c, b]
+    dab = a - b
+    dcb = c - b
+    spread = np.maximum(np.maximum(np.abs(dab), np.abs(dcb)), np.abs(a - c))
+    out = np.empty(dab.shape)
+    use_ab = np.abs(dab) >= np.abs(dcb)        # widest pair (a, b): middle c
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v_ab = (fac - fcb) / dab               # f[a, c, b]
+        v_cb = (fac - fab) / dcb               # f[c, a, b]
+    out[:] = np.where(use_ab, v_ab, v_cb)
+    near = spread * beta <= quad
+    if np.any(near):
+        pi, kk = np.nonzero(near)
+        out[pi, kk] = second_dd_quadrature(eps[I[pi]], eps[kk], eps[J[pi]], mu, beta, n)
+    return out
+
+
+def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
+              close: float = 1.0, quad: float = 1.0, batch: int = 1024):
+    """Second-order canonical response P2 = (1/2) d^2 P / d lambda^2 of P(H0 + lambda H1).
+
+    Second-order Daleckii-Krein formula in the eigenbasis of H0, with
+    ht = h - mu1 I (h = V^T H1 V, mu1 the first-order canonical shift):
+      (P2)_ij = sum_k f[e_i, e_k, e_j] ht_ik ht_kj - mu2 f'_i delta_ij,
+    and mu2 = sum_i (P2)_ii|_{mu2=0} / sum_i f'_i from Tr P2 = 0 (the second-
+    order canonical condition of Algorithm 1). For pairs with beta |e_i - e_j|
+    > close the sum over k is the exact identity
+      [(F o ht) ht - ht (F o ht)]_ij / (e_i - e_j),
+    F the first divided differences; closer pairs are summed explicitly, with
+    the quadrature for triples of spread <= quad / beta.
+    Returns the first-order results of ``solve`` plus P2 (D, N, N), mu2 (D,)
+    and grad_alpha = -4 P2 (d alpha_d / d H0, by the symmetry of the third
+    derivatives of the canonical free energy, whose gradient is P0).
+    """
+    H0 = np.asarray(H0, dtype=np.float64)
+    H1 = np.asarray(H1, dtype=np.float64)
+    if H1.ndim == 2:
+        H1 = H1[None]
+    nn = n if kind == "rec" else None
+    eps, V = np.linalg.eigh(H0) if eig is None else eig
+    base = solve(H0, H1, beta, nocc, n, kind, eig=(eps, V))
+    mu = base["mu"]
+    F = divided_differences(eps, mu, beta, nn)
+    fp = np.diag(F).copy()
+    N = eps.shape[0]
+    diff = eps[:, None] - eps[None, :]
+    ci, cj = np.nonzero(np.abs(diff) * beta <= close)
+    P2 = np.empty_like(H1)
+    mu2 = np.zeros(H1.shape[0])
+    for d in range(H1.shape[0]):
+        ht = V.T @ H1[d] @ V - base["mu1"][d] * np.eye(N)
+        G = F * ht
+        with np.errstate(divide="ignore", invalid="ignore"):
+            S = (G @ ht - ht @ G) / diff
+        for s0 in range(0, ci.shape[0], batch):
+            I = ci[s0:s0 + batch]
+            J = cj[s0:s0 + batch]
+            F3 = _second_dd_for_pairs(I, J, eps, F, mu, beta, nn, quad)
+            S[I, J] = np.sum(F3 * ht[I, :] * ht[:, J].T, axis=1)
+        mu2[d] = float(np.trace(S) / np.sum(fp))
+        P2[d] = V @ (S - mu2[d] * np.diag(fp)) @ V.T
+    out = dict(base)
+    out.update(P2=P2, mu2=mu2, grad_alpha=-4.0 * P2)
+    return out
+
+
+def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M):
+    """The inner loop of Algorithm 1 for orders 0, 1 and 2 (H^(2) = 0), dense solves.
+
+    X_0^(2) = -2^-(M+2) beta (H^(2) - mu2 I) = 2^-(M+2) beta mu2 I, and per step
+    T X^(2) = C^(2) + B^(2) X_n^(0) + B^(1) X_n^(1), with
+    C^(2) = X^(0) X^(2) + X^(1) X^(1) + X^(2) X^(0) and B^(2) = 2 (X^(2) - C^(2)).
+    Returns (X_M^(0), X_M^(1), X_M^(2)).
+    """
+    N = H0.shape[0]
+    I = np.eye(N)
+    s = 2.0 ** (-(M + 2)) * beta
+    X0 = 0.5 * I - s * (H0 - mu * I)
+    X1 = -s * (H1 - mu1 * I)
+    X2 = s * mu2 * I
+    for _ in range(M):
+        T = 2.0 * X0 @ (X0 - I) + I
+        C0 = X0 @ X0
+        C1 = X0 @ X1 + X1 @ X0
+        C2 = X0 @ X2 + X1 @ X1 + X2 @ X0
+        B1 = 2.0 * (X1 - C1)
+        B2 = 2.0 * (X2 - C2)
+        X0n = np.linalg.solve(T, C0)
+        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
+        X2n = np.linalg.solve(T, C2 + B2 @ X0n + B1 @ X1n)
+        X0, X1, X2 = X0n, X1n, X2n
+    return X0, X1, X2

@@ -320,3 +320,118 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(o.dmpt_oracle, "occupation",
                         lambda e, mu, b, n=None: real_occ(e, mu, 0.5 * b, n))
     assert fd_error() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# P2: second-order canonical response (Algorithm 1, order 2) and the
+# polarizability gradient d alpha / d H0 = -4 P2
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_second_derivative_closed_form(kind, n):
+    """f'' against central differences of f' (both kinds)."""
+    e = np.linspace(-3.0, 3.0, 41)
+    mu, beta, h = 0.3, 2.5, 1e-5
+    d2 = o.occupation_second_derivative(e, mu, beta, n)
+    fd = (o.occupation_derivative(e + h, mu, beta, n) -
+          o.occupation_derivative(e - h, mu, beta, n)) / (2 * h)
+    assert np.max(np.abs(d2 - fd)) < 1e-8 * np.max(np.abs(d2))
+
+
+def test_second_divided_difference_quadrature_matches_quotient():
+    """Hermite-Genocchi quadrature == (f[a,b] - f[b,c]) / (a - c) where both are accurate."""
+    rng = np.random.default_rng(4)
+    beta, mu, n = 3.0, 0.1, 10
+    a = rng.uniform(-1, 1, 200)
+    spread = rng.uniform(1.0, 2.0, 200) / beta
+    c = a + spread
+    b = a + rng.uniform(0, 1, 200) * spread
+    q = o.second_dd_quadrature(a, b, c, mu, beta, n)
+    occ = lambda x: o.occupation(x, mu, beta, n)
+    fab = (occ(a) - occ(b)) / (a - b)
+    fbc = (occ(b) - occ(c)) / (b - c)
+    quot = (fab - fbc) / (a - c)
+    assert np.max(np.abs(q - quot)) < 1e-9 * np.max(np.abs(q))
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_p2_equals_finite_difference_of_p1(kind, n):
+    """2 P2 == dP1/dlambda of the canonical P1(H0 + lambda H1) (5-point stencil)."""
+    H0 = _rand_sym(12, 8)
+    H1 = np.diag(np.arange(12) - 5.5) * 0.3
+    beta, nocc, h = 2.0, 6.0, 1e-3
+    r = o.response2(H0, H1, beta, nocc, n=n, kind=kind)
+    P1 = {k: o.solve(H0 + k * h * H1, H1, beta, nocc, n=n, kind=kind)["P1"][0]
+          for k in (-2, -1, 1, 2)}
+    fd = (P1[-2] - 8 * P1[-1] + 8 * P1[1] - P1[2]) / (12 * h)
+    assert o.rel_frobenius(2.0 * r["P2"][0], fd) < 1e-8
+    assert abs(np.trace(r["P2"][0])) < 1e-12 * np.linalg.norm(r["P2"][0])
+    assert np.abs(r["P2"][0] - r["P2"][0].T).max() < 1e-12 * np.abs(r["P2"][0]).max()
+
+
+def test_p2_equals_literal_algorithm1_second_order():
+    """The closed form == Algorithm 1's order-2 recursion (dense solves), chain64, and
+    the oracle's mu2 makes the literal Tr X^(2) vanish (the canonical condition)."""
+    p = syn.workload("chain64")
+    r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    X0, X1, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0],
+                                      r["mu2"][0], p.n)
+    assert o.rel_frobenius(X1, r["P1"][0]) < 1e-10
+    assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
+    assert abs(np.trace(X2)) < 1e-10 * np.linalg.norm(X2)
+
+
+def test_p2_degenerate_clean_lattice():
+    """Exactly degenerate levels (clean periodic lattice): the close-pair path against
+    Algorithm 1's order-2 recursion."""
+    p = syn.cubic_lattice((4, 4, 4), seed=1, beta=6.0, n=12, onsite_sigma=0.0,
+                          bond_disorder=0.0)
+    r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    _, _, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0],
+                                    r["mu2"][0], p.n)
+    assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_alpha_gradient_equals_finite_differences(kind, n):
+    """<grad alpha, E> == d alpha(H0 + t E)/dt (5-point) for random symmetric E."""
+    H0 = _rand_sym(12, 9)
+    H1 = np.diag(np.arange(12) - 5.5) * 0.3
+    beta, nocc, h = 2.0, 6.0, 1e-3
+    g = o.response2(H0, H1, beta, nocc, n=n, kind=kind)["grad_alpha"][0]
+    for seed in range(3):
+        E = _rand_sym(12, 100 + seed)
+        al = {k: o.solve(H0 + k * h * E, H1, beta, nocc, n=n, kind=kind)["alpha"][0]
+              for k in (-2, -1, 1, 2)}
+        fd = (al[-2] - 8 * al[-1] + 8 * al[1] - al[2]) / (12 * h)
+        assert abs(np.sum(g * E) - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_second_order_pins_catch_planted_mistakes(monkeypatch):
+    """Plant slips in the second-order oracle (CPU) and check the pins notice them."""
+    H0 = _rand_sym(12, 8)
+    H1 = np.diag(np.arange(12) - 5.5) * 0.3
+    beta, nocc, h = 2.0, 6.0, 1e-3
+    P1 = {k: o.solve(H0 + k * h * H1, H1, beta, nocc, kind="fd")["P1"][0] for k in (-2, -1, 1, 2)}
+    fd = (P1[-2] - 8 * P1[-1] + 8 * P1[1] - P1[2]) / (12 * h)
+
+    def err(**kw):
+        return o.rel_frobenius(2.0 * o.response2(H0, H1, beta, nocc, kind="fd", **kw)["P2"][0], fd)
+
+    assert err() < 1e-8
+    assert err(close=100.0) < 1e-8          # every pair through the explicit sums
+    real = o.dmpt_oracle.occupation_second_derivative
+    # wrong sign of f'' (seen through the quadrature of clustered triples)
+    monkeypatch.setattr(o.dmpt_oracle, "occupation_second_derivative",
+                        lambda *a, **k: -real(*a, **k))
+    assert err(close=100.0) > 1e-3
+    monkeypatch.setattr(o.dmpt_oracle, "occupation_second_derivative", real)
+    # mu1 left out of the second order (ht = h instead of h - mu1 I)
+    real_solve = o.dmpt_oracle.solve
+
+    def no_mu1(*a, **k):
+        r = real_solve(*a, **k)
+        r["mu1"] = np.zeros_like(r["mu1"])
+        return r
+    monkeypatch.setattr(o.dmpt_oracle, "solve", no_mu1)
+    assert err() > 1e-3
