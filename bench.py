@@ -43,7 +43,7 @@ WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
 # DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
 # profiles/ (per engine); None until the kernel's counters are re-taken after a change
-TRAFFIC = {2: None, 3: None}
+TRAFFIC = {2: 233.8e6, 3: 996.0e6}   # TF32 two-SM, 3xTF32 chunk 2 (profiles/gemm_*_n4096.md)
 
 
 def dist_env():
@@ -324,10 +324,20 @@ def run_ours(args):
             if hm is not h:
                 hm.close()
 
+    if "fp32_3xtf32" in modes and "fp32_ffma" in modes and args.precision in modes:
+        me = modes[args.precision]["solves_per_s"]
+        modes["speedup_vs_fp32_3xtf32"] = me / modes["fp32_3xtf32"]["solves_per_s"]
+        modes["speedup_vs_fp32_ffma"] = me / modes["fp32_ffma"]["solves_per_s"]
+
     # batched workload: 96 disordered clusters, N_b ~ U{128..1536}, 3 directions, beta 20, n 12
     batched = None
     if not args.no_batch:
         batched = run_batched(pkg, args, barrier)
+
+    # the N = 8192 product chain: one mixed solve of the banded workload, per-engine rates
+    chain = None
+    if not args.no_chain:
+        chain = run_chain(pkg, pk)
 
     cpu = None
     err = None
@@ -370,6 +380,7 @@ def run_ours(args):
             "clocks": clk,
             "modes": modes,
             "batched": batched,
+            "chain_n8192": chain,
             "error": err,
             "detail": {
                 "gemm_share_of_step_time": gemm_ms_total / (ms / world) if ms else None,
@@ -390,6 +401,47 @@ def run_ours(args):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def run_chain(pkg, pk):
+    """GEMM chain at N = 8192: one mixed-precision solve of the banded workload (bandwidth 64,
+    beta 20, n 14) with every product timed; achieved rate per engine against the TF32 peak."""
+    import torch
+
+    import synthetic
+    p = synthetic.workload("banded8192")
+    names = {1: "CUDA-core", 2: "tcgen05 TF32", 3: "tcgen05 3xTF32"}
+    peak = pk["bf16_sustained"] * TF32_OVER_BF16
+    with pkg.Handle(precision="mixed", profile=True) as h:
+        h.set_H(p.H0, p.H1)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = h.stats()
+    out = {"workload": "banded N=8192 (bandwidth 64, seed 1004), beta 20, n 14, mixed precision",
+           "solve_s": dt, "engines": {}}
+    tensor_fl = 0.0
+    gemm_s = 0.0
+    for e in (2, 3):
+        n_l = st["engine_launches"][e]
+        if not n_l:
+            continue
+        ms = st["engine_ms"][e]
+        fl = st["engine_flops"][e]
+        ach = fl / (ms / 1e3) / 1e12
+        tensor_fl += fl * (3 if e == 3 else 1)
+        gemm_s += ms / 1e3
+        out["engines"][names[e]] = {"launches": n_l, "ms": ms, "algorithmic_tflops": ach,
+                                    "frac_of_tf32_peak": ach / peak,
+                                    "tensor_pipe_frac": ach * (3 if e == 3 else 1) / peak}
+    out["tensor_pipe_frac_all_products"] = (tensor_fl / gemm_s / 1e12 / peak) if gemm_s else None
+    out["gemm_share_of_solve"] = gemm_s / dt if dt else None
+    out["peak_note"] = (f"tf32 peak = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
+                        f"{TF32_OVER_BF16:.4f}")
+    return out
 
 
 def run_batched(pkg, args, barrier):
@@ -415,7 +467,9 @@ def run_batched(pkg, args, barrier):
     ms = ev0.elapsed_time(ev1)
     st = bt.stats()
     out = {"workload": "96 clusters, N_b ~ U{128..1536} (seed 1005), D = 3, beta 20, n 12, FP32 "
-                       "split-TF32, one grouped tcgen05 launch per product",
+                       "split-TF32, one grouped tcgen05 launch per product, CG iterations as a "
+                       "CUDA graph, tile width from the autotuner",
+           "tuning": bt.tuning(),
            "solves_per_s": 96 / (ms / 1e3), "ms": ms, "sum_N3": float(sum(float(N) ** 3 for N in sizes)),
            "mu_sweeps": st["mu_iterations"], "kernel_launches": st["kernel_launches"],
            "algorithmic_tflops": st["gemm_flops"] / (ms / 1e3) / 1e12}
@@ -453,6 +507,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched 96-cluster measurement")
+    ap.add_argument("--no-chain", action="store_true",
+                    help="skip the N = 8192 product-chain measurement")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the one-step runs of the other precisions")
     args = ap.parse_args()

@@ -62,16 +62,19 @@ typedef enum {
 typedef enum {
     CDMPT_FP64 = 0,       /* FP64 storage, FP64 products (CUDA-core DFMA) */
     CDMPT_FP32 = 1,       /* FP32 storage, FP32-accurate products (3xTF32 on tcgen05 by default) */
-    CDMPT_MIXED_TF32 = 2, /* TF32 products for the occupation sweeps and response,
-                             FP32-accurate residual refinement of the trajectory */
-    CDMPT_MIXED_BF16 = 3  /* reserved: BF16 products + refinement */
+    CDMPT_MIXED_TF32 = 2, /* one-pass TF32 products for the occupation sweeps, split-TF32
+                             (FP32-accurate) residual refinement of the trajectory and
+                             split-TF32 response */
+    CDMPT_MIXED_BF16 = 3  /* as MIXED_TF32 with BF16 products (FP32 accumulation) for the
+                             occupation sweeps */
 } cdmpt_precision;
 
 typedef enum {
     CDMPT_GEMM_AUTO = 0,      /* engine chosen from the precision */
     CDMPT_GEMM_SIMT = 1,      /* CUDA-core FFMA/DFMA tiles */
     CDMPT_GEMM_TC_TF32 = 2,   /* tcgen05 kind::tf32, one pass, FP32 accumulate in TMEM */
-    CDMPT_GEMM_TC_3XTF32 = 3  /* tcgen05 kind::tf32, hi/lo split, three passes */
+    CDMPT_GEMM_TC_3XTF32 = 3, /* tcgen05 kind::tf32, hi/lo split, three passes */
+    CDMPT_GEMM_TC_BF16 = 4    /* tcgen05 kind::f16 on operands rounded to BF16, one pass */
 } cdmpt_gemm_engine;
 
 typedef struct {
@@ -106,9 +109,9 @@ typedef struct {
     double mu, trace_P0, trace_Q;  /* final mu, Tr P0, Tr dP0/dmu */
     double occupation_error;       /* |Tr P0 - N_occ| + sum_d |Tr P1_d| */
     double seconds;                /* host wall time of the last solve */
-    double engine_ms[4];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
-    int engine_launches[4];        /* timed GEMM launches per engine */
-    double engine_flops[4];        /* algorithmic flops of those launches */
+    double engine_ms[5];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
+    int engine_launches[5];        /* timed GEMM launches per engine */
+    double engine_flops[5];        /* algorithmic flops of those launches */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -169,6 +172,25 @@ cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
  * successful cdmpt_solve on this handle (its trajectory is reused).
  * Errors: ERR_ARG (no solve yet, NULL pointers), ERR_CG_MAXITER, ERR_CUDA. */
 cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int on_device);
+
+/* Second-order canonical response of the last solve, per direction d of H1:
+ * P2_d = (1/2) d^2 P / d lambda_d^2 of P(H0 + lambda_d H1_d) (Algorithm 1, the
+ * order-2 line, with H^(2) = 0), with the second-order chemical-potential
+ * shift mu2_d fixed by Tr P2_d = 0 (the canonical condition of Algorithm 1).
+ * Also the gradient of L = sum_d w_d alpha_d, alpha_d = -2 Tr(P1_d H1_d), with
+ * respect to H0: dL/dH0 = -4 sum_d w_d P2_d. This follows from the symmetry of
+ * the third derivatives of the canonical free energy, whose H0-gradient is P0
+ * (App. B), and holds exactly for the recursion's own occupation function.
+ * w: host array of D weights, or NULL for all ones.
+ * P2: D x N x N (row-major FP64), may be NULL. mu2: host array of D doubles,
+ * may be NULL. gradH0: N x N, may be NULL. P2 and gradH0 are host or device
+ * memory per on_device. The call reruns the first order with the known mu1,
+ * storing its trajectory, then the order-2 recursion (four products and one
+ * CG solve per step and direction) in the precision of the solve.
+ * Errors: ERR_ARG (no solve yet, no directions), ERR_CG_MAXITER,
+ * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
+                             double* gradH0, int on_device);
 
 /* Spectral interval of a symmetric matrix from Gershgorin discs:
  * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).
@@ -240,6 +262,16 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
 
 /* Statistics of the last batch solve (N holds B). */
 cdmpt_status cdmpt_batch_get_stats(const cdmpt_batch* b, cdmpt_stats* st);
+
+/* Tile autotuner and graph report of a batch. tile_n: the grouped kernel's
+ * tile width chosen by timing each candidate (128 and 64 columns, the same
+ * accumulation and so the same rounding) on the batch's first product over all
+ * systems; 0 before the first solve. ms[0], ms[1]: the measured time per
+ * launch of the 128- and 64-column candidates (0 if not timed). graphs: 1 when
+ * the CG iterations replay a captured CUDA graph (CDMPT_BATCH_GRAPH=0 turns
+ * capture off; CDMPT_BATCH_TILE=64|128 fixes the tile width). Any pointer may
+ * be NULL. Errors: ERR_ARG (b NULL). */
+cdmpt_status cdmpt_batch_get_tuning(const cdmpt_batch* b, int* tile_n, double* ms, int* graphs);
 
 /* Last error of the batch ("" if none). */
 const char* cdmpt_batch_last_error(const cdmpt_batch* b);

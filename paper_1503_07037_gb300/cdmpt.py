@@ -17,10 +17,11 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcdmpt.so")
 
 FP64, FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
-GEMM_AUTO, GEMM_SIMT, GEMM_TC_TF32, GEMM_TC_3XTF32 = 0, 1, 2, 3
+GEMM_AUTO, GEMM_SIMT, GEMM_TC_TF32, GEMM_TC_3XTF32, GEMM_TC_BF16 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_TF32, "mixed_tf32": MIXED_TF32,
               "mixed_bf16": MIXED_BF16}
-ENGINES = {"auto": GEMM_AUTO, "simt": GEMM_SIMT, "tf32": GEMM_TC_TF32, "3xtf32": GEMM_TC_3XTF32}
+ENGINES = {"auto": GEMM_AUTO, "simt": GEMM_SIMT, "tf32": GEMM_TC_TF32, "3xtf32": GEMM_TC_3XTF32,
+           "bf16": GEMM_TC_BF16}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_RANGE", 3: "ERR_NO_CONVERGENCE", 4: "ERR_CG_MAXITER",
           5: "ERR_TIMEOUT", 6: "ERR_CUDA", 7: "ERR_OOM", 8: "ERR_UNSUPPORTED"}
 
@@ -65,9 +66,9 @@ class Stats(ctypes.Structure):
         ("mu", ctypes.c_double), ("trace_P0", ctypes.c_double), ("trace_Q", ctypes.c_double),
         ("occupation_error", ctypes.c_double),
         ("seconds", ctypes.c_double),
-        ("engine_ms", ctypes.c_double * 4),
-        ("engine_launches", ctypes.c_int * 4),
-        ("engine_flops", ctypes.c_double * 4),
+        ("engine_ms", ctypes.c_double * 5),
+        ("engine_launches", ctypes.c_int * 5),
+        ("engine_flops", ctypes.c_double * 5),
     ]
 
     def as_dict(self):
@@ -85,7 +86,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_spectral_bounds_noalloc", "cdmpt_vjp_P0", "cdmpt_batch_create",
            "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
-           "cdmpt_gemm_f32_split"]
+           "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning"]
 
 
 def lib() -> ctypes.CDLL:
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
         "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
         "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
+        "cdmpt_response2": (I, [P, P, P, P, P, I]),
+        "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
         "cdmpt_batch_solve": (I, [P, P, P, I, P, P, P, P, P, I]),
@@ -354,6 +357,23 @@ class Handle:
         _check(lib().cdmpt_vjp_P0(self.h, _ptr(G), _ptr(out), 1 if G.is_cuda else 0), self.h)
         return out
 
+    def response2(self, weights=None, want_P2=True, want_grad=True, device="cuda"):
+        """Second-order canonical response of the last solve: dict(P2 (D, N, N), mu2 (D,),
+        grad) with grad = d(sum_d w_d alpha_d)/dH0 = -4 sum_d w_d P2_d (float64 tensors)."""
+        import torch
+        N, D = self.N, self.D
+        dev = torch.device(device)
+        on_dev = 1 if dev.type == "cuda" else 0
+        P2 = torch.empty((D, N, N), dtype=torch.float64, device=dev) if want_P2 else None
+        G = torch.empty((N, N), dtype=torch.float64, device=dev) if want_grad else None
+        w = None
+        if weights is not None:
+            w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), (D,)))
+        mu2 = np.zeros(max(D, 1))
+        _check(lib().cdmpt_response2(self.h, None if w is None else w.ctypes.data, _ptr(P2),
+                                     mu2.ctypes.data, _ptr(G), on_dev), self.h)
+        return {"P2": P2, "mu2": mu2[:D].copy(), "grad": G}
+
     def stats(self):
         return get_stats(self.h)
 
@@ -434,6 +454,16 @@ class Batch:
         return {"P0": P0, "P1": P1, "mu": mu, "mu1": mu1[:B * D].reshape(B, D),
                 "alpha": al[:B * D].reshape(B, D)}
 
+    def tuning(self):
+        """The tile autotuner's choice and timings, and whether CG iterations replay a graph."""
+        tn = ctypes.c_int(0)
+        ms = np.zeros(2)
+        gr = ctypes.c_int(0)
+        self._check(lib().cdmpt_batch_get_tuning(self.h, ctypes.addressof(tn), ms.ctypes.data,
+                                                 ctypes.addressof(gr)))
+        return {"tile_n": tn.value, "ms_128": float(ms[0]), "ms_64": float(ms[1]),
+                "graphs": bool(gr.value)}
+
     def stats(self):
         s = Stats()
         self._check(lib().cdmpt_batch_get_stats(self.h, ctypes.byref(s)))
@@ -475,6 +505,36 @@ class DensityMatrix:
             @staticmethod
             def backward(ctx, G):
                 return handle.vjp_P0(G)
+
+        return _Fn.apply(H0)
+
+
+class Polarizability:
+    """Differentiable canonical polarizabilities alpha_d(H0) = -2 Tr(P1_d H1_d) (torch.autograd).
+
+    alpha = Polarizability.apply(H0, H1, beta, nocc, n, handle) returns the (D,)
+    tensor of alpha_d for the symmetric CUDA float64 tensor H0 and fixed
+    perturbations H1 (D, N, N); backward gives dL/dH0 = sum_d (dL/dalpha_d)
+    (-4 P2_d) through the second-order response (cdmpt_response2). Call
+    backward before the next solve on the same handle.
+    """
+
+    @staticmethod
+    def apply(H0, H1, beta, nocc, n, handle):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, H):
+                handle.set_H(H.detach(), H1)
+                handle.solve(beta, nocc, n, want_P0=False, want_P1=False)
+                return torch.as_tensor(handle.polarizability(), dtype=torch.float64,
+                                       device=H.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                w = g.detach().to(torch.float64).cpu().numpy()
+                return handle.response2(weights=w, want_P2=False, device=g.device.type)["grad"]
 
         return _Fn.apply(H0)
 

@@ -90,7 +90,7 @@ cdmpt_status fail_msg(cdmpt_handle* h, cdmpt_status s, const std::string& m) {
 
 bool valid_opts(const cdmpt_opts* o) {
     if (o->precision < CDMPT_FP64 || o->precision > CDMPT_MIXED_BF16) return false;
-    if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_3XTF32) return false;
+    if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_BF16) return false;
     if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
     return true;
 }
@@ -125,8 +125,6 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
 cdmpt_status cdmpt_set_opts(cdmpt_handle* h, const cdmpt_opts* opts) {
     if (!h || !opts) return CDMPT_ERR_ARG;
     if (!valid_opts(opts)) return fail_msg(h, CDMPT_ERR_ARG, "invalid options");
-    if (opts->precision == CDMPT_MIXED_BF16)
-        return fail_msg(h, CDMPT_ERR_UNSUPPORTED, "MIXED_BF16 is not available");
     const bool needs_tc =
         opts->precision != CDMPT_FP64 &&
         (opts->gemm_engine == CDMPT_GEMM_AUTO || opts->gemm_engine >= CDMPT_GEMM_TC_TF32);
@@ -261,7 +259,8 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
             if (cudaEventElapsedTime(&e, h->cx.ev[2 * i], h->cx.ev[2 * i + 1]) == cudaSuccess) {
                 ms += e;
                 ++timed;
-                const int eng = h->cx.ev_engine[i] & 3;
+                const int eng = h->cx.ev_engine[i];
+                if (eng < 0 || eng > 4) continue;
                 h->st.engine_ms[eng] += e;
                 h->st.engine_launches[eng] += 1;
                 h->st.engine_flops[eng] += h->cx.ev_flops[i];
@@ -324,6 +323,49 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
     return CDMPT_OK;
 }
 
+cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
+                             double* gradH0, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "response2: no completed solve on this handle");
+    if (h->D < 1)
+        return fail_msg(h, CDMPT_ERR_ARG, "response2: the handle has no perturbation directions");
+    cudaStream_t s = h->cx.stream;
+    const int D = h->D;
+    const size_t nn = (size_t)h->N * h->N;
+    double* p2 = P2;
+    double* g = gradH0;
+    double* tmp = nullptr;
+    if (!on_device && (P2 || gradH0)) {
+        const size_t elems = (P2 ? (size_t)D * nn : 0) + (gradH0 ? nn : 0);
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, elems * sizeof(double), s));
+        p2 = P2 ? tmp : nullptr;
+        g = gradH0 ? tmp + (P2 ? (size_t)D * nn : 0) : nullptr;
+    }
+    std::vector<double> m2(D, 0.0);
+    cdmpt_stats keep = h->st;
+    h->cx.st = &h->st;
+    cdmpt_status st;
+    if (h->opts.precision == CDMPT_FP64)
+        st = h->sd ? h->sd->response2(h->cx, h->H1, D, w, p2, m2.data(), g) : CDMPT_ERR_ARG;
+    else
+        st = h->sf ? h->sf->response2(h->cx, h->H1, D, w, p2, m2.data(), g) : CDMPT_ERR_ARG;
+    h->st = keep;
+    if (st == CDMPT_OK && !on_device) {
+        if (P2)
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(P2, p2, (size_t)D * nn * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s));
+        if (gradH0)
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, g, nn * sizeof(double), cudaMemcpyDeviceToHost,
+                                           s));
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st != CDMPT_OK) return fail(h, st);
+    if (mu2)
+        for (int d = 0; d < D; ++d) mu2[d] = m2[d];
+    return CDMPT_OK;
+}
+
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha) {
     if (!h || !alpha) return CDMPT_ERR_ARG;
     if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "polarizability: no completed solve");
@@ -381,6 +423,12 @@ cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X,
     cudaStream_t s = (cudaStream_t)stream;
     if (engine == CDMPT_GEMM_SIMT) return gemm_simt<float>(M, Ncols, K, X, ldx, Y, ldy, D, ldd, ep,
                                                            nullptr, s);
+    if (engine == CDMPT_GEMM_TC_BF16) {
+        Operand<float> ox, oy;
+        ox.x = X;
+        oy.x = Y;
+        return gemm_tc_f32(engine, M, Ncols, K, ox, ldx, oy, ldy, D, ldd, ep, nullptr, s);
+    }
     if (engine != CDMPT_GEMM_AUTO && engine != CDMPT_GEMM_TC_TF32 && engine != CDMPT_GEMM_TC_3XTF32) {
         set_error("gemm_f32: unknown engine");
         return CDMPT_ERR_ARG;

@@ -8,6 +8,14 @@
 // potential on the device; a converged system is skipped through its flag
 // (its GEMM tiles and elementwise blocks return at once). Storage is FP32 with
 // split-TF32 (3xTF32) products, as in the single-system FP32 mode.
+//
+// Tile autotuner: before the first product of a batch, each candidate tile
+// width of the grouped kernel (128 and 64 columns, same accumulation chunk, so
+// the same rounding) is timed on that product over all systems, which is
+// idempotent (W_0 = Z_0 Z_0 and its split), and the fastest is kept for the
+// batch's lifetime. CUDA graph: one CG iteration over all systems (grouped
+// product, update, direction, scalar step) is captured once per launch shape
+// from dedicated descriptor arrays and replayed for every iteration.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -15,6 +23,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <new>
 #include <string>
@@ -78,6 +87,17 @@ struct cdmpt_batch {
     char* stage_dev = nullptr;
     size_t stage_slot = 0, stage_slots = 0, slot_bytes = 0;
     double* pinned = nullptr;     // scalar readback, B x kSlots
+    // tile autotuner: chosen tile width (0 = not tuned yet) and the timings
+    int tile_bn = 0;
+    double tune_ms[2] = {0.0, 0.0};   // per launch, tile widths 128 and 64
+    // CUDA graph of one CG iteration: dedicated descriptors, graphs by shape
+    GemmProblem* it_gemm = nullptr;   // B problems
+    GrpEw* it_ew = nullptr;           // 3 B: update, direction, scalar step
+    std::map<std::pair<int, long long>, cudaGraphExec_t> it_graphs;
+    bool graphs = true;
+    // capture runs on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); replays go to the caller's stream
+    cudaStream_t cap_stream = nullptr;
     Context cx;                   // stream, profile events, statistics hookup
     cdmpt_stats st;
     std::string err;
@@ -155,10 +175,11 @@ cdmpt_status quad_of(cdmpt_batch* b, const Mat* X, int rows, const Mat* Y, int N
         return CDMPT_ERR_OOM;
     }
     CUtensorMap m[4];
-    if (!tc_encode_operand(&m[0], X->hi, rows, N, ld, false, kEngine) ||
-        !tc_encode_operand(&m[1], Y->hi, N, N, ld, true, kEngine) ||
-        !tc_encode_operand(&m[2], X->lo, rows, N, ld, false, kEngine) ||
-        !tc_encode_operand(&m[3], Y->lo, N, N, ld, true, kEngine)) {
+    const int bn = b->tile_bn;
+    if (!tc_encode_operand(&m[0], X->hi, rows, N, ld, false, kEngine, bn) ||
+        !tc_encode_operand(&m[1], Y->hi, N, N, ld, true, kEngine, bn) ||
+        !tc_encode_operand(&m[2], X->lo, rows, N, ld, false, kEngine, bn) ||
+        !tc_encode_operand(&m[3], Y->lo, N, N, ld, true, kEngine, bn)) {
         set_error("batch: tensor map encoding failed");
         return CDMPT_ERR_ARG;
     }
@@ -216,12 +237,14 @@ EpiParams<float> epi(float* D, int M, int N, int ld, float alpha = 1.f, float be
     return p;
 }
 
-cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
-    std::vector<GemmProblem> probs;
+// Problem descriptors of one grouped product (tensor maps resolved and uploaded).
+cdmpt_status prepare_grouped(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
+                             std::vector<GemmProblem>* probs, int* tiles_out) {
     std::vector<int> quad;
-    probs.reserve(specs.size());
+    probs->clear();
+    probs->reserve(specs.size());
     int tiles = 0;
-    const int bm = tc_tile_m(), bn = tc_tile_n(kEngine);
+    const int bm = tc_tile_m(), bn = b->tile_bn > 0 ? b->tile_bn : tc_tile_n(kEngine);
     for (const GemmSpec& g : specs) {
         const int N = g.p.N;
         int q = 0;
@@ -233,17 +256,120 @@ cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
         pr.num_mt = (g.p.M + bm - 1) / bm;
         pr.skip = g.skip;
         pr.maps = nullptr;
-        probs.push_back(pr);
+        probs->push_back(pr);
         quad.push_back(q);
         tiles += pr.num_mt * ((N + bn - 1) / bn);
     }
-    if (probs.empty()) return CDMPT_OK;
     CDMPT_TRY(flush_maps(b));
-    for (size_t i = 0; i < probs.size(); ++i) probs[i].maps = b->maps_dev + quad[i];
+    for (size_t i = 0; i < probs->size(); ++i) (*probs)[i].maps = b->maps_dev + quad[i];
+    *tiles_out = tiles;
+    return CDMPT_OK;
+}
+
+cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
+    std::vector<GemmProblem> probs;
+    int tiles = 0;
+    CDMPT_TRY(prepare_grouped(b, specs, &probs, &tiles));
+    if (probs.empty()) return CDMPT_OK;
     const GemmProblem* dev = nullptr;
     CDMPT_TRY(stage(b, probs, &dev));
     if (b->cx.st) b->cx.st->gemm_launches += 1;
-    return gemm_tc_grouped(kEngine, dev, (int)probs.size(), tiles, b->cx.stream);
+    return gemm_tc_grouped(kEngine, dev, (int)probs.size(), tiles, b->cx.stream, b->tile_bn);
+}
+
+void clear_maps(cdmpt_batch* b) {
+    b->map_index.clear();
+    b->maps_host.clear();
+    b->maps_uploaded = 0;
+}
+
+// Times each candidate tile width on one grouped product (which must be
+// idempotent) and keeps the fastest. CDMPT_BATCH_TILE=64|128 fixes the choice.
+cdmpt_status tune_tiles(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
+    const char* env = getenv("CDMPT_BATCH_TILE");
+    if (env && (atoi(env) == 64 || atoi(env) == 128)) {
+        clear_maps(b);
+        b->tile_bn = atoi(env);
+        return CDMPT_OK;
+    }
+    const int cand[2] = {128, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CDMPT_CUDA_TRY(cudaEventCreate(&e0));
+    CDMPT_CUDA_TRY(cudaEventCreate(&e1));
+    cdmpt_stats* keep = b->cx.st;
+    b->cx.st = nullptr;   // tuning launches are not part of the solve's statistics
+    int best = 128;
+    double best_ms = 1e300;
+    cdmpt_status st = CDMPT_OK;
+    for (int c = 0; c < 2 && st == CDMPT_OK; ++c) {
+        clear_maps(b);
+        b->tile_bn = cand[c];
+        st = grouped_gemm(b, specs);   // warm-up (kernel attributes, maps)
+        if (st != CDMPT_OK) break;
+        cudaEventRecord(e0, b->cx.stream);
+        for (int r = 0; r < 3 && st == CDMPT_OK; ++r) st = grouped_gemm(b, specs);
+        cudaEventRecord(e1, b->cx.stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = CDMPT_ERR_CUDA;
+        float ms = 0.f;
+        if (st == CDMPT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            b->tune_ms[c] = ms / 3.0;
+            if (ms / 3.0 < best_ms) {
+                best_ms = ms / 3.0;
+                best = cand[c];
+            }
+        }
+    }
+    b->cx.st = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    clear_maps(b);
+    b->tile_bn = best;
+    if (st == CDMPT_OK) st = check_device_error(b->cx.stream);
+    return st;
+}
+
+// Graph of one CG iteration over all systems for this launch shape (tiles of
+// the grouped product, elements of the largest system's block); null when
+// capture is unavailable (the caller then launches the kernels one by one).
+cudaGraphExec_t iteration_graph(cdmpt_batch* b, int tiles, long long maxc) {
+    const auto key = std::make_pair(tiles, maxc);
+    auto it = b->it_graphs.find(key);
+    if (it != b->it_graphs.end()) return it->second;
+    if (!b->cap_stream &&
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        b->graphs = false;
+        return nullptr;
+    }
+    cudaStream_t s = b->cap_stream;
+    const int G = b->B;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        b->graphs = false;
+        return nullptr;
+    }
+    cdmpt_status st = gemm_tc_grouped(kEngine, b->it_gemm, G, tiles, s, b->tile_bn);
+    if (st == CDMPT_OK) st = grouped_ew(G_CG_UPDATE, b->it_ew, G, maxc, s);
+    if (st == CDMPT_OK) st = grouped_ew(G_CG_DIR, b->it_ew + G, G, maxc, s);
+    if (st == CDMPT_OK) st = grouped_cg_step(b->it_ew + 2 * G, G, s);
+    count_launch(-4);   // captured, not run: replays are counted instead
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (st == CDMPT_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != CDMPT_OK || e != cudaSuccess || !exec) {
+        cudaGetLastError();
+        b->graphs = false;
+        return nullptr;
+    }
+    b->it_graphs[key] = exec;
+    return exec;
+}
+
+void drop_graphs(cdmpt_batch* b) {
+    for (auto& kv : b->it_graphs) cudaGraphExecDestroy(kv.second);
+    b->it_graphs.clear();
 }
 
 }  // namespace
@@ -422,9 +548,32 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
         st.sc = sy.sc;
         ds.push_back(st);
     }
+    // the iteration as a CUDA graph: descriptors into the dedicated arrays
+    cudaGraphExec_t graph = nullptr;
+    if (b->graphs) {
+        std::vector<GemmProblem> probs;
+        int tiles = 0;
+        CDMPT_TRY(prepare_grouped(b, gi, &probs, &tiles));
+        long long maxc = 0;
+        for (const GrpEw& e : du) maxc = std::max(maxc, (long long)e.rows * e.ld);
+        std::vector<GrpEw> ew(du);
+        ew.insert(ew.end(), dd.begin(), dd.end());
+        ew.insert(ew.end(), ds.begin(), ds.end());
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(b->it_gemm, probs.data(), probs.size() * sizeof(GemmProblem),
+                                       cudaMemcpyHostToDevice, b->cx.stream));
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(b->it_ew, ew.data(), ew.size() * sizeof(GrpEw),
+                                       cudaMemcpyHostToDevice, b->cx.stream));
+        graph = iteration_graph(b, tiles, maxc);
+    }
     int chunk = std::max(1, hint), done_iters = 0;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
+            if (graph) {
+                CDMPT_CUDA_TRY(cudaGraphLaunch(graph, b->cx.stream));
+                count_launch(4);
+                if (b->cx.st) b->cx.st->gemm_launches += 1;
+                continue;
+            }
             CDMPT_TRY(grouped_gemm(b, gi));
             CDMPT_TRY(run_ew(b, G_CG_UPDATE, du));
             CDMPT_TRY(run_ew(b, G_CG_DIR, dd));
@@ -513,6 +662,7 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
             y.skip = skip[i];
             dsym.push_back(y);
         }
+        if (b->tile_bn == 0) CDMPT_TRY(tune_tiles(b, gw));   // first product of the batch
         CDMPT_TRY(grouped_gemm(b, gw));
         CDMPT_TRY(grouped_gemm(b, gr));
         for (int i = 0; i < G; ++i)
@@ -531,6 +681,7 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
 
 cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
     if (b->n_alloc >= n) return CDMPT_OK;
+    drop_graphs(b);
     for (void* p : b->allocs) cudaFree(p);
     b->allocs.clear();
     b->map_index.clear();
@@ -542,6 +693,8 @@ cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
     CDMPT_TRY(grab(b, (size_t)B * sizeof(double), (void**)&b->inactive));
     b->maps_cap = B * (8 * n + 16) * 4;
     CDMPT_TRY(grab(b, (size_t)b->maps_cap * sizeof(CUtensorMap), (void**)&b->maps_dev));
+    CDMPT_TRY(grab(b, (size_t)B * sizeof(GemmProblem), (void**)&b->it_gemm));
+    CDMPT_TRY(grab(b, (size_t)3 * B * sizeof(GrpEw), (void**)&b->it_ew));
     b->maps_host.reserve(b->maps_cap);
     for (int i = 0; i < B; ++i) {
         Sys& sy = b->sys[i];
@@ -597,6 +750,10 @@ cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int
         return CDMPT_ERR_UNSUPPORTED;
     }
     std::memset(&b->st, 0, sizeof(b->st));
+    {
+        const char* g = getenv("CDMPT_BATCH_GRAPH");
+        b->graphs = !(g && g[0] == '0');
+    }
     b->B = B;
     b->D = D;
     b->sys.resize(B);
@@ -967,8 +1124,21 @@ const char* cdmpt_batch_last_error(const cdmpt_batch* b) {
     return b->err.c_str();
 }
 
+cdmpt_status cdmpt_batch_get_tuning(const cdmpt_batch* b, int* tile_n, double* ms, int* graphs) {
+    if (!b) return CDMPT_ERR_ARG;
+    if (tile_n) *tile_n = b->tile_bn;
+    if (ms) {
+        ms[0] = b->tune_ms[0];
+        ms[1] = b->tune_ms[1];
+    }
+    if (graphs) *graphs = (b->graphs && !b->it_graphs.empty()) ? 1 : 0;
+    return CDMPT_OK;
+}
+
 void cdmpt_batch_destroy(cdmpt_batch* b) {
     if (!b) return;
+    drop_graphs(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (void* p : b->allocs) cudaFree(p);
     if (b->stage_host) cudaFreeHost(b->stage_host);
     if (b->stage_dev) cudaFree(b->stage_dev);

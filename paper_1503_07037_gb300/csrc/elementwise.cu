@@ -283,6 +283,22 @@ __global__ void k_split(const float* __restrict__ X, size_t nvec, float* __restr
     }
 }
 
+// BF16 copy (round to nearest even) of a contiguous array, four elements per
+// thread; returns at once while *skip != 0.
+__global__ void k_to_bf16(const float* __restrict__ X, size_t nvec, uint2* __restrict__ out,
+                          const double* skip) {
+    if (skip && *skip != 0.0) return;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec;
+         v += (size_t)gridDim.x * blockDim.x) {
+        float x[4];
+        load16(X + v * 4, x);
+        uint32_t lo, hi;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x[1]), "f"(x[0]));
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x[3]), "f"(x[2]));
+        out[v] = make_uint2(lo, hi);
+    }
+}
+
 // A[b N + i][i] += s for every block b (diagonal shift of a stack).
 template <typename T>
 __global__ void k_add_diag(T* __restrict__ A, int N, int ld, size_t rows, double s,
@@ -611,6 +627,15 @@ cdmpt_status Ew<T>::add_diag(T* A, int N, int ld, int blocks, double shift, cuda
                              T* lo) {
     const size_t rows = (size_t)blocks * N;
     k_add_diag<T><<<grid_for(rows), kThreads, 0, s>>>(A, N, ld, rows, shift, hi, lo);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+cdmpt_status to_bf16(const float* x, size_t count, void* out, const double* skip,
+                     cudaStream_t s) {
+    const size_t nvec = count / 4;
+    if (!nvec) return CDMPT_OK;
+    k_to_bf16<<<grid_for(nvec), kThreads, 0, s>>>(x, nvec, (uint2*)out, skip);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }

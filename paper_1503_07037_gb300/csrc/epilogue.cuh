@@ -63,4 +63,58 @@ __device__ __forceinline__ T epi_apply(const EpiParams<T>& p, int m, int n, T ac
     return T(0);
 }
 
+// True when four consecutive columns of a row can be handled with 16-byte
+// accesses: no transposed placement, leading dimensions multiples of 4 and
+// 16-byte aligned arrays.
+__device__ __forceinline__ bool epi_vec4_ok(const EpiParams<float>& p) {
+    const int lds = p.ldd | (p.C ? p.ldc : 0) | (p.E ? p.lde : 0);
+    const uintptr_t a = (uintptr_t)p.D | (uintptr_t)p.C | (uintptr_t)p.E | (uintptr_t)p.Dhi |
+                        (uintptr_t)p.Dlo;
+    return p.trans_block <= 0 && (lds & 3) == 0 && (a & 15) == 0;
+}
+
+// epi_apply for columns n .. n + 3 of row m (n % 4 == 0, n + 3 < N, and
+// epi_vec4_ok); returns the D * E contribution of the four elements.
+__device__ __forceinline__ float epi_apply4(const EpiParams<float>& p, int m, int n, float a0,
+                                            float a1, float a2, float a3) {
+    float v[4] = {p.alpha * a0, p.alpha * a1, p.alpha * a2, p.alpha * a3};
+    if (p.beta != 0.f) {
+        const float4 c = *(const float4*)(p.C + (size_t)m * p.ldc + n);
+        v[0] = fmaf(p.beta, c.x, v[0]);
+        v[1] = fmaf(p.beta, c.y, v[1]);
+        v[2] = fmaf(p.beta, c.z, v[2]);
+        v[3] = fmaf(p.beta, c.w, v[3]);
+    }
+    if (p.gamma != 0.f) {
+        const int d = (m % p.diag_block) - n;
+        v[0] += d == 0 ? p.gamma : 0.f;
+        v[1] += d == 1 ? p.gamma : 0.f;
+        v[2] += d == 2 ? p.gamma : 0.f;
+        v[3] += d == 3 ? p.gamma : 0.f;
+    }
+    const size_t o = (size_t)m * p.ldd + n;
+    *(float4*)(p.D + o) = make_float4(v[0], v[1], v[2], v[3]);
+    if (p.Dhi) {
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t hb, lb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v[i]));
+            h[i] = __uint_as_float(hb);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v[i] - h[i]));
+            l[i] = __uint_as_float(lb);
+        }
+        *(float4*)(p.Dhi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *(float4*)(p.Dlo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+    if (p.dot) {
+        if (p.E) {
+            const float4 e = *(const float4*)(p.E + (size_t)m * p.lde + n);
+            return v[0] * e.x + v[1] * e.y + v[2] * e.z + v[3] * e.w;
+        }
+        return v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    }
+    return 0.f;
+}
+
 }  // namespace cdmpt

@@ -18,9 +18,9 @@ struct GemmProblem {
 };
 
 // Tensor map of an FP32 operand (rows x cols, leading dimension ld) as the X
-// (box 128 rows) or the Y operand (box of the engine's tile width) of the
-// tcgen05 kernel. Returns false if the driver rejects it (alignment).
+// (box 128 rows) or the Y operand (box of bn rows, 0 = the engine's tile
+// width) of the tcgen05 kernel. Returns false if the driver rejects it.
 bool tc_encode_operand(CUtensorMap* map, const float* base, int rows, int cols, int ld,
-                       bool as_y, int engine);
+                       bool as_y, int engine, int bn = 0);
 
 }  // namespace cdmpt

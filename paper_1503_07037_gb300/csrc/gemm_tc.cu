@@ -18,6 +18,9 @@
 // loads the hi and lo tiles of both operands, so the MMA forms
 // lo*hi + hi*lo + hi*hi (Ootomo & Yokota's split-TF32 scheme) with FP32
 // accumulation in TMEM, restarted every KCH k-blocks and summed in registers.
+// The finished sums of a tile are parked in a TMEM sum buffer and stored four
+// columns at a time between the chunk drains of the next tile (tc_deferred.cuh),
+// so the global stores overlap the MMAs.
 //
 // Every mbarrier wait is bounded (about 2 s of %globaltimer). On timeout a
 // thread records the error, raises a shared abort flag that ends the other
@@ -35,15 +38,15 @@
 #include "epilogue.cuh"
 #include "gemm_problem.cuh"
 #include "internal.cuh"
+#include "tc_deferred.cuh"
+#include "tc_ptx.cuh"
 
 namespace cdmpt {
 
 namespace {
 
-constexpr int BM = 128;
-constexpr int BK = 32;        // FP32 elements per 128-byte swizzle row
-constexpr int UMMA_K = 8;     // K of one kind::tf32 instruction
-constexpr unsigned long long kWaitNs = 2000000000ull;
+using namespace tc;
+
 // k-blocks (of 32) accumulated in TMEM before the partial sum moves to registers
 // in the 3xTF32 engine. The tensor-core FP32 accumulation is not round-to-
 // nearest; short chunks keep its bias at the level of FP32 rounding. The
@@ -76,209 +79,6 @@ struct Cfg {
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
-
-// ---------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true when the phase of the given parity completed; false when
-// the abort flag is raised or the time limit passed (then the flag is raised
-// and the error recorded).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          volatile int* abort_flag, int* err, int code) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
-            *abort_flag = 1;
-            if (err) atomicCAS(err, 0, code);
-            return false;
-        }
-    }
-}
-
-// Bounded wait that ignores the abort flag (used while draining).
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitNs / 4) return;
-    }
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of both CTAs of a cluster pair.
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
-                     "memory");
-}
-
-// TMA load of one box into the same shared-memory offset of every CTA in
-// mask, each CTA's mbarrier at the same offset receiving the transaction bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
-                                               uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// Orders the tensormap proxy after the generic writes (a host copy) that put a
-// tensor map into global memory, before TMA first reads it.
-__device__ __forceinline__ void acquire_map(const CUtensorMap* map) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-}
-
-__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t cols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(holder)),
-                 "r"(cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
-// rows of 128 bytes, 8-row core groups 1024 bytes apart (stride byte offset),
-// descriptor version 1 at bits 46-47, swizzle mode 2 (128 B) at bits 61-63.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
-// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
-template <int BN>
-__device__ __forceinline__ constexpr uint32_t idesc_tf32() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
-// Arrives on the mbarrier at the same offset in every CTA of mask once this
-// thread's prior tcgen05 operations complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t rna_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
 
 // ---------------------------------------------------------------- kernel
 
@@ -347,9 +147,12 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* tfull = empty + STAGES;   // [2]
-    uint64_t* tempty = tfull + 2;       // [2]
-    uint64_t* drain = tempty + 2;       // [1]
+    // TMEM accumulators: two, or three for the chunked engine (the MMA may then
+    // run two chunks ahead of the epilogue)
+    constexpr int NB = KCH > 0 ? 3 : 2;
+    uint64_t* tfull = empty + STAGES;   // [NB]
+    uint64_t* tempty = tfull + 3;       // [NB]
+    uint64_t* drain = tempty + 3;       // [1]
     uint32_t* tmem_holder = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
@@ -382,7 +185,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], PAIR ? 2 : 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NB; ++a) {
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], 128);
         }
@@ -391,7 +194,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         fence_barrier_init();
         fence_proxy_async();
     }
-    if (warp == 1) tmem_alloc(tmem_holder, C::TMEM_COLS);
+    // chunked engine: three chunk accumulators and a sum buffer (power-of-two allocation)
+    constexpr uint32_t kTmemCols = KCH > 0 ? 4 * BN : C::TMEM_COLS;
+    static_assert(kTmemCols <= 512, "TMEM columns");
+    if (warp == 1) tmem_alloc(tmem_holder, kTmemCols);
     tc_fence_before();
     __syncthreads();
     if constexpr (PAIR) cluster_sync();   // peer barriers initialised before any multicast
@@ -462,7 +268,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32<BN>();
+            constexpr uint32_t idesc = idesc_tf32<BM, BN>();
             uint32_t it = 0, g = 0;
             bool ok = true, issued = false;
             for (int t = t_first; t < total_tiles && ok; t += t_step) {
@@ -471,8 +277,8 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 int kc = 0;
                 const int nch = chunks(r.num_k, &kc);
                 for (int c = 0; c < nch && ok; ++c, ++g) {
-                    const int b = g & 1;
-                    if (!mbar_wait(&tempty[b], ((g >> 1) & 1) ^ 1, abort_flag, err,
+                    const int b = g % NB;
+                    if (!mbar_wait(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
                                    DEV_TIMEOUT_ACCUM)) {
                         ok = false;
                         break;
@@ -525,10 +331,24 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         double dsum = 0.0;
         uint32_t g = 0;
+        PendingTile<BN> pend;   // chunked engine: finished tile parked in TMEM columns NB BN ..
+        auto finish_pending = [&]() {
+            if constexpr (GROUPED) {
+                // each problem has its own dot target: flush per tile
+                if (pend.p->dot) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                    if (lane == 0 && dsum != 0.0) atomicAdd(pend.p->dot, dsum);
+                }
+                dsum = 0.0;
+            }
+            pend.p = nullptr;
+        };
         for (int t = t_first; t < total_tiles; t += t_step) {
             const TileRef r = tile(t);
             if (r.skip) continue;
             const EpiParams<float> p = r.pr->p;
+            const bool vec4 = epi_vec4_ok(p);
             const int m = r.m0 + 32 * q + lane;
             int kc = 0;
             const int nch = chunks(r.num_k, &kc);
@@ -539,10 +359,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < BN; ++j) acc[j] = 0.f;
                 for (int c = 0; c < nch; ++c, ++g) {
-                    const int b = g & 1;
+                    const int b = g % NB;
                     int w = 1;
                     if (lane == 0)
-                        w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                        w = mbar_wait(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
                     w = __shfl_sync(0xffffffffu, w, 0);
                     if (!w) {
                         ok = false;
@@ -550,25 +370,26 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int c0 = 0; c0 < BN; c0 += 32) {
-                        uint32_t rr[32];
-                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
+                    for (int c0 = 0; c0 < BN; c0 += 64) {
+                        uint32_t rr[64];
+                        tmem_ld64(lane_base + (uint32_t)(b * BN + c0), rr);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
+                        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[b]);
+                    // a share of the previous tile's stores, spread over this tile's chunks
+                    if (pend.p) {
+                        const int left = BN / 4 - pend.next;
+                        if (pend.drain((left + (nch - c) - 1) / (nch - c), dsum)) finish_pending();
+                    }
                 }
                 if (!ok) break;
-                if (m < p.M) {
-                    float local = 0.f;
-#pragma unroll
-                    for (int j = 0; j < BN; ++j) {
-                        const int n = r.n0 + j;
-                        if (n < p.N) local += epi_apply(p, m, n, acc[j]);
-                    }
-                    dsum += (double)local;
+                if (pend.p) {
+                    pend.drain(BN / 4, dsum);
+                    finish_pending();
                 }
+                pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, acc);
             } else {
                 (void)nch;
                 const int b = g & 1;
@@ -585,10 +406,19 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     if (m < p.M) {
                         float local = 0.f;
                         const int nb = r.n0 + c0;
+                        if (vec4 && nb + 32 <= p.N) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int n = nb + j;
-                            if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
+                            for (int j = 0; j < 32; j += 4)
+                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
+                                                    __uint_as_float(rr[j + 1]),
+                                                    __uint_as_float(rr[j + 2]),
+                                                    __uint_as_float(rr[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int n = nb + j;
+                                if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
+                            }
                         }
                         dsum += (double)local;
                     }
@@ -597,7 +427,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 mbar_arrive(&tempty[b]);
                 ++g;
             }
-            if constexpr (GROUPED) {
+            if constexpr (GROUPED && KCH == 0) {
                 // each problem has its own dot target: flush per tile
                 if (p.dot) {
 #pragma unroll
@@ -605,6 +435,12 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
                 }
                 dsum = 0.0;
+            }
+        }
+        if constexpr (KCH > 0) {
+            if (pend.p) {
+                pend.drain(BN / 4, dsum);
+                finish_pending();
             }
         }
         if constexpr (!GROUPED) {
@@ -622,48 +458,8 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem_base, C::TMEM_COLS);
+        tmem_dealloc(tmem_base, kTmemCols);
     }
-}
-
-// ---------------------------------------------------------------- host side
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
-    });
-    return fn;
-}
-
-bool make_map(CUtensorMap* map, const float* base, int rows, int cols, int ld, int box_rows) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
 }
 
 template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED>
@@ -798,6 +594,19 @@ bool pair_enabled() {
     return v == 1;
 }
 
+// Kernel family for single (non-grouped) products: one SM per tile (with
+// cluster-pair multicast when enabled) or the two-SM MMA (cta_group::2, 256-row
+// tiles). Default: two-SM for TF32, one-SM for 3xTF32 (measured fastest);
+// CDMPT_TC_MODE=1sm|2sm forces one family.
+bool use_2sm(bool three) {
+    static int v = -2;
+    if (v == -2) {
+        const char* e = getenv("CDMPT_TC_MODE");
+        v = !e ? -1 : (std::strcmp(e, "2sm") == 0 ? 1 : 0);
+    }
+    return v < 0 ? !three : v == 1;
+}
+
 template <int BN, int STAGES, int PASSES, int KCH>
 cdmpt_status launch_grouped(const GemmProblem* problems, int G, int total_tiles, cudaStream_t s) {
     using C = Cfg<BN, STAGES, PASSES>;
@@ -827,19 +636,20 @@ int tc_tile_n(int engine) { return engine == CDMPT_GEMM_TC_TF32 ? 256 : 128; }
 int tc_tile_m() { return BM; }
 
 bool tc_encode_operand(CUtensorMap* map, const float* base, int rows, int cols, int ld,
-                       bool as_y, int engine) {
-    // as X: box of 128 rows (BM); as Y: box of the engine's BN rows
-    return make_map(map, base, rows, cols, ld, as_y ? tc_tile_n(engine) : BM);
+                       bool as_y, int engine, int bn) {
+    // as X: box of 128 rows (BM); as Y: box of BN rows (bn, else the engine's default)
+    return make_map(map, base, rows, cols, ld, as_y ? (bn > 0 ? bn : tc_tile_n(engine)) : BM);
 }
 
 cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int total_tiles,
-                             cudaStream_t s) {
+                             cudaStream_t s, int bn) {
     if (G <= 0 || total_tiles <= 0) return CDMPT_OK;
     if (!tc_supported()) {
         set_error("tcgen05 GEMM needs an sm_103 device");
         return CDMPT_ERR_UNSUPPORTED;
     }
     if (engine == CDMPT_GEMM_TC_TF32) return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
+    if (bn == 64) return launch_grouped<64, 4, 3, 2>(problems, G, total_tiles, s);
     switch (split_chunk()) {
         case 1: return launch_grouped<128, 3, 3, 1>(problems, G, total_tiles, s);
         case 4: return launch_grouped<128, 3, 3, 4>(problems, G, total_tiles, s);
@@ -867,6 +677,45 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     if (!tc_supported()) {
         set_error("tcgen05 GEMM needs an sm_103 device");
         return CDMPT_ERR_UNSUPPORTED;
+    }
+    if (engine == CDMPT_GEMM_TC_BF16) {
+        // operands rounded to BF16 in stream-ordered scratch (one copy when X is Y)
+        if ((ldx & 7) || (ldy & 7) || !X.x || !Y.x || K < 1) {
+            set_error("BF16 GEMM: X/Y needed, ld a multiple of 8, K >= 1");
+            return CDMPT_ERR_ARG;
+        }
+        const bool same = X.x == Y.x && ldx == ldy && M == N;
+        const size_t nx = (size_t)M * ldx, ny = same ? 0 : (size_t)N * ldy;
+        void* buf = nullptr;
+        if (cudaMallocAsync(&buf, (nx + ny) * 2 + 256, s) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("BF16 GEMM: scratch allocation failed");
+            return CDMPT_ERR_OOM;
+        }
+        char* xb = (char*)buf;
+        char* yb = same ? xb : xb + ((nx * 2 + 255) & ~(size_t)255);
+        cdmpt_status st = to_bf16(X.x, nx, xb, skip, s);
+        if (st == CDMPT_OK && !same) st = to_bf16(Y.x, ny, yb, skip, s);
+        EpiParams<float> p;
+        p.alpha = (float)ep.alpha;
+        p.beta = (float)ep.beta;
+        p.gamma = (float)ep.gamma;
+        p.C = ep.C;
+        p.ldc = ep.ldc;
+        p.D = D;
+        p.ldd = ldd;
+        p.M = M;
+        p.N = N;
+        p.diag_block = ep.diag_block > 0 ? ep.diag_block : M;
+        p.trans_block = ep.trans_block;
+        p.dot = ep.dot;
+        p.E = ep.E;
+        p.lde = ep.lde;
+        p.Dhi = ep.Dhi;
+        p.Dlo = ep.Dlo;
+        if (st == CDMPT_OK) st = gemm_tc_bf16(M, N, K, xb, ldx, yb, ldy, p, skip, s);
+        cudaFreeAsync(buf, s);
+        return st;
     }
     const bool three = engine != CDMPT_GEMM_TC_TF32;
     const float* xh = X.hi ? X.hi : X.x;
@@ -898,6 +747,9 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     p.lde = ep.lde;
     p.Dhi = ep.Dhi;
     p.Dlo = ep.Dlo;
+    if (use_2sm(three) && M > BM)
+        return gemm_tc_2sm(three, split_chunk(), M, N, K, xh, three ? X.lo : xh, ldx, yh, three ? Y.lo : yh,
+                           ldy, p, skip, s);
     const bool pair = pair_enabled() && ((M + BM - 1) / BM) % 2 == 0;
     if (!three) {
         if (pair) return launch_pair<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);

@@ -1,0 +1,563 @@
+// Two-SM tcgen05 GEMM for sm_103a: the same product as k_gemm_tc,
+// D = alpha X Y^T + beta C + gamma I, with each MMA spanning a pair of SMs
+// (tcgen05.mma.cta_group::2, M = 256).
+//
+// A cluster of two CTAs owns a 256 x BN output tile. CTA r of the pair keeps
+// rows 128 r .. 128 r + 127 of the X tile and rows r BN/2 .. r BN/2 + BN/2 - 1
+// of the Y tile in its own shared memory. The MMA, issued by one thread of
+// CTA 0, reads both halves of both operands and writes accumulator rows
+// 128 r .. 128 r + 127 into CTA r's tensor memory. Each SM thus stages half of
+// the Y tile instead of all of it: per flop it receives fewer bytes, so the
+// same shared memory holds more k-blocks of lookahead.
+//
+// Roles per CTA (192 threads):
+//   warp 0      TMA producer in both CTAs, each loading its own halves. The
+//               copies of both CTAs complete on CTA 0's full barrier (the
+//               .cta_group::2 form of the copy may signal the peer's barrier),
+//               whose expected byte count covers both CTAs;
+//   warp 1      collective TMEM allocation of the pair; in CTA 0, lane 0
+//               issues the MMAs and commits them to the empty and
+//               accumulator-full barriers of both CTAs (multicast);
+//   warps 2..5  epilogue of this CTA's 128 rows (as in k_gemm_tc, including
+//               the deferred stores of the chunked engine); after draining an
+//               accumulator each warp arrives on CTA 0's accumulator-empty
+//               barrier, which counts 8 warps.
+// All tcgen05 instructions of the kernel use .cta_group::2.
+//
+// Every mbarrier wait is bounded by %globaltimer. On timeout the waiting
+// thread records the error and raises its CTA's abort flag; the peer's waits
+// then run out as well. Both CTAs meet at a cluster barrier before freeing
+// tensor memory, so neither leaves while the other may still signal it.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "epilogue.cuh"
+#include "internal.cuh"
+#include "tc_deferred.cuh"
+#include "tc_ptx.cuh"
+
+namespace cdmpt {
+
+namespace {
+
+using namespace tc;
+
+template <int BN, int STAGES, int PASSES>
+struct Cfg2 {
+    static constexpr int A_BYTES = BM * BK * 4;          // this CTA's 128 rows of X
+    static constexpr int B_BYTES = (BN / 2) * BK * 4;    // this CTA's half of the Y tile
+    static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGE_BYTES = PAIR_BYTES * (PASSES == 3 ? 2 : 1);
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+    static constexpr int THREADS = 192;
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "BN");
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert((2 * STAGES + 8) * 8 + 8 <= BAR_BYTES, "barrier area");
+};
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t caddr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(caddr) : "memory");
+    return v;
+}
+
+// Arrive on an mbarrier given by its shared::cluster address (either CTA).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait with cluster-scope acquire (barriers that the peer CTA signals).
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity,
+                                             volatile int* abort_flag, int* err, int code) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait_cl(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
+// TMA tile load into this CTA's shared memory whose completion is counted on
+// the mbarrier at cluster address bar_c, which may belong to the peer CTA.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar_c) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar_c)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* holder, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(holder)),
+                 "r"(cols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// kind::f16 with both operands BF16 (K = 16 per instruction), FP32 accumulation.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 and
+// 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int M, int N>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// Arrive on the mbarrier at the same offset in both CTAs of the pair once the
+// MMAs issued so far by this thread complete.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"((uint16_t)0x3)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_local_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// BF16: operands are BF16 (64 elements per 128-byte row, kind::f16); else FP32
+// read as TF32. The shared-memory layout is the same: 128-byte swizzled rows,
+// four 32-byte k-steps per k-block.
+template <int BN, int STAGES, int PASSES, int KCH, bool BF16 = false>
+__global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
+    k_gemm_tc2sm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                 const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
+                 const __grid_constant__ EpiParams<float> p, int K, int num_mt, int total_tiles,
+                 const double* skip, int* err) {
+    using C = Cfg2<BN, STAGES, PASSES>;
+    // two accumulators; the chunked engine adds a sum buffer (power-of-two allocation)
+    constexpr uint32_t kTmemCols = KCH > 0 ? 4 * BN : 2 * BN;
+    static_assert(kTmemCols <= 512, "TMEM columns");
+    // both CTAs of a pair read the same flag, so both return or neither does
+    if (skip != nullptr && *skip != 0.0) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    // the same offsets in both CTAs: the MMA addresses the peer's tiles by ours
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);   // used in CTA 0
+    uint64_t* empty = full + STAGES;
+    // TMEM accumulators: two, or three for the chunked engine
+    constexpr int NB = KCH > 0 ? 3 : 2;
+    uint64_t* tfull = empty + STAGES;   // [NB]
+    uint64_t* tempty = tfull + 3;       // [NB], used in CTA 0
+    uint64_t* drain = tempty + 3;       // [1]
+    uint32_t* tmem_holder = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    constexpr int KB = BF16 ? 2 * BK : BK;   // K elements per 128-byte k-block
+    static_assert(!BF16 || PASSES == 1, "BF16 is one pass");
+    const int num_k = (K + KB - 1) / KB;
+    auto chunks = [&](int* kc) {
+        *kc = KCH > 0 ? KCH : num_k;
+        return (num_k + *kc - 1) / *kc;
+    };
+    auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
+    auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::PAIR_BYTES; };
+    auto stage_blo = [&](int s) {
+        return smem + s * C::STAGE_BYTES + C::PAIR_BYTES + C::A_BYTES;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NB; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 8);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_holder, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // barriers of both CTAs initialised, TMEM of the pair allocated
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    // the pair's accumulators must sit at the same TMEM address in both CTAs
+    const bool bad = ld_cluster_u32(mapa_u32(smem_u32(tmem_holder), rank ^ 1u)) != tmem_base;
+    if (bad && threadIdx.x == 0) atomicCAS(err, 0, DEV_TMEM_MISMATCH);
+
+    if (bad) {
+        // fall through to the final barrier and free the allocation
+    } else if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            prefetch_map(&tmX);
+            prefetch_map(&tmY);
+            if constexpr (PASSES == 3) {
+                prefetch_map(&tmXl);
+                prefetch_map(&tmYl);
+            }
+            const uint32_t full0 = mapa_u32(smem_u32(full), 0);   // CTA 0's full[0]
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = cid; t < total_tiles && ok; t += ncl) {
+                const int m0 = (t % num_mt) * (2 * BM) + (int)rank * BM;
+                const int y0 = (t / num_mt) * BN + (int)rank * (BN / 2);
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait_cl(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_expect_tx(&full[s], 2 * C::STAGE_BYTES);
+                    const uint32_t fb = full0 + (uint32_t)s * 8u;
+                    tma_load_2d_pair(stage_a(s), &tmX, kb * KB, m0, fb);
+                    tma_load_2d_pair(stage_b(s), &tmY, kb * KB, y0, fb);
+                    if constexpr (PASSES == 3) {
+                        tma_load_2d_pair(stage_alo(s), &tmXl, kb * KB, m0, fb);
+                        tma_load_2d_pair(stage_blo(s), &tmYl, kb * KB, y0, fb);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (CTA 0)
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = BF16 ? idesc_bf16<2 * BM, BN>() : idesc_tf32<2 * BM, BN>();
+            uint32_t it = 0, g = 0;
+            bool ok = true, issued = false;
+            for (int t = cid; t < total_tiles && ok; t += ncl) {
+                int kc = 0;
+                const int nch = chunks(&kc);
+                for (int c = 0; c < nch && ok; ++c, ++g) {
+                    const int b = g % NB;
+                    if (!mbar_wait_cl(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
+                                      DEV_TIMEOUT_ACCUM)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
+                    const int kb0 = c * kc, kb1 = min(num_k, kb0 + kc);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        if (!mbar_wait_cl(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {   // 32-byte k-steps of the 128-byte row
+                            const uint32_t off = kk * 32;
+                            const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
+                            const uint32_t first = ((kb - kb0) | kk) != 0 ? 1u : 0u;
+                            if constexpr (PASSES == 3) {
+                                const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
+                                const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
+                                mma_tf32_pair(tmem_d, al, bh, idesc, first);
+                                mma_tf32_pair(tmem_d, ah, bl, idesc, 1u);
+                                mma_tf32_pair(tmem_d, ah, bh, idesc, 1u);
+                            } else if constexpr (BF16) {
+                                mma_bf16_pair(tmem_d, ah, bh, idesc, first);
+                            } else {
+                                mma_tf32_pair(tmem_d, ah, bh, idesc, first);
+                            }
+                        }
+                        issued = true;
+                        mma_commit_pair(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(&tfull[b]);
+                }
+            }
+            if (!ok && issued) {
+                mma_commit_local_pair(drain);
+                mbar_drain(drain, 0);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;     // TMEM lane quarter this warp may read
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        const uint32_t tempty0 = mapa_u32(smem_u32(tempty), 0);   // CTA 0's tempty[0]
+        const bool vec4 = epi_vec4_ok(p);
+        double dsum = 0.0;
+        uint32_t g = 0;
+        PendingTile<BN> pend;   // chunked engine: finished tile parked in TMEM columns NB BN ..
+        for (int t = cid; t < total_tiles; t += ncl) {
+            const int m = (t % num_mt) * (2 * BM) + (int)rank * BM + 32 * q + lane;
+            const int n0 = (t / num_mt) * BN;
+            int kc = 0;
+            const int nch = chunks(&kc);
+            bool ok = true;
+            auto wait_full = [&](int b) {
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait_cl(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                return __shfl_sync(0xffffffffu, w, 0) != 0;
+            };
+            auto release = [&](int b) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)b * 8u);
+            };
+            if constexpr (KCH > 0) {
+                // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
+                float acc[BN];
+#pragma unroll
+                for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+                for (int c = 0; c < nch; ++c, ++g) {
+                    const int b = g % NB;
+                    if (!wait_full(b)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += 64) {
+                        uint32_t rr[64];
+                        tmem_ld64(lane_base + (uint32_t)(b * BN + c0), rr);
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
+                    }
+                    release(b);
+                    // a share of the previous tile's stores, spread over this tile's chunks
+                    if (pend.p) {
+                        const int left = BN / 4 - pend.next;
+                        if (pend.drain((left + (nch - c) - 1) / (nch - c), dsum)) pend.p = nullptr;
+                    }
+                }
+                if (!ok) break;
+                if (pend.p) {
+                    pend.drain(BN / 4, dsum);
+                    pend.p = nullptr;
+                }
+                pend.park(&p, lane_base + (uint32_t)(NB * BN), m, n0, acc);
+            } else {
+                (void)nch;
+                const int b = g & 1;
+                if (!wait_full(b)) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t rr[32];
+                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
+                    if (m < p.M) {
+                        float local = 0.f;
+                        const int nb = n0 + c0;
+                        if (vec4 && nb + 32 <= p.N) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
+                                                    __uint_as_float(rr[j + 1]),
+                                                    __uint_as_float(rr[j + 2]),
+                                                    __uint_as_float(rr[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int n = nb + j;
+                                if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
+                            }
+                        }
+                        dsum += (double)local;
+                    }
+                }
+                release(b);
+                ++g;
+            }
+        }
+        if constexpr (KCH > 0) {
+            if (pend.p) pend.drain(BN / 4, dsum);
+        }
+        if (p.dot) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+            if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        // after an abort, give copies still in flight time to land
+        const unsigned long long t0 = globaltimer();
+        while (globaltimer() - t0 < 100000ull) {
+        }
+    }
+    __syncthreads();
+    cluster_sync();   // no CTA frees TMEM or leaves while its peer may still signal it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, kTmemCols);
+    }
+}
+
+// Tensor map of a BF16 operand (rows x cols, leading dimension ld elements).
+bool make_map_bf16(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, int PASSES, int KCH, bool BF16 = false>
+cdmpt_status launch_2sm(int M, int N, int K, const void* X, const void* Xl, int ldx,
+                        const void* Y, const void* Yl, int ldy, const EpiParams<float>& p,
+                        const double* skip, cudaStream_t s) {
+    using C = Cfg2<BN, STAGES, PASSES>;
+    auto kern = k_gemm_tc2sm<BN, STAGES, PASSES, KCH, BF16>;
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM);
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3(2 * (sm_count() / 2));
+        q.blockDim = dim3(C::THREADS);
+        q.dynamicSmemBytes = C::SMEM;
+        cudaLaunchAttribute a;
+        a.id = cudaLaunchAttributeClusterDimension;
+        a.val.clusterDim.x = 2;
+        a.val.clusterDim.y = 1;
+        a.val.clusterDim.z = 1;
+        q.attrs = &a;
+        q.numAttrs = 1;
+        int n = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
+        if (e != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            set_error("tcgen05 two-SM GEMM: no resident cluster of two");
+            return CDMPT_ERR_UNSUPPORTED;
+        }
+        max_clusters = n;
+    }
+    CUtensorMap mx, my, mxl, myl;
+    bool ok;
+    if constexpr (BF16) {
+        ok = make_map_bf16(&mx, X, M, K, ldx, BM) && make_map_bf16(&my, Y, N, K, ldy, BN / 2);
+        mxl = mx;
+        myl = my;
+    } else {
+        ok = make_map(&mx, (const float*)X, M, K, ldx, BM) &&
+             make_map(&my, (const float*)Y, N, K, ldy, BN / 2) &&
+             make_map(&mxl, (const float*)Xl, M, K, ldx, BM) &&
+             make_map(&myl, (const float*)Yl, N, K, ldy, BN / 2);
+    }
+    if (!ok) {
+        set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
+        return CDMPT_ERR_ARG;
+    }
+    const int num_mt = (M + 2 * BM - 1) / (2 * BM);
+    const int tiles = num_mt * ((N + BN - 1) / BN);
+    const int clusters = tiles < max_clusters ? tiles : max_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 2;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, p, K, num_mt, tiles, skip,
+                                       device_error_word());
+    count_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("tcgen05 two-SM GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
+}  // namespace
+
+cdmpt_status gemm_tc_2sm(bool three, int kch, int M, int N, int K, const float* X,
+                         const float* Xl, int ldx, const float* Y, const float* Yl, int ldy,
+                         const EpiParams<float>& p, const double* skip, cudaStream_t s) {
+    if (!three) return launch_2sm<256, 6, 1, 0>(M, N, K, X, X, ldx, Y, Y, ldy, p, skip, s);
+    switch (kch) {
+        case 0: return launch_2sm<128, 4, 3, 0>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        case 4: return launch_2sm<128, 4, 3, 4>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        default: return launch_2sm<128, 4, 3, 2>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+    }
+}
+
+cdmpt_status gemm_tc_bf16(int M, int N, int K, const void* X, int ldx, const void* Y, int ldy,
+                         const EpiParams<float>& p, const double* skip, cudaStream_t s) {
+    return launch_2sm<256, 6, 1, 0, true>(M, N, K, X, X, ldx, Y, Y, ldy, p, skip, s);
+}
+
+}  // namespace cdmpt

@@ -77,6 +77,7 @@ enum DeviceError {
     DEV_TIMEOUT_EMPTY = 2,
     DEV_TIMEOUT_CONV = 3,
     DEV_TIMEOUT_ACCUM = 4,
+    DEV_TMEM_MISMATCH = 5,   // the two CTAs of a pair got different TMEM addresses
 };
 
 int* device_error_word();   // per-device word, zeroed at first use
@@ -93,14 +94,31 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
                          const Operand<float>& Y, int ldy, float* D, int ldd,
                          const Epilogue<float>& ep, const double* skip, cudaStream_t s);
 bool tc_supported();   // device is sm_103 (tcgen05 kernels built for sm_103a)
+// Two-SM variant (tcgen05.mma.cta_group::2, 256-row tiles per CTA pair);
+// X / Y are the hi operands (TF32) and Xl / Yl the lo operands (3xTF32).
+template <typename T>
+struct EpiParams;
+// BF16 engine: operands already rounded to BF16 (row-major, ld a multiple of 8).
+cdmpt_status gemm_tc_bf16(int M, int N, int K, const void* X, int ldx, const void* Y, int ldy,
+                          const EpiParams<float>& p, const double* skip, cudaStream_t s);
+// out[i] = BF16(x[i]) rounded to nearest even, count a multiple of 4; skipped while *skip != 0.
+cdmpt_status to_bf16(const float* x, size_t count, void* out, const double* skip,
+                     cudaStream_t s);
+// kch: k-blocks per TMEM accumulation chunk of the 3xTF32 engine (0 = whole K).
+cdmpt_status gemm_tc_2sm(bool three, int kch, int M, int N, int K, const float* X,
+                         const float* Xl, int ldx, const float* Y, const float* Yl, int ldy,
+                         const EpiParams<float>& p, const double* skip, cudaStream_t s);
 
 // Grouped tcgen05 launches (batched solves). A GemmProblem holds one problem's
 // epilogue, K, tile offset, skip flag and four tensor maps in device memory.
 struct GemmProblem;
 int tc_tile_n(int engine);
 int tc_tile_m();
+// bn: tile width of the split-TF32 grouped kernel (128, or 64 for many small
+// problems); 0 = the engine's default. Tensor maps of Y operands must be
+// encoded with the same bn (tc_encode_operand).
 cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int total_tiles,
-                             cudaStream_t s);
+                             cudaStream_t s, int bn = 0);
 
 // Elementwise / reduction launchers (T = float or double). "count" is the
 // number of elements of a contiguous rows x ld block; padding columns hold 0.

@@ -30,7 +30,8 @@
 // Z_{k+1} is found by CG whose iterations use one-pass TF32 products (mixed-
 // precision iterative refinement of each step's linear system). Between
 // passes a Newton step on mu shifts Z_0 by s2 dmu I. The response then uses
-// split-TF32 products throughout.
+// split-TF32 products throughout. CDMPT_MIXED_BF16 is the same with the
+// occupation sweeps on BF16-rounded operands (kind::f16, FP32 accumulation).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +68,9 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n) {
     allocs_.clear();
     Z_.clear();
     W_.clear();
+    Z1t_.clear();
+    A1t_.clear();
+    r2_n_ = -1;
     N_ = N;
     D_ = D;
     n_ = n;
@@ -137,7 +141,9 @@ int Solver<T>::engine_of(const Context& cx, int override_engine) const {
 }
 
 static double tensor_factor(int engine) {
-    return engine == CDMPT_GEMM_TC_3XTF32 ? 3.0 : engine == CDMPT_GEMM_TC_TF32 ? 1.0 : 0.0;
+    return engine == CDMPT_GEMM_TC_3XTF32 ? 3.0
+           : (engine == CDMPT_GEMM_TC_TF32 || engine == CDMPT_GEMM_TC_BF16) ? 1.0
+                                                                            : 0.0;
 }
 
 template <typename T>
@@ -494,6 +500,216 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
 }
 
 template <typename T>
+cdmpt_status Solver<T>::reserve_response2(int n) {
+    if (r2_n_ >= n) return CDMPT_OK;
+    auto buf = [&](Buf<T>* b) -> cdmpt_status {
+        *b = Buf<T>();
+        const int parts = sizeof(T) == 4 ? 3 : 1;
+        T* q[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < parts; ++i) {
+            void* p = nullptr;
+            if (cudaMalloc(&p, blk_ * sizeof(T)) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation for the second-order response failed");
+                return CDMPT_ERR_OOM;
+            }
+            if (cudaMemset(p, 0, blk_ * sizeof(T)) != cudaSuccess) return CDMPT_ERR_CUDA;
+            allocs_.push_back(p);
+            q[i] = (T*)p;
+        }
+        b->x = q[0];
+        b->hi = q[1];
+        b->lo = q[2];
+        return CDMPT_OK;
+    };
+    const int have_z = (int)Z1t_.size(), have_a = (int)A1t_.size();
+    Z1t_.resize(n + 1);
+    A1t_.resize(n);
+    for (int k = have_z; k <= n; ++k) CDMPT_TRY(buf(&Z1t_[k]));
+    for (int k = have_a; k < n; ++k) CDMPT_TRY(buf(&A1t_[k]));
+    if (r2_n_ < 0) {
+        CDMPT_TRY(buf(&Z2a_));
+        CDMPT_TRY(buf(&Z2b_));
+        CDMPT_TRY(buf(&A2_));
+        CDMPT_TRY(buf(&G_));
+    }
+    r2_n_ = n;
+    return CDMPT_OK;
+}
+
+// Canonical first-order trajectory of one direction, with mu1 already known:
+// Z1_0 = -s2 (H1 - mu1 I), and per step (correction form, as in solve)
+//   A1_k = Z_k Z1_k + Z1_k Z_k,  d1 (I + W_k) = -Z_{k+1} A1_k - 2 Z1_k W_k,
+//   Z1_{k+1} = sym(2 Z1_k + d1); every Z1_k and A1_k is kept.
+template <typename T>
+cdmpt_status Solver<T>::first_order_trajectory(Context& cx, const double* H1d, double mu1) {
+    const int n = last_n_, N = N_;
+    const int acc = last_acc_;
+    const cdmpt_opts& o = last_opts_;
+    CDMPT_TRY(Ew<T>::init_z(Z1t_[0].x, H1d, N, ld, ld, 1, -last_s2_, mu1, cx.stream, Z1t_[0].hi,
+                            Z1t_[0].lo));
+    int hint = 1;
+    for (int k = 0; k < n; ++k) {
+        {   // S^T = Z1_k Z_k
+            Epilogue<T> ep;
+            CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), Z_[k].op(), S_.x, ep, nullptr, acc));
+        }
+        CDMPT_TRY(Ew<T>::transpose_add(A1t_[k].x, S_.x, N, ld, 1, cx.stream, A1t_[k].hi,
+                                       A1t_[k].lo));
+        {   // -Z_{k+1} A1_k = -(A1_k Z_{k+1})^T
+            Epilogue<T> ep;
+            ep.alpha = -1.0;
+            ep.trans_block = N;
+            CDMPT_TRY(gemm(cx, N, N, N, A1t_[k].op(), Z_[k + 1].op(), RHS_.x, ep, nullptr, acc));
+        }
+        {   // -= 2 Z1_k W_k
+            Epilogue<T> ep;
+            ep.alpha = -2.0;
+            ep.beta = 1.0;
+            ep.C = RHS_.x;
+            ep.ldc = ld;
+            CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
+        }
+        CgArgs a;
+        a.W = &W_[k];
+        a.rhs = RHS_.x;
+        a.rows = N;
+        a.tol = o.cg_tol;
+        a.maxit = o.cg_maxit;
+        a.init_engine = a.iter_engine = acc;
+        a.hint = hint;
+        int it = 0;
+        CDMPT_TRY(cg(cx, Z1t_[k + 1].x, a, &it, nullptr));
+        hint = std::max(1, it);
+        CDMPT_TRY(Ew<T>::axpby(Z1t_[k + 1].x, Z1t_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
+        CDMPT_TRY(Ew<T>::symmetrize(Z1t_[k + 1].x, N, ld, 1, cx.stream, Z1t_[k + 1].hi,
+                                    Z1t_[k + 1].lo));
+    }
+    return CDMPT_OK;
+}
+
+// Second order (Algorithm 1, the X^(2) line, with H^(2) = 0) in the deviation
+// form. Differentiating A_k Z_{k+1} = 2 Z_k twice in lambda, with A = I + Z^2:
+//   A_k Z2_{k+1} = 2 Z2_k - A1_k Z1_{k+1} - A2_k Z_{k+1},
+//   A2_k = Z_k Z2_k + Z2_k Z_k + Z1_k Z1_k,
+// solved in correction form d2 (I + W_k) = -Z1_{k+1} A1_k - Z_{k+1} A2_k -
+// 2 Z2_k W_k, Z2_{k+1} = sym(2 Z2_k + d2), from Z2_0 = 0 (mu2 = 0). P2 is linear
+// in mu2 with slope Q = dP0/dmu (Z2_0 = s2 mu2 I enters through the same
+// tangent map as a uniform shift of Z_0), so mu2 = -Tr P2|_0 / Tr Q and
+// P2 = Z2_n / 2 + mu2 Q. The polarizability gradient follows from the symmetry
+// of the third derivatives of the canonical free energy (whose gradient in H0
+// is P0): d alpha_d / d H0 = -2 d^2 P / d lambda_d^2 = -4 P2_d.
+template <typename T>
+cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
+                                  double* P2, double* mu2_out, double* grad) {
+    if (!traj_valid_ || D < 1 || (int)last_mu1_.size() < D) {
+        set_error("second-order response: no completed solve with perturbations on this handle");
+        return CDMPT_ERR_ARG;
+    }
+    const int n = last_n_, N = N_;
+    const int acc = last_acc_;
+    const cdmpt_opts& o = last_opts_;
+    CDMPT_TRY(reserve_response2(n));
+    if (!q_valid_) CDMPT_TRY(compute_q(cx));
+    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, sizeof(double), cx.stream));
+    CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+    const double trQ = cx.pinned[S_TRQ];
+    if (!(trQ > 0)) {
+        set_error("second-order response: Tr dP0/dmu is not positive");
+        return CDMPT_ERR_NO_CONVERGENCE;
+    }
+    if (grad) CDMPT_CUDA_TRY(cudaMemsetAsync(G_.x, 0, blk_ * sizeof(T), cx.stream));
+    auto zero = [&](Buf<T>& b) -> cdmpt_status {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, blk_ * sizeof(T), cx.stream));
+        if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, blk_ * sizeof(T), cx.stream));
+        if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, blk_ * sizeof(T), cx.stream));
+        return CDMPT_OK;
+    };
+    for (int d = 0; d < D; ++d) {
+        CDMPT_TRY(first_order_trajectory(cx, H1 + (size_t)d * blk_, last_mu1_[d]));
+        Buf<T>* Z2 = &Z2a_;
+        Buf<T>* Z2n = &Z2b_;
+        CDMPT_TRY(zero(*Z2));
+        int hint = 1;
+        for (int k = 0; k < n; ++k) {
+            {   // S^T = Z2_k Z_k
+                Epilogue<T> ep;
+                CDMPT_TRY(gemm(cx, N, N, N, Z2->op(), Z_[k].op(), S_.x, ep, nullptr, acc));
+            }
+            CDMPT_TRY(Ew<T>::transpose_add(A2_.x, S_.x, N, ld, 1, cx.stream));
+            {   // A2 += Z1_k Z1_k (split for its use as a left factor)
+                Epilogue<T> ep;
+                ep.beta = 1.0;
+                ep.C = A2_.x;
+                ep.ldc = ld;
+                ep.Dhi = A2_.hi;
+                ep.Dlo = A2_.lo;
+                CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), Z1t_[k].op(), A2_.x, ep, nullptr, acc));
+            }
+            {   // RHS = -Z1_{k+1} A1_k = -(A1_k Z1_{k+1})^T
+                Epilogue<T> ep;
+                ep.alpha = -1.0;
+                ep.trans_block = N;
+                CDMPT_TRY(gemm(cx, N, N, N, A1t_[k].op(), Z1t_[k + 1].op(), RHS_.x, ep, nullptr,
+                               acc));
+            }
+            {   // -= Z_{k+1} A2_k = (A2_k Z_{k+1})^T
+                Epilogue<T> ep;
+                ep.alpha = -1.0;
+                ep.beta = 1.0;
+                ep.C = RHS_.x;
+                ep.ldc = ld;
+                ep.trans_block = N;
+                CDMPT_TRY(gemm(cx, N, N, N, A2_.op(), Z_[k + 1].op(), RHS_.x, ep, nullptr, acc));
+            }
+            {   // -= 2 Z2_k W_k
+                Epilogue<T> ep;
+                ep.alpha = -2.0;
+                ep.beta = 1.0;
+                ep.C = RHS_.x;
+                ep.ldc = ld;
+                CDMPT_TRY(gemm(cx, N, N, N, Z2->op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
+            }
+            CgArgs a;
+            a.W = &W_[k];
+            a.rhs = RHS_.x;
+            a.rows = N;
+            a.tol = o.cg_tol;
+            a.maxit = o.cg_maxit;
+            a.init_engine = a.iter_engine = acc;
+            a.hint = hint;
+            int it = 0;
+            CDMPT_TRY(cg(cx, Z2n->x, a, &it, nullptr));
+            hint = std::max(1, it);
+            CDMPT_TRY(Ew<T>::axpby(Z2n->x, Z2->x, blk_, 2.0, 1.0, nullptr, cx.stream));
+            CDMPT_TRY(Ew<T>::symmetrize(Z2n->x, N, ld, 1, cx.stream, Z2n->hi, Z2n->lo));
+            std::swap(Z2, Z2n);
+        }
+        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
+        CDMPT_TRY(Ew<T>::trace(Z2->x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
+        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+        const double mu2 = -0.5 * cx.pinned[S_TRQ + 1] / trQ;
+        if (mu2_out) mu2_out[d] = mu2;
+        // Z2 += 2 mu2 Q  (P2 = Z2 / 2)
+        CDMPT_TRY(Ew<T>::axpby(Z2->x, Qmu_.x, blk_, 2.0 * mu2, 1.0, nullptr, cx.stream));
+        if (P2)
+            CDMPT_TRY(Ew<T>::to_f64(P2 + (size_t)d * N * N, N, Z2->x, ld, N, N, 0.5, 0.0,
+                                    cx.stream));
+        if (grad) {   // -4 w_d P2_d = -2 w_d Z2
+            const double wd = w ? w[d] : 1.0;
+            CDMPT_TRY(Ew<T>::axpby(G_.x, Z2->x, blk_, -2.0 * wd, 1.0, nullptr, cx.stream));
+        }
+    }
+    if (grad) {
+        CDMPT_TRY(Ew<T>::symmetrize(G_.x, N, ld, 1, cx.stream));
+        CDMPT_TRY(Ew<T>::to_f64(grad, N, G_.x, ld, N, N, 1.0, 0.0, cx.stream));
+    }
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
+    return check_device_error(cx.stream);
+}
+
+template <typename T>
 cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, int N, int D,
                               double gmin, double gmax, double trH0, const cdmpt_opts& o,
                               double beta, double nocc, int n, double* P0, double* P1,
@@ -505,6 +721,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     }
     CDMPT_TRY(reserve(N, D, n));
     traj_valid_ = q_valid_ = false;
+    last_mu1_.assign(std::max(D, 0), 0.0);
     cdmpt_stats& st = *cx.st;
     const double s2 = std::ldexp(beta, -(n + 1));
     const double width = gmax - gmin;
@@ -513,22 +730,25 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                   " >= 1: X_0 leaves [0, 1]; use more recursion steps");
         return CDMPT_ERR_RANGE;
     }
-    const bool mixed = sizeof(T) == 4 && o.precision == CDMPT_MIXED_TF32;
+    const bool bf16 = sizeof(T) == 4 && o.precision == CDMPT_MIXED_BF16;
+    const bool mixed = sizeof(T) == 4 && (o.precision == CDMPT_MIXED_TF32 || bf16);
     if (mixed && cx.engine == CDMPT_GEMM_SIMT) {
-        set_error("MIXED_TF32 needs the tcgen05 engines");
+        set_error("mixed precision needs the tcgen05 engines");
         return CDMPT_ERR_ARG;
     }
     // engines: "acc" for FP32-accurate products, "fast" for the occupation sweeps
     const int acc = mixed ? (int)CDMPT_GEMM_TC_3XTF32 : engine_of(cx, 0);
-    const int fast = mixed ? (int)CDMPT_GEMM_TC_TF32 : acc;
+    const int fast = mixed ? (bf16 ? (int)CDMPT_GEMM_TC_BF16 : (int)CDMPT_GEMM_TC_TF32) : acc;
     const double pad = std::min(40.0 / beta, 0.45 * (1.0 / s2 - width));
     double lo = gmin - pad, hi = gmax + pad;
     double mu = o.have_mu_guess ? o.mu_guess : trH0 / N;
     mu = std::min(std::max(mu, lo + 1e-3 * pad), hi - 1e-3 * pad);
     const double occ_tol = o.occ_tol > 0 ? o.occ_tol : N * (sizeof(T) == 8 ? 1e-12 : 1e-7);
-    // one-pass TF32 traces are good to about 1e-4 relative; the refinement finishes mu
-    const double occ_tol_sweep = mixed ? std::max(occ_tol, 1e-5 * N) : occ_tol;
-    const double sweep_tol = mixed ? 1e-4 : o.cg_tol;
+    // one-pass TF32 traces are good to about 1e-4 relative, BF16 ones to about 1e-2;
+    // the refinement finishes mu
+    const double occ_tol_sweep =
+        mixed ? std::max(occ_tol, (bf16 ? 1e-3 : 1e-5) * N) : occ_tol;
+    const double sweep_tol = mixed ? (bf16 ? 1e-3 : 1e-4) : o.cg_tol;
 
     // -------------------------------------------------- occupation loop
     bool converged = false;
@@ -569,7 +789,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     if (mixed) {
         const int min_pass = std::max(1, o.refine_rounds);
         bool done = false;
-        for (int pass = 0; pass < min_pass + 6 && !done; ++pass) {
+        for (int pass = 0; pass < min_pass + (bf16 ? 10 : 6) && !done; ++pass) {
             int iters = 0;
             double worst = 0.0;
             CDMPT_TRY(refine(cx, o, n, &iters, &worst));
@@ -669,6 +889,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             const double trP1 = 0.5 * cx.pinned[S_TRZ1 + d];
             const double mu1 = trQ > 0 ? -trP1 / trQ : 0.0;
             if (mu1_out) mu1_out[d] = mu1;
+            last_mu1_[d] = mu1;
             // P1 = Z1/2 + mu1 Q  <=>  Z1 += 2 mu1 Q
             CDMPT_TRY(Ew<T>::axpby(Z1->x + (size_t)d * blk_, Qmu_.x, blk_, 2.0 * mu1, 1.0, nullptr,
                                    cx.stream));

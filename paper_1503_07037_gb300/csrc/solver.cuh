@@ -58,6 +58,15 @@ public:
     // the canonical constraint, by a reverse sweep through the stored
     // trajectory. G0 and grad are N x N FP64 device arrays (leading dimension N).
     cdmpt_status vjp_p0(Context& cx, const double* G0, double* grad);
+
+    // Second-order canonical response of the last solve (Algorithm 1, order 2,
+    // H^(2) = 0) for each of the D directions of H1 (device, D x N x ld FP64):
+    // P2_d = 1/2 d^2 P / d lambda_d^2 and mu2_d with Tr P2_d = 0. Optionally
+    // grad = -4 sum_d w_d P2_d = d (sum_d w_d alpha_d) / d H0 (w null: all 1).
+    // P2 (D x N x N) and grad (N x N) are FP64 device arrays with leading
+    // dimension N, or null; mu2 is a host array of D doubles, or null.
+    cdmpt_status response2(Context& cx, const double* H1, int D, const double* w, double* P2,
+                           double* mu2, double* grad);
     bool trajectory_valid() const { return traj_valid_; }
 
     int ld = 0;
@@ -92,6 +101,8 @@ private:
     cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);
     cdmpt_status compute_q(Context& cx);
     cdmpt_status read_scalars(Context& cx, const double* dev, int count);
+    cdmpt_status reserve_response2(int n);
+    cdmpt_status first_order_trajectory(Context& cx, const double* H1d, double mu1);
     int engine_of(const Context& cx, int override_engine) const;
 
     int N_ = 0, D_ = 0, n_ = 0;
@@ -102,6 +113,12 @@ private:
     Buf<T> Z1a_, Z1b_;               // response iterates
     Buf<T> Qmu_;                     // dP/dmu
     Buf<T> Zh_;                      // adjoint of Z_k in the reverse sweep
+    // second order: canonical first-order trajectory Z1_0..Z1_n, A1_k = Z_k Z1_k +
+    // Z1_k Z_k (k < n), the order-2 iterates, A2 and the gradient accumulator
+    std::vector<Buf<T>> Z1t_, A1t_;
+    Buf<T> Z2a_, Z2b_, A2_, G_;
+    int r2_n_ = -1;                  // steps the second-order buffers hold (-1: none)
+    std::vector<double> last_mu1_;
     // state of the last solve, for the response's Q and the adjoint
     bool traj_valid_ = false, q_valid_ = false;
     double last_beta_ = 0, last_s2_ = 0;

@@ -28,7 +28,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "f64"])
+    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -45,8 +45,9 @@ def main():
     def run():
         if a.engine == "f64":
             pkg.gemm_f64(Z, Z, D, gamma=1.0)
-        elif a.engine == "simt":
-            pkg.gemm_f32(Z, Z, D, gamma=1.0, engine="simt")
+        elif a.engine in ("simt", "bf16"):
+            # bf16: includes rounding the operand to BF16 (one pass, X is Y)
+            pkg.gemm_f32(Z, Z, D, gamma=1.0, engine=a.engine)
         else:
             pkg.gemm_f32_split(Zs, Zs, D, gamma=1.0, engine=a.engine)
 

@@ -41,3 +41,48 @@ def test_batch_matches_single_solves(cuda, cdmpt_lib):
             s = h.solve(p.beta, p.nocc, p.n)
         assert oracle.rel_frobenius(r["P0"][i].cpu().numpy(), s["P0"].cpu().numpy()) < 1e-5
     b.close()
+
+
+def test_batch_tuner_and_graph(cuda, cdmpt_lib):
+    """The tile autotuner picks one of its candidates after timing both; CG iterations
+    replay a CUDA graph; each fixed tile width and the graph-free path give the same
+    solution (tile width and capture change no arithmetic)."""
+    import os
+    probs = syn.clusters(B=6, seed=4005, sizes=[128, 700, 250, 96, 513, 1100], n=12)
+    args = ([p.beta for p in probs], [p.nocc for p in probs], 12)
+
+    def run(env):
+        old = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
+        try:
+            b = cdmpt_lib.Batch([p.N for p in probs], 3)
+            b.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
+            r = b.solve(*args)
+            t = b.tuning()
+            b.close()
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        return r, t
+
+    r, t = run({})
+    assert t["tile_n"] in (64, 128)
+    assert t["ms_128"] > 0 and t["ms_64"] > 0
+    assert t["graphs"]
+    for env in ({"CDMPT_BATCH_TILE": "64"}, {"CDMPT_BATCH_TILE": "128"},
+                {"CDMPT_BATCH_GRAPH": "0"}):
+        r2, t2 = run(env)
+        if "CDMPT_BATCH_TILE" in env:
+            assert t2["tile_n"] == int(env["CDMPT_BATCH_TILE"])
+        else:
+            assert not t2["graphs"]
+        for i in range(len(probs)):
+            assert oracle.rel_frobenius(r2["P0"][i].cpu().numpy(), r["P0"][i].cpu().numpy()) < 1e-6
+            for d in range(3):
+                assert oracle.rel_frobenius(r2["P1"][i][d].cpu().numpy(),
+                                            r["P1"][i][d].cpu().numpy()) < 1e-5
+    ref = oracle.solve(probs[5].H0, probs[5].H1, probs[5].beta, probs[5].nocc, n=12, kind="rec")
+    assert oracle.rel_frobenius(r["P0"][5].cpu().numpy(), ref["P0"]) < 1e-5

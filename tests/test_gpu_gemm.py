@@ -137,3 +137,35 @@ def test_spectral_bounds(cuda, cdmpt_lib):
         assert abs(b[0] - lo) < 1e-12 and abs(b[1] - hi) < 1e-12
         ev = np.linalg.eigvalsh(p.H0)
         assert b[0] <= ev[0] + 1e-12 and ev[-1] <= b[1] + 1e-12
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 200, 136), (1024, 1024, 1024),
+                                   (777, 513, 2056)])
+def test_gemm_bf16(cuda, cdmpt_lib, M, N, K):
+    """BF16 engine (kind::f16, FP32 accumulation) on operands rounded to BF16 inside the call:
+    close to the exact FP64 product of the BF16-rounded inputs, and within BF16 rounding of
+    the FP32 product."""
+    import torch
+    rng = np.random.default_rng(M + 5 * N + 11 * K)
+    ld = (K + 7) // 8 * 8
+    X = _mat(rng, M, K, ld)
+    Y = _mat(rng, N, K, ld)
+    dev = torch.device("cuda")
+    D = torch.zeros((M, N), dtype=torch.float32, device=dev)
+    cdmpt_lib.gemm_f32(_t(X, dev), _t(Y, dev), D, gamma=0.5, engine="bf16", M=M, Ncols=N, K=K)
+    torch.cuda.synchronize()
+    Xb = torch.from_numpy(X[:, :K]).to(torch.bfloat16).double().numpy()
+    Yb = torch.from_numpy(Y[:, :K]).to(torch.bfloat16).double().numpy()
+    ref_b = Xb @ Yb.T + 0.5 * np.eye(M, N)
+    ref = X[:, :K].astype(np.float64) @ Y[:, :K].astype(np.float64).T + 0.5 * np.eye(M, N)
+    got = D.cpu().numpy().astype(np.float64)
+    assert _rel(got, ref_b) < 4e-5     # FP32 accumulation in TMEM over K
+    assert _rel(got, ref) < 1e-2
+
+
+def test_gemm_bf16_rejects_unaligned_ld(cuda, cdmpt_lib):
+    import torch
+    X = torch.zeros((64, 36), dtype=torch.float32, device="cuda")
+    D = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(cdmpt_lib.CdmptError):
+        cdmpt_lib.gemm_f32(X, X, D, engine="bf16", K=36)
