@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         }
         for (int a = 0; a < NB; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 128);
+            mbar_init(&tempty[a], 4);   // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
                     }
                     tc_fence_before();
-                    mbar_arrive(&tempty[b]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
                     // a share of the previous tile's stores, spread over this tile's chunks
                     if (pend.p) {
                         const int left = BN / 4 - pend.next;
@@ -424,7 +425,8 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&tempty[b]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
                 ++g;
             }
             if constexpr (GROUPED && KCH == 0) {
