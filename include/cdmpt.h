@@ -237,7 +237,9 @@ void cdmpt_destroy(cdmpt_handle* h);
  * product of a recursion step is one grouped persistent tcgen05 launch over
  * all systems, every vector update one grouped launch; each system keeps its
  * own CG scalars and chemical potential, and converged systems are skipped.
- * Storage FP32, split-TF32 products (only CDMPT_FP32 is accepted).
+ * Storage FP32. CDMPT_FP32: split-TF32 products throughout. CDMPT_MIXED_TF32:
+ * one-pass TF32 occupation sweeps, then split-TF32 refinement of every
+ * trajectory and a split-TF32 response, as in cdmpt_solve.
  */
 typedef struct cdmpt_batch cdmpt_batch;
 
@@ -290,6 +292,11 @@ void cdmpt_batch_destroy(cdmpt_batch* b);
  * engines ldx and ldy must be multiples of 4 and X, Y 16-byte aligned).
  * trans_block > 0 writes (and reads C at) the transposed position inside
  * consecutive row blocks of height trans_block (requires Ncols == trans_block).
+ * trans_block = -1 declares the result symmetric (M == Ncols; C and E
+ * symmetric): the tensor-core engines then compute only the upper-triangular
+ * tiles and mirror each off-diagonal tile, half the work; the CUDA-core
+ * engines compute every element. Every 0th-order product of the recursion is
+ * symmetric (functions of Z_k that commute).
  * dot != NULL accumulates sum_{m,n} D[m][n] * E[m][n] into *dot (device
  * double; E NULL means E = D). C may alias D. Asynchronous on stream.
  * engine: cdmpt_gemm_engine (AUTO = 3xTF32).

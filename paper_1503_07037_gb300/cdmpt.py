@@ -403,9 +403,9 @@ class Batch:
     float64 torch CUDA tensors.
     """
 
-    def __init__(self, sizes, D, stream=None, **kw):
+    def __init__(self, sizes, D, stream=None, precision="fp32", **kw):
         o = default_opts()
-        o.precision = FP32
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         for k, v in kw.items():
             setattr(o, k, v)
         o.stream = _stream_ptr(stream)

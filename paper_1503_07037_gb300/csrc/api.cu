@@ -416,7 +416,8 @@ cdmpt_status cdmpt_gemm_f32(int engine, int M, int Ncols, int K, const float* X,
     ep.ldc = ldc;
     ep.gamma = gamma;
     ep.diag_block = diag_block;
-    ep.trans_block = trans_block;
+    ep.trans_block = trans_block > 0 ? trans_block : 0;
+    ep.sym = trans_block < 0;
     ep.dot = dot;
     ep.E = E;
     ep.lde = lde;
@@ -493,7 +494,8 @@ cdmpt_status cdmpt_gemm_f32_split(int engine, int M, int Ncols, int K, const flo
     ep.ldc = ldc;
     ep.gamma = gamma;
     ep.diag_block = diag_block;
-    ep.trans_block = trans_block;
+    ep.trans_block = trans_block > 0 ? trans_block : 0;
+    ep.sym = trans_block < 0;
     ep.dot = dot;
     ep.E = E;
     ep.lde = lde;
@@ -528,7 +530,8 @@ cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, c
     ep.ldc = ldc;
     ep.gamma = gamma;
     ep.diag_block = diag_block;
-    ep.trans_block = trans_block;
+    ep.trans_block = trans_block > 0 ? trans_block : 0;
+    ep.sym = trans_block < 0;
     ep.dot = dot;
     ep.E = E;
     ep.lde = lde;

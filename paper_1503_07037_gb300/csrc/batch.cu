@@ -7,7 +7,10 @@
 // Each system keeps its own CG scalars, convergence flag and chemical
 // potential on the device; a converged system is skipped through its flag
 // (its GEMM tiles and elementwise blocks return at once). Storage is FP32 with
-// split-TF32 (3xTF32) products, as in the single-system FP32 mode.
+// split-TF32 (3xTF32) products, as in the single-system FP32 mode; with
+// CDMPT_MIXED_TF32 the occupation sweeps use one-pass TF32 products and the
+// trajectories are then refined (split-TF32 residuals, TF32 corrections,
+// Newton steps on each system's mu), as in the single-system mixed mode.
 //
 // Tile autotuner: before the first product of a batch, each candidate tile
 // width of the grouped kernel (128 and 64 columns, same accumulation chunk, so
@@ -93,7 +96,7 @@ struct cdmpt_batch {
     // CUDA graph of one CG iteration: dedicated descriptors, graphs by shape
     GemmProblem* it_gemm = nullptr;   // B problems
     GrpEw* it_ew = nullptr;           // 3 B: update, direction, scalar step
-    std::map<std::pair<int, long long>, cudaGraphExec_t> it_graphs;
+    std::map<std::tuple<int, long long, int>, cudaGraphExec_t> it_graphs;   // (tiles, block, engine)
     bool graphs = true;
     // capture runs on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); replays go to the caller's stream
@@ -204,11 +207,18 @@ cdmpt_status flush_maps(cdmpt_batch* b) {
 }
 
 // One problem of a grouped GEMM: D = alpha X Y^T + beta C + gamma I (rows x N_b, K = N_b).
-void add_flops(cdmpt_batch* b, double f) {
+void add_flops(cdmpt_batch* b, double f, int engine = kEngine) {
     if (b->cx.st) {
         b->cx.st->gemm_flops += f;
-        b->cx.st->tensor_flops += 3.0 * f;
+        b->cx.st->tensor_flops += (engine == CDMPT_GEMM_TC_3XTF32 ? 3.0 : 1.0) * f;
     }
+}
+
+// Flops of one symmetric N x N x N product: the upper-triangular tiles only
+// when the grouped kernel's tiles are square (tile width 128), else all.
+double sym_flops(const cdmpt_batch* b, int N) {
+    const double n = N;
+    return b->tile_bn == 128 || b->tile_bn == 0 ? n * (n + 1) * n : 2.0 * n * n * n;
 }
 
 struct GemmSpec {
@@ -256,9 +266,11 @@ cdmpt_status prepare_grouped(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
         pr.num_mt = (g.p.M + bm - 1) / bm;
         pr.skip = g.skip;
         pr.maps = nullptr;
+        // symmetric results need square tiles: the upper triangle only
+        pr.p.sym = (g.p.sym && bn == bm && g.p.M == N) ? 1 : 0;
         probs->push_back(pr);
         quad.push_back(q);
-        tiles += pr.num_mt * ((N + bn - 1) / bn);
+        tiles += pr.p.sym ? pr.num_mt * (pr.num_mt + 1) / 2 : pr.num_mt * ((N + bn - 1) / bn);
     }
     CDMPT_TRY(flush_maps(b));
     for (size_t i = 0; i < probs->size(); ++i) (*probs)[i].maps = b->maps_dev + quad[i];
@@ -266,7 +278,9 @@ cdmpt_status prepare_grouped(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
     return CDMPT_OK;
 }
 
-cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
+// engine: split TF32 (default) or one-pass TF32 (the occupation sweeps of mixed precision)
+cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
+                          int engine = kEngine) {
     std::vector<GemmProblem> probs;
     int tiles = 0;
     CDMPT_TRY(prepare_grouped(b, specs, &probs, &tiles));
@@ -274,7 +288,7 @@ cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
     const GemmProblem* dev = nullptr;
     CDMPT_TRY(stage(b, probs, &dev));
     if (b->cx.st) b->cx.st->gemm_launches += 1;
-    return gemm_tc_grouped(kEngine, dev, (int)probs.size(), tiles, b->cx.stream, b->tile_bn);
+    return gemm_tc_grouped(engine, dev, (int)probs.size(), tiles, b->cx.stream, b->tile_bn);
 }
 
 void clear_maps(cdmpt_batch* b) {
@@ -331,8 +345,8 @@ cdmpt_status tune_tiles(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
 // Graph of one CG iteration over all systems for this launch shape (tiles of
 // the grouped product, elements of the largest system's block); null when
 // capture is unavailable (the caller then launches the kernels one by one).
-cudaGraphExec_t iteration_graph(cdmpt_batch* b, int tiles, long long maxc) {
-    const auto key = std::make_pair(tiles, maxc);
+cudaGraphExec_t iteration_graph(cdmpt_batch* b, int tiles, long long maxc, int engine) {
+    const auto key = std::make_tuple(tiles, maxc, engine);
     auto it = b->it_graphs.find(key);
     if (it != b->it_graphs.end()) return it->second;
     if (!b->cap_stream &&
@@ -348,7 +362,7 @@ cudaGraphExec_t iteration_graph(cdmpt_batch* b, int tiles, long long maxc) {
         b->graphs = false;
         return nullptr;
     }
-    cdmpt_status st = gemm_tc_grouped(kEngine, b->it_gemm, G, tiles, s, b->tile_bn);
+    cdmpt_status st = gemm_tc_grouped(engine, b->it_gemm, G, tiles, s, b->tile_bn);
     if (st == CDMPT_OK) st = grouped_ew(G_CG_UPDATE, b->it_ew, G, maxc, s);
     if (st == CDMPT_OK) st = grouped_ew(G_CG_DIR, b->it_ew + G, G, maxc, s);
     if (st == CDMPT_OK) st = grouped_cg_step(b->it_ew + 2 * G, G, s);
@@ -429,8 +443,11 @@ struct BCg {
     int rows;
 };
 
+// sym: every system's iterates are symmetric (0th-order solves), so the
+// products run on upper-triangular tiles.
 cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, double t, double tol,
-                      const std::vector<const double*>& skip, int hint, int* iters) {
+                      const std::vector<const double*>& skip, int hint, int* iters,
+                      bool sym = false, int engine = kEngine) {
     const int G = b->B;
     CDMPT_TRY(zero_slots(b, 0, CG_NSLOTS));
     std::vector<GrpEw> dx, dr, drr, dbb, dp;
@@ -459,6 +476,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
             gs.rows = c.rows;
             gs.Y = c.W;
             gs.p = epi(sy.R.x, c.rows, sy.N, sy.ld, (float)-t, 1.f, sy.R.x);
+            gs.p.sym = sym && c.rows == sy.N;
             gs.p.dot = sy.sc + CG_RR;
             gs.skip = skip[i];
             g0.push_back(gs);
@@ -498,7 +516,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
     if (!g0.empty()) {
         CDMPT_TRY(run_ew(b, G_AXPBY, dx));
         CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
-        CDMPT_TRY(grouped_gemm(b, g0));
+        CDMPT_TRY(grouped_gemm(b, g0, engine));
     } else {
         CDMPT_TRY(run_ew(b, G_ZERO, dx));
         CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
@@ -532,6 +550,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
         gs.rows = c.rows;
         gs.Y = c.W;
         gs.p = epi(sy.Q.x, c.rows, sy.N, sy.ld, (float)t, (float)s, sy.P.x);
+        gs.p.sym = sym && c.rows == sy.N;
         gs.p.dot = sy.sc + CG_PQ;
         gs.p.E = sy.P.x;
         gs.skip = sy.sc + CG_DONE;
@@ -563,7 +582,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
                                        cudaMemcpyHostToDevice, b->cx.stream));
         CDMPT_CUDA_TRY(cudaMemcpyAsync(b->it_ew, ew.data(), ew.size() * sizeof(GrpEw),
                                        cudaMemcpyHostToDevice, b->cx.stream));
-        graph = iteration_graph(b, tiles, maxc);
+        graph = iteration_graph(b, tiles, maxc, engine);
     }
     int chunk = std::max(1, hint), done_iters = 0;
     while (true) {
@@ -574,7 +593,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
                 if (b->cx.st) b->cx.st->gemm_launches += 1;
                 continue;
             }
-            CDMPT_TRY(grouped_gemm(b, gi));
+            CDMPT_TRY(grouped_gemm(b, gi, engine));
             CDMPT_TRY(run_ew(b, G_CG_UPDATE, du));
             CDMPT_TRY(run_ew(b, G_CG_DIR, dd));
             const GrpEw* dev = nullptr;
@@ -593,9 +612,10 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
             *iters = most;
             for (int i = 0; i < G; ++i) {
                 const Sys& sy = b->sys[i];
-                const double f = 2.0 * a[i].rows * (double)sy.N * sy.N;
-                add_flops(b, f * b->pinned[i * kSlots + CG_ITERS]);
-                if (a[i].x0 && !(skip[i] && b->sys[i].converged)) add_flops(b, f);
+                const double f = (sym && a[i].rows == sy.N) ? sym_flops(b, sy.N)
+                                                             : 2.0 * a[i].rows * (double)sy.N * sy.N;
+                add_flops(b, f * b->pinned[i * kSlots + CG_ITERS], engine);
+                if (a[i].x0 && !(skip[i] && b->sys[i].converged)) add_flops(b, f, engine);
             }
             return CDMPT_OK;
         }
@@ -608,8 +628,9 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
     }
 }
 
-// One 0th-order pass for the systems whose inactive flag is 0.
-cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
+// One 0th-order pass for the systems whose inactive flag is 0, with products on
+// engine and CG to relative residual tol.
+cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, double tol) {
     const int G = b->B;
     std::vector<const double*> skip(G);
     for (int i = 0; i < G; ++i) skip[i] = b->inactive + i;
@@ -639,6 +660,7 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
             w.rows = sy.N;
             w.Y = &sy.Z[k];
             w.p = epi(sy.W[k].x, sy.N, sy.N, sy.ld);
+            w.p.sym = 1;
             w.p.Dhi = sy.W[k].hi;
             w.p.Dlo = sy.W[k].lo;
             w.skip = skip[i];
@@ -648,6 +670,7 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
             r.rows = sy.N;
             r.Y = &sy.W[k];
             r.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -2.f);
+            r.p.sym = 1;
             r.skip = skip[i];
             gr.push_back(r);
             cg[i] = BCg{sy.Z[k + 1].x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
@@ -663,13 +686,12 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
             dsym.push_back(y);
         }
         if (b->tile_bn == 0) CDMPT_TRY(tune_tiles(b, gw));   // first product of the batch
-        CDMPT_TRY(grouped_gemm(b, gw));
-        CDMPT_TRY(grouped_gemm(b, gr));
+        CDMPT_TRY(grouped_gemm(b, gw, engine));
+        CDMPT_TRY(grouped_gemm(b, gr, engine));
         for (int i = 0; i < G; ++i)
-            if (!b->sys[i].converged)
-                add_flops(b, 4.0 * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
+            if (!b->sys[i].converged) add_flops(b, 2.0 * sym_flops(b, b->sys[i].N), engine);
         int it = 0;
-        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, skip, hint, &it));
+        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, tol, skip, hint, &it, true, engine));
         total += it;
         hint = std::max(1, it);
         CDMPT_TRY(run_ew(b, G_AXPBY, dz));
@@ -677,6 +699,97 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out) {
     }
     *iters_out = total;
     return CDMPT_OK;
+}
+
+// One refinement pass of the stored trajectories (mixed precision), for the
+// systems whose inactive flag is 0: per step, W_k = Z_k Z_k and the residual
+// 2 Z_k - Z_{k+1} - Z_{k+1} W_k with split-TF32 products, then the correction
+// d (I + W_k) = residual by CG with one-pass TF32 products (relative residual
+// 1e-3), Z_{k+1} += d, symmetrised. The residual uses full tiles: the stored
+// Z_{k+1} does not commute with W_k to first order in its error.
+cdmpt_status refine_batch(cdmpt_batch* b, int n, int* iters_out) {
+    const int G = b->B;
+    std::vector<const double*> skip(G);
+    for (int i = 0; i < G; ++i) skip[i] = b->inactive + i;
+    int total = 0;
+    for (int k = 0; k < n; ++k) {
+        std::vector<GemmSpec> gw, gr;
+        std::vector<BCg> cg(G);
+        std::vector<GrpEw> ds, dz, dsym;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            GemmSpec w;                  // W_k = Z_k Z_k, split-TF32
+            w.X = &sy.Z[k];
+            w.rows = sy.N;
+            w.Y = &sy.Z[k];
+            w.p = epi(sy.W[k].x, sy.N, sy.N, sy.ld);
+            w.p.sym = 1;
+            w.p.Dhi = sy.W[k].hi;
+            w.p.Dlo = sy.W[k].lo;
+            w.skip = skip[i];
+            gw.push_back(w);
+            GrpEw e = ewd(sy.S.x, sy.Z[k].x, sy.Z[k + 1].x);   // S = 2 Z_k - Z_{k+1}
+            e.rows = sy.N; e.ld = sy.ld; e.N = sy.N; e.count = (long long)sy.N * sy.ld;
+            e.s0 = 2.0;
+            e.s1 = -1.0;
+            e.skip = skip[i];
+            ds.push_back(e);
+            GemmSpec r;                  // RHS = S - Z_{k+1} W_k, full tiles
+            r.X = &sy.Z[k + 1];
+            r.rows = sy.N;
+            r.Y = &sy.W[k];
+            r.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -1.f, 1.f, sy.S.x);
+            r.skip = skip[i];
+            gr.push_back(r);
+            cg[i] = BCg{sy.A1.x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
+            GrpEw z = ewd(sy.Z[k + 1].x, sy.A1.x);   // Z_{k+1} += d
+            z.rows = sy.N; z.ld = sy.ld; z.N = sy.N; z.count = (long long)sy.N * sy.ld;
+            z.s0 = 1.0;
+            z.s1 = 1.0;
+            z.skip = skip[i];
+            dz.push_back(z);
+            GrpEw y = ewd(sy.Z[k + 1].x, nullptr, sy.Z[k + 1].hi, sy.Z[k + 1].lo);
+            y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
+            y.skip = skip[i];
+            dsym.push_back(y);
+        }
+        CDMPT_TRY(grouped_gemm(b, gw));
+        CDMPT_TRY(run_ew(b, G_LINCOMB, ds));
+        CDMPT_TRY(grouped_gemm(b, gr));
+        for (int i = 0; i < G; ++i) {
+            if (b->sys[i].converged) continue;
+            const double nn = b->sys[i].N;
+            add_flops(b, sym_flops(b, b->sys[i].N) + 2.0 * nn * nn * nn);
+        }
+        int it = 0;
+        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, 1e-3, skip, 2, &it, false, CDMPT_GEMM_TC_TF32));
+        total += it;
+        CDMPT_TRY(run_ew(b, G_AXPBY, dz));
+        CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));
+    }
+    *iters_out = total;
+    return CDMPT_OK;
+}
+
+// Tr P0 and ||Z_n||_F^2 of every active system into its scalar slots (host copy in pinned).
+cdmpt_status occupations(cdmpt_batch* b, int n) {
+    const int G = b->B;
+    CDMPT_TRY(zero_slots(b, B_TRZ, 2));
+    std::vector<GrpEw> dt, dd;
+    for (int i = 0; i < G; ++i) {
+        Sys& sy = b->sys[i];
+        GrpEw e = ewd(sy.Z[n].x, sy.Z[n].x);
+        e.rows = sy.N; e.ld = sy.ld; e.N = sy.N; e.count = (long long)sy.blk;
+        e.sc = sy.sc;
+        e.skip = b->inactive + i;
+        e.s0 = B_TRZ;
+        dt.push_back(e);
+        e.s0 = B_ZZ;
+        dd.push_back(e);
+    }
+    CDMPT_TRY(run_tiles(b, dt, 1, grouped_trace));
+    CDMPT_TRY(run_ew(b, G_DOT, dd));
+    return read_all(b);
 }
 
 cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
@@ -739,9 +852,9 @@ cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int
     else
         cdmpt_default_opts(&b->opts);
     if (!(b->opts.cg_tol > 0)) b->opts.cg_tol = 1e-7;
-    if (b->opts.precision != CDMPT_FP32) {
+    if (b->opts.precision != CDMPT_FP32 && b->opts.precision != CDMPT_MIXED_TF32) {
         delete b;
-        set_error("batch: only CDMPT_FP32 (split-TF32 products) is available");
+        set_error("batch: CDMPT_FP32 (split-TF32 products) or CDMPT_MIXED_TF32 only");
         return CDMPT_ERR_UNSUPPORTED;
     }
     if (!tc_supported()) {
@@ -845,6 +958,10 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         sy.mu = std::min(std::max(sy.trH0 / sy.N, sy.lo + 1e-3 * pad), sy.hi - 1e-3 * pad);
         sy.converged = false;
     }
+    // mixed precision: one-pass TF32 sweeps, then split-TF32 refinement (as in cdmpt_solve)
+    const bool mixed = b->opts.precision == CDMPT_MIXED_TF32;
+    const int sweep_engine = mixed ? (int)CDMPT_GEMM_TC_TF32 : kEngine;
+    const double sweep_tol = mixed ? 1e-4 : b->opts.cg_tol;
     // -------------------------------------------------- occupation loops, in lockstep
     int sweeps = 0;
     for (; sweeps < b->opts.mu_maxit; ++sweeps) {
@@ -852,7 +969,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
                                        cudaMemcpyHostToDevice, st));
         int iters = 0;
-        cdmpt_status s = sweep_batch(b, n, &iters);
+        cdmpt_status s = sweep_batch(b, n, &iters, sweep_engine, sweep_tol);
         if (s != CDMPT_OK) return bfail(b, s);
         b->st.cg_iterations_sweeps += iters;
         CDMPT_TRY(zero_slots(b, B_TRZ, 2));
@@ -882,7 +999,9 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             const double trP = 0.5 * (sy.N + b->pinned[i * kSlots + B_TRZ]);
             const double zz = b->pinned[i * kSlots + B_ZZ];
             const double err = trP - sy.nocc;
-            const double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-7 * sy.N;
+            double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-7 * sy.N;
+            // one-pass TF32 traces are good to about 1e-4; the refinement finishes mu
+            if (mixed) tol = std::max(tol, 1e-5 * sy.N);
             if (std::fabs(err) <= tol) {
                 sy.converged = true;
                 continue;
@@ -904,6 +1023,54 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         if (!b->sys[i].converged)
             return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
                              "batch: occupation of system " + std::to_string(i) + " not reached");
+    // -------------------------------------------------- refinement (mixed), in lockstep
+    if (mixed) {
+        const int min_pass = std::max(1, b->opts.refine_rounds);
+        for (int i = 0; i < G; ++i) b->sys[i].converged = false;
+        bool all = false;
+        for (int pass = 0; pass < min_pass + 6 && !all; ++pass) {
+            for (int i = 0; i < G; ++i) inact[i] = b->sys[i].converged ? 1.0 : 0.0;
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
+                                           cudaMemcpyHostToDevice, st));
+            int iters = 0;
+            cdmpt_status s = refine_batch(b, n, &iters);
+            if (s != CDMPT_OK) return bfail(b, s);
+            b->st.cg_iterations_refine += iters;
+            s = occupations(b, n);
+            if (s != CDMPT_OK) return bfail(b, s);
+            all = true;
+            std::vector<GrpEw> reinit;
+            for (int i = 0; i < G; ++i) {
+                Sys& sy = b->sys[i];
+                if (sy.converged) continue;
+                const double trP = 0.5 * (sy.N + b->pinned[i * kSlots + B_TRZ]);
+                const double zz = b->pinned[i * kSlots + B_ZZ];
+                const double err = trP - sy.nocc;
+                // refined traces are good to about 1e-9 N: finish mu that far
+                const double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-9 * sy.N;
+                const bool occ_ok = std::fabs(err) <= tol;
+                if (occ_ok && pass + 1 >= min_pass) {
+                    sy.converged = true;
+                    continue;
+                }
+                all = false;
+                if (!occ_ok) {   // Newton step on mu; Z_0 = -s2 (H0 - mu I) is rebuilt
+                    const double slope = 0.25 * sy.beta * (sy.N - zz);
+                    if (slope > 0) sy.mu -= err / slope;
+                    GrpEw e = ewd(sy.Z[0].x, nullptr, sy.Z[0].hi, sy.Z[0].lo);
+                    e.h = sy.H0;
+                    e.rows = sy.N; e.ld = sy.ld; e.N = sy.N;
+                    e.s0 = -sy.s2;
+                    e.s1 = sy.mu;
+                    reinit.push_back(e);
+                }
+            }
+            if (!reinit.empty()) CDMPT_TRY(run_ew(b, G_INIT_Z, reinit));
+        }
+        if (!all)
+            return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
+                             "batch: mixed-precision refinement did not converge");
+    }
     if (mu)
         for (int i = 0; i < G; ++i) mu[i] = b->sys[i].mu;
     std::fill(inact.begin(), inact.end(), 0.0);
@@ -996,6 +1163,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 q.rows = sy.N;
                 q.Y = &sy.Z[n];
                 q.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -1.f, 0.f, nullptr, 1.f);
+                q.p.sym = 1;
                 q.p.Dhi = sy.RHS.hi;
                 q.p.Dlo = sy.RHS.lo;
                 q.skip = nullptr;
@@ -1006,10 +1174,9 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 dsym.push_back(y);
             }
             CDMPT_TRY(grouped_gemm(b, gq));
-            for (int i = 0; i < G; ++i)
-                add_flops(b, 2.0 * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
+            for (int i = 0; i < G; ++i) add_flops(b, sym_flops(b, b->sys[i].N));
             int it = 0;
-            cdmpt_status s = cg_batch(b, cg, 1.0, -1.0, b->opts.cg_tol, none, 1, &it);
+            cdmpt_status s = cg_batch(b, cg, 1.0, -1.0, b->opts.cg_tol, none, 1, &it, true);
             if (s != CDMPT_OK) return bfail(b, s);
             b->st.cg_iterations_q = it;
             CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));

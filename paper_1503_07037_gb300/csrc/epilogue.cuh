@@ -25,6 +25,7 @@ struct EpiParams {
     int lde;
     T* Dhi;   // optional TF32 split of D (float only), same ld as D
     T* Dlo;
+    int sym;  // symmetric result: upper-triangular tiles only, mirrored (see epi_apply_sym)
 };
 
 template <typename T>
@@ -63,6 +64,41 @@ __device__ __forceinline__ T epi_apply(const EpiParams<T>& p, int m, int n, T ac
     return T(0);
 }
 
+// Symmetric-result epilogue for element (m, n) of an upper-triangular tile:
+// on a diagonal tile only n >= m is taken; the value goes to (m, n) and, off
+// the diagonal, to (n, m) as well (C and E symmetric, no transposed placement).
+// Returns the D * E contribution of both positions.
+template <typename T>
+__device__ __forceinline__ T epi_apply_sym(const EpiParams<T>& p, int m, int n, T acc,
+                                           bool diag_tile) {
+    if (diag_tile && n < m) return T(0);
+    T v = p.alpha * acc;
+    if (p.beta != T(0)) v = fma(p.beta, p.C[(size_t)m * p.ldc + n], v);
+    if (p.gamma != T(0) && (m % p.diag_block) == n) v += p.gamma;
+    const size_t a = (size_t)m * p.ldd + n, b = (size_t)n * p.ldd + m;
+    p.D[a] = v;
+    if (m != n) p.D[b] = v;
+    if constexpr (sizeof(T) == 4) {
+        if (p.Dhi) {
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            const float hv = __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hv));
+            p.Dhi[a] = hv;
+            p.Dlo[a] = __uint_as_float(l);
+            if (m != n) {
+                p.Dhi[b] = hv;
+                p.Dlo[b] = __uint_as_float(l);
+            }
+        }
+    }
+    if (p.dot) {
+        const T e = p.E ? p.E[(size_t)m * p.lde + n] : v;
+        return (m != n ? T(2) : T(1)) * v * e;
+    }
+    return T(0);
+}
+
 // True when four consecutive columns of a row can be handled with 16-byte
 // accesses: no transposed placement, leading dimensions multiples of 4 and
 // 16-byte aligned arrays.
@@ -74,7 +110,8 @@ __device__ __forceinline__ bool epi_vec4_ok(const EpiParams<float>& p) {
 }
 
 // epi_apply for columns n .. n + 3 of row m (n % 4 == 0, n + 3 < N, and
-// epi_vec4_ok); returns the D * E contribution of the four elements.
+// epi_vec4_ok); returns the D * E contribution of the four elements. With
+// p.sym (only on off-diagonal tiles) the four values are mirrored to (n + i, m).
 __device__ __forceinline__ float epi_apply4(const EpiParams<float>& p, int m, int n, float a0,
                                             float a1, float a2, float a3) {
     float v[4] = {p.alpha * a0, p.alpha * a1, p.alpha * a2, p.alpha * a3};
@@ -94,6 +131,12 @@ __device__ __forceinline__ float epi_apply4(const EpiParams<float>& p, int m, in
     }
     const size_t o = (size_t)m * p.ldd + n;
     *(float4*)(p.D + o) = make_float4(v[0], v[1], v[2], v[3]);
+    if (p.sym) {
+        // mirror of an off-diagonal tile: column n + i of row m to row n + i (the
+        // 32 lanes of a warp hold consecutive rows, so these stores coalesce)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p.D[(size_t)(n + i) * p.ldd + m] = v[i];
+    }
     if (p.Dhi) {
         float h[4], l[4];
 #pragma unroll
@@ -106,13 +149,23 @@ __device__ __forceinline__ float epi_apply4(const EpiParams<float>& p, int m, in
         }
         *(float4*)(p.Dhi + o) = make_float4(h[0], h[1], h[2], h[3]);
         *(float4*)(p.Dlo + o) = make_float4(l[0], l[1], l[2], l[3]);
+        if (p.sym) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                p.Dhi[(size_t)(n + i) * p.ldd + m] = h[i];
+                p.Dlo[(size_t)(n + i) * p.ldd + m] = l[i];
+            }
+        }
     }
     if (p.dot) {
+        float d;
         if (p.E) {
             const float4 e = *(const float4*)(p.E + (size_t)m * p.lde + n);
-            return v[0] * e.x + v[1] * e.y + v[2] * e.z + v[3] * e.w;
+            d = v[0] * e.x + v[1] * e.y + v[2] * e.z + v[3] * e.w;
+        } else {
+            d = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
         }
-        return v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+        return p.sym ? 2.f * d : d;   // off-diagonal tile: the mirror counts too
     }
     return 0.f;
 }

@@ -105,6 +105,7 @@ cdmpt_status gemm_simt(int M, int N, int K, const T* X, int ldx, const T* Y, int
     p.lde = ep.lde;
     p.Dhi = ep.Dhi;
     p.Dlo = ep.Dlo;
+    p.sym = 0;   // every element is computed here
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     k_gemm_simt<T><<<grid, 256, 0, s>>>(X, ldx, Y, ldy, K, p, skip);
     count_launch();

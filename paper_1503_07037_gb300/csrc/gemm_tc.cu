@@ -88,6 +88,7 @@ struct TileRef {
     const CUtensorMap *mx, *my, *mxl, *myl;
     int m0, n0, num_k;
     bool skip;
+    bool diag;   // symmetric result: a tile on the block diagonal
 };
 
 // Tile t of the launch. A single problem uses the __grid_constant__ maps; a
@@ -157,10 +158,20 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // symmetric results (p.sym, square tiles) enumerate the upper-triangular tiles only
     auto tile = [&](int t) {
         TileRef r = tile_ref<GROUPED>(t, single, groups, G, &tmX, &tmY, &tmXl, &tmYl);
         const int lt = t - r.pr->tile_begin;
-        r.n0 = (lt / r.pr->num_mt) * BN;
+        r.diag = false;
+        if (BN == BM && r.pr->p.sym) {
+            int mi = 0, ni = 0;
+            tri_tile(lt, r.pr->num_mt, &mi, &ni);
+            r.m0 = mi * BM;
+            r.n0 = ni * BN;
+            r.diag = mi == ni;
+        } else {
+            r.n0 = (lt / r.pr->num_mt) * BN;
+        }
         return r;
     };
     // K is accumulated in TMEM in chunks of kc k-blocks (KCH = 0: the whole K)
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     pend.drain(BN / 4, dsum);
                     finish_pending();
                 }
-                pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, acc);
+                pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
             } else {
                 (void)nch;
                 const int b = g & 1;
@@ -404,7 +415,26 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     uint32_t rr[32];
                     tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
-                    if (m < p.M) {
+                    if (m < p.M && p.sym) {
+                        float local = 0.f;
+                        const int nb = r.n0 + c0;
+                        if (vec4 && !r.diag && nb + 32 <= p.N) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
+                                                    __uint_as_float(rr[j + 1]),
+                                                    __uint_as_float(rr[j + 2]),
+                                                    __uint_as_float(rr[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int n = nb + j;
+                                if (n < p.N)
+                                    local += epi_apply_sym(p, m, n, __uint_as_float(rr[j]), r.diag);
+                            }
+                        }
+                        dsum += (double)local;
+                    } else if (m < p.M) {
                         float local = 0.f;
                         const int nb = r.n0 + c0;
                         if (vec4 && nb + 32 <= p.N) {
@@ -502,7 +532,10 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     pr.num_mt = (M + BM - 1) / BM;
     pr.skip = skip;
     pr.maps = nullptr;
-    const int tiles = pr.num_mt * ((N + BN - 1) / BN);
+    // symmetric results need square tiles: upper-triangular tiles only
+    const bool sym = p.sym && BN == BM && M == N;
+    pr.p.sym = sym ? 1 : 0;
+    const int tiles = sym ? pr.num_mt * (pr.num_mt + 1) / 2 : pr.num_mt * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
     k_gemm_tc<BN, STAGES, PASSES, KCH, false><<<grid, C::THREADS, C::SMEM, s>>>(
         mx, my, mxl, myl, pr, nullptr, 1, tiles, device_error_word());
@@ -650,7 +683,13 @@ cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int
         set_error("tcgen05 GEMM needs an sm_103 device");
         return CDMPT_ERR_UNSUPPORTED;
     }
-    if (engine == CDMPT_GEMM_TC_TF32) return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
+    if (engine == CDMPT_GEMM_TC_TF32) {
+        // one pass over the hi arrays; 128- and 64-column tiles share the tensor maps
+        // of the split-TF32 engine with the same tile width (batched mixed precision)
+        if (bn == 128) return launch_grouped<128, 6, 1, 0>(problems, G, total_tiles, s);
+        if (bn == 64) return launch_grouped<64, 8, 1, 0>(problems, G, total_tiles, s);
+        return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
+    }
     if (bn == 64) return launch_grouped<64, 4, 3, 2>(problems, G, total_tiles, s);
     switch (split_chunk()) {
         case 1: return launch_grouped<128, 3, 3, 1>(problems, G, total_tiles, s);
@@ -715,6 +754,7 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
         p.lde = ep.lde;
         p.Dhi = ep.Dhi;
         p.Dlo = ep.Dlo;
+        p.sym = (ep.sym && M == N && ep.trans_block <= 0) ? 1 : 0;
         if (st == CDMPT_OK) st = gemm_tc_bf16(M, N, K, xb, ldx, yb, ldy, p, skip, s);
         cudaFreeAsync(buf, s);
         return st;
@@ -749,6 +789,19 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     p.lde = ep.lde;
     p.Dhi = ep.Dhi;
     p.Dlo = ep.Dlo;
+    p.sym = (ep.sym && M == N && ep.trans_block <= 0) ? 1 : 0;
+    if (p.sym) {
+        // symmetric result: square tiles, upper triangle only (TF32: 256 x 256 two-SM
+        // tiles; split TF32: 128 x 128 one-SM tiles without cluster pairs)
+        if (!three)
+            return gemm_tc_2sm(false, 0, M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
+        switch (split_chunk()) {
+            case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+            case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+            case 0: return launch<128, 3, 3, 0>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+            default: return launch<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+        }
+    }
     if (use_2sm(three) && M > BM)
         return gemm_tc_2sm(three, split_chunk(), M, N, K, xh, three ? X.lo : xh, ldx, yh, three ? Y.lo : yh,
                            ldy, p, skip, s);

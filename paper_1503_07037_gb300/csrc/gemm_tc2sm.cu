@@ -212,6 +212,16 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
     constexpr int KB = BF16 ? 2 * BK : BK;   // K elements per 128-byte k-block
     static_assert(!BF16 || PASSES == 1, "BF16 is one pass");
     const int num_k = (K + KB - 1) / KB;
+    // symmetric result with square 256 x 256 tiles: upper-triangular tiles only
+    const bool sym = p.sym && BN == 2 * BM;
+    auto tile_of = [&](int t, int* mt, int* nt) {
+        if (sym) {
+            tri_tile(t, num_mt, mt, nt);
+        } else {
+            *mt = t % num_mt;
+            *nt = t / num_mt;
+        }
+    };
     auto chunks = [&](int* kc) {
         *kc = KCH > 0 ? KCH : num_k;
         return (num_k + *kc - 1) / *kc;
@@ -261,8 +271,10 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             for (int t = cid; t < total_tiles && ok; t += ncl) {
-                const int m0 = (t % num_mt) * (2 * BM) + (int)rank * BM;
-                const int y0 = (t / num_mt) * BN + (int)rank * (BN / 2);
+                int mt = 0, nt = 0;
+                tile_of(t, &mt, &nt);
+                const int m0 = mt * (2 * BM) + (int)rank * BM;
+                const int y0 = nt * BN + (int)rank * (BN / 2);
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -348,8 +360,11 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
         uint32_t g = 0;
         PendingTile<BN> pend;   // chunked engine: finished tile parked in TMEM columns NB BN ..
         for (int t = cid; t < total_tiles; t += ncl) {
-            const int m = (t % num_mt) * (2 * BM) + (int)rank * BM + 32 * q + lane;
-            const int n0 = (t / num_mt) * BN;
+            int mt = 0, nt = 0;
+            tile_of(t, &mt, &nt);
+            const bool diag = sym && mt == nt;
+            const int m = mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
+            const int n0 = nt * BN;
             int kc = 0;
             const int nch = chunks(&kc);
             bool ok = true;
@@ -395,7 +410,7 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
                     pend.drain(BN / 4, dsum);
                     pend.p = nullptr;
                 }
-                pend.park(&p, lane_base + (uint32_t)(NB * BN), m, n0, acc);
+                pend.park(&p, lane_base + (uint32_t)(NB * BN), m, n0, diag, acc);
             } else {
                 (void)nch;
                 const int b = g & 1;
@@ -405,7 +420,26 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     uint32_t rr[32];
                     tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
-                    if (m < p.M) {
+                    if (m < p.M && sym) {
+                        float local = 0.f;
+                        const int nb = n0 + c0;
+                        if (vec4 && !diag && nb + 32 <= p.N) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
+                                                    __uint_as_float(rr[j + 1]),
+                                                    __uint_as_float(rr[j + 2]),
+                                                    __uint_as_float(rr[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int n = nb + j;
+                                if (n < p.N)
+                                    local += epi_apply_sym(p, m, n, __uint_as_float(rr[j]), diag);
+                            }
+                        }
+                        dsum += (double)local;
+                    } else if (m < p.M) {
                         float local = 0.f;
                         const int nb = n0 + c0;
                         if (vec4 && nb + 32 <= p.N) {
@@ -517,7 +551,10 @@ cdmpt_status launch_2sm(int M, int N, int K, const void* X, const void* Xl, int 
         return CDMPT_ERR_ARG;
     }
     const int num_mt = (M + 2 * BM - 1) / (2 * BM);
-    const int tiles = num_mt * ((N + BN - 1) / BN);
+    const bool sym = p.sym && BN == 2 * BM && M == N;
+    const int tiles = sym ? num_mt * (num_mt + 1) / 2 : num_mt * ((N + BN - 1) / BN);
+    EpiParams<float> pk = p;
+    pk.sym = sym ? 1 : 0;
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters);
@@ -531,7 +568,7 @@ cdmpt_status launch_2sm(int M, int N, int K, const void* X, const void* Xl, int 
     a.val.clusterDim.z = 1;
     cfg.attrs = &a;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, p, K, num_mt, tiles, skip,
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, pk, K, num_mt, tiles, skip,
                                        device_error_word());
     count_launch();
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -46,6 +46,10 @@ struct Epilogue {
     int lde = 0;
     T* Dhi = nullptr;      // optional TF32 hi/lo split of D (float only)
     T* Dlo = nullptr;
+    // symmetric result (M = N, C and E symmetric, no trans_block): the tcgen05
+    // engines compute only the upper-triangular tiles and mirror them; the
+    // other engines ignore the flag (they compute every element)
+    bool sym = false;
 };
 
 // A GEMM operand: the values and, for float storage, their TF32 split

@@ -151,6 +151,12 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
                              const Operand<T>& Y, T* D, const Epilogue<T>& ep, const double* skip,
                              int engine_override) {
     const int engine = engine_of(cx, engine_override);
+    // flops the product needs: a symmetric result on the tensor-core engines is
+    // computed on its upper-triangular tiles only, N (N + 1) K instead of 2 N^2 K
+    const bool sym_tc = ep.sym && M == Nc && (engine == CDMPT_GEMM_TC_TF32 ||
+                                              engine == CDMPT_GEMM_TC_3XTF32 ||
+                                              engine == CDMPT_GEMM_TC_BF16);
+    const double flops = sym_tc ? (double)M * (M + 1) * K : 2.0 * M * (double)Nc * K;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cx.profile) {
         while (cx.ev.size() < 2 * (cx.ev_used + 1)) {
@@ -165,7 +171,7 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
         }
         cx.ev_ok[cx.ev_used] = 1;
         cx.ev_engine[cx.ev_used] = engine;
-        cx.ev_flops[cx.ev_used] = 2.0 * M * (double)Nc * K;
+        cx.ev_flops[cx.ev_used] = flops;
         e0 = cx.ev[2 * cx.ev_used];
         e1 = cx.ev[2 * cx.ev_used + 1];
         CDMPT_CUDA_TRY(cudaEventRecord(e0, cx.stream));
@@ -185,7 +191,7 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
         ++cx.ev_used;
     }
     if (cx.st && skip == nullptr) {
-        const double f = 2.0 * M * (double)Nc * K;
+        const double f = flops;
         cx.st->gemm_launches += 1;
         cx.st->gemm_flops += f;
         cx.st->tensor_flops += tensor_factor(engine) * f;
@@ -220,6 +226,7 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
         ep.C = R_.x;
         ep.ldc = ld;
         ep.dot = sc + CG_RR;
+        ep.sym = a.sym && a.rows == N_;
         CDMPT_TRY(gemm(cx, a.rows, N_, N_, a.x0->op(), a.W->op(), R_.x, ep, nullptr, init_engine));
     } else {
         CDMPT_CUDA_TRY(cudaMemsetAsync(X, 0, count * sizeof(T), cx.stream));
@@ -244,6 +251,7 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
             ep.dot = sc + CG_PQ;
             ep.E = P_.x;
             ep.lde = ld;
+            ep.sym = a.sym && a.rows == N_;
             CDMPT_TRY(gemm(cx, a.rows, N_, N_, P_.op(), a.W->op(), Q_.x, ep, sc + CG_DONE,
                            iter_engine));
             CDMPT_TRY(Ew<T>::cg_update(X, R_.x, P_.x, Q_.x, count, sc, cx.stream));
@@ -259,7 +267,9 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
             for (size_t e = ev_first + ran; e < cx.ev_used; ++e) cx.ev_ok[e] = 0;
         }
         if (cx.st) {
-            const double f = 2.0 * a.rows * (double)N_ * N_;
+            const bool sym_tc = a.sym && a.rows == N_ && iter_engine != CDMPT_GEMM_SIMT;
+            const double f =
+                sym_tc ? (double)N_ * (N_ + 1) * N_ : 2.0 * a.rows * (double)N_ * N_;
             cx.st->gemm_launches += ran;
             cx.st->gemm_flops += ran * f;
             cx.st->tensor_flops += ran * tensor_factor(iter_engine) * f;
@@ -293,15 +303,17 @@ cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s
     CDMPT_TRY(Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo));
     int total = 0, hint = 1;
     for (int k = 0; k < n; ++k) {
-        {   // W_k = Z_k Z_k
+        {   // W_k = Z_k Z_k (symmetric)
             Epilogue<T> ep;
             ep.Dhi = W_[k].hi;
             ep.Dlo = W_[k].lo;
+            ep.sym = true;
             CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr, engine));
         }
-        {   // right side of the correction: -2 Z_k W_k
+        {   // right side of the correction: -2 Z_k W_k = -2 Z_k^3 (symmetric)
             Epilogue<T> ep;
             ep.alpha = -2.0;
+            ep.sym = true;
             CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, engine));
         }
         CgArgs a;
@@ -312,6 +324,7 @@ cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s
         a.maxit = o.cg_maxit;
         a.init_engine = a.iter_engine = engine;
         a.hint = hint;
+        a.sym = true;
         int it = 0;
         CDMPT_TRY(cg(cx, Z_[k + 1].x, a, &it, nullptr));   // d, in the Z_{k+1} buffer
         total += it;
@@ -337,12 +350,15 @@ cdmpt_status Solver<T>::refine(Context& cx, const cdmpt_opts& o, int n, int* cg_
             Epilogue<T> ep;
             ep.Dhi = W_[k].hi;
             ep.Dlo = W_[k].lo;
+            ep.sym = true;
             CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr,
                            CDMPT_GEMM_TC_3XTF32));
         }
         // accurate residual r = 2 Z_k - Z_{k+1} - Z_{k+1} W_k of the stored Z_{k+1}
         CDMPT_TRY(Ew<T>::lincomb(S_.x, Z_[k].x, 2.0, Z_[k + 1].x, -1.0, blk_, cx.stream));
-        {
+        {   // full tiles: the stored Z_{k+1} differs from the exact one by an error that
+            // does not commute with W_k, so Z_{k+1} W_k is not symmetric and its upper
+            // triangle alone would change the correction at first order
             Epilogue<T> ep;
             ep.alpha = -1.0;
             ep.beta = 1.0;
@@ -403,6 +419,7 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
     ep.gamma = 0.25 * beta;
     ep.Dhi = RHS_.hi;
     ep.Dlo = RHS_.lo;
+    ep.sym = true;
     CDMPT_TRY(gemm(cx, N, N, N, Z_[n].op(), Z_[n].op(), RHS_.x, ep, nullptr, acc));
     CgArgs a;   // (I - W_0) Q = beta/4 (I - Z_n^2), i.e. operator X - X W_0
     a.W = &W_[0];
@@ -414,6 +431,7 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
     a.tol = o.cg_tol;
     a.maxit = o.cg_maxit;
     a.init_engine = a.iter_engine = acc;
+    a.sym = true;
     int it = 0;
     CDMPT_TRY(cg(cx, Qmu_.x, a, &it, nullptr));
     st.cg_iterations_q = it;

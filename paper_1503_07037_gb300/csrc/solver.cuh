@@ -89,6 +89,9 @@ private:
         int init_engine = 0;            // engine of the initial residual (0: context default)
         int iter_engine = 0;            // engine of the iterations
         int hint = 1;                   // iterations expected (first chunk size)
+        // symmetric iterates: rhs and x0 symmetric and commuting with W (every
+        // 0th-order solve), so each product is computed on upper-triangular tiles
+        bool sym = false;
     };
     cdmpt_status gemm(Context& cx, int M, int Nc, int K, const Operand<T>& X,
                       const Operand<T>& Y, T* D, const Epilogue<T>& ep, const double* skip,

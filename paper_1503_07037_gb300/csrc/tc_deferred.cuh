@@ -20,10 +20,11 @@ struct PendingTile {
     uint32_t sbuf = 0;                     // TMEM address of this warp's lanes, buffer column 0
     int m = 0, n0 = 0, next = 0;           // row of this lane, first column, next 4-column group
     bool vec4 = false;
+    bool diag = false;                     // diagonal tile of a symmetric result
 
     // Parks a finished tile: acc holds this lane's row, columns n0 .. n0 + BN - 1.
     __device__ __forceinline__ void park(const EpiParams<float>* pp, uint32_t sb, int mm, int nn0,
-                                         const float (&acc)[BN]) {
+                                         bool dg, const float (&acc)[BN]) {
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 32) tmem_st32(sb + (uint32_t)c0, acc + c0);
         tmem_wait_st();
@@ -32,7 +33,8 @@ struct PendingTile {
         m = mm;
         n0 = nn0;
         next = 0;
-        vec4 = epi_vec4_ok(*pp) && nn0 + BN <= pp->N;
+        diag = dg;
+        vec4 = epi_vec4_ok(*pp) && nn0 + BN <= pp->N && !(pp->sym && dg);
     }
 
     // Stores up to `groups` groups of four columns (warp-collective); adds the
@@ -47,6 +49,11 @@ struct PendingTile {
                 if (vec4) {
                     local = epi_apply4(*p, m, n, __uint_as_float(v[0]), __uint_as_float(v[1]),
                                        __uint_as_float(v[2]), __uint_as_float(v[3]));
+                } else if (p->sym) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (n + i < p->N)
+                            local += epi_apply_sym(*p, m, n + i, __uint_as_float(v[i]), diag);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 4; ++i)

@@ -239,6 +239,18 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
         : "memory");
 }
 
+// Tile t (0-based) of the upper triangle (mi <= ni) of a T x T tile grid, row by row.
+__device__ __forceinline__ void tri_tile(int t, int T, int* mi, int* ni) {
+    int i = 0, len = T;
+    while (t >= len && len > 0) {
+        t -= len;
+        ++i;
+        --len;
+    }
+    *mi = i;
+    *ni = i + t;
+}
+
 // Stores 32 consecutive columns of this warp's 32 TMEM lanes (one row per lane).
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
     asm volatile(

@@ -86,3 +86,22 @@ def test_batch_tuner_and_graph(cuda, cdmpt_lib):
                                             r["P1"][i][d].cpu().numpy()) < 1e-5
     ref = oracle.solve(probs[5].H0, probs[5].H1, probs[5].beta, probs[5].nocc, n=12, kind="rec")
     assert oracle.rel_frobenius(r["P0"][5].cpu().numpy(), ref["P0"]) < 1e-5
+
+
+def test_batch_mixed_precision_matches_oracle(cuda, cdmpt_lib):
+    """CDMPT_MIXED_TF32 batches: one-pass TF32 sweeps, refined trajectories (per-system Newton
+    steps on mu), split-TF32 response; each system against the oracle at the mixed bar."""
+    probs = syn.clusters(B=5, seed=5005, sizes=[128, 420, 333, 96, 700], n=12)
+    b = cdmpt_lib.Batch([p.N for p in probs], 3, precision="mixed")
+    b.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
+    r = b.solve([p.beta for p in probs], [p.nocc for p in probs], 12)
+    st = b.stats()
+    assert st["cg_iterations_refine"] > 0
+    for i, p in enumerate(probs):
+        ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+        e0 = oracle.rel_frobenius(r["P0"][i].cpu().numpy(), ref["P0"])
+        assert e0 < 1e-6, (i, e0)
+        for d in range(3):
+            e1 = oracle.rel_frobenius(r["P1"][i][d].cpu().numpy(), ref["P1"][d])
+            assert e1 < 1e-6, (i, d, e1)
+    b.close()

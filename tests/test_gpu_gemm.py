@@ -169,3 +169,43 @@ def test_gemm_bf16_rejects_unaligned_ld(cuda, cdmpt_lib):
     D = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
     with pytest.raises(cdmpt_lib.CdmptError):
         cdmpt_lib.gemm_f32(X, X, D, engine="bf16", K=36)
+
+
+@pytest.mark.parametrize("engine", ["3xtf32", "tf32", "bf16"])
+@pytest.mark.parametrize("N", [128, 300, 1024, 1100])
+def test_gemm_symmetric_result(cuda, cdmpt_lib, engine, N):
+    """trans_block = -1 (symmetric result): only upper-triangular tiles are computed and
+    mirrored. For commuting symmetric factors (Z and Z^3) with symmetric C and E the result
+    equals the full product within the engine's tolerance, is exactly symmetric, and the
+    fused dot counts both halves."""
+    import torch
+    rng = np.random.default_rng(N + len(engine))
+    ld = (N + 7) // 8 * 8
+    Z = rng.standard_normal((N, N)) / np.sqrt(N)
+    Z = 0.5 * (Z + Z.T)
+    Y = Z @ Z @ Z
+    S = rng.standard_normal((N, N))
+    S = 0.5 * (S + S.T)
+    E = rng.standard_normal((N, N))
+    E = 0.5 * (E + E.T)
+
+    def pad(A):
+        B = np.zeros((N, ld), dtype=np.float32)
+        B[:, :N] = A
+        return torch.from_numpy(B).cuda()
+
+    dev = torch.device("cuda")
+    D = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+    dot = torch.zeros(1, dtype=torch.float64, device=dev)
+    cdmpt_lib.gemm_f32(pad(Z), pad(Y), D, alpha=-2.0, beta=0.5, C=pad(S), gamma=0.25,
+                       trans_block=-1, dot=dot, E=pad(E), engine=engine, M=N, Ncols=N, K=N)
+    torch.cuda.synchronize()
+    got = D.cpu().numpy()[:, :N].astype(np.float64)
+    Zf = Z.astype(np.float32).astype(np.float64)
+    Yf = Y.astype(np.float32).astype(np.float64)
+    ref = -2.0 * Zf @ Yf.T + 0.5 * S.astype(np.float32) + 0.25 * np.eye(N)
+    tol = {"3xtf32": 4e-6, "tf32": 3e-3, "bf16": 1e-2}[engine]
+    assert np.array_equal(got, got.T)
+    assert _rel(got, ref) < tol
+    want = float(np.sum(got * E.astype(np.float32)))
+    assert abs(float(dot.item()) - want) < 1e-5 * max(1.0, abs(want))
