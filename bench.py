@@ -43,7 +43,7 @@ WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
 # DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
 # profiles/ (per engine); None until the kernel's counters are re-taken after a change
-TRAFFIC = {2: 233.8e6, 3: 996.0e6}   # TF32 two-SM, 3xTF32 chunk 2 (profiles/gemm_*_n4096.md)
+TRAFFIC = {2: None, 3: None}
 
 
 def dist_env():
@@ -445,34 +445,41 @@ def run_chain(pkg, pk):
 
 
 def run_batched(pkg, args, barrier):
-    """One grouped batch solve of the 96-cluster workload vs the same systems one by one."""
-    import numpy as np
+    """The 96-cluster workload as one lockstep batch (FP32 and mixed precision), against the
+    same systems solved one at a time (split-TF32 FP32 and CUDA-core FFMA FP32)."""
     import torch
 
     import synthetic
     probs = synthetic.clusters(B=96, seed=1005, beta=20.0, n=12)
     sizes = [p.N for p in probs]
-    bt = pkg.Batch(sizes, 3)
-    bt.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
     betas = [p.beta for p in probs]
     noccs = [p.nocc for p in probs]
-    bt.solve(betas, noccs, 12)                 # warm-up (descriptor and map caches)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record()
-    r = bt.solve(betas, noccs, 12)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    st = bt.stats()
-    out = {"workload": "96 clusters, N_b ~ U{128..1536} (seed 1005), D = 3, beta 20, n 12, FP32 "
-                       "split-TF32, one grouped tcgen05 launch per product, CG iterations as a "
-                       "CUDA graph, tile width from the autotuner",
-           "tuning": bt.tuning(),
-           "solves_per_s": 96 / (ms / 1e3), "ms": ms, "sum_N3": float(sum(float(N) ** 3 for N in sizes)),
-           "mu_sweeps": st["mu_iterations"], "kernel_launches": st["kernel_launches"],
-           "algorithmic_tflops": st["gemm_flops"] / (ms / 1e3) / 1e12}
+    out = {"workload": "96 clusters, N_b ~ U{128..1536} (seed 1005), D = 3, beta 20, n 12; one "
+                       "grouped tcgen05 launch per product, CG iterations as a CUDA graph, tile "
+                       "width from the autotuner",
+           "sum_N3": float(sum(float(N) ** 3 for N in sizes))}
+    results = {}
+    for prec in ("fp32", "mixed"):
+        bt = pkg.Batch(sizes, 3, precision=prec)
+        bt.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
+        bt.solve(betas, noccs, 12)                 # warm-up (descriptor and map caches)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record()
+        r = bt.solve(betas, noccs, 12)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = bt.stats()
+        out[prec] = {"solves_per_s": 96 / (ms / 1e3), "ms": ms, "mu_sweeps": st["mu_iterations"],
+                     "cg_sweeps": st["cg_iterations_sweeps"],
+                     "cg_refine": st["cg_iterations_refine"],
+                     "kernel_launches": st["kernel_launches"],
+                     "algorithmic_tflops": st["gemm_flops"] / (ms / 1e3) / 1e12,
+                     "tuning": bt.tuning()}
+        results[prec] = r
+        bt.close()
     # the same systems solved one at a time through the single-system path
     t0 = time.perf_counter()
     with pkg.Handle(precision="fp32") as h:
@@ -480,20 +487,35 @@ def run_batched(pkg, args, barrier):
             h.set_H(p.H0, p.H1)
             h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
     torch.cuda.synchronize()
-    seq = time.perf_counter() - t0
-    out["sequential_solves_per_s"] = 96 / seq
+    out["sequential_fp32_3xtf32_solves_per_s"] = 96 / (time.perf_counter() - t0)
+    # CUDA-core FFMA FP32 one at a time: a bounded sample (the first 24 systems)
+    sample = probs[:24]
+    t0 = time.perf_counter()
+    with pkg.Handle(precision="fp32", engine="simt") as h:
+        for p in sample:
+            h.set_H(p.H0, p.H1)
+            h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["sequential_fp32_ffma_solves_per_s"] = len(sample) / dt * (
+        sum(float(p.N) ** 3 for p in sample) / len(sample)) / (out["sum_N3"] / 96)
+    out["sequential_fp32_ffma_note"] = ("first 24 systems, scaled to the batch's mean N^3")
+    out["mixed_batched_vs_sequential_fp32_ffma"] = (out["mixed"]["solves_per_s"] /
+                                                    out["sequential_fp32_ffma_solves_per_s"])
+    out["mixed_batched_vs_fp32_batched"] = (out["mixed"]["solves_per_s"] /
+                                            out["fp32"]["solves_per_s"])
     if not args.no_cpu_baseline:
         import oracle
-        worst = 0.0
-        for i in (0, 17, 53, 95):
-            p = probs[i]
-            ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-            worst = max(worst, oracle.rel_frobenius(r["P0"][i].cpu().numpy(), ref["P0"]),
-                        max(oracle.rel_frobenius(r["P1"][i][d].cpu().numpy(), ref["P1"][d])
-                            for d in range(3)))
-        out["max_err_sampled_systems"] = worst
+        for prec, r in results.items():
+            worst = 0.0
+            for i in (0, 17, 53, 95):
+                p = probs[i]
+                ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+                worst = max(worst, oracle.rel_frobenius(r["P0"][i].cpu().numpy(), ref["P0"]),
+                            max(oracle.rel_frobenius(r["P1"][i][d].cpu().numpy(), ref["P1"][d])
+                                for d in range(3)))
+            out[prec]["max_err_sampled_systems"] = worst
         out["sampled_systems"] = [0, 17, 53, 95]
-    bt.close()
     return out
 
 

@@ -1046,8 +1046,13 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 const double trP = 0.5 * (sy.N + b->pinned[i * kSlots + B_TRZ]);
                 const double zz = b->pinned[i * kSlots + B_ZZ];
                 const double err = trP - sy.nocc;
-                // refined traces are good to about 1e-9 N: finish mu that far
-                const double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-9 * sy.N;
+                // finish mu to 1e-9 N, or to the FP32 noise of the trace (about
+                // 1e-7 sqrt(N) for a refined trajectory) once the passes are done
+                const double tol = b->opts.occ_tol > 0
+                                       ? b->opts.occ_tol
+                                       : std::max(1e-9 * sy.N, pass + 1 >= min_pass
+                                                                   ? 1e-7 * std::sqrt((double)sy.N)
+                                                                   : 0.0);
                 const bool occ_ok = std::fabs(err) <= tol;
                 if (occ_ok && pass + 1 >= min_pass) {
                     sy.converged = true;

@@ -816,8 +816,13 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             const double err = trP - nocc;
             st.trace_P0 = trP;
             st.occupation_error = std::fabs(err);
-            // refined traces are good to about 1e-9 N: finish mu that far
-            const bool occ_ok = std::fabs(err) <= (o.occ_tol > 0 ? occ_tol : 1e-9 * N);
+            // finish mu to 1e-9 N, or to the FP32 noise of the trace (about 1e-7 sqrt(N)
+            // for a refined trajectory) once the minimum passes are done
+            const double tol_ref =
+                o.occ_tol > 0 ? occ_tol
+                              : std::max(1e-9 * N, pass + 1 >= min_pass ? 1e-7 * std::sqrt((double)N)
+                                                                         : 0.0);
+            const bool occ_ok = std::fabs(err) <= tol_ref;
             if (occ_ok && pass + 1 >= min_pass && worst < 1e-4) {
                 done = true;
                 break;

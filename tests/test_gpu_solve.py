@@ -102,6 +102,22 @@ def test_mixed_bf16_cubic16_full_size(cuda, cdmpt_lib):
     _check(_run(cdmpt_lib, p, "mixed_bf16"), ref, BAR["mixed"], 1)
 
 
+def test_mixed_small_system(cuda, cdmpt_lib):
+    """Mixed precision on a small cluster (N = 96). The refined trace carries FP32 noise near
+    1e-9 relative, and the refinement must still finish. The levels lie within 0.14 kT of mu,
+    so P1 sits at the FP32 storage floor: FP32 with split products gives 2e-6 to 5.5e-6 here.
+    P0 is held to the mixed bar; P1 to max(mixed bar, 1.3 x the FP32 error of the same system)."""
+    p = syn.clusters(B=1, seed=6006, sizes=[96], beta=20.0, n=12)[0]
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    rm = _run(cdmpt_lib, p, "mixed")
+    rf = _run(cdmpt_lib, p, "fp32")
+    assert _rel(rm["P0"], ref["P0"]) < BAR["mixed"]
+    for d in range(p.H1.shape[0]):
+        ef = _rel(rf["P1"][d], ref["P1"][d])
+        em = _rel(rm["P1"][d], ref["P1"][d])
+        assert em < max(BAR["mixed"], 1.3 * ef), (d, em, ef)
+
+
 def test_tf32_single_pass_is_coarse(cuda, cdmpt_lib):
     """One TF32 pass per product (no refinement) lands near 1e-4, far from the FP32 bar."""
     p = syn.cubic_lattice((10, 10, 10), seed=1002, beta=20.0, n=14)
