@@ -43,7 +43,7 @@ WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
 # DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
 # profiles/ (per engine); None until the kernel's counters are re-taken after a change
-TRAFFIC = {2: None, 3: None}
+TRAFFIC = {2: None, 3: 996.2e6}   # per launch at N = 4096 (3xTF32 captured on the current kernel)
 
 
 def dist_env():
@@ -51,6 +51,16 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def reduce_max(pg, x, device):
+    """Maximum of a host scalar over all ranks (x itself without a process group)."""
+    if not pg:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -207,11 +217,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(pg, x, dev)
 
     probs = problems()
     N, D = probs[0].N, probs[0].D
@@ -332,7 +338,7 @@ def run_ours(args):
     # batched workload: 96 disordered clusters, N_b ~ U{128..1536}, 3 directions, beta 20, n 12
     batched = None
     if not args.no_batch:
-        batched = run_batched(pkg, args, barrier)
+        batched = run_batched(pkg, args, barrier, max_over_ranks, rank, world)
 
     # the N = 8192 product chain: one mixed solve of the banded workload, per-engine rates
     chain = None
@@ -444,20 +450,26 @@ def run_chain(pkg, pk):
     return out
 
 
-def run_batched(pkg, args, barrier):
+def run_batched(pkg, args, barrier, max_over_ranks=lambda x: x, rank=0, world=1):
     """The 96-cluster workload as one lockstep batch (FP32 and mixed precision), against the
-    same systems solved one at a time (split-TF32 FP32 and CUDA-core FFMA FP32)."""
+    same systems solved one at a time (split-TF32 FP32 and CUDA-core FFMA FP32). With several
+    ranks each solves its LPT share of the clusters (no exchange) and the time is the slowest
+    rank's: the batch leg scales strongly."""
     import torch
 
     import synthetic
-    probs = synthetic.clusters(B=96, seed=1005, beta=20.0, n=12)
+    from paper_1503_07037_gb300.shard import cube_weights, lpt_partition
+    all_probs = synthetic.clusters(B=96, seed=1005, beta=20.0, n=12)
+    share = lpt_partition(cube_weights([p.N for p in all_probs]), world)[rank]
+    probs = [all_probs[i] for i in share]
     sizes = [p.N for p in probs]
     betas = [p.beta for p in probs]
     noccs = [p.nocc for p in probs]
     out = {"workload": "96 clusters, N_b ~ U{128..1536} (seed 1005), D = 3, beta 20, n 12; one "
                        "grouped tcgen05 launch per product, CG iterations as a CUDA graph, tile "
                        "width from the autotuner",
-           "sum_N3": float(sum(float(N) ** 3 for N in sizes))}
+           "sum_N3": float(sum(float(p.N) ** 3 for p in all_probs)),
+           "ranks": world, "systems_on_rank0": len(probs)}
     results = {}
     for prec in ("fp32", "mixed"):
         bt = pkg.Batch(sizes, 3, precision=prec)
@@ -470,7 +482,7 @@ def run_batched(pkg, args, barrier):
         r = bt.solve(betas, noccs, 12)
         ev1.record()
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
         st = bt.stats()
         out[prec] = {"solves_per_s": 96 / (ms / 1e3), "ms": ms, "mu_sweeps": st["mu_iterations"],
                      "cg_sweeps": st["cg_iterations_sweeps"],
@@ -487,7 +499,7 @@ def run_batched(pkg, args, barrier):
             h.set_H(p.H0, p.H1)
             h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
     torch.cuda.synchronize()
-    out["sequential_fp32_3xtf32_solves_per_s"] = 96 / (time.perf_counter() - t0)
+    out["sequential_fp32_3xtf32_solves_per_s"] = 96 / max_over_ranks(time.perf_counter() - t0)
     # CUDA-core FFMA FP32 one at a time: a bounded sample (the first 24 systems)
     sample = probs[:24]
     t0 = time.perf_counter()
@@ -497,25 +509,25 @@ def run_batched(pkg, args, barrier):
             h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    out["sequential_fp32_ffma_solves_per_s"] = len(sample) / dt * (
+    out["sequential_fp32_ffma_solves_per_s"] = world * len(sample) / max_over_ranks(dt) * (
         sum(float(p.N) ** 3 for p in sample) / len(sample)) / (out["sum_N3"] / 96)
     out["sequential_fp32_ffma_note"] = ("first 24 systems, scaled to the batch's mean N^3")
     out["mixed_batched_vs_sequential_fp32_ffma"] = (out["mixed"]["solves_per_s"] /
                                                     out["sequential_fp32_ffma_solves_per_s"])
     out["mixed_batched_vs_fp32_batched"] = (out["mixed"]["solves_per_s"] /
                                             out["fp32"]["solves_per_s"])
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and rank == 0:
         import oracle
         for prec, r in results.items():
             worst = 0.0
-            for i in (0, 17, 53, 95):
+            for i in range(0, len(probs), max(1, len(probs) // 4))[:4]:
                 p = probs[i]
                 ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
                 worst = max(worst, oracle.rel_frobenius(r["P0"][i].cpu().numpy(), ref["P0"]),
                             max(oracle.rel_frobenius(r["P1"][i][d].cpu().numpy(), ref["P1"][d])
                                 for d in range(3)))
             out[prec]["max_err_sampled_systems"] = worst
-        out["sampled_systems"] = [0, 17, 53, 95]
+        out["sampled_systems"] = "4 evenly spaced systems of rank 0's share"
     return out
 
 

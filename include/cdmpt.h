@@ -90,6 +90,10 @@ typedef struct {
     double mu_guess;
     int profile;        /* 1: time every GEMM launch with CUDA events (see cdmpt_stats) */
     void* stream;       /* cudaStream_t for all work of this handle; NULL = default stream */
+    int grand_canonical; /* 1: grand-canonical solve at the fixed mu = mu_guess (needs
+                            have_mu_guess): one occupation sweep, no mu update, mu1 = 0 (the
+                            fixed-mu scheme Sec. II mentions beside Algorithm 1); nocc is
+                            ignored. Batches are always canonical. */
 } cdmpt_opts;
 
 typedef struct {

@@ -392,7 +392,8 @@ def _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad):
 
 
 def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
-              close: float = 1.0, quad: float = 1.0, batch: int = 1024):
+              close: float = 1.0, quad: float = 1.0, batch: int = 1024, canonical: bool = True,
+              mu: Optional[float] = None):
     """Second-order canonical response P2 = (1/2) d^2 P / d lambda^2 of P(H0 + lambda H1).
 
     Second-order Daleckii-Krein formula in the eigenbasis of H0, with
@@ -407,6 +408,8 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     Returns the first-order results of ``solve`` plus P2 (D, N, N), mu2 (D,)
     and grad_alpha = -4 P2 (d alpha_d / d H0, by the symmetry of the third
     derivatives of the canonical free energy, whose gradient is P0).
+    canonical=False keeps mu fixed (given by ``mu``, else found from nocc):
+    mu1 = mu2 = 0, the grand-canonical response.
     """
     H0 = np.asarray(H0, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
@@ -414,7 +417,7 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
         H1 = H1[None]
     nn = n if kind == "rec" else None
     eps, V = np.linalg.eigh(H0) if eig is None else eig
-    base = solve(H0, H1, beta, nocc, n, kind, eig=(eps, V))
+    base = solve(H0, H1, beta, nocc, n, kind, canonical=canonical, mu=mu, eig=(eps, V))
     mu = base["mu"]
     F = divided_differences(eps, mu, beta, nn)
     fp = np.diag(F).copy()
@@ -433,7 +436,7 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
             J = cj[s0:s0 + batch]
             F3 = _second_dd_for_pairs(I, J, eps, F, mu, beta, nn, quad)
             S[I, J] = np.sum(F3 * ht[I, :] * ht[:, J].T, axis=1)
-        mu2[d] = float(np.trace(S) / np.sum(fp))
+        mu2[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
         P2[d] = V @ (S - mu2[d] * np.diag(fp)) @ V.T
     out = dict(base)
     out.update(P2=P2, mu2=mu2, grad_alpha=-4.0 * P2)

@@ -45,6 +45,7 @@ class Opts(ctypes.Structure):
         ("mu_guess", ctypes.c_double),
         ("profile", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("grand_canonical", ctypes.c_int),
     ]
 
 
@@ -286,7 +287,7 @@ class Handle:
 
     def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
                  refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
-                 stream=None):
+                 stream=None, grand_canonical=False):
         o = default_opts()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.gemm_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
@@ -299,6 +300,7 @@ class Handle:
         o.mu_guess = 0.0 if mu_guess is None else float(mu_guess)
         o.profile = 1 if profile else 0
         o.stream = _stream_ptr(stream)
+        o.grand_canonical = 1 if grand_canonical else 0
         self.opts = o
         self.h = create(o)
         self.N = 0

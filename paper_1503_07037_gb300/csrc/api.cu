@@ -92,6 +92,7 @@ bool valid_opts(const cdmpt_opts* o) {
     if (o->precision < CDMPT_FP64 || o->precision > CDMPT_MIXED_BF16) return false;
     if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_BF16) return false;
     if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
+    if (o->grand_canonical && !o->have_mu_guess) return false;
     return true;
 }
 
@@ -119,6 +120,7 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
     o->mu_guess = 0.0;
     o->profile = 0;
     o->stream = nullptr;
+    o->grand_canonical = 0;
     return CDMPT_OK;
 }
 
@@ -223,7 +225,8 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
                          double* P1, double* mu, double* mu1, int out_on_device) {
     if (!h) return CDMPT_ERR_ARG;
     if (h->N < 1) return fail_msg(h, CDMPT_ERR_ARG, "solve: call cdmpt_set_H first");
-    if (!(beta > 0) || !(nocc > 0) || !(nocc < h->N) || n < 1 || n > 60)
+    const bool gc = h->opts.grand_canonical != 0;   // nocc unused at fixed mu
+    if (!(beta > 0) || (!gc && (!(nocc > 0) || !(nocc < h->N))) || n < 1 || n > 60)
         return fail_msg(h, CDMPT_ERR_ARG, "solve: need beta > 0, 0 < nocc < N, 1 <= n <= 60");
     std::memset(&h->st, 0, sizeof(h->st));
     h->st.N = h->N;

@@ -691,7 +691,8 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
         for (int i = 0; i < G; ++i)
             if (!b->sys[i].converged) add_flops(b, 2.0 * sym_flops(b, b->sys[i].N), engine);
         int it = 0;
-        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, tol, skip, hint, &it, true, engine));
+        // mirrored CG products only in the one-pass sweeps of mixed precision (refined later)
+        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, tol, skip, hint, &it, engine != kEngine, engine));
         total += it;
         hint = std::max(1, it);
         CDMPT_TRY(run_ew(b, G_AXPBY, dz));

@@ -596,7 +596,7 @@ cdmpt_status Ew<T>::to_f64(double* out, int ldo, const T* in, int ldi, int N, in
 }
 
 template <typename T>
-cdmpt_status Ew<T>::diag_dot(const T* A, const double* H, int N, int ld, int ldh, double* out,
+cdmpt_status Ew<T>::dot_h(const T* A, const double* H, int N, int ld, int ldh, double* out,
                              cudaStream_t s) {
     k_dot_f64h<T><<<grid_for((size_t)N * N), kThreads, 0, s>>>(A, H, N, ld, ldh, out);
     LAUNCH_CHECK();

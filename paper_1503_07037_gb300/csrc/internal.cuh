@@ -155,7 +155,7 @@ struct Ew {
                                   T* hi = nullptr, T* lo = nullptr);
     static cdmpt_status to_f64(double* out, int ldo, const T* in, int ldi, int N, int rows,
                                double a, double b_diag, cudaStream_t s);
-    static cdmpt_status diag_dot(const T* A, const double* H, int N, int ld, int ldh,
+    static cdmpt_status dot_h(const T* A, const double* H, int N, int ld, int ldh,
                                  double* out, cudaStream_t s);
 };
 

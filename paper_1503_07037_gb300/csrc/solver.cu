@@ -324,7 +324,10 @@ cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s
         a.maxit = o.cg_maxit;
         a.init_engine = a.iter_engine = engine;
         a.hint = hint;
-        a.sym = true;
+        // mirrored CG products only in the one-pass sweeps that are refined afterwards:
+        // the iterates drift from commuting with W_k at rounding level, and the mirrored
+        // operator is then not self-adjoint (measured: FP32-mode P1 errors doubled)
+        a.sym = engine == CDMPT_GEMM_TC_TF32 || engine == CDMPT_GEMM_TC_BF16;
         int it = 0;
         CDMPT_TRY(cg(cx, Z_[k + 1].x, a, &it, nullptr));   // d, in the Z_{k+1} buffer
         total += it;
@@ -504,13 +507,15 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
         }
         CDMPT_TRY(Ew<T>::symmetrize(Zh_.x, N, ld, 1, cx.stream));
     }
-    if (!q_valid_) CDMPT_TRY(compute_q(cx));
+    // canonical: mu follows H0 through Tr P0 = N_occ (the Q term); grand canonical: fixed mu
+    const bool gc = o.grand_canonical != 0;
+    if (!q_valid_ && !gc) CDMPT_TRY(compute_q(cx));
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, 2 * sizeof(double), cx.stream));
-    CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+    if (!gc) CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
     CDMPT_TRY(Ew<T>::trace(Zh_.x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
     CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
     const double trQ = cx.pinned[S_TRQ], trZh = cx.pinned[S_TRQ + 1];
-    const double c = trQ > 0 ? last_s2_ * trZh / trQ : 0.0;
+    const double c = (!gc && trQ > 0) ? last_s2_ * trZh / trQ : 0.0;
     CDMPT_TRY(Ew<T>::lincomb(Zh_.x, Zh_.x, -last_s2_, Qmu_.x, c, blk_, cx.stream));
     CDMPT_TRY(Ew<T>::to_f64(grad, N, Zh_.x, ld, N, N, 1.0, 0.0, cx.stream));
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
@@ -628,12 +633,13 @@ cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const do
     const int acc = last_acc_;
     const cdmpt_opts& o = last_opts_;
     CDMPT_TRY(reserve_response2(n));
-    if (!q_valid_) CDMPT_TRY(compute_q(cx));
+    const bool gc = o.grand_canonical != 0;   // fixed mu: mu2 = 0, no Q term
+    if (!q_valid_ && !gc) CDMPT_TRY(compute_q(cx));
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, sizeof(double), cx.stream));
-    CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+    if (!gc) CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
     CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
     const double trQ = cx.pinned[S_TRQ];
-    if (!(trQ > 0)) {
+    if (!gc && !(trQ > 0)) {
         set_error("second-order response: Tr dP0/dmu is not positive");
         return CDMPT_ERR_NO_CONVERGENCE;
     }
@@ -707,10 +713,10 @@ cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const do
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
         CDMPT_TRY(Ew<T>::trace(Z2->x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
         CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-        const double mu2 = -0.5 * cx.pinned[S_TRQ + 1] / trQ;
+        const double mu2 = gc ? 0.0 : -0.5 * cx.pinned[S_TRQ + 1] / trQ;
         if (mu2_out) mu2_out[d] = mu2;
         // Z2 += 2 mu2 Q  (P2 = Z2 / 2)
-        CDMPT_TRY(Ew<T>::axpby(Z2->x, Qmu_.x, blk_, 2.0 * mu2, 1.0, nullptr, cx.stream));
+        if (!gc) CDMPT_TRY(Ew<T>::axpby(Z2->x, Qmu_.x, blk_, 2.0 * mu2, 1.0, nullptr, cx.stream));
         if (P2)
             CDMPT_TRY(Ew<T>::to_f64(P2 + (size_t)d * N * N, N, Z2->x, ld, N, N, 0.5, 0.0,
                                     cx.stream));
@@ -759,8 +765,18 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     const int fast = mixed ? (bf16 ? (int)CDMPT_GEMM_TC_BF16 : (int)CDMPT_GEMM_TC_TF32) : acc;
     const double pad = std::min(40.0 / beta, 0.45 * (1.0 / s2 - width));
     double lo = gmin - pad, hi = gmax + pad;
+    const bool gc = o.grand_canonical != 0;   // fixed mu: no occupation loop, mu1 = 0
     double mu = o.have_mu_guess ? o.mu_guess : trH0 / N;
-    mu = std::min(std::max(mu, lo + 1e-3 * pad), hi - 1e-3 * pad);
+    if (gc) {
+        // X_0 keeps its spectrum in [0, 1] iff |eps - mu| < 2^(n+1) / beta over the spectrum
+        if (!(gmax - mu < 1.0 / s2 && mu - gmin < 1.0 / s2)) {
+            set_error("grand canonical: mu = " + std::to_string(mu) +
+                      " puts X_0 outside [0, 1]; use more recursion steps");
+            return CDMPT_ERR_RANGE;
+        }
+    } else {
+        mu = std::min(std::max(mu, lo + 1e-3 * pad), hi - 1e-3 * pad);
+    }
     const double occ_tol = o.occ_tol > 0 ? o.occ_tol : N * (sizeof(T) == 8 ? 1e-12 : 1e-7);
     // one-pass TF32 traces are good to about 1e-4 relative, BF16 ones to about 1e-2;
     // the refinement finishes mu
@@ -778,7 +794,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         st.cg_iterations_sweeps += iters;
         st.cg_iterations_last_sweep = iters;
         CDMPT_TRY(occupation(cx, n, &trP, &zz));
-        const double err = trP - nocc;
+        const double err = gc ? 0.0 : trP - nocc;
         st.mu = mu;
         st.trace_P0 = trP;
         st.occupation_error = std::fabs(err);
@@ -813,7 +829,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             CDMPT_TRY(refine(cx, o, n, &iters, &worst));
             st.cg_iterations_refine += iters;
             CDMPT_TRY(occupation(cx, n, &trP, &zz));
-            const double err = trP - nocc;
+            const double err = gc ? 0.0 : trP - nocc;
             st.trace_P0 = trP;
             st.occupation_error = std::fabs(err);
             // finish mu to 1e-9 N, or to the FP32 noise of the trace (about 1e-7 sqrt(N)
@@ -900,23 +916,25 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         }
         st.cg_iterations_response = total;
 
-        CDMPT_TRY(compute_q(cx));
+        if (!gc) CDMPT_TRY(compute_q(cx));
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, (S_NSLOTS - S_TRQ) * sizeof(double),
                                        cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+        if (!gc) CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
         CDMPT_TRY(Ew<T>::trace(Z1->x, N, ld, D, sc_ + S_TRZ1, cx.stream));
         CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
         const double trQ = cx.pinned[S_TRQ];
         st.trace_Q = trQ;
         for (int d = 0; d < D; ++d) {
             const double trP1 = 0.5 * cx.pinned[S_TRZ1 + d];
-            const double mu1 = trQ > 0 ? -trP1 / trQ : 0.0;
+            // grand canonical: mu stays fixed, so mu1 = 0 and P1 = Z1 / 2
+            const double mu1 = (!gc && trQ > 0) ? -trP1 / trQ : 0.0;
             if (mu1_out) mu1_out[d] = mu1;
             last_mu1_[d] = mu1;
             // P1 = Z1/2 + mu1 Q  <=>  Z1 += 2 mu1 Q
-            CDMPT_TRY(Ew<T>::axpby(Z1->x + (size_t)d * blk_, Qmu_.x, blk_, 2.0 * mu1, 1.0, nullptr,
-                                   cx.stream));
-            CDMPT_TRY(Ew<T>::diag_dot(Z1->x + (size_t)d * blk_, H1 + (size_t)d * blk_, N, ld, ld,
+            if (!gc)
+                CDMPT_TRY(Ew<T>::axpby(Z1->x + (size_t)d * blk_, Qmu_.x, blk_, 2.0 * mu1, 1.0,
+                                       nullptr, cx.stream));
+            CDMPT_TRY(Ew<T>::dot_h(Z1->x + (size_t)d * blk_, H1 + (size_t)d * blk_, N, ld, ld,
                                       sc_ + S_ALPHA + d, cx.stream));
         }
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRZ1, 0, kMaxD * sizeof(double), cx.stream));

@@ -9,6 +9,7 @@ from .tightbinding import (  # noqa: F401
     chain_1d,
     cubic_lattice,
     banded_random,
+    cluster_sizes,
     clusters,
     workload,
     WORKLOADS,

@@ -126,12 +126,17 @@ def _cluster(Nb: int, seed: int, beta: float, n: int) -> Problem:
                    meta={"seed": seed})
 
 
+def cluster_sizes(B: int = 96, seed: int = 1005, nmin: int = 128, nmax: int = 1536) -> List[int]:
+    """The sizes N_b ~ U{nmin..nmax} that clusters() draws (without building the systems)."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.integers(nmin, nmax + 1, size=B)]
+
+
 def clusters(B: int = 96, seed: int = 1005, nmin: int = 128, nmax: int = 1536,
              beta: float = 20.0, n: int = 12, sizes: Optional[List[int]] = None) -> List[Problem]:
     """B disordered 3D clusters of uneven size, three dipole directions each."""
     if sizes is None:
-        rng = np.random.default_rng(seed)
-        sizes = [int(v) for v in rng.integers(nmin, nmax + 1, size=B)]
+        sizes = cluster_sizes(B, seed, nmin, nmax)
     return [_cluster(Nb, seed + b, beta, n) for b, Nb in enumerate(sizes)]
 
 

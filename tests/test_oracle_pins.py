@@ -435,3 +435,17 @@ def test_second_order_pins_catch_planted_mistakes(monkeypatch):
         return r
     monkeypatch.setattr(o.dmpt_oracle, "solve", no_mu1)
     assert err() > 1e-3
+
+
+def test_grand_canonical_orders_match_literal_recursion():
+    """Fixed mu (the grand-canonical scheme beside Algorithm 1): P0, P1 and P2 of the closed
+    forms equal Algorithm 1's recursion with mu1 = mu2 = 0 (dense solves), chain64."""
+    p = syn.workload("chain64")
+    mu = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")["mu"] + 0.05
+    r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", canonical=False, mu=mu)
+    assert r["mu1"][0] == 0.0 and r["mu2"][0] == 0.0
+    X0, X1, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, mu, 0.0, 0.0, p.n)
+    assert o.rel_frobenius(X0, r["P0"]) < 1e-12
+    assert o.rel_frobenius(X1, r["P1"][0]) < 1e-10
+    assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
+    assert abs(np.trace(X1)) > 1e-3     # no canonical constraint: Tr P1 != 0
