@@ -185,16 +185,18 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
  * respect to H0: dL/dH0 = -4 sum_d w_d P2_d. This follows from the symmetry of
  * the third derivatives of the canonical free energy, whose H0-gradient is P0
  * (App. B), and holds exactly for the recursion's own occupation function.
+ * Also Omega^(3)_d = (1/3) Tr[H1_d P2_d], the third-order free-energy term of
+ * Eq. (Resp_0) with H^(1) = H1_d (the n+1 rule: P^(2) suffices for it).
  * w: host array of D weights, or NULL for all ones.
- * P2: D x N x N (row-major FP64), may be NULL. mu2: host array of D doubles,
- * may be NULL. gradH0: N x N, may be NULL. P2 and gradH0 are host or device
+ * P2: D x N x N (row-major FP64), may be NULL. mu2, omega3: host arrays of D
+ * doubles, may be NULL. gradH0: N x N, may be NULL. P2 and gradH0 are host or device
  * memory per on_device. The call reruns the first order with the known mu1,
  * storing its trajectory, then the order-2 recursion (four products and one
  * CG solve per step and direction) in the precision of the solve.
  * Errors: ERR_ARG (no solve yet, no directions), ERR_CG_MAXITER,
  * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
 cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
-                             double* gradH0, int on_device);
+                             double* omega3, double* gradH0, int on_device);
 
 /* Spectral interval of a symmetric matrix from Gershgorin discs:
  * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).

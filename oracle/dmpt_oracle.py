@@ -405,9 +405,11 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
       [(F o ht) ht - ht (F o ht)]_ij / (e_i - e_j),
     F the first divided differences; closer pairs are summed explicitly, with
     the quadrature for triples of spread <= quad / beta.
-    Returns the first-order results of ``solve`` plus P2 (D, N, N), mu2 (D,)
-    and grad_alpha = -4 P2 (d alpha_d / d H0, by the symmetry of the third
-    derivatives of the canonical free energy, whose gradient is P0).
+    Returns the first-order results of ``solve`` plus P2 (D, N, N), mu2 (D,),
+    grad_alpha = -4 P2 (d alpha_d / d H0, by the symmetry of the third
+    derivatives of the canonical free energy, whose gradient is P0) and
+    omega3 (D,) = (1/3) Tr[H1 P2], the third-order free-energy term of
+    Eq. (Resp_0) (the n+1 rule: P^(2) suffices for Omega^(3)).
     canonical=False keeps mu fixed (given by ``mu``, else found from nocc):
     mu1 = mu2 = 0, the grand-canonical response.
     """
@@ -439,7 +441,9 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
         mu2[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
         P2[d] = V @ (S - mu2[d] * np.diag(fp)) @ V.T
     out = dict(base)
-    out.update(P2=P2, mu2=mu2, grad_alpha=-4.0 * P2)
+    # Eq. (Resp_0) with H^(1) = H1 and no higher orders: Omega^(3) = (1/3) Tr[H1 P^(2)]
+    omega3 = np.array([np.sum(H1[d] * P2[d]) / 3.0 for d in range(H1.shape[0])])
+    out.update(P2=P2, mu2=mu2, grad_alpha=-4.0 * P2, omega3=omega3)
     return out
 
 

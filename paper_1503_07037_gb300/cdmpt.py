@@ -116,7 +116,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
         "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
-        "cdmpt_response2": (I, [P, P, P, P, P, I]),
+        "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -361,7 +361,8 @@ class Handle:
 
     def response2(self, weights=None, want_P2=True, want_grad=True, device="cuda"):
         """Second-order canonical response of the last solve: dict(P2 (D, N, N), mu2 (D,),
-        grad) with grad = d(sum_d w_d alpha_d)/dH0 = -4 sum_d w_d P2_d (float64 tensors)."""
+        omega3 (D,), grad) with omega3 = 1/3 Tr[H1 P2] (Eq. Resp_0) and
+        grad = d(sum_d w_d alpha_d)/dH0 = -4 sum_d w_d P2_d (float64 tensors)."""
         import torch
         N, D = self.N, self.D
         dev = torch.device(device)
@@ -372,9 +373,10 @@ class Handle:
         if weights is not None:
             w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), (D,)))
         mu2 = np.zeros(max(D, 1))
+        om3 = np.zeros(max(D, 1))
         _check(lib().cdmpt_response2(self.h, None if w is None else w.ctypes.data, _ptr(P2),
-                                     mu2.ctypes.data, _ptr(G), on_dev), self.h)
-        return {"P2": P2, "mu2": mu2[:D].copy(), "grad": G}
+                                     mu2.ctypes.data, om3.ctypes.data, _ptr(G), on_dev), self.h)
+        return {"P2": P2, "mu2": mu2[:D].copy(), "omega3": om3[:D].copy(), "grad": G}
 
     def stats(self):
         return get_stats(self.h)

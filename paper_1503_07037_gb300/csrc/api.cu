@@ -327,7 +327,7 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
 }
 
 cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
-                             double* gradH0, int on_device) {
+                             double* omega3, double* gradH0, int on_device) {
     if (!h) return CDMPT_ERR_ARG;
     if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "response2: no completed solve on this handle");
     if (h->D < 1)
@@ -344,14 +344,18 @@ cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, doubl
         p2 = P2 ? tmp : nullptr;
         g = gradH0 ? tmp + (P2 ? (size_t)D * nn : 0) : nullptr;
     }
-    std::vector<double> m2(D, 0.0);
+    std::vector<double> m2(D, 0.0), om3(D, 0.0);
     cdmpt_stats keep = h->st;
     h->cx.st = &h->st;
     cdmpt_status st;
     if (h->opts.precision == CDMPT_FP64)
-        st = h->sd ? h->sd->response2(h->cx, h->H1, D, w, p2, m2.data(), g) : CDMPT_ERR_ARG;
+        st = h->sd ? h->sd->response2(h->cx, h->H1, D, w, p2, m2.data(),
+                                      omega3 ? om3.data() : nullptr, g)
+                   : CDMPT_ERR_ARG;
     else
-        st = h->sf ? h->sf->response2(h->cx, h->H1, D, w, p2, m2.data(), g) : CDMPT_ERR_ARG;
+        st = h->sf ? h->sf->response2(h->cx, h->H1, D, w, p2, m2.data(),
+                                      omega3 ? om3.data() : nullptr, g)
+                   : CDMPT_ERR_ARG;
     h->st = keep;
     if (st == CDMPT_OK && !on_device) {
         if (P2)
@@ -366,6 +370,8 @@ cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, doubl
     if (st != CDMPT_OK) return fail(h, st);
     if (mu2)
         for (int d = 0; d < D; ++d) mu2[d] = m2[d];
+    if (omega3)
+        for (int d = 0; d < D; ++d) omega3[d] = om3[d];
     return CDMPT_OK;
 }
 

@@ -624,7 +624,7 @@ cdmpt_status Solver<T>::first_order_trajectory(Context& cx, const double* H1d, d
 // is P0): d alpha_d / d H0 = -2 d^2 P / d lambda_d^2 = -4 P2_d.
 template <typename T>
 cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
-                                  double* P2, double* mu2_out, double* grad) {
+                                  double* P2, double* mu2_out, double* omega3, double* grad) {
     if (!traj_valid_ || D < 1 || (int)last_mu1_.size() < D) {
         set_error("second-order response: no completed solve with perturbations on this handle");
         return CDMPT_ERR_ARG;
@@ -717,6 +717,13 @@ cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const do
         if (mu2_out) mu2_out[d] = mu2;
         // Z2 += 2 mu2 Q  (P2 = Z2 / 2)
         if (!gc) CDMPT_TRY(Ew<T>::axpby(Z2->x, Qmu_.x, blk_, 2.0 * mu2, 1.0, nullptr, cx.stream));
+        if (omega3) {   // Omega^(3) = 1/3 Tr[H1 P2] = 1/6 <Z2, H1>
+            CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 2, 0, sizeof(double), cx.stream));
+            CDMPT_TRY(Ew<T>::dot_h(Z2->x, H1 + (size_t)d * blk_, N, ld, ld, sc_ + S_TRQ + 2,
+                                   cx.stream));
+            CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+            omega3[d] = cx.pinned[S_TRQ + 2] / 6.0;
+        }
         if (P2)
             CDMPT_TRY(Ew<T>::to_f64(P2 + (size_t)d * N * N, N, Z2->x, ld, N, N, 0.5, 0.0,
                                     cx.stream));

@@ -65,8 +65,9 @@ public:
     // grad = -4 sum_d w_d P2_d = d (sum_d w_d alpha_d) / d H0 (w null: all 1).
     // P2 (D x N x N) and grad (N x N) are FP64 device arrays with leading
     // dimension N, or null; mu2 is a host array of D doubles, or null.
+    // omega3 (host, D doubles, or null): Omega^(3)_d = 1/3 Tr[H1_d P2_d] (Eq. Resp_0).
     cdmpt_status response2(Context& cx, const double* H1, int D, const double* w, double* P2,
-                           double* mu2, double* grad);
+                           double* mu2, double* omega3, double* grad);
     bool trajectory_valid() const { return traj_valid_; }
 
     int ld = 0;

@@ -1,7 +1,8 @@
 """GPU tests of the second-order canonical response and the polarizability gradient.
 
 cdmpt_response2 returns P2 = (1/2) d^2 P / d lambda^2 (Algorithm 1, order 2,
-with H^(2) = 0), mu2 (Tr P2 = 0), and d(sum_d w_d alpha_d)/dH0 = -4 sum_d w_d P2_d.
+with H^(2) = 0), mu2 (Tr P2 = 0), Omega^(3) = 1/3 Tr[H1 P2] (Eq. Resp_0), and
+d(sum_d w_d alpha_d)/dH0 = -4 sum_d w_d P2_d.
 
 References:
 - The oracle's second-order Daleckii-Krein response (kind="rec", the function
@@ -30,7 +31,8 @@ def _r2(pkg, p, precision, weights=None):
         h.set_H(p.H0, p.H1)
         h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
         r = h.response2(weights=weights)
-    return {"P2": r["P2"].cpu().numpy(), "mu2": r["mu2"], "grad": r["grad"].cpu().numpy()}
+    return {"P2": r["P2"].cpu().numpy(), "mu2": r["mu2"], "omega3": r["omega3"],
+            "grad": r["grad"].cpu().numpy()}
 
 
 def test_p2_fp64_chain64(cuda, cdmpt_lib):
@@ -40,6 +42,7 @@ def test_p2_fp64_chain64(cuda, cdmpt_lib):
     assert oracle.rel_frobenius(r["P2"][0], ref["P2"][0]) < 1e-10
     assert abs(r["mu2"][0] - ref["mu2"][0]) < 1e-9 * max(1.0, abs(ref["mu2"][0]))
     assert oracle.rel_frobenius(r["grad"], ref["grad_alpha"][0]) < 1e-10
+    assert abs(r["omega3"][0] - ref["omega3"][0]) < 1e-10 * abs(ref["omega3"][0])
 
 
 def test_p2_fp64_three_directions_weighted(cuda, cdmpt_lib):
@@ -53,6 +56,7 @@ def test_p2_fp64_three_directions_weighted(cuda, cdmpt_lib):
     r = _r2(cdmpt_lib, p, "fp64", weights=w)
     for d in range(3):
         assert oracle.rel_frobenius(r["P2"][d], ref["P2"][d]) < 1e-10
+        assert abs(r["omega3"][d] - ref["omega3"][d]) < 1e-9 * abs(ref["omega3"][d])
     g = sum(w[d] * ref["grad_alpha"][d] for d in range(3))
     assert oracle.rel_frobenius(r["grad"], g) < 1e-10
 
@@ -64,6 +68,7 @@ def test_p2_float_lattice_512(cuda, cdmpt_lib, precision):
     r = _r2(cdmpt_lib, p, precision)
     assert oracle.rel_frobenius(r["P2"][0], ref["P2"][0]) < 1e-5
     assert oracle.rel_frobenius(r["grad"], ref["grad_alpha"][0]) < 1e-5
+    assert abs(r["omega3"][0] - ref["omega3"][0]) < 1e-5 * abs(ref["omega3"][0])
 
 
 def test_alpha_gradient_fp64_central_differences_20_directions(cuda, cdmpt_lib):

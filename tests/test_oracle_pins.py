@@ -449,3 +449,15 @@ def test_grand_canonical_orders_match_literal_recursion():
     assert o.rel_frobenius(X1, r["P1"][0]) < 1e-10
     assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
     assert abs(np.trace(X1)) > 1e-3     # no canonical constraint: Tr P1 != 0
+
+
+def test_n_plus_one_rule_third_order():
+    """Omega^(3) = 1/3 Tr[H1 P2] (Eq. Resp_0, H^(k >= 2) = 0) against the third derivative of
+    the canonical free energy Omega(lambda) / 6 (six-point central differences)."""
+    H0 = _rand_sym(10, 8)
+    H1 = _rand_sym(10, 9, 0.3)
+    beta, nocc, h = 3.0, 4.0, 1e-2
+    om3 = o.response2(H0, H1, beta, nocc, kind="fd")["omega3"][0]
+    w = {k: _omega(H0, H1, k * h, beta, nocc) for k in (-3, -2, -1, 1, 2, 3)}
+    d3 = (-w[3] + 8 * w[2] - 13 * w[1] + 13 * w[-1] - 8 * w[-2] + w[-3]) / (8 * h ** 3)
+    assert abs(d3 / 6.0 - om3) < 1e-6 * abs(om3)
