@@ -31,9 +31,17 @@ The response uses the Daleckii-Krein divided-difference formula: in the
 eigenbasis, (P1)_ij = f[eps_i, eps_j] (h_ij - mu1 delta_ij) with h = V^T H1 V,
 and mu1 = sum_i f'_i h_ii / sum_i f'_i from Tr P1 = 0.
 
-``literal_recursion`` and ``literal_canonical`` restate Algorithm 1 (first
-order) in the paper's X-notation with dense linear solves. They exist to pin
-the closed forms above against the iteration the paper prints.
+Higher orders use the higher Daleckii-Krein formulas: the second order
+(``response2``) sums third divided differences f[e_i, e_k, e_j], the third
+order (``response3``) fourth divided differences f[e_i, e_k, e_l, e_j], with
+the canonical shifts mu2 and mu3 from Tr P2 = Tr P3 = 0 (Algorithm 1), and
+the free-energy terms Omega^(3) = Tr[H1 P2]/3 and Omega^(4) = Tr[H1 P3]/4 of
+Eq. (Resp_0).
+
+``literal_recursion``, ``literal_canonical``, ``literal_recursion2`` and
+``literal_recursion3`` restate Algorithm 1 (orders 1 to 3) in the paper's
+X-notation with dense linear solves. They exist to pin the closed forms above
+against the iteration the paper prints.
 """
 from __future__ import annotations
 
@@ -391,6 +399,26 @@ def _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad):
     return out
 
 
+def _dk2_matrix(ht, eps, F, mu, beta, n, close, quad, batch):
+    """S_ij = sum_k f[e_i, e_k, e_j] ht_ik ht_kj, the second-order Daleckii-Krein sum.
+
+    For pairs with beta |e_i - e_j| > close it is the exact identity
+    [(F o ht) ht - ht (F o ht)]_ij / (e_i - e_j); closer pairs are summed
+    explicitly with ``_second_dd_for_pairs``.
+    """
+    diff = eps[:, None] - eps[None, :]
+    ci, cj = np.nonzero(np.abs(diff) * beta <= close)
+    G = F * ht
+    with np.errstate(divide="ignore", invalid="ignore"):
+        S = (G @ ht - ht @ G) / diff
+    for s0 in range(0, ci.shape[0], batch):
+        I = ci[s0:s0 + batch]
+        J = cj[s0:s0 + batch]
+        F3 = _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad)
+        S[I, J] = np.sum(F3 * ht[I, :] * ht[:, J].T, axis=1)
+    return S
+
+
 def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
               close: float = 1.0, quad: float = 1.0, batch: int = 1024, canonical: bool = True,
               mu: Optional[float] = None):
@@ -424,20 +452,11 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     F = divided_differences(eps, mu, beta, nn)
     fp = np.diag(F).copy()
     N = eps.shape[0]
-    diff = eps[:, None] - eps[None, :]
-    ci, cj = np.nonzero(np.abs(diff) * beta <= close)
     P2 = np.empty_like(H1)
     mu2 = np.zeros(H1.shape[0])
     for d in range(H1.shape[0]):
         ht = V.T @ H1[d] @ V - base["mu1"][d] * np.eye(N)
-        G = F * ht
-        with np.errstate(divide="ignore", invalid="ignore"):
-            S = (G @ ht - ht @ G) / diff
-        for s0 in range(0, ci.shape[0], batch):
-            I = ci[s0:s0 + batch]
-            J = cj[s0:s0 + batch]
-            F3 = _second_dd_for_pairs(I, J, eps, F, mu, beta, nn, quad)
-            S[I, J] = np.sum(F3 * ht[I, :] * ht[:, J].T, axis=1)
+        S = _dk2_matrix(ht, eps, F, mu, beta, nn, close, quad, batch)
         mu2[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
         P2[d] = V @ (S - mu2[d] * np.diag(fp)) @ V.T
     out = dict(base)
@@ -473,3 +492,199 @@ def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M):
         X2n = np.linalg.solve(T, C2 + B2 @ X0n + B1 @ X1n)
         X0, X1, X2 = X0n, X1n, X2n
     return X0, X1, X2
+
+
+# ----------------------------------------------------------------------------
+# third order: P3 = (1/6) d^3 P / d lambda^3 (Algorithm 1, order 3, with
+# H^(2) = H^(3) = 0) and Omega^(4) = (1/4) Tr[H1 P3] (Eq. Resp_0)
+# ----------------------------------------------------------------------------
+
+def occupation_third_derivative(eps, mu, beta, n: Optional[int] = None):
+    """d^3 occupation / d eps^3.
+
+    Fermi-Dirac, x = beta (e - mu)/2, t = tanh x: (beta^3/8) (1 - t^2)(1 - 3 t^2).
+    Recursion (n steps): g = (1 + tanh u)/2 with u = 2^n atanh z(e), z linear in e
+    with slope -c (c = beta / 2^(n+1)). With t = tanh u, S = 1 - t^2 and
+    u' = -2^n c / (1 - z^2), u'' = 2^(n+1) c^2 z / (1 - z^2)^2,
+    u''' = -2^(n+1) c^3 (1 + 3 z^2) / (1 - z^2)^3, the chain rule gives
+    g''' = S/2 [u''' - 6 t u' u'' + (6 t^2 - 2) u'^3].
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    if n is None:
+        t = np.tanh(0.5 * beta * (eps - mu))
+        return beta ** 3 / 8.0 * (1.0 - t * t) * (1.0 - 3.0 * t * t)
+    z = z0_of(eps, mu, beta, n)
+    m = 2.0 ** n
+    c = beta / 2.0 ** (n + 1)
+    t = np.tanh(m * np.arctanh(z))
+    S = 1.0 - t * t
+    q = 1.0 - z * z
+    u1 = -m * c / q
+    u2 = 2.0 * m * c * c * z / q ** 2
+    u3 = -2.0 * m * c ** 3 * (1.0 + 3.0 * z * z) / q ** 3
+    return 0.5 * S * (u3 - 6.0 * t * u1 * u2 + (6.0 * t * t - 2.0) * u1 ** 3)
+
+
+def third_dd_quadrature(a, b, c, d, mu, beta, n: Optional[int] = None):
+    """f[a, b, c, d] as the Hermite-Genocchi integral of f''' over the 3-simplex,
+    a + t1 (b - a) + t2 (c - a) + t3 (d - a), after the collapse t1 = x,
+    t2 = (1 - x) y, t3 = (1 - x)(1 - y) z (Jacobian (1 - x)^2 (1 - y)), with an
+    8 x 8 x 8 Gauss-Legendre rule. For clustered points (beta * spread <= 1)."""
+    a = np.asarray(a, dtype=np.float64)[..., None, None, None]
+    b = np.asarray(b, dtype=np.float64)[..., None, None, None]
+    c = np.asarray(c, dtype=np.float64)[..., None, None, None]
+    d = np.asarray(d, dtype=np.float64)[..., None, None, None]
+    x = _GL_X[:, None, None]
+    y = _GL_X[None, :, None]
+    z = _GL_X[None, None, :]
+    t1 = x
+    t2 = (1.0 - x) * y
+    t3 = (1.0 - x) * (1.0 - y) * z
+    pts = a + t1 * (b - a) + t2 * (c - a) + t3 * (d - a)
+    w = (_GL_W[:, None, None] * _GL_W[None, :, None] * _GL_W[None, None, :]
+         * (1.0 - x) ** 2 * (1.0 - y))
+    return np.sum(occupation_third_derivative(pts, mu, beta, n) * w, axis=(-3, -2, -1))
+
+
+def _dd3_idx(p, q, r, eps, F, mu, beta, n, quad):
+    """f[e_p, e_q, e_r] for broadcastable index arrays p, q, r.
+
+    The quotient f[x, y, z] = (f[y, z] - f[x, y]) / (z - x) is taken across the
+    widest of the three pairs (any order of the points gives the same value);
+    triples whose spread is within quad / beta use ``second_dd_quadrature``.
+    """
+    p, q, r = np.broadcast_arrays(np.asarray(p), np.asarray(q), np.asarray(r))
+    ep, eq, er = eps[p], eps[q], eps[r]
+    dpq, dqr, dpr = np.abs(ep - eq), np.abs(eq - er), np.abs(ep - er)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v_pr = (F[q, r] - F[p, q]) / (er - ep)      # outer p, r; middle q
+        v_pq = (F[r, q] - F[p, r]) / (eq - ep)      # outer p, q; middle r
+        v_qr = (F[p, r] - F[q, p]) / (er - eq)      # outer q, r; middle p
+    out = np.where((dpr >= dpq) & (dpr >= dqr), v_pr, np.where(dpq >= dqr, v_pq, v_qr))
+    spread = np.maximum(np.maximum(dpq, dqr), dpr)
+    near = spread * beta <= quad
+    if np.any(near):
+        out = np.array(out, dtype=np.float64)
+        out[near] = second_dd_quadrature(ep[near], eq[near], er[near], mu, beta, n)
+    return out
+
+
+def _dd4_idx(i, k, l, j, eps, F, mu, beta, n, quad):
+    """f[e_i, e_k, e_l, e_j] for broadcastable index arrays.
+
+    With (s, t) the widest pair of the four points and (u, v) the other two,
+    f = (f[u, v, t] - f[s, u, v]) / (e_t - e_s); quadruples whose spread is
+    within quad / beta use ``third_dd_quadrature``.
+    """
+    idx = np.broadcast_arrays(np.asarray(i), np.asarray(k), np.asarray(l), np.asarray(j))
+    e = [eps[x] for x in idx]
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    dist = np.stack([np.abs(e[a] - e[b]) for a, b in pairs])
+    widest = np.argmax(dist, axis=0)
+    spread = np.max(dist, axis=0)
+    out = np.zeros(idx[0].shape)
+    for w, (a, b) in enumerate(pairs):
+        sel = widest == w
+        if not np.any(sel):
+            continue
+        u, v = [x for x in range(4) if x not in (a, b)]
+        sa, sb, su, sv = idx[a][sel], idx[b][sel], idx[u][sel], idx[v][sel]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[sel] = ((_dd3_idx(su, sv, sb, eps, F, mu, beta, n, quad)
+                         - _dd3_idx(sa, su, sv, eps, F, mu, beta, n, quad))
+                        / (eps[sb] - eps[sa]))
+    near = spread * beta <= quad
+    if np.any(near):
+        out[near] = third_dd_quadrature(e[0][near], e[1][near], e[2][near], e[3][near],
+                                        mu, beta, n)
+    return out
+
+
+def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
+              close: float = 1.0, quad: float = 1.0, batch: int = 1024, canonical: bool = True,
+              mu: Optional[float] = None):
+    """Third-order canonical response P3 = (1/6) d^3 P / d lambda^3 of P(H0 + lambda H1).
+
+    P(lambda) = f(H0 + lambda ht - lambda^2 mu2 I - lambda^3 mu3 I) with ht = H1 -
+    mu1 I, so in the eigenbasis of H0 (g = V^T H1 V - mu1 I) the third-order
+    Daleckii-Krein expansion reads
+      (P3)_ij = sum_kl f[e_i, e_k, e_l, e_j] g_ik g_kl g_lj
+                - mu2 (f[e_i, e_i, e_j] + f[e_i, e_j, e_j]) g_ij - mu3 f'_i delta_ij,
+    with mu2 the second-order shift and mu3 = sum_i (P3)_ii|_{mu3=0} / sum_i f'_i
+    from Tr P3 = 0 (the third-order canonical condition of Algorithm 1). For
+    pairs with beta |e_i - e_j| > close the double sum is the exact identity
+      [S2 g - g S2]_ij / (e_i - e_j),  S2_il = sum_k f[e_i, e_k, e_l] g_ik g_kl;
+    closer pairs are summed explicitly over (k, l). Omega^(4) = (1/4) Tr[H1 P3]
+    (Eq. Resp_0 with H^(1) = H1 only). Returns the results of ``response2`` plus
+    P3 (D, N, N), mu3 (D,) and omega4 (D,). canonical=False: mu fixed, mu1 =
+    mu2 = mu3 = 0.
+    """
+    H0 = np.asarray(H0, dtype=np.float64)
+    H1 = np.asarray(H1, dtype=np.float64)
+    if H1.ndim == 2:
+        H1 = H1[None]
+    nn = n if kind == "rec" else None
+    eps, V = np.linalg.eigh(H0) if eig is None else eig
+    base = response2(H0, H1, beta, nocc, n, kind, eig=(eps, V), close=close, quad=quad,
+                     batch=batch, canonical=canonical, mu=mu)
+    mu = base["mu"]
+    F = divided_differences(eps, mu, beta, nn)
+    fp = np.diag(F).copy()
+    N = eps.shape[0]
+    diff = eps[:, None] - eps[None, :]
+    ci, cj = np.nonzero(np.abs(diff) * beta <= close)
+    ii, jj = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    # f[e_i, e_i, e_j] + f[e_i, e_j, e_j], the coefficient of the mu2 cross terms
+    f_iij = (_dd3_idx(ii, ii, jj, eps, F, mu, beta, nn, quad)
+             + _dd3_idx(ii, jj, jj, eps, F, mu, beta, nn, quad))
+    kk, ll = ii, jj
+    P3 = np.empty_like(H1)
+    mu3 = np.zeros(H1.shape[0])
+    for d in range(H1.shape[0]):
+        g = V.T @ H1[d] @ V - base["mu1"][d] * np.eye(N)
+        S2 = _dk2_matrix(g, eps, F, mu, beta, nn, close, quad, batch)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            S = (S2 @ g - g @ S2) / diff
+        for p in range(ci.shape[0]):
+            i, j = ci[p], cj[p]
+            f4 = _dd4_idx(i, kk, ll, j, eps, F, mu, beta, nn, quad)
+            S[i, j] = np.sum(f4 * g[i, :][:, None] * g * g[:, j][None, :])
+        S = S - base["mu2"][d] * f_iij * g
+        mu3[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
+        P3[d] = V @ (S - mu3[d] * np.diag(fp)) @ V.T
+    out = dict(base)
+    omega4 = np.array([np.sum(H1[d] * P3[d]) / 4.0 for d in range(H1.shape[0])])
+    out.update(P3=P3, mu3=mu3, omega4=omega4)
+    return out
+
+
+def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M):
+    """The inner loop of Algorithm 1 for orders 0 to 3 (H^(2) = H^(3) = 0), dense solves.
+
+    X_0^(k) = 2^-(M+2) beta mu_k I for k = 2, 3, and per step
+    T X^(3) = C^(3) + B^(3) X_n^(0) + B^(2) X_n^(1) + B^(1) X_n^(2), with
+    C^(3) = sum_{i+j=3} X^(i) X^(j) and B^(3) = 2 (X^(3) - C^(3)).
+    Returns (X_M^(0), X_M^(1), X_M^(2), X_M^(3)).
+    """
+    N = H0.shape[0]
+    I = np.eye(N)
+    s = 2.0 ** (-(M + 2)) * beta
+    X0 = 0.5 * I - s * (H0 - mu * I)
+    X1 = -s * (H1 - mu1 * I)
+    X2 = s * mu2 * I
+    X3 = s * mu3 * I
+    for _ in range(M):
+        T = 2.0 * X0 @ (X0 - I) + I
+        C0 = X0 @ X0
+        C1 = X0 @ X1 + X1 @ X0
+        C2 = X0 @ X2 + X1 @ X1 + X2 @ X0
+        C3 = X0 @ X3 + X1 @ X2 + X2 @ X1 + X3 @ X0
+        B1 = 2.0 * (X1 - C1)
+        B2 = 2.0 * (X2 - C2)
+        B3 = 2.0 * (X3 - C3)
+        X0n = np.linalg.solve(T, C0)
+        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
+        X2n = np.linalg.solve(T, C2 + B2 @ X0n + B1 @ X1n)
+        X3n = np.linalg.solve(T, C3 + B3 @ X0n + B2 @ X1n + B1 @ X2n)
+        X0, X1, X2, X3 = X0n, X1n, X2n, X3n
+    return X0, X1, X2, X3

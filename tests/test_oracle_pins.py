@@ -461,3 +461,159 @@ def test_n_plus_one_rule_third_order():
     w = {k: _omega(H0, H1, k * h, beta, nocc) for k in (-3, -2, -1, 1, 2, 3)}
     d3 = (-w[3] + 8 * w[2] - 13 * w[1] + 13 * w[-1] - 8 * w[-2] + w[-3]) / (8 * h ** 3)
     assert abs(d3 / 6.0 - om3) < 1e-6 * abs(om3)
+
+
+# --------------------------------------------------------------------------
+# P3: third-order canonical response (Algorithm 1, order 3) and Omega^(4)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 8)])
+def test_third_derivative_closed_form(kind, n):
+    """f''' against central differences of the closed-form f''."""
+    e = np.linspace(-1.5, 1.5, 41)
+    beta, mu, h = 4.0, 0.2, 1e-5
+    d3 = o.occupation_third_derivative(e, mu, beta, n)
+    fd = (o.occupation_second_derivative(e + h, mu, beta, n)
+          - o.occupation_second_derivative(e - h, mu, beta, n)) / (2 * h)
+    assert np.max(np.abs(d3 - fd)) < 1e-7 * np.max(np.abs(d3))
+
+
+def test_third_divided_difference_quadrature():
+    """The Hermite-Genocchi quadrature of f[a, b, c, d] equals the recursive quotient of
+    well-separated points, and f'''/6 when the four points coincide."""
+    beta, mu, n = 2.0, 0.1, 10
+    pts = np.array([-0.3, -0.05, 0.2, 0.45])        # spread 0.75 / beta-scale 1.5
+    fq = o.third_dd_quadrature(*pts, mu, beta, n)
+
+    def f(x):
+        return o.occupation(np.array(x), mu, beta, n)
+
+    def dd(xs):
+        if len(xs) == 1:
+            return float(f(xs[0]))
+        return (dd(xs[1:]) - dd(xs[:-1])) / (xs[-1] - xs[0])
+    assert abs(fq - dd(list(pts))) < 1e-9 * abs(fq)
+    x = 0.37
+    assert abs(o.third_dd_quadrature(x, x, x, x, mu, beta, n)
+               - o.occupation_third_derivative(x, mu, beta, n) / 6.0) < 1e-14
+
+
+def test_p3_equals_literal_algorithm1_third_order():
+    """The closed form == Algorithm 1's order-3 recursion (dense solves), chain64, and
+    the oracle's mu3 makes the literal Tr X^(3) vanish (the canonical condition)."""
+    p = syn.workload("chain64")
+    r = o.response3(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    X = o.literal_recursion3(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], r["mu2"][0],
+                             r["mu3"][0], p.n)
+    assert o.rel_frobenius(X[2], r["P2"][0]) < 1e-10
+    assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-10
+    assert abs(np.trace(X[3])) < 1e-10 * np.linalg.norm(X[3])
+
+
+def test_p3_degenerate_clean_lattice():
+    """Exactly degenerate levels (clean 4 x 4 x 2 lattice): explicit sums and quadrature agree
+    with the literal recursion."""
+    p = syn.cubic_lattice((4, 4, 2), seed=0, beta=5.0, n=10, onsite_sigma=0.0, bond_disorder=0.0)
+    r = o.response3(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+    X = o.literal_recursion3(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], r["mu2"][0],
+                             r["mu3"][0], p.n)
+    assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-9
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_p3_equals_finite_difference_of_p2(kind, n):
+    """3 P3 = d P2 / dt along H0 + t H1 (the canonical expansion re-centred at t)."""
+    H0 = _rand_sym(20, 31, 0.4)
+    H1 = _rand_sym(20, 32, 0.1) + np.diag(np.arange(20) - 9.5) * 0.05
+    beta, nocc, h = 5.0, 10.0, 1e-4
+    r = o.response3(H0, H1, beta, nocc, n=n, kind=kind)
+    P2 = {k: o.response2(H0 + k * h * H1, H1, beta, nocc, n=n, kind=kind)["P2"][0]
+          for k in (-2, -1, 1, 2)}
+    fd = (P2[-2] - 8 * P2[-1] + 8 * P2[1] - P2[2]) / (12 * h)
+    assert o.rel_frobenius(r["P3"][0], fd / 3.0) < 1e-7
+
+
+def test_p3_and_mu_series_against_high_precision_brute_force():
+    """Brute force at 60 digits (mpmath): P(lambda) = g_n(H0 + lambda H1 - mu(lambda) I) with
+    mu(lambda) from Tr P = N_occ, by eigendecomposition at lambda = 0, +-h, +-2h, +-3h;
+    Taylor coefficients of P and mu from central differences. Pins P3, mu1, mu2 and mu3."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    N, beta, nocc, n = 5, 3.0, 2.0, 6
+    H0 = _rand_sym(N, 41)
+    H1 = _rand_sym(N, 42, 0.5)
+    r = o.response3(H0, H1, beta, nocc, n=n, kind="rec")
+    B = mp.mpf(beta)
+    m2 = mp.mpf(2) ** n
+    c = B / mp.mpf(2) ** (n + 1)
+
+    def g(e, mu):
+        return (1 + mp.tanh(m2 * mp.atanh(-c * (e - mu)))) / 2
+
+    def at(lam):
+        A = mp.matrix(H0.tolist()) + lam * mp.matrix(H1.tolist())
+        E, Q = mp.eigsy(A)
+        mu = mp.findroot(lambda u: sum(g(E[i], u) for i in range(N)) - nocc, mp.mpf(r["mu"]))
+        P = Q * mp.diag([g(E[i], mu) for i in range(N)]) * Q.T
+        return P, mu
+
+    h = mp.mpf("1e-12")
+    vals = {k: at(k * h) for k in (-2, -1, 0, 1, 2)}
+    P = {k: v[0] for k, v in vals.items()}
+    mu = {k: v[1] for k, v in vals.items()}
+    c3 = (P[2] - 2 * P[1] + 2 * P[-1] - P[-2]) / (12 * h ** 3)
+    mu1 = (mu[1] - mu[-1]) / (2 * h)
+    mu2 = (mu[1] - 2 * mu[0] + mu[-1]) / (2 * h ** 2)
+    mu3 = (mu[2] - 2 * mu[1] + 2 * mu[-1] - mu[-2]) / (12 * h ** 3)
+    P3 = np.array([[float(c3[i, j]) for j in range(N)] for i in range(N)])
+    assert o.rel_frobenius(r["P3"][0], P3) < 1e-10
+    assert abs(float(mu1) - r["mu1"][0]) < 1e-12
+    assert abs(float(mu2) - r["mu2"][0]) < 1e-11 * max(1.0, abs(r["mu2"][0]))
+    assert abs(float(mu3) - r["mu3"][0]) < 1e-10 * max(1.0, abs(r["mu3"][0]))
+
+
+def test_n_plus_one_rule_fourth_order():
+    """Omega^(4) = 1/4 Tr[H1 P3] (Eq. Resp_0, H^(k >= 2) = 0) against the fourth derivative of
+    the canonical free energy Omega(lambda) / 24 (seven-point central differences)."""
+    H0 = _rand_sym(10, 8)
+    H1 = _rand_sym(10, 9, 0.3)
+    beta, nocc, h = 3.0, 4.0, 2e-2
+    om4 = o.response3(H0, H1, beta, nocc, kind="fd")["omega4"][0]
+    w = {k: _omega(H0, H1, k * h, beta, nocc) for k in (-3, -2, -1, 0, 1, 2, 3)}
+    d4 = (-w[3] + 12 * w[2] - 39 * w[1] + 56 * w[0] - 39 * w[-1] + 12 * w[-2] - w[-3]) / (
+        6 * h ** 4)
+    assert abs(d4 / 24.0 - om4) < 1e-4 * abs(om4)
+
+
+def test_third_order_pins_catch_planted_mistakes(monkeypatch):
+    """Plant slips in the third-order oracle (CPU) and check the pins notice them."""
+    H0 = _rand_sym(24, 3, 0.4)
+    H1 = _rand_sym(24, 4, 0.1) + np.diag(np.arange(24) - 11.5) * 0.1
+    beta, nocc, n = 6.0, 12.0, 10
+    X3 = None
+
+    def err(**kw):
+        nonlocal X3
+        r = o.response3(H0, H1, beta, nocc, n=n, kind="rec", **kw)
+        if X3 is None:   # the literal recursion at the unplanted oracle's shifts
+            X3 = o.literal_recursion3(H0, H1, beta, r["mu"], r["mu1"][0], r["mu2"][0],
+                                      r["mu3"][0], n)[3]
+        return o.rel_frobenius(r["P3"][0], X3)
+
+    assert err() < 1e-10
+    assert err(close=100.0) < 1e-10
+    real3 = o.dmpt_oracle.occupation_third_derivative
+    # wrong sign of f''' (seen through the quadrature of clustered quadruples)
+    monkeypatch.setattr(o.dmpt_oracle, "occupation_third_derivative",
+                        lambda *a, **k: -real3(*a, **k))
+    assert err(close=100.0) > 1e-3
+    monkeypatch.setattr(o.dmpt_oracle, "occupation_third_derivative", real3)
+    # mu2 cross terms dropped (mu2 taken as zero inside the third order)
+    real2 = o.dmpt_oracle.response2
+
+    def no_mu2(*a, **k):
+        r = real2(*a, **k)
+        r["mu2"] = np.zeros_like(r["mu2"])
+        return r
+    monkeypatch.setattr(o.dmpt_oracle, "response2", no_mu2)
+    assert err() > 1e-3
