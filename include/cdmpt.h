@@ -94,6 +94,12 @@ typedef struct {
                             have_mu_guess): one occupation sweep, no mu update, mu1 = 0 (the
                             fixed-mu scheme Sec. II mentions beside Algorithm 1); nocc is
                             ignored. Batches are always canonical. */
+    int ckpt_stride;    /* trajectory checkpoints (FP64 and FP32 precisions): 0 keeps every
+                           Z_k; s > 0 keeps Z_k for k a multiple of s, Z_n and W_0, and
+                           recomputes the other steps one segment of s steps at a time when
+                           the response, the adjoint or a higher order needs them; -1 selects
+                           s = ceil(sqrt(n)), which keeps about 3 sqrt(n) matrices instead of
+                           2n. Mixed precisions return ERR_ARG for a nonzero value. */
 } cdmpt_opts;
 
 typedef struct {
@@ -116,6 +122,8 @@ typedef struct {
     double engine_ms[5];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
     int engine_launches[5];        /* timed GEMM launches per engine */
     double engine_flops[5];        /* algorithmic flops of those launches */
+    int cg_iterations_recompute;   /* CG iterations spent recomputing checkpointed segments */
+    int checkpoint_stride;         /* stride in use (0: whole trajectory stored) */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -190,13 +198,28 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
  * w: host array of D weights, or NULL for all ones.
  * P2: D x N x N (row-major FP64), may be NULL. mu2, omega3: host arrays of D
  * doubles, may be NULL. gradH0: N x N, may be NULL. P2 and gradH0 are host or device
- * memory per on_device. The call reruns the first order with the known mu1,
- * storing its trajectory, then the order-2 recursion (four products and one
- * CG solve per step and direction) in the precision of the solve.
+ * memory per on_device. The call runs, per direction, one joint forward sweep
+ * of orders 1 and 2 with the known mu1 (seven products and two CG solves per
+ * step) in the precision of the solve.
  * Errors: ERR_ARG (no solve yet, no directions), ERR_CG_MAXITER,
  * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
 cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
                              double* omega3, double* gradH0, int on_device);
+
+/* Third-order canonical response of the last solve, per direction d of H1:
+ * P3_d = (1/6) d^3 P / d lambda_d^3 of P(H0 + lambda_d H1_d) (Algorithm 1, the
+ * order-3 line, with H^(2) = H^(3) = 0). mu2_d comes from an order-2 pass and
+ * mu3_d from Tr P3_d = 0 (the canonical conditions of Algorithm 1). Also
+ * Omega^(4)_d = (1/4) Tr[H1_d P3_d], the fourth-order free-energy term of
+ * Eq. (Resp_0) (the n+1 rule: P^(3) suffices for it).
+ * P3: D x N x N (row-major FP64), host or device memory per on_device, may be
+ * NULL. mu3, omega4: host arrays of D doubles, may be NULL. The call runs, per
+ * direction, one joint sweep of orders 1-2 and one of orders 1-3 (every order
+ * solved with the step matrix of the 0th order) in the precision of the solve.
+ * Errors: ERR_ARG (no solve yet, no directions), ERR_CG_MAXITER,
+ * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_response3(cdmpt_handle* h, double* P3, double* mu3, double* omega4,
+                             int on_device);
 
 /* Spectral interval of a symmetric matrix from Gershgorin discs:
  * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).

@@ -46,6 +46,7 @@ class Opts(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("grand_canonical", ctypes.c_int),
+        ("ckpt_stride", ctypes.c_int),
     ]
 
 
@@ -70,6 +71,8 @@ class Stats(ctypes.Structure):
         ("engine_ms", ctypes.c_double * 5),
         ("engine_launches", ctypes.c_int * 5),
         ("engine_flops", ctypes.c_double * 5),
+        ("cg_iterations_recompute", ctypes.c_int),
+        ("checkpoint_stride", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -87,7 +90,8 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_spectral_bounds_noalloc", "cdmpt_vjp_P0", "cdmpt_batch_create",
            "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
-           "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning"]
+           "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
+           "cdmpt_response3"]
 
 
 def lib() -> ctypes.CDLL:
@@ -117,6 +121,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
+        "cdmpt_response3": (I, [P, P, P, P, I]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -287,7 +292,10 @@ class Handle:
 
     def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
                  refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
-                 stream=None, grand_canonical=False):
+                 stream=None, grand_canonical=False, ckpt_stride=0):
+        """ckpt_stride: 0 stores the whole recursion trajectory; s > 0 keeps every s-th
+        step and recomputes the rest segment by segment; "sqrt" (or -1) picks
+        s = ceil(sqrt(n)). FP64 and FP32 precisions only."""
         o = default_opts()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.gemm_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
@@ -301,6 +309,7 @@ class Handle:
         o.profile = 1 if profile else 0
         o.stream = _stream_ptr(stream)
         o.grand_canonical = 1 if grand_canonical else 0
+        o.ckpt_stride = -1 if ckpt_stride == "sqrt" else int(ckpt_stride)
         self.opts = o
         self.h = create(o)
         self.N = 0
@@ -377,6 +386,20 @@ class Handle:
         _check(lib().cdmpt_response2(self.h, None if w is None else w.ctypes.data, _ptr(P2),
                                      mu2.ctypes.data, om3.ctypes.data, _ptr(G), on_dev), self.h)
         return {"P2": P2, "mu2": mu2[:D].copy(), "omega3": om3[:D].copy(), "grad": G}
+
+    def response3(self, want_P3=True, device="cuda"):
+        """Third-order canonical response of the last solve: dict(P3 (D, N, N), mu3 (D,),
+        omega4 (D,)) with omega4 = 1/4 Tr[H1 P3] (Eq. Resp_0), float64 tensors."""
+        import torch
+        N, D = self.N, self.D
+        dev = torch.device(device)
+        on_dev = 1 if dev.type == "cuda" else 0
+        P3 = torch.empty((D, N, N), dtype=torch.float64, device=dev) if want_P3 else None
+        mu3 = np.zeros(max(D, 1))
+        om4 = np.zeros(max(D, 1))
+        _check(lib().cdmpt_response3(self.h, _ptr(P3), mu3.ctypes.data, om4.ctypes.data, on_dev),
+               self.h)
+        return {"P3": P3, "mu3": mu3[:D].copy(), "omega4": om4[:D].copy()}
 
     def stats(self):
         return get_stats(self.h)

@@ -93,6 +93,10 @@ bool valid_opts(const cdmpt_opts* o) {
     if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_BF16) return false;
     if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
     if (o->grand_canonical && !o->have_mu_guess) return false;
+    if (o->ckpt_stride < -1) return false;
+    if (o->ckpt_stride != 0 &&
+        (o->precision == CDMPT_MIXED_TF32 || o->precision == CDMPT_MIXED_BF16))
+        return false;
     return true;
 }
 
@@ -121,6 +125,7 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
     o->profile = 0;
     o->stream = nullptr;
     o->grand_canonical = 0;
+    o->ckpt_stride = 0;
     return CDMPT_OK;
 }
 
@@ -326,40 +331,52 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
     return CDMPT_OK;
 }
 
-cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
-                             double* omega3, double* gradH0, int on_device) {
+// Orders 2 and 3 share the marshalling: P^(m) (and the gradient) through a
+// device scratch when the caller's buffers are on the host.
+static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm, double* mu,
+                            double* omega, double* gradH0, int on_device) {
+    const char* name = m == 2 ? "response2" : "response3";
     if (!h) return CDMPT_ERR_ARG;
-    if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "response2: no completed solve on this handle");
+    if (!h->solved)
+        return fail_msg(h, CDMPT_ERR_ARG, std::string(name) + ": no completed solve on this handle");
     if (h->D < 1)
-        return fail_msg(h, CDMPT_ERR_ARG, "response2: the handle has no perturbation directions");
+        return fail_msg(h, CDMPT_ERR_ARG,
+                        std::string(name) + ": the handle has no perturbation directions");
     cudaStream_t s = h->cx.stream;
     const int D = h->D;
     const size_t nn = (size_t)h->N * h->N;
-    double* p2 = P2;
+    double* pm = Pm;
     double* g = gradH0;
     double* tmp = nullptr;
-    if (!on_device && (P2 || gradH0)) {
-        const size_t elems = (P2 ? (size_t)D * nn : 0) + (gradH0 ? nn : 0);
+    if (!on_device && (Pm || gradH0)) {
+        const size_t elems = (Pm ? (size_t)D * nn : 0) + (gradH0 ? nn : 0);
         CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, elems * sizeof(double), s));
-        p2 = P2 ? tmp : nullptr;
-        g = gradH0 ? tmp + (P2 ? (size_t)D * nn : 0) : nullptr;
+        pm = Pm ? tmp : nullptr;
+        g = gradH0 ? tmp + (Pm ? (size_t)D * nn : 0) : nullptr;
     }
-    std::vector<double> m2(D, 0.0), om3(D, 0.0);
+    std::vector<double> mus(D, 0.0), om(D, 0.0);
     cdmpt_stats keep = h->st;
     h->cx.st = &h->st;
     cdmpt_status st;
-    if (h->opts.precision == CDMPT_FP64)
-        st = h->sd ? h->sd->response2(h->cx, h->H1, D, w, p2, m2.data(),
-                                      omega3 ? om3.data() : nullptr, g)
-                   : CDMPT_ERR_ARG;
-    else
-        st = h->sf ? h->sf->response2(h->cx, h->H1, D, w, p2, m2.data(),
-                                      omega3 ? om3.data() : nullptr, g)
-                   : CDMPT_ERR_ARG;
+    if (h->opts.precision == CDMPT_FP64) {
+        if (!h->sd)
+            st = CDMPT_ERR_ARG;
+        else if (m == 2)
+            st = h->sd->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g);
+        else
+            st = h->sd->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr);
+    } else {
+        if (!h->sf)
+            st = CDMPT_ERR_ARG;
+        else if (m == 2)
+            st = h->sf->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g);
+        else
+            st = h->sf->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr);
+    }
     h->st = keep;
     if (st == CDMPT_OK && !on_device) {
-        if (P2)
-            CDMPT_CUDA_TRY(cudaMemcpyAsync(P2, p2, (size_t)D * nn * sizeof(double),
+        if (Pm)
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(Pm, pm, (size_t)D * nn * sizeof(double),
                                            cudaMemcpyDeviceToHost, s));
         if (gradH0)
             CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, g, nn * sizeof(double), cudaMemcpyDeviceToHost,
@@ -368,11 +385,21 @@ cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, doubl
     }
     if (tmp) cudaFreeAsync(tmp, s);
     if (st != CDMPT_OK) return fail(h, st);
-    if (mu2)
-        for (int d = 0; d < D; ++d) mu2[d] = m2[d];
-    if (omega3)
-        for (int d = 0; d < D; ++d) omega3[d] = om3[d];
+    if (mu)
+        for (int d = 0; d < D; ++d) mu[d] = mus[d];
+    if (omega)
+        for (int d = 0; d < D; ++d) omega[d] = om[d];
     return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, double* mu2,
+                             double* omega3, double* gradH0, int on_device) {
+    return respond(h, 2, w, P2, mu2, omega3, gradH0, on_device);
+}
+
+cdmpt_status cdmpt_response3(cdmpt_handle* h, double* P3, double* mu3, double* omega4,
+                             int on_device) {
+    return respond(h, 3, nullptr, P3, mu3, omega4, nullptr, on_device);
 }
 
 cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha) {

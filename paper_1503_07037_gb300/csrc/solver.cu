@@ -60,17 +60,20 @@ Solver<T>::~Solver() {
 }
 
 template <typename T>
-cdmpt_status Solver<T>::reserve(int N, int D, int n) {
+cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     const int ld_new = (N + 31) / 32 * 32;
     const int rows_needed = std::max(1, D) * N;
-    if (N == N_ && D <= D_ && n <= n_ && ld == ld_new && rows_cap_ >= rows_needed) return CDMPT_OK;
+    seg_ = -1;
+    // with checkpoints the trajectory views are laid out for exactly n steps
+    if (N == N_ && D <= D_ && (ckpt == 0 ? n <= n_ : n == n_) && ckpt == ck_ && ld == ld_new &&
+        rows_cap_ >= rows_needed)
+        return CDMPT_OK;
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
     Z_.clear();
     W_.clear();
-    Z1t_.clear();
-    A1t_.clear();
-    r2_n_ = -1;
+    orders_ready_ = false;
+    ck_ = ckpt;
     N_ = N;
     D_ = D;
     n_ = n;
@@ -101,8 +104,23 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n) {
     };
     Z_.resize(n + 1);
     W_.resize(n);
-    for (int k = 0; k <= n; ++k) CDMPT_TRY(buf(blk_, &Z_[k], true));
-    for (int k = 0; k < n; ++k) CDMPT_TRY(buf(blk_, &W_[k], true));
+    if (ck_ == 0) {
+        for (int k = 0; k <= n; ++k) CDMPT_TRY(buf(blk_, &Z_[k], true));
+        for (int k = 0; k < n; ++k) CDMPT_TRY(buf(blk_, &W_[k], true));
+    } else {
+        std::vector<Buf<T>> zseg(std::max(0, ck_ - 1)), wseg(ck_);
+        for (auto& b : zseg) CDMPT_TRY(buf(blk_, &b, true));
+        for (auto& b : wseg) CDMPT_TRY(buf(blk_, &b, true));
+        for (int k = 0; k < n; ++k) {
+            if (k % ck_ == 0)
+                CDMPT_TRY(buf(blk_, &Z_[k], true));   // checkpoint
+            else
+                Z_[k] = zseg[k % ck_ - 1];
+        }
+        CDMPT_TRY(buf(blk_, &Z_[n], true));
+        CDMPT_TRY(buf(blk_, &W_[0], true));
+        for (int k = 1; k < n; ++k) W_[k] = wseg[k % ck_];
+    }
     const size_t big = (size_t)rows_needed * ld;
     CDMPT_TRY(buf(big, &R_, false));
     CDMPT_TRY(buf(big, &P_, true));
@@ -295,48 +313,80 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
     return CDMPT_OK;
 }
 
+// One step of the 0th-order recursion: W_k = Z_k Z_k and the correction d of
+// d (I + W_k) = -2 Z_k W_k, then Z_{k+1} = sym(2 Z_k + d) with its TF32 split.
+template <typename T>
+cdmpt_status Solver<T>::step0(Context& cx, int k, int engine, double tol, int maxit,
+                              bool make_w, bool solve, int* hint, int* iters) {
+    if (make_w) {   // W_k = Z_k Z_k (symmetric)
+        Epilogue<T> ep;
+        ep.Dhi = W_[k].hi;
+        ep.Dlo = W_[k].lo;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr, engine));
+    }
+    if (!solve) return CDMPT_OK;
+    {   // right side of the correction: -2 Z_k W_k = -2 Z_k^3 (symmetric)
+        Epilogue<T> ep;
+        ep.alpha = -2.0;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, engine));
+    }
+    CgArgs a;
+    a.W = &W_[k];
+    a.rhs = RHS_.x;
+    a.rows = N_;
+    a.tol = tol;
+    a.maxit = maxit;
+    a.init_engine = a.iter_engine = engine;
+    a.hint = *hint;
+    // mirrored CG products only in the one-pass sweeps that are refined afterwards:
+    // the iterates drift from commuting with W_k at rounding level, and the mirrored
+    // operator is then not self-adjoint (measured: FP32-mode P1 errors doubled)
+    a.sym = engine == CDMPT_GEMM_TC_TF32 || engine == CDMPT_GEMM_TC_BF16;
+    int it = 0;
+    CDMPT_TRY(cg(cx, Z_[k + 1].x, a, &it, nullptr));   // d, in the Z_{k+1} buffer
+    *iters += it;
+    *hint = std::max(1, it);
+    CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, Z_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
+    CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
+    return CDMPT_OK;
+}
+
 // One 0th-order pass of Algorithm 1 at chemical potential mu: Z_0 .. Z_n, A_0 .. A_{n-1}.
+// With checkpointing the segment buffers end up holding the last segment.
 template <typename T>
 cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s2,
                               const cdmpt_opts& o, int n, int engine, double tol,
                               int* cg_iters) {
     CDMPT_TRY(Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo));
     int total = 0, hint = 1;
-    for (int k = 0; k < n; ++k) {
-        {   // W_k = Z_k Z_k (symmetric)
-            Epilogue<T> ep;
-            ep.Dhi = W_[k].hi;
-            ep.Dlo = W_[k].lo;
-            ep.sym = true;
-            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr, engine));
-        }
-        {   // right side of the correction: -2 Z_k W_k = -2 Z_k^3 (symmetric)
-            Epilogue<T> ep;
-            ep.alpha = -2.0;
-            ep.sym = true;
-            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, engine));
-        }
-        CgArgs a;
-        a.W = &W_[k];
-        a.rhs = RHS_.x;
-        a.rows = N_;
-        a.tol = tol;
-        a.maxit = o.cg_maxit;
-        a.init_engine = a.iter_engine = engine;
-        a.hint = hint;
-        // mirrored CG products only in the one-pass sweeps that are refined afterwards:
-        // the iterates drift from commuting with W_k at rounding level, and the mirrored
-        // operator is then not self-adjoint (measured: FP32-mode P1 errors doubled)
-        a.sym = engine == CDMPT_GEMM_TC_TF32 || engine == CDMPT_GEMM_TC_BF16;
-        int it = 0;
-        CDMPT_TRY(cg(cx, Z_[k + 1].x, a, &it, nullptr));   // d, in the Z_{k+1} buffer
-        total += it;
-        hint = std::max(1, it);
-        // Z_{k+1} = 2 Z_k + d, symmetrised, with its TF32 split
-        CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, Z_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
-        CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
-    }
+    for (int k = 0; k < n; ++k)
+        CDMPT_TRY(step0(cx, k, engine, tol, o.cg_maxit, true, true, &hint, &total));
+    seg_ = ck_ ? (n - 1) / ck_ : -1;
     *cg_iters = total;
+    return CDMPT_OK;
+}
+
+// Checkpointed trajectory: recompute segment j = k / ck_ from its checkpoint
+// Z_{j ck_} at the final mu, with the engine and tolerance of the final sweep
+// (the CG runs the same iterations on the same data, so the recomputed Z_k
+// equal the sweep's up to the summation order of the device reductions). W_0
+// is kept; the segment's last step ends on the next checkpoint (or Z_n), so it
+// needs W only.
+template <typename T>
+cdmpt_status Solver<T>::need(Context& cx, int k) {
+    if (ck_ == 0) return CDMPT_OK;
+    const int j = k / ck_;
+    if (j == seg_) return CDMPT_OK;
+    const int k0 = j * ck_, k1 = std::min(k0 + ck_, last_n_);
+    int hint = 1, iters = 0;
+    seg_ = -1;   // invalid while being rewritten
+    for (int i = k0; i < k1; ++i)
+        CDMPT_TRY(step0(cx, i, last_acc_, last_sweep_tol_, last_opts_.cg_maxit, i > 0, i + 1 < k1,
+                        &hint, &iters));
+    replay_iters_ += iters;
+    seg_ = j;
     return CDMPT_OK;
 }
 
@@ -468,6 +518,7 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
     Buf<T>& M1T = A1_;
     Buf<T>& B = RHS_;
     for (int k = n - 1; k >= 0; --k) {
+        CDMPT_TRY(need(cx, k));   // checkpointing: each segment recomputed once, last first
         CgArgs a;
         a.W = &W_[k];
         a.rhs = Zh_.x;
@@ -523,8 +574,8 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
 }
 
 template <typename T>
-cdmpt_status Solver<T>::reserve_response2(int n) {
-    if (r2_n_ >= n) return CDMPT_OK;
+cdmpt_status Solver<T>::reserve_orders() {
+    if (orders_ready_) return CDMPT_OK;
     auto buf = [&](Buf<T>* b) -> cdmpt_status {
         *b = Buf<T>();
         const int parts = sizeof(T) == 4 ? 3 : 1;
@@ -533,7 +584,7 @@ cdmpt_status Solver<T>::reserve_response2(int n) {
             void* p = nullptr;
             if (cudaMalloc(&p, blk_ * sizeof(T)) != cudaSuccess) {
                 cudaGetLastError();
-                set_error("device allocation for the second-order response failed");
+                set_error("device allocation for the higher-order response failed");
                 return CDMPT_ERR_OOM;
             }
             if (cudaMemset(p, 0, blk_ * sizeof(T)) != cudaSuccess) return CDMPT_ERR_CUDA;
@@ -545,155 +596,99 @@ cdmpt_status Solver<T>::reserve_response2(int n) {
         b->lo = q[2];
         return CDMPT_OK;
     };
-    const int have_z = (int)Z1t_.size(), have_a = (int)A1t_.size();
-    Z1t_.resize(n + 1);
-    A1t_.resize(n);
-    for (int k = have_z; k <= n; ++k) CDMPT_TRY(buf(&Z1t_[k]));
-    for (int k = have_a; k < n; ++k) CDMPT_TRY(buf(&A1t_[k]));
-    if (r2_n_ < 0) {
-        CDMPT_TRY(buf(&Z2a_));
-        CDMPT_TRY(buf(&Z2b_));
-        CDMPT_TRY(buf(&A2_));
-        CDMPT_TRY(buf(&G_));
+    for (int q = 0; q < 3; ++q) {
+        CDMPT_TRY(buf(&zo_[q][0]));
+        CDMPT_TRY(buf(&zo_[q][1]));
+        CDMPT_TRY(buf(&ao_[q]));
     }
-    r2_n_ = n;
+    CDMPT_TRY(buf(&G_));
+    orders_ready_ = true;
     return CDMPT_OK;
 }
 
-// Canonical first-order trajectory of one direction, with mu1 already known:
-// Z1_0 = -s2 (H1 - mu1 I), and per step (correction form, as in solve)
-//   A1_k = Z_k Z1_k + Z1_k Z_k,  d1 (I + W_k) = -Z_{k+1} A1_k - 2 Z1_k W_k,
-//   Z1_{k+1} = sym(2 Z1_k + d1); every Z1_k and A1_k is kept.
+// Joint forward sweep of the perturbation orders 1..m (the inner loop of
+// Algorithm 1 to third order, with H^(q) = 0 for q >= 2) in the deviation form.
+// With Z(lambda) = sum_q lambda^q Z^(q) and A = I + Z^2, the order-q part of
+// A_k Z_{k+1} = 2 Z_k reads
+//   A_k Z^(q)_{k+1} = 2 Z^(q)_k - sum_{j=1..q} A^(j)_k Z^(q-j)_{k+1},
+//   A^(j)_k = sum_{i=0..j} Z^(i)_k Z^(j-i)_k   (Z^(0) = Z, the trajectory),
+// the deviation-form image of the paper's C^(m) and B^(m) terms. Each order is
+// solved in correction form d (I + W_k) = -sum_j Z^(q-j)_{k+1} A^(j)_k -
+// 2 Z^(q)_k W_k, Z^(q)_{k+1} = sym(2 Z^(q)_k + d), lower orders first, all with
+// the same step matrix. Start: Z^(1)_0 = -s2 (H1 - mu1 I), Z^(q)_0 = s2 mu^(q) I
+// for q >= 2. Only the current and next iterate of each order are kept.
 template <typename T>
-cdmpt_status Solver<T>::first_order_trajectory(Context& cx, const double* H1d, double mu1) {
+cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const double* mus) {
     const int n = last_n_, N = N_;
     const int acc = last_acc_;
     const cdmpt_opts& o = last_opts_;
-    CDMPT_TRY(Ew<T>::init_z(Z1t_[0].x, H1d, N, ld, ld, 1, -last_s2_, mu1, cx.stream, Z1t_[0].hi,
-                            Z1t_[0].lo));
-    int hint = 1;
-    for (int k = 0; k < n; ++k) {
-        {   // S^T = Z1_k Z_k
-            Epilogue<T> ep;
-            CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), Z_[k].op(), S_.x, ep, nullptr, acc));
-        }
-        CDMPT_TRY(Ew<T>::transpose_add(A1t_[k].x, S_.x, N, ld, 1, cx.stream, A1t_[k].hi,
-                                       A1t_[k].lo));
-        {   // -Z_{k+1} A1_k = -(A1_k Z_{k+1})^T
-            Epilogue<T> ep;
-            ep.alpha = -1.0;
-            ep.trans_block = N;
-            CDMPT_TRY(gemm(cx, N, N, N, A1t_[k].op(), Z_[k + 1].op(), RHS_.x, ep, nullptr, acc));
-        }
-        {   // -= 2 Z1_k W_k
-            Epilogue<T> ep;
-            ep.alpha = -2.0;
-            ep.beta = 1.0;
-            ep.C = RHS_.x;
-            ep.ldc = ld;
-            CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
-        }
-        CgArgs a;
-        a.W = &W_[k];
-        a.rhs = RHS_.x;
-        a.rows = N;
-        a.tol = o.cg_tol;
-        a.maxit = o.cg_maxit;
-        a.init_engine = a.iter_engine = acc;
-        a.hint = hint;
-        int it = 0;
-        CDMPT_TRY(cg(cx, Z1t_[k + 1].x, a, &it, nullptr));
-        hint = std::max(1, it);
-        CDMPT_TRY(Ew<T>::axpby(Z1t_[k + 1].x, Z1t_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
-        CDMPT_TRY(Ew<T>::symmetrize(Z1t_[k + 1].x, N, ld, 1, cx.stream, Z1t_[k + 1].hi,
-                                    Z1t_[k + 1].lo));
-    }
-    return CDMPT_OK;
-}
-
-// Second order (Algorithm 1, the X^(2) line, with H^(2) = 0) in the deviation
-// form. Differentiating A_k Z_{k+1} = 2 Z_k twice in lambda, with A = I + Z^2:
-//   A_k Z2_{k+1} = 2 Z2_k - A1_k Z1_{k+1} - A2_k Z_{k+1},
-//   A2_k = Z_k Z2_k + Z2_k Z_k + Z1_k Z1_k,
-// solved in correction form d2 (I + W_k) = -Z1_{k+1} A1_k - Z_{k+1} A2_k -
-// 2 Z2_k W_k, Z2_{k+1} = sym(2 Z2_k + d2), from Z2_0 = 0 (mu2 = 0). P2 is linear
-// in mu2 with slope Q = dP0/dmu (Z2_0 = s2 mu2 I enters through the same
-// tangent map as a uniform shift of Z_0), so mu2 = -Tr P2|_0 / Tr Q and
-// P2 = Z2_n / 2 + mu2 Q. The polarizability gradient follows from the symmetry
-// of the third derivatives of the canonical free energy (whose gradient in H0
-// is P0): d alpha_d / d H0 = -2 d^2 P / d lambda_d^2 = -4 P2_d.
-template <typename T>
-cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
-                                  double* P2, double* mu2_out, double* omega3, double* grad) {
-    if (!traj_valid_ || D < 1 || (int)last_mu1_.size() < D) {
-        set_error("second-order response: no completed solve with perturbations on this handle");
-        return CDMPT_ERR_ARG;
-    }
-    const int n = last_n_, N = N_;
-    const int acc = last_acc_;
-    const cdmpt_opts& o = last_opts_;
-    CDMPT_TRY(reserve_response2(n));
-    const bool gc = o.grand_canonical != 0;   // fixed mu: mu2 = 0, no Q term
-    if (!q_valid_ && !gc) CDMPT_TRY(compute_q(cx));
-    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, sizeof(double), cx.stream));
-    if (!gc) CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
-    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-    const double trQ = cx.pinned[S_TRQ];
-    if (!gc && !(trQ > 0)) {
-        set_error("second-order response: Tr dP0/dmu is not positive");
-        return CDMPT_ERR_NO_CONVERGENCE;
-    }
-    if (grad) CDMPT_CUDA_TRY(cudaMemsetAsync(G_.x, 0, blk_ * sizeof(T), cx.stream));
-    auto zero = [&](Buf<T>& b) -> cdmpt_status {
+    auto cur = [&](int q) -> Buf<T>& { return zo_[q - 1][cur_[q - 1]]; };
+    auto nxt = [&](int q) -> Buf<T>& { return zo_[q - 1][1 - cur_[q - 1]]; };
+    auto mu_of = [&](int q) { return q < m ? mus[q - 1] : 0.0; };
+    for (int q = 1; q <= m; ++q) cur_[q - 1] = 0;
+    CDMPT_TRY(Ew<T>::init_z(cur(1).x, H1d, N, ld, ld, 1, -last_s2_, mu_of(1), cx.stream,
+                            cur(1).hi, cur(1).lo));
+    for (int q = 2; q <= m; ++q) {
+        Buf<T>& b = cur(q);
         CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, blk_ * sizeof(T), cx.stream));
         if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, blk_ * sizeof(T), cx.stream));
         if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, blk_ * sizeof(T), cx.stream));
-        return CDMPT_OK;
-    };
-    for (int d = 0; d < D; ++d) {
-        CDMPT_TRY(first_order_trajectory(cx, H1 + (size_t)d * blk_, last_mu1_[d]));
-        Buf<T>* Z2 = &Z2a_;
-        Buf<T>* Z2n = &Z2b_;
-        CDMPT_TRY(zero(*Z2));
-        int hint = 1;
-        for (int k = 0; k < n; ++k) {
-            {   // S^T = Z2_k Z_k
+        if (mu_of(q) != 0.0)
+            CDMPT_TRY(Ew<T>::add_diag(b.x, N, ld, 1, last_s2_ * mu_of(q), cx.stream, b.hi, b.lo));
+    }
+    int hint[3] = {1, 1, 1};
+    for (int k = 0; k < n; ++k) {
+        CDMPT_TRY(need(cx, k));
+        // A^(q)_k from the step-k iterates: S = Z^(q) Z + sum_{1 <= i < q-i} Z^(q-i) Z^(i)
+        // (products X Y^T with Y symmetric), A^(q) = S + S^T, plus Z^(q/2) Z^(q/2) for even q
+        for (int q = 1; q <= m; ++q) {
+            {
                 Epilogue<T> ep;
-                CDMPT_TRY(gemm(cx, N, N, N, Z2->op(), Z_[k].op(), S_.x, ep, nullptr, acc));
+                CDMPT_TRY(gemm(cx, N, N, N, cur(q).op(), Z_[k].op(), S_.x, ep, nullptr, acc));
             }
-            CDMPT_TRY(Ew<T>::transpose_add(A2_.x, S_.x, N, ld, 1, cx.stream));
-            {   // A2 += Z1_k Z1_k (split for its use as a left factor)
+            for (int i = 1; i < q - i; ++i) {
                 Epilogue<T> ep;
                 ep.beta = 1.0;
-                ep.C = A2_.x;
+                ep.C = S_.x;
                 ep.ldc = ld;
-                ep.Dhi = A2_.hi;
-                ep.Dlo = A2_.lo;
-                CDMPT_TRY(gemm(cx, N, N, N, Z1t_[k].op(), Z1t_[k].op(), A2_.x, ep, nullptr, acc));
+                CDMPT_TRY(gemm(cx, N, N, N, cur(q - i).op(), cur(i).op(), S_.x, ep, nullptr, acc));
             }
-            {   // RHS = -Z1_{k+1} A1_k = -(A1_k Z1_{k+1})^T
+            Buf<T>& A = ao_[q - 1];
+            const bool middle = q % 2 == 0;
+            CDMPT_TRY(Ew<T>::transpose_add(A.x, S_.x, N, ld, 1, cx.stream, middle ? nullptr : A.hi,
+                                           middle ? nullptr : A.lo));
+            if (middle) {   // += Z^(q/2) Z^(q/2), with the split for A's use as a left factor
                 Epilogue<T> ep;
-                ep.alpha = -1.0;
-                ep.trans_block = N;
-                CDMPT_TRY(gemm(cx, N, N, N, A1t_[k].op(), Z1t_[k + 1].op(), RHS_.x, ep, nullptr,
+                ep.beta = 1.0;
+                ep.C = A.x;
+                ep.ldc = ld;
+                ep.Dhi = A.hi;
+                ep.Dlo = A.lo;
+                CDMPT_TRY(gemm(cx, N, N, N, cur(q / 2).op(), cur(q / 2).op(), A.x, ep, nullptr,
                                acc));
             }
-            {   // -= Z_{k+1} A2_k = (A2_k Z_{k+1})^T
+        }
+        for (int q = 1; q <= m; ++q) {
+            // RHS = -sum_{j=1..q} Z^(q-j)_{k+1} A^(j)_k = -sum_j (A^(j)_k Z^(q-j)_{k+1})^T
+            for (int j = 1; j <= q; ++j) {
+                const Buf<T>& Zn = j == q ? Z_[k + 1] : nxt(q - j);
                 Epilogue<T> ep;
                 ep.alpha = -1.0;
-                ep.beta = 1.0;
-                ep.C = RHS_.x;
-                ep.ldc = ld;
+                if (j > 1) {
+                    ep.beta = 1.0;
+                    ep.C = RHS_.x;
+                    ep.ldc = ld;
+                }
                 ep.trans_block = N;
-                CDMPT_TRY(gemm(cx, N, N, N, A2_.op(), Z_[k + 1].op(), RHS_.x, ep, nullptr, acc));
+                CDMPT_TRY(gemm(cx, N, N, N, ao_[j - 1].op(), Zn.op(), RHS_.x, ep, nullptr, acc));
             }
-            {   // -= 2 Z2_k W_k
+            {   // -= 2 Z^(q)_k W_k
                 Epilogue<T> ep;
                 ep.alpha = -2.0;
                 ep.beta = 1.0;
                 ep.C = RHS_.x;
                 ep.ldc = ld;
-                CDMPT_TRY(gemm(cx, N, N, N, Z2->op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
+                CDMPT_TRY(gemm(cx, N, N, N, cur(q).op(), W_[k].op(), RHS_.x, ep, nullptr, acc));
             }
             CgArgs a;
             a.W = &W_[k];
@@ -702,34 +697,76 @@ cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const do
             a.tol = o.cg_tol;
             a.maxit = o.cg_maxit;
             a.init_engine = a.iter_engine = acc;
-            a.hint = hint;
+            a.hint = hint[q - 1];
             int it = 0;
-            CDMPT_TRY(cg(cx, Z2n->x, a, &it, nullptr));
-            hint = std::max(1, it);
-            CDMPT_TRY(Ew<T>::axpby(Z2n->x, Z2->x, blk_, 2.0, 1.0, nullptr, cx.stream));
-            CDMPT_TRY(Ew<T>::symmetrize(Z2n->x, N, ld, 1, cx.stream, Z2n->hi, Z2n->lo));
-            std::swap(Z2, Z2n);
+            Buf<T>& Zq = nxt(q);
+            CDMPT_TRY(cg(cx, Zq.x, a, &it, nullptr));
+            hint[q - 1] = std::max(1, it);
+            CDMPT_TRY(Ew<T>::axpby(Zq.x, cur(q).x, blk_, 2.0, 1.0, nullptr, cx.stream));
+            CDMPT_TRY(Ew<T>::symmetrize(Zq.x, N, ld, 1, cx.stream, Zq.hi, Zq.lo));
         }
-        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
-        CDMPT_TRY(Ew<T>::trace(Z2->x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
-        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-        const double mu2 = gc ? 0.0 : -0.5 * cx.pinned[S_TRQ + 1] / trQ;
-        if (mu2_out) mu2_out[d] = mu2;
-        // Z2 += 2 mu2 Q  (P2 = Z2 / 2)
-        if (!gc) CDMPT_TRY(Ew<T>::axpby(Z2->x, Qmu_.x, blk_, 2.0 * mu2, 1.0, nullptr, cx.stream));
-        if (omega3) {   // Omega^(3) = 1/3 Tr[H1 P2] = 1/6 <Z2, H1>
-            CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 2, 0, sizeof(double), cx.stream));
-            CDMPT_TRY(Ew<T>::dot_h(Z2->x, H1 + (size_t)d * blk_, N, ld, ld, sc_ + S_TRQ + 2,
-                                   cx.stream));
+        for (int q = 1; q <= m; ++q) cur_[q - 1] ^= 1;
+    }
+    return CDMPT_OK;
+}
+
+// Canonical response of order m = 2 or 3 per direction. P^(m) is linear in
+// mu^(m) with slope Q = dP0/dmu (Z^(m)_0 = s2 mu^(m) I enters through the same
+// tangent map as a uniform shift of Z_0), so one sweep with mu^(m) = 0 gives
+// mu^(m) = -Tr P^(m)|_0 / Tr Q and P^(m) = Z^(m)_n / 2 + mu^(m) Q. Order 3 needs
+// mu2 first, from an order-2 sweep. Omega^(m+1) = 1/(m+1) Tr[H1 P^(m)] (Eq.
+// Resp_0 with H^(1) = H1 only).
+template <typename T>
+cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, const double* w,
+                               double* Pm, double* mu_out, double* omega, double* grad) {
+    if (!traj_valid_ || D < 1 || (int)last_mu1_.size() < D) {
+        set_error("higher-order response: no completed solve with perturbations on this handle");
+        return CDMPT_ERR_ARG;
+    }
+    const int N = N_;
+    const cdmpt_opts& o = last_opts_;
+    CDMPT_TRY(reserve_orders());
+    const bool gc = o.grand_canonical != 0;   // fixed mu: mu^(m) = 0, no Q term
+    if (!q_valid_ && !gc) CDMPT_TRY(compute_q(cx));
+    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ, 0, sizeof(double), cx.stream));
+    if (!gc) CDMPT_TRY(Ew<T>::trace(Qmu_.x, N, ld, 1, sc_ + S_TRQ, cx.stream));
+    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+    const double trQ = cx.pinned[S_TRQ];
+    if (!gc && !(trQ > 0)) {
+        set_error("higher-order response: Tr dP0/dmu is not positive");
+        return CDMPT_ERR_NO_CONVERGENCE;
+    }
+    if (grad) CDMPT_CUDA_TRY(cudaMemsetAsync(G_.x, 0, blk_ * sizeof(T), cx.stream));
+    for (int d = 0; d < D; ++d) {
+        const double* H1d = H1 + (size_t)d * blk_;
+        double mus[2] = {last_mu1_[d], 0.0};
+        for (int q = 2; q <= m; ++q) {
+            CDMPT_TRY(orders(cx, H1d, q, mus));
+            Buf<T>& Zq = zo_[q - 1][cur_[q - 1]];
+            CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
+            CDMPT_TRY(Ew<T>::trace(Zq.x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
             CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-            omega3[d] = cx.pinned[S_TRQ + 2] / 6.0;
-        }
-        if (P2)
-            CDMPT_TRY(Ew<T>::to_f64(P2 + (size_t)d * N * N, N, Z2->x, ld, N, N, 0.5, 0.0,
-                                    cx.stream));
-        if (grad) {   // -4 w_d P2_d = -2 w_d Z2
-            const double wd = w ? w[d] : 1.0;
-            CDMPT_TRY(Ew<T>::axpby(G_.x, Z2->x, blk_, -2.0 * wd, 1.0, nullptr, cx.stream));
+            const double muq = gc ? 0.0 : -0.5 * cx.pinned[S_TRQ + 1] / trQ;
+            if (q < m) {
+                mus[q - 1] = muq;
+                continue;
+            }
+            if (mu_out) mu_out[d] = muq;
+            // Z^(m) += 2 mu^(m) Q  (P^(m) = Z^(m) / 2)
+            if (!gc) CDMPT_TRY(Ew<T>::axpby(Zq.x, Qmu_.x, blk_, 2.0 * muq, 1.0, nullptr, cx.stream));
+            if (omega) {   // Omega^(m+1) = 1/(m+1) Tr[H1 P^(m)] = <Z^(m), H1> / (2 (m+1))
+                CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 2, 0, sizeof(double), cx.stream));
+                CDMPT_TRY(Ew<T>::dot_h(Zq.x, H1d, N, ld, ld, sc_ + S_TRQ + 2, cx.stream));
+                CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+                omega[d] = cx.pinned[S_TRQ + 2] / (2.0 * (m + 1));
+            }
+            if (Pm)
+                CDMPT_TRY(Ew<T>::to_f64(Pm + (size_t)d * N * N, N, Zq.x, ld, N, N, 0.5, 0.0,
+                                        cx.stream));
+            if (grad) {   // -4 w_d P2_d = -2 w_d Z2
+                const double wd = w ? w[d] : 1.0;
+                CDMPT_TRY(Ew<T>::axpby(G_.x, Zq.x, blk_, -2.0 * wd, 1.0, nullptr, cx.stream));
+            }
         }
     }
     if (grad) {
@@ -738,6 +775,21 @@ cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const do
     }
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
     return check_device_error(cx.stream);
+}
+
+// Second order (H^(2) = 0). The polarizability gradient follows from the
+// symmetry of the third derivatives of the canonical free energy (whose gradient
+// in H0 is P0): d alpha_d / d H0 = -2 d^2 P / d lambda_d^2 = -4 P2_d.
+template <typename T>
+cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
+                                  double* P2, double* mu2_out, double* omega3, double* grad) {
+    return higher(cx, H1, D, 2, w, P2, mu2_out, omega3, grad);
+}
+
+template <typename T>
+cdmpt_status Solver<T>::response3(Context& cx, const double* H1, int D, double* P3,
+                                  double* mu3_out, double* omega4) {
+    return higher(cx, H1, D, 3, nullptr, P3, mu3_out, omega4, nullptr);
 }
 
 template <typename T>
@@ -750,8 +802,26 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         set_error("at most 16 perturbation directions per solve");
         return CDMPT_ERR_ARG;
     }
-    CDMPT_TRY(reserve(N, D, n));
+    const bool bf16 = sizeof(T) == 4 && o.precision == CDMPT_MIXED_BF16;
+    const bool mixed = sizeof(T) == 4 && (o.precision == CDMPT_MIXED_TF32 || bf16);
+    if (mixed && cx.engine == CDMPT_GEMM_SIMT) {
+        set_error("mixed precision needs the tcgen05 engines");
+        return CDMPT_ERR_ARG;
+    }
+    // trajectory checkpoints: every ck-th Z_k (ckpt_stride < 0: ck = ceil(sqrt(n)))
+    int ck = 0;
+    if (o.ckpt_stride != 0) {
+        if (mixed) {
+            set_error("checkpointing needs the FP64 or FP32 precision: the mixed-precision "
+                      "refinement revisits every stored step");
+            return CDMPT_ERR_ARG;
+        }
+        ck = o.ckpt_stride < 0 ? (int)std::ceil(std::sqrt((double)n) - 1e-9)
+                               : std::min(o.ckpt_stride, n);
+    }
+    CDMPT_TRY(reserve(N, D, n, ck));
     traj_valid_ = q_valid_ = false;
+    replay_iters_ = 0;
     last_mu1_.assign(std::max(D, 0), 0.0);
     cdmpt_stats& st = *cx.st;
     const double s2 = std::ldexp(beta, -(n + 1));
@@ -760,12 +830,6 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         set_error("beta * (lambda_max - lambda_min) / 2^(n+1) = " + std::to_string(s2 * width) +
                   " >= 1: X_0 leaves [0, 1]; use more recursion steps");
         return CDMPT_ERR_RANGE;
-    }
-    const bool bf16 = sizeof(T) == 4 && o.precision == CDMPT_MIXED_BF16;
-    const bool mixed = sizeof(T) == 4 && (o.precision == CDMPT_MIXED_TF32 || bf16);
-    if (mixed && cx.engine == CDMPT_GEMM_SIMT) {
-        set_error("mixed precision needs the tcgen05 engines");
-        return CDMPT_ERR_ARG;
     }
     // engines: "acc" for FP32-accurate products, "fast" for the occupation sweeps
     const int acc = mixed ? (int)CDMPT_GEMM_TC_3XTF32 : engine_of(cx, 0);
@@ -871,6 +935,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     last_s2_ = s2;
     last_n_ = n;
     last_acc_ = acc;
+    last_sweep_tol_ = sweep_tol;
     last_opts_ = o;
 
     // -------------------------------------------------- first-order response
@@ -882,6 +947,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         CDMPT_TRY(Ew<T>::init_z(Z1->x, H1, N, ld, ld, D, -s2, 0.0, cx.stream, Z1->hi, Z1->lo));
         int total = 0, hint = 1;
         for (int k = 0; k < n; ++k) {
+            CDMPT_TRY(need(cx, k));
             {   // S^T = Z1 Z_k (stacked over directions)
                 Epilogue<T> ep;
                 CDMPT_TRY(gemm(cx, rows, N, N, Z1->op(), Z_[k].op(), S_.x, ep, nullptr, acc));
@@ -981,6 +1047,8 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             CDMPT_CUDA_TRY(cudaFreeAsync(tmp, cx.stream));
         }
     }
+    st.cg_iterations_recompute = replay_iters_;
+    st.checkpoint_stride = ck_;
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
     return check_device_error(cx.stream);
 }

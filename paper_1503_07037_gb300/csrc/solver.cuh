@@ -1,5 +1,5 @@
-// Device-resident solver of one canonical DMPT problem (Algorithm 1 to first
-// order) for storage type T. Host code here only sequences kernel launches
+// Device-resident solver of one canonical DMPT problem (Algorithm 1, orders
+// 0 to 3) for storage type T. Host code here only sequences kernel launches
 // and reads back a handful of FP64 scalars (traces, CG status).
 #pragma once
 
@@ -47,8 +47,10 @@ template <typename T>
 class Solver {
 public:
     ~Solver();
-    // (Re)allocate for N x N problems with D directions and n steps.
-    cdmpt_status reserve(int N, int D, int n);
+    // (Re)allocate for N x N problems with D directions and n steps. ckpt > 0
+    // keeps only every ckpt-th Z_k of the trajectory (plus Z_n and W_0); the
+    // other steps are recomputed one segment at a time when they are needed.
+    cdmpt_status reserve(int N, int D, int n, int ckpt);
     cdmpt_status solve(Context& cx, const double* H0, const double* H1, int N, int D,
                        double gmin, double gmax, double trH0, const cdmpt_opts& o, double beta,
                        double nocc, int n, double* P0, double* P1, double* mu_out,
@@ -68,6 +70,14 @@ public:
     // omega3 (host, D doubles, or null): Omega^(3)_d = 1/3 Tr[H1_d P2_d] (Eq. Resp_0).
     cdmpt_status response2(Context& cx, const double* H1, int D, const double* w, double* P2,
                            double* mu2, double* omega3, double* grad);
+
+    // Third-order canonical response of the last solve (Algorithm 1, the order-3
+    // line, H^(2) = H^(3) = 0): P3_d = 1/6 d^3 P / d lambda_d^3 with mu3_d from
+    // Tr P3_d = 0 (mu2_d from an order-2 pass first), and Omega^(4)_d =
+    // 1/4 Tr[H1_d P3_d] (Eq. Resp_0). P3: D x N x N FP64 device array (leading
+    // dimension N) or null; mu3, omega4: host arrays of D doubles, or null.
+    cdmpt_status response3(Context& cx, const double* H1, int D, double* P3, double* mu3,
+                           double* omega4);
     bool trajectory_valid() const { return traj_valid_; }
 
     int ld = 0;
@@ -100,33 +110,56 @@ private:
     cdmpt_status cg(Context& cx, T* X, const CgArgs& a, int* iters_out, double* rel_res0);
     cdmpt_status sweep(Context& cx, const double* H0, double mu, double s2, const cdmpt_opts& o,
                        int n, int engine, double tol, int* cg_iters);
+    // One 0th-order step: W_k = Z_k^2 (unless make_w is false) and, if solve,
+    // Z_{k+1} from the step's linear system. *hint carries the CG chunk size.
+    cdmpt_status step0(Context& cx, int k, int engine, double tol, int maxit, bool make_w,
+                       bool solve, int* hint, int* iters);
+    // Make Z_k, W_k and Z_{k+1} of step k valid (checkpointing: recompute the
+    // segment of step k from its checkpoint unless the segment buffers hold it).
+    cdmpt_status need(Context& cx, int k);
+    // Joint forward sweep of the orders 1..m (m <= 3) for one direction H1d, with
+    // mu^(1..m-1) = mus[0..m-2] known and mu^(m) = 0. Leaves Z^(o)_n in
+    // zo_[o-1][cur_[o-1]].
+    cdmpt_status orders(Context& cx, const double* H1d, int m, const double* mus);
+    cdmpt_status reserve_orders();
+    // Canonical response of order m (2 or 3) for every direction: P^(m), mu^(m),
+    // Omega^(m+1), and for m = 2 the weighted polarizability gradient.
+    cdmpt_status higher(Context& cx, const double* H1, int D, int m, const double* w,
+                        double* Pm, double* mu_out, double* omega, double* grad);
     cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
                         double* max_rel_res);
     cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);
     cdmpt_status compute_q(Context& cx);
     cdmpt_status read_scalars(Context& cx, const double* dev, int count);
-    cdmpt_status reserve_response2(int n);
-    cdmpt_status first_order_trajectory(Context& cx, const double* H1d, double mu1);
     int engine_of(const Context& cx, int override_engine) const;
 
     int N_ = 0, D_ = 0, n_ = 0;
     size_t blk_ = 0;                 // N * ld elements
-    std::vector<Buf<T>> Z_, W_;      // trajectory Z_0..Z_n and W_k = Z_k^2, k < n
+    // trajectory views Z_0..Z_n and W_k = Z_k^2 (k < n). Without checkpointing
+    // each view has its own storage. With stride ck_ the views of Z at
+    // multiples of ck_ and of Z_n own storage (checkpoints), W_0 owns storage,
+    // and the interior views of every segment [j ck_, (j+1) ck_) alias the same
+    // ck_ - 1 Z and ck_ W segment buffers; seg_ is the segment they hold.
+    std::vector<Buf<T>> Z_, W_;
+    int ck_ = 0, seg_ = -1;
+    int replay_iters_ = 0;           // CG iterations spent recomputing segments
     Buf<T> R_, P_, Q_;               // CG work (D' * N rows)
     Buf<T> S_, A1_, RHS_;            // response work
     Buf<T> Z1a_, Z1b_;               // response iterates
     Buf<T> Qmu_;                     // dP/dmu
     Buf<T> Zh_;                      // adjoint of Z_k in the reverse sweep
-    // second order: canonical first-order trajectory Z1_0..Z1_n, A1_k = Z_k Z1_k +
-    // Z1_k Z_k (k < n), the order-2 iterates, A2 and the gradient accumulator
-    std::vector<Buf<T>> Z1t_, A1t_;
-    Buf<T> Z2a_, Z2b_, A2_, G_;
-    int r2_n_ = -1;                  // steps the second-order buffers hold (-1: none)
+    // orders 1..3 of the joint forward sweep: iterates Z^(o)_k, Z^(o)_{k+1}
+    // (zo_[o-1][cur_[o-1]] is the current one), A^(o)_k = sum_{i+j=o} Z^(i)_k
+    // Z^(j)_k, and the gradient accumulator
+    Buf<T> zo_[3][2], ao_[3], G_;
+    int cur_[3] = {0, 0, 0};
+    bool orders_ready_ = false;
     std::vector<double> last_mu1_;
     // state of the last solve, for the response's Q and the adjoint
     bool traj_valid_ = false, q_valid_ = false;
     double last_beta_ = 0, last_s2_ = 0;
     int last_n_ = 0, last_acc_ = 0;
+    double last_sweep_tol_ = 0;
     cdmpt_opts last_opts_{};
     double* sc_ = nullptr;           // device scalars
     std::vector<void*> allocs_;
