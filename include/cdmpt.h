@@ -199,7 +199,7 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
  * P2: D x N x N (row-major FP64), may be NULL. mu2, omega3: host arrays of D
  * doubles, may be NULL. gradH0: N x N, may be NULL. P2 and gradH0 are host or device
  * memory per on_device. The call runs, per direction, one joint forward sweep
- * of orders 1 and 2 with the known mu1 (seven products and two CG solves per
+ * of orders 1 and 2 with the known mu1 (eight products and two CG solves per
  * step) in the precision of the solve.
  * Errors: ERR_ARG (no solve yet, no directions), ERR_CG_MAXITER,
  * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
