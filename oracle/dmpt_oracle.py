@@ -688,3 +688,39 @@ def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M):
         X3n = np.linalg.solve(T, C3 + B3 @ X0n + B2 @ X1n + B1 @ X2n)
         X0, X1, X2, X3 = X0n, X1n, X2n, X3n
     return X0, X1, X2, X3
+
+
+# ----------------------------------------------------------------------------
+# the free energy Omega = Tr[P H0] - T_e S[P] (Eqs. FreeE, SED) as a loss of H0
+# ----------------------------------------------------------------------------
+
+def free_energy(H0, beta, nocc, n: Optional[int] = None, kind: str = "rec",
+                canonical: bool = True, mu: Optional[float] = None, eig=None):
+    """Omega(H0) = Tr[P H0] - (1/beta) S[P] at P = f(H0) and its gradient dOmega/dH0.
+
+    P is the occupation function applied to H0 (the recursion's own function
+    for kind="rec"). With u = ln(f / (1 - f)) per level (u = -beta (e - mu) for
+    Fermi-Dirac, u = 2^(n+1) atanh z0 for the recursion), dOmega/dP = H0 +
+    (1/beta) ln(P (I - P)^-1) has eigenvalues G_i = e_i + u_i / beta, and the
+    chain rule through the canonical first-order response (Sec. II) gives
+      dOmega/dH0 = V diag(f_i + f'_i (G_i - Gbar)) V^T,
+    Gbar = sum_i f'_i G_i / sum_i f'_i (canonical; Gbar = 0 at fixed mu). For
+    Fermi-Dirac G_i = mu, so the canonical gradient is P0 itself.
+    Returns dict(omega, grad, mu, P0).
+    """
+    H0 = np.asarray(H0, dtype=np.float64)
+    nn = n if kind == "rec" else None
+    eps, V = np.linalg.eigh(H0) if eig is None else eig
+    if mu is None:
+        mu = find_mu(eps, nocc, beta, nn)
+    occ = occupation(eps, mu, beta, nn)
+    fp = occupation_derivative(eps, mu, beta, nn)
+    if nn is None:
+        u = -beta * (eps - mu)
+    else:
+        u = 2.0 ** (nn + 1) * np.arctanh(z0_of(eps, mu, beta, nn))
+    G = eps + u / beta
+    gbar = float(np.sum(fp * G) / np.sum(fp)) if canonical else 0.0
+    grad = (V * (occ + fp * (G - gbar))) @ V.T
+    return dict(omega=free_energy_levels(eps, occ, beta), grad=grad, mu=float(mu),
+                P0=(V * occ) @ V.T)

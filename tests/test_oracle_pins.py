@@ -617,3 +617,62 @@ def test_third_order_pins_catch_planted_mistakes(monkeypatch):
         return r
     monkeypatch.setattr(o.dmpt_oracle, "response2", no_mu2)
     assert err() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# the free energy as a loss of H0 (Eqs. FreeE, SED)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n,canonical", [("fd", None, True), ("rec", 8, True),
+                                              ("rec", 8, False)])
+def test_free_energy_gradient_central_differences(kind, n, canonical):
+    """<dOmega/dH0, E> == (Omega(H0 + hE) - Omega(H0 - hE)) / 2h along random symmetric E
+    (canonical: mu re-found at every point; grand canonical: mu held)."""
+    H0 = _rand_sym(14, 51, 0.5)
+    beta, nocc, h = 4.0, 6.0, 1e-5
+    r = o.free_energy(H0, beta, nocc, n=n, kind=kind)
+    mu = None if canonical else r["mu"]
+    g = o.free_energy(H0, beta, nocc, n=n, kind=kind, canonical=canonical, mu=mu)["grad"]
+    for seed in range(5):
+        E = _rand_sym(14, 100 + seed, 1.0)
+        wp = o.free_energy(H0 + h * E, beta, nocc, n=n, kind=kind, mu=mu)["omega"]
+        wm = o.free_energy(H0 - h * E, beta, nocc, n=n, kind=kind, mu=mu)["omega"]
+        fd = (wp - wm) / (2 * h)
+        assert abs(fd - np.sum(g * E)) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_free_energy_fermi_dirac_gradient_is_P0_and_grand_potential_identity():
+    """Fermi-Dirac: the canonical gradient is P0 (the entropy term cancels the response,
+    Eq. EntDer), and Omega = mu N_occ + (1/beta) sum_i ln(1 - f_i)."""
+    H0 = _rand_sym(16, 52, 0.5)
+    beta, nocc = 6.0, 7.0
+    r = o.free_energy(H0, beta, nocc, kind="fd")
+    assert o.rel_frobenius(r["grad"], r["P0"]) < 1e-13
+    eps = np.linalg.eigvalsh(H0)
+    ln_1mf = -np.logaddexp(0.0, -beta * (eps - r["mu"]))     # ln(1 - f), no cancellation
+    assert abs(r["omega"] - (r["mu"] * nocc + np.sum(ln_1mf) / beta)) < 1e-13 * abs(r["omega"])
+
+
+def test_free_energy_of_recursion_equals_telescoped_log_determinants():
+    """For P = X_n of n recursion steps, 1 - x_{k+1} = (1 - x_k)^2 / T_k with
+    T_k = x_k^2 + (1 - x_k)^2, so ln det(I - P) = 2^n ln det(I - X_0) -
+    sum_k 2^(n-1-k) ln det T_k. With ln(P (I - P)^-1) = 2^(n+1) atanh(Z_0) this gives
+    Omega = mu Tr P + (1/beta) ln det(I - P) + (2^(n+1)/beta) Tr[P (atanh Z_0 - Z_0)],
+    checked here with dense slogdet along Algorithm 1's own iterates."""
+    H0 = _rand_sym(20, 53, 0.5)
+    beta, nocc, n = 10.0, 9.0, 8
+    r = o.free_energy(H0, beta, nocc, n=n, kind="rec")
+    mu = r["mu"]
+    N = H0.shape[0]
+    I = np.eye(N)
+    X = 0.5 * I - beta / 2.0 ** (n + 2) * (H0 - mu * I)
+    Z0 = 2 * X - I
+    logdet = 2.0 ** n * np.linalg.slogdet(I - X)[1]
+    for k in range(n):
+        T = X @ X + (I - X) @ (I - X)
+        logdet -= 2.0 ** (n - 1 - k) * np.linalg.slogdet(T)[1]
+        X = np.linalg.solve(T, X @ X)
+    w, U = np.linalg.eigh(Z0)
+    R = (U * (np.arctanh(w) - w)) @ U.T
+    omega = mu * np.trace(X) + logdet / beta + 2.0 ** (n + 1) / beta * np.trace(X @ R)
+    assert abs(omega - r["omega"]) < 1e-11 * abs(r["omega"])
