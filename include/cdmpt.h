@@ -221,6 +221,25 @@ cdmpt_status cdmpt_response2(cdmpt_handle* h, const double* w, double* P2, doubl
 cdmpt_status cdmpt_response3(cdmpt_handle* h, double* P3, double* mu3, double* omega4,
                              int on_device);
 
+/* Free energy of the last solve, Omega = Tr[P0 H0] - T_e S[P0] with the
+ * entropy S[P] = -Tr[P ln P + (I - P) ln(I - P)] (Eqs. FreeE, SED; k_B = 1,
+ * T_e = 1/beta), for the recursion's own P0 (the n-step function of Eq.
+ * Rec_F_2), and optionally its gradient gradH0 = dOmega/dH0 under the solve's
+ * constraint (canonical: Tr P0 = N_occ held, mu follows H0; grand canonical:
+ * mu held). No eigenvalues are used: per level 1 - x_{k+1} = (1 - x_k)^2 /
+ * (x_k^2 + (1 - x_k)^2), so ln det(I - P0) is a weighted sum of the
+ * log-determinants of I - Z_0 and of the step matrices A_k = I + Z_k^2, each
+ * found by one CG solve and a short series; the entropy's remaining term
+ * needs atanh(Z_0) - Z_0, a series in Z_0^2. For the Fermi-Dirac function the
+ * canonical gradient would be P0 (App. B); for the n-step function it is P0
+ * plus one adjoint sweep (as cdmpt_vjp_P0) of mu I + T_e ln(P0 (I - P0)^-1) -
+ * (H0 - mu I), a correction of the size of the recursion's truncation error.
+ * omega: host double, may be NULL. gradH0: N x N FP64, host or device per
+ * on_device, may be NULL (then no adjoint sweep runs). Must follow a
+ * successful cdmpt_solve on this handle.
+ * Errors: ERR_ARG (no solve yet), ERR_CG_MAXITER, ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, int on_device);
+
 /* Spectral interval of a symmetric matrix from Gershgorin discs:
  * bounds[0] = min_i (H_ii - sum_{j != i} |H_ij|), bounds[1] = max_i (H_ii + sum_{j != i} |H_ij|).
  * Every eigenvalue of H lies in [bounds[0], bounds[1]]. cdmpt_solve needs

@@ -91,7 +91,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
-           "cdmpt_response3"]
+           "cdmpt_response3", "cdmpt_free_energy"]
 
 
 def lib() -> ctypes.CDLL:
@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_response3": (I, [P, P, P, P, I]),
+        "cdmpt_free_energy": (I, [P, P, P, I]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -401,6 +402,18 @@ class Handle:
                self.h)
         return {"P3": P3, "mu3": mu3[:D].copy(), "omega4": om4[:D].copy()}
 
+    def free_energy(self, want_grad=True, device="cuda"):
+        """Free energy of the last solve, Omega = Tr[P0 H0] - T_e S[P0] (Eqs. FreeE, SED), for
+        the recursion's own P0: dict(omega, grad) with grad = dOmega/dH0 (float64 tensor)."""
+        import torch
+        N = self.N
+        dev = torch.device(device)
+        on_dev = 1 if dev.type == "cuda" else 0
+        G = torch.empty((N, N), dtype=torch.float64, device=dev) if want_grad else None
+        om = ctypes.c_double(0.0)
+        _check(lib().cdmpt_free_energy(self.h, ctypes.addressof(om), _ptr(G), on_dev), self.h)
+        return {"omega": om.value, "grad": G}
+
     def stats(self):
         return get_stats(self.h)
 
@@ -562,6 +575,37 @@ class Polarizability:
             def backward(ctx, g):
                 w = g.detach().to(torch.float64).cpu().numpy()
                 return handle.response2(weights=w, want_P2=False, device=g.device.type)["grad"]
+
+        return _Fn.apply(H0)
+
+
+class FreeEnergy:
+    """Differentiable free energy Omega(H0) = Tr[P0 H0] - T_e S[P0] (torch.autograd).
+
+    omega = FreeEnergy.apply(H0, beta, nocc, n, handle) returns the scalar free
+    energy (Eqs. FreeE, SED) of the recursion's P0 for the symmetric CUDA
+    float64 tensor H0; backward gives dL/dH0 = (dL/dOmega) dOmega/dH0 from
+    cdmpt_free_energy (P0 plus one adjoint sweep). Call backward before the
+    next solve on the same handle.
+    """
+
+    @staticmethod
+    def apply(H0, beta, nocc, n, handle):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, H):
+                handle.set_H(H.detach(), None)
+                handle.solve(beta, nocc, n, want_P0=False, want_P1=False)
+                r = handle.free_energy(want_grad=True, device=H.device.type)
+                ctx.save_for_backward(r["grad"])
+                return torch.tensor(r["omega"], dtype=torch.float64, device=H.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                (grad,) = ctx.saved_tensors
+                return g * grad
 
         return _Fn.apply(H0)
 

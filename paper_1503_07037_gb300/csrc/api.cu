@@ -331,6 +331,37 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
     return CDMPT_OK;
 }
 
+cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (!h->solved)
+        return fail_msg(h, CDMPT_ERR_ARG, "free_energy: no completed solve on this handle");
+    cudaStream_t s = h->cx.stream;
+    const size_t bytes = (size_t)h->N * h->N * sizeof(double);
+    double* g = gradH0;
+    double* tmp = nullptr;
+    if (gradH0 && !on_device) {
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, bytes, s));
+        g = tmp;
+    }
+    cdmpt_stats keep = h->st;
+    h->cx.st = &h->st;
+    double om = 0.0;
+    cdmpt_status st;
+    if (h->opts.precision == CDMPT_FP64)
+        st = h->sd ? h->sd->free_energy(h->cx, &om, g) : CDMPT_ERR_ARG;
+    else
+        st = h->sf ? h->sf->free_energy(h->cx, &om, g) : CDMPT_ERR_ARG;
+    h->st = keep;
+    if (st == CDMPT_OK && gradH0 && !on_device) {
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, g, bytes, cudaMemcpyDeviceToHost, s));
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st != CDMPT_OK) return fail(h, st);
+    if (omega) *omega = om;
+    return CDMPT_OK;
+}
+
 // Orders 2 and 3 share the marshalling: P^(m) (and the gradient) through a
 // device scratch when the caller's buffers are on the host.
 static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm, double* mu,

@@ -49,6 +49,7 @@ enum Slot {
     S_TRQ = 10,     // Tr Q
     S_TRZ1 = 16,    // Tr Z1_d (d < 16)
     S_ALPHA = 32,   // sum P1_d * H1_d (d < 16)
+    S_FE = 48,      // free energy: traces and dots (3 slots)
     S_NSLOTS = 64
 };
 constexpr int kMaxD = 16;
@@ -793,6 +794,159 @@ cdmpt_status Solver<T>::response3(Context& cx, const double* H1, int D, double* 
 }
 
 template <typename T>
+cdmpt_status Solver<T>::logdet(Context& cx, const Buf<T>& M, double a, double b, double lo,
+                               double hi, double eps, double* out) {
+    const int N = N_;
+    const cdmpt_opts& o = last_opts_;
+    const int acc = last_acc_;
+    const double c = std::sqrt(lo * hi);
+    const double r = (std::sqrt(hi) - std::sqrt(lo)) / (std::sqrt(hi) + std::sqrt(lo));
+    // terms j = 0..J of sum Tr(Y^(2j+1)) / (2j+1), |y| <= r: remainder below eps per level
+    int J = 0;
+    while (J < 64 && std::pow(r, 2 * J + 3) / ((2 * J + 3) * (1.0 - r * r)) > eps) ++J;
+    Buf<T>& Y = zo_[0][0];
+    Buf<T>& Y2 = zo_[0][1];
+    Buf<T>* Pw = &zo_[1][0];
+    Buf<T>* Pn = &zo_[1][1];
+    // Y (A + c I) = A - c I with A = a I + b M: operator X -> (a + c) X + b X M
+    CDMPT_TRY(Ew<T>::axpby(RHS_.x, M.x, blk_, b, 0.0, nullptr, cx.stream));
+    CDMPT_TRY(Ew<T>::add_diag(RHS_.x, N, ld, 1, a - c, cx.stream));
+    CgArgs g;
+    g.W = &M;
+    g.s = a + c;
+    g.t = b;
+    g.rhs = RHS_.x;
+    g.rows = N;
+    g.tol = o.cg_tol;
+    g.maxit = o.cg_maxit;
+    g.init_engine = g.iter_engine = acc;
+    g.hint = 4;
+    int it = 0;
+    CDMPT_TRY(cg(cx, Y.x, g, &it, nullptr));
+    CDMPT_TRY(Ew<T>::symmetrize(Y.x, N, ld, 1, cx.stream, Y.hi, Y.lo));
+    auto trace_of = [&](const Buf<T>& B, double* v) -> cdmpt_status {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, sizeof(double), cx.stream));
+        CDMPT_TRY(Ew<T>::trace(B.x, N, ld, 1, sc_ + S_FE, cx.stream));
+        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+        *v = cx.pinned[S_FE];
+        return CDMPT_OK;
+    };
+    double sum = 0.0, t = 0.0;
+    CDMPT_TRY(trace_of(Y, &t));
+    sum = t;
+    if (J > 0) {
+        Epilogue<T> ep;   // Y^2 (symmetric)
+        ep.Dhi = Y2.hi;
+        ep.Dlo = Y2.lo;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N, N, N, Y.op(), Y.op(), Y2.x, ep, nullptr, acc));
+    }
+    const Buf<T>* odd = &Y;
+    for (int j = 1; j <= J; ++j) {   // Y^(2j+1) = Y^(2j-1) Y^2
+        Epilogue<T> ep;
+        ep.Dhi = Pn->hi;
+        ep.Dlo = Pn->lo;
+        CDMPT_TRY(gemm(cx, N, N, N, odd->op(), Y2.op(), Pn->x, ep, nullptr, acc));
+        CDMPT_TRY(trace_of(*Pn, &t));
+        sum += t / (2 * j + 1);
+        odd = Pn;
+        std::swap(Pw, Pn);
+    }
+    *out = N * std::log(c) + 2.0 * sum;
+    return CDMPT_OK;
+}
+
+// Free energy without eigenvalues. For P = X_n of the recursion,
+// 1 - x_{k+1} = (1 - x_k)^2 / t_k with t_k = x_k^2 + (1 - x_k)^2 = (1 + z_k^2)/2
+// per level, so
+//   ln det(I - P) = 2^n ln det(I - X_0) - sum_k 2^(n-1-k) ln det(A_k / 2)
+//                 = 2^n ln det(I - Z_0) - sum_k 2^(n-1-k) ln det A_k - N ln 2,
+// every determinant of a matrix with spectrum well inside (0, 2]. With
+// ln(P (I - P)^-1) = 2^(n+1) atanh(Z_0) (the closed form of n steps, Appendix A)
+// and H0 - mu I = -T 2^(n+1) Z_0, the functional of Eqs. (FreeE), (SED) becomes
+//   Omega = mu Tr P + T ln det(I - P) + T 2^(n+1) Tr[P R],  R = atanh(Z_0) - Z_0,
+// with R = Z_0 W_0 sum_j W_0^j / (2j + 3) by Horner in W_0 = Z_0^2. dOmega/dP =
+// H0 + T ln(P (I - P)^-1) = mu I + T 2^(n+1) R, so the gradient is P0 plus the
+// adjoint of the recursion applied to that matrix (vjp_p0 carries the
+// canonical or fixed-mu constraint of the solve).
+template <typename T>
+cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
+    if (!traj_valid_) {
+        set_error("free energy: no completed solve on this handle");
+        return CDMPT_ERR_ARG;
+    }
+    const int n = last_n_, N = N_;
+    const int acc = last_acc_;
+    const double beta = last_beta_, mu = last_mu_, rho = std::min(last_rho_, 1.0 - 1e-12);
+    const double Te = 1.0 / beta;
+    const double eps = sizeof(T) == 8 ? 1e-17 : 1e-12;
+    CDMPT_TRY(reserve_orders());
+    // ln det(I - Z_0): spectrum of I - Z_0 in [1 - rho, 1 + rho]
+    double ld0 = 0.0;
+    CDMPT_TRY(logdet(cx, Z_[0], 1.0, -1.0, 1.0 - rho, 1.0 + rho, eps, &ld0));
+    // ln det A_k, A_k = I + W_k with W_k in [0, tanh(2^k atanh rho)^2]
+    double lda = 0.0;
+    const double u0 = std::atanh(rho);
+    for (int k = 0; k < n; ++k) {
+        CDMPT_TRY(need(cx, k));
+        const double zk = std::tanh(std::ldexp(u0, k));
+        double v = 0.0;
+        CDMPT_TRY(logdet(cx, W_[k], 1.0, 1.0, 1.0, 1.0 + zk * zk, eps, &v));
+        lda += std::ldexp(v, n - 1 - k);
+    }
+    const double logdet_1mp = std::ldexp(ld0, n) - lda - N * std::log(2.0);
+    // R = Z_0 W_0 h(W_0), h = sum_{j=0..J} W_0^j / (2j + 3), Horner from the top
+    int J = 0;
+    while (J < 200 && std::pow(rho, 2 * J + 2) > eps * (2 * J + 5) / 3.0) ++J;
+    Buf<T>* Hc = &ao_[0];
+    Buf<T>* Hn = &ao_[1];
+    Buf<T>& R = ao_[2];
+    CDMPT_CUDA_TRY(cudaMemsetAsync(Hc->x, 0, blk_ * sizeof(T), cx.stream));
+    if (Hc->hi) CDMPT_CUDA_TRY(cudaMemsetAsync(Hc->hi, 0, blk_ * sizeof(T), cx.stream));
+    if (Hc->lo) CDMPT_CUDA_TRY(cudaMemsetAsync(Hc->lo, 0, blk_ * sizeof(T), cx.stream));
+    CDMPT_TRY(Ew<T>::add_diag(Hc->x, N, ld, 1, 1.0 / (2 * J + 3), cx.stream, Hc->hi, Hc->lo));
+    for (int j = J - 1; j >= -1; --j) {   // j >= 0: h <- W_0 h + I/(2j+3); j = -1: W_0 h
+        Epilogue<T> ep;
+        ep.gamma = j >= 0 ? 1.0 / (2 * j + 3) : 0.0;
+        ep.Dhi = Hn->hi;
+        ep.Dlo = Hn->lo;
+        CDMPT_TRY(gemm(cx, N, N, N, W_[0].op(), Hc->op(), Hn->x, ep, nullptr, acc));
+        std::swap(Hc, Hn);
+    }
+    {
+        Epilogue<T> ep;   // R = Z_0 (W_0 h)
+        ep.Dhi = R.hi;
+        ep.Dlo = R.lo;
+        CDMPT_TRY(gemm(cx, N, N, N, Z_[0].op(), Hc->op(), R.x, ep, nullptr, acc));
+    }
+    // Tr P0 = (N + Tr Z_n)/2 and Tr[P0 R] = (Tr R + <Z_n, R>)/2
+    CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, 3 * sizeof(double), cx.stream));
+    CDMPT_TRY(Ew<T>::trace(Z_[n].x, N, ld, 1, sc_ + S_FE, cx.stream));
+    CDMPT_TRY(Ew<T>::trace(R.x, N, ld, 1, sc_ + S_FE + 1, cx.stream));
+    CDMPT_TRY(Ew<T>::dot(Z_[n].x, R.x, blk_, sc_ + S_FE + 2, nullptr, cx.stream));
+    CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+    const double trP = 0.5 * (N + cx.pinned[S_FE]);
+    const double trPR = 0.5 * (cx.pinned[S_FE + 1] + cx.pinned[S_FE + 2]);
+    const double scale = std::ldexp(Te, n + 1);   // T 2^(n+1)
+    if (omega) *omega = mu * trP + Te * logdet_1mp + scale * trPR;
+    if (grad) {
+        const size_t nn = (size_t)N * N;
+        double* tmp = nullptr;
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 2 * nn * sizeof(double), cx.stream));
+        double* G0 = tmp;
+        double* P0 = tmp + nn;
+        CDMPT_TRY(Ew<T>::to_f64(G0, N, R.x, ld, N, N, scale, mu, cx.stream));
+        CDMPT_TRY(Ew<T>::to_f64(P0, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
+        cdmpt_status s = vjp_p0(cx, G0, grad);
+        if (s == CDMPT_OK) s = Ew<double>::lincomb(grad, grad, 1.0, P0, 1.0, nn, cx.stream);
+        cudaFreeAsync(tmp, cx.stream);
+        CDMPT_TRY(s);
+    }
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
+    return check_device_error(cx.stream);
+}
+
+template <typename T>
 cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, int N, int D,
                               double gmin, double gmax, double trH0, const cdmpt_opts& o,
                               double beta, double nocc, int n, double* P0, double* P1,
@@ -932,6 +1086,8 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     if (mu_out) *mu_out = mu;
     traj_valid_ = true;
     last_beta_ = beta;
+    last_mu_ = mu;
+    last_rho_ = s2 * std::max(gmax - mu, mu - gmin);
     last_s2_ = s2;
     last_n_ = n;
     last_acc_ = acc;

@@ -78,6 +78,12 @@ public:
     // dimension N) or null; mu3, omega4: host arrays of D doubles, or null.
     cdmpt_status response3(Context& cx, const double* H1, int D, double* P3, double* mu3,
                            double* omega4);
+
+    // Free energy of the last solve, Omega = Tr[P0 H0] - T_e S[P0] (Eqs. FreeE,
+    // SED; k_B = 1, T_e = 1/beta) for the recursion's own P0, evaluated without
+    // eigenvalues, and optionally grad = dOmega/dH0 under the solve's constraint
+    // (N x N FP64 device array, leading dimension N). omega: host double or null.
+    cdmpt_status free_energy(Context& cx, double* omega, double* grad);
     bool trajectory_valid() const { return traj_valid_; }
 
     int ld = 0;
@@ -122,6 +128,12 @@ private:
     // zo_[o-1][cur_[o-1]].
     cdmpt_status orders(Context& cx, const double* H1d, int m, const double* mus);
     cdmpt_status reserve_orders();
+    // Tr ln(a I + b M) for symmetric M whose spectrum puts a I + b M inside
+    // [lo, hi] (0 < lo <= hi), by the Cayley transform Y = (A - cI)(A + cI)^-1,
+    // c = sqrt(lo hi), one CG solve and the odd series of 2 Tr atanh(Y),
+    // truncated where the remainder falls below eps per level. Uses zo_ buffers.
+    cdmpt_status logdet(Context& cx, const Buf<T>& M, double a, double b, double lo, double hi,
+                        double eps, double* out);
     // Canonical response of order m (2 or 3) for every direction: P^(m), mu^(m),
     // Omega^(m+1), and for m = 2 the weighted polarizability gradient.
     cdmpt_status higher(Context& cx, const double* H1, int D, int m, const double* w,
@@ -158,6 +170,7 @@ private:
     // state of the last solve, for the response's Q and the adjoint
     bool traj_valid_ = false, q_valid_ = false;
     double last_beta_ = 0, last_s2_ = 0;
+    double last_mu_ = 0, last_rho_ = 0;   // mu and max |z0| over the Gershgorin interval
     int last_n_ = 0, last_acc_ = 0;
     double last_sweep_tol_ = 0;
     cdmpt_opts last_opts_{};
