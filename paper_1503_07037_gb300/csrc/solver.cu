@@ -503,7 +503,7 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
 // Z_0 = -s2 (H0 - mu I) and the canonical dmu = Tr(Q dH0) / Tr Q give
 //   grad = -s2 Zh_0 + s2 Tr(Zh_0) Q / Tr Q.
 template <typename T>
-cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
+cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad, double p0_weight) {
     if (!traj_valid_) {
         set_error("vjp: no completed solve on this handle");
         return CDMPT_ERR_ARG;
@@ -569,7 +569,11 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad) {
     const double trQ = cx.pinned[S_TRQ], trZh = cx.pinned[S_TRQ + 1];
     const double c = (!gc && trQ > 0) ? last_s2_ * trZh / trQ : 0.0;
     CDMPT_TRY(Ew<T>::lincomb(Zh_.x, Zh_.x, -last_s2_, Qmu_.x, c, blk_, cx.stream));
-    CDMPT_TRY(Ew<T>::to_f64(grad, N, Zh_.x, ld, N, N, 1.0, 0.0, cx.stream));
+    // optional + p0_weight P0 = p0_weight (I + Z_n) / 2, added in the padded buffer (the
+    // identity part through the diagonal shift of the FP64 conversion)
+    if (p0_weight != 0.0)
+        CDMPT_TRY(Ew<T>::axpby(Zh_.x, Z_[n].x, blk_, 0.5 * p0_weight, 1.0, nullptr, cx.stream));
+    CDMPT_TRY(Ew<T>::to_f64(grad, N, Zh_.x, ld, N, N, 1.0, 0.5 * p0_weight, cx.stream));
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
     return check_device_error(cx.stream);
 }
@@ -929,17 +933,12 @@ cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
     const double trPR = 0.5 * (cx.pinned[S_FE + 1] + cx.pinned[S_FE + 2]);
     const double scale = std::ldexp(Te, n + 1);   // T 2^(n+1)
     if (omega) *omega = mu * trP + Te * logdet_1mp + scale * trPR;
-    if (grad) {
-        const size_t nn = (size_t)N * N;
-        double* tmp = nullptr;
-        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 2 * nn * sizeof(double), cx.stream));
-        double* G0 = tmp;
-        double* P0 = tmp + nn;
+    if (grad) {   // grad = vjp(mu I + T 2^(n+1) R) + P0
+        double* G0 = nullptr;
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&G0, (size_t)N * N * sizeof(double), cx.stream));
         CDMPT_TRY(Ew<T>::to_f64(G0, N, R.x, ld, N, N, scale, mu, cx.stream));
-        CDMPT_TRY(Ew<T>::to_f64(P0, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
-        cdmpt_status s = vjp_p0(cx, G0, grad);
-        if (s == CDMPT_OK) s = Ew<double>::lincomb(grad, grad, 1.0, P0, 1.0, nn, cx.stream);
-        cudaFreeAsync(tmp, cx.stream);
+        const cdmpt_status s = vjp_p0(cx, G0, grad, 1.0);
+        cudaFreeAsync(G0, cx.stream);
         CDMPT_TRY(s);
     }
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));

@@ -59,7 +59,8 @@ public:
     // Vector-Jacobian product of the last solve: grad = d Tr[G0 P0] / d H0 under
     // the canonical constraint, by a reverse sweep through the stored
     // trajectory. G0 and grad are N x N FP64 device arrays (leading dimension N).
-    cdmpt_status vjp_p0(Context& cx, const double* G0, double* grad);
+    // p0_weight != 0 adds p0_weight P0 to the gradient.
+    cdmpt_status vjp_p0(Context& cx, const double* G0, double* grad, double p0_weight = 0.0);
 
     // Second-order canonical response of the last solve (Algorithm 1, order 2,
     // H^(2) = 0) for each of the D directions of H1 (device, D x N x ld FP64):
