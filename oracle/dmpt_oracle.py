@@ -724,3 +724,57 @@ def free_energy(H0, beta, nocc, n: Optional[int] = None, kind: str = "rec",
     grad = (V * (occ + fp * (G - gbar))) @ V.T
     return dict(omega=free_energy_levels(eps, occ, beta), grad=grad, mu=float(mu),
                 P0=(V * occ) @ V.T)
+
+
+# ----------------------------------------------------------------------------
+# non-orthogonal basis (Sec. IV, Eq. Fermi_D): D = Z f(Z^T F Z) Z^T with Z^T S Z = I
+# ----------------------------------------------------------------------------
+
+def cholesky_factor(S):
+    """Inverse Cholesky factor: Linv = L^-1 with S = L L^T, so Z = Linv^T satisfies
+    Z^T S Z = I. (A different inverse factor than the Loewdin S^(-1/2) the library uses;
+    D and every derivative mapped back to the non-orthogonal basis do not depend on the
+    choice.)"""
+    import scipy.linalg
+    L = np.linalg.cholesky(np.asarray(S, dtype=np.float64))
+    return scipy.linalg.solve_triangular(L, np.eye(L.shape[0]), lower=True)
+
+
+def to_orthogonal(X, Linv):
+    """X_perp = Z^T X Z = Linv X Linv^T (Hamiltonian-like matrices, Eq. Fermi_D)."""
+    return Linv @ X @ Linv.T
+
+
+def from_orthogonal(P, Linv):
+    """D = Z P Z^T = Linv^T P Linv (density-like matrices and gradients with respect to F:
+    F_perp = Z^T F Z gives dL/dF = Z (dL/dF_perp) Z^T)."""
+    return Linv.T @ P @ Linv
+
+
+def solve_nonorthogonal(F, h1, S, beta, nocc, n: Optional[int] = None, kind: str = "rec",
+                        order: int = 1, canonical: bool = True, mu: Optional[float] = None):
+    """Canonical DMPT in a non-orthogonal basis (Eq. Fermi_D with the perturbation h1 of
+    Eq. FirstOrderPRT, no self-consistency): the orthogonal oracle applied to
+    F_perp = Z^T F Z and h1_perp = Z^T h1 Z, results mapped back. Returns D0, D1 (D, N, N),
+    mu, mu1, alpha (basis independent), omega, and for order >= 2 also D2, mu2 and
+    grad_alpha = d alpha / dF (D, N, N); free-energy gradient dOmega/dF as grad_omega."""
+    h1 = np.asarray(h1, dtype=np.float64)
+    if h1.ndim == 2:
+        h1 = h1[None]
+    Linv = cholesky_factor(S)
+    Fp = to_orthogonal(F, Linv)
+    h1p = np.stack([to_orthogonal(h1[d], Linv) for d in range(h1.shape[0])])
+    if order >= 2:
+        r = response2(Fp, h1p, beta, nocc, n, kind, canonical=canonical, mu=mu)
+    else:
+        r = solve(Fp, h1p, beta, nocc, n, kind, canonical=canonical, mu=mu)
+    fe = free_energy(Fp, beta, nocc, n, kind, canonical=canonical, mu=r["mu"] if not canonical
+                     else None)
+    out = dict(mu=r["mu"], mu1=r["mu1"], alpha=r["alpha"], omega=r["omega"], Linv=Linv,
+               D0=from_orthogonal(r["P0"], Linv),
+               D1=np.stack([from_orthogonal(p, Linv) for p in r["P1"]]),
+               grad_omega=from_orthogonal(fe["grad"], Linv))
+    if order >= 2:
+        out.update(mu2=r["mu2"], D2=np.stack([from_orthogonal(p, Linv) for p in r["P2"]]),
+                   grad_alpha=np.stack([from_orthogonal(g, Linv) for g in r["grad_alpha"]]))
+    return out

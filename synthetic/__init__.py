@@ -10,6 +10,7 @@ from .tightbinding import (  # noqa: F401
     cubic_lattice,
     banded_random,
     cluster_sizes,
+    nonorthogonal_cluster,
     clusters,
     workload,
     WORKLOADS,

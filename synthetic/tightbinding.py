@@ -126,6 +126,33 @@ def _cluster(Nb: int, seed: int, beta: float, n: int) -> Problem:
                    meta={"seed": seed})
 
 
+def nonorthogonal_cluster(Nb: int = 256, seed: int = 2001, beta: float = 20.0, n: int = 14,
+                          s0: float = 0.3, sigma: float = 0.8) -> Problem:
+    """Non-orthogonal s-orbital cluster (extended-Hueckel-like), the input of Eq. Fermi_D.
+
+    Sites uniform in a cube of side Nb^(1/3) (unit density). Overlap
+    S = (1 - s0) I + s0 G with the Gaussian kernel G_ij = exp(-r_ij^2 / (2 sigma^2)), which
+    is positive semidefinite, so S is positive definite with eigenvalues >= 1 - s0. Fockian
+    F_ii = eps_i ~ N(0, 0.3^2), F_ij = -4 S_ij. Dipoles in the Mulliken form
+    (h1)_ij = S_ij (x_i + x_j) / 2 for x, y, z (centred coordinates). F is returned as H0,
+    the dipoles as H1 and S in meta["S"]; N_occ = Nb / 2.
+    """
+    rng = np.random.default_rng(seed)
+    side = Nb ** (1.0 / 3.0)
+    pos = rng.uniform(0.0, side, size=(Nb, 3))
+    eps = rng.normal(0.0, 0.3, size=Nb)
+    diff = pos[:, None, :] - pos[None, :, :]
+    r2 = np.einsum("ijk,ijk->ij", diff, diff)
+    S = (1.0 - s0) * np.eye(Nb) + s0 * np.exp(-r2 / (2.0 * sigma * sigma))
+    S = 0.5 * (S + S.T)
+    F = -4.0 * S
+    F[np.diag_indices(Nb)] = eps
+    c = pos - pos.mean(axis=0)
+    H1 = np.stack([S * 0.5 * (c[:, a][:, None] + c[:, a][None, :]) for a in range(3)])
+    return Problem(f"nonorth_cluster_{Nb}", F, H1, nocc=float(Nb // 2), beta=beta, n=n,
+                   meta={"seed": seed, "S": S})
+
+
 def cluster_sizes(B: int = 96, seed: int = 1005, nmin: int = 128, nmax: int = 1536) -> List[int]:
     """The sizes N_b ~ U{nmin..nmax} that clusters() draws (without building the systems)."""
     rng = np.random.default_rng(seed)

@@ -676,3 +676,57 @@ def test_free_energy_of_recursion_equals_telescoped_log_determinants():
     R = (U * (np.arctanh(w) - w)) @ U.T
     omega = mu * np.trace(X) + logdet / beta + 2.0 ** (n + 1) / beta * np.trace(X @ R)
     assert abs(omega - r["omega"]) < 1e-11 * abs(r["omega"])
+
+
+# --------------------------------------------------------------------------
+# non-orthogonal basis (Sec. IV, Eq. Fermi_D)
+# --------------------------------------------------------------------------
+
+def _nonorth_case(N=40, seed=71):
+    p = syn.nonorthogonal_cluster(N, seed=seed, beta=6.0, n=10)
+    return p.H0, p.H1[0], p.meta["S"], p.beta, p.nocc, p.n
+
+
+def test_nonorthogonal_D_equals_generalized_eigenproblem():
+    """D from the Cholesky route == C f(e) C^T from LAPACK's generalized symmetric
+    eigensolver (F C = S C e, C^T S C = I), and Tr[D S] = N_occ, Tr[D1 S] = 0."""
+    import scipy.linalg
+    F, h1, S, beta, nocc, n = _nonorth_case()
+    r = o.solve_nonorthogonal(F, h1, S, beta, nocc, n=n)
+    e, C = scipy.linalg.eigh(F, S)
+    D = (C * o.occupation(e, r["mu"], beta, n)) @ C.T
+    assert o.rel_frobenius(r["D0"], D) < 1e-12
+    assert abs(np.trace(r["D0"] @ S) - nocc) < 1e-10
+    assert abs(np.trace(r["D1"][0] @ S)) < 1e-10
+
+
+def test_nonorthogonal_response_is_covariant_under_a_change_of_basis():
+    """With F' = B^T F B, S' = B^T S B, h1' = B^T h1 B for an invertible B: D' = B^-1 D B^-T,
+    D1' likewise, mu, mu1 and alpha unchanged, and d alpha / dF' = B^-1 (d alpha / dF) B^-T."""
+    F, h1, S, beta, nocc, n = _nonorth_case()
+    rng = np.random.default_rng(5)
+    B = np.eye(F.shape[0]) + 0.2 * rng.standard_normal(F.shape)
+    Bi = np.linalg.inv(B)
+    r = o.solve_nonorthogonal(F, h1, S, beta, nocc, n=n, order=2)
+    q = o.solve_nonorthogonal(B.T @ F @ B, B.T @ h1 @ B, B.T @ S @ B, beta, nocc, n=n, order=2)
+    assert o.rel_frobenius(q["D0"], Bi @ r["D0"] @ Bi.T) < 1e-10
+    assert o.rel_frobenius(q["D1"][0], Bi @ r["D1"][0] @ Bi.T) < 1e-9
+    assert o.rel_frobenius(q["grad_alpha"][0], Bi @ r["grad_alpha"][0] @ Bi.T) < 1e-9
+    assert abs(q["alpha"][0] - r["alpha"][0]) < 1e-10 * abs(r["alpha"][0])
+    assert abs(q["mu1"][0] - r["mu1"][0]) < 1e-10
+
+
+def test_nonorthogonal_D1_and_alpha_gradient_equal_finite_differences():
+    """D1 = dD/dlambda along F + lambda h1 (canonical), and <d alpha/dF, E> by central
+    differences of alpha(F + hE) along a random symmetric E."""
+    F, h1, S, beta, nocc, n = _nonorth_case(30, 72)
+    h = 1e-4
+    r = o.solve_nonorthogonal(F, h1, S, beta, nocc, n=n, order=2)
+    D = {k: o.solve_nonorthogonal(F + k * h * h1, h1, S, beta, nocc, n=n)["D0"]
+         for k in (-2, -1, 1, 2)}
+    fd = (D[-2] - 8 * D[-1] + 8 * D[1] - D[2]) / (12 * h)
+    assert o.rel_frobenius(r["D1"][0], fd) < 1e-8
+    E = _rand_sym(F.shape[0], 73, 0.5)
+    ap = o.solve_nonorthogonal(F + h * E, h1, S, beta, nocc, n=n)["alpha"][0]
+    am = o.solve_nonorthogonal(F - h * E, h1, S, beta, nocc, n=n)["alpha"][0]
+    assert abs((ap - am) / (2 * h) - np.sum(r["grad_alpha"][0] * E)) < 1e-6 * abs(ap)
