@@ -145,6 +145,29 @@ cdmpt_status cdmpt_create(const cdmpt_opts* opts, cdmpt_handle** out);
 /* Replace the options of an existing handle (stream, tolerances, precision). */
 cdmpt_status cdmpt_set_opts(cdmpt_handle* h, const cdmpt_opts* opts);
 
+/* Non-orthogonal basis (Sec. IV, Eq. Fermi_D): set the overlap matrix S (N x N,
+ * symmetric positive definite, row-major FP64, host or device per on_device).
+ * The handle computes the Loewdin factor Z = S^(-1/2) on the device by the
+ * coupled Newton-Schulz iteration (products only, FP64, stopped when
+ * ||Z Y - I||_F / sqrt(N) < 1e-12 plus one more step), so that Z^T S Z = I.
+ * From then on cdmpt_set_H takes the non-orthogonal F (as H0) and h1 (as H1):
+ * the solve works on F_perp = Z F Z and h1_perp = Z h1 Z, and every N x N
+ * output is mapped back with the same congruence: P0 -> D = Z P_perp Z
+ * (Tr[D S] = N_occ), P1 -> D1, P2 and P3 -> D2 and D3, and the gradients of
+ * cdmpt_vjp_P0 (whose G0 is then dL/dD), cdmpt_response2 and cdmpt_free_energy
+ * become derivatives with respect to F. alpha, mu and the mu^(k) are basis
+ * independent. S = NULL returns to the orthogonal mode. Either call discards
+ * the stored Hamiltonian, so cdmpt_set_H must follow. Batches are always
+ * orthogonal. Errors: ERR_ARG (N < 1, no positive Gershgorin bound),
+ * ERR_NO_CONVERGENCE (S not positive definite or too ill-conditioned for 200
+ * iterations), ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_set_overlap(cdmpt_handle* h, int N, const double* S, int on_device);
+
+/* Newton-Schulz iterations and final residual ||Z Y - I||_F / sqrt(N) of the
+ * last cdmpt_set_overlap (0 and 0.0 in the orthogonal mode). Either pointer may
+ * be NULL. Errors: ERR_ARG (h NULL). */
+cdmpt_status cdmpt_get_overlap_info(const cdmpt_handle* h, int* iterations, double* residual);
+
 /* Load the unperturbed Hamiltonian H0 (N x N) and D >= 0 perturbations H1
  * (D x N x N), Eq. (H_prt) with H^(1) = H1, in an orthogonal basis (Sec. II).
  * on_device = 0: host pointers; 1: device pointers. Both are copied into

@@ -91,7 +91,8 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_batch_set_H", "cdmpt_batch_solve", "cdmpt_batch_get_stats",
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
-           "cdmpt_response3", "cdmpt_free_energy"]
+           "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
+           "cdmpt_get_overlap_info"]
 
 
 def lib() -> ctypes.CDLL:
@@ -123,6 +124,8 @@ def lib() -> ctypes.CDLL:
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_response3": (I, [P, P, P, P, I]),
         "cdmpt_free_energy": (I, [P, P, P, I]),
+        "cdmpt_set_overlap": (I, [P, I, P, I]),
+        "cdmpt_get_overlap_info": (I, [P, P, P]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -316,6 +319,29 @@ class Handle:
         self.N = 0
         self.D = 0
         self._keep = None
+
+    def set_overlap(self, S):
+        """Non-orthogonal basis: S (N x N SPD; numpy or torch) or None for the orthogonal mode.
+        Afterwards set_H takes F and h1, and the outputs are D = Z P_perp Z etc."""
+        import torch
+        if S is None:
+            _check(lib().cdmpt_set_overlap(self.h, 0, None, 0), self.h)
+            return
+        if isinstance(S, torch.Tensor):
+            Sc = S.detach().to(torch.float64).contiguous()
+            _check(lib().cdmpt_set_overlap(self.h, Sc.shape[0], Sc.data_ptr(),
+                                           1 if Sc.is_cuda else 0), self.h)
+        else:
+            Sc = np.ascontiguousarray(S, dtype=np.float64)
+            _check(lib().cdmpt_set_overlap(self.h, Sc.shape[0], Sc.ctypes.data, 0), self.h)
+        self.N = self.D = 0
+
+    def overlap_info(self):
+        """(Newton-Schulz iterations, final residual) of the last set_overlap."""
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        _check(lib().cdmpt_get_overlap_info(self.h, ctypes.byref(it), ctypes.byref(res)), self.h)
+        return it.value, res.value
 
     def set_H(self, H0, H1=None):
         import torch

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cdmpt.h"
+#include "overlap.cuh"
 #include "solver.cuh"
 
 namespace cdmpt {
@@ -74,6 +75,12 @@ struct cdmpt_handle {
     std::string err;
     bool solved = false;
     std::vector<double> alpha;
+    // non-orthogonal basis (cdmpt_set_overlap): Loewdin factor Z = S^(-1/2), N x ld FP64,
+    // and 2 N x ld doubles of scratch for the congruences X -> Z X Z
+    double* Zov = nullptr;
+    double* ovtmp = nullptr;
+    int ovN = 0, ov_iters = 0;
+    double ov_resid = 0;
 };
 
 namespace {
@@ -86,6 +93,25 @@ cdmpt_status fail(cdmpt_handle* h, cdmpt_status s) {
 cdmpt_status fail_msg(cdmpt_handle* h, cdmpt_status s, const std::string& m) {
     set_error(m);
     return fail(h, s);
+}
+
+// Non-orthogonal mode: dst_b = Z src_b Z for `blocks` FP64 N x N matrices (leading
+// dimension N) held on the device, written to device or host memory.
+cdmpt_status ov_map(cdmpt_handle* h, const double* src, double* dst, int blocks,
+                    int dst_on_device) {
+    const int N = h->N, ld = h->ld;
+    const size_t nn = (size_t)N * N, blk = (size_t)N * ld;
+    cudaStream_t s = h->cx.stream;
+    for (int b = 0; b < blocks; ++b) {
+        double* out = dst_on_device ? dst + b * nn : h->ovtmp + blk;
+        CDMPT_TRY(congruence(h->Zov, ld, N, src + b * nn, N, out, N, h->ovtmp, s));
+        if (!dst_on_device) {
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(dst + b * nn, out, nn * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s));
+            CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    return CDMPT_OK;
 }
 
 bool valid_opts(const cdmpt_opts* o) {
@@ -179,6 +205,84 @@ cdmpt_status cdmpt_create(const cdmpt_opts* opts, cdmpt_handle** out) {
     return CDMPT_OK;
 }
 
+cdmpt_status cdmpt_set_overlap(cdmpt_handle* h, int N, const double* S, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    cudaStream_t s = h->cx.stream;
+    // the stored Hamiltonian belongs to the previous basis: cdmpt_set_H must follow
+    cudaFree(h->H0);
+    cudaFree(h->H1);
+    h->H0 = h->H1 = nullptr;
+    h->N = h->D = h->ld = 0;
+    h->solved = false;
+    cudaFree(h->Zov);
+    cudaFree(h->ovtmp);
+    h->Zov = h->ovtmp = nullptr;
+    h->ovN = 0;
+    if (!S) return CDMPT_OK;
+    if (N < 1) return fail_msg(h, CDMPT_ERR_ARG, "set_overlap: need N >= 1");
+    const int ld = (N + 31) / 32 * 32;
+    const size_t blk = (size_t)N * ld;
+    double* work = nullptr;   // four Newton-Schulz iterates and the padded copy of S
+    if (cudaMalloc((void**)&work, 5 * blk * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&h->Zov, blk * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&h->ovtmp, 2 * blk * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(work);
+        cudaFree(h->Zov);
+        cudaFree(h->ovtmp);
+        h->Zov = h->ovtmp = nullptr;
+        return fail_msg(h, CDMPT_ERR_OOM, "set_overlap: device allocation failed");
+    }
+    double* Sd = work + 4 * blk;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cdmpt_status st = CDMPT_OK;
+    double host[2] = {0, 0};
+    if (cudaMemsetAsync(Sd, 0, blk * sizeof(double), s) != cudaSuccess ||
+        cudaMemsetAsync(h->Zov, 0, blk * sizeof(double), s) != cudaSuccess ||
+        cudaMemcpy2DAsync(Sd, ld * sizeof(double), S, N * sizeof(double), N * sizeof(double), N,
+                          kind, s) != cudaSuccess ||
+        cudaMemsetAsync(h->dscal, 0, 8 * sizeof(double), s) != cudaSuccess) {
+        set_error("set_overlap: copy of S failed");
+        st = CDMPT_ERR_CUDA;
+    }
+    if (st == CDMPT_OK) st = gershgorin(Sd, N, ld, h->dscal, s);
+    if (st == CDMPT_OK &&
+        (cudaMemcpyAsync(host, h->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+        set_error("set_overlap: reading the bounds of S failed");
+        st = CDMPT_ERR_CUDA;
+    }
+    if (st == CDMPT_OK && !(host[1] > 0)) {
+        set_error("set_overlap: S has no positive Gershgorin bound");
+        st = CDMPT_ERR_ARG;
+    }
+    int it = 0;
+    double res = 0;
+    if (st == CDMPT_OK)
+        st = lowdin_factor(Sd, N, ld, host[1], h->Zov, work, h->dscal + 4, 200, 1e-12, &it, &res,
+                           s);
+    cudaStreamSynchronize(s);
+    cudaFree(work);
+    if (st != CDMPT_OK) {
+        cudaFree(h->Zov);
+        cudaFree(h->ovtmp);
+        h->Zov = h->ovtmp = nullptr;
+        return fail(h, st);
+    }
+    h->ovN = N;
+    h->ov_iters = it;
+    h->ov_resid = res;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_get_overlap_info(const cdmpt_handle* h, int* iterations, double* residual) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (iterations) *iterations = h->ovN ? h->ov_iters : 0;
+    if (residual) *residual = h->ovN ? h->ov_resid : 0.0;
+    return CDMPT_OK;
+}
+
 cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const double* H1,
                          int on_device) {
     if (!h) return CDMPT_ERR_ARG;
@@ -210,6 +314,14 @@ cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const 
         CDMPT_CUDA_TRY(cudaMemsetAsync(h->H1, 0, D * blk * sizeof(double), s));
         CDMPT_CUDA_TRY(cudaMemcpy2DAsync(h->H1, ld * sizeof(double), H1, N * sizeof(double),
                                          N * sizeof(double), (size_t)D * N, kind, s));
+    }
+    if (h->ovN) {   // non-orthogonal input: F_perp = Z F Z, h1_perp = Z h1 Z (Eq. Fermi_D)
+        if (N != h->ovN)
+            return fail_msg(h, CDMPT_ERR_ARG, "set_H: N differs from the overlap's size");
+        cdmpt_status st = congruence(h->Zov, ld, N, h->H0, ld, h->H0, ld, h->ovtmp, s);
+        for (int d = 0; d < D && st == CDMPT_OK; ++d)
+            st = congruence(h->Zov, ld, N, h->H1 + d * blk, ld, h->H1 + d * blk, ld, h->ovtmp, s);
+        if (st != CDMPT_OK) return fail(h, st);
     }
     CDMPT_CUDA_TRY(cudaMemsetAsync(h->dscal, 0, 8 * sizeof(double), s));
     cdmpt_status st = gershgorin(h->H0, N, ld, h->dscal, s);
@@ -243,17 +355,36 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
     h->alpha.assign(h->D, 0.0);
     const long long launches0 = launch_count();
     const auto t0 = std::chrono::steady_clock::now();
+    // non-orthogonal mode: the solver writes P_perp to device scratch, mapped to D = Z P Z below
+    double* P0u = P0;
+    double* P1u = (h->D > 0) ? P1 : nullptr;
+    int od = out_on_device;
+    double* scratch = nullptr;
+    const size_t nn = (size_t)h->N * h->N;
+    if (h->ovN && (P0u || P1u)) {
+        const size_t elems = (P0u ? nn : 0) + (P1u ? (size_t)h->D * nn : 0);
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&scratch, elems * sizeof(double), h->cx.stream));
+        P0u = P0 ? scratch : nullptr;
+        P1u = P1u ? scratch + (P0 ? nn : 0) : nullptr;
+        od = 1;
+    }
     cdmpt_status s;
     if (h->opts.precision == CDMPT_FP64) {
         if (!h->sd) h->sd = new (std::nothrow) Solver<double>();
         if (!h->sd) return fail_msg(h, CDMPT_ERR_OOM, "solver allocation");
         s = h->sd->solve(h->cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts,
-                         beta, nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
+                         beta, nocc, n, P0u, P1u, mu, mu1, od, h->alpha.data());
     } else {
         if (!h->sf) h->sf = new (std::nothrow) Solver<float>();
         if (!h->sf) return fail_msg(h, CDMPT_ERR_OOM, "solver allocation");
         s = h->sf->solve(h->cx, h->H0, h->H1, h->N, h->D, h->gmin, h->gmax, h->trH0, h->opts,
-                         beta, nocc, n, P0, P1, mu, mu1, out_on_device, h->alpha.data());
+                         beta, nocc, n, P0u, P1u, mu, mu1, od, h->alpha.data());
+    }
+    if (scratch) {
+        if (s == CDMPT_OK && P0u) s = ov_map(h, P0u, P0, 1, out_on_device);
+        if (s == CDMPT_OK && P1u) s = ov_map(h, P1u, P1, h->D, out_on_device);
+        cudaFreeAsync(scratch, h->cx.stream);
+        cudaStreamSynchronize(h->cx.stream);
     }
     h->st.kernel_launches = (int)(launch_count() - launches0);
     h->st.seconds =
@@ -304,25 +435,37 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
     if (!G0 || !gradH0) return fail_msg(h, CDMPT_ERR_ARG, "vjp_P0: NULL pointer");
     if (!h->solved) return fail_msg(h, CDMPT_ERR_ARG, "vjp_P0: no completed solve on this handle");
     cudaStream_t s = h->cx.stream;
-    const size_t bytes = (size_t)h->N * h->N * sizeof(double);
+    const size_t nn = (size_t)h->N * h->N;
+    const size_t bytes = nn * sizeof(double);
+    const bool ov = h->ovN != 0;
     const double* g = G0;
     double* out = gradH0;
     double* tmp = nullptr;
-    if (!on_device) {
-        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 2 * bytes, s));
-        CDMPT_CUDA_TRY(cudaMemcpyAsync(tmp, G0, bytes, cudaMemcpyHostToDevice, s));
-        g = tmp;
-        out = tmp + (size_t)h->N * h->N;
+    if (!on_device || ov) {   // [G0 on the device | Z G0 Z | gradient]
+        CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, 3 * bytes, s));
+        if (!on_device) {
+            CDMPT_CUDA_TRY(cudaMemcpyAsync(tmp, G0, bytes, cudaMemcpyHostToDevice, s));
+            g = tmp;
+        }
+        out = tmp + 2 * nn;
+    }
+    cdmpt_status st = CDMPT_OK;
+    if (ov) {   // D = Z P_perp Z, so dL/dP_perp = Z G0 Z
+        st = ov_map(h, g, tmp + nn, 1, 1);
+        g = tmp + nn;
     }
     cdmpt_stats keep = h->st;
     h->cx.st = &h->st;
-    cdmpt_status st;
-    if (h->opts.precision == CDMPT_FP64)
-        st = h->sd ? h->sd->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
-    else
-        st = h->sf ? h->sf->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
+    if (st == CDMPT_OK) {
+        if (h->opts.precision == CDMPT_FP64)
+            st = h->sd ? h->sd->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
+        else
+            st = h->sf ? h->sf->vjp_p0(h->cx, g, out) : CDMPT_ERR_ARG;
+    }
     h->st = keep;
-    if (st == CDMPT_OK && !on_device) {
+    if (st == CDMPT_OK && ov) {   // F_perp = Z F Z, so dL/dF = Z (dL/dF_perp) Z
+        st = ov_map(h, out, gradH0, 1, on_device);
+    } else if (st == CDMPT_OK && !on_device) {
         CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, out, bytes, cudaMemcpyDeviceToHost, s));
         CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
     }
@@ -339,7 +482,8 @@ cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, i
     const size_t bytes = (size_t)h->N * h->N * sizeof(double);
     double* g = gradH0;
     double* tmp = nullptr;
-    if (gradH0 && !on_device) {
+    const bool ov = h->ovN != 0;
+    if (gradH0 && (!on_device || ov)) {
         CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, bytes, s));
         g = tmp;
     }
@@ -352,7 +496,9 @@ cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, i
     else
         st = h->sf ? h->sf->free_energy(h->cx, &om, g) : CDMPT_ERR_ARG;
     h->st = keep;
-    if (st == CDMPT_OK && gradH0 && !on_device) {
+    if (st == CDMPT_OK && gradH0 && ov) {
+        st = ov_map(h, g, gradH0, 1, on_device);   // dOmega/dF = Z (dOmega/dF_perp) Z
+    } else if (st == CDMPT_OK && gradH0 && !on_device) {
         CDMPT_CUDA_TRY(cudaMemcpyAsync(gradH0, g, bytes, cudaMemcpyDeviceToHost, s));
         CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
     }
@@ -379,7 +525,8 @@ static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm,
     double* pm = Pm;
     double* g = gradH0;
     double* tmp = nullptr;
-    if (!on_device && (Pm || gradH0)) {
+    const bool ov = h->ovN != 0;
+    if ((!on_device || ov) && (Pm || gradH0)) {
         const size_t elems = (Pm ? (size_t)D * nn : 0) + (gradH0 ? nn : 0);
         CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, elems * sizeof(double), s));
         pm = Pm ? tmp : nullptr;
@@ -405,7 +552,10 @@ static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm,
             st = h->sf->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr);
     }
     h->st = keep;
-    if (st == CDMPT_OK && !on_device) {
+    if (st == CDMPT_OK && ov) {   // D^(m) = Z P^(m) Z; d alpha / dF = Z (d alpha / dF_perp) Z
+        if (Pm) st = ov_map(h, pm, Pm, D, on_device);
+        if (st == CDMPT_OK && gradH0) st = ov_map(h, g, gradH0, 1, on_device);
+    } else if (st == CDMPT_OK && !on_device) {
         if (Pm)
             CDMPT_CUDA_TRY(cudaMemcpyAsync(Pm, pm, (size_t)D * nn * sizeof(double),
                                            cudaMemcpyDeviceToHost, s));
@@ -459,6 +609,8 @@ void cdmpt_destroy(cdmpt_handle* h) {
     cudaFree(h->H0);
     cudaFree(h->H1);
     cudaFree(h->dscal);
+    cudaFree(h->Zov);
+    cudaFree(h->ovtmp);
     if (h->cx.pinned) cudaFreeHost(h->cx.pinned);
     delete h;
 }
