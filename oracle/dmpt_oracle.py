@@ -778,3 +778,80 @@ def solve_nonorthogonal(F, h1, S, beta, nocc, n: Optional[int] = None, kind: str
         out.update(mu2=r["mu2"], D2=np.stack([from_orthogonal(p, Linv) for p in r["P2"]]),
                    grad_alpha=np.stack([from_orthogonal(g, Linv) for g in r["grad_alpha"]]))
     return out
+
+
+# ----------------------------------------------------------------------------
+# self-consistent charge layer (Sec. IV with a synthetic G(D)): F = h + G(D),
+# G_ij = S_ij (V_i + V_j) / 2, V = gamma dq, dq_i = 2 (D S)_ii - q0_i
+# ----------------------------------------------------------------------------
+
+def scc_fock(hcore, S, gamma, dq):
+    V = gamma @ dq
+    return hcore + 0.5 * S * (V[:, None] + V[None, :])
+
+
+def scc_charges(D, S, q0):
+    return 2.0 * np.sum(D * S, axis=1) - q0
+
+
+def scc_solve(hcore, h1, S, gamma, q0, beta, nocc, n: Optional[int] = None, kind: str = "rec",
+              tol: float = 1e-13, maxit: int = 2000, mix: float = 0.3):
+    """Self-consistent canonical solve and its coupled-perturbed response.
+
+    SCF: plain fixed-point iteration on the charges with linear mixing, each step the
+    non-orthogonal solve of F(dq) (eigenvalues of the Cholesky-orthogonalised F). CPSCF:
+    the response charges satisfy the linear system (I - K) dq1 = b, where b are the charges
+    of R(h1) and column j of K the charges of R(G(e_j)), R the canonical first-order
+    response of the converged solve; it is solved directly (LAPACK), then
+    D1 = R(h1 + G(dq1)). Omega_SCF^(m) = (2/m) Tr[h1 D^(m-1)] (Eq. Resp_Omega).
+    The free energy Omega_SCF = 2 Tr[h D] + 1/2 dq^T gamma dq - 2 T_e S[D_perp] (Eq.
+    FreeE_tot for this model) is returned as omega.
+    """
+    h1 = np.asarray(h1, dtype=np.float64)
+    if h1.ndim == 2:
+        h1 = h1[None]
+    nn = n if kind == "rec" else None
+    N = hcore.shape[0]
+    Linv = cholesky_factor(S)
+    x = np.zeros(N)
+    for it in range(maxit):
+        F = scc_fock(hcore, S, gamma, x)
+        eps, V = np.linalg.eigh(to_orthogonal(F, Linv))
+        mu = find_mu(eps, nocc, beta, nn)
+        occ = occupation(eps, mu, beta, nn)
+        D = from_orthogonal((V * occ) @ V.T, Linv)
+        y = scc_charges(D, S, q0)
+        if np.max(np.abs(y - x)) < tol:
+            break
+        x = x + mix * (y - x)
+    else:
+        raise RuntimeError("oracle SCF did not converge")
+    Fdd = divided_differences(eps, mu, beta, nn)
+    fp = np.diag(Fdd)
+
+    def response(dF):
+        """Canonical first-order response of D to dF (non-orthogonal), with its mu1."""
+        h = V.T @ to_orthogonal(dF, Linv) @ V
+        m1 = float(np.dot(fp, np.diag(h)) / np.sum(fp))
+        P1 = V @ (Fdd * (h - m1 * np.eye(N))) @ V.T
+        return from_orthogonal(P1, Linv), m1
+
+    K = np.empty((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        K[:, j] = scc_charges(response(scc_fock(np.zeros((N, N)), S, gamma, e))[0], S,
+                              np.zeros(N))
+    D1 = np.empty_like(h1)
+    mu1 = np.zeros(h1.shape[0])
+    for d in range(h1.shape[0]):
+        b = scc_charges(response(h1[d])[0], S, np.zeros(N))
+        dq1 = np.linalg.solve(np.eye(N) - K, b)
+        D1[d], mu1[d] = response(scc_fock(h1[d], S, gamma, dq1))
+    ent = -np.sum(np.where(occ > 0, occ * np.log(np.where(occ > 0, occ, 1.0)), 0.0)
+                  + np.where(occ < 1, (1 - occ) * np.log1p(-np.where(occ < 1, occ, 0.0)), 0.0))
+    omega = 2.0 * np.sum(hcore * D) + 0.5 * x @ gamma @ x - 2.0 * ent / beta
+    return dict(D0=D, D1=D1, mu=float(mu), mu1=mu1, dq=y, iters=it + 1,
+                omega1=np.array([2.0 * np.sum(h1[d] * D) for d in range(h1.shape[0])]),
+                omega2=np.array([np.sum(h1[d] * D1[d]) for d in range(h1.shape[0])]),
+                omega=float(omega))

@@ -135,7 +135,9 @@ def nonorthogonal_cluster(Nb: int = 256, seed: int = 2001, beta: float = 20.0, n
     is positive semidefinite, so S is positive definite with eigenvalues >= 1 - s0. Fockian
     F_ii = eps_i ~ N(0, 0.3^2), F_ij = -4 S_ij. Dipoles in the Mulliken form
     (h1)_ij = S_ij (x_i + x_j) / 2 for x, y, z (centred coordinates). F is returned as H0,
-    the dipoles as H1 and S in meta["S"]; N_occ = Nb / 2.
+    the dipoles as H1 and S in meta["S"]; N_occ = Nb / 2. For the self-consistent charge
+    model, meta["gamma"] = U exp(-r^2 / (2 a^2)) (U = 0.5, a = 1; a positive semidefinite
+    Gaussian kernel) and meta["q0"] = 1 per site (neutral at half filling).
     """
     rng = np.random.default_rng(seed)
     side = Nb ** (1.0 / 3.0)
@@ -149,8 +151,10 @@ def nonorthogonal_cluster(Nb: int = 256, seed: int = 2001, beta: float = 20.0, n
     F[np.diag_indices(Nb)] = eps
     c = pos - pos.mean(axis=0)
     H1 = np.stack([S * 0.5 * (c[:, a][:, None] + c[:, a][None, :]) for a in range(3)])
+    gamma = 0.5 * np.exp(-r2 / 2.0)
     return Problem(f"nonorth_cluster_{Nb}", F, H1, nocc=float(Nb // 2), beta=beta, n=n,
-                   meta={"seed": seed, "S": S})
+                   meta={"seed": seed, "S": S, "gamma": 0.5 * (gamma + gamma.T),
+                         "q0": np.ones(Nb)})
 
 
 def cluster_sizes(B: int = 96, seed: int = 1005, nmin: int = 128, nmax: int = 1536) -> List[int]:

@@ -730,3 +730,47 @@ def test_nonorthogonal_D1_and_alpha_gradient_equal_finite_differences():
     ap = o.solve_nonorthogonal(F + h * E, h1, S, beta, nocc, n=n)["alpha"][0]
     am = o.solve_nonorthogonal(F - h * E, h1, S, beta, nocc, n=n)["alpha"][0]
     assert abs((ap - am) / (2 * h) - np.sum(r["grad_alpha"][0] * E)) < 1e-6 * abs(ap)
+
+
+# --------------------------------------------------------------------------
+# self-consistent charge layer (Sec. IV, Eqs. FirstOrderPRT, Resp_Omega)
+# --------------------------------------------------------------------------
+
+def _scc_case(N=24, seed=81):
+    p = syn.nonorthogonal_cluster(N, seed=seed, beta=4.0, n=10)
+    return p.H0, p.H1[0], p.meta["S"], p.meta["gamma"], p.meta["q0"], p.beta, p.nocc, p.n
+
+
+def test_scc_without_coupling_equals_non_self_consistent_solve():
+    hc, h1, S, gamma, q0, beta, nocc, n = _scc_case()
+    r = o.scc_solve(hc, h1, S, 0.0 * gamma, q0, beta, nocc, n=n)
+    q = o.solve_nonorthogonal(hc, h1, S, beta, nocc, n=n)
+    assert o.rel_frobenius(r["D0"], q["D0"]) < 1e-12
+    assert o.rel_frobenius(r["D1"][0], q["D1"][0]) < 1e-10
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_scc_D1_equals_finite_difference_of_self_consistent_D(kind, n):
+    """D1 = dD/dlambda of the self-consistent solution of h + lambda h1."""
+    hc, h1, S, gamma, q0, beta, nocc, _ = _scc_case()
+    h = 1e-4
+    r = o.scc_solve(hc, h1, S, gamma, q0, beta, nocc, n=n, kind=kind)
+    D = {k: o.scc_solve(hc + k * h * h1, h1, S, gamma, q0, beta, nocc, n=n, kind=kind)["D0"]
+         for k in (-2, -1, 1, 2)}
+    fd = (D[-2] - 8 * D[-1] + 8 * D[1] - D[2]) / (12 * h)
+    assert o.rel_frobenius(r["D1"][0], fd) < 1e-7
+
+
+def test_scc_free_energy_response_rule():
+    """Eq. Resp_Omega at self-consistency (Fermi-Dirac, where the functional is variational):
+    Omega_SCF^(1) = 2 Tr[h1 D0] = dOmega_SCF/dlambda and Omega_SCF^(2) = Tr[h1 D1] =
+    (1/2) d^2 Omega_SCF / dlambda^2, by five-point differences of the free energy."""
+    hc, h1, S, gamma, q0, beta, nocc, _ = _scc_case()
+    h = 1e-3
+    r = o.scc_solve(hc, h1, S, gamma, q0, beta, nocc, kind="fd")
+    w = {k: o.scc_solve(hc + k * h * h1, h1, S, gamma, q0, beta, nocc, kind="fd")["omega"]
+         for k in (-2, -1, 0, 1, 2)}
+    d1 = (w[-2] - 8 * w[-1] + 8 * w[1] - w[2]) / (12 * h)
+    d2 = (-w[-2] + 16 * w[-1] - 30 * w[0] + 16 * w[1] - w[2]) / (12 * h * h)
+    assert abs(d1 - r["omega1"][0]) < 1e-8 * max(1.0, abs(d1))
+    assert abs(0.5 * d2 - r["omega2"][0]) < 1e-5 * abs(r["omega2"][0])
