@@ -178,6 +178,44 @@ cdmpt_status cdmpt_get_overlap_info(const cdmpt_handle* h, int* iterations, doub
 cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const double* H1,
                          int on_device);
 
+/* A self-consistent charge (SCC) tight-binding model: a synthetic two-electron part
+ * G(D) for the self-consistent layer of Sec. IV. With Mulliken charge fluctuations
+ * dq_i = 2 (D S)_ii - q0_i (restricted: two electrons per orbital) and the potential
+ * V = gamma dq, G(D)_ij = (S_ij / 2)(V_i + V_j) (S = I in the orthogonal mode).
+ * G is the derivative of E(D) = 2 Tr[h D] + 1/2 dq^T gamma dq with respect to 2 D,
+ * so Omega_SCF = E(D) - 2 T_e S[D_perp] is the variational free energy of Eq.
+ * FreeE_tot for this model. */
+typedef struct {
+    const double* gamma;  /* N x N symmetric kernel of the charge fluctuations (FP64) */
+    const double* q0;     /* N reference populations, or NULL for zero */
+    double tol;           /* stop each loop when max_i |dq_out - dq_in| < tol;
+                             <= 0: 1e-10 (FP64) or 1e-6 (otherwise) */
+    int maxit;            /* iteration cap of each loop; <= 0: 200 */
+    int history;          /* Anderson mixing depth; <= 0: 6 */
+    double mix;           /* mixing weight of the residual; <= 0: 0.3 */
+} cdmpt_scc_model;
+
+/* Self-consistent canonical solve and its coupled-perturbed response (Sec. IV,
+ * Eqs. FirstOrderPRT, Fermi_D, Resp_Omega) for the model above, in the basis set by
+ * cdmpt_set_overlap (orthogonal if none).
+ * SCF: the charges dq are iterated to a fixed point, each step a canonical solve
+ * of F = hcore + G(D) (Tr[D S] = nocc) with Anderson mixing.
+ * CPSCF: per direction d, D1 = R(h1_d + G(D1)) with R the canonical first-order
+ * response on the converged trajectory; G is linear in D, so this is a linear
+ * fixed point in dq1, iterated the same way.
+ * Outputs (any may be NULL): D0 (N x N), D1 (D x N x N) in the caller's basis, host or device per
+ * on_device; mu (1 double), mu1, omega1, omega2 (D doubles each, host) with
+ * Omega_SCF^(m) = (2/m) Tr[h1 D^(m-1)]: omega1 = 2 Tr[h1 D0], omega2 = Tr[h1 D1].
+ * iters (2 ints, host): SCF iterations and CPSCF iterations summed over directions.
+ * Inputs hcore, h1 (D x N x N), model->gamma and model->q0 are host or device per
+ * on_device. The handle's stored Hamiltonian is the last F afterwards.
+ * Errors: ERR_ARG, ERR_NO_CONVERGENCE, ERR_CG_MAXITER, ERR_OOM, ERR_CUDA, and those of
+ * cdmpt_solve. */
+cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* model, int N,
+                             const double* hcore, int D, const double* h1, double beta,
+                             double nocc, int n, double* D0, double* D1, double* mu, double* mu1,
+                             double* omega1, double* omega2, int* iters, int on_device);
+
 /* Canonical solve, Algorithm 1 to first order.
  * beta > 0: inverse temperature; nocc in (0, N): occupation; n >= 1:
  * recursion steps (M in the paper).

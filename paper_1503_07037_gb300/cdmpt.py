@@ -50,6 +50,17 @@ class Opts(ctypes.Structure):
     ]
 
 
+class SccModel(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_void_p),
+        ("q0", ctypes.c_void_p),
+        ("tol", ctypes.c_double),
+        ("maxit", ctypes.c_int),
+        ("history", ctypes.c_int),
+        ("mix", ctypes.c_double),
+    ]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("N", ctypes.c_int), ("D", ctypes.c_int), ("n", ctypes.c_int),
@@ -92,7 +103,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
-           "cdmpt_get_overlap_info"]
+           "cdmpt_get_overlap_info", "cdmpt_scc_solve"]
 
 
 def lib() -> ctypes.CDLL:
@@ -126,6 +137,8 @@ def lib() -> ctypes.CDLL:
         "cdmpt_free_energy": (I, [P, P, P, I]),
         "cdmpt_set_overlap": (I, [P, I, P, I]),
         "cdmpt_get_overlap_info": (I, [P, P, P]),
+        "cdmpt_scc_solve": (I, [P, ctypes.POINTER(SccModel), I, P, I, P, D, D, I, P, P, P, P, P, P,
+                                P, I]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -439,6 +452,34 @@ class Handle:
         om = ctypes.c_double(0.0)
         _check(lib().cdmpt_free_energy(self.h, ctypes.addressof(om), _ptr(G), on_dev), self.h)
         return {"omega": om.value, "grad": G}
+
+    def scc_solve(self, hcore, h1, gamma, beta, nocc, n, q0=None, tol=0.0, maxit=0, history=0,
+                  mix=0.0):
+        """Self-consistent charge solve and coupled-perturbed response (cdmpt_scc_solve) in
+        the basis of the last set_overlap. Host (numpy) inputs and outputs: dict(D0, D1, mu,
+        mu1, omega1, omega2, iters) with omega1 = 2 Tr[h1 D0], omega2 = Tr[h1 D1]."""
+        hc = np.ascontiguousarray(hcore, dtype=np.float64)
+        N = hc.shape[0]
+        H1 = np.ascontiguousarray(np.zeros((0, N, N)) if h1 is None else h1, dtype=np.float64)
+        if H1.ndim == 2:
+            H1 = H1[None]
+        D = H1.shape[0]
+        g = np.ascontiguousarray(gamma, dtype=np.float64)
+        q = None if q0 is None else np.ascontiguousarray(q0, dtype=np.float64)
+        m = SccModel(g.ctypes.data, None if q is None else q.ctypes.data, tol, maxit, history, mix)
+        D0 = np.empty((N, N))
+        D1 = np.empty((max(D, 1), N, N))
+        mu = ctypes.c_double(0.0)
+        mu1, om1, om2 = np.zeros(max(D, 1)), np.zeros(max(D, 1)), np.zeros(max(D, 1))
+        it = np.zeros(2, dtype=np.int32)
+        _check(lib().cdmpt_scc_solve(self.h, ctypes.byref(m), N, hc.ctypes.data, D,
+                                     H1.ctypes.data if D else None, beta, nocc, n,
+                                     D0.ctypes.data, D1.ctypes.data if D else None,
+                                     ctypes.addressof(mu), mu1.ctypes.data, om1.ctypes.data,
+                                     om2.ctypes.data, it.ctypes.data, 0), self.h)
+        self.N, self.D = N, 0
+        return {"D0": D0, "D1": D1[:D], "mu": mu.value, "mu1": mu1[:D].copy(),
+                "omega1": om1[:D].copy(), "omega2": om2[:D].copy(), "iters": tuple(int(v) for v in it)}
 
     def stats(self):
         return get_stats(self.h)

@@ -11,6 +11,7 @@
 
 #include "cdmpt.h"
 #include "overlap.cuh"
+#include "scc.cuh"
 #include "solver.cuh"
 
 namespace cdmpt {
@@ -78,6 +79,7 @@ struct cdmpt_handle {
     // non-orthogonal basis (cdmpt_set_overlap): Loewdin factor Z = S^(-1/2), N x ld FP64,
     // and 2 N x ld doubles of scratch for the congruences X -> Z X Z
     double* Zov = nullptr;
+    double* Sov = nullptr;     // S itself (N x ld), for the Mulliken charges of the SCC layer
     double* ovtmp = nullptr;
     int ovN = 0, ov_iters = 0;
     double ov_resid = 0;
@@ -215,25 +217,28 @@ cdmpt_status cdmpt_set_overlap(cdmpt_handle* h, int N, const double* S, int on_d
     h->N = h->D = h->ld = 0;
     h->solved = false;
     cudaFree(h->Zov);
+    cudaFree(h->Sov);
     cudaFree(h->ovtmp);
-    h->Zov = h->ovtmp = nullptr;
+    h->Zov = h->Sov = h->ovtmp = nullptr;
     h->ovN = 0;
     if (!S) return CDMPT_OK;
     if (N < 1) return fail_msg(h, CDMPT_ERR_ARG, "set_overlap: need N >= 1");
     const int ld = (N + 31) / 32 * 32;
     const size_t blk = (size_t)N * ld;
-    double* work = nullptr;   // four Newton-Schulz iterates and the padded copy of S
-    if (cudaMalloc((void**)&work, 5 * blk * sizeof(double)) != cudaSuccess ||
+    double* work = nullptr;   // four Newton-Schulz iterates
+    if (cudaMalloc((void**)&work, 4 * blk * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&h->Zov, blk * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&h->Sov, blk * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&h->ovtmp, 2 * blk * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(work);
         cudaFree(h->Zov);
+        cudaFree(h->Sov);
         cudaFree(h->ovtmp);
-        h->Zov = h->ovtmp = nullptr;
+        h->Zov = h->Sov = h->ovtmp = nullptr;
         return fail_msg(h, CDMPT_ERR_OOM, "set_overlap: device allocation failed");
     }
-    double* Sd = work + 4 * blk;
+    double* Sd = h->Sov;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cdmpt_status st = CDMPT_OK;
     double host[2] = {0, 0};
@@ -266,8 +271,9 @@ cdmpt_status cdmpt_set_overlap(cdmpt_handle* h, int N, const double* S, int on_d
     cudaFree(work);
     if (st != CDMPT_OK) {
         cudaFree(h->Zov);
+        cudaFree(h->Sov);
         cudaFree(h->ovtmp);
-        h->Zov = h->ovtmp = nullptr;
+        h->Zov = h->Sov = h->ovtmp = nullptr;
         return fail(h, st);
     }
     h->ovN = N;
@@ -508,6 +514,182 @@ cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, i
     return CDMPT_OK;
 }
 
+// Self-consistent charge layer (Sec. IV with a synthetic G(D)); see cdmpt_scc_solve in cdmpt.h.
+cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, const double* hcore,
+                             int D, const double* h1, double beta, double nocc, int n, double* D0,
+                             double* D1, double* mu, double* mu1, double* omega1, double* omega2,
+                             int* iters, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (!m || !m->gamma || !hcore || N < 1 || D < 0 || D > 16 || (D > 0 && !h1))
+        return fail_msg(h, CDMPT_ERR_ARG,
+                        "scc_solve: need the model (gamma), hcore, N >= 1, 0 <= D <= 16 and h1");
+    if (h->ovN && h->ovN != N)
+        return fail_msg(h, CDMPT_ERR_ARG, "scc_solve: N differs from the overlap's size");
+    if (h->opts.grand_canonical)
+        return fail_msg(h, CDMPT_ERR_ARG, "scc_solve: the self-consistent layer is canonical");
+    cudaStream_t s = h->cx.stream;
+    const int ld = (N + 31) / 32 * 32;
+    const size_t nn = (size_t)N * N, blk = (size_t)N * ld;
+    const double tol = m->tol > 0 ? m->tol : (h->opts.precision == CDMPT_FP64 ? 1e-10 : 1e-6);
+    const int maxit = m->maxit > 0 ? m->maxit : 200;
+    const int depth = m->history > 0 ? m->history : 6;
+    const double mix = m->mix > 0 ? m->mix : 0.3;
+    // device work: hcore, gamma, F, D, D1 (orthogonal), D1 (caller's basis), h1, F1 (padded),
+    // q0, dq, V
+    double* w = nullptr;
+    const size_t elems = 6 * nn + (size_t)D * nn + blk + 3 * (size_t)N;
+    if (cudaMalloc((void**)&w, elems * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(h, CDMPT_ERR_OOM, "scc_solve: device allocation failed");
+    }
+    double *hc = w, *gam = hc + nn, *F = gam + nn, *Dd = F + nn, *D1p = Dd + nn, *D1d = D1p + nn;
+    double *h1d = D1d + nn, *F1 = h1d + (size_t)D * nn, *q0d = F1 + blk, *dq = q0d + N,
+           *V = dq + N;
+    const double* Sg = h->ovN ? h->Sov : nullptr;
+    const cdmpt_opts saved = h->opts;
+    cdmpt_status st = CDMPT_OK;
+    int scf_it = 0, cp_it = 0;
+    double mu_last = 0.0;
+    auto cuda_ok = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && st == CDMPT_OK) {
+            set_error(std::string("scc_solve: ") + what + ": " + cudaGetErrorString(e));
+            st = CDMPT_ERR_CUDA;
+        }
+    };
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cuda_ok(cudaMemcpyAsync(hc, hcore, nn * sizeof(double), kin, s), "copy hcore");
+    cuda_ok(cudaMemcpyAsync(gam, m->gamma, nn * sizeof(double), kin, s), "copy gamma");
+    if (D > 0) cuda_ok(cudaMemcpyAsync(h1d, h1, D * nn * sizeof(double), kin, s), "copy h1");
+    cuda_ok(cudaMemsetAsync(q0d, 0, N * sizeof(double), s), "zero q0");
+    if (m->q0) cuda_ok(cudaMemcpyAsync(q0d, m->q0, N * sizeof(double), kin, s), "copy q0");
+    cuda_ok(cudaMemsetAsync(F1, 0, blk * sizeof(double), s), "zero F1");
+    std::vector<double> x(N, 0.0), y(N), r(N);
+    // ---- SCF on the charges: F = h + G(D(F)) (a fixed point in dq)
+    bool conv = false;
+    {
+        Anderson mixer(N, depth, mix);
+        for (; st == CDMPT_OK && scf_it < maxit; ++scf_it) {
+            cuda_ok(cudaMemcpyAsync(dq, x.data(), N * sizeof(double), cudaMemcpyHostToDevice, s),
+                    "charges to device");
+            if (st == CDMPT_OK) st = scc_gemv(gam, N, dq, N, V, s);
+            if (st == CDMPT_OK) st = scc_fock(hc, N, Sg, ld, V, N, F, N, s);
+            if (st == CDMPT_OK) st = cdmpt_set_H(h, N, F, 0, nullptr, 1);
+            if (st == CDMPT_OK && scf_it > 0) {   // warm start mu from the previous iteration
+                h->opts.have_mu_guess = 1;
+                h->opts.mu_guess = mu_last;
+            }
+            if (st == CDMPT_OK) st = cdmpt_solve(h, beta, nocc, n, Dd, nullptr, &mu_last, nullptr, 1);
+            if (st == CDMPT_OK) st = scc_charges(Dd, N, Sg, ld, q0d, N, dq, s);
+            cuda_ok(cudaMemcpyAsync(y.data(), dq, N * sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "charges to host");
+            cuda_ok(cudaStreamSynchronize(s), "synchronize");
+            if (st != CDMPT_OK) break;
+            double res = 0.0;
+            for (int i = 0; i < N; ++i) {
+                r[i] = y[i] - x[i];
+                res = std::max(res, std::fabs(r[i]));
+            }
+            if (res < tol) {
+                conv = true;
+                break;
+            }
+            mixer.next(x, r);
+        }
+    }
+    h->opts = saved;
+    if (st == CDMPT_OK && !conv) {
+        set_error("scc_solve: the charges did not converge in " + std::to_string(maxit) +
+                  " iterations");
+        st = CDMPT_ERR_NO_CONVERGENCE;
+    }
+    // ---- coupled-perturbed SCF per direction: D1 = R(h1 + G(D1)) (linear fixed point in dq1)
+    std::vector<double> om1(D, 0.0), om2(D, 0.0), m1(D, 0.0);
+    Solver<float>* sf = h->sf;
+    Solver<double>* sd = h->sd;
+    for (int d = 0; d < D && st == CDMPT_OK; ++d) {
+        std::vector<double> x1(N, 0.0), y1(N);
+        Anderson mixer(N, depth, mix);
+        bool c1 = false;
+        for (int it = 0; st == CDMPT_OK && it < maxit; ++it, ++cp_it) {
+            cuda_ok(cudaMemcpyAsync(dq, x1.data(), N * sizeof(double), cudaMemcpyHostToDevice, s),
+                    "response charges to device");
+            if (st == CDMPT_OK) st = scc_gemv(gam, N, dq, N, V, s);
+            if (st == CDMPT_OK) st = scc_fock(h1d + d * nn, N, Sg, ld, V, N, F1, ld, s);
+            if (st == CDMPT_OK && h->ovN)
+                st = congruence(h->Zov, ld, N, F1, ld, F1, ld, h->ovtmp, s);
+            double mud = 0.0;
+            cdmpt_stats keep = h->st;
+            h->cx.st = &h->st;
+            if (st == CDMPT_OK)
+                st = h->opts.precision == CDMPT_FP64 ? sd->response1(h->cx, F1, 1, D1p, &mud, nullptr)
+                                                     : sf->response1(h->cx, F1, 1, D1p, &mud, nullptr);
+            h->st = keep;
+            const double* D1c = D1p;
+            if (st == CDMPT_OK && h->ovN) {
+                st = ov_map(h, D1p, D1d, 1, 1);
+                D1c = D1d;
+            }
+            if (st == CDMPT_OK) st = scc_charges(D1c, N, Sg, ld, nullptr, N, dq, s);
+            cuda_ok(cudaMemcpyAsync(y1.data(), dq, N * sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "response charges to host");
+            cuda_ok(cudaStreamSynchronize(s), "synchronize");
+            if (st != CDMPT_OK) break;
+            double res = 0.0;
+            for (int i = 0; i < N; ++i) {
+                r[i] = y1[i] - x1[i];
+                res = std::max(res, std::fabs(r[i]));
+            }
+            m1[d] = mud;
+            if (res < tol) {
+                c1 = true;
+                if (D1c != D1d) cuda_ok(cudaMemcpyAsync(D1d, D1c, nn * sizeof(double),
+                                                        cudaMemcpyDeviceToDevice, s), "keep D1");
+                break;
+            }
+            mixer.next(x1, r);
+        }
+        if (st == CDMPT_OK && !c1) {
+            set_error("scc_solve: the response charges of direction " + std::to_string(d) +
+                      " did not converge");
+            st = CDMPT_ERR_NO_CONVERGENCE;
+        }
+        // Omega_SCF^(m) = (2/m) Tr[h1 D^(m-1)] (Eq. Resp_Omega): m = 1 with D0, m = 2 with D1
+        if (st == CDMPT_OK) {
+            cuda_ok(cudaMemsetAsync(h->dscal, 0, 2 * sizeof(double), s), "zero dots");
+            if (st == CDMPT_OK) st = scc_dot(h1d + d * nn, Dd, nn, h->dscal, s);
+            if (st == CDMPT_OK) st = scc_dot(h1d + d * nn, D1d, nn, h->dscal + 1, s);
+            double dots[2] = {0, 0};
+            cuda_ok(cudaMemcpyAsync(dots, h->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "dots to host");
+            cuda_ok(cudaStreamSynchronize(s), "synchronize");
+            om1[d] = 2.0 * dots[0];
+            om2[d] = dots[1];
+        }
+        if (st == CDMPT_OK && D1) {
+            const cudaMemcpyKind ko = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            cuda_ok(cudaMemcpyAsync(D1 + d * nn, D1d, nn * sizeof(double), ko, s), "copy D1");
+        }
+    }
+    if (st == CDMPT_OK && D0) {
+        const cudaMemcpyKind ko = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        cuda_ok(cudaMemcpyAsync(D0, Dd, nn * sizeof(double), ko, s), "copy D0");
+    }
+    cuda_ok(cudaStreamSynchronize(s), "synchronize");
+    cudaFree(w);
+    if (iters) {
+        iters[0] = scf_it + 1;
+        iters[1] = cp_it;
+    }
+    if (st != CDMPT_OK) return fail(h, st);
+    if (mu) *mu = mu_last;
+    for (int d = 0; d < D; ++d) {
+        if (mu1) mu1[d] = m1[d];
+        if (omega1) omega1[d] = om1[d];
+        if (omega2) omega2[d] = om2[d];
+    }
+    return CDMPT_OK;
+}
+
 // Orders 2 and 3 share the marshalling: P^(m) (and the gradient) through a
 // device scratch when the caller's buffers are on the host.
 static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm, double* mu,
@@ -610,6 +792,7 @@ void cdmpt_destroy(cdmpt_handle* h) {
     cudaFree(h->H1);
     cudaFree(h->dscal);
     cudaFree(h->Zov);
+    cudaFree(h->Sov);
     cudaFree(h->ovtmp);
     if (h->cx.pinned) cudaFreeHost(h->cx.pinned);
     delete h;

@@ -165,9 +165,6 @@ cdmpt_status cg_scalar_step(double* sc, cudaStream_t s);
 cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s);
 cdmpt_status gershgorin(const double* H, int N, int ld, double* out2, cudaStream_t s);
 cdmpt_status gershgorin_noalloc(const double* H, int N, int ld, double* out2, cudaStream_t s);
-cdmpt_status frob_dot_f64_full(const double* A, const double* B, size_t count, double* out,
-                               cudaStream_t s);
-
 // Count of kernel launches issued by this thread (for statistics).
 void count_launch(int k = 1);
 long long launch_count();

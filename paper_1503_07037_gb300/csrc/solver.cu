@@ -715,7 +715,8 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const doub
     return CDMPT_OK;
 }
 
-// Canonical response of order m = 2 or 3 per direction. P^(m) is linear in
+// Canonical response of order m = 1, 2 or 3 per direction (m = 1: a first-order pass for
+// perturbations other than the solve's, on the stored trajectory). P^(m) is linear in
 // mu^(m) with slope Q = dP0/dmu (Z^(m)_0 = s2 mu^(m) I enters through the same
 // tangent map as a uniform shift of Z_0), so one sweep with mu^(m) = 0 gives
 // mu^(m) = -Tr P^(m)|_0 / Tr Q and P^(m) = Z^(m)_n / 2 + mu^(m) Q. Order 3 needs
@@ -724,7 +725,7 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const doub
 template <typename T>
 cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, const double* w,
                                double* Pm, double* mu_out, double* omega, double* grad) {
-    if (!traj_valid_ || D < 1 || (int)last_mu1_.size() < D) {
+    if (!traj_valid_ || D < 1 || (m > 1 && (int)last_mu1_.size() < D)) {
         set_error("higher-order response: no completed solve with perturbations on this handle");
         return CDMPT_ERR_ARG;
     }
@@ -744,8 +745,8 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
     if (grad) CDMPT_CUDA_TRY(cudaMemsetAsync(G_.x, 0, blk_ * sizeof(T), cx.stream));
     for (int d = 0; d < D; ++d) {
         const double* H1d = H1 + (size_t)d * blk_;
-        double mus[2] = {last_mu1_[d], 0.0};
-        for (int q = 2; q <= m; ++q) {
+        double mus[2] = {m > 1 ? last_mu1_[d] : 0.0, 0.0};
+        for (int q = std::min(m, 2); q <= m; ++q) {
             CDMPT_TRY(orders(cx, H1d, q, mus));
             Buf<T>& Zq = zo_[q - 1][cur_[q - 1]];
             CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
@@ -789,6 +790,12 @@ template <typename T>
 cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
                                   double* P2, double* mu2_out, double* omega3, double* grad) {
     return higher(cx, H1, D, 2, w, P2, mu2_out, omega3, grad);
+}
+
+template <typename T>
+cdmpt_status Solver<T>::response1(Context& cx, const double* H1, int D, double* P1,
+                                  double* mu1_out, double* omega2) {
+    return higher(cx, H1, D, 1, nullptr, P1, mu1_out, omega2, nullptr);
 }
 
 template <typename T>

@@ -72,6 +72,12 @@ public:
     cdmpt_status response2(Context& cx, const double* H1, int D, const double* w, double* P2,
                            double* mu2, double* omega3, double* grad);
 
+    // First-order canonical response of the last solve to other perturbations H1 (device,
+    // D x N x ld FP64), on the stored trajectory: P1 (D x N x N FP64 device, leading
+    // dimension N, or null), mu1 and Omega^(2) = 1/2 Tr[H1 P1] (host arrays of D, or null).
+    cdmpt_status response1(Context& cx, const double* H1, int D, double* P1, double* mu1,
+                           double* omega2);
+
     // Third-order canonical response of the last solve (Algorithm 1, the order-3
     // line, H^(2) = H^(3) = 0): P3_d = 1/6 d^3 P / d lambda_d^3 with mu3_d from
     // Tr P3_d = 0 (mu2_d from an order-2 pass first), and Omega^(4)_d =
