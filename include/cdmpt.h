@@ -100,6 +100,15 @@ typedef struct {
                            the response, the adjoint or a higher order needs them; -1 selects
                            s = ceil(sqrt(n)), which keeps about 3 sqrt(n) matrices instead of
                            2n. Mixed precisions return ERR_ARG for a nonzero value. */
+    int fd_exact;       /* 1: start the recursion from Z_0 = tanh(-beta (H0 - mu I) / 2^(n+1))
+                           (X_0 = (I + Z_0) / 2) instead of the linear X_0 of Eq. Rec_F_2. The
+                           n steps then give P0 = [exp(beta (H0 - mu I)) + I]^-1 exactly (the
+                           Fermi-Dirac function, Eq. Rec_F_1) rather than the n-step
+                           approximation, and dP0/dmu = beta P0 (I - P0) holds exactly. tanh
+                           is its odd Taylor series (converges since |Y| < 1 < pi/2), a few
+                           products on the Gershgorin interval. Solve, first-order response,
+                           mu1 and alpha only: the adjoint, cdmpt_response2/3,
+                           cdmpt_free_energy and cdmpt_scc_solve return ERR_ARG. */
 } cdmpt_opts;
 
 typedef struct {

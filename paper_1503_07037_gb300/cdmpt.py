@@ -47,6 +47,7 @@ class Opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("grand_canonical", ctypes.c_int),
         ("ckpt_stride", ctypes.c_int),
+        ("fd_exact", ctypes.c_int),
     ]
 
 
@@ -309,7 +310,7 @@ class Handle:
 
     def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
                  refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
-                 stream=None, grand_canonical=False, ckpt_stride=0):
+                 stream=None, grand_canonical=False, ckpt_stride=0, fd_exact=False):
         """ckpt_stride: 0 stores the whole recursion trajectory; s > 0 keeps every s-th
         step and recomputes the rest segment by segment; "sqrt" (or -1) picks
         s = ceil(sqrt(n)). FP64 and FP32 precisions only."""
@@ -327,6 +328,7 @@ class Handle:
         o.stream = _stream_ptr(stream)
         o.grand_canonical = 1 if grand_canonical else 0
         o.ckpt_stride = -1 if ckpt_stride == "sqrt" else int(ckpt_stride)
+        o.fd_exact = 1 if fd_exact else 0
         self.opts = o
         self.h = create(o)
         self.N = 0

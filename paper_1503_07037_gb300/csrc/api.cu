@@ -154,6 +154,7 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
     o->stream = nullptr;
     o->grand_canonical = 0;
     o->ckpt_stride = 0;
+    o->fd_exact = 0;
     return CDMPT_OK;
 }
 

@@ -314,6 +314,155 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
     return CDMPT_OK;
 }
 
+// Fermi-Dirac-exact start (opts.fd_exact). With Y = -s2 (H0 - mu I), the n-step recursion
+// maps Z_0 to Z_n = tanh(2^n atanh Z_0) (Appendix A), so Z_0 = tanh(Y) gives
+// Z_n = tanh(-beta (H0 - mu I) / 2), i.e. P0 = the Fermi-Dirac function itself instead of the
+// n-step function of the linear X_0 of Eq. Rec_F_2. tanh(Y) = Y h(U), U = Y^2,
+// h(u) = sum_k a_k u^k, with the Taylor coefficients of tanh from tanh' = 1 - tanh^2:
+// a_0 = 1, (2k + 1) a_k = -sum_{i+j=k-1} a_i a_j. The series converges for |y| < pi/2 and
+// |y| <= rho < 1 here; it is cut where |a_k| rho^(2k) falls below eps.
+static int tanh_terms(double rho, double eps, std::vector<double>* a) {
+    a->assign(1, 1.0);
+    for (int k = 1; k < 64; ++k) {
+        double s = 0.0;
+        for (int i = 0; i <= k - 1; ++i) s += (*a)[i] * (*a)[k - 1 - i];
+        a->push_back(-s / (2 * k + 1));
+        if (std::fabs(a->back()) * std::pow(rho, 2 * k) < eps) break;
+    }
+    return (int)a->size() - 1;   // highest power of U
+}
+
+template <typename T>
+double Solver<T>::fdx_eps() const {
+    return sizeof(T) == 8 ? 1e-17 : 1e-12;
+}
+
+template <typename T>
+cdmpt_status Solver<T>::init_z0(Context& cx, const double* H0, double mu, double s2, double rho,
+                                int engine) {
+    if (!fdx_) {
+        return Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo);
+    }
+    std::vector<double> a;
+    const int K = tanh_terms(rho, fdx_eps(), &a);
+    // scratch outside the trajectory (the mixed refinement rebuilds Z_0 while the stored
+    // Z_1 .. Z_n are still needed)
+    CDMPT_TRY(reserve_orders());
+    Buf<T>& Y = zo_[0][0];
+    Buf<T>& U = zo_[0][1];
+    CDMPT_TRY(Ew<T>::init_z(Y.x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Y.hi, Y.lo));
+    {
+        Epilogue<T> ep;
+        ep.Dhi = U.hi;
+        ep.Dlo = U.lo;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N_, N_, N_, Y.op(), Y.op(), U.x, ep, nullptr, engine));
+    }
+    Buf<T>* hc = &zo_[1][0];
+    Buf<T>* hn = &zo_[1][1];
+    CDMPT_CUDA_TRY(cudaMemsetAsync(hc->x, 0, blk_ * sizeof(T), cx.stream));
+    if (hc->hi) CDMPT_CUDA_TRY(cudaMemsetAsync(hc->hi, 0, blk_ * sizeof(T), cx.stream));
+    if (hc->lo) CDMPT_CUDA_TRY(cudaMemsetAsync(hc->lo, 0, blk_ * sizeof(T), cx.stream));
+    CDMPT_TRY(Ew<T>::add_diag(hc->x, N_, ld, 1, a[K], cx.stream, hc->hi, hc->lo));
+    for (int k = K - 1; k >= 0; --k) {   // h <- U h + a_k I
+        Epilogue<T> ep;
+        ep.gamma = a[k];
+        ep.Dhi = hn->hi;
+        ep.Dlo = hn->lo;
+        CDMPT_TRY(gemm(cx, N_, N_, N_, U.op(), hc->op(), hn->x, ep, nullptr, engine));
+        std::swap(hc, hn);
+    }
+    Epilogue<T> ep;   // Z_0 = Y h
+    ep.Dhi = Z_[0].hi;
+    ep.Dlo = Z_[0].lo;
+    CDMPT_TRY(gemm(cx, N_, N_, N_, Y.op(), hc->op(), Z_[0].x, ep, nullptr, engine));
+    return Ew<T>::symmetrize(Z_[0].x, N_, ld, 1, cx.stream, Z_[0].hi, Z_[0].lo);
+}
+
+// First-order start of the Fermi-Dirac-exact variant: Z1_0 = Dtanh(Y)[Y1] for the stacked
+// directions Y1_d = -s2 H1_d (mu1 = 0; the mu1 term is added through Q afterwards), by the
+// tangent of the Horner scheme: with U1 = Y Y1 + Y1 Y, h1 <- U1 h + U h1 alongside h <- U h +
+// a_k I, and Z1_0 = Y1 h + Y h1. Left products with the symmetric N x N factors use the
+// transposed epilogue, (X_d F)^T = F X_d.
+template <typename T>
+cdmpt_status Solver<T>::init_z1(Context& cx, const double* H0, const double* H1, int D, T* out,
+                                T* out_hi, T* out_lo) {
+    const int N = N_;
+    const int rows = D * N;
+    const size_t count = (size_t)rows * ld;
+    const int acc = last_acc_;
+    std::vector<double> a;
+    const int K = tanh_terms(last_rho_, fdx_eps(), &a);
+    CDMPT_TRY(reserve_orders());
+    Buf<T>& Y = zo_[0][0];
+    Buf<T>& U = zo_[0][1];
+    Buf<T>* hc = &zo_[1][0];
+    Buf<T>* hn = &zo_[1][1];
+    Buf<T>& Y1 = Z1b_;
+    Buf<T>& U1 = A1_;
+    Buf<T>* gc = &RHS_;
+    Buf<T>* gn = &P_;
+    CDMPT_TRY(Ew<T>::init_z(Y.x, H0, N, ld, ld, 1, -last_s2_, last_mu_, cx.stream, Y.hi, Y.lo));
+    CDMPT_TRY(Ew<T>::init_z(Y1.x, H1, N, ld, ld, D, -last_s2_, 0.0, cx.stream, Y1.hi, Y1.lo));
+    auto zero = [&](Buf<T>& b, size_t c) -> cdmpt_status {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, c * sizeof(T), cx.stream));
+        if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, c * sizeof(T), cx.stream));
+        if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, c * sizeof(T), cx.stream));
+        return CDMPT_OK;
+    };
+    {
+        Epilogue<T> ep;   // U = Y Y
+        ep.Dhi = U.hi;
+        ep.Dlo = U.lo;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N, N, N, Y.op(), Y.op(), U.x, ep, nullptr, acc));
+    }
+    {
+        Epilogue<T> ep;   // S = Y1_d Y, then U1_d = S + S^T
+        CDMPT_TRY(gemm(cx, rows, N, N, Y1.op(), Y.op(), S_.x, ep, nullptr, acc));
+        CDMPT_TRY(Ew<T>::transpose_add(U1.x, S_.x, N, ld, D, cx.stream, U1.hi, U1.lo));
+    }
+    CDMPT_TRY(zero(*hc, blk_));
+    CDMPT_TRY(Ew<T>::add_diag(hc->x, N, ld, 1, a[K], cx.stream, hc->hi, hc->lo));
+    CDMPT_TRY(zero(*gc, count));
+    for (int k = K - 1; k >= 0; --k) {
+        {   // h1 <- U1 h + U h1  (U h1_d = (h1_d U)^T)
+            Epilogue<T> ep;
+            ep.Dhi = gn->hi;
+            ep.Dlo = gn->lo;
+            CDMPT_TRY(gemm(cx, rows, N, N, U1.op(), hc->op(), gn->x, ep, nullptr, acc));
+            Epilogue<T> e2;
+            e2.beta = 1.0;
+            e2.C = gn->x;
+            e2.ldc = ld;
+            e2.trans_block = N;
+            e2.Dhi = gn->hi;
+            e2.Dlo = gn->lo;
+            CDMPT_TRY(gemm(cx, rows, N, N, gc->op(), U.op(), gn->x, e2, nullptr, acc));
+        }
+        {   // h <- U h + a_k I
+            Epilogue<T> ep;
+            ep.gamma = a[k];
+            ep.Dhi = hn->hi;
+            ep.Dlo = hn->lo;
+            CDMPT_TRY(gemm(cx, N, N, N, U.op(), hc->op(), hn->x, ep, nullptr, acc));
+        }
+        std::swap(hc, hn);
+        std::swap(gc, gn);
+    }
+    {   // Z1_0 = Y1 h + Y h1  (Y h1_d = (h1_d Y)^T)
+        Epilogue<T> ep;
+        CDMPT_TRY(gemm(cx, rows, N, N, Y1.op(), hc->op(), out, ep, nullptr, acc));
+        Epilogue<T> e2;
+        e2.beta = 1.0;
+        e2.C = out;
+        e2.ldc = ld;
+        e2.trans_block = N;
+        CDMPT_TRY(gemm(cx, rows, N, N, gc->op(), Y.op(), out, e2, nullptr, acc));
+    }
+    return Ew<T>::symmetrize(out, N, ld, D, cx.stream, out_hi, out_lo);
+}
+
 // One step of the 0th-order recursion: W_k = Z_k Z_k and the correction d of
 // d (I + W_k) = -2 Z_k W_k, then Z_{k+1} = sym(2 Z_k + d) with its TF32 split.
 template <typename T>
@@ -360,7 +509,7 @@ template <typename T>
 cdmpt_status Solver<T>::sweep(Context& cx, const double* H0, double mu, double s2,
                               const cdmpt_opts& o, int n, int engine, double tol,
                               int* cg_iters) {
-    CDMPT_TRY(Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo));
+    CDMPT_TRY(init_z0(cx, H0, mu, s2, s2 * std::max(gmax_ - mu, mu - gmin_), acc_cur_));
     int total = 0, hint = 1;
     for (int k = 0; k < n; ++k)
         CDMPT_TRY(step0(cx, k, engine, tol, o.cg_maxit, true, true, &hint, &total));
@@ -475,6 +624,12 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
     ep.Dlo = RHS_.lo;
     ep.sym = true;
     CDMPT_TRY(gemm(cx, N, N, N, Z_[n].op(), Z_[n].op(), RHS_.x, ep, nullptr, acc));
+    if (fdx_) {   // Z_0 = tanh(Y): dZ_0/dmu = s2 (I - Z_0^2), so Q = beta/4 (I - Z_n^2) = beta P0 (I - P0)
+        CDMPT_TRY(Ew<T>::axpby(Qmu_.x, RHS_.x, blk_, 1.0, 0.0, nullptr, cx.stream));
+        st.cg_iterations_q = 0;
+        q_valid_ = true;
+        return CDMPT_OK;
+    }
     CgArgs a;   // (I - W_0) Q = beta/4 (I - Z_n^2), i.e. operator X - X W_0
     a.W = &W_[0];
     a.s = 1.0;
@@ -504,6 +659,10 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
 //   grad = -s2 Zh_0 + s2 Tr(Zh_0) Q / Tr Q.
 template <typename T>
 cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad, double p0_weight) {
+    if (fdx_) {
+        set_error("the adjoint is not available with the Fermi-Dirac-exact start (fd_exact)");
+        return CDMPT_ERR_ARG;
+    }
     if (!traj_valid_) {
         set_error("vjp: no completed solve on this handle");
         return CDMPT_ERR_ARG;
@@ -725,6 +884,11 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const doub
 template <typename T>
 cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, const double* w,
                                double* Pm, double* mu_out, double* omega, double* grad) {
+    if (fdx_) {
+        set_error("response orders other than the solve's are not available with the "
+                  "Fermi-Dirac-exact start (fd_exact)");
+        return CDMPT_ERR_ARG;
+    }
     if (!traj_valid_ || D < 1 || (m > 1 && (int)last_mu1_.size() < D)) {
         set_error("higher-order response: no completed solve with perturbations on this handle");
         return CDMPT_ERR_ARG;
@@ -882,6 +1046,10 @@ cdmpt_status Solver<T>::logdet(Context& cx, const Buf<T>& M, double a, double b,
 // canonical or fixed-mu constraint of the solve).
 template <typename T>
 cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
+    if (fdx_) {
+        set_error("the free energy is not available with the Fermi-Dirac-exact start (fd_exact)");
+        return CDMPT_ERR_ARG;
+    }
     if (!traj_valid_) {
         set_error("free energy: no completed solve on this handle");
         return CDMPT_ERR_ARG;
@@ -981,6 +1149,9 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     }
     CDMPT_TRY(reserve(N, D, n, ck));
     traj_valid_ = q_valid_ = false;
+    fdx_ = o.fd_exact != 0;
+    gmin_ = gmin;
+    gmax_ = gmax;
     replay_iters_ = 0;
     last_mu1_.assign(std::max(D, 0), 0.0);
     cdmpt_stats& st = *cx.st;
@@ -994,6 +1165,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     // engines: "acc" for FP32-accurate products, "fast" for the occupation sweeps
     const int acc = mixed ? (int)CDMPT_GEMM_TC_3XTF32 : engine_of(cx, 0);
     const int fast = mixed ? (bf16 ? (int)CDMPT_GEMM_TC_BF16 : (int)CDMPT_GEMM_TC_TF32) : acc;
+    acc_cur_ = acc;
     const double pad = std::min(40.0 / beta, 0.45 * (1.0 / s2 - width));
     double lo = gmin - pad, hi = gmax + pad;
     const bool gc = o.grand_canonical != 0;   // fixed mu: no occupation loop, mu1 = 0
@@ -1078,8 +1250,11 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                 const double slope = 0.25 * beta * (N - zz);
                 const double dmu = slope > 0 ? -err / slope : 0.0;
                 mu += dmu;
-                CDMPT_TRY(Ew<T>::add_diag(Z_[0].x, N, ld, 1, s2 * dmu, cx.stream, Z_[0].hi,
-                                          Z_[0].lo));
+                if (fdx_)   // Z_0 = tanh(Y) is not shifted by a multiple of I: rebuild it
+                    CDMPT_TRY(init_z0(cx, H0, mu, s2, s2 * std::max(gmax - mu, mu - gmin), acc));
+                else
+                    CDMPT_TRY(Ew<T>::add_diag(Z_[0].x, N, ld, 1, s2 * dmu, cx.stream, Z_[0].hi,
+                                              Z_[0].lo));
             }
         }
         if (!done) {
@@ -1106,7 +1281,11 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         const size_t count = (size_t)rows * ld;
         Buf<T>* Z1 = &Z1a_;
         Buf<T>* Z1n = &Z1b_;
-        CDMPT_TRY(Ew<T>::init_z(Z1->x, H1, N, ld, ld, D, -s2, 0.0, cx.stream, Z1->hi, Z1->lo));
+        if (fdx_)
+            CDMPT_TRY(init_z1(cx, H0, H1, D, Z1->x, Z1->hi, Z1->lo));
+        else
+            CDMPT_TRY(Ew<T>::init_z(Z1->x, H1, N, ld, ld, D, -s2, 0.0, cx.stream, Z1->hi,
+                                    Z1->lo));
         int total = 0, hint = 1;
         for (int k = 0; k < n; ++k) {
             CDMPT_TRY(need(cx, k));

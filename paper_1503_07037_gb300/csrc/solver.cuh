@@ -127,6 +127,14 @@ private:
     // Z_{k+1} from the step's linear system. *hint carries the CG chunk size.
     cdmpt_status step0(Context& cx, int k, int engine, double tol, int maxit, bool make_w,
                        bool solve, int* hint, int* iters);
+    // Z_0 at chemical potential mu: -s2 (H0 - mu I), or with fd_exact tanh of it (odd
+    // Taylor series in Y, |Y| <= rho); and the matching first-order start for D stacked
+    // directions of H1 (into out, with its TF32 split).
+    cdmpt_status init_z0(Context& cx, const double* H0, double mu, double s2, double rho,
+                         int engine);
+    cdmpt_status init_z1(Context& cx, const double* H0, const double* H1, int D, T* out,
+                         T* out_hi, T* out_lo);
+    double fdx_eps() const;
     // Make Z_k, W_k and Z_{k+1} of step k valid (checkpointing: recompute the
     // segment of step k from its checkpoint unless the segment buffers hold it).
     cdmpt_status need(Context& cx, int k);
@@ -178,6 +186,9 @@ private:
     bool traj_valid_ = false, q_valid_ = false;
     double last_beta_ = 0, last_s2_ = 0;
     double last_mu_ = 0, last_rho_ = 0;   // mu and max |z0| over the Gershgorin interval
+    bool fdx_ = false;                    // Fermi-Dirac-exact start of the current solve
+    double gmin_ = 0, gmax_ = 0;          // Gershgorin interval of H0
+    int acc_cur_ = 0;                     // FP32-accurate engine of the current solve
     int last_n_ = 0, last_acc_ = 0;
     double last_sweep_tol_ = 0;
     cdmpt_opts last_opts_{};
