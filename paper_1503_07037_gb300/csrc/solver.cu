@@ -1181,10 +1181,13 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         mu = std::min(std::max(mu, lo + 1e-3 * pad), hi - 1e-3 * pad);
     }
     const double occ_tol = o.occ_tol > 0 ? o.occ_tol : N * (sizeof(T) == 8 ? 1e-12 : 1e-7);
-    // one-pass TF32 traces are good to about 1e-4 relative, BF16 ones to about 1e-2;
-    // the refinement finishes mu
+    // one-pass TF32 traces are good to about 1e-4 relative, BF16 ones to about 1e-2, and
+    // their per-level rounding (2^-11, 2^-8) adds noise of about that times sqrt(N), which
+    // dominates for small N; the refinement finishes mu
     const double occ_tol_sweep =
-        mixed ? std::max(occ_tol, (bf16 ? 1e-3 : 1e-5) * N) : occ_tol;
+        mixed ? std::max({occ_tol, (bf16 ? 1e-3 : 1e-5) * N,
+                          (bf16 ? 1e-2 : 5e-4) * std::sqrt((double)N)})
+              : occ_tol;
     const double sweep_tol = mixed ? (bf16 ? 1e-3 : 1e-4) : o.cg_tol;
 
     // -------------------------------------------------- occupation loop
