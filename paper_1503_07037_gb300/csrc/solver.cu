@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <string>
 
@@ -157,6 +158,17 @@ int Solver<T>::engine_of(const Context& cx, int override_engine) const {
         const int e = override_engine ? override_engine : cx.engine;
         return e == CDMPT_GEMM_AUTO ? CDMPT_GEMM_TC_3XTF32 : e;
     }
+}
+
+// CDMPT_RESPONSE_IR=0 turns off the iterative-refinement CG of the mixed first-order
+// response (every iteration then uses the FP32-accurate engine).
+static bool response_ir() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("CDMPT_RESPONSE_IR");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 static double tensor_factor(int engine) {
@@ -1324,7 +1336,30 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             a.init_engine = a.iter_engine = acc;
             a.hint = hint;
             int it = 0;
-            CDMPT_TRY(cg(cx, Z1n->x, a, &it, nullptr));
+            if (mixed && response_ir()) {
+                // mixed-precision iterative refinement of the step's system: one-pass TF32
+                // CG iterations, each cycle stopped after about three digits, restarted from
+                // an FP32-accurate (split-TF32) residual of the current solution
+                a.iter_engine = fast == (int)CDMPT_GEMM_TC_BF16 ? (int)CDMPT_GEMM_TC_TF32 : fast;
+                a.tol_r0 = 1e-3;
+                for (int cyc = 0; cyc < 8; ++cyc) {
+                    if (cyc > 0) {
+                        a.x0 = Z1n;
+                        if constexpr (sizeof(T) == 4)
+                            CDMPT_TRY(split_tf32(Z1n->x, count, Z1n->hi, Z1n->lo, cx.stream));
+                    }
+                    int itc = 0;
+                    double rel0 = 0.0;
+                    CDMPT_TRY(cg(cx, Z1n->x, a, &itc, &rel0));
+                    it += itc;
+                    a.hint = std::max(1, itc);
+                    // done when the accurate residual already met the tolerance, or when this
+                    // cycle's three digits reached it
+                    if (itc == 0 || rel0 * a.tol_r0 <= o.cg_tol) break;
+                }
+            } else {
+                CDMPT_TRY(cg(cx, Z1n->x, a, &it, nullptr));
+            }
             total += it;
             hint = std::max(1, it);
             CDMPT_TRY(Ew<T>::axpby(Z1n->x, Z1->x, count, 2.0, 1.0, nullptr, cx.stream));
