@@ -445,9 +445,14 @@ struct BCg {
 
 // sym: every system's iterates are symmetric (0th-order solves), so the
 // products run on upper-triangular tiles.
+// init_engine (>= 0) computes the initial residual of warm-started systems with another
+// engine than the iterations; tol_r0 > 0 also stops a system once ||R|| <= tol_r0 ||R_0||;
+// rel0 (optional) receives the largest ||R_0|| / ||RHS|| over the systems.
 cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, double t, double tol,
                       const std::vector<const double*>& skip, int hint, int* iters,
-                      bool sym = false, int engine = kEngine) {
+                      bool sym = false, int engine = kEngine, int init_engine = -1,
+                      double tol_r0 = 0.0, double* rel0 = nullptr) {
+    if (init_engine < 0) init_engine = engine;
     const int G = b->B;
     CDMPT_TRY(zero_slots(b, 0, CG_NSLOTS));
     std::vector<GrpEw> dx, dr, drr, dbb, dp;
@@ -516,7 +521,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
     if (!g0.empty()) {
         CDMPT_TRY(run_ew(b, G_AXPBY, dx));
         CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
-        CDMPT_TRY(grouped_gemm(b, g0, engine));
+        CDMPT_TRY(grouped_gemm(b, g0, init_engine));
     } else {
         CDMPT_TRY(run_ew(b, G_ZERO, dx));
         CDMPT_TRY(run_ew(b, G_LINCOMB, dr));
@@ -529,7 +534,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
             di[i] = ewd(nullptr);
             di[i].sc = b->sys[i].sc;
             di[i].s0 = tol * tol;
-            di[i].s1 = 0.0;
+            di[i].s1 = tol_r0 * tol_r0;
             di[i].skip = skip[i];
         }
         const GrpEw* dev = nullptr;
@@ -610,13 +615,17 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
         }
         if (all) {
             *iters = most;
+            double worst = 0.0;
             for (int i = 0; i < G; ++i) {
                 const Sys& sy = b->sys[i];
                 const double f = (sym && a[i].rows == sy.N) ? sym_flops(b, sy.N)
                                                              : 2.0 * a[i].rows * (double)sy.N * sy.N;
                 add_flops(b, f * b->pinned[i * kSlots + CG_ITERS], engine);
-                if (a[i].x0 && !(skip[i] && b->sys[i].converged)) add_flops(b, f, engine);
+                if (a[i].x0 && !(skip[i] && b->sys[i].converged)) add_flops(b, f, init_engine);
+                const double bb = b->pinned[i * kSlots + CG_BB];
+                if (bb > 0) worst = std::max(worst, std::sqrt(b->pinned[i * kSlots + CG_RR0] / bb));
             }
+            if (rel0) *rel0 = worst;
             return CDMPT_OK;
         }
         if (done_iters >= b->opts.cg_maxit) {
@@ -1001,8 +1010,10 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             const double zz = b->pinned[i * kSlots + B_ZZ];
             const double err = trP - sy.nocc;
             double tol = b->opts.occ_tol > 0 ? b->opts.occ_tol : 1e-7 * sy.N;
-            // one-pass TF32 traces are good to about 1e-4; the refinement finishes mu
-            if (mixed) tol = std::max(tol, 1e-5 * sy.N);
+            // one-pass TF32 traces are good to about 1e-4, and their per-level rounding adds
+            // noise of about 5e-4 sqrt(N), which dominates for small N; the refinement
+            // finishes mu
+            if (mixed) tol = std::max({tol, 1e-5 * sy.N, 5e-4 * std::sqrt((double)sy.N)});
             if (std::fabs(err) <= tol) {
                 sy.converged = true;
                 continue;
@@ -1149,7 +1160,40 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             for (int i = 0; i < G; ++i)
                 add_flops(b, 6.0 * D * (double)b->sys[i].N * b->sys[i].N * b->sys[i].N);
             int it = 0;
-            cdmpt_status s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it);
+            cdmpt_status s = CDMPT_OK;
+            if (mixed) {
+                // mixed-precision iterative refinement of each step's system, as in
+                // cdmpt_solve: one-pass TF32 cycles that cut the residual about three digits,
+                // restarted from the split-TF32 residual of the current solution
+                std::vector<GrpEw> dsplit;   // hi/lo of the current solution for the restart
+                for (int i = 0; i < G; ++i) {
+                    Sys& sy = b->sys[i];
+                    Mat* Z1n = (k % 2 == 0) ? &sy.Z1b : &sy.Z1a;
+                    GrpEw e = ewd(Z1n->x, Z1n->x, Z1n->hi, Z1n->lo);
+                    e.rows = D * sy.N; e.ld = sy.ld; e.N = sy.N;
+                    e.count = (long long)D * sy.N * sy.ld;
+                    e.s0 = 1.0;
+                    e.s1 = 0.0;
+                    dsplit.push_back(e);
+                }
+                int h = hint;
+                for (int cyc = 0; cyc < 8 && s == CDMPT_OK; ++cyc) {
+                    if (cyc > 0) {
+                        for (int i = 0; i < G; ++i)
+                            cg[i].x0 = (k % 2 == 0) ? &b->sys[i].Z1b : &b->sys[i].Z1a;
+                        CDMPT_TRY(run_ew(b, G_AXPBY, dsplit));
+                    }
+                    int itc = 0;
+                    double r0 = 0.0;
+                    s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, h, &itc, false,
+                                 CDMPT_GEMM_TC_TF32, kEngine, 1e-3, &r0);
+                    it += itc;
+                    h = std::max(1, itc);
+                    if (itc == 0 || r0 * 1e-3 <= b->opts.cg_tol) break;
+                }
+            } else {
+                s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it);
+            }
             if (s != CDMPT_OK) return bfail(b, s);
             total += it;
             hint = std::max(1, it);

@@ -77,8 +77,9 @@ def test_extreme_temperatures_fp64(cuda, cdmpt_lib, beta, n):
     assert oracle.rel_frobenius(r["P1"][0], ref["P1"][0]) < 1e-9
 
 
-def test_batch_with_tiny_and_ragged_systems(cuda, cdmpt_lib):
-    """Sizes 1, 3, 33, 129 and 300 in one lockstep batch (FP32)."""
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_batch_with_tiny_and_ragged_systems(cuda, cdmpt_lib, precision):
+    """Sizes 1, 3, 33, 129 and 300 in one lockstep batch."""
     sizes = [1, 3, 33, 129, 300]
     probs = []
     for i, N in enumerate(sizes):
@@ -86,7 +87,7 @@ def test_batch_with_tiny_and_ragged_systems(cuda, cdmpt_lib):
         q.H1 = np.concatenate([q.H1, q.H1, q.H1]) * np.array([1.0, 0.5, -1.0])[:, None, None]
         q.beta, q.n = 10.0, 12
         probs.append(q)
-    bt = cdmpt_lib.Batch(sizes, 3)
+    bt = cdmpt_lib.Batch(sizes, 3, precision=precision)
     try:
         bt.set_H([q.H0 for q in probs], [q.H1 for q in probs], 12)
         rb = bt.solve([q.beta for q in probs], [q.nocc for q in probs], 12)
