@@ -113,7 +113,7 @@ __device__ __forceinline__ void put_split16(T* hi, T* lo, size_t i, const T (&v)
                 l[k] = __uint_as_float(b);
             }
             store16(hi + i, h);
-            store16(lo + i, l);
+            if (lo) store16(lo + i, l);   // lo = null: the one-pass TF32 engine reads hi only
         }
     }
 }

@@ -267,7 +267,12 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
     CDMPT_TRY(Ew<T>::dot(a.rhs, a.rhs, count, sc + CG_BB, nullptr, cx.stream));
     CDMPT_TRY(cg_scalar_init(sc, a.tol * a.tol * a.rhs_scale * a.rhs_scale, a.tol_r0 * a.tol_r0,
                              cx.stream));
-    CDMPT_TRY(Ew<T>::axpby(P_.x, R_.x, count, 1.0, 0.0, sc + CG_DONE, cx.stream, P_.hi, P_.lo));
+    // the split of the direction P: both halves for the split-TF32 iterations, hi alone for
+    // one-pass TF32, none for the engines that read P itself
+    T* p_hi = (iter_engine == CDMPT_GEMM_TC_3XTF32 || iter_engine == CDMPT_GEMM_TC_TF32) ? P_.hi
+                                                                                        : nullptr;
+    T* p_lo = iter_engine == CDMPT_GEMM_TC_3XTF32 ? P_.lo : nullptr;
+    CDMPT_TRY(Ew<T>::axpby(P_.x, R_.x, count, 1.0, 0.0, sc + CG_DONE, cx.stream, p_hi, p_lo));
 
     int chunk = std::max(1, a.hint);
     int iters = 0;
@@ -286,7 +291,7 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
             CDMPT_TRY(gemm(cx, a.rows, N_, N_, P_.op(), a.W->op(), Q_.x, ep, sc + CG_DONE,
                            iter_engine));
             CDMPT_TRY(Ew<T>::cg_update(X, R_.x, P_.x, Q_.x, count, sc, cx.stream));
-            CDMPT_TRY(Ew<T>::cg_direction(P_.x, R_.x, count, sc, cx.stream, P_.hi, P_.lo));
+            CDMPT_TRY(Ew<T>::cg_direction(P_.x, R_.x, count, sc, cx.stream, p_hi, p_lo));
             CDMPT_TRY(cg_scalar_step(sc, cx.stream));
         }
         CDMPT_TRY(read_scalars(cx, sc, CG_NSLOTS));
