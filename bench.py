@@ -154,6 +154,34 @@ def time_oracle(sample_betas, cores_note=True):
     return len(sample_betas) / dt, dt, res
 
 
+def time_oracle_one_core():
+    """The oracle's beta = 20 solve of a 16 x 16 x 8 lattice (N = 2048) on one host core, in a
+    child process whose BLAS pools are limited to one thread; scaled to the N = 4096 workload by
+    the N^3 cost of the eigendecomposition and the Daleckii-Krein products (x 8). A bounded sample:
+    about 10 s on one core."""
+    import subprocess
+    import sys
+    code = ("import time, oracle, synthetic\n"
+            "p = synthetic.cubic_lattice((16, 16, 8), seed=1002, beta=20.0, n=14)\n"
+            "t = time.perf_counter()\n"
+            "oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind='rec')\n"
+            "print(time.perf_counter() - t)\n")
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
+        env[k] = "1"
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=here, env=env, capture_output=True,
+                             text=True, timeout=300, check=True)
+        dt = float(out.stdout.strip().splitlines()[-1])
+    except Exception as e:   # a missing baseline must not fail the bench
+        return {"unavailable": f"one-core oracle run failed: {e}"[:200]}
+    return {"value": 1.0 / (8.0 * dt), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"beta=20 solve of the 16x16x8 lattice (N=2048) in {dt:.1f} s on one core, "
+                      f"scaled x8 (N^3) to N=4096"}
+
+
 def blas_threads():
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(k):
@@ -350,6 +378,7 @@ def run_ours(args):
         chain = run_chain(pkg, pk)
 
     cpu = None
+    cpu1 = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # bounded oracle sample: the beta = 20 solve of the workload, eigendecomposition included
@@ -357,6 +386,7 @@ def run_ours(args):
         v, dt, res = time_oracle([20.0])
         cpu = {"value": v, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"1 of the 3 solves of a step (beta=20, N=4096), {dt:.1f} s"}
+        cpu1 = time_oracle_one_core()
         if outs_by_mode:
             eig = np.linalg.eigh(probs[0].H0)
             refs = {p.beta: oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=eig)
@@ -378,13 +408,15 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "gemm": {"fp32": "tcgen05 3xTF32", "fp64": "CUDA-core DFMA",
-                                "mixed": "tcgen05 TF32 sweeps, 3xTF32 refinement and response"
+                                "mixed": "tcgen05 TF32 sweeps and response CG iterations, 3xTF32 "
+                                         "refinement, response right-hand sides and restarts"
                                 }[args.precision],
                        "l2": "no flush: working set (trajectory of 29 N x N matrices plus "
                              "their TF32 splits, 5.4 GiB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "cpu_baseline_one_core": cpu1,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
