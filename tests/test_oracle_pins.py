@@ -774,3 +774,21 @@ def test_scc_free_energy_response_rule():
     d2 = (-w[-2] + 16 * w[-1] - 30 * w[0] + 16 * w[1] - w[2]) / (12 * h * h)
     assert abs(d1 - r["omega1"][0]) < 1e-8 * max(1.0, abs(d1))
     assert abs(0.5 * d2 - r["omega2"][0]) < 1e-5 * abs(r["omega2"][0])
+
+
+def test_table2_pattern_low_temperature_needs_enough_steps():
+    """Tab. 2's qualitative pattern, on a gapped tight-binding chain instead of H2O: at low
+    temperature Algorithm 1's occupation loop (Newton with P_mu = beta P (I - P)) does not
+    converge with too few recursion steps (beta = 1000: M = 4 and 6 fail, M >= 8 converge),
+    while at high temperature every M converges. With M too small X_0 lies far outside
+    [0, 1], where x^2 / (x^2 + (1 - x)^2) sends distant levels towards 1/2, so the occupation
+    is wrong. The library refuses such (beta, n) with ERR_RANGE before they are run."""
+    H0, H1 = _dimer_chain(24)
+    H1 = H1 * 0.05
+    for M in (4, 6):
+        with pytest.raises(RuntimeError):
+            o.literal_canonical(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
+    for M in (8, 12, 16):
+        o.literal_canonical(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
+    for M in (4, 6, 8):
+        o.literal_canonical(H0, H1, 10.0, 12.0, M, mu0=0.3, maxit=100)
