@@ -255,6 +255,18 @@ cdmpt_status cdmpt_polarizability(cdmpt_handle* h, double* alpha);
  * Errors: ERR_ARG (no solve yet, NULL pointers), ERR_CG_MAXITER, ERR_CUDA. */
 cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int on_device);
 
+/* First-order canonical response of the last solve to other perturbations: D
+ * directions H1_d (D x N x N FP64, host or device per on_device), answered on the
+ * stored trajectory without a new solve (every order and direction shares the step
+ * matrices T_k, Sec. II). P1_d (D x N x N, may be NULL) with mu1_d from Tr P1_d = 0,
+ * and Omega^(2)_d = 1/2 Tr[H1_d P1_d] (Eq. Resp_0; alpha_d = -4 Omega^(2)_d), host
+ * arrays of D doubles (may be NULL). In the non-orthogonal mode H1 is h1 and P1 is
+ * D1. Not available with fd_exact (ERR_ARG).
+ * Errors: ERR_ARG (no solve yet, D outside 1..16, H1 NULL), ERR_CG_MAXITER,
+ * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,
+                             double* omega2, int on_device);
+
 /* Second-order canonical response of the last solve, per direction d of H1:
  * P2_d = (1/2) d^2 P / d lambda_d^2 of P(H0 + lambda_d H1_d) (Algorithm 1, the
  * order-2 line, with H^(2) = 0), with the second-order chemical-potential

@@ -104,7 +104,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
-           "cdmpt_get_overlap_info", "cdmpt_scc_solve"]
+           "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1"]
 
 
 def lib() -> ctypes.CDLL:
@@ -135,6 +135,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_response3": (I, [P, P, P, P, I]),
+        "cdmpt_response1": (I, [P, I, P, P, P, P, I]),
         "cdmpt_free_energy": (I, [P, P, P, I]),
         "cdmpt_set_overlap": (I, [P, I, P, I]),
         "cdmpt_get_overlap_info": (I, [P, P, P]),
@@ -409,6 +410,36 @@ class Handle:
         out = torch.empty_like(G)
         _check(lib().cdmpt_vjp_P0(self.h, _ptr(G), _ptr(out), 1 if G.is_cuda else 0), self.h)
         return out
+
+    def response1(self, H1, want_P1=True, device="cuda"):
+        """First-order response of the last solve to new perturbations H1 ((D, N, N) or (N, N);
+        numpy or torch) on the stored trajectory: dict(P1, mu1, omega2, alpha)."""
+        import torch
+        N = self.N
+        if isinstance(H1, torch.Tensor):
+            h = H1.detach().to(torch.float64).contiguous()
+            if h.ndim == 2:
+                h = h[None]
+            on_in = 1 if h.is_cuda else 0
+            ptr_in = h.data_ptr()
+        else:
+            h = np.ascontiguousarray(H1, dtype=np.float64)
+            if h.ndim == 2:
+                h = h[None]
+            on_in = 0
+            ptr_in = h.ctypes.data
+        D = h.shape[0]
+        dev = torch.device(device)
+        if (dev.type == "cuda") != bool(on_in):   # one placement for inputs and outputs
+            h = (torch.from_numpy(h) if not on_in else h.cpu()).to(dev).contiguous()
+            ptr_in = h.data_ptr()
+            on_in = 1 if dev.type == "cuda" else 0
+        P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev) if want_P1 else None
+        mu1 = np.zeros(D)
+        om2 = np.zeros(D)
+        _check(lib().cdmpt_response1(self.h, D, ptr_in, _ptr(P1), mu1.ctypes.data,
+                                     om2.ctypes.data, on_in), self.h)
+        return {"P1": P1, "mu1": mu1, "omega2": om2, "alpha": -4.0 * om2}
 
     def response2(self, weights=None, want_P2=True, want_grad=True, device="cuda"):
         """Second-order canonical response of the last solve: dict(P2 (D, N, N), mu2 (D,),

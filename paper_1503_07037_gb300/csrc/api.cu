@@ -691,6 +691,66 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
     return CDMPT_OK;
 }
 
+cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,
+                             double* omega2, int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (!h->solved)
+        return fail_msg(h, CDMPT_ERR_ARG, "response1: no completed solve on this handle");
+    if (D < 1 || D > 16 || !H1)
+        return fail_msg(h, CDMPT_ERR_ARG, "response1: need 1 <= D <= 16 and H1");
+    cudaStream_t s = h->cx.stream;
+    const int N = h->N, ld = h->ld;
+    const size_t nn = (size_t)N * N, blk = (size_t)N * ld;
+    const bool ov = h->ovN != 0;
+    // padded FP64 copy of the perturbations (and of P1 when it needs mapping or a host copy)
+    const bool via = P1 && (!on_device || ov);
+    double* w = nullptr;
+    const size_t elems = (size_t)D * blk + (via ? (size_t)D * nn : 0);
+    CDMPT_CUDA_TRY(cudaMallocAsync((void**)&w, elems * sizeof(double), s));
+    double* h1p = w;
+    double* pout = via ? w + (size_t)D * blk : P1;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cdmpt_status st = CDMPT_OK;
+    if (cudaMemsetAsync(h1p, 0, (size_t)D * blk * sizeof(double), s) != cudaSuccess ||
+        cudaMemcpy2DAsync(h1p, ld * sizeof(double), H1, N * sizeof(double), N * sizeof(double),
+                          (size_t)D * N, kind, s) != cudaSuccess) {
+        set_error("response1: copy of H1 failed");
+        st = CDMPT_ERR_CUDA;
+    }
+    for (int d = 0; d < D && st == CDMPT_OK && ov; ++d)   // h1_perp = Z h1 Z
+        st = congruence(h->Zov, ld, N, h1p + d * blk, ld, h1p + d * blk, ld, h->ovtmp, s);
+    std::vector<double> m1(D, 0.0), om(D, 0.0);
+    cdmpt_stats keep = h->st;
+    h->cx.st = &h->st;
+    if (st == CDMPT_OK) {
+        if (h->opts.precision == CDMPT_FP64)
+            st = h->sd ? h->sd->response1(h->cx, h1p, D, pout, m1.data(), om.data())
+                       : CDMPT_ERR_ARG;
+        else
+            st = h->sf ? h->sf->response1(h->cx, h1p, D, pout, m1.data(), om.data())
+                       : CDMPT_ERR_ARG;
+    }
+    h->st = keep;
+    if (st == CDMPT_OK && P1 && ov) {
+        st = ov_map(h, pout, P1, D, on_device);   // D1 = Z P1 Z
+    } else if (st == CDMPT_OK && via) {
+        if (cudaMemcpyAsync(P1, pout, (size_t)D * nn * sizeof(double), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("response1: copy of P1 failed");
+            st = CDMPT_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(w, s);
+    cudaStreamSynchronize(s);
+    if (st != CDMPT_OK) return fail(h, st);
+    for (int d = 0; d < D; ++d) {
+        if (mu1) mu1[d] = m1[d];
+        if (omega2) omega2[d] = om[d];
+    }
+    return CDMPT_OK;
+}
+
 // Orders 2 and 3 share the marshalling: P^(m) (and the gradient) through a
 // device scratch when the caller's buffers are on the host.
 static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm, double* mu,
