@@ -399,29 +399,31 @@ def _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad):
     return out
 
 
-def _dk2_matrix(ht, eps, F, mu, beta, n, close, quad, batch):
-    """S_ij = sum_k f[e_i, e_k, e_j] ht_ik ht_kj, the second-order Daleckii-Krein sum.
+def _dk2_matrix(ht, eps, F, mu, beta, n, close, quad, batch, b=None):
+    """S_ij = sum_k f[e_i, e_k, e_j] ht_ik b_kj (b = ht if None), the second-order
+    Daleckii-Krein sum.
 
     For pairs with beta |e_i - e_j| > close it is the exact identity
-    [(F o ht) ht - ht (F o ht)]_ij / (e_i - e_j); closer pairs are summed
+    [(F o ht) b - ht (F o b)]_ij / (e_i - e_j); closer pairs are summed
     explicitly with ``_second_dd_for_pairs``.
     """
+    if b is None:
+        b = ht
     diff = eps[:, None] - eps[None, :]
     ci, cj = np.nonzero(np.abs(diff) * beta <= close)
-    G = F * ht
     with np.errstate(divide="ignore", invalid="ignore"):
-        S = (G @ ht - ht @ G) / diff
+        S = ((F * ht) @ b - ht @ (F * b)) / diff
     for s0 in range(0, ci.shape[0], batch):
         I = ci[s0:s0 + batch]
         J = cj[s0:s0 + batch]
         F3 = _second_dd_for_pairs(I, J, eps, F, mu, beta, n, quad)
-        S[I, J] = np.sum(F3 * ht[I, :] * ht[:, J].T, axis=1)
+        S[I, J] = np.sum(F3 * ht[I, :] * b[:, J].T, axis=1)
     return S
 
 
 def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
               close: float = 1.0, quad: float = 1.0, batch: int = 1024, canonical: bool = True,
-              mu: Optional[float] = None):
+              mu: Optional[float] = None, H2=None):
     """Second-order canonical response P2 = (1/2) d^2 P / d lambda^2 of P(H0 + lambda H1).
 
     Second-order Daleckii-Krein formula in the eigenbasis of H0, with
@@ -440,6 +442,10 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     Eq. (Resp_0) (the n+1 rule: P^(2) suffices for Omega^(3)).
     canonical=False keeps mu fixed (given by ``mu``, else found from nocc):
     mu1 = mu2 = 0, the grand-canonical response.
+    H2 (D, N, N), optional: a second-order term of the perturbation, H(lambda) = H0 +
+    lambda H1 + lambda^2 H2 (Eq. H_prt); it adds sum f[e_i, e_j] (h2)_ij, and Omega^(3)
+    becomes (1/3)(Tr[H1 P2] + 2 Tr[H2 P1]) (Eq. Resp_0). grad_alpha is the gradient of
+    alpha = -2 Tr[P1 H1] and does not involve H2.
     """
     H0 = np.asarray(H0, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
@@ -454,19 +460,27 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     N = eps.shape[0]
     P2 = np.empty_like(H1)
     mu2 = np.zeros(H1.shape[0])
+    grad = np.empty_like(H1)
     for d in range(H1.shape[0]):
         ht = V.T @ H1[d] @ V - base["mu1"][d] * np.eye(N)
         S = _dk2_matrix(ht, eps, F, mu, beta, nn, close, quad, batch)
+        # d alpha / d H0 = -4 P2 of H1 alone (mu2 from Tr = 0 for that part)
+        m0 = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
+        grad[d] = -4.0 * V @ (S - m0 * np.diag(fp)) @ V.T
+        if H2 is not None:
+            S = S + F * (V.T @ H2[d] @ V)
         mu2[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
         P2[d] = V @ (S - mu2[d] * np.diag(fp)) @ V.T
     out = dict(base)
-    # Eq. (Resp_0) with H^(1) = H1 and no higher orders: Omega^(3) = (1/3) Tr[H1 P^(2)]
-    omega3 = np.array([np.sum(H1[d] * P2[d]) / 3.0 for d in range(H1.shape[0])])
-    out.update(P2=P2, mu2=mu2, grad_alpha=-4.0 * P2, omega3=omega3)
+    # Eq. (Resp_0): Omega^(3) = (1/3)(Tr[H1 P2] + 2 Tr[H2 P1] + 3 Tr[H3 P0]), H3 = 0 here
+    omega3 = np.array([(np.sum(H1[d] * P2[d])
+                        + (2.0 * np.sum(H2[d] * base["P1"][d]) if H2 is not None else 0.0)) / 3.0
+                       for d in range(H1.shape[0])])
+    out.update(P2=P2, mu2=mu2, grad_alpha=grad, omega3=omega3)
     return out
 
 
-def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M):
+def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M, H2=None):
     """The inner loop of Algorithm 1 for orders 0, 1 and 2 (H^(2) = 0), dense solves.
 
     X_0^(2) = -2^-(M+2) beta (H^(2) - mu2 I) = 2^-(M+2) beta mu2 I, and per step
@@ -479,7 +493,7 @@ def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M):
     s = 2.0 ** (-(M + 2)) * beta
     X0 = 0.5 * I - s * (H0 - mu * I)
     X1 = -s * (H1 - mu1 * I)
-    X2 = s * mu2 * I
+    X2 = -s * ((0.0 if H2 is None else H2) - mu2 * I)
     for _ in range(M):
         T = 2.0 * X0 @ (X0 - I) + I
         C0 = X0 @ X0
@@ -602,7 +616,7 @@ def _dd4_idx(i, k, l, j, eps, F, mu, beta, n, quad):
 
 def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", eig=None,
               close: float = 1.0, quad: float = 1.0, batch: int = 1024, canonical: bool = True,
-              mu: Optional[float] = None):
+              mu: Optional[float] = None, H2=None, H3=None):
     """Third-order canonical response P3 = (1/6) d^3 P / d lambda^3 of P(H0 + lambda H1).
 
     P(lambda) = f(H0 + lambda ht - lambda^2 mu2 I - lambda^3 mu3 I) with ht = H1 -
@@ -618,6 +632,11 @@ def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     (Eq. Resp_0 with H^(1) = H1 only). Returns the results of ``response2`` plus
     P3 (D, N, N), mu3 (D,) and omega4 (D,). canonical=False: mu fixed, mu1 =
     mu2 = mu3 = 0.
+    H2, H3 (D, N, N), optional: higher terms of the perturbation, H(lambda) = H0 +
+    lambda H1 + lambda^2 H2 + lambda^3 H3 (Eq. H_prt). With h2 = V^T H2 V and h3 =
+    V^T H3 V the mu2 cross term becomes sum_k f[e_i, e_k, e_j] (g_ik g2_kj + g2_ik g_kj)
+    with g2 = h2 - mu2 I, the first-order term f[e_i, e_j] (h3)_ij is added, and
+    Omega^(4) = (1/4)(Tr[H1 P3] + 2 Tr[H2 P2] + 3 Tr[H3 P1]) (Eq. Resp_0).
     """
     H0 = np.asarray(H0, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
@@ -626,7 +645,7 @@ def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
     nn = n if kind == "rec" else None
     eps, V = np.linalg.eigh(H0) if eig is None else eig
     base = response2(H0, H1, beta, nocc, n, kind, eig=(eps, V), close=close, quad=quad,
-                     batch=batch, canonical=canonical, mu=mu)
+                     batch=batch, canonical=canonical, mu=mu, H2=H2)
     mu = base["mu"]
     F = divided_differences(eps, mu, beta, nn)
     fp = np.diag(F).copy()
@@ -650,15 +669,27 @@ def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
             f4 = _dd4_idx(i, kk, ll, j, eps, F, mu, beta, nn, quad)
             S[i, j] = np.sum(f4 * g[i, :][:, None] * g * g[:, j][None, :])
         S = S - base["mu2"][d] * f_iij * g
+        if H2 is not None:
+            h2 = V.T @ H2[d] @ V
+            S = (S + _dk2_matrix(g, eps, F, mu, beta, nn, close, quad, batch, b=h2)
+                 + _dk2_matrix(h2, eps, F, mu, beta, nn, close, quad, batch, b=g))
+        if H3 is not None:
+            S = S + F * (V.T @ H3[d] @ V)
         mu3[d] = float(np.trace(S) / np.sum(fp)) if canonical else 0.0
         P3[d] = V @ (S - mu3[d] * np.diag(fp)) @ V.T
     out = dict(base)
-    omega4 = np.array([np.sum(H1[d] * P3[d]) / 4.0 for d in range(H1.shape[0])])
+    if H3 is not None:   # Omega^(3) gains 3 Tr[H3 P0] / 3 (Eq. Resp_0)
+        out["omega3"] = out["omega3"] + np.array([np.sum(H3[d] * base["P0"])
+                                                  for d in range(H1.shape[0])])
+    omega4 = np.array([(np.sum(H1[d] * P3[d])
+                        + (2.0 * np.sum(H2[d] * base["P2"][d]) if H2 is not None else 0.0)
+                        + (3.0 * np.sum(H3[d] * base["P1"][d]) if H3 is not None else 0.0)) / 4.0
+                       for d in range(H1.shape[0])])
     out.update(P3=P3, mu3=mu3, omega4=omega4)
     return out
 
 
-def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M):
+def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M, H2=None, H3=None):
     """The inner loop of Algorithm 1 for orders 0 to 3 (H^(2) = H^(3) = 0), dense solves.
 
     X_0^(k) = 2^-(M+2) beta mu_k I for k = 2, 3, and per step
@@ -671,8 +702,8 @@ def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M):
     s = 2.0 ** (-(M + 2)) * beta
     X0 = 0.5 * I - s * (H0 - mu * I)
     X1 = -s * (H1 - mu1 * I)
-    X2 = s * mu2 * I
-    X3 = s * mu3 * I
+    X2 = -s * ((0.0 if H2 is None else H2) - mu2 * I)
+    X3 = -s * ((0.0 if H3 is None else H3) - mu3 * I)
     for _ in range(M):
         T = 2.0 * X0 @ (X0 - I) + I
         C0 = X0 @ X0

@@ -792,3 +792,82 @@ def test_table2_pattern_low_temperature_needs_enough_steps():
         o.literal_canonical(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
     for M in (4, 6, 8):
         o.literal_canonical(H0, H1, 10.0, 12.0, M, mu0=0.3, maxit=100)
+
+
+# --------------------------------------------------------------------------
+# higher perturbation terms H(lambda) = H0 + lambda H1 + lambda^2 H2 + lambda^3 H3
+# (Eq. H_prt; Algorithm 1's X_0^(i) with H^(i) for i = 1..3)
+# --------------------------------------------------------------------------
+
+def _higher_case(N=18, seed=91):
+    H0 = _rand_sym(N, seed, 0.4)
+    H1 = _rand_sym(N, seed + 1, 0.1) + np.diag(np.arange(N) - (N - 1) / 2) * 0.05
+    return H0, H1, _rand_sym(N, seed + 2, 0.05), _rand_sym(N, seed + 3, 0.03)
+
+
+def test_higher_terms_match_literal_algorithm1():
+    """With H2 and H3 the closed forms equal Algorithm 1's recursion of orders 2 and 3, whose
+    traces vanish at the oracle's mu2 and mu3."""
+    H0, H1, H2, H3 = _higher_case()
+    beta, nocc, n = 5.0, 9.0, 10
+    r = o.response3(H0, H1[None], beta, nocc, n=n, H2=H2[None], H3=H3[None])
+    X = o.literal_recursion3(H0, H1, beta, r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0], n,
+                             H2=H2, H3=H3)
+    assert o.rel_frobenius(X[2], r["P2"][0]) < 1e-10
+    assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-10
+    assert abs(np.trace(X[2])) < 1e-11 and abs(np.trace(X[3])) < 1e-11
+
+
+def test_higher_terms_against_high_precision_brute_force():
+    """60-digit brute force of the canonical P(lambda) for H(lambda) = H0 + lambda H1 +
+    lambda^2 H2 + lambda^3 H3: P2, P3, mu2 and mu3 by central differences."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    N, beta, nocc, n = 5, 3.0, 2.0, 6
+    H0, H1, H2, H3 = (_rand_sym(N, 61), _rand_sym(N, 62, 0.5), _rand_sym(N, 63, 0.3),
+                      _rand_sym(N, 64, 0.2))
+    r = o.response3(H0, H1[None], beta, nocc, n=n, H2=H2[None], H3=H3[None])
+    m2 = mp.mpf(2) ** n
+    c = mp.mpf(beta) / mp.mpf(2) ** (n + 1)
+
+    def g(e, mu):
+        return (1 + mp.tanh(m2 * mp.atanh(-c * (e - mu)))) / 2
+
+    def at(lam):
+        A = (mp.matrix(H0.tolist()) + lam * mp.matrix(H1.tolist())
+             + lam ** 2 * mp.matrix(H2.tolist()) + lam ** 3 * mp.matrix(H3.tolist()))
+        E, Q = mp.eigsy(A)
+        mu = mp.findroot(lambda u: sum(g(E[i], u) for i in range(N)) - nocc, mp.mpf(r["mu"]))
+        return Q * mp.diag([g(E[i], mu) for i in range(N)]) * Q.T, mu
+
+    h = mp.mpf("1e-12")
+    vals = {k: at(k * h) for k in (-2, -1, 0, 1, 2)}
+    P = {k: v[0] for k, v in vals.items()}
+    mu = {k: v[1] for k, v in vals.items()}
+    c2 = (P[1] - 2 * P[0] + P[-1]) / (2 * h ** 2)
+    c3 = (P[2] - 2 * P[1] + 2 * P[-1] - P[-2]) / (12 * h ** 3)
+    to_np = lambda M: np.array([[float(M[i, j]) for j in range(N)] for i in range(N)])
+    assert o.rel_frobenius(r["P2"][0], to_np(c2)) < 1e-10
+    assert o.rel_frobenius(r["P3"][0], to_np(c3)) < 1e-10
+    assert abs(float((mu[1] - 2 * mu[0] + mu[-1]) / (2 * h ** 2)) - r["mu2"][0]) < 1e-10
+    assert abs(float((mu[2] - 2 * mu[1] + 2 * mu[-1] - mu[-2]) / (12 * h ** 3))
+               - r["mu3"][0]) < 1e-10
+
+
+def test_n_plus_one_rule_with_higher_perturbation_terms():
+    """Eq. Resp_0 in general: Omega^(3) = (1/3)(Tr[H1 P2] + 2 Tr[H2 P1]) and
+    Omega^(4) = (1/4)(Tr[H1 P3] + 2 Tr[H2 P2] + 3 Tr[H3 P1]), against the third and fourth
+    derivatives of the canonical free energy of H(lambda) (Fermi-Dirac)."""
+    H0, H1, H2, H3 = _higher_case(10, 8)
+    beta, nocc, h = 3.0, 4.0, 2e-2
+    r = o.response3(H0, H1[None], beta, nocc, kind="fd", H2=H2[None], H3=H3[None])
+
+    def omega(lam):
+        H = H0 + lam * H1 + lam ** 2 * H2 + lam ** 3 * H3
+        return o.solve(H, H1, beta, nocc, kind="fd")["omega"]
+    w = {k: omega(k * h) for k in (-3, -2, -1, 0, 1, 2, 3)}
+    d3 = (-w[3] + 8 * w[2] - 13 * w[1] + 13 * w[-1] - 8 * w[-2] + w[-3]) / (8 * h ** 3)
+    d4 = (-w[3] + 12 * w[2] - 39 * w[1] + 56 * w[0] - 39 * w[-1] + 12 * w[-2] - w[-3]) / (
+        6 * h ** 4)
+    assert abs(d3 / 6.0 - r["omega3"][0]) < 1e-5 * abs(r["omega3"][0])
+    assert abs(d4 / 24.0 - r["omega4"][0]) < 1e-3 * abs(r["omega4"][0])
