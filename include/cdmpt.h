@@ -225,6 +225,20 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* model, int 
                              double nocc, int n, double* D0, double* D1, double* mu, double* mu1,
                              double* omega1, double* omega2, int* iters, int on_device);
 
+/* Higher terms of the perturbation, H(lambda) = H0 + lambda H1 + lambda^2 H2 +
+ * lambda^3 H3 per direction (Eq. H_prt; Algorithm 1 starts order i from
+ * X_0^(i) = -2^-(M+2) beta (H^(i) - mu^(i) I)). H2 and H3 are D x N x N FP64 (D and N
+ * of the last cdmpt_set_H), host or device per on_device, either may be NULL (zero).
+ * They enter cdmpt_response2 (P2, mu2, Omega^(3) = 1/3 (Tr[H1 P2] + 2 Tr[H2 P1] +
+ * 3 Tr[H3 P0])) and cdmpt_response3 (P3, mu3, Omega^(4) = 1/4 (Tr[H1 P3] +
+ * 2 Tr[H2 P2] + 3 Tr[H3 P1])), Eq. Resp_0; the first order and the solve do not
+ * depend on them. While either is set, cdmpt_response2 refuses the polarizability
+ * gradient (it is d alpha / d H0 for H^(2) = H^(3) = 0). cdmpt_set_H and
+ * cdmpt_set_overlap clear them; in the non-orthogonal mode they are mapped like h1.
+ * Errors: ERR_ARG (no directions set), ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_set_H_orders(cdmpt_handle* h, const double* H2, const double* H3,
+                                int on_device);
+
 /* Canonical solve, Algorithm 1 to first order.
  * beta > 0: inverse temperature; nocc in (0, N): occupation; n >= 1:
  * recursion steps (M in the paper).

@@ -104,7 +104,8 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_batch_last_error", "cdmpt_batch_destroy", "cdmpt_split_tf32",
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
-           "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1"]
+           "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1",
+           "cdmpt_set_H_orders"]
 
 
 def lib() -> ctypes.CDLL:
@@ -136,6 +137,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_response3": (I, [P, P, P, P, I]),
         "cdmpt_response1": (I, [P, I, P, P, P, P, I]),
+        "cdmpt_set_H_orders": (I, [P, P, P, I]),
         "cdmpt_free_energy": (I, [P, P, P, I]),
         "cdmpt_set_overlap": (I, [P, I, P, I]),
         "cdmpt_get_overlap_info": (I, [P, P, P]),
@@ -385,6 +387,21 @@ class Handle:
         set_H(self.h, N, p0, D, p1, on_dev)
         self._keep = None
         self.N, self.D = N, D
+
+    def set_H_orders(self, H2=None, H3=None):
+        """Higher perturbation terms H2, H3 ((D, N, N) numpy arrays, or None for zero) of
+        H(lambda) = H0 + lambda H1 + lambda^2 H2 + lambda^3 H3, used by response2/3."""
+        keep = []
+
+        def ptr(A):
+            if A is None:
+                return None
+            a = np.ascontiguousarray(A, dtype=np.float64)
+            if a.ndim == 2:
+                a = a[None]
+            keep.append(a)
+            return a.ctypes.data
+        _check(lib().cdmpt_set_H_orders(self.h, ptr(H2), ptr(H3), 0), self.h)
 
     def solve(self, beta, nocc, n, want_P0=True, want_P1=True, device="cuda"):
         """Returns dict(P0, P1, mu, mu1) with P0/P1 float64 torch tensors on `device`."""

@@ -67,6 +67,8 @@ struct cdmpt_handle {
     int N = 0, D = 0, ld = 0;
     double* H0 = nullptr;     // N x ld, FP64, zero padding
     double* H1 = nullptr;     // D x N x ld
+    double* H2 = nullptr;     // D x N x ld higher perturbation terms (cdmpt_set_H_orders), or null
+    double* H3 = nullptr;
     double* dscal = nullptr;  // device scalars for set_H (bounds, trace)
     double gmin = 0, gmax = 0, trH0 = 0;
     Solver<float>* sf = nullptr;
@@ -214,7 +216,9 @@ cdmpt_status cdmpt_set_overlap(cdmpt_handle* h, int N, const double* S, int on_d
     // the stored Hamiltonian belongs to the previous basis: cdmpt_set_H must follow
     cudaFree(h->H0);
     cudaFree(h->H1);
-    h->H0 = h->H1 = nullptr;
+    cudaFree(h->H2);
+    cudaFree(h->H3);
+    h->H0 = h->H1 = h->H2 = h->H3 = nullptr;
     h->N = h->D = h->ld = 0;
     h->solved = false;
     cudaFree(h->Zov);
@@ -299,6 +303,9 @@ cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const 
     cudaStream_t s = h->cx.stream;
     const int ld = (N + 31) / 32 * 32;
     const size_t blk = (size_t)N * ld;
+    cudaFree(h->H2);   // higher perturbation terms belong to the previous H1
+    cudaFree(h->H3);
+    h->H2 = h->H3 = nullptr;
     if (N != h->N || D != h->D || ld != h->ld) {
         cudaFree(h->H0);
         cudaFree(h->H1);
@@ -342,6 +349,38 @@ cdmpt_status cdmpt_set_H(cdmpt_handle* h, int N, const double* H0, int D, const 
     h->gmax = host[1];
     h->trH0 = host[2];
     h->solved = false;
+    return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_set_H_orders(cdmpt_handle* h, const double* H2, const double* H3,
+                                int on_device) {
+    if (!h) return CDMPT_ERR_ARG;
+    if (h->N < 1 || h->D < 1)
+        return fail_msg(h, CDMPT_ERR_ARG, "set_H_orders: call cdmpt_set_H with directions first");
+    cudaStream_t s = h->cx.stream;
+    const int N = h->N, D = h->D, ld = h->ld;
+    const size_t blk = (size_t)N * ld;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* src[2] = {H2, H3};
+    double** dst[2] = {&h->H2, &h->H3};
+    for (int t = 0; t < 2; ++t) {
+        cudaFree(*dst[t]);
+        *dst[t] = nullptr;
+        if (!src[t]) continue;
+        if (cudaMalloc((void**)dst[t], D * blk * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_msg(h, CDMPT_ERR_OOM, "set_H_orders: device allocation failed");
+        }
+        CDMPT_CUDA_TRY(cudaMemsetAsync(*dst[t], 0, D * blk * sizeof(double), s));
+        CDMPT_CUDA_TRY(cudaMemcpy2DAsync(*dst[t], ld * sizeof(double), src[t], N * sizeof(double),
+                                         N * sizeof(double), (size_t)D * N, kind, s));
+        for (int d = 0; d < D && h->ovN; ++d) {   // non-orthogonal input: Z H Z
+            const cdmpt_status st = congruence(h->Zov, ld, N, *dst[t] + d * blk, ld,
+                                               *dst[t] + d * blk, ld, h->ovtmp, s);
+            if (st != CDMPT_OK) return fail(h, st);
+        }
+    }
+    CDMPT_CUDA_TRY(cudaStreamSynchronize(s));
     return CDMPT_OK;
 }
 
@@ -783,16 +822,20 @@ static cdmpt_status respond(cdmpt_handle* h, int m, const double* w, double* Pm,
         if (!h->sd)
             st = CDMPT_ERR_ARG;
         else if (m == 2)
-            st = h->sd->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g);
+            st = h->sd->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g,
+                                  h->H2, h->H3);
         else
-            st = h->sd->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr);
+            st = h->sd->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr,
+                                  h->H2, h->H3);
     } else {
         if (!h->sf)
             st = CDMPT_ERR_ARG;
         else if (m == 2)
-            st = h->sf->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g);
+            st = h->sf->response2(h->cx, h->H1, D, w, pm, mus.data(), omega ? om.data() : nullptr, g,
+                                  h->H2, h->H3);
         else
-            st = h->sf->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr);
+            st = h->sf->response3(h->cx, h->H1, D, pm, mus.data(), omega ? om.data() : nullptr,
+                                  h->H2, h->H3);
     }
     h->st = keep;
     if (st == CDMPT_OK && ov) {   // D^(m) = Z P^(m) Z; d alpha / dF = Z (d alpha / dF_perp) Z
@@ -851,6 +894,8 @@ void cdmpt_destroy(cdmpt_handle* h) {
     for (cudaEvent_t e : h->cx.ev) cudaEventDestroy(e);
     cudaFree(h->H0);
     cudaFree(h->H1);
+    cudaFree(h->H2);
+    cudaFree(h->H3);
     cudaFree(h->dscal);
     cudaFree(h->Zov);
     cudaFree(h->Sov);

@@ -50,7 +50,7 @@ enum Slot {
     S_TRQ = 10,     // Tr Q
     S_TRZ1 = 16,    // Tr Z1_d (d < 16)
     S_ALPHA = 32,   // sum P1_d * H1_d (d < 16)
-    S_FE = 48,      // free energy: traces and dots (3 slots)
+    S_FE = 48,      // free energy and Omega terms: traces and dots (5 slots)
     S_NSLOTS = 64
 };
 constexpr int kMaxD = 16;
@@ -799,7 +799,8 @@ cdmpt_status Solver<T>::reserve_orders() {
 // the same step matrix. Start: Z^(1)_0 = -s2 (H1 - mu1 I), Z^(q)_0 = s2 mu^(q) I
 // for q >= 2. Only the current and next iterate of each order are kept.
 template <typename T>
-cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const double* mus) {
+cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, const double* H2d,
+                               const double* H3d, int m, const double* mus) {
     const int n = last_n_, N = N_;
     const int acc = last_acc_;
     const cdmpt_opts& o = last_opts_;
@@ -811,6 +812,12 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const doub
                             cur(1).hi, cur(1).lo));
     for (int q = 2; q <= m; ++q) {
         Buf<T>& b = cur(q);
+        const double* Hq = q == 2 ? H2d : H3d;
+        if (Hq) {   // Z^(q)_0 = -s2 (H^(q) - mu^(q) I)
+            CDMPT_TRY(Ew<T>::init_z(b.x, Hq, N, ld, ld, 1, -last_s2_, mu_of(q), cx.stream, b.hi,
+                                    b.lo));
+            continue;
+        }
         CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, blk_ * sizeof(T), cx.stream));
         if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, blk_ * sizeof(T), cx.stream));
         if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, blk_ * sizeof(T), cx.stream));
@@ -900,7 +907,13 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, int m, const doub
 // Resp_0 with H^(1) = H1 only).
 template <typename T>
 cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, const double* w,
-                               double* Pm, double* mu_out, double* omega, double* grad) {
+                               double* Pm, double* mu_out, double* omega, double* grad,
+                               const double* H2, const double* H3) {
+    if (grad && (H2 || H3)) {
+        set_error("the polarizability gradient is d alpha / d H0 for H^(2) = H^(3) = 0: clear "
+                  "the higher perturbation terms first");
+        return CDMPT_ERR_ARG;
+    }
     if (fdx_) {
         set_error("response orders other than the solve's are not available with the "
                   "Fermi-Dirac-exact start (fd_exact)");
@@ -926,9 +939,11 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
     if (grad) CDMPT_CUDA_TRY(cudaMemsetAsync(G_.x, 0, blk_ * sizeof(T), cx.stream));
     for (int d = 0; d < D; ++d) {
         const double* H1d = H1 + (size_t)d * blk_;
+        const double* H2d = H2 ? H2 + (size_t)d * blk_ : nullptr;
+        const double* H3d = H3 ? H3 + (size_t)d * blk_ : nullptr;
         double mus[2] = {m > 1 ? last_mu1_[d] : 0.0, 0.0};
         for (int q = std::min(m, 2); q <= m; ++q) {
-            CDMPT_TRY(orders(cx, H1d, q, mus));
+            CDMPT_TRY(orders(cx, H1d, H2d, H3d, q, mus));
             Buf<T>& Zq = zo_[q - 1][cur_[q - 1]];
             CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 1, 0, sizeof(double), cx.stream));
             CDMPT_TRY(Ew<T>::trace(Zq.x, N, ld, 1, sc_ + S_TRQ + 1, cx.stream));
@@ -941,11 +956,38 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
             if (mu_out) mu_out[d] = muq;
             // Z^(m) += 2 mu^(m) Q  (P^(m) = Z^(m) / 2)
             if (!gc) CDMPT_TRY(Ew<T>::axpby(Zq.x, Qmu_.x, blk_, 2.0 * muq, 1.0, nullptr, cx.stream));
-            if (omega) {   // Omega^(m+1) = 1/(m+1) Tr[H1 P^(m)] = <Z^(m), H1> / (2 (m+1))
-                CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRQ + 2, 0, sizeof(double), cx.stream));
-                CDMPT_TRY(Ew<T>::dot_h(Zq.x, H1d, N, ld, ld, sc_ + S_TRQ + 2, cx.stream));
+            if (omega) {
+                // Eq. Resp_0: Omega^(m+1) = 1/(m+1) sum_k k Tr[H^(k) P^(m+1-k)], with
+                // P^(q) = Z^(q)_n / 2 (q >= 1, canonical shifts included) and P0 = (I + Z_n)/2
+                CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, 5 * sizeof(double), cx.stream));
+                CDMPT_TRY(Ew<T>::dot_h(Zq.x, H1d, N, ld, ld, sc_ + S_FE, cx.stream));
+                if (m == 1 && H2d) {
+                    CDMPT_TRY(Ew<T>::dot_h(Z_[last_n_].x, H2d, N, ld, ld, sc_ + S_FE + 1, cx.stream));
+                    CDMPT_TRY(Ew<double>::trace(H2d, N, ld, 1, sc_ + S_FE + 2, cx.stream));
+                }
+                if (m >= 2 && H2d)
+                    CDMPT_TRY(Ew<T>::dot_h(zo_[m - 2][cur_[m - 2]].x, H2d, N, ld, ld,
+                                           sc_ + S_FE + 1, cx.stream));
+                const double* H3k = m == 2 ? H3d : nullptr;   // Tr[H3 P0] enters Omega^(3)
+                if (H3k) {
+                    CDMPT_TRY(Ew<T>::dot_h(Z_[last_n_].x, H3k, N, ld, ld, sc_ + S_FE + 3,
+                                           cx.stream));
+                    CDMPT_TRY(Ew<double>::trace(H3k, N, ld, 1, sc_ + S_FE + 4, cx.stream));
+                }
+                if (m == 3 && H3d)   // 3 Tr[H3 P1] enters Omega^(4)
+                    CDMPT_TRY(Ew<T>::dot_h(zo_[0][cur_[0]].x, H3d, N, ld, ld, sc_ + S_FE + 3,
+                                           cx.stream));
                 CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
-                omega[d] = cx.pinned[S_TRQ + 2] / (2.0 * (m + 1));
+                const double* v = cx.pinned + S_FE;
+                double sum = 0.5 * v[0];                 // Tr[H1 P^(m)]
+                if (m == 1) {
+                    sum += 2.0 * 0.5 * (v[2] + v[1]);   // 2 Tr[H2 P0]
+                } else {
+                    sum += 2.0 * 0.5 * v[1];            // 2 Tr[H2 P^(m-1)]
+                    if (m == 2) sum += 3.0 * 0.5 * (v[4] + v[3]);   // 3 Tr[H3 P0]
+                    else sum += 3.0 * 0.5 * v[3];                   // 3 Tr[H3 P1]
+                }
+                omega[d] = sum / (m + 1);
             }
             if (Pm)
                 CDMPT_TRY(Ew<T>::to_f64(Pm + (size_t)d * N * N, N, Zq.x, ld, N, N, 0.5, 0.0,
@@ -969,8 +1011,9 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
 // in H0 is P0): d alpha_d / d H0 = -2 d^2 P / d lambda_d^2 = -4 P2_d.
 template <typename T>
 cdmpt_status Solver<T>::response2(Context& cx, const double* H1, int D, const double* w,
-                                  double* P2, double* mu2_out, double* omega3, double* grad) {
-    return higher(cx, H1, D, 2, w, P2, mu2_out, omega3, grad);
+                                  double* P2, double* mu2_out, double* omega3, double* grad,
+                                  const double* H2, const double* H3) {
+    return higher(cx, H1, D, 2, w, P2, mu2_out, omega3, grad, H2, H3);
 }
 
 template <typename T>
@@ -981,8 +1024,9 @@ cdmpt_status Solver<T>::response1(Context& cx, const double* H1, int D, double* 
 
 template <typename T>
 cdmpt_status Solver<T>::response3(Context& cx, const double* H1, int D, double* P3,
-                                  double* mu3_out, double* omega4) {
-    return higher(cx, H1, D, 3, nullptr, P3, mu3_out, omega4, nullptr);
+                                  double* mu3_out, double* omega4, const double* H2,
+                                  const double* H3) {
+    return higher(cx, H1, D, 3, nullptr, P3, mu3_out, omega4, nullptr, H2, H3);
 }
 
 template <typename T>

@@ -69,8 +69,13 @@ public:
     // P2 (D x N x N) and grad (N x N) are FP64 device arrays with leading
     // dimension N, or null; mu2 is a host array of D doubles, or null.
     // omega3 (host, D doubles, or null): Omega^(3)_d = 1/3 Tr[H1_d P2_d] (Eq. Resp_0).
+    // H2, H3 (device, D x N x ld FP64, or null): higher terms of the perturbation,
+    // H(lambda) = H0 + lambda H1 + lambda^2 H2 + lambda^3 H3 (Eq. H_prt); Omega^(3) is then
+    // (1/3)(Tr[H1 P2] + 2 Tr[H2 P1] + 3 Tr[H3 P0]), and grad (which is d alpha / d H0 for
+    // H2 = 0) is refused.
     cdmpt_status response2(Context& cx, const double* H1, int D, const double* w, double* P2,
-                           double* mu2, double* omega3, double* grad);
+                           double* mu2, double* omega3, double* grad,
+                           const double* H2 = nullptr, const double* H3 = nullptr);
 
     // First-order canonical response of the last solve to other perturbations H1 (device,
     // D x N x ld FP64), on the stored trajectory: P1 (D x N x N FP64 device, leading
@@ -84,7 +89,8 @@ public:
     // 1/4 Tr[H1_d P3_d] (Eq. Resp_0). P3: D x N x N FP64 device array (leading
     // dimension N) or null; mu3, omega4: host arrays of D doubles, or null.
     cdmpt_status response3(Context& cx, const double* H1, int D, double* P3, double* mu3,
-                           double* omega4);
+                           double* omega4, const double* H2 = nullptr,
+                           const double* H3 = nullptr);
 
     // Free energy of the last solve, Omega = Tr[P0 H0] - T_e S[P0] (Eqs. FreeE,
     // SED; k_B = 1, T_e = 1/beta) for the recursion's own P0, evaluated without
@@ -141,7 +147,8 @@ private:
     // Joint forward sweep of the orders 1..m (m <= 3) for one direction H1d, with
     // mu^(1..m-1) = mus[0..m-2] known and mu^(m) = 0. Leaves Z^(o)_n in
     // zo_[o-1][cur_[o-1]].
-    cdmpt_status orders(Context& cx, const double* H1d, int m, const double* mus);
+    cdmpt_status orders(Context& cx, const double* H1d, const double* H2d, const double* H3d,
+                        int m, const double* mus);
     cdmpt_status reserve_orders();
     // Tr ln(a I + b M) for symmetric M whose spectrum puts a I + b M inside
     // [lo, hi] (0 < lo <= hi), by the Cayley transform Y = (A - cI)(A + cI)^-1,
@@ -152,7 +159,8 @@ private:
     // Canonical response of order m (2 or 3) for every direction: P^(m), mu^(m),
     // Omega^(m+1), and for m = 2 the weighted polarizability gradient.
     cdmpt_status higher(Context& cx, const double* H1, int D, int m, const double* w,
-                        double* Pm, double* mu_out, double* omega, double* grad);
+                        double* Pm, double* mu_out, double* omega, double* grad,
+                        const double* H2 = nullptr, const double* H3 = nullptr);
     cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
                         double* max_rel_res);
     cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);
