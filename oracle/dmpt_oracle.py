@@ -826,7 +826,7 @@ def scc_charges(D, S, q0):
 
 
 def scc_solve(hcore, h1, S, gamma, q0, beta, nocc, n: Optional[int] = None, kind: str = "rec",
-              tol: float = 1e-13, maxit: int = 2000, mix: float = 0.3):
+              tol: float = 1e-13, maxit: int = 2000, mix: float = 0.3, order: int = 1):
     """Self-consistent canonical solve and its coupled-perturbed response.
 
     SCF: plain fixed-point iteration on the charges with linear mixing, each step the
@@ -837,6 +837,10 @@ def scc_solve(hcore, h1, S, gamma, q0, beta, nocc, n: Optional[int] = None, kind
     D1 = R(h1 + G(dq1)). Omega_SCF^(m) = (2/m) Tr[h1 D^(m-1)] (Eq. Resp_Omega).
     The free energy Omega_SCF = 2 Tr[h D] + 1/2 dq^T gamma dq - 2 T_e S[D_perp] (Eq.
     FreeE_tot for this model) is returned as omega.
+    order=2 adds the second-order self-consistent response D2 = (1/2) d^2 D / d lambda^2:
+    the canonical order-2 response to F^(1) = h1 + G(D1) and F^(2) = G(D2), a linear fixed
+    point in its charges, (I - K) dq2 = b2 with the same K, and Omega_SCF^(3) =
+    (2/3) Tr[h1 D2] (Eq. Resp_Omega).
     """
     h1 = np.asarray(h1, dtype=np.float64)
     if h1.ndim == 2:
@@ -874,15 +878,34 @@ def scc_solve(hcore, h1, S, gamma, q0, beta, nocc, n: Optional[int] = None, kind
         K[:, j] = scc_charges(response(scc_fock(np.zeros((N, N)), S, gamma, e))[0], S,
                               np.zeros(N))
     D1 = np.empty_like(h1)
+    D2 = np.empty_like(h1)
     mu1 = np.zeros(h1.shape[0])
+    mu2 = np.zeros(h1.shape[0])
     for d in range(h1.shape[0]):
         b = scc_charges(response(h1[d])[0], S, np.zeros(N))
         dq1 = np.linalg.solve(np.eye(N) - K, b)
-        D1[d], mu1[d] = response(scc_fock(h1[d], S, gamma, dq1))
+        F1 = scc_fock(h1[d], S, gamma, dq1)
+        D1[d], mu1[d] = response(F1)
+        if order >= 2:
+            # second order: sum_k f[e_i, e_k, e_j] g_ik g_kj of g = F1 in the eigenbasis (mu1
+            # shift included), then the first-order response to F2 = G(dq2)
+            g = V.T @ to_orthogonal(F1, Linv) @ V - mu1[d] * np.eye(N)
+            S2 = _dk2_matrix(g, eps, Fdd, mu, beta, nn, 1.0, 1.0, 1024)
+            m2 = float(np.trace(S2) / np.sum(fp))
+            D2a = from_orthogonal(V @ (S2 - m2 * np.diag(fp)) @ V.T, Linv)
+            dq2 = np.linalg.solve(np.eye(N) - K, scc_charges(D2a, S, np.zeros(N)))
+            D2b, m2b = response(scc_fock(np.zeros((N, N)), S, gamma, dq2))
+            D2[d] = D2a + D2b
+            mu2[d] = m2 + m2b
     ent = -np.sum(np.where(occ > 0, occ * np.log(np.where(occ > 0, occ, 1.0)), 0.0)
                   + np.where(occ < 1, (1 - occ) * np.log1p(-np.where(occ < 1, occ, 0.0)), 0.0))
     omega = 2.0 * np.sum(hcore * D) + 0.5 * x @ gamma @ x - 2.0 * ent / beta
-    return dict(D0=D, D1=D1, mu=float(mu), mu1=mu1, dq=y, iters=it + 1,
-                omega1=np.array([2.0 * np.sum(h1[d] * D) for d in range(h1.shape[0])]),
-                omega2=np.array([np.sum(h1[d] * D1[d]) for d in range(h1.shape[0])]),
-                omega=float(omega))
+    out = dict(D0=D, D1=D1, mu=float(mu), mu1=mu1, dq=y, iters=it + 1,
+               omega1=np.array([2.0 * np.sum(h1[d] * D) for d in range(h1.shape[0])]),
+               omega2=np.array([np.sum(h1[d] * D1[d]) for d in range(h1.shape[0])]),
+               omega=float(omega))
+    if order >= 2:
+        out.update(D2=D2, mu2=mu2,
+                   omega3=np.array([2.0 / 3.0 * np.sum(h1[d] * D2[d])
+                                    for d in range(h1.shape[0])]))
+    return out

@@ -871,3 +871,27 @@ def test_n_plus_one_rule_with_higher_perturbation_terms():
         6 * h ** 4)
     assert abs(d3 / 6.0 - r["omega3"][0]) < 1e-5 * abs(r["omega3"][0])
     assert abs(d4 / 24.0 - r["omega4"][0]) < 1e-3 * abs(r["omega4"][0])
+
+
+@pytest.mark.parametrize("kind,n", [("fd", None), ("rec", 10)])
+def test_scc_D2_equals_finite_difference_of_self_consistent_D(kind, n):
+    """D2 = (1/2) d^2 D / d lambda^2 of the self-consistent solution of h + lambda h1."""
+    hc, h1, S, gamma, q0, beta, nocc, _ = _scc_case()
+    h = 1e-3
+    r = o.scc_solve(hc, h1, S, gamma, q0, beta, nocc, n=n, kind=kind, order=2)
+    D = {k: o.scc_solve(hc + k * h * h1, h1, S, gamma, q0, beta, nocc, n=n, kind=kind)["D0"]
+         for k in (-2, -1, 0, 1, 2)}
+    fd = (-D[-2] + 16 * D[-1] - 30 * D[0] + 16 * D[1] - D[2]) / (12 * h * h)
+    assert o.rel_frobenius(r["D2"][0], 0.5 * fd) < 1e-6
+
+
+def test_scc_free_energy_third_order_rule():
+    """Eq. Resp_Omega at m = 3: Omega_SCF^(3) = (2/3) Tr[h1 D2] = (1/6) d^3 Omega_SCF /
+    dlambda^3 at self-consistency (Fermi-Dirac), six-point differences of the free energy."""
+    hc, h1, S, gamma, q0, beta, nocc, _ = _scc_case()
+    h = 1e-2
+    r = o.scc_solve(hc, h1, S, gamma, q0, beta, nocc, kind="fd", order=2)
+    w = {k: o.scc_solve(hc + k * h * h1, h1, S, gamma, q0, beta, nocc, kind="fd")["omega"]
+         for k in (-3, -2, -1, 1, 2, 3)}
+    d3 = (-w[3] + 8 * w[2] - 13 * w[1] + 13 * w[-1] - 8 * w[-2] + w[-3]) / (8 * h ** 3)
+    assert abs(d3 / 6.0 - r["omega3"][0]) < 1e-4 * abs(r["omega3"][0])
