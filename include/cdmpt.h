@@ -225,6 +225,19 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* model, int 
                              double nocc, int n, double* D0, double* D1, double* mu, double* mu1,
                              double* omega1, double* omega2, int* iters, int on_device);
 
+/* cdmpt_scc_solve plus the second-order self-consistent response (the hyperpolarizability
+ * of Sec. IV): per direction, D2 = (1/2) d^2 D / d lambda^2, the canonical order-2 response
+ * to F^(1) = h1 + G(D1) and F^(2) = G(D2) on the converged trajectory (one joint order-1-2
+ * sweep per step of a second charge fixed point, iterated like the first), its shift mu2,
+ * and Omega_SCF^(3) = (2/3) Tr[h1 D2] (Eq. Resp_Omega). D2: D x N x N in the caller's basis,
+ * host or device per on_device; mu2, omega3: host arrays of D doubles; any may be NULL
+ * (all NULL: no second order). iters[1] then counts both coupled-perturbed loops. */
+cdmpt_status cdmpt_scc_solve2(cdmpt_handle* h, const cdmpt_scc_model* model, int N,
+                              const double* hcore, int D, const double* h1, double beta,
+                              double nocc, int n, double* D0, double* D1, double* mu, double* mu1,
+                              double* omega1, double* omega2, double* D2, double* mu2,
+                              double* omega3, int* iters, int on_device);
+
 /* Higher terms of the perturbation, H(lambda) = H0 + lambda H1 + lambda^2 H2 +
  * lambda^3 H3 per direction (Eq. H_prt; Algorithm 1 starts order i from
  * X_0^(i) = -2^-(M+2) beta (H^(i) - mu^(i) I)). H2 and H3 are D x N x N FP64 (D and N

@@ -105,7 +105,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
            "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1",
-           "cdmpt_set_H_orders"]
+           "cdmpt_set_H_orders", "cdmpt_scc_solve2"]
 
 
 def lib() -> ctypes.CDLL:
@@ -143,6 +143,8 @@ def lib() -> ctypes.CDLL:
         "cdmpt_get_overlap_info": (I, [P, P, P]),
         "cdmpt_scc_solve": (I, [P, ctypes.POINTER(SccModel), I, P, I, P, D, D, I, P, P, P, P, P, P,
                                 P, I]),
+        "cdmpt_scc_solve2": (I, [P, ctypes.POINTER(SccModel), I, P, I, P, D, D, I, P, P, P, P, P,
+                                 P, P, P, P, P, I]),
         "cdmpt_batch_get_tuning": (I, [P, P, P, P]),
         "cdmpt_batch_create": (I, [ctypes.POINTER(Opts), I, P, I, ctypes.POINTER(P)]),
         "cdmpt_batch_set_H": (I, [P, P, P, I, I]),
@@ -504,10 +506,11 @@ class Handle:
         return {"omega": om.value, "grad": G}
 
     def scc_solve(self, hcore, h1, gamma, beta, nocc, n, q0=None, tol=0.0, maxit=0, history=0,
-                  mix=0.0):
+                  mix=0.0, order=1):
         """Self-consistent charge solve and coupled-perturbed response (cdmpt_scc_solve) in
         the basis of the last set_overlap. Host (numpy) inputs and outputs: dict(D0, D1, mu,
-        mu1, omega1, omega2, iters) with omega1 = 2 Tr[h1 D0], omega2 = Tr[h1 D1]."""
+        mu1, omega1, omega2, iters) with omega1 = 2 Tr[h1 D0], omega2 = Tr[h1 D1]; order=2
+        adds D2, mu2 and omega3 = (2/3) Tr[h1 D2] (cdmpt_scc_solve2)."""
         hc = np.ascontiguousarray(hcore, dtype=np.float64)
         N = hc.shape[0]
         H1 = np.ascontiguousarray(np.zeros((0, N, N)) if h1 is None else h1, dtype=np.float64)
@@ -522,14 +525,24 @@ class Handle:
         mu = ctypes.c_double(0.0)
         mu1, om1, om2 = np.zeros(max(D, 1)), np.zeros(max(D, 1)), np.zeros(max(D, 1))
         it = np.zeros(2, dtype=np.int32)
-        _check(lib().cdmpt_scc_solve(self.h, ctypes.byref(m), N, hc.ctypes.data, D,
-                                     H1.ctypes.data if D else None, beta, nocc, n,
-                                     D0.ctypes.data, D1.ctypes.data if D else None,
-                                     ctypes.addressof(mu), mu1.ctypes.data, om1.ctypes.data,
-                                     om2.ctypes.data, it.ctypes.data, 0), self.h)
+        D2 = np.empty((max(D, 1), N, N))
+        mu2, om3 = np.zeros(max(D, 1)), np.zeros(max(D, 1))
+        second = order >= 2 and D > 0
+        _check(lib().cdmpt_scc_solve2(self.h, ctypes.byref(m), N, hc.ctypes.data, D,
+                                      H1.ctypes.data if D else None, beta, nocc, n,
+                                      D0.ctypes.data, D1.ctypes.data if D else None,
+                                      ctypes.addressof(mu), mu1.ctypes.data, om1.ctypes.data,
+                                      om2.ctypes.data, D2.ctypes.data if second else None,
+                                      mu2.ctypes.data if second else None,
+                                      om3.ctypes.data if second else None, it.ctypes.data, 0),
+               self.h)
         self.N, self.D = N, 0
-        return {"D0": D0, "D1": D1[:D], "mu": mu.value, "mu1": mu1[:D].copy(),
-                "omega1": om1[:D].copy(), "omega2": om2[:D].copy(), "iters": tuple(int(v) for v in it)}
+        out = {"D0": D0, "D1": D1[:D], "mu": mu.value, "mu1": mu1[:D].copy(),
+               "omega1": om1[:D].copy(), "omega2": om2[:D].copy(),
+               "iters": tuple(int(v) for v in it)}
+        if second:
+            out.update(D2=D2[:D], mu2=mu2[:D].copy(), omega3=om3[:D].copy())
+        return out
 
     def stats(self):
         return get_stats(self.h)

@@ -555,10 +555,12 @@ cdmpt_status cdmpt_free_energy(cdmpt_handle* h, double* omega, double* gradH0, i
 }
 
 // Self-consistent charge layer (Sec. IV with a synthetic G(D)); see cdmpt_scc_solve in cdmpt.h.
-cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, const double* hcore,
-                             int D, const double* h1, double beta, double nocc, int n, double* D0,
-                             double* D1, double* mu, double* mu1, double* omega1, double* omega2,
-                             int* iters, int on_device) {
+cdmpt_status cdmpt_scc_solve2(cdmpt_handle* h, const cdmpt_scc_model* m, int N,
+                              const double* hcore, int D, const double* h1, double beta,
+                              double nocc, int n, double* D0, double* D1, double* mu, double* mu1,
+                              double* omega1, double* omega2, double* D2, double* mu2,
+                              double* omega3, int* iters, int on_device) {
+    const bool second = D2 || mu2 || omega3;
     if (!h) return CDMPT_ERR_ARG;
     if (!m || !m->gamma || !hcore || N < 1 || D < 0 || D > 16 || (D > 0 && !h1))
         return fail_msg(h, CDMPT_ERR_ARG,
@@ -575,9 +577,9 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
     const int depth = m->history > 0 ? m->history : 6;
     const double mix = m->mix > 0 ? m->mix : 0.3;
     // device work: hcore, gamma, F, D, D1 (orthogonal), D1 (caller's basis), h1, F1 (padded),
-    // q0, dq, V
+    // q0, dq, V; for the second order also F2 (padded) and a zero matrix
     double* w = nullptr;
-    const size_t elems = 6 * nn + (size_t)D * nn + blk + 3 * (size_t)N;
+    const size_t elems = 6 * nn + (size_t)D * nn + blk + 3 * (size_t)N + (second ? blk + nn : 0);
     if (cudaMalloc((void**)&w, elems * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return fail_msg(h, CDMPT_ERR_OOM, "scc_solve: device allocation failed");
@@ -585,6 +587,8 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
     double *hc = w, *gam = hc + nn, *F = gam + nn, *Dd = F + nn, *D1p = Dd + nn, *D1d = D1p + nn;
     double *h1d = D1d + nn, *F1 = h1d + (size_t)D * nn, *q0d = F1 + blk, *dq = q0d + N,
            *V = dq + N;
+    double* F2 = second ? V + N : nullptr;
+    double* zero = second ? F2 + blk : nullptr;
     const double* Sg = h->ovN ? h->Sov : nullptr;
     const cdmpt_opts saved = h->opts;
     cdmpt_status st = CDMPT_OK;
@@ -603,6 +607,10 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
     cuda_ok(cudaMemsetAsync(q0d, 0, N * sizeof(double), s), "zero q0");
     if (m->q0) cuda_ok(cudaMemcpyAsync(q0d, m->q0, N * sizeof(double), kin, s), "copy q0");
     cuda_ok(cudaMemsetAsync(F1, 0, blk * sizeof(double), s), "zero F1");
+    if (second) {
+        cuda_ok(cudaMemsetAsync(F2, 0, blk * sizeof(double), s), "zero F2");
+        cuda_ok(cudaMemsetAsync(zero, 0, nn * sizeof(double), s), "zero matrix");
+    }
     std::vector<double> x(N, 0.0), y(N), r(N);
     // ---- SCF on the charges: F = h + G(D(F)) (a fixed point in dq)
     bool conv = false;
@@ -643,7 +651,7 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
         st = CDMPT_ERR_NO_CONVERGENCE;
     }
     // ---- coupled-perturbed SCF per direction: D1 = R(h1 + G(D1)) (linear fixed point in dq1)
-    std::vector<double> om1(D, 0.0), om2(D, 0.0), m1(D, 0.0);
+    std::vector<double> om1(D, 0.0), om2(D, 0.0), m1(D, 0.0), om3(D, 0.0), m2v(D, 0.0);
     Solver<float>* sf = h->sf;
     Solver<double>* sd = h->sd;
     for (int d = 0; d < D && st == CDMPT_OK; ++d) {
@@ -709,6 +717,74 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
             const cudaMemcpyKind ko = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
             cuda_ok(cudaMemcpyAsync(D1 + d * nn, D1d, nn * sizeof(double), ko, s), "copy D1");
         }
+        // second order: D2 = R2(F^(1) = h1 + G(D1), F^(2) = G(D2)), a linear fixed point in the
+        // second-order charges; F1 still holds the converged F^(1) (mapped to the orthogonal
+        // basis), and D1p / D1d are free again
+        if (st == CDMPT_OK && second) {
+            cuda_ok(cudaStreamSynchronize(s), "synchronize");
+            std::vector<double> x2(N, 0.0), y2(N);
+            Anderson mixer2(N, depth, mix);
+            bool c2 = false;
+            for (int it = 0; st == CDMPT_OK && it < maxit; ++it, ++cp_it) {
+                cuda_ok(cudaMemcpyAsync(dq, x2.data(), N * sizeof(double), cudaMemcpyHostToDevice,
+                                        s), "second-order charges to device");
+                if (st == CDMPT_OK) st = scc_gemv(gam, N, dq, N, V, s);
+                if (st == CDMPT_OK) st = scc_fock(zero, N, Sg, ld, V, N, F2, ld, s);
+                if (st == CDMPT_OK && h->ovN)
+                    st = congruence(h->Zov, ld, N, F2, ld, F2, ld, h->ovtmp, s);
+                double m2d = 0.0;
+                cdmpt_stats keep = h->st;
+                h->cx.st = &h->st;
+                if (st == CDMPT_OK)
+                    st = h->opts.precision == CDMPT_FP64
+                             ? sd->response2_at(h->cx, F1, F2, 1, &m1[d], D1p, &m2d)
+                             : sf->response2_at(h->cx, F1, F2, 1, &m1[d], D1p, &m2d);
+                h->st = keep;
+                const double* D2c = D1p;
+                if (st == CDMPT_OK && h->ovN) {
+                    st = ov_map(h, D1p, D1d, 1, 1);
+                    D2c = D1d;
+                }
+                if (st == CDMPT_OK) st = scc_charges(D2c, N, Sg, ld, nullptr, N, dq, s);
+                cuda_ok(cudaMemcpyAsync(y2.data(), dq, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                        s), "second-order charges to host");
+                cuda_ok(cudaStreamSynchronize(s), "synchronize");
+                if (st != CDMPT_OK) break;
+                double res = 0.0;
+                for (int i = 0; i < N; ++i) {
+                    r[i] = y2[i] - x2[i];
+                    res = std::max(res, std::fabs(r[i]));
+                }
+                m2v[d] = m2d;
+                if (res < tol) {
+                    c2 = true;
+                    if (D2c != D1d)
+                        cuda_ok(cudaMemcpyAsync(D1d, D2c, nn * sizeof(double),
+                                                cudaMemcpyDeviceToDevice, s), "keep D2");
+                    break;
+                }
+                mixer2.next(x2, r);
+            }
+            if (st == CDMPT_OK && !c2) {
+                set_error("scc_solve: the second-order charges of direction " +
+                          std::to_string(d) + " did not converge");
+                st = CDMPT_ERR_NO_CONVERGENCE;
+            }
+            if (st == CDMPT_OK) {   // Omega_SCF^(3) = (2/3) Tr[h1 D2] (Eq. Resp_Omega)
+                cuda_ok(cudaMemsetAsync(h->dscal, 0, sizeof(double), s), "zero dot");
+                if (st == CDMPT_OK) st = scc_dot(h1d + d * nn, D1d, nn, h->dscal, s);
+                double dot3 = 0.0;
+                cuda_ok(cudaMemcpyAsync(&dot3, h->dscal, sizeof(double), cudaMemcpyDeviceToHost,
+                                        s), "dot to host");
+                cuda_ok(cudaStreamSynchronize(s), "synchronize");
+                om3[d] = 2.0 / 3.0 * dot3;
+            }
+            if (st == CDMPT_OK && D2) {
+                const cudaMemcpyKind ko =
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+                cuda_ok(cudaMemcpyAsync(D2 + d * nn, D1d, nn * sizeof(double), ko, s), "copy D2");
+            }
+        }
     }
     if (st == CDMPT_OK && D0) {
         const cudaMemcpyKind ko = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -726,8 +802,18 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
         if (mu1) mu1[d] = m1[d];
         if (omega1) omega1[d] = om1[d];
         if (omega2) omega2[d] = om2[d];
+        if (mu2) mu2[d] = m2v[d];
+        if (omega3) omega3[d] = om3[d];
     }
     return CDMPT_OK;
+}
+
+cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, const double* hcore,
+                             int D, const double* h1, double beta, double nocc, int n, double* D0,
+                             double* D1, double* mu, double* mu1, double* omega1, double* omega2,
+                             int* iters, int on_device) {
+    return cdmpt_scc_solve2(h, m, N, hcore, D, h1, beta, nocc, n, D0, D1, mu, mu1, omega1, omega2,
+                            nullptr, nullptr, nullptr, iters, on_device);
 }
 
 cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,

@@ -908,7 +908,7 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, const double* H2d
 template <typename T>
 cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, const double* w,
                                double* Pm, double* mu_out, double* omega, double* grad,
-                               const double* H2, const double* H3) {
+                               const double* H2, const double* H3, const double* mu1s) {
     if (grad && (H2 || H3)) {
         set_error("the polarizability gradient is d alpha / d H0 for H^(2) = H^(3) = 0: clear "
                   "the higher perturbation terms first");
@@ -919,7 +919,7 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
                   "Fermi-Dirac-exact start (fd_exact)");
         return CDMPT_ERR_ARG;
     }
-    if (!traj_valid_ || D < 1 || (m > 1 && (int)last_mu1_.size() < D)) {
+    if (!traj_valid_ || D < 1 || (m > 1 && !mu1s && (int)last_mu1_.size() < D)) {
         set_error("higher-order response: no completed solve with perturbations on this handle");
         return CDMPT_ERR_ARG;
     }
@@ -941,7 +941,7 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
         const double* H1d = H1 + (size_t)d * blk_;
         const double* H2d = H2 ? H2 + (size_t)d * blk_ : nullptr;
         const double* H3d = H3 ? H3 + (size_t)d * blk_ : nullptr;
-        double mus[2] = {m > 1 ? last_mu1_[d] : 0.0, 0.0};
+        double mus[2] = {m > 1 ? (mu1s ? mu1s[d] : last_mu1_[d]) : 0.0, 0.0};
         for (int q = std::min(m, 2); q <= m; ++q) {
             CDMPT_TRY(orders(cx, H1d, H2d, H3d, q, mus));
             Buf<T>& Zq = zo_[q - 1][cur_[q - 1]];
@@ -1020,6 +1020,12 @@ template <typename T>
 cdmpt_status Solver<T>::response1(Context& cx, const double* H1, int D, double* P1,
                                   double* mu1_out, double* omega2) {
     return higher(cx, H1, D, 1, nullptr, P1, mu1_out, omega2, nullptr);
+}
+
+template <typename T>
+cdmpt_status Solver<T>::response2_at(Context& cx, const double* H1, const double* H2, int D,
+                                     const double* mu1s, double* P2, double* mu2) {
+    return higher(cx, H1, D, 2, nullptr, P2, mu2, nullptr, nullptr, H2, nullptr, mu1s);
 }
 
 template <typename T>

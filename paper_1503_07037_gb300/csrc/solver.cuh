@@ -83,6 +83,13 @@ public:
     cdmpt_status response1(Context& cx, const double* H1, int D, double* P1, double* mu1,
                            double* omega2);
 
+    // Second-order canonical response of the last solve to a perturbation series with
+    // first-order term H1 (whose canonical mu1 per direction is given in mu1s, host) and
+    // second-order term H2 (both device, D x N x ld FP64): P2 (device, D x N x N, leading
+    // dimension N) and mu2 (host). Used by the self-consistent layer, whose H1 is h1 + G(D1).
+    cdmpt_status response2_at(Context& cx, const double* H1, const double* H2, int D,
+                              const double* mu1s, double* P2, double* mu2);
+
     // Third-order canonical response of the last solve (Algorithm 1, the order-3
     // line, H^(2) = H^(3) = 0): P3_d = 1/6 d^3 P / d lambda_d^3 with mu3_d from
     // Tr P3_d = 0 (mu2_d from an order-2 pass first), and Omega^(4)_d =
@@ -160,7 +167,8 @@ private:
     // Omega^(m+1), and for m = 2 the weighted polarizability gradient.
     cdmpt_status higher(Context& cx, const double* H1, int D, int m, const double* w,
                         double* Pm, double* mu_out, double* omega, double* grad,
-                        const double* H2 = nullptr, const double* H3 = nullptr);
+                        const double* H2 = nullptr, const double* H3 = nullptr,
+                        const double* mu1s = nullptr);
     cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
                         double* max_rel_res);
     cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);

@@ -25,15 +25,17 @@ pytestmark = pytest.mark.gpu
 def _case(N, seed):
     p = syn.nonorthogonal_cluster(N, seed=seed, beta=20.0, n=14)
     m = p.meta
-    ref = oracle.scc_solve(p.H0, p.H1, m["S"], m["gamma"], m["q0"], p.beta, p.nocc, n=p.n)
+    ref = oracle.scc_solve(p.H0, p.H1, m["S"], m["gamma"], m["q0"], p.beta, p.nocc, n=p.n,
+                           order=2)
     return p, ref
 
 
-def _run(pkg, p, precision, tol):
+def _run(pkg, p, precision, tol, order=1):
     m = p.meta
     with pkg.Handle(precision=precision) as h:
         h.set_overlap(m["S"])
-        return h.scc_solve(p.H0, p.H1, m["gamma"], p.beta, p.nocc, p.n, q0=m["q0"], tol=tol)
+        return h.scc_solve(p.H0, p.H1, m["gamma"], p.beta, p.nocc, p.n, q0=m["q0"], tol=tol,
+                           order=order)
 
 
 def test_scc_fp64_cluster(cuda, cdmpt_lib):
@@ -69,3 +71,14 @@ def test_scc_orthogonal_without_coupling_equals_plain_solve(cuda, cdmpt_lib):
     assert r["iters"][0] <= 4, r["iters"]
     assert oracle.rel_frobenius(r["D0"], base["P0"].cpu().numpy()) < 1e-13
     assert oracle.rel_frobenius(r["D1"][0], base["P1"][0].cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_scc_second_order(cuda, cdmpt_lib, precision, bar):
+    """The second-order self-consistent response D2 and Omega_SCF^(3) = (2/3) Tr[h1 D2]."""
+    p, ref = _case(120, 3001)
+    r = _run(cdmpt_lib, p, precision, 1e-12 if precision == "fp64" else 0.0, order=2)
+    for d in range(3):
+        assert oracle.rel_frobenius(r["D2"][d], ref["D2"][d]) < bar
+        assert abs(r["omega3"][d] - ref["omega3"][d]) < bar * abs(ref["omega3"][d])
+        assert abs(r["mu2"][d] - ref["mu2"][d]) < bar * max(1.0, abs(ref["mu2"][d]))
