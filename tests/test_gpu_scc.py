@@ -73,12 +73,16 @@ def test_scc_orthogonal_without_coupling_equals_plain_solve(cuda, cdmpt_lib):
     assert oracle.rel_frobenius(r["D1"][0], base["P1"][0].cpu().numpy()) < 1e-11
 
 
-@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("fp32", 1e-5)])
-def test_scc_second_order(cuda, cdmpt_lib, precision, bar):
-    """The second-order self-consistent response D2 and Omega_SCF^(3) = (2/3) Tr[h1 D2]."""
+@pytest.mark.parametrize("precision,bar,wbar", [("fp64", 1e-9, 1e-12), ("fp32", 1e-5, 1e-6)])
+def test_scc_second_order(cuda, cdmpt_lib, precision, bar, wbar):
+    """The second-order self-consistent response D2 and Omega_SCF^(3) = (2/3) Tr[h1 D2].
+    Omega_SCF^(3) is a trace that cancels: (2/3) ||h1||_F ||D2||_F is 27 to 4000 times
+    |Omega_SCF^(3)| for these directions, so its bar is normwise, wbar (2/3) ||h1|| ||D2||, at
+    the storage rounding of each precision (FP32: 1e-6, about 16 ulp)."""
     p, ref = _case(120, 3001)
     r = _run(cdmpt_lib, p, precision, 1e-12 if precision == "fp64" else 0.0, order=2)
     for d in range(3):
         assert oracle.rel_frobenius(r["D2"][d], ref["D2"][d]) < bar
-        assert abs(r["omega3"][d] - ref["omega3"][d]) < bar * abs(ref["omega3"][d])
+        norm = 2.0 / 3.0 * np.linalg.norm(p.H1[d]) * np.linalg.norm(ref["D2"][d])
+        assert abs(r["omega3"][d] - ref["omega3"][d]) < wbar * norm
         assert abs(r["mu2"][d] - ref["mu2"][d]) < bar * max(1.0, abs(ref["mu2"][d]))
