@@ -106,9 +106,12 @@ typedef struct {
                            Fermi-Dirac function, Eq. Rec_F_1) rather than the n-step
                            approximation, and dP0/dmu = beta P0 (I - P0) holds exactly. tanh
                            is its odd Taylor series (converges since |Y| < 1 < pi/2), a few
-                           products on the Gershgorin interval. Solve, first-order response,
-                           mu1 and alpha only: the adjoint, cdmpt_response2/3,
-                           cdmpt_free_energy and cdmpt_scc_solve return ERR_ARG. */
+                           products on the Gershgorin interval. Every derivative follows the
+                           start: the response orders through the Taylor coefficients of tanh
+                           along H(lambda), the adjoint through its (self-adjoint) tangent,
+                           and cdmpt_free_energy gives the Fermi-Dirac Mermin free energy,
+                           whose canonical gradient is P0. cdmpt_batch_create refuses it
+                           (ERR_UNSUPPORTED). */
 } cdmpt_opts;
 
 typedef struct {
@@ -288,7 +291,7 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
  * matrices T_k, Sec. II). P1_d (D x N x N, may be NULL) with mu1_d from Tr P1_d = 0,
  * and Omega^(2)_d = 1/2 Tr[H1_d P1_d] (Eq. Resp_0; alpha_d = -4 Omega^(2)_d), host
  * arrays of D doubles (may be NULL). In the non-orthogonal mode H1 is h1 and P1 is
- * D1. Not available with fd_exact (ERR_ARG).
+ * D1.
  * Errors: ERR_ARG (no solve yet, D outside 1..16, H1 NULL), ERR_CG_MAXITER,
  * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
 cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,
@@ -401,8 +404,8 @@ void cdmpt_destroy(cdmpt_handle* h);
 typedef struct cdmpt_batch cdmpt_batch;
 
 /* Create a batch of B systems of sizes N[0..B-1] with D directions each.
- * Errors: ERR_ARG, ERR_UNSUPPORTED (precision other than FP32, or no sm_103
- * device), ERR_OOM. */
+ * Errors: ERR_ARG, ERR_UNSUPPORTED (precision other than FP32 or MIXED_TF32,
+ * fd_exact or grand_canonical set, or no sm_103 device), ERR_OOM. */
 cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int D,
                                 cdmpt_batch** out);
 

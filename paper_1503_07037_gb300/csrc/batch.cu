@@ -867,6 +867,12 @@ cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int
         set_error("batch: CDMPT_FP32 (split-TF32 products) or CDMPT_MIXED_TF32 only");
         return CDMPT_ERR_UNSUPPORTED;
     }
+    if (b->opts.fd_exact || b->opts.grand_canonical) {
+        delete b;
+        set_error("batch: canonical solves from the linear start of Eq. Rec_F_2 only "
+                  "(no fd_exact, no grand_canonical)");
+        return CDMPT_ERR_UNSUPPORTED;
+    }
     if (!tc_supported()) {
         delete b;
         set_error("batch: needs an sm_103 GPU (tcgen05)");

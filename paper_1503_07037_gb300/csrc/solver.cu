@@ -362,11 +362,11 @@ cdmpt_status Solver<T>::init_z0(Context& cx, const double* H0, double mu, double
     }
     std::vector<double> a;
     const int K = tanh_terms(rho, fdx_eps(), &a);
-    // scratch outside the trajectory (the mixed refinement rebuilds Z_0 while the stored
-    // Z_1 .. Z_n are still needed)
+    // Y and U = Y^2 stay for the tangents of the start; Horner scratch outside the
+    // trajectory (the mixed refinement rebuilds Z_0 while the stored Z_1 .. Z_n are needed)
     CDMPT_TRY(reserve_orders());
-    Buf<T>& Y = zo_[0][0];
-    Buf<T>& U = zo_[0][1];
+    Buf<T>& Y = Yfd_;
+    Buf<T>& U = Ufd_;
     CDMPT_TRY(Ew<T>::init_z(Y.x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Y.hi, Y.lo));
     {
         Epilogue<T> ep;
@@ -397,13 +397,24 @@ cdmpt_status Solver<T>::init_z0(Context& cx, const double* H0, double mu, double
 }
 
 // First-order start of the Fermi-Dirac-exact variant: Z1_0 = Dtanh(Y)[Y1] for the stacked
-// directions Y1_d = -s2 H1_d (mu1 = 0; the mu1 term is added through Q afterwards), by the
-// tangent of the Horner scheme: with U1 = Y Y1 + Y1 Y, h1 <- U1 h + U h1 alongside h <- U h +
-// a_k I, and Z1_0 = Y1 h + Y h1. Left products with the symmetric N x N factors use the
-// transposed epilogue, (X_d F)^T = F X_d.
+// directions Y1_d = -s2 H1_d (mu1 = 0; the mu1 term is added through Q afterwards).
 template <typename T>
-cdmpt_status Solver<T>::init_z1(Context& cx, const double* H0, const double* H1, int D, T* out,
-                                T* out_hi, T* out_lo) {
+cdmpt_status Solver<T>::init_z1(Context& cx, const double* H1, int D, T* out, T* out_hi,
+                                T* out_lo) {
+    CDMPT_TRY(Ew<T>::init_z(Z1b_.x, H1, N_, ld, ld, D, -last_s2_, 0.0, cx.stream, Z1b_.hi,
+                            Z1b_.lo));
+    return tanh_tangent(cx, D, out, out_hi, out_lo);
+}
+
+// out_d = Dtanh(Y)[E_d] for the stacked symmetric directions E_d held in Z1b_ (with its TF32
+// split in FP32), Y = -s2 (H0 - mu I) at the trajectory's mu, by the tangent of the Horner
+// scheme of tanh(Y) = Y h(Y^2): with U1 = Y E + E Y, h1 <- U1 h + U h1 alongside h <- U h +
+// a_k I, and out = E h + Y h1. Left products with the symmetric N x N factors use the
+// transposed epilogue, (X_d F)^T = F X_d. The Frechet derivative of a polynomial of a
+// symmetric matrix is self-adjoint in the Frobenius product, so the same map also carries an
+// adjoint of Z_0 back to one of Y. Scratch: zo_[0..1], A1_, RHS_, P_, S_.
+template <typename T>
+cdmpt_status Solver<T>::tanh_tangent(Context& cx, int D, T* out, T* out_hi, T* out_lo) {
     const int N = N_;
     const int rows = D * N;
     const size_t count = (size_t)rows * ld;
@@ -411,29 +422,20 @@ cdmpt_status Solver<T>::init_z1(Context& cx, const double* H0, const double* H1,
     std::vector<double> a;
     const int K = tanh_terms(last_rho_, fdx_eps(), &a);
     CDMPT_TRY(reserve_orders());
-    Buf<T>& Y = zo_[0][0];
-    Buf<T>& U = zo_[0][1];
+    Buf<T>& Y = Yfd_;
+    Buf<T>& U = Ufd_;
     Buf<T>* hc = &zo_[1][0];
     Buf<T>* hn = &zo_[1][1];
     Buf<T>& Y1 = Z1b_;
     Buf<T>& U1 = A1_;
     Buf<T>* gc = &RHS_;
     Buf<T>* gn = &P_;
-    CDMPT_TRY(Ew<T>::init_z(Y.x, H0, N, ld, ld, 1, -last_s2_, last_mu_, cx.stream, Y.hi, Y.lo));
-    CDMPT_TRY(Ew<T>::init_z(Y1.x, H1, N, ld, ld, D, -last_s2_, 0.0, cx.stream, Y1.hi, Y1.lo));
     auto zero = [&](Buf<T>& b, size_t c) -> cdmpt_status {
         CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, c * sizeof(T), cx.stream));
         if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, c * sizeof(T), cx.stream));
         if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, c * sizeof(T), cx.stream));
         return CDMPT_OK;
     };
-    {
-        Epilogue<T> ep;   // U = Y Y
-        ep.Dhi = U.hi;
-        ep.Dlo = U.lo;
-        ep.sym = true;
-        CDMPT_TRY(gemm(cx, N, N, N, Y.op(), Y.op(), U.x, ep, nullptr, acc));
-    }
     {
         Epilogue<T> ep;   // S = Y1_d Y, then U1_d = S + S^T
         CDMPT_TRY(gemm(cx, rows, N, N, Y1.op(), Y.op(), S_.x, ep, nullptr, acc));
@@ -478,6 +480,92 @@ cdmpt_status Solver<T>::init_z1(Context& cx, const double* H0, const double* H1,
         CDMPT_TRY(gemm(cx, rows, N, N, gc->op(), Y.op(), out, e2, nullptr, acc));
     }
     return Ew<T>::symmetrize(out, N, ld, D, cx.stream, out_hi, out_lo);
+}
+
+// Higher-order starts of the Fermi-Dirac-exact variant. With Y(lambda) = sum_q lambda^q Y^(q)
+// (Y^(0) = Y, Y^(q) = -s2 (H^(q) - mu^(q) I)) the order-q Taylor coefficient of tanh Y(lambda) =
+// Y(lambda) h(U(lambda)), U(lambda) = Y(lambda)^2, follows from the Horner scheme run on
+// truncated power series in lambda: U^(q) = sum_{i+j=q} Y^(i) Y^(j),
+//   h^(q) <- sum_{i+j=q} U^(i) h^(j) (+ a_k I for q = 0),
+// and Z^(q)_0 = sum_{i+j=q} Y^(i) h^(j). Each coefficient of h is symmetric (h(lambda) is a
+// polynomial of the symmetric U(lambda)), so h^(j) serves as a transposed right factor. The
+// orders are updated from the top down, each into one spare buffer that then takes the old
+// coefficient's place. Scratch: ao_ (U^(1..m)), P_, A1_, RHS_, Z1a_, Z1b_ (h and the spare).
+template <typename T>
+cdmpt_status Solver<T>::tanh_taylor(Context& cx, int m) {
+    const int N = N_;
+    const int acc = last_acc_;
+    std::vector<double> a;
+    const int K = tanh_terms(last_rho_, fdx_eps(), &a);
+    Buf<T>* Yq[4] = {&Yfd_, &zo_[0][1], &zo_[1][1], &zo_[2][1]};
+    Buf<T>* Uq[4] = {&Ufd_, &ao_[0], &ao_[1], &ao_[2]};
+    Buf<T>* h[4] = {&P_, &A1_, &RHS_, &Z1a_};
+    Buf<T>* spare = &Z1b_;
+    for (int q = 1; q <= m; ++q) {   // U^(q) = S + S^T (+ Y^(q/2)^2), S = sum_{i<q-i} Y^(i) Y^(q-i)
+        for (int i = 0; i < q - i; ++i) {
+            Epilogue<T> ep;
+            if (i > 0) {
+                ep.beta = 1.0;
+                ep.C = S_.x;
+                ep.ldc = ld;
+            }
+            CDMPT_TRY(gemm(cx, N, N, N, Yq[i]->op(), Yq[q - i]->op(), S_.x, ep, nullptr, acc));
+        }
+        Buf<T>& U = *Uq[q];
+        const bool middle = q % 2 == 0;
+        CDMPT_TRY(Ew<T>::transpose_add(U.x, S_.x, N, ld, 1, cx.stream, middle ? nullptr : U.hi,
+                                       middle ? nullptr : U.lo));
+        if (middle) {
+            Epilogue<T> ep;
+            ep.beta = 1.0;
+            ep.C = U.x;
+            ep.ldc = ld;
+            ep.Dhi = U.hi;
+            ep.Dlo = U.lo;
+            CDMPT_TRY(gemm(cx, N, N, N, Yq[q / 2]->op(), Yq[q / 2]->op(), U.x, ep, nullptr, acc));
+        }
+    }
+    for (int q = 0; q <= m; ++q) {   // h = a_K I
+        Buf<T>& b = *h[q];
+        CDMPT_CUDA_TRY(cudaMemsetAsync(b.x, 0, blk_ * sizeof(T), cx.stream));
+        if (b.hi) CDMPT_CUDA_TRY(cudaMemsetAsync(b.hi, 0, blk_ * sizeof(T), cx.stream));
+        if (b.lo) CDMPT_CUDA_TRY(cudaMemsetAsync(b.lo, 0, blk_ * sizeof(T), cx.stream));
+        if (q == 0) CDMPT_TRY(Ew<T>::add_diag(b.x, N, ld, 1, a[K], cx.stream, b.hi, b.lo));
+    }
+    for (int k = K - 1; k >= 0; --k) {
+        for (int q = m; q >= 0; --q) {
+            for (int i = 0; i <= q; ++i) {
+                Epilogue<T> ep;
+                if (i > 0) {
+                    ep.beta = 1.0;
+                    ep.C = spare->x;
+                    ep.ldc = ld;
+                }
+                if (i == q) {   // the last term also rounds the split and adds a_k I (q = 0)
+                    ep.gamma = q == 0 ? a[k] : 0.0;
+                    ep.Dhi = spare->hi;
+                    ep.Dlo = spare->lo;
+                }
+                CDMPT_TRY(gemm(cx, N, N, N, Uq[i]->op(), h[q - i]->op(), spare->x, ep, nullptr,
+                               acc));
+            }
+            std::swap(h[q], spare);
+        }
+    }
+    for (int q = 1; q <= m; ++q) {   // Z^(q)_0 = sum_{i+j=q} Y^(i) h^(j)
+        Buf<T>& out = zo_[q - 1][0];
+        for (int i = 0; i <= q; ++i) {
+            Epilogue<T> ep;
+            if (i > 0) {
+                ep.beta = 1.0;
+                ep.C = out.x;
+                ep.ldc = ld;
+            }
+            CDMPT_TRY(gemm(cx, N, N, N, Yq[i]->op(), h[q - i]->op(), out.x, ep, nullptr, acc));
+        }
+        CDMPT_TRY(Ew<T>::symmetrize(out.x, N, ld, 1, cx.stream, out.hi, out.lo));
+    }
+    return CDMPT_OK;
 }
 
 // One step of the 0th-order recursion: W_k = Z_k Z_k and the correction d of
@@ -674,12 +762,11 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
 // Z_k V^T = gemm(Z_k, V), Z_{k+1} V Z_k = gemm(Z_{k+1}, Z_k V^T), B V = gemm(B, V^T).
 // Z_0 = -s2 (H0 - mu I) and the canonical dmu = Tr(Q dH0) / Tr Q give
 //   grad = -s2 Zh_0 + s2 Tr(Zh_0) Q / Tr Q.
+// With the Fermi-Dirac-exact start Z_0 = tanh(Y), Y = -s2 (H0 - mu I), the adjoint of Y is
+// Yh = Dtanh(Y)[Zh_0] (the derivative is self-adjoint), and the same formula holds with Yh
+// for Zh_0: Tr Yh = <Zh_0, Dtanh(Y)[I]> is the mu-sensitivity through the start.
 template <typename T>
 cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad, double p0_weight) {
-    if (fdx_) {
-        set_error("the adjoint is not available with the Fermi-Dirac-exact start (fd_exact)");
-        return CDMPT_ERR_ARG;
-    }
     if (!traj_valid_) {
         set_error("vjp: no completed solve on this handle");
         return CDMPT_ERR_ARG;
@@ -735,6 +822,13 @@ cdmpt_status Solver<T>::vjp_p0(Context& cx, const double* G0, double* grad, doub
         }
         CDMPT_TRY(Ew<T>::symmetrize(Zh_.x, N, ld, 1, cx.stream));
     }
+    if (fdx_) {   // Zh_0 -> Yh = Dtanh(Y)[Zh_0]
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(Z1b_.x, Zh_.x, blk_ * sizeof(T),
+                                       cudaMemcpyDeviceToDevice, cx.stream));
+        if constexpr (sizeof(T) == 4)
+            CDMPT_TRY(split_tf32(Z1b_.x, blk_, Z1b_.hi, Z1b_.lo, cx.stream));
+        CDMPT_TRY(tanh_tangent(cx, 1, Zh_.x, nullptr, nullptr));
+    }
     // canonical: mu follows H0 through Tr P0 = N_occ (the Q term); grand canonical: fixed mu
     const bool gc = o.grand_canonical != 0;
     if (!q_valid_ && !gc) CDMPT_TRY(compute_q(cx));
@@ -783,6 +877,8 @@ cdmpt_status Solver<T>::reserve_orders() {
         CDMPT_TRY(buf(&ao_[q]));
     }
     CDMPT_TRY(buf(&G_));
+    CDMPT_TRY(buf(&Yfd_));
+    CDMPT_TRY(buf(&Ufd_));
     orders_ready_ = true;
     return CDMPT_OK;
 }
@@ -797,7 +893,8 @@ cdmpt_status Solver<T>::reserve_orders() {
 // solved in correction form d (I + W_k) = -sum_j Z^(q-j)_{k+1} A^(j)_k -
 // 2 Z^(q)_k W_k, Z^(q)_{k+1} = sym(2 Z^(q)_k + d), lower orders first, all with
 // the same step matrix. Start: Z^(1)_0 = -s2 (H1 - mu1 I), Z^(q)_0 = s2 mu^(q) I
-// for q >= 2. Only the current and next iterate of each order are kept.
+// for q >= 2 (minus s2 H^(q) where given); with the Fermi-Dirac-exact start these are the
+// Y^(q) of tanh_taylor. Only the current and next iterate of each order are kept.
 template <typename T>
 cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, const double* H2d,
                                const double* H3d, int m, const double* mus) {
@@ -808,10 +905,13 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, const double* H2d
     auto nxt = [&](int q) -> Buf<T>& { return zo_[q - 1][1 - cur_[q - 1]]; };
     auto mu_of = [&](int q) { return q < m ? mus[q - 1] : 0.0; };
     for (int q = 1; q <= m; ++q) cur_[q - 1] = 0;
-    CDMPT_TRY(Ew<T>::init_z(cur(1).x, H1d, N, ld, ld, 1, -last_s2_, mu_of(1), cx.stream,
-                            cur(1).hi, cur(1).lo));
+    // the linear starts Y^(q) = -s2 (H^(q) - mu^(q) I); the Fermi-Dirac-exact start keeps them
+    // in the next-iterate buffers and maps them through the Taylor coefficients of tanh
+    auto start = [&](int q) -> Buf<T>& { return fdx_ ? nxt(q) : cur(q); };
+    CDMPT_TRY(Ew<T>::init_z(start(1).x, H1d, N, ld, ld, 1, -last_s2_, mu_of(1), cx.stream,
+                            start(1).hi, start(1).lo));
     for (int q = 2; q <= m; ++q) {
-        Buf<T>& b = cur(q);
+        Buf<T>& b = start(q);
         const double* Hq = q == 2 ? H2d : H3d;
         if (Hq) {   // Z^(q)_0 = -s2 (H^(q) - mu^(q) I)
             CDMPT_TRY(Ew<T>::init_z(b.x, Hq, N, ld, ld, 1, -last_s2_, mu_of(q), cx.stream, b.hi,
@@ -824,6 +924,7 @@ cdmpt_status Solver<T>::orders(Context& cx, const double* H1d, const double* H2d
         if (mu_of(q) != 0.0)
             CDMPT_TRY(Ew<T>::add_diag(b.x, N, ld, 1, last_s2_ * mu_of(q), cx.stream, b.hi, b.lo));
     }
+    if (fdx_) CDMPT_TRY(tanh_taylor(cx, m));
     int hint[3] = {1, 1, 1};
     for (int k = 0; k < n; ++k) {
         CDMPT_TRY(need(cx, k));
@@ -912,11 +1013,6 @@ cdmpt_status Solver<T>::higher(Context& cx, const double* H1, int D, int m, cons
     if (grad && (H2 || H3)) {
         set_error("the polarizability gradient is d alpha / d H0 for H^(2) = H^(3) = 0: clear "
                   "the higher perturbation terms first");
-        return CDMPT_ERR_ARG;
-    }
-    if (fdx_) {
-        set_error("response orders other than the solve's are not available with the "
-                  "Fermi-Dirac-exact start (fd_exact)");
         return CDMPT_ERR_ARG;
     }
     if (!traj_valid_ || D < 1 || (m > 1 && !mu1s && (int)last_mu1_.size() < D)) {
@@ -1111,19 +1207,20 @@ cdmpt_status Solver<T>::logdet(Context& cx, const Buf<T>& M, double a, double b,
 // H0 + T ln(P (I - P)^-1) = mu I + T 2^(n+1) R, so the gradient is P0 plus the
 // adjoint of the recursion applied to that matrix (vjp_p0 carries the
 // canonical or fixed-mu constraint of the solve).
+// With the Fermi-Dirac-exact start Z_0 = tanh(Y), atanh(Z_0) = Y = -(H0 - mu I) / (T 2^(n+1))
+// to the series cut, so R = 0: Omega = mu Tr P + T ln det(I - P), dOmega/dP = mu I, and the
+// canonical gradient is P0 itself (Tr dP0 = 0); at fixed mu it is P0 + vjp(mu I).
 template <typename T>
 cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
-    if (fdx_) {
-        set_error("the free energy is not available with the Fermi-Dirac-exact start (fd_exact)");
-        return CDMPT_ERR_ARG;
-    }
     if (!traj_valid_) {
         set_error("free energy: no completed solve on this handle");
         return CDMPT_ERR_ARG;
     }
     const int n = last_n_, N = N_;
     const int acc = last_acc_;
-    const double beta = last_beta_, mu = last_mu_, rho = std::min(last_rho_, 1.0 - 1e-12);
+    // |Z_0| <= rho: the bound on |Y| for the linear start, tanh of it for the exact one
+    const double rho = std::min(fdx_ ? std::tanh(last_rho_) : last_rho_, 1.0 - 1e-12);
+    const double beta = last_beta_, mu = last_mu_;
     const double Te = 1.0 / beta;
     const double eps = sizeof(T) == 8 ? 1e-17 : 1e-12;
     CDMPT_TRY(reserve_orders());
@@ -1141,6 +1238,26 @@ cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
         lda += std::ldexp(v, n - 1 - k);
     }
     const double logdet_1mp = std::ldexp(ld0, n) - lda - N * std::log(2.0);
+    if (fdx_) {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, sizeof(double), cx.stream));
+        CDMPT_TRY(Ew<T>::trace(Z_[n].x, N, ld, 1, sc_ + S_FE, cx.stream));
+        CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
+        if (omega) *omega = mu * 0.5 * (N + cx.pinned[S_FE]) + Te * logdet_1mp;
+        if (grad && last_opts_.grand_canonical == 0) {   // P0 = (I + Z_n) / 2
+            CDMPT_TRY(Ew<T>::to_f64(grad, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
+        } else if (grad) {
+            double* G0 = nullptr;
+            CDMPT_CUDA_TRY(cudaMallocAsync((void**)&G0, (size_t)N * N * sizeof(double),
+                                           cx.stream));
+            CDMPT_CUDA_TRY(cudaMemsetAsync(G0, 0, (size_t)N * N * sizeof(double), cx.stream));
+            CDMPT_TRY(Ew<double>::add_diag(G0, N, N, 1, mu, cx.stream));
+            const cdmpt_status s = vjp_p0(cx, G0, grad, 1.0);
+            cudaFreeAsync(G0, cx.stream);
+            CDMPT_TRY(s);
+        }
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
+        return check_device_error(cx.stream);
+    }
     // R = Z_0 W_0 h(W_0), h = sum_{j=0..J} W_0^j / (2j + 3), Horner from the top
     int J = 0;
     while (J < 200 && std::pow(rho, 2 * J + 2) > eps * (2 * J + 5) / 3.0) ++J;
@@ -1352,7 +1469,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         Buf<T>* Z1 = &Z1a_;
         Buf<T>* Z1n = &Z1b_;
         if (fdx_)
-            CDMPT_TRY(init_z1(cx, H0, H1, D, Z1->x, Z1->hi, Z1->lo));
+            CDMPT_TRY(init_z1(cx, H1, D, Z1->x, Z1->hi, Z1->lo));
         else
             CDMPT_TRY(Ew<T>::init_z(Z1->x, H1, N, ld, ld, D, -s2, 0.0, cx.stream, Z1->hi,
                                     Z1->lo));

@@ -145,8 +145,13 @@ private:
     // directions of H1 (into out, with its TF32 split).
     cdmpt_status init_z0(Context& cx, const double* H0, double mu, double s2, double rho,
                          int engine);
-    cdmpt_status init_z1(Context& cx, const double* H0, const double* H1, int D, T* out,
-                         T* out_hi, T* out_lo);
+    cdmpt_status init_z1(Context& cx, const double* H1, int D, T* out, T* out_hi, T* out_lo);
+    // out_d = Dtanh(Y)[E_d] for D stacked directions E_d held in Z1b_ (Fermi-Dirac-exact
+    // start; the map is self-adjoint, so it also serves the reverse sweep).
+    cdmpt_status tanh_tangent(Context& cx, int D, T* out, T* out_hi, T* out_lo);
+    // Taylor coefficients Z^(q)_0, q = 1..m (m <= 3), of tanh(Y + sum_q lambda^q Y^(q)) for
+    // the Fermi-Dirac-exact start, with the Y^(q) held in zo_[q-1][1]; written to zo_[q-1][0].
+    cdmpt_status tanh_taylor(Context& cx, int m);
     double fdx_eps() const;
     // Make Z_k, W_k and Z_{k+1} of step k valid (checkpointing: recompute the
     // segment of step k from its checkpoint unless the segment buffers hold it).
@@ -195,6 +200,8 @@ private:
     // (zo_[o-1][cur_[o-1]] is the current one), A^(o)_k = sum_{i+j=o} Z^(i)_k
     // Z^(j)_k, and the gradient accumulator
     Buf<T> zo_[3][2], ao_[3], G_;
+    // Fermi-Dirac-exact start: Y = -s2 (H0 - mu I) at the trajectory's mu and U = Y^2
+    Buf<T> Yfd_, Ufd_;
     int cur_[3] = {0, 0, 0};
     bool orders_ready_ = false;
     std::vector<double> last_mu1_;

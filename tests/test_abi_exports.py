@@ -66,3 +66,12 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+@pytest.mark.parametrize("flag", ["fd_exact", "grand_canonical"])
+def test_batch_refuses_options_it_does_not_implement(cdmpt_lib, flag):
+    """The batched path solves the canonical problem from the linear start only; the host-side
+    option check refuses the rest before any device call."""
+    with pytest.raises(cdmpt_lib.CdmptError) as e:
+        cdmpt_lib.Batch([8, 12], 1, **{flag: 1})
+    assert e.value.status == 8   # ERR_UNSUPPORTED

@@ -7,6 +7,10 @@ kind="fd" (eigenvalues of H0, the Fermi-Dirac function, Daleckii-Krein), the
 plain definition. Bars: 1e-10 (FP64); FP32 1e-5; mixed 1e-6 for P0 and max(1e-6,
 1.3 x the FP32 error) for P1 (the FP32 storage floor). The linear start misses
 the Fermi-Dirac reference by its truncation error, which the first test shows.
+The derivatives of the last solve (adjoint, free energy, orders 1 to 3 with the
+higher perturbation terms, and the self-consistent charge layer) go through the
+tangent and the Taylor coefficients of the tanh start; their references are the
+oracle's Fermi-Dirac free energy, Daleckii-Krein orders and SCC solve.
 """
 import numpy as np
 import pytest
@@ -74,14 +78,122 @@ def test_fd_exact_float_lattice_512(cuda, cdmpt_lib, precision):
     assert oracle.rel_frobenius(r["P1"][0], ref["P1"][0]) < b1
 
 
-def test_fd_exact_refuses_the_other_derivatives(cuda, cdmpt_lib):
+def _sym(N, seed, scale=1.0):
+    A = np.random.default_rng(seed).standard_normal((N, N)) * scale
+    return 0.5 * (A + A.T)
+
+
+def _gc_args(p, gc):
+    """Grand canonical: mu fixed 0.05 above the canonical one."""
+    if not gc:
+        return None, {}
+    mu = oracle.solve(p.H0, p.H1, p.beta, p.nocc, kind="fd")["mu"] + 0.05
+    return mu, dict(mu_guess=mu, grand_canonical=True)
+
+
+@pytest.mark.parametrize("gc", [False, True])
+def test_fd_exact_adjoint_fp64(cuda, cdmpt_lib, gc):
+    """d Tr[G P0] / d H0 through the reverse sweep and the tanh start equals the first-order
+    Fermi-Dirac response to G (the response operator is self-adjoint)."""
     import torch
     p = syn.workload("chain64")
+    G = _sym(p.N, 17)
+    mu, kw = _gc_args(p, gc)
+    ref = oracle.solve(p.H0, G, p.beta, p.nocc, kind="fd", canonical=not gc, mu=mu)["P1"][0]
+    with cdmpt_lib.Handle(precision="fp64", fd_exact=True, **kw) as h:
+        h.set_H(p.H0, p.H1)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        g = h.vjp_P0(torch.from_numpy(G).cuda()).cpu().numpy()
+    assert oracle.rel_frobenius(g, ref) < 1e-10
+
+
+@pytest.mark.parametrize("gc", [False, True])
+def test_fd_exact_free_energy_fp64(cuda, cdmpt_lib, gc):
+    """The Mermin free energy of the Fermi-Dirac P0 (R = atanh Z_0 - Y vanishes) and its
+    gradient: P0 itself (canonical) or P0 + mu dTr P0/dH0 (fixed mu)."""
+    p = syn.workload("chain64")
+    mu, kw = _gc_args(p, gc)
+    ref = oracle.free_energy(p.H0, p.beta, p.nocc, kind="fd", canonical=not gc, mu=mu)
+    with cdmpt_lib.Handle(precision="fp64", fd_exact=True, **kw) as h:
+        h.set_H(p.H0, None)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        r = h.free_energy()
+    assert abs(r["omega"] - ref["omega"]) < 1e-10 * abs(ref["omega"])
+    assert oracle.rel_frobenius(r["grad"].cpu().numpy(), ref["grad"]) < 1e-10
+
+
+@pytest.mark.parametrize("gc", [False, True])
+def test_fd_exact_orders_1_to_3_fp64(cuda, cdmpt_lib, gc):
+    """response1/2/3 from the Taylor coefficients of the tanh start against the Fermi-Dirac
+    Daleckii-Krein orders, with mu2, mu3, Omega^(3), Omega^(4) and d alpha / d H0."""
+    p = syn.workload("chain64")
+    mu, kw = _gc_args(p, gc)
+    ref = oracle.response3(p.H0, p.H1, p.beta, p.nocc, kind="fd", canonical=not gc, mu=mu)
+    with cdmpt_lib.Handle(precision="fp64", fd_exact=True, **kw) as h:
+        h.set_H(p.H0, p.H1)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        r1 = h.response1(p.H1)
+        r2 = h.response2()
+        r3 = h.response3()
+    assert oracle.rel_frobenius(r1["P1"][0].cpu().numpy(), ref["P1"][0]) < 1e-10
+    assert oracle.rel_frobenius(r2["P2"][0].cpu().numpy(), ref["P2"][0]) < 1e-10
+    assert oracle.rel_frobenius(r3["P3"][0].cpu().numpy(), ref["P3"][0]) < 1e-10
+    assert oracle.rel_frobenius(r2["grad"].cpu().numpy(), ref["grad_alpha"][0]) < 1e-10
+    assert abs(r2["mu2"][0] - ref["mu2"][0]) < 1e-10 * max(1.0, abs(ref["mu2"][0]))
+    assert abs(r3["mu3"][0] - ref["mu3"][0]) < 1e-10 * max(1.0, abs(ref["mu3"][0]))
+    assert abs(r2["omega3"][0] - ref["omega3"][0]) < 1e-10 * abs(ref["omega3"][0])
+    assert abs(r3["omega4"][0] - ref["omega4"][0]) < 1e-10 * abs(ref["omega4"][0])
+
+
+def test_fd_exact_higher_terms_fp64_lattice(cuda, cdmpt_lib):
+    """H(lambda) = H0 + lambda H1 + lambda^2 H2 + lambda^3 H3: the Y^(2), Y^(3) of the start."""
+    p = syn.cubic_lattice((5, 5, 5), seed=23, beta=8.0, n=12)
+    H2, H3 = _sym(p.N, 4, 0.05)[None], _sym(p.N, 5, 0.03)[None]
+    ref = oracle.response3(p.H0, p.H1, p.beta, p.nocc, kind="fd", close=0.2, quad=0.2, H2=H2,
+                           H3=H3)
     with cdmpt_lib.Handle(precision="fp64", fd_exact=True) as h:
         h.set_H(p.H0, p.H1)
-        h.solve(p.beta, p.nocc, p.n)
-        for call in (lambda: h.vjp_P0(torch.eye(p.N, dtype=torch.float64).cuda()),
-                     lambda: h.response2(), lambda: h.free_energy()):
-            with pytest.raises(cdmpt_lib.CdmptError) as e:
-                call()
-            assert e.value.status == 1
+        h.set_H_orders(H2, H3)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        r2 = h.response2(want_grad=False)
+        r3 = h.response3()
+    assert oracle.rel_frobenius(r2["P2"][0].cpu().numpy(), ref["P2"][0]) < 1e-10
+    assert oracle.rel_frobenius(r3["P3"][0].cpu().numpy(), ref["P3"][0]) < 1e-10
+    assert abs(r2["omega3"][0] - ref["omega3"][0]) < 1e-10 * abs(ref["omega3"][0])
+    assert abs(r3["omega4"][0] - ref["omega4"][0]) < 1e-10 * abs(ref["omega4"][0])
+
+
+def test_fd_exact_fp32_lattice_512_derivatives(cuda, cdmpt_lib):
+    import torch
+    p = syn.cubic_lattice((8, 8, 8), seed=1002, beta=20.0, n=14)
+    G = _sym(p.N, 29, 0.1)
+    ref1 = oracle.solve(p.H0, G, p.beta, p.nocc, kind="fd")
+    ref2 = oracle.response2(p.H0, p.H1, p.beta, p.nocc, kind="fd", close=0.2, quad=0.2)
+    reff = oracle.free_energy(p.H0, p.beta, p.nocc, kind="fd")
+    with cdmpt_lib.Handle(precision="fp32", fd_exact=True) as h:
+        h.set_H(p.H0, p.H1)
+        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        g = h.vjp_P0(torch.from_numpy(G).cuda()).cpu().numpy()
+        r2 = h.response2(want_grad=False)
+        fe = h.free_energy()
+    assert oracle.rel_frobenius(g, ref1["P1"][0]) < 1e-5
+    assert oracle.rel_frobenius(r2["P2"][0].cpu().numpy(), ref2["P2"][0]) < 1e-5
+    assert abs(fe["omega"] - reff["omega"]) < 1e-6 * abs(reff["omega"])
+    assert oracle.rel_frobenius(fe["grad"].cpu().numpy(), reff["grad"]) < 1e-5
+
+
+def test_fd_exact_scc_second_order_fp64(cuda, cdmpt_lib):
+    """The self-consistent charge layer on the Fermi-Dirac start, through its CPSCF orders."""
+    p = syn.nonorthogonal_cluster(120, seed=3001, beta=20.0, n=14)
+    m = p.meta
+    ref = oracle.scc_solve(p.H0, p.H1, m["S"], m["gamma"], m["q0"], p.beta, p.nocc,
+                           kind="fd", order=2)
+    with cdmpt_lib.Handle(precision="fp64", fd_exact=True) as h:
+        h.set_overlap(m["S"])
+        r = h.scc_solve(p.H0, p.H1, m["gamma"], p.beta, p.nocc, p.n, q0=m["q0"], tol=1e-12,
+                        order=2)
+    assert oracle.rel_frobenius(r["D0"], ref["D0"]) < 1e-9
+    for d in range(p.H1.shape[0]):
+        assert oracle.rel_frobenius(r["D1"][d], ref["D1"][d]) < 1e-9
+        assert oracle.rel_frobenius(r["D2"][d], ref["D2"][d]) < 1e-9
+        assert abs(r["omega2"][d] - ref["omega2"][d]) < 1e-9 * abs(ref["omega2"][d])
