@@ -377,6 +377,11 @@ def run_ours(args):
     if not args.no_chain:
         chain = run_chain(pkg, pk)
 
+    # block-sparse screened products on the 1D chain (Sec. VI): dense against screened
+    screened = None
+    if not args.no_screen and rank == 0:
+        screened = run_screened(pkg)
+
     cpu = None
     cpu1 = None
     err = None
@@ -423,6 +428,7 @@ def run_ours(args):
             "modes": modes,
             "batched": batched,
             "chain_n8192": chain,
+            "screened_chain": screened,
             "error": err,
             "detail": {
                 "gemm_share_of_step_time": gemm_ms_total / (ms / world) if ms else None,
@@ -483,6 +489,45 @@ def run_chain(pkg, pk):
     out["gemm_share_of_solve"] = gemm_s / dt if dt else None
     out["peak_note"] = (f"tf32 peak = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
                         f"{TF32_OVER_BF16:.4f}")
+    return out
+
+
+def run_screened(pkg, tau=1e-8):
+    """Block-sparse screened products (opts.screen_tau) on the Anderson-disordered 1D chain,
+    beta 10, n 12, mixed precision: one dense and one screened solve per size after a warm-up
+    of each, timed with CUDA events around the solve; the fraction of 128 x 32 k-slices
+    the screened products computed, and the screened-vs-dense change of alpha and P1."""
+    import numpy as np
+    import torch
+
+    import synthetic
+    out = {"workload": f"1D chain (seed 1001), beta 10, n 12, mixed precision, tau {tau:g}",
+           "sizes": {}}
+    for N in (8192, 16384):
+        p = synthetic.chain_1d(N, 1001, 10.0, 12)
+        res = {}
+        for label, t in (("dense", 0.0), ("screened", tau)):
+            with pkg.Handle(precision="mixed", screen_tau=t) as h:
+                h.set_H(p.H0, p.H1)
+                h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)   # warm-up
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                r = h.solve(p.beta, p.nocc, p.n, want_P0=False)
+                e1.record()
+                torch.cuda.synchronize()
+                st = h.stats()
+                res[label] = {"s": e0.elapsed_time(e1) / 1e3, "alpha": float(h.polarizability()[0]),
+                              "P1": r["P1"][0].cpu().numpy(),
+                              "computed": st["screen_slices_computed"],
+                              "examined": st["screen_slices_examined"]}
+        d, s_ = res["dense"], res["screened"]
+        out["sizes"][str(N)] = {
+            "dense_s": d["s"], "screened_s": s_["s"], "speedup": d["s"] / s_["s"],
+            "slices_computed_frac": s_["computed"] / s_["examined"] if s_["examined"] else None,
+            "alpha_rel_change": abs(s_["alpha"] - d["alpha"]) / abs(d["alpha"]),
+            "P1_rel_change": float(np.linalg.norm(s_["P1"] - d["P1"]) / np.linalg.norm(d["P1"]))}
     return out
 
 
@@ -579,6 +624,8 @@ def main():
                     help="skip the batched 96-cluster measurement")
     ap.add_argument("--no-chain", action="store_true",
                     help="skip the N = 8192 product-chain measurement")
+    ap.add_argument("--no-screen", action="store_true",
+                    help="skip the screened-product (block-sparse) chain measurement")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the one-step runs of the other precisions")
     args = ap.parse_args()

@@ -112,6 +112,15 @@ typedef struct {
                            and cdmpt_free_energy gives the Fermi-Dirac Mermin free energy,
                            whose canonical gradient is P0. cdmpt_batch_create refuses it
                            (ERR_UNSUPPORTED). */
+    double screen_tau;  /* > 0: block-sparse products (Sec. VI, Fig. 3: thresholded algebra
+                           for linear scaling). Each product X Y^T of the solve and of its
+                           derivatives drops the k-slice terms X_IK Y_JK^T of 128 x 32 tiles
+                           whose Frobenius norms satisfy ||X_IK|| ||Y_JK|| <= screen_tau, so
+                           the error of an output tile is at most screen_tau times the
+                           number of dropped slices, and the work follows the number of
+                           blocks above the threshold. Storage stays dense. FP32 and
+                           MIXED_TF32 with the tcgen05 engines only (ERR_ARG otherwise);
+                           0 (the default) keeps every product dense. */
 } cdmpt_opts;
 
 typedef struct {
@@ -136,6 +145,8 @@ typedef struct {
     double engine_flops[5];        /* algorithmic flops of those launches */
     int cg_iterations_recompute;   /* CG iterations spent recomputing checkpointed segments */
     int checkpoint_stride;         /* stride in use (0: whole trajectory stored) */
+    double screen_slices_computed; /* screened products of the last solve: 128 x 32 k-slices */
+    double screen_slices_examined; /* multiplied, and all slices of their output tiles */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -405,7 +416,7 @@ typedef struct cdmpt_batch cdmpt_batch;
 
 /* Create a batch of B systems of sizes N[0..B-1] with D directions each.
  * Errors: ERR_ARG, ERR_UNSUPPORTED (precision other than FP32 or MIXED_TF32,
- * fd_exact or grand_canonical set, or no sm_103 device), ERR_OOM. */
+ * fd_exact, grand_canonical or screen_tau set, or no sm_103 device), ERR_OOM. */
 cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int D,
                                 cdmpt_batch** out);
 

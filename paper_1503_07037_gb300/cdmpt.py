@@ -48,6 +48,7 @@ class Opts(ctypes.Structure):
         ("grand_canonical", ctypes.c_int),
         ("ckpt_stride", ctypes.c_int),
         ("fd_exact", ctypes.c_int),
+        ("screen_tau", ctypes.c_double),
     ]
 
 
@@ -85,6 +86,8 @@ class Stats(ctypes.Structure):
         ("engine_flops", ctypes.c_double * 5),
         ("cg_iterations_recompute", ctypes.c_int),
         ("checkpoint_stride", ctypes.c_int),
+        ("screen_slices_computed", ctypes.c_double),
+        ("screen_slices_examined", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -315,10 +318,13 @@ class Handle:
 
     def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
                  refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
-                 stream=None, grand_canonical=False, ckpt_stride=0, fd_exact=False):
+                 stream=None, grand_canonical=False, ckpt_stride=0, fd_exact=False,
+                 screen_tau=0.0):
         """ckpt_stride: 0 stores the whole recursion trajectory; s > 0 keeps every s-th
         step and recomputes the rest segment by segment; "sqrt" (or -1) picks
-        s = ceil(sqrt(n)). FP64 and FP32 precisions only."""
+        s = ceil(sqrt(n)). FP64 and FP32 precisions only. screen_tau > 0: block-sparse
+        products that drop 128 x 32 tile terms with norm product <= screen_tau (FP32 and
+        mixed TF32 only)."""
         o = default_opts()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.gemm_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
@@ -334,6 +340,7 @@ class Handle:
         o.grand_canonical = 1 if grand_canonical else 0
         o.ckpt_stride = -1 if ckpt_stride == "sqrt" else int(ckpt_stride)
         o.fd_exact = 1 if fd_exact else 0
+        o.screen_tau = float(screen_tau)
         self.opts = o
         self.h = create(o)
         self.N = 0

@@ -127,6 +127,13 @@ bool valid_opts(const cdmpt_opts* o) {
     if (o->ckpt_stride != 0 &&
         (o->precision == CDMPT_MIXED_TF32 || o->precision == CDMPT_MIXED_BF16))
         return false;
+    // screened products run on the tcgen05 TF32 engines only
+    if (!(o->screen_tau >= 0.0) || o->screen_tau > 1e30) return false;
+    if (o->screen_tau > 0.0 &&
+        ((o->precision != CDMPT_FP32 && o->precision != CDMPT_MIXED_TF32) ||
+         (o->gemm_engine != CDMPT_GEMM_AUTO && o->gemm_engine != CDMPT_GEMM_TC_TF32 &&
+          o->gemm_engine != CDMPT_GEMM_TC_3XTF32)))
+        return false;
     return true;
 }
 
@@ -157,6 +164,7 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
     o->grand_canonical = 0;
     o->ckpt_stride = 0;
     o->fd_exact = 0;
+    o->screen_tau = 0.0;
     return CDMPT_OK;
 }
 
@@ -185,6 +193,10 @@ cdmpt_status cdmpt_create(const cdmpt_opts* opts, cdmpt_handle** out) {
         o = *opts;
     else
         cdmpt_default_opts(&o);
+    if (!valid_opts(&o)) {   // host-side check before any device call
+        set_error("invalid options");
+        return CDMPT_ERR_ARG;
+    }
     cdmpt_handle* h = new (std::nothrow) cdmpt_handle();
     if (!h) return CDMPT_ERR_OOM;
     std::memset(&h->st, 0, sizeof(h->st));

@@ -266,6 +266,9 @@ cdmpt_status prepare_grouped(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
         pr.num_mt = (g.p.M + bm - 1) / bm;
         pr.skip = g.skip;
         pr.maps = nullptr;
+        pr.mask = nullptr;   // grouped launches are never screened
+        pr.nnt = pr.nmw = 0;
+        pr.counts = nullptr;
         // symmetric results need square tiles: the upper triangle only
         pr.p.sym = (g.p.sym && bn == bm && g.p.M == N) ? 1 : 0;
         probs->push_back(pr);
@@ -867,10 +870,10 @@ cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int
         set_error("batch: CDMPT_FP32 (split-TF32 products) or CDMPT_MIXED_TF32 only");
         return CDMPT_ERR_UNSUPPORTED;
     }
-    if (b->opts.fd_exact || b->opts.grand_canonical) {
+    if (b->opts.fd_exact || b->opts.grand_canonical || b->opts.screen_tau != 0.0) {
         delete b;
-        set_error("batch: canonical solves from the linear start of Eq. Rec_F_2 only "
-                  "(no fd_exact, no grand_canonical)");
+        set_error("batch: canonical dense solves from the linear start of Eq. Rec_F_2 only "
+                  "(no fd_exact, grand_canonical or screen_tau)");
         return CDMPT_ERR_UNSUPPORTED;
     }
     if (!tc_supported()) {

@@ -497,6 +497,58 @@ thread_local long long g_launches = 0;
 constexpr int kNoAllocMaxN = 32768;
 __device__ __align__(256) double g_bounds_scratch[2 * kNoAllocMaxN];
 
+// Frobenius norms of the 128 x 32 tiles of a rows x cols FP32 matrix, one CTA of
+// 128 threads per tile: each warp covers 32 rows, four rows per step with eight
+// lanes (one float4 each) per 128-byte row segment, so every load is coalesced.
+__global__ void k_tile_norms(const float* __restrict__ X, int rows, int cols, int ld, int nkb,
+                             bool vec, float* __restrict__ out, const double* __restrict__ skip) {
+    if (skip && *skip != 0.0) return;
+    const int rb = blockIdx.x / nkb, kb = blockIdx.x - rb * nkb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = kb * 32 + (lane & 7) * 4;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = rb * 128 + warp * 32 + i * 4 + (lane >> 3);
+        if (r >= rows) continue;
+        const float* x = X + (size_t)r * ld + c;
+        if (vec && c + 4 <= cols) {
+            const float4 v = *reinterpret_cast<const float4*>(x);
+            acc += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+        } else {
+            for (int j = 0; j < 4 && c + j < cols; ++j) acc += x[j] * x[j];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ float part[4];
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrtf(part[0] + part[1] + part[2] + part[3]);
+}
+
+// Screening mask of a product from the tile norms of its operands: bit kb of word w of
+// output tile (I, J) is set unless nx[I][kb] * ny[J][kb] <= tau (a NaN norm keeps the
+// slice, so non-finite values propagate as in the dense product).
+__global__ void k_screen_mask(const float* __restrict__ nx, const float* __restrict__ ny,
+                              int mt, int nt, int nkb, int nmw, float tau,
+                              uint32_t* __restrict__ mask, const double* __restrict__ skip) {
+    if (skip && *skip != 0.0) return;
+    const size_t total = (size_t)mt * nt * nmw;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int w = (int)(e % nmw);
+        const size_t tile = e / nmw;
+        const int J = (int)(tile % nt), I = (int)(tile / nt);
+        const int k0 = w * 32, k1 = min(nkb, k0 + 32);
+        uint32_t bits = 0u;
+        for (int kb = k0; kb < k1; ++kb)
+            if (!(nx[(size_t)I * nkb + kb] * ny[(size_t)J * nkb + kb] <= tau))
+                bits |= 1u << (kb - k0);
+        mask[e] = bits;
+    }
+}
+
 }  // namespace
 
 void count_launch(int k) { g_launches += k; }
@@ -636,6 +688,27 @@ cdmpt_status to_bf16(const float* x, size_t count, void* out, const double* skip
     const size_t nvec = count / 4;
     if (!nvec) return CDMPT_OK;
     k_to_bf16<<<grid_for(nvec), kThreads, 0, s>>>(x, nvec, (uint2*)out, skip);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+cdmpt_status tile_norms(const float* X, int rows, int cols, int ld, float* out,
+                        const double* skip, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return CDMPT_OK;
+    const int nrb = (rows + 127) / 128, nkb = (cols + 31) / 32;
+    const bool vec = (ld % 4) == 0 && (((uintptr_t)X) & 15) == 0;
+    k_tile_norms<<<(unsigned)((size_t)nrb * nkb), 128, 0, s>>>(X, rows, cols, ld, nkb, vec, out,
+                                                               skip);
+    LAUNCH_CHECK();
+    return CDMPT_OK;
+}
+
+cdmpt_status screen_mask(const float* nx, const float* ny, int M, int N, int nkb, float tau,
+                         uint32_t* mask, const double* skip, cudaStream_t s) {
+    const int mt = (M + 127) / 128, nt = (N + 127) / 128, nmw = (nkb + 31) / 32;
+    if (mt <= 0 || nt <= 0 || nmw <= 0) return CDMPT_OK;
+    k_screen_mask<<<grid_for((size_t)mt * nt * nmw), kThreads, 0, s>>>(nx, ny, mt, nt, nkb, nmw,
+                                                                        tau, mask, skip);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }

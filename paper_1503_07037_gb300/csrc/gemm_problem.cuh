@@ -15,6 +15,13 @@ struct GemmProblem {
     int num_mt;                // output tiles along M
     const double* skip;        // the problem is skipped while *skip != 0
     const CUtensorMap* maps;   // grouped launches: X hi, Y hi, X lo, Y lo (device memory)
+    // Block-norm screening (single launches with 128-column tiles only; mask null:
+    // dense). Bit kb of mask[(I * nnt + J) * nmw + kb / 32] says whether k-slice kb (32
+    // columns of K) of output tile (I, J) is computed; nnt tiles per tile row, nmw words
+    // per tile. counts, if not null, receives += [slices computed, slices examined].
+    const uint32_t* mask;
+    int nnt, nmw;
+    unsigned long long* counts;
 };
 
 // Tensor map of an FP32 operand (rows x cols, leading dimension ld) as the X

@@ -22,6 +22,14 @@
 // columns at a time between the chunk drains of the next tile (tc_deferred.cuh),
 // so the global stores overlap the MMAs.
 //
+// Block-norm screening (single launches with a GemmProblem::mask): k-slice kb of
+// an output tile is skipped when the product of the Frobenius norms of its X and Y
+// tiles is at most tau, as recorded in a per-tile bit mask built before the launch
+// (screen_mask). Producer, MMA issuer and epilogue read the same mask words, so
+// they walk the same sequence of slices; a tile with no slice left is written by the
+// epilogue from a zero accumulator without touching TMEM or a barrier, and chunks
+// group the remaining slices.
+//
 // Every mbarrier wait is bounded (about 2 s of %globaltimer). On timeout a
 // thread records the error, raises a shared abort flag that ends the other
 // roles' loops, in-flight TMA/MMA work is drained with bounded waits, and the
@@ -179,6 +187,18 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         *kc = KCH > 0 ? KCH : num_k;
         return (num_k + *kc - 1) / *kc;
     };
+    // block-norm screening: the mask words of tile r (BN = BM = 128 when screened)
+    const bool screen = !GROUPED && single.mask != nullptr;
+    auto mask_of = [&](const TileRef& r) -> const uint32_t* {
+        return single.mask + ((size_t)(r.m0 / BM) * single.nnt + r.n0 / BM) * single.nmw;
+    };
+    auto count_active = [&](const TileRef& r) -> int {
+        if (!screen) return r.num_k;
+        const uint32_t* w = mask_of(r);
+        int c = 0;
+        for (int i = 0; i < single.nmw; ++i) c += __popc(w[i]);
+        return c;
+    };
 
     auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
@@ -243,7 +263,13 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         last = r.pr;
                     }
                 }
-                for (int kb = 0; kb < r.num_k; ++kb, ++it) {
+                const uint32_t* mw = screen ? mask_of(r) : nullptr;
+                uint32_t word = 0xffffffffu;
+                for (int kb = 0; kb < r.num_k; ++kb) {
+                    if (screen) {
+                        if ((kb & 31) == 0) word = mw[kb >> 5];
+                        if (!((word >> (kb & 31)) & 1u)) continue;
+                    }
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
@@ -268,6 +294,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         if constexpr (PASSES == 3)
                             tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
                     }
+                    ++it;
                 }
             }
             if (!ok) {
@@ -281,12 +308,22 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32<BM, BN>();
             uint32_t it = 0, g = 0;
+            unsigned long long computed = 0, examined = 0;
             bool ok = true, issued = false;
             for (int t = t_first; t < total_tiles && ok; t += t_step) {
                 const TileRef r = tile(t);
                 if (r.skip) continue;
+                const int na = count_active(r);
+                computed += (unsigned long long)na;
+                examined += (unsigned long long)r.num_k;
+                if (na == 0) continue;   // the epilogue writes this tile from zero
                 int kc = 0;
-                const int nch = chunks(r.num_k, &kc);
+                const int nch = chunks(na, &kc);
+                int kb = 0;   // next k-slice to examine
+                const uint32_t* mw = screen ? mask_of(r) : nullptr;
+                auto is_active = [&](int k) {
+                    return !screen || ((mw[k >> 5] >> (k & 31)) & 1u) != 0u;
+                };
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int b = g % NB;
                     if (!mbar_wait(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
@@ -296,8 +333,9 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
-                    const int kb0 = c * kc, kb1 = min(r.num_k, kb0 + kc);
-                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int cnt = min(kc, na - c * kc);
+                    for (int j = 0; j < cnt; ++j, ++kb, ++it) {
+                        while (kb < r.num_k && !is_active(kb)) ++kb;
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
                         if (!mbar_wait(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL)) {
@@ -310,7 +348,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         for (int kk = 0; kk < BK / UMMA_K; ++kk) {
                             const uint32_t off = kk * UMMA_K * 4;
                             const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
-                            const uint32_t first = ((kb - kb0) | kk) != 0 ? 1u : 0u;
+                            const uint32_t first = (j | kk) != 0 ? 1u : 0u;
                             if constexpr (PASSES == 3) {
                                 const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
                                 const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
@@ -334,6 +372,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             if (!ok && issued) {
                 mma_commit(drain);
                 mbar_drain(drain, 0);
+            }
+            if (screen && single.counts) {
+                atomicAdd(single.counts, computed);
+                atomicAdd(single.counts + 1, examined);
             }
         }
     } else {
@@ -361,8 +403,13 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             const EpiParams<float> p = r.pr->p;
             const bool vec4 = epi_vec4_ok(p);
             const int m = r.m0 + 32 * q + lane;
+            int na = r.num_k;
+            if (screen) {   // the same count as the MMA issuer's, broadcast from lane 0
+                if (lane == 0) na = count_active(r);
+                na = __shfl_sync(0xffffffffu, na, 0);
+            }
             int kc = 0;
-            const int nch = chunks(r.num_k, &kc);
+            const int nch = na > 0 ? chunks(na, &kc) : 0;
             bool ok = true;
             if constexpr (KCH > 0) {
                 // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
@@ -403,18 +450,26 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 }
                 pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
             } else {
-                (void)nch;
+                const bool empty_tile = nch == 0;   // screened to nothing: zero accumulator
                 const int b = g & 1;
-                int w = 1;
-                if (lane == 0)
-                    w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-                w = __shfl_sync(0xffffffffu, w, 0);
-                if (!w) break;
-                tc_fence_after();
+                if (!empty_tile) {
+                    int w = 1;
+                    if (lane == 0)
+                        w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err,
+                                      DEV_TIMEOUT_ACCUM);
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (!w) break;
+                    tc_fence_after();
+                }
 #pragma unroll 1
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     uint32_t rr[32];
-                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
+                    if (!empty_tile) {
+                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) rr[j] = 0u;
+                    }
                     if (m < p.M && p.sym) {
                         float local = 0.f;
                         const int nb = r.n0 + c0;
@@ -454,10 +509,12 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         dsum += (double)local;
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
-                ++g;
+                if (!empty_tile) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                    ++g;
+                }
             }
             if constexpr (GROUPED && KCH == 0) {
                 // each problem has its own dot target: flush per tile
@@ -513,7 +570,7 @@ cdmpt_status set_smem_attr() {
 template <int BN, int STAGES, int PASSES, int KCH>
 cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ldx, const float* Y,
                     const float* Yl, int ldy, const EpiParams<float>& p, const double* skip,
-                    cudaStream_t s) {
+                    cudaStream_t s, const GemmScreen* sc = nullptr) {
     using C = Cfg<BN, STAGES, PASSES>;
     {
         const cdmpt_status st = set_smem_attr<BN, STAGES, PASSES, KCH, false>();
@@ -532,6 +589,11 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     pr.num_mt = (M + BM - 1) / BM;
     pr.skip = skip;
     pr.maps = nullptr;
+    const bool screened = sc && sc->mask && BN == BM;
+    pr.mask = screened ? sc->mask : nullptr;
+    pr.nnt = screened ? (N + BM - 1) / BM : 0;
+    pr.nmw = screened ? sc->nmw : 0;
+    pr.counts = screened ? sc->counts : nullptr;
     // symmetric results need square tiles: upper-triangular tiles only
     const bool sym = p.sym && BN == BM && M == N;
     pr.p.sym = sym ? 1 : 0;
@@ -594,6 +656,9 @@ cdmpt_status launch_pair(int M, int N, int K, const float* X, const float* Xl, i
     pr.num_mt = (M + BM - 1) / BM;
     pr.skip = skip;
     pr.maps = nullptr;
+    pr.mask = nullptr;   // pairs share B tiles: never screened
+    pr.nnt = pr.nmw = 0;
+    pr.counts = nullptr;
     const int tiles = pr.num_mt * ((N + BN - 1) / BN);
     const int pairs = tiles / 2;
     const int clusters = pairs < max_clusters ? pairs : max_clusters;
@@ -713,7 +778,8 @@ bool tc_supported() {
 
 cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& X, int ldx,
                          const Operand<float>& Y, int ldy, float* D, int ldd,
-                         const Epilogue<float>& ep, const double* skip, cudaStream_t s) {
+                         const Epilogue<float>& ep, const double* skip, cudaStream_t s,
+                         const GemmScreen* screen) {
     if (M <= 0 || N <= 0) return CDMPT_OK;
     if (!tc_supported()) {
         set_error("tcgen05 GEMM needs an sm_103 device");
@@ -790,6 +856,22 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     p.Dhi = ep.Dhi;
     p.Dlo = ep.Dlo;
     p.sym = (ep.sym && M == N && ep.trans_block <= 0) ? 1 : 0;
+    if (screen && screen->mask) {
+        // screened: one-SM kernel with 128 x 128 tiles (the mask's granularity),
+        // symmetric results on the upper triangle
+        if (screen->nmw != ((K + BK - 1) / BK + 31) / 32) {
+            set_error("screened tcgen05 GEMM: the mask does not match the product");
+            return CDMPT_ERR_ARG;
+        }
+        if (!three)
+            return launch<128, 6, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s, screen);
+        switch (split_chunk()) {
+            case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            case 0: return launch<128, 3, 3, 0>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            default: return launch<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+        }
+    }
     if (p.sym) {
         // symmetric result: square tiles, upper triangle only (TF32: 256 x 256 two-SM
         // tiles; split TF32: 128 x 128 one-SM tiles without cluster pairs)

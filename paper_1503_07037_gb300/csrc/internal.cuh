@@ -92,11 +92,33 @@ template <typename T>
 cdmpt_status gemm_simt(int M, int N, int K, const T* X, int ldx, const T* Y, int ldy, T* D,
                        int ldd, const Epilogue<T>& ep, const double* skip, cudaStream_t s);
 
+// Block-norm screening of one tcgen05 product X Y^T (M x N, depth K): the bit mask of
+// the k-slices each 128 x 128 output tile computes (see GemmProblem), nmw words per
+// tile, ceil(N / 128) tiles per tile row. counts, if not null, receives
+// += [slices computed, slices examined] (two device counters).
+struct GemmScreen {
+    const uint32_t* mask = nullptr;
+    int nmw = 0;
+    unsigned long long* counts = nullptr;
+};
+// Tile norms for screening: out[rb * nkb + kb] = || X[128 rb .., 32 kb ..] ||_F over
+// the rows x cols matrix (leading dimension ld), nkb = ceil(cols / 32). The kernel
+// returns at once while *skip != 0 (skip may be null).
+cdmpt_status tile_norms(const float* X, int rows, int cols, int ld, float* out,
+                        const double* skip, cudaStream_t s);
+// Screening mask of the product of X (M rows) and Y (N rows) from their tile norms:
+// bit kb of tile (I, J) is set when nx[I][kb] * ny[J][kb] > tau. mask holds
+// ceil(M / 128) * ceil(N / 128) * ceil(nkb / 32) words.
+cdmpt_status screen_mask(const float* nx, const float* ny, int M, int N, int nkb, float tau,
+                         uint32_t* mask, const double* skip, cudaStream_t s);
+
 // tcgen05 engines. TF32 reads X.hi / Y.hi when given (round-to-nearest
 // operands), else X.x / Y.x; 3xTF32 requires the hi and lo arrays of both.
+// screen (TF32 and 3xTF32 only; null or tau = 0: dense) skips negligible k-slices.
 cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& X, int ldx,
                          const Operand<float>& Y, int ldy, float* D, int ldd,
-                         const Epilogue<float>& ep, const double* skip, cudaStream_t s);
+                         const Epilogue<float>& ep, const double* skip, cudaStream_t s,
+                         const GemmScreen* screen = nullptr);
 bool tc_supported();   // device is sm_103 (tcgen05 kernels built for sm_103a)
 // Two-SM variant (tcgen05.mma.cta_group::2, 256-row tiles per CTA pair);
 // X / Y are the hi operands (TF32) and Xl / Yl the lo operands (3xTF32).

@@ -134,6 +134,30 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     CDMPT_TRY(buf(big, &Z1b_, true));
     CDMPT_TRY(buf(blk_, &Qmu_, false));
     CDMPT_TRY(buf(blk_, &Zh_, false));
+    tnx_ = tny_ = nullptr;
+    tmask_ = nullptr;
+    tcnt_ = nullptr;
+    if (sizeof(T) == 4) {
+        // screening: norm tables of 128-row blocks x 32-column slices, the slice mask of
+        // 128 x 128 output tiles, and two counters
+        const size_t rb = (size_t)(rows_needed + 127) / 128, nkb = (size_t)(N + 31) / 32;
+        const size_t words = rb * ((size_t)(N + 127) / 128) * ((nkb + 31) / 32);
+        void* q[4] = {nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[4] = {rb * nkb * sizeof(float), rb * nkb * sizeof(float),
+                                 words * sizeof(uint32_t), 2 * sizeof(unsigned long long)};
+        for (int i = 0; i < 4; ++i) {
+            if (cudaMalloc(&q[i], bytes[i]) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation of the screening tables failed");
+                return CDMPT_ERR_OOM;
+            }
+            allocs_.push_back(q[i]);
+        }
+        tnx_ = (float*)q[0];
+        tny_ = (float*)q[1];
+        tmask_ = (uint32_t*)q[2];
+        tcnt_ = (unsigned long long*)q[3];
+    }
     traj_valid_ = q_valid_ = false;
     void* p = nullptr;
     if (cudaMalloc(&p, S_NSLOTS * sizeof(double)) != cudaSuccess) return CDMPT_ERR_OOM;
@@ -209,10 +233,31 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
     }
     cdmpt_status s;
     if constexpr (sizeof(T) == 4) {
-        if (engine == CDMPT_GEMM_SIMT)
+        if (engine == CDMPT_GEMM_SIMT) {
             s = gemm_simt<float>(M, Nc, K, X.x, ld, Y.x, ld, D, ld, ep, skip, cx.stream);
-        else
-            s = gemm_tc_f32(engine, M, Nc, K, X, ld, Y, ld, D, ld, ep, skip, cx.stream);
+        } else {
+            // block-norm screening: tile norms of both operands, then the screened kernel
+            GemmScreen sc;
+            const GemmScreen* psc = nullptr;
+            const bool tf32 = engine == CDMPT_GEMM_TC_TF32 || engine == CDMPT_GEMM_TC_3XTF32;
+            if (screen_tau_ > 0.f && tf32 && tnx_ && M <= rows_cap_ && Nc <= N_ && K <= N_) {
+                const float* xs = X.x ? X.x : X.hi;
+                const float* ys = Y.x ? Y.x : Y.hi;
+                CDMPT_TRY(tile_norms(xs, M, K, ld, tnx_, skip, cx.stream));
+                const float* ny = tnx_;
+                if (!(ys == xs && Nc == M)) {
+                    CDMPT_TRY(tile_norms(ys, Nc, K, ld, tny_, skip, cx.stream));
+                    ny = tny_;
+                }
+                const int nkb = (K + 31) / 32;
+                CDMPT_TRY(screen_mask(tnx_, ny, M, Nc, nkb, screen_tau_, tmask_, skip, cx.stream));
+                sc.mask = tmask_;
+                sc.nmw = (nkb + 31) / 32;
+                sc.counts = tcnt_;
+                psc = &sc;
+            }
+            s = gemm_tc_f32(engine, M, Nc, K, X, ld, Y, ld, D, ld, ep, skip, cx.stream, psc);
+        }
     } else {
         s = gemm_simt<double>(M, Nc, K, X.x, ld, Y.x, ld, D, ld, ep, skip, cx.stream);
     }
@@ -1334,6 +1379,9 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     CDMPT_TRY(reserve(N, D, n, ck));
     traj_valid_ = q_valid_ = false;
     fdx_ = o.fd_exact != 0;
+    screen_tau_ = (sizeof(T) == 4 && tcnt_) ? (float)o.screen_tau : 0.f;
+    if (screen_tau_ > 0.f)
+        CDMPT_CUDA_TRY(cudaMemsetAsync(tcnt_, 0, 2 * sizeof(unsigned long long), cx.stream));
     gmin_ = gmin;
     gmax_ = gmax;
     replay_iters_ = 0;
@@ -1600,6 +1648,14 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     }
     st.cg_iterations_recompute = replay_iters_;
     st.checkpoint_stride = ck_;
+    st.screen_slices_computed = st.screen_slices_examined = 0.0;
+    if (screen_tau_ > 0.f) {
+        unsigned long long c[2] = {0, 0};
+        CDMPT_CUDA_TRY(cudaMemcpyAsync(c, tcnt_, sizeof(c), cudaMemcpyDeviceToHost, cx.stream));
+        CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
+        st.screen_slices_computed = (double)c[0];
+        st.screen_slices_examined = (double)c[1];
+    }
     CDMPT_CUDA_TRY(cudaStreamSynchronize(cx.stream));
     return check_device_error(cx.stream);
 }

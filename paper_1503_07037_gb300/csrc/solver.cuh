@@ -202,6 +202,13 @@ private:
     Buf<T> zo_[3][2], ao_[3], G_;
     // Fermi-Dirac-exact start: Y = -s2 (H0 - mu I) at the trajectory's mu and U = Y^2
     Buf<T> Yfd_, Ufd_;
+    // block-norm screening (opts.screen_tau, FP32 storage): tile-norm tables of the two
+    // operands of the current product, and the [computed, examined] slice counters
+    float* tnx_ = nullptr;
+    float* tny_ = nullptr;
+    uint32_t* tmask_ = nullptr;   // slice mask of the current product
+    unsigned long long* tcnt_ = nullptr;
+    float screen_tau_ = 0.f;
     int cur_[3] = {0, 0, 0};
     bool orders_ready_ = false;
     std::vector<double> last_mu1_;

@@ -75,3 +75,24 @@ def test_batch_refuses_options_it_does_not_implement(cdmpt_lib, flag):
     with pytest.raises(cdmpt_lib.CdmptError) as e:
         cdmpt_lib.Batch([8, 12], 1, **{flag: 1})
     assert e.value.status == 8   # ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["fp64", "bf16", "simt", "negative", "nan"])
+def test_screening_option_checks(cdmpt_lib, case):
+    """screen_tau > 0 needs FP32 storage and a TF32 tensor-core engine; it must be >= 0."""
+    import math
+    o = cdmpt_lib.default_opts()
+    o.screen_tau = 1e-6
+    if case == "fp64":
+        o.precision = cdmpt_lib.FP64
+    elif case == "bf16":
+        o.precision = cdmpt_lib.MIXED_BF16
+    elif case == "simt":
+        o.gemm_engine = cdmpt_lib.GEMM_SIMT
+    elif case == "negative":
+        o.screen_tau = -1.0
+    else:
+        o.screen_tau = math.nan
+    with pytest.raises(cdmpt_lib.CdmptError) as e:
+        cdmpt_lib.create(o)
+    assert e.value.status == 1   # ERR_ARG, before any device call
