@@ -380,7 +380,7 @@ def run_ours(args):
     # block-sparse screened products on the 1D chain (Sec. VI): dense against screened
     screened = None
     if not args.no_screen and rank == 0:
-        screened = run_screened(pkg)
+        screened = run_screened(pkg, sizes=[int(x) for x in args.screen_sizes.split(",") if x])
 
     cpu = None
     cpu1 = None
@@ -492,7 +492,7 @@ def run_chain(pkg, pk):
     return out
 
 
-def run_screened(pkg, tau=1e-8):
+def run_screened(pkg, tau=1e-8, sizes=(8192, 16384)):
     """Block-sparse screened products (opts.screen_tau) on the Anderson-disordered 1D chain,
     beta 10, n 12, mixed precision: one dense and one screened solve per size after a warm-up
     of each, timed with CUDA events around the solve; the fraction of 128 x 32 k-slices
@@ -503,10 +503,10 @@ def run_screened(pkg, tau=1e-8):
     import synthetic
     out = {"workload": f"1D chain (seed 1001), beta 10, n 12, mixed precision, tau {tau:g}",
            "sizes": {}}
-    for N in (8192, 16384):
+    for N in sizes:
         p = synthetic.chain_1d(N, 1001, 10.0, 12)
         res = {}
-        for label, t in (("dense", 0.0), ("screened", tau)):
+        for label, t in (("screened", tau), ("dense", 0.0)):
             with pkg.Handle(precision="mixed", screen_tau=t) as h:
                 h.set_H(p.H0, p.H1)
                 h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)   # warm-up
@@ -628,9 +628,18 @@ def main():
                     help="skip the screened-product (block-sparse) chain measurement")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the one-step runs of the other precisions")
+    ap.add_argument("--screen-sizes", default="8192,16384",
+                    help="chain sizes of the screened-product measurement")
+    ap.add_argument("--screened-only", action="store_true",
+                    help="run only the screened-product chain measurement (one JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.screened_only:
+        import paper_1503_07037_gb300 as pkg
+        sizes = [int(x) for x in args.screen_sizes.split(",") if x]
+        print(json.dumps(run_screened(pkg, sizes=sizes)), flush=True)
+        return 0
     return run_ours(args)
 
 
