@@ -143,7 +143,8 @@ __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
 // columns); each CTA loads its own A tile and half of the B tile, multicast to
 // both, so each SM fetches half as many B bytes. Stage reuse then waits for
 // both CTAs' MMAs (empty barriers count two commits).
-template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool PAIR = false>
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool PAIR = false,
+          bool SCREEN = false>
 __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
@@ -187,17 +188,21 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         *kc = KCH > 0 ? KCH : num_k;
         return (num_k + *kc - 1) / *kc;
     };
-    // block-norm screening: the mask words of tile r (BN = BM = 128 when screened)
-    const bool screen = !GROUPED && single.mask != nullptr;
+    // block-norm screening (compiled in only for the screened instantiations): the mask
+    // words of tile r (BN = BM = 128 when screened)
+    constexpr bool screen = SCREEN && !GROUPED;
     auto mask_of = [&](const TileRef& r) -> const uint32_t* {
         return single.mask + ((size_t)(r.m0 / BM) * single.nnt + r.n0 / BM) * single.nmw;
     };
     auto count_active = [&](const TileRef& r) -> int {
-        if (!screen) return r.num_k;
-        const uint32_t* w = mask_of(r);
-        int c = 0;
-        for (int i = 0; i < single.nmw; ++i) c += __popc(w[i]);
-        return c;
+        if constexpr (!screen) {
+            return r.num_k;
+        } else {
+            const uint32_t* w = mask_of(r);
+            int c = 0;
+            for (int i = 0; i < single.nmw; ++i) c += __popc(w[i]);
+            return c;
+        }
     };
 
     auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
@@ -266,7 +271,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 const uint32_t* mw = screen ? mask_of(r) : nullptr;
                 uint32_t word = 0xffffffffu;
                 for (int kb = 0; kb < r.num_k; ++kb) {
-                    if (screen) {
+                    if constexpr (screen) {
                         if ((kb & 31) == 0) word = mw[kb >> 5];
                         if (!((word >> (kb & 31)) & 1u)) continue;
                     }
@@ -317,13 +322,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 computed += (unsigned long long)na;
                 examined += (unsigned long long)r.num_k;
                 if (na == 0) continue;   // the epilogue writes this tile from zero
+                // the producer issues the computed slices in order, so the issuer only
+                // needs their number
                 int kc = 0;
                 const int nch = chunks(na, &kc);
-                int kb = 0;   // next k-slice to examine
-                const uint32_t* mw = screen ? mask_of(r) : nullptr;
-                auto is_active = [&](int k) {
-                    return !screen || ((mw[k >> 5] >> (k & 31)) & 1u) != 0u;
-                };
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int b = g % NB;
                     if (!mbar_wait(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
@@ -333,9 +335,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
-                    const int cnt = min(kc, na - c * kc);
-                    for (int j = 0; j < cnt; ++j, ++kb, ++it) {
-                        while (kb < r.num_k && !is_active(kb)) ++kb;
+                    // positions kb0 .. kb1 - 1 of the sequence of computed k-slices (all of
+                    // them when dense)
+                    const int kb0 = c * kc, kb1 = min(na, kb0 + kc);
+                    for (int q = kb0; q < kb1; ++q, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
                         if (!mbar_wait(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL)) {
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         for (int kk = 0; kk < BK / UMMA_K; ++kk) {
                             const uint32_t off = kk * UMMA_K * 4;
                             const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
-                            const uint32_t first = (j | kk) != 0 ? 1u : 0u;
+                            const uint32_t first = ((q - kb0) | kk) != 0 ? 1u : 0u;
                             if constexpr (PASSES == 3) {
                                 const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
                                 const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
@@ -373,9 +376,11 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 mma_commit(drain);
                 mbar_drain(drain, 0);
             }
-            if (screen && single.counts) {
-                atomicAdd(single.counts, computed);
-                atomicAdd(single.counts + 1, examined);
+            if constexpr (screen) {
+                if (single.counts) {
+                    atomicAdd(single.counts, computed);
+                    atomicAdd(single.counts + 1, examined);
+                }
             }
         }
     } else {
@@ -404,12 +409,12 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             const bool vec4 = epi_vec4_ok(p);
             const int m = r.m0 + 32 * q + lane;
             int na = r.num_k;
-            if (screen) {   // the same count as the MMA issuer's, broadcast from lane 0
+            if constexpr (screen) {   // the same count as the MMA issuer's, from lane 0
                 if (lane == 0) na = count_active(r);
                 na = __shfl_sync(0xffffffffu, na, 0);
             }
             int kc = 0;
-            const int nch = na > 0 ? chunks(na, &kc) : 0;
+            const int nch = (screen && na == 0) ? 0 : chunks(na, &kc);
             bool ok = true;
             if constexpr (KCH > 0) {
                 // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                 }
                 pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
             } else {
-                const bool empty_tile = nch == 0;   // screened to nothing: zero accumulator
+                const bool empty_tile = screen && nch == 0;   // screened to nothing: zero acc
                 const int b = g & 1;
                 if (!empty_tile) {
                     int w = 1;
@@ -551,12 +556,12 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     }
 }
 
-template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED>
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool SCREEN = false>
 cdmpt_status set_smem_attr() {
     using C = Cfg<BN, STAGES, PASSES>;
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, PASSES, KCH, GROUPED>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, PASSES, KCH, GROUPED, false, SCREEN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) {
             set_error(std::string("tcgen05 GEMM smem attribute: ") + cudaGetErrorString(e));
@@ -567,13 +572,18 @@ cdmpt_status set_smem_attr() {
     return CDMPT_OK;
 }
 
-template <int BN, int STAGES, int PASSES, int KCH>
+template <int BN, int STAGES, int PASSES, int KCH, bool SCREEN = false>
 cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ldx, const float* Y,
                     const float* Yl, int ldy, const EpiParams<float>& p, const double* skip,
                     cudaStream_t s, const GemmScreen* sc = nullptr) {
     using C = Cfg<BN, STAGES, PASSES>;
+    static_assert(!SCREEN || BN == BM, "screened products use square tiles");
+    if (SCREEN && !(sc && sc->mask)) {
+        set_error("screened tcgen05 GEMM without a mask");
+        return CDMPT_ERR_ARG;
+    }
     {
-        const cdmpt_status st = set_smem_attr<BN, STAGES, PASSES, KCH, false>();
+        const cdmpt_status st = set_smem_attr<BN, STAGES, PASSES, KCH, false, SCREEN>();
         if (st != CDMPT_OK) return st;
     }
     CUtensorMap mx, my, mxl, myl;
@@ -589,17 +599,16 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     pr.num_mt = (M + BM - 1) / BM;
     pr.skip = skip;
     pr.maps = nullptr;
-    const bool screened = sc && sc->mask && BN == BM;
-    pr.mask = screened ? sc->mask : nullptr;
-    pr.nnt = screened ? (N + BM - 1) / BM : 0;
-    pr.nmw = screened ? sc->nmw : 0;
-    pr.counts = screened ? sc->counts : nullptr;
+    pr.mask = SCREEN ? sc->mask : nullptr;
+    pr.nnt = SCREEN ? (N + BM - 1) / BM : 0;
+    pr.nmw = SCREEN ? sc->nmw : 0;
+    pr.counts = SCREEN ? sc->counts : nullptr;
     // symmetric results need square tiles: upper-triangular tiles only
     const bool sym = p.sym && BN == BM && M == N;
     pr.p.sym = sym ? 1 : 0;
     const int tiles = sym ? pr.num_mt * (pr.num_mt + 1) / 2 : pr.num_mt * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_tc<BN, STAGES, PASSES, KCH, false><<<grid, C::THREADS, C::SMEM, s>>>(
+    k_gemm_tc<BN, STAGES, PASSES, KCH, false, false, SCREEN><<<grid, C::THREADS, C::SMEM, s>>>(
         mx, my, mxl, myl, pr, nullptr, 1, tiles, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -864,12 +873,13 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
             return CDMPT_ERR_ARG;
         }
         if (!three)
-            return launch<128, 6, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s, screen);
+            return launch<128, 6, 1, 0, true>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s,
+                                              screen);
         switch (split_chunk()) {
-            case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
-            case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
-            case 0: return launch<128, 3, 3, 0>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
-            default: return launch<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            case 1: return launch<128, 3, 3, 1, true>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            case 4: return launch<128, 3, 3, 4, true>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            case 0: return launch<128, 3, 3, 0, true>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
+            default: return launch<128, 3, 3, 2, true>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s, screen);
         }
     }
     if (p.sym) {
