@@ -134,7 +134,8 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     CDMPT_TRY(buf(big, &Z1b_, true));
     CDMPT_TRY(buf(blk_, &Qmu_, false));
     CDMPT_TRY(buf(blk_, &Zh_, false));
-    tnx_ = tny_ = nullptr;
+    tnx_ = tny_ = tnw_ = nullptr;
+    wnorm_src_ = nullptr;
     tmask_ = nullptr;
     tcnt_ = nullptr;
     if (sizeof(T) == 4) {
@@ -142,10 +143,11 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
         // 128 x 128 output tiles, and two counters
         const size_t rb = (size_t)(rows_needed + 127) / 128, nkb = (size_t)(N + 31) / 32;
         const size_t words = rb * ((size_t)(N + 127) / 128) * ((nkb + 31) / 32);
-        void* q[4] = {nullptr, nullptr, nullptr, nullptr};
-        const size_t bytes[4] = {rb * nkb * sizeof(float), rb * nkb * sizeof(float),
-                                 words * sizeof(uint32_t), 2 * sizeof(unsigned long long)};
-        for (int i = 0; i < 4; ++i) {
+        void* q[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[5] = {rb * nkb * sizeof(float), rb * nkb * sizeof(float),
+                                 words * sizeof(uint32_t), 2 * sizeof(unsigned long long),
+                                 rb * nkb * sizeof(float)};
+        for (int i = 0; i < 5; ++i) {
             if (cudaMalloc(&q[i], bytes[i]) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("device allocation of the screening tables failed");
@@ -157,6 +159,7 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
         tny_ = (float*)q[1];
         tmask_ = (uint32_t*)q[2];
         tcnt_ = (unsigned long long*)q[3];
+        tnw_ = (float*)q[4];
     }
     traj_valid_ = q_valid_ = false;
     void* p = nullptr;
@@ -245,7 +248,9 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
                 const float* ys = Y.x ? Y.x : Y.hi;
                 CDMPT_TRY(tile_norms(xs, M, K, ld, tnx_, skip, cx.stream));
                 const float* ny = tnx_;
-                if (!(ys == xs && Nc == M)) {
+                if (ys == wnorm_src_ && Nc == N_ && K == N_) {
+                    ny = tnw_;   // the CG operator's factor: norms taken once per solve
+                } else if (!(ys == xs && Nc == M)) {
                     CDMPT_TRY(tile_norms(ys, Nc, K, ld, tny_, skip, cx.stream));
                     ny = tny_;
                 }
@@ -289,6 +294,19 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
     double* sc = sc_;
     const int init_engine = engine_of(cx, a.init_engine);
     const int iter_engine = engine_of(cx, a.iter_engine);
+    // screened products: the operator's right factor W is fixed for the whole solve, so its
+    // tile norms are taken once here and reused by every product with it
+    struct NormCache {
+        const float** src;
+        ~NormCache() { *src = nullptr; }
+    } norm_cache{&wnorm_src_};
+    if constexpr (sizeof(T) == 4) {
+        if (screen_tau_ > 0.f && tnw_ && a.W) {
+            const float* w = a.W->x ? a.W->x : a.W->hi;
+            CDMPT_TRY(tile_norms(w, N_, N_, ld, tnw_, nullptr, cx.stream));
+            wnorm_src_ = w;
+        }
+    }
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc, 0, CG_NSLOTS * sizeof(double), cx.stream));
     if (a.x0) {
         if (X != a.x0->x || a.x0_scale != 1.0)

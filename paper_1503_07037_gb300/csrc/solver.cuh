@@ -207,6 +207,8 @@ private:
     float* tnx_ = nullptr;
     float* tny_ = nullptr;
     uint32_t* tmask_ = nullptr;   // slice mask of the current product
+    float* tnw_ = nullptr;        // norms of the fixed right factor of the running CG solve
+    const float* wnorm_src_ = nullptr;   // that factor's data while tnw_ holds its norms
     unsigned long long* tcnt_ = nullptr;
     float screen_tau_ = 0.f;
     int cur_[3] = {0, 0, 0};
