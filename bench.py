@@ -43,7 +43,7 @@ WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
 # DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
 # profiles/ (per engine); None until the kernel's counters are re-taken after a change
-TRAFFIC = {2: None, 3: 996.2e6}   # per launch at N = 4096 (3xTF32 captured on the current kernel)
+TRAFFIC = {2: None, 3: 995.9e6}   # per launch at N = 4096 (3xTF32 captured on the current kernel)
 
 
 def dist_env():
