@@ -492,11 +492,12 @@ def run_chain(pkg, pk):
     return out
 
 
-def run_screened(pkg, tau=1e-8, sizes=(8192, 16384)):
+def run_screened(pkg, tau=1e-8, sizes=(4096, 8192, 16384)):
     """Block-sparse screened products (opts.screen_tau) on the Anderson-disordered 1D chain,
     beta 10, n 12, mixed precision: one dense and one screened solve per size after a warm-up
     of each, timed with CUDA events around the solve; the fraction of 128 x 32 k-slices
-    the screened products computed, and the screened-vs-dense change of alpha and P1."""
+    the screened products computed, the screened-vs-dense change of alpha and P1, and (as in
+    Fig. 3) the number of elements above 1e-5 in the screened P0, P1 and P2."""
     import numpy as np
     import torch
 
@@ -514,7 +515,7 @@ def run_screened(pkg, tau=1e-8, sizes=(8192, 16384)):
                 e1 = torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record()
-                r = h.solve(p.beta, p.nocc, p.n, want_P0=False)
+                r = h.solve(p.beta, p.nocc, p.n)
                 e1.record()
                 torch.cuda.synchronize()
                 st = h.stats()
@@ -522,10 +523,17 @@ def run_screened(pkg, tau=1e-8, sizes=(8192, 16384)):
                               "P1": r["P1"][0].cpu().numpy(),
                               "computed": st["screen_slices_computed"],
                               "examined": st["screen_slices_examined"]}
+                if label == "screened":
+                    # Fig. 3: elements above the paper's threshold of 1e-5 in P0, P1 and P2
+                    P2 = h.response2(want_grad=False)["P2"][0]
+                    res[label]["nnz"] = {k: int((m.abs() > 1e-5).sum())
+                                         for k, m in (("P0", r["P0"]), ("P1", r["P1"][0]),
+                                                      ("P2", P2))}
         d, s_ = res["dense"], res["screened"]
         out["sizes"][str(N)] = {
             "dense_s": d["s"], "screened_s": s_["s"], "speedup": d["s"] / s_["s"],
             "slices_computed_frac": s_["computed"] / s_["examined"] if s_["examined"] else None,
+            "nnz_above_1e-5": s_["nnz"],
             "alpha_rel_change": abs(s_["alpha"] - d["alpha"]) / abs(d["alpha"]),
             "P1_rel_change": float(np.linalg.norm(s_["P1"] - d["P1"]) / np.linalg.norm(d["P1"]))}
     return out
@@ -628,7 +636,7 @@ def main():
                     help="skip the screened-product (block-sparse) chain measurement")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the one-step runs of the other precisions")
-    ap.add_argument("--screen-sizes", default="8192,16384",
+    ap.add_argument("--screen-sizes", default="4096,8192,16384",
                     help="chain sizes of the screened-product measurement")
     ap.add_argument("--screened-only", action="store_true",
                     help="run only the screened-product chain measurement (one JSON line)")
