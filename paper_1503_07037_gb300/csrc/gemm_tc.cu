@@ -27,8 +27,8 @@
 // tiles is at most tau, as recorded in a per-tile bit mask built before the launch
 // (screen_mask). Producer, MMA issuer and epilogue read the same mask words, so
 // they walk the same sequence of slices; a tile with no slice left is written by the
-// epilogue from a zero accumulator without touching TMEM or a barrier, and chunks
-// group the remaining slices.
+// epilogue as beta C + gamma I with coalesced stores (epi_fill_zero_tile), without
+// touching TMEM or a barrier, and chunks group the remaining slices.
 //
 // Every mbarrier wait is bounded (about 2 s of %globaltimer). On timeout a
 // thread records the error, raises a shared abort flag that ends the other
@@ -137,6 +137,44 @@ __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
     r.n0 = 0;   // set by the caller, which knows BN
     r.num_k = (pr->K + BK - 1) / BK;
     return r;
+}
+
+// Epilogue of a tile whose product is zero (every k-slice screened out): D = beta C + gamma I
+// over the tile and, for a symmetric result off the diagonal, over its mirror. Without TMEM
+// the lanes need not own rows: warps take rows and lanes 16-byte column groups, so every
+// store is coalesced (the mirror gets its own row-major pass, C and E being symmetric). With
+// transposed placement the lanes take rows instead, which the placement turns into
+// consecutive columns. Returns the D * E contribution of the lane's elements.
+template <int BN>
+__device__ double epi_fill_zero_tile(const EpiParams<float>& p, int m0, int n0, bool diag, int q,
+                                     int lane) {
+    double dsum = 0.0;
+    if (p.trans_block > 0) {
+        for (int j = q; j < BN && n0 + j < p.N; j += 4)
+            for (int i = lane; i < BM && m0 + i < p.M; i += 32)
+                dsum += (double)epi_apply(p, m0 + i, n0 + j, 0.f);
+        return dsum;
+    }
+    EpiParams<float> f = p;
+    f.sym = 0;
+    const bool vec4 = epi_vec4_ok(f);
+    auto pass = [&](int r0, int c0, int rows, int cols) {
+        for (int i = q; i < rows && r0 + i < f.M; i += 4) {
+            const int m = r0 + i;
+            for (int c = lane * 4; c < cols; c += 128) {
+                const int n = c0 + c;
+                if (vec4 && n + 4 <= f.N) {
+                    dsum += (double)epi_apply4(f, m, n, 0.f, 0.f, 0.f, 0.f);
+                } else {
+                    for (int t = 0; t < 4 && n + t < f.N; ++t)
+                        dsum += (double)epi_apply(f, m, n + t, 0.f);
+                }
+            }
+        }
+    };
+    pass(m0, n0, BM, BN);
+    if (p.sym && !diag) pass(n0, m0, BN, BM);
+    return dsum;
 }
 
 // PAIR: a cluster of two CTAs works on vertically adjacent tiles (same B
@@ -453,28 +491,29 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     pend.drain(BN / 4, dsum);
                     finish_pending();
                 }
-                pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
+                if (screen && nch == 0)
+                    dsum += epi_fill_zero_tile<BN>(r.pr->p, r.m0, r.n0, r.diag, q, lane);
+                else
+                    pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
             } else {
-                const bool empty_tile = screen && nch == 0;   // screened to nothing: zero acc
-                const int b = g & 1;
-                if (!empty_tile) {
-                    int w = 1;
-                    if (lane == 0)
-                        w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err,
-                                      DEV_TIMEOUT_ACCUM);
-                    w = __shfl_sync(0xffffffffu, w, 0);
-                    if (!w) break;
-                    tc_fence_after();
+                (void)nch;
+                if constexpr (screen) {
+                    if (nch == 0) {   // every slice screened out: no TMEM, no barrier
+                        dsum += epi_fill_zero_tile<BN>(p, r.m0, r.n0, r.diag, q, lane);
+                        continue;
+                    }
                 }
+                const int b = g & 1;
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) break;
+                tc_fence_after();
 #pragma unroll 1
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     uint32_t rr[32];
-                    if (!empty_tile) {
-                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) rr[j] = 0u;
-                    }
+                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
                     if (m < p.M && p.sym) {
                         float local = 0.f;
                         const int nb = r.n0 + c0;
@@ -514,12 +553,10 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                         dsum += (double)local;
                     }
                 }
-                if (!empty_tile) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[b]);
-                    ++g;
-                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+                ++g;
             }
             if constexpr (GROUPED && KCH == 0) {
                 // each problem has its own dot target: flush per tile
