@@ -177,12 +177,8 @@ __device__ double epi_fill_zero_tile(const EpiParams<float>& p, int m0, int n0, 
     return dsum;
 }
 
-// PAIR: a cluster of two CTAs works on vertically adjacent tiles (same B
-// columns); each CTA loads its own A tile and half of the B tile, multicast to
-// both, so each SM fetches half as many B bytes. Stage reuse then waits for
-// both CTAs' MMAs (empty barriers count two commits).
-template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool PAIR = false,
-          bool SCREEN = false>
+// Every CTA loads its own A and B tiles (no cluster, no multicast).
+template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool SCREEN = false>
 __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
@@ -250,14 +246,13 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         return smem + s * C::STAGE_BYTES + C::PAIR_BYTES + C::A_BYTES;
     };
 
-    const uint32_t rank = PAIR ? cluster_rank() : 0;
-    // tile t of this CTA: single CTAs stride over tiles, pairs over tile pairs
-    const int t_first = PAIR ? (int)(blockIdx.x / 2) * 2 + (int)rank : (int)blockIdx.x;
-    const int t_step = PAIR ? (int)gridDim.x : (int)gridDim.x;
+    // tile t of this CTA: CTAs stride over the tiles
+    const int t_first = (int)blockIdx.x;
+    const int t_step = (int)gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], PAIR ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < NB; ++a) {
             mbar_init(&tfull[a], 1);
@@ -274,7 +269,6 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     if (warp == 1) tmem_alloc(tmem_holder, kTmemCols);
     tc_fence_before();
     __syncthreads();
-    if constexpr (PAIR) cluster_sync();   // peer barriers initialised before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
 
@@ -323,20 +317,9 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                     tma_load_2d(stage_a(s), r.mx, kb * BK, r.m0, &full[s]);
                     if constexpr (PASSES == 3)
                         tma_load_2d(stage_alo(s), r.mxl, kb * BK, r.m0, &full[s]);
-                    if constexpr (PAIR) {
-                        // this CTA's half of the B box, into both CTAs
-                        const int half = BN / 2;
-                        const uint32_t off = rank * (uint32_t)(C::B_BYTES / 2);
-                        tma_load_2d_mc(stage_b(s) + off, r.my, kb * BK, r.n0 + (int)rank * half,
-                                       &full[s], (uint16_t)0x3);
-                        if constexpr (PASSES == 3)
-                            tma_load_2d_mc(stage_blo(s) + off, r.myl, kb * BK,
-                                           r.n0 + (int)rank * half, &full[s], (uint16_t)0x3);
-                    } else {
-                        tma_load_2d(stage_b(s), r.my, kb * BK, r.n0, &full[s]);
-                        if constexpr (PASSES == 3)
-                            tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
-                    }
+                    tma_load_2d(stage_b(s), r.my, kb * BK, r.n0, &full[s]);
+                    if constexpr (PASSES == 3)
+                        tma_load_2d(stage_blo(s), r.myl, kb * BK, r.n0, &full[s]);
                     ++it;
                 }
             }
@@ -401,10 +384,7 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                             }
                         }
                         issued = true;
-                        if constexpr (PAIR)
-                            mma_commit_mc(&empty[s], (uint16_t)0x3);
-                        else
-                            mma_commit(&empty[s]);
+                        mma_commit(&empty[s]);
                     }
                     if (!ok) break;
                     mma_commit(&tfull[b]);
@@ -585,7 +565,6 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
-    if constexpr (PAIR) cluster_sync();   // no CTA leaves while its peer may still signal it
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -598,7 +577,7 @@ cdmpt_status set_smem_attr() {
     using C = Cfg<BN, STAGES, PASSES>;
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, PASSES, KCH, GROUPED, false, SCREEN>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, PASSES, KCH, GROUPED, SCREEN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) {
             set_error(std::string("tcgen05 GEMM smem attribute: ") + cudaGetErrorString(e));
@@ -645,7 +624,7 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     pr.p.sym = sym ? 1 : 0;
     const int tiles = sym ? pr.num_mt * (pr.num_mt + 1) / 2 : pr.num_mt * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_tc<BN, STAGES, PASSES, KCH, false, false, SCREEN><<<grid, C::THREADS, C::SMEM, s>>>(
+    k_gemm_tc<BN, STAGES, PASSES, KCH, false, SCREEN><<<grid, C::THREADS, C::SMEM, s>>>(
         mx, my, mxl, myl, pr, nullptr, 1, tiles, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -656,93 +635,8 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     return CDMPT_OK;
 }
 
-// Cluster-pair launch (B multicast); needs an even number of M tiles.
-template <int BN, int STAGES, int PASSES, int KCH>
-cdmpt_status launch_pair(int M, int N, int K, const float* X, const float* Xl, int ldx,
-                         const float* Y, const float* Yl, int ldy, const EpiParams<float>& p,
-                         const double* skip, cudaStream_t s) {
-    using C = Cfg<BN, STAGES, PASSES>;
-    auto kern = k_gemm_tc<BN, STAGES, PASSES, KCH, false, true>;
-    static int max_clusters = 0;
-    if (max_clusters == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-        cudaLaunchConfig_t q = {};
-        q.gridDim = dim3(2 * sm_count() / 2);
-        q.blockDim = dim3(C::THREADS);
-        q.dynamicSmemBytes = C::SMEM;
-        cudaLaunchAttribute a;
-        a.id = cudaLaunchAttributeClusterDimension;
-        a.val.clusterDim.x = 2;
-        a.val.clusterDim.y = 1;
-        a.val.clusterDim.z = 1;
-        q.attrs = &a;
-        q.numAttrs = 1;
-        int n = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
-        if (e != cudaSuccess || n < 1) {
-            cudaGetLastError();
-            set_error("tcgen05 pair GEMM: no resident cluster of two");
-            return CDMPT_ERR_UNSUPPORTED;
-        }
-        max_clusters = n;
-    }
-    CUtensorMap mx, my, mxl, myl;
-    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, BN / 2) ||
-        !make_map(&mxl, Xl, M, K, ldx, BM) || !make_map(&myl, Yl, N, K, ldy, BN / 2)) {
-        set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
-        return CDMPT_ERR_ARG;
-    }
-    GemmProblem pr;
-    pr.p = p;
-    pr.K = K;
-    pr.tile_begin = 0;
-    pr.num_mt = (M + BM - 1) / BM;
-    pr.skip = skip;
-    pr.maps = nullptr;
-    pr.mask = nullptr;   // pairs share B tiles: never screened
-    pr.nnt = pr.nmw = 0;
-    pr.counts = nullptr;
-    const int tiles = pr.num_mt * ((N + BN - 1) / BN);
-    const int pairs = tiles / 2;
-    const int clusters = pairs < max_clusters ? pairs : max_clusters;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * clusters);
-    cfg.blockDim = dim3(C::THREADS);
-    cfg.dynamicSmemBytes = C::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute a;
-    a.id = cudaLaunchAttributeClusterDimension;
-    a.val.clusterDim.x = 2;
-    a.val.clusterDim.y = 1;
-    a.val.clusterDim.z = 1;
-    cfg.attrs = &a;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, pr,
-                                       (const GemmProblem*)nullptr, 1, tiles, device_error_word());
-    count_launch();
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error(std::string("tcgen05 pair GEMM launch: ") + cudaGetErrorString(e));
-        return CDMPT_ERR_CUDA;
-    }
-    return CDMPT_OK;
-}
-
-bool pair_enabled() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("CDMPT_PAIR");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
-
-// Kernel family for single (non-grouped) products: one SM per tile (with
-// cluster-pair multicast when enabled) or the two-SM MMA (cta_group::2, 256-row
-// tiles). Default: two-SM for TF32, one-SM for 3xTF32 (measured fastest);
+// Kernel family for single (non-grouped) products: one SM per tile or the
+// two-SM MMA (cta_group::2, 256-row tiles). Default: two-SM for TF32, one-SM for 3xTF32 (measured fastest);
 // CDMPT_TC_MODE=1sm|2sm forces one family.
 bool use_2sm(bool three) {
     static int v = -2;
@@ -934,13 +828,7 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
     if (use_2sm(three) && M > BM)
         return gemm_tc_2sm(three, split_chunk(), M, N, K, xh, three ? X.lo : xh, ldx, yh, three ? Y.lo : yh,
                            ldy, p, skip, s);
-    const bool pair = pair_enabled() && ((M + BM - 1) / BM) % 2 == 0;
-    if (!three) {
-        if (pair) return launch_pair<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
-        return launch<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
-    }
-    if (pair && split_chunk() == 2)
-        return launch_pair<128, 3, 3, 2>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
+    if (!three) return launch<256, 4, 1, 0>(M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
     switch (split_chunk()) {
         case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
         case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);

@@ -1,5 +1,5 @@
 // Inline-PTX building blocks shared by the tcgen05 GEMM kernels (sm_103a):
-// mbarriers with bounded waits, TMA tile loads (plain and cluster multicast),
+// mbarriers with bounded waits, TMA tile loads (each CTA its own tiles),
 // tcgen05 TMEM allocation, MMA issue, commit and TMEM loads, the shared-memory
 // and instruction descriptors, and the host-side tensor-map encoder.
 #pragma once
@@ -111,17 +111,6 @@ __device__ __forceinline__ void cluster_sync() {
                      "memory");
 }
 
-// TMA load of one box into the same shared-memory offset of every CTA in
-// mask, each CTA's mbarrier at the same offset receiving the transaction bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
-                                               uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 // Orders the tensormap proxy after the generic writes (a host copy) that put a
 // tensor map into global memory, before TMA first reads it.
 __device__ __forceinline__ void acquire_map(const CUtensorMap* map) {
@@ -187,16 +176,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
-        : "memory");
-}
-
-// Arrives on the mbarrier at the same offset in every CTA of mask once this
-// thread's prior tcgen05 operations complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
         : "memory");
 }
 
