@@ -38,10 +38,12 @@ the canonical shifts mu2 and mu3 from Tr P2 = Tr P3 = 0 (Algorithm 1), and
 the free-energy terms Omega^(3) = Tr[H1 P2]/3 and Omega^(4) = Tr[H1 P3]/4 of
 Eq. (Resp_0).
 
-``literal_recursion``, ``literal_canonical``, ``literal_recursion2`` and
-``literal_recursion3`` restate Algorithm 1 (orders 1 to 3) in the paper's
-X-notation with dense linear solves. They exist to pin the closed forms above
-against the iteration the paper prints.
+``series_recursion`` evaluates the recursion of Eq. (Rec_F_2) itself on
+truncated power series in lambda (every product and inverse in the ring of
+matrix polynomials), so its Taylor coefficients are the response orders of
+Eq. (P_resp) computed without eigenvalues; ``canonical_newton`` adds the
+Newton steps of Eq. (NewtRaphs) on mu and mu1. They pin the closed forms above
+against the iteration of the map.
 """
 from __future__ import annotations
 
@@ -259,56 +261,76 @@ def rel_frobenius(A, B):
 
 
 # ----------------------------------------------------------------------------
-# Algorithm 1 restated in the paper's X-notation (first order), dense solves
+# the recursion of Eq. (Rec_F_2) on truncated power series in lambda
 # ----------------------------------------------------------------------------
 
-def literal_recursion(H0, H1, beta, mu, mu1, M):
-    """One pass of the inner loop of Algorithm 1 for orders 0 and 1.
+def _series_mul(A, B):
+    """Cauchy product of two matrix power series in lambda, truncated to len(A) terms."""
+    return [sum(A[i] @ B[k - i] for i in range(k + 1)) for k in range(len(A))]
 
-    X_0^(0) = I/2 - 2^-(M+2) beta (H0 - mu I);  X_0^(1) = -2^-(M+2) beta (H1 - mu1 I).
-    For n = 1..M:  T X_n^(0) = C^(0),  T X_n^(1) = C^(1) + B^(1) X_n^(0), with
-    T = 2 X^(0) (X^(0) - I) + I,  C^(0) = X^(0) X^(0),
-    C^(1) = X^(0) X^(1) + X^(1) X^(0),  B^(1) = 2 (X^(1) - C^(1)),
-    all taken at step n-1. Returns (X_M^(0), X_M^(1), condition numbers of T).
+
+def _series_inv(A):
+    """Inverse of a matrix power series with invertible A[0]: B[0] = A[0]^-1 and
+    A[0] B[k] = -sum_{j=1..k} A[j] B[k-j], from the coefficients of A(lambda) B(lambda) = I."""
+    B = [np.linalg.inv(A[0])]
+    for k in range(1, len(A)):
+        B.append(-np.linalg.solve(A[0], sum(A[j] @ B[k - j] for j in range(1, k + 1))))
+    return B
+
+
+def series_recursion(Hs, beta, mus, M):
+    """X_M(lambda) of Eq. (Rec_F_2) as a truncated power series in lambda.
+
+    H(lambda) = sum_k lambda^k Hs[k] (Eq. H_prt) and mu(lambda) = sum_k lambda^k mus[k];
+    X_0(lambda) = I/2 - 2^-(M+2) beta (H(lambda) - mu(lambda) I), then M applications of the
+    map X -> X^2 [X^2 + (I - X)^2]^-1, every product and inverse taken in the ring of matrix
+    polynomials in lambda truncated after lambda^m, m = len(Hs) - 1. Coefficient k of X_M is
+    the k-th order density matrix response P^(k) of Eq. (P_resp) at the given mu^(k). This is
+    a direct evaluation of the Taylor coefficients of the map, independent of how Algorithm 1
+    arranges them. Hs[k] or mus[k] may be 0 (zero term).
+
+    Returns (list of the m + 1 coefficients of X_M, spectral condition numbers of the
+    order-0 denominator X^2 + (I - X)^2 at each application).
     """
+    H0 = np.asarray(Hs[0], dtype=np.float64)
     N = H0.shape[0]
     I = np.eye(N)
     s = 2.0 ** (-(M + 2)) * beta
-    X0 = 0.5 * I - s * (H0 - mu * I)
-    X1 = -s * (H1 - mu1 * I)
+    X = []
+    for k, Hk in enumerate(Hs):
+        Hk = np.zeros((N, N)) if (np.isscalar(Hk) and Hk == 0) else np.asarray(Hk, dtype=np.float64)
+        term = -s * (Hk - float(mus[k]) * I)
+        X.append(0.5 * I + term if k == 0 else term)
     conds = []
     for _ in range(M):
-        T = 2.0 * X0 @ (X0 - I) + I
-        C0 = X0 @ X0
-        C1 = X0 @ X1 + X1 @ X0
-        B1 = 2.0 * (X1 - C1)
-        ev = np.linalg.eigvalsh(0.5 * (T + T.T))
+        X2 = _series_mul(X, X)
+        IX = [I - X[0]] + [-x for x in X[1:]]
+        den = [a + b for a, b in zip(X2, _series_mul(IX, IX))]
+        ev = np.linalg.eigvalsh(0.5 * (den[0] + den[0].T))
         conds.append(float(ev[-1] / ev[0]))
-        X0n = np.linalg.solve(T, C0)
-        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
-        X0, X1 = X0n, X1n
-    return X0, X1, conds
+        X = _series_mul(X2, _series_inv(den))
+    return X, conds
 
 
-def literal_canonical(H0, H1, beta, nocc, M, mu0=0.0, tol=1e-9, maxit=100):
-    """The outer loop of Algorithm 1 (orders 0 and 1) with P_mu = beta P0 (I - P0).
-
-    mu  <- mu  + (N_occ - Tr P0) / Tr P_mu
-    mu1 <- mu1 - Tr P1 / Tr P_mu
-    until |Tr P0 - N_occ| + |Tr P1| <= tol.
+def canonical_newton(H0, H1, beta, nocc, M, mu0=0.0, tol=1e-9, maxit=100):
+    """mu and mu1 of the canonical conditions Tr P0 = N_occ and Tr P1 = 0 by Newton steps
+    with the slope of Eq. (NewtRaphs), Tr P_mu = beta Tr[P0 (I - P0)] (exact only as
+    M -> infinity), on the series evaluation of Eq. (Rec_F_2):
+      mu  <- mu  + (N_occ - Tr P0) / Tr P_mu,   mu1 <- mu1 - Tr P1 / Tr P_mu,
+    until |Tr P0 - N_occ| + |Tr P1| <= tol. Returns (P0, P1, mu, mu1, iterations); raises
+    RuntimeError when maxit steps do not get there.
     """
     mu, mu1 = float(mu0), 0.0
     for it in range(maxit):
-        P0, P1, _ = literal_recursion(H0, H1, beta, mu, mu1, M)
-        tr0 = np.trace(P0)
-        tr1 = np.trace(P1)
-        err = abs(tr0 - nocc) + abs(tr1)
-        if err <= tol:
+        X, _ = series_recursion([H0, H1], beta, [mu, mu1], M)
+        P0, P1 = X[0], X[1]
+        tr0, tr1 = np.trace(P0), np.trace(P1)
+        if abs(tr0 - nocc) + abs(tr1) <= tol:
             return P0, P1, mu, mu1, it
-        trPmu = beta * np.trace(P0 @ (np.eye(P0.shape[0]) - P0))
-        mu = mu + (nocc - tr0) / trPmu
-        mu1 = mu1 - tr1 / trPmu
-    raise RuntimeError("Algorithm 1 occupation loop did not converge")
+        slope = beta * np.trace(P0 @ (np.eye(P0.shape[0]) - P0))
+        mu = mu + (nocc - tr0) / slope
+        mu1 = mu1 - tr1 / slope
+    raise RuntimeError("canonical Newton iteration did not converge")
 
 
 def pade_f(x, m):
@@ -478,34 +500,6 @@ def response2(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
                        for d in range(H1.shape[0])])
     out.update(P2=P2, mu2=mu2, grad_alpha=grad, omega3=omega3)
     return out
-
-
-def literal_recursion2(H0, H1, beta, mu, mu1, mu2, M, H2=None):
-    """The inner loop of Algorithm 1 for orders 0, 1 and 2 (H^(2) = 0), dense solves.
-
-    X_0^(2) = -2^-(M+2) beta (H^(2) - mu2 I) = 2^-(M+2) beta mu2 I, and per step
-    T X^(2) = C^(2) + B^(2) X_n^(0) + B^(1) X_n^(1), with
-    C^(2) = X^(0) X^(2) + X^(1) X^(1) + X^(2) X^(0) and B^(2) = 2 (X^(2) - C^(2)).
-    Returns (X_M^(0), X_M^(1), X_M^(2)).
-    """
-    N = H0.shape[0]
-    I = np.eye(N)
-    s = 2.0 ** (-(M + 2)) * beta
-    X0 = 0.5 * I - s * (H0 - mu * I)
-    X1 = -s * (H1 - mu1 * I)
-    X2 = -s * ((0.0 if H2 is None else H2) - mu2 * I)
-    for _ in range(M):
-        T = 2.0 * X0 @ (X0 - I) + I
-        C0 = X0 @ X0
-        C1 = X0 @ X1 + X1 @ X0
-        C2 = X0 @ X2 + X1 @ X1 + X2 @ X0
-        B1 = 2.0 * (X1 - C1)
-        B2 = 2.0 * (X2 - C2)
-        X0n = np.linalg.solve(T, C0)
-        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
-        X2n = np.linalg.solve(T, C2 + B2 @ X0n + B1 @ X1n)
-        X0, X1, X2 = X0n, X1n, X2n
-    return X0, X1, X2
 
 
 # ----------------------------------------------------------------------------
@@ -687,38 +681,6 @@ def response3(H0, H1, beta, nocc, n: Optional[int] = None, kind: str = "rec", ei
                        for d in range(H1.shape[0])])
     out.update(P3=P3, mu3=mu3, omega4=omega4)
     return out
-
-
-def literal_recursion3(H0, H1, beta, mu, mu1, mu2, mu3, M, H2=None, H3=None):
-    """The inner loop of Algorithm 1 for orders 0 to 3 (H^(2) = H^(3) = 0), dense solves.
-
-    X_0^(k) = 2^-(M+2) beta mu_k I for k = 2, 3, and per step
-    T X^(3) = C^(3) + B^(3) X_n^(0) + B^(2) X_n^(1) + B^(1) X_n^(2), with
-    C^(3) = sum_{i+j=3} X^(i) X^(j) and B^(3) = 2 (X^(3) - C^(3)).
-    Returns (X_M^(0), X_M^(1), X_M^(2), X_M^(3)).
-    """
-    N = H0.shape[0]
-    I = np.eye(N)
-    s = 2.0 ** (-(M + 2)) * beta
-    X0 = 0.5 * I - s * (H0 - mu * I)
-    X1 = -s * (H1 - mu1 * I)
-    X2 = -s * ((0.0 if H2 is None else H2) - mu2 * I)
-    X3 = -s * ((0.0 if H3 is None else H3) - mu3 * I)
-    for _ in range(M):
-        T = 2.0 * X0 @ (X0 - I) + I
-        C0 = X0 @ X0
-        C1 = X0 @ X1 + X1 @ X0
-        C2 = X0 @ X2 + X1 @ X1 + X2 @ X0
-        C3 = X0 @ X3 + X1 @ X2 + X2 @ X1 + X3 @ X0
-        B1 = 2.0 * (X1 - C1)
-        B2 = 2.0 * (X2 - C2)
-        B3 = 2.0 * (X3 - C3)
-        X0n = np.linalg.solve(T, C0)
-        X1n = np.linalg.solve(T, C1 + B1 @ X0n)
-        X2n = np.linalg.solve(T, C2 + B2 @ X0n + B1 @ X1n)
-        X3n = np.linalg.solve(T, C3 + B3 @ X0n + B2 @ X1n + B1 @ X2n)
-        X0, X1, X2, X3 = X0n, X1n, X2n, X3n
-    return X0, X1, X2, X3
 
 
 # ----------------------------------------------------------------------------

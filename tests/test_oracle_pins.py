@@ -73,26 +73,27 @@ def test_trace_symmetry_spectrum(kind, n):
 
 
 # --------------------------------------------------------------------------
-# Algorithm 1, first order: closed form vs the printed iteration
+# first order: closed form vs the iterated map of Eq. Rec_F_2 on power series in lambda
 # --------------------------------------------------------------------------
 
-def test_closed_form_equals_literal_recursion():
-    """P0, P1 of kind='rec' == Algorithm 1 (X-notation, dense solves) at the same mu, mu1."""
+def test_closed_form_equals_series_recursion():
+    """P0, P1 of kind='rec' == the first two Taylor coefficients in lambda of n applications of
+    Eq. Rec_F_2's map to X_0(lambda), at the same mu, mu1."""
     p = syn.workload("chain64")
     r = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    X0, X1, conds = o.literal_recursion(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], p.n)
+    (X0, X1), conds = o.series_recursion([p.H0, p.H1[0]], p.beta, [r["mu"], r["mu1"][0]], p.n)
     assert o.rel_frobenius(X0, r["P0"]) < 1e-12
     assert o.rel_frobenius(X1, r["P1"][0]) < 1e-11
-    # T is SPD with spectral condition number <= 2 at every step (Sec. II)
+    # the denominator X^2 + (I - X)^2 (the paper's T) is SPD with condition number <= 2 (Sec. II)
     assert max(conds) <= 2.0 + 1e-12 and min(conds) >= 1.0
 
 
-def test_literal_canonical_loop_fixed_point():
-    """Algorithm 1's Newton loop with P_mu = beta P(I-P) reaches the closed-form mu, mu1."""
+def test_canonical_newton_fixed_point():
+    """Newton steps of Eq. NewtRaphs with P_mu = beta P(I-P) reach the closed-form mu, mu1."""
     H0, H1 = _dimer_chain(24)
     beta, nocc, n = 6.0, 12.0, 8
     r = o.solve(H0, H1, beta, nocc, n=n, kind="rec")
-    P0, P1, mu, mu1, it = o.literal_canonical(H0, H1, beta, nocc, n, mu0=0.3)
+    P0, P1, mu, mu1, it = o.canonical_newton(H0, H1, beta, nocc, n, mu0=0.3)
     assert abs(mu - r["mu"]) < 1e-11
     assert abs(mu1 - r["mu1"][0]) < 1e-9
     assert o.rel_frobenius(P1, r["P1"][0]) < 1e-10
@@ -369,26 +370,26 @@ def test_p2_equals_finite_difference_of_p1(kind, n):
     assert np.abs(r["P2"][0] - r["P2"][0].T).max() < 1e-12 * np.abs(r["P2"][0]).max()
 
 
-def test_p2_equals_literal_algorithm1_second_order():
-    """The closed form == Algorithm 1's order-2 recursion (dense solves), chain64, and
-    the oracle's mu2 makes the literal Tr X^(2) vanish (the canonical condition)."""
+def test_p2_equals_series_recursion_second_order():
+    """The closed form == the lambda^2 coefficient of the iterated map (chain64), and the
+    oracle's mu2 makes its trace vanish (the canonical condition)."""
     p = syn.workload("chain64")
     r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    X0, X1, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0],
-                                      r["mu2"][0], p.n)
+    (X0, X1, X2), _ = o.series_recursion([p.H0, p.H1[0], 0], p.beta,
+                                         [r["mu"], r["mu1"][0], r["mu2"][0]], p.n)
     assert o.rel_frobenius(X1, r["P1"][0]) < 1e-10
     assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
     assert abs(np.trace(X2)) < 1e-10 * np.linalg.norm(X2)
 
 
 def test_p2_degenerate_clean_lattice():
-    """Exactly degenerate levels (clean periodic lattice): the close-pair path against
-    Algorithm 1's order-2 recursion."""
+    """Exactly degenerate levels (clean periodic lattice): the close-pair path against the
+    lambda^2 coefficient of the iterated map."""
     p = syn.cubic_lattice((4, 4, 4), seed=1, beta=6.0, n=12, onsite_sigma=0.0,
                           bond_disorder=0.0)
     r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    _, _, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0],
-                                    r["mu2"][0], p.n)
+    (_, _, X2), _ = o.series_recursion([p.H0, p.H1[0], 0], p.beta,
+                                       [r["mu"], r["mu1"][0], r["mu2"][0]], p.n)
     assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
 
 
@@ -437,14 +438,14 @@ def test_second_order_pins_catch_planted_mistakes(monkeypatch):
     assert err() > 1e-3
 
 
-def test_grand_canonical_orders_match_literal_recursion():
+def test_grand_canonical_orders_match_series_recursion():
     """Fixed mu (the grand-canonical scheme beside Algorithm 1): P0, P1 and P2 of the closed
-    forms equal Algorithm 1's recursion with mu1 = mu2 = 0 (dense solves), chain64."""
+    forms equal the coefficients of the iterated map with mu1 = mu2 = 0, chain64."""
     p = syn.workload("chain64")
     mu = o.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")["mu"] + 0.05
     r = o.response2(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", canonical=False, mu=mu)
     assert r["mu1"][0] == 0.0 and r["mu2"][0] == 0.0
-    X0, X1, X2 = o.literal_recursion2(p.H0, p.H1[0], p.beta, mu, 0.0, 0.0, p.n)
+    (X0, X1, X2), _ = o.series_recursion([p.H0, p.H1[0], 0], p.beta, [mu, 0.0, 0.0], p.n)
     assert o.rel_frobenius(X0, r["P0"]) < 1e-12
     assert o.rel_frobenius(X1, r["P1"][0]) < 1e-10
     assert o.rel_frobenius(X2, r["P2"][0]) < 1e-10
@@ -498,13 +499,13 @@ def test_third_divided_difference_quadrature():
                - o.occupation_third_derivative(x, mu, beta, n) / 6.0) < 1e-14
 
 
-def test_p3_equals_literal_algorithm1_third_order():
-    """The closed form == Algorithm 1's order-3 recursion (dense solves), chain64, and
-    the oracle's mu3 makes the literal Tr X^(3) vanish (the canonical condition)."""
+def test_p3_equals_series_recursion_third_order():
+    """The closed form == the lambda^3 coefficient of the iterated map (chain64), and the
+    oracle's mu3 makes its trace vanish (the canonical condition)."""
     p = syn.workload("chain64")
     r = o.response3(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    X = o.literal_recursion3(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], r["mu2"][0],
-                             r["mu3"][0], p.n)
+    X, _ = o.series_recursion([p.H0, p.H1[0], 0, 0], p.beta,
+                              [r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0]], p.n)
     assert o.rel_frobenius(X[2], r["P2"][0]) < 1e-10
     assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-10
     assert abs(np.trace(X[3])) < 1e-10 * np.linalg.norm(X[3])
@@ -512,11 +513,11 @@ def test_p3_equals_literal_algorithm1_third_order():
 
 def test_p3_degenerate_clean_lattice():
     """Exactly degenerate levels (clean 4 x 4 x 2 lattice): explicit sums and quadrature agree
-    with the literal recursion."""
+    with the iterated map."""
     p = syn.cubic_lattice((4, 4, 2), seed=0, beta=5.0, n=10, onsite_sigma=0.0, bond_disorder=0.0)
     r = o.response3(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    X = o.literal_recursion3(p.H0, p.H1[0], p.beta, r["mu"], r["mu1"][0], r["mu2"][0],
-                             r["mu3"][0], p.n)
+    X, _ = o.series_recursion([p.H0, p.H1[0], 0, 0], p.beta,
+                              [r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0]], p.n)
     assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-9
 
 
@@ -595,9 +596,9 @@ def test_third_order_pins_catch_planted_mistakes(monkeypatch):
     def err(**kw):
         nonlocal X3
         r = o.response3(H0, H1, beta, nocc, n=n, kind="rec", **kw)
-        if X3 is None:   # the literal recursion at the unplanted oracle's shifts
-            X3 = o.literal_recursion3(H0, H1, beta, r["mu"], r["mu1"][0], r["mu2"][0],
-                                      r["mu3"][0], n)[3]
+        if X3 is None:   # the iterated map at the unplanted oracle's shifts
+            X3 = o.series_recursion([H0, H1, 0, 0], beta,
+                                    [r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0]], n)[0][3]
         return o.rel_frobenius(r["P3"][0], X3)
 
     assert err() < 1e-10
@@ -778,7 +779,7 @@ def test_scc_free_energy_response_rule():
 
 def test_table2_pattern_low_temperature_needs_enough_steps():
     """Tab. 2's qualitative pattern, on a gapped tight-binding chain instead of H2O: at low
-    temperature Algorithm 1's occupation loop (Newton with P_mu = beta P (I - P)) does not
+    temperature the occupation loop (Newton with P_mu = beta P (I - P), Eq. NewtRaphs) does not
     converge with too few recursion steps (beta = 1000: M = 4 and 6 fail, M >= 8 converge),
     while at high temperature every M converges. With M too small X_0 lies far outside
     [0, 1], where x^2 / (x^2 + (1 - x)^2) sends distant levels towards 1/2, so the occupation
@@ -787,11 +788,11 @@ def test_table2_pattern_low_temperature_needs_enough_steps():
     H1 = H1 * 0.05
     for M in (4, 6):
         with pytest.raises(RuntimeError):
-            o.literal_canonical(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
+            o.canonical_newton(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
     for M in (8, 12, 16):
-        o.literal_canonical(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
+        o.canonical_newton(H0, H1, 1000.0, 12.0, M, mu0=0.3, maxit=100)
     for M in (4, 6, 8):
-        o.literal_canonical(H0, H1, 10.0, 12.0, M, mu0=0.3, maxit=100)
+        o.canonical_newton(H0, H1, 10.0, 12.0, M, mu0=0.3, maxit=100)
 
 
 # --------------------------------------------------------------------------
@@ -805,14 +806,15 @@ def _higher_case(N=18, seed=91):
     return H0, H1, _rand_sym(N, seed + 2, 0.05), _rand_sym(N, seed + 3, 0.03)
 
 
-def test_higher_terms_match_literal_algorithm1():
-    """With H2 and H3 the closed forms equal Algorithm 1's recursion of orders 2 and 3, whose
-    traces vanish at the oracle's mu2 and mu3."""
+def test_higher_terms_match_series_recursion():
+    """With H2 and H3 the closed forms equal the lambda^2 and lambda^3 coefficients of the
+    iterated map for H0 + lambda H1 + lambda^2 H2 + lambda^3 H3, whose traces vanish at the
+    oracle's mu2 and mu3."""
     H0, H1, H2, H3 = _higher_case()
     beta, nocc, n = 5.0, 9.0, 10
     r = o.response3(H0, H1[None], beta, nocc, n=n, H2=H2[None], H3=H3[None])
-    X = o.literal_recursion3(H0, H1, beta, r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0], n,
-                             H2=H2, H3=H3)
+    X, _ = o.series_recursion([H0, H1, H2, H3], beta,
+                              [r["mu"], r["mu1"][0], r["mu2"][0], r["mu3"][0]], n)
     assert o.rel_frobenius(X[2], r["P2"][0]) < 1e-10
     assert o.rel_frobenius(X[3], r["P3"][0]) < 1e-10
     assert abs(np.trace(X[2])) < 1e-11 and abs(np.trace(X[3])) < 1e-11
