@@ -74,7 +74,10 @@ typedef enum {
     CDMPT_GEMM_SIMT = 1,      /* CUDA-core FFMA/DFMA tiles */
     CDMPT_GEMM_TC_TF32 = 2,   /* tcgen05 kind::tf32, one pass, FP32 accumulate in TMEM */
     CDMPT_GEMM_TC_3XTF32 = 3, /* tcgen05 kind::tf32, hi/lo split, three passes */
-    CDMPT_GEMM_TC_BF16 = 4    /* tcgen05 kind::f16 on operands rounded to BF16, one pass */
+    CDMPT_GEMM_TC_BF16 = 4,   /* tcgen05 kind::f16 on operands rounded to BF16, one pass */
+    CDMPT_GEMM_TC_OZAKI = 5   /* statistics only (not a gemm_engine choice): Ozaki-sliced BF16
+                                 products of pair-stored operands, the FP64-class refinement
+                                 residuals of the mixed precisions (cdmpt_gemm_pair) */
 } cdmpt_gemm_engine;
 
 typedef struct {
@@ -121,6 +124,17 @@ typedef struct {
                            blocks above the threshold. Storage stays dense. FP32 and
                            MIXED_TF32 with the tcgen05 engines only (ERR_ARG otherwise);
                            0 (the default) keeps every product dense. */
+    int fp64_residual;  /* MIXED_* only: the refinement that recovers accuracy keeps the
+                           0th-order trajectory Z_0 .. Z_n as FP32 pairs (about 48 bits) and
+                           ends with a pass whose step residuals r_k = 2 Z_k - Z_{k+1} A_k
+                           (Algorithm 1's per-step system) and step matrices A_k = I + Z_k^2
+                           come from Ozaki-sliced BF16 tensor-core products accurate to about
+                           2^-31 (cdmpt_gemm_pair) instead of split-TF32 ones. 0 (default):
+                           on the steps whose spectral bound tanh(2^k atanh rho) exceeds
+                           1/2, rho = beta max|lambda - mu| / 2^(n+1) over the Gershgorin
+                           interval (for the earlier steps the split-TF32 residual is already
+                           that accurate, its error carrying the factor ||Z_k||^2); 1: on
+                           every step; -1: no such pass (split-TF32 residuals only). */
 } cdmpt_opts;
 
 typedef struct {
@@ -140,13 +154,15 @@ typedef struct {
     double mu, trace_P0, trace_Q;  /* final mu, Tr P0, Tr dP0/dmu */
     double occupation_error;       /* |Tr P0 - N_occ| + sum_d |Tr P1_d| */
     double seconds;                /* host wall time of the last solve */
-    double engine_ms[5];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
-    int engine_launches[5];        /* timed GEMM launches per engine */
-    double engine_flops[5];        /* algorithmic flops of those launches */
+    double engine_ms[6];           /* GEMM device time per cdmpt_gemm_engine (profile = 1) */
+    int engine_launches[6];        /* timed GEMM launches per engine */
+    double engine_flops[6];        /* algorithmic flops of those launches */
     int cg_iterations_recompute;   /* CG iterations spent recomputing checkpointed segments */
     int checkpoint_stride;         /* stride in use (0: whole trajectory stored) */
     double screen_slices_computed; /* screened products of the last solve: 128 x 32 k-slices */
     double screen_slices_examined; /* multiplied, and all slices of their output tiles */
+    int fp64_residual_passes;      /* refinement passes with Ozaki-sliced (FP64-class) residuals */
+    int fp64_residual_first_step;  /* first step k they covered (n: none) */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -493,6 +509,42 @@ cdmpt_status cdmpt_gemm_f32_split(int engine, int M, int Ncols, int K, const flo
                                   const float* C, int ldc, double gamma, int diag_block,
                                   int trans_block, double* dot, const float* E, int lde,
                                   void* stream);
+
+/* Product of pair-stored FP32 matrices (value = hi + lo) to about 31 bits, the building block
+ * of the FP64-class refinement residual of the mixed precision (the per-step system of
+ * Algorithm 1, T X = RHS, whose residual must be formed beyond FP32 accuracy). The paper has
+ * no such kernel; the method is the error-free slicing of Ozaki et al. on tensor cores
+ * (Mukunoki, Ozaki, Ogita and Imamura): each row of X and of Y is scaled by its own power of
+ * two and cut into five signed 8-bit integer digits stored in BF16 (39 bits), the fifteen
+ * digit products of weight above 2^-40 run on tcgen05 (kind::f16, FP32 accumulation in TMEM)
+ * with the three leading groups summed exactly over every chunk of 256 k, and the epilogue
+ * combines the exact sums in double-float:
+ *   D + Dl = alpha (Xh + Xl)(Yh + Yl)^T + b1 (C1h + C1l) + b2 (C2h + C2l).
+ * X is M x K, Y is Ncols x K (row-major device arrays, leading dimensions ldx, ldy multiples
+ * of 8 elements, 16-byte aligned), C1/C2/D/Dl share ldc and ldd. Xl, Yl, C1h, C1l, C2h, C2l
+ * and Dl may be NULL (a NULL low part is zero; a NULL C term is skipped; Dl NULL: D only).
+ * alpha, b1 and b2 must be powers of two or zero, so every scaling is exact. The error of
+ * D + Dl is about 2^-39 of max_k |x_ik| max_k |y_jk| times sqrt(K). K <= 32768. The digits
+ * of both operands (10 (M + Ncols) ld bytes plus one int per row) are allocated and freed
+ * stream-ordered on the stream. Errors: ERR_ARG, ERR_UNSUPPORTED (not an sm_103 device),
+ * ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_gemm_pair(int M, int Ncols, int K, const float* Xh, const float* Xl, int ldx,
+                             const float* Yh, const float* Yl, int ldy, float* D, float* Dl,
+                             int ldd, double alpha, double b1, const float* C1h, const float* C1l,
+                             double b2, const float* C2h, const float* C2l, int ldc,
+                             void* stream);
+
+/* Check of the failure detection of the device waits (Sec. II of the paper names loss of
+ * convergence as its only failure; the bounded waits of this library have no counterpart in
+ * it). Every mbarrier wait of the tcgen05 kernels gives up after a time limit, records a code
+ * in a device error word, and the next status check of the library returns
+ * CDMPT_ERR_TIMEOUT. This call launches one CTA that waits, through that same bounded wait
+ * with a limit of limit_ms milliseconds, on a barrier that nothing arrives on; no copy or
+ * tensor-core operation is in flight. It returns CDMPT_ERR_TIMEOUT when the wait gave up as
+ * designed (the error word is then cleared, so later calls are unaffected), CDMPT_OK never in
+ * a working build, ERR_ARG for limit_ms outside (0, 1000], ERR_CUDA on a launch failure.
+ * stream: cudaStream_t or NULL. */
+cdmpt_status cdmpt_check_bounded_wait(double limit_ms, void* stream);
 
 /* FP64 counterpart of cdmpt_gemm_f32 on CUDA cores (no alignment rule). */
 cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, const double* Y,

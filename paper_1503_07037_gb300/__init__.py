@@ -8,7 +8,7 @@ from .cdmpt import (  # noqa: F401
     Handle, CdmptError, solve, gemm_f32, gemm_f64, lib, version, default_opts, create,
     set_opts, set_H, solve_raw, polarizability, get_stats, last_error, destroy, EXPORTS,
     LIB_PATH, spectral_bounds, spectral_bounds_noalloc, DensityMatrix, Polarizability, FreeEnergy,
-    Batch, split_tf32, gemm_f32_split, FP64, FP32, MIXED_TF32, MIXED_BF16, GEMM_AUTO, GEMM_SIMT,
+    Batch, split_tf32, gemm_f32_split, gemm_pair, check_bounded_wait, FP64, FP32, MIXED_TF32, MIXED_BF16, GEMM_AUTO, GEMM_SIMT,
     GEMM_TC_TF32,
     GEMM_TC_3XTF32, GEMM_TC_BF16,
 )

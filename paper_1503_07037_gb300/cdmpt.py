@@ -49,6 +49,7 @@ class Opts(ctypes.Structure):
         ("ckpt_stride", ctypes.c_int),
         ("fd_exact", ctypes.c_int),
         ("screen_tau", ctypes.c_double),
+        ("fp64_residual", ctypes.c_int),
     ]
 
 
@@ -81,13 +82,15 @@ class Stats(ctypes.Structure):
         ("mu", ctypes.c_double), ("trace_P0", ctypes.c_double), ("trace_Q", ctypes.c_double),
         ("occupation_error", ctypes.c_double),
         ("seconds", ctypes.c_double),
-        ("engine_ms", ctypes.c_double * 5),
-        ("engine_launches", ctypes.c_int * 5),
-        ("engine_flops", ctypes.c_double * 5),
+        ("engine_ms", ctypes.c_double * 6),
+        ("engine_launches", ctypes.c_int * 6),
+        ("engine_flops", ctypes.c_double * 6),
         ("cg_iterations_recompute", ctypes.c_int),
         ("checkpoint_stride", ctypes.c_int),
         ("screen_slices_computed", ctypes.c_double),
         ("screen_slices_examined", ctypes.c_double),
+        ("fp64_residual_passes", ctypes.c_int),
+        ("fp64_residual_first_step", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -108,7 +111,8 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_gemm_f32_split", "cdmpt_response2", "cdmpt_batch_get_tuning",
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
            "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1",
-           "cdmpt_set_H_orders", "cdmpt_scc_solve2"]
+           "cdmpt_set_H_orders", "cdmpt_scc_solve2", "cdmpt_gemm_pair",
+           "cdmpt_check_bounded_wait"]
 
 
 def lib() -> ctypes.CDLL:
@@ -158,6 +162,8 @@ def lib() -> ctypes.CDLL:
         "cdmpt_split_tf32": (I, [P, ctypes.c_size_t, P, P, P]),
         "cdmpt_gemm_f32_split": (I, [I, I, I, I, P, P, I, P, P, I, P, I, D, D, P, I, D, I, I, P, P, I,
                                      P]),
+        "cdmpt_gemm_pair": (I, [I, I, I, P, P, I, P, P, I, P, P, I, D, D, P, P, D, P, P, I, P]),
+        "cdmpt_check_bounded_wait": (I, [D, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -281,6 +287,26 @@ def gemm_f32_split(Xs, Ys, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, engine="3x
                                       None, None, 0, _stream_ptr(stream)))
 
 
+def gemm_pair(Xh, Xl, Yh, Yl, D, Dl=None, alpha=1.0, b1=0.0, C1=(None, None), b2=0.0,
+              C2=(None, None), K=None, stream=None):
+    """Ozaki-sliced product of pair-stored FP32 matrices (cdmpt_gemm_pair):
+    D (+ Dl) = alpha (Xh + Xl)(Yh + Yl)^T + b1 C1 + b2 C2 with C1, C2 given as (hi, lo)
+    pairs. All tensors are float32 CUDA tensors with row strides that are multiples of 8;
+    any low part may be None. alpha, b1, b2 are powers of two or zero."""
+    M, Ncols = Xh.shape[0], Yh.shape[0]
+    K = Xh.shape[1] if K is None else K
+    ldc = C1[0].stride(0) if C1[0] is not None else (C2[0].stride(0) if C2[0] is not None else D.stride(0))
+    _check(lib().cdmpt_gemm_pair(M, Ncols, K, _ptr(Xh), _ptr(Xl), Xh.stride(0), _ptr(Yh), _ptr(Yl),
+                                 Yh.stride(0), _ptr(D), _ptr(Dl), D.stride(0), float(alpha),
+                                 float(b1), _ptr(C1[0]), _ptr(C1[1]), float(b2), _ptr(C2[0]),
+                                 _ptr(C2[1]), ldc, _stream_ptr(stream)))
+
+
+def check_bounded_wait(limit_ms=2.0, stream=None) -> int:
+    """Runs cdmpt_check_bounded_wait and returns its status code (5 = ERR_TIMEOUT expected)."""
+    return int(lib().cdmpt_check_bounded_wait(float(limit_ms), _stream_ptr(stream)))
+
+
 def gemm_f64(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, trans_block=0,
              dot=None, E=None, M=None, Ncols=None, K=None, stream=None):
     """FP64 counterpart of gemm_f32 (CUDA cores)."""
@@ -319,12 +345,14 @@ class Handle:
     def __init__(self, precision="fp32", engine="auto", cg_tol=0.0, cg_maxit=200,
                  refine_rounds=2, occ_tol=0.0, mu_maxit=60, mu_guess=None, profile=False,
                  stream=None, grand_canonical=False, ckpt_stride=0, fd_exact=False,
-                 screen_tau=0.0):
+                 screen_tau=0.0, fp64_residual=0):
         """ckpt_stride: 0 stores the whole recursion trajectory; s > 0 keeps every s-th
         step and recomputes the rest segment by segment; "sqrt" (or -1) picks
         s = ceil(sqrt(n)). FP64 and FP32 precisions only. screen_tau > 0: block-sparse
         products that drop 128 x 32 tile terms with norm product <= screen_tau (FP32 and
-        mixed TF32 only)."""
+        mixed TF32 only). fp64_residual (mixed only): 0 forms the final refinement pass's
+        step residuals with Ozaki-sliced products on the late steps, 1 on every step, -1
+        never."""
         o = default_opts()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.gemm_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
@@ -341,6 +369,7 @@ class Handle:
         o.ckpt_stride = -1 if ckpt_stride == "sqrt" else int(ckpt_stride)
         o.fd_exact = 1 if fd_exact else 0
         o.screen_tau = float(screen_tau)
+        o.fp64_residual = int(fp64_residual)
         self.opts = o
         self.h = create(o)
         self.N = 0

@@ -124,6 +124,7 @@ bool valid_opts(const cdmpt_opts* o) {
     if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
     if (o->grand_canonical && !o->have_mu_guess) return false;
     if (o->ckpt_stride < -1) return false;
+    if (o->fp64_residual < -1 || o->fp64_residual > 1) return false;
     if (o->ckpt_stride != 0 &&
         (o->precision == CDMPT_MIXED_TF32 || o->precision == CDMPT_MIXED_BF16))
         return false;
@@ -165,6 +166,7 @@ cdmpt_status cdmpt_default_opts(cdmpt_opts* o) {
     o->ckpt_stride = 0;
     o->fd_exact = 0;
     o->screen_tau = 0.0;
+    o->fp64_residual = 0;
     return CDMPT_OK;
 }
 
@@ -1146,3 +1148,69 @@ cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, c
 }
 
 }  // extern "C"
+
+namespace {
+bool pow2_or_zero(double a) {
+    if (a == 0.0) return true;
+    int e = 0;
+    return std::frexp(std::fabs(a), &e) == 0.5;
+}
+}  // namespace
+
+extern "C" cdmpt_status cdmpt_gemm_pair(int M, int Ncols, int K, const float* Xh, const float* Xl,
+                                        int ldx, const float* Yh, const float* Yl, int ldy,
+                                        float* D, float* Dl, int ldd, double alpha, double b1,
+                                        const float* C1h, const float* C1l, double b2,
+                                        const float* C2h, const float* C2l, int ldc,
+                                        void* stream) {
+    using namespace cdmpt;
+    if (M < 0 || Ncols < 0 || K < 1 || K > 32768 || !Xh || !Yh || !D || ldx < K || ldy < K ||
+        (ldx & 7) || (ldy & 7) || ldd < Ncols || ((C1h || C2h) && ldc < Ncols) ||
+        !pow2_or_zero(alpha) || !pow2_or_zero(b1) || !pow2_or_zero(b2)) {
+        set_error("gemm_pair: bad arguments (ld multiples of 8 and >= K, K <= 32768, alpha, b1, "
+                  "b2 powers of two or zero)");
+        return CDMPT_ERR_ARG;
+    }
+    if (M == 0 || Ncols == 0) return CDMPT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t dx = up((size_t)M * ldx * 2), dy = up((size_t)Ncols * ldy * 2);
+    const size_t ex = up((size_t)M * 4), ey = up((size_t)Ncols * 4);
+    char* buf = nullptr;
+    const int nd = kOzDigits;
+    if (cudaMallocAsync((void**)&buf, nd * dx + nd * dy + ex + ey, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("gemm_pair: scratch allocation failed");
+        return CDMPT_ERR_OOM;
+    }
+    OzOperand ox, oy;
+    for (int d = 0; d < nd; ++d) {
+        ox.s[d] = buf + d * dx;
+        oy.s[d] = buf + nd * dx + d * dy;
+    }
+    ox.e = (int*)(buf + nd * dx + nd * dy);
+    oy.e = (int*)(buf + nd * dx + nd * dy + ex);
+    ox.ld = ldx;
+    oy.ld = ldy;
+    cdmpt_status st = oz_slice(Xh, Xl, M, K, ldx, ox, s);
+    if (st == CDMPT_OK) st = oz_slice(Yh, Yl, Ncols, K, ldy, oy, s);
+    OzEpi ep;
+    ep.D = D;
+    ep.Dl = Dl;
+    ep.ldd = ldd;
+    ep.c1h = C1h;
+    ep.c1l = C1l;
+    ep.c2h = C2h;
+    ep.c2l = C2l;
+    ep.ldc = ldc;
+    ep.alpha = (float)alpha;
+    ep.b1 = (float)b1;
+    ep.b2 = (float)b2;
+    if (st == CDMPT_OK) st = gemm_oz(M, Ncols, K, ox, oy, ep, s);
+    cudaFreeAsync(buf, s);
+    return st;
+}
+
+extern "C" cdmpt_status cdmpt_check_bounded_wait(double limit_ms, void* stream) {
+    return cdmpt::bounded_wait_probe(limit_ms, (cudaStream_t)stream);
+}

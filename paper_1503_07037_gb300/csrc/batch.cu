@@ -50,6 +50,7 @@ struct Mat {   // FP32 matrix stack with TF32 split
     float* x = nullptr;
     float* hi = nullptr;
     float* lo = nullptr;
+    float* xl = nullptr;   // mixed-precision trajectory: low FP32 part of a pair, value = x + xl
 };
 
 struct Sys {
@@ -105,6 +106,10 @@ struct cdmpt_batch {
     cdmpt_stats st;
     std::string err;
     bool have_H = false;
+    // mixed precision: Ozaki digits of three operands (sized for the largest system) and the
+    // low part of an Ozaki-formed W_k, shared by the systems one after another
+    OzOperand oz[3];
+    float* oz_wl = nullptr;
 };
 
 namespace {
@@ -640,31 +645,38 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
     }
 }
 
+// Z_0 = -s2 (H0 - mu I) of every active system (pair-stored in mixed precision).
+cdmpt_status init_z0_batch(cdmpt_batch* b, const std::vector<const double*>& skip,
+                           const std::vector<char>* only = nullptr) {
+    std::vector<GrpEw> d, dp;
+    for (int i = 0; i < b->B; ++i) {
+        if (only && !(*only)[i]) continue;
+        Sys& sy = b->sys[i];
+        GrpEw e = sy.Z[0].xl ? ewd(sy.Z[0].x, sy.Z[0].xl, sy.Z[0].hi, sy.Z[0].lo)
+                             : ewd(sy.Z[0].x, nullptr, sy.Z[0].hi, sy.Z[0].lo);
+        e.h = sy.H0;
+        e.rows = sy.N; e.ld = sy.ld; e.N = sy.N;
+        e.s0 = -sy.s2;
+        e.s1 = sy.mu;
+        e.skip = skip[i];
+        (sy.Z[0].xl ? dp : d).push_back(e);
+    }
+    CDMPT_TRY(run_ew(b, G_INIT_Z, d));
+    return run_ew(b, G_PAIR_INIT, dp);
+}
+
 // One 0th-order pass for the systems whose inactive flag is 0, with products on
 // engine and CG to relative residual tol.
 cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, double tol) {
     const int G = b->B;
     std::vector<const double*> skip(G);
     for (int i = 0; i < G; ++i) skip[i] = b->inactive + i;
-    {
-        std::vector<GrpEw> d;
-        for (int i = 0; i < G; ++i) {
-            Sys& sy = b->sys[i];
-            GrpEw e = ewd(sy.Z[0].x, nullptr, sy.Z[0].hi, sy.Z[0].lo);
-            e.h = sy.H0;
-            e.rows = sy.N; e.ld = sy.ld; e.N = sy.N;
-            e.s0 = -sy.s2;
-            e.s1 = sy.mu;
-            e.skip = skip[i];
-            d.push_back(e);
-        }
-        CDMPT_TRY(run_ew(b, G_INIT_Z, d));
-    }
+    CDMPT_TRY(init_z0_batch(b, skip));
     int total = 0, hint = 1;
     for (int k = 0; k < n; ++k) {
         std::vector<GemmSpec> gw, gr;
         std::vector<BCg> cg(G);
-        std::vector<GrpEw> dz, dsym;
+        std::vector<GrpEw> dz, dsym, dzl;
         for (int i = 0; i < G; ++i) {
             Sys& sy = b->sys[i];
             GemmSpec w;                  // W_k = Z_k Z_k
@@ -696,6 +708,12 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
             y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
             y.skip = skip[i];
             dsym.push_back(y);
+            if (sy.Z[k + 1].xl) {   // a sweep step leaves an FP32 iterate: zero low part
+                GrpEw zl = ewd(sy.Z[k + 1].xl);
+                zl.rows = sy.N; zl.ld = sy.ld; zl.N = sy.N; zl.count = (long long)sy.blk;
+                zl.skip = skip[i];
+                dzl.push_back(zl);
+            }
         }
         if (b->tile_bn == 0) CDMPT_TRY(tune_tiles(b, gw));   // first product of the batch
         CDMPT_TRY(grouped_gemm(b, gw, engine));
@@ -709,18 +727,62 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
         hint = std::max(1, it);
         CDMPT_TRY(run_ew(b, G_AXPBY, dz));
         CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));
+        CDMPT_TRY(run_ew(b, G_ZERO, dzl));
     }
     *iters_out = total;
     return CDMPT_OK;
 }
 
-// One refinement pass of the stored trajectories (mixed precision), for the
-// systems whose inactive flag is 0: per step, W_k = Z_k Z_k and the residual
-// 2 Z_k - Z_{k+1} - Z_{k+1} W_k with split-TF32 products, then the correction
-// d (I + W_k) = residual by CG with one-pass TF32 products (relative residual
-// 1e-3), Z_{k+1} += d, symmetrised. The residual uses full tiles: the stored
-// Z_{k+1} does not commute with W_k to first order in its error.
-cdmpt_status refine_batch(cdmpt_batch* b, int n, int* iters_out) {
+// W_k and the residual 2 Z_k - Z_{k+1} - Z_{k+1} W_k of step k from Ozaki-sliced products of
+// the pair-stored trajectory, for every active system one after another (they share the
+// digit buffers); W_k's FP32 part and split replace the stored W_k, the residual goes to RHS.
+cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& active) {
+    cudaStream_t s = b->cx.stream;
+    for (int i = 0; i < b->B; ++i) {
+        if (!active[i]) continue;
+        Sys& sy = b->sys[i];
+        for (auto& o : b->oz) o.ld = sy.ld;
+        CDMPT_TRY(oz_slice(sy.Z[k].x, sy.Z[k].xl, sy.N, sy.N, sy.ld, b->oz[0], s));
+        OzEpi w;
+        w.D = sy.W[k].x;
+        w.Dl = b->oz_wl;
+        w.Dthi = sy.W[k].hi;
+        w.Dtlo = sy.W[k].lo;
+        w.ldd = sy.ld;
+        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[0], b->oz[0], w, s));
+        CDMPT_TRY(oz_slice(sy.W[k].x, b->oz_wl, sy.N, sy.N, sy.ld, b->oz[1], s));
+        CDMPT_TRY(oz_slice(sy.Z[k + 1].x, sy.Z[k + 1].xl, sy.N, sy.N, sy.ld, b->oz[2], s));
+        OzEpi r;
+        r.D = sy.RHS.x;
+        r.ldd = sy.ld;
+        r.alpha = -1.f;
+        r.b1 = 2.f;
+        r.c1h = sy.Z[k].x;
+        r.c1l = sy.Z[k].xl;
+        r.b2 = -1.f;
+        r.c2h = sy.Z[k + 1].x;
+        r.c2l = sy.Z[k + 1].xl;
+        r.ldc = sy.ld;
+        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[2], b->oz[1], r, s));
+        if (b->cx.st) {
+            const double f = 2.0 * sy.N * (double)sy.N * sy.N;
+            b->cx.st->gemm_launches += 2;
+            b->cx.st->gemm_flops += 2.0 * f;
+            b->cx.st->tensor_flops += 20.0 * f;
+        }
+    }
+    return CDMPT_OK;
+}
+
+// One refinement pass of the stored trajectories (mixed precision), for the systems whose
+// inactive flag is 0 (active[i] on the host): per step, W_k = Z_k Z_k and the residual
+// 2 Z_k - Z_{k+1} - Z_{k+1} W_k, then the correction d (I + W_k) = residual by CG with
+// one-pass TF32 products (relative residual 1e-3), Z_{k+1} += d added to the pair,
+// symmetrised. Steps k < k_hp form W_k and the residual with grouped split-TF32 products
+// (full tiles for the residual: the stored Z_{k+1} does not commute with W_k to first order
+// in its error); steps k >= k_hp with Ozaki-sliced products.
+cdmpt_status refine_batch(cdmpt_batch* b, int n, int k_hp, const std::vector<char>& active,
+                          int* iters_out) {
     const int G = b->B;
     std::vector<const double*> skip(G);
     for (int i = 0; i < G; ++i) skip[i] = b->inactive + i;
@@ -731,6 +793,16 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int* iters_out) {
         std::vector<GrpEw> ds, dz, dsym;
         for (int i = 0; i < G; ++i) {
             Sys& sy = b->sys[i];
+            cg[i] = BCg{sy.A1.x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
+            GrpEw z = ewd(sy.Z[k + 1].x, sy.Z[k + 1].xl, sy.A1.x);   // Z_{k+1} += d, to the pair
+            z.rows = sy.N; z.ld = sy.ld; z.N = sy.N; z.count = (long long)sy.N * sy.ld;
+            z.skip = skip[i];
+            dz.push_back(z);
+            GrpEw y = ewd(sy.Z[k + 1].x, sy.Z[k + 1].xl, sy.Z[k + 1].hi, sy.Z[k + 1].lo);
+            y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
+            y.skip = skip[i];
+            dsym.push_back(y);
+            if (k >= k_hp) continue;
             GemmSpec w;                  // W_k = Z_k Z_k, split-TF32
             w.X = &sy.Z[k];
             w.rows = sy.N;
@@ -741,7 +813,9 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int* iters_out) {
             w.p.Dlo = sy.W[k].lo;
             w.skip = skip[i];
             gw.push_back(w);
-            GrpEw e = ewd(sy.S.x, sy.Z[k].x, sy.Z[k + 1].x);   // S = 2 Z_k - Z_{k+1}
+            // S = 2 Z_k - Z_{k+1} from the pairs
+            GrpEw e = ewd(sy.S.x, sy.Z[k].x, sy.Z[k].xl, sy.Z[k + 1].x);
+            e.p4 = sy.Z[k + 1].xl;
             e.rows = sy.N; e.ld = sy.ld; e.N = sy.N; e.count = (long long)sy.N * sy.ld;
             e.s0 = 2.0;
             e.s1 = -1.0;
@@ -754,31 +828,24 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int* iters_out) {
             r.p = epi(sy.RHS.x, sy.N, sy.N, sy.ld, -1.f, 1.f, sy.S.x);
             r.skip = skip[i];
             gr.push_back(r);
-            cg[i] = BCg{sy.A1.x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
-            GrpEw z = ewd(sy.Z[k + 1].x, sy.A1.x);   // Z_{k+1} += d
-            z.rows = sy.N; z.ld = sy.ld; z.N = sy.N; z.count = (long long)sy.N * sy.ld;
-            z.s0 = 1.0;
-            z.s1 = 1.0;
-            z.skip = skip[i];
-            dz.push_back(z);
-            GrpEw y = ewd(sy.Z[k + 1].x, nullptr, sy.Z[k + 1].hi, sy.Z[k + 1].lo);
-            y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
-            y.skip = skip[i];
-            dsym.push_back(y);
         }
-        CDMPT_TRY(grouped_gemm(b, gw));
-        CDMPT_TRY(run_ew(b, G_LINCOMB, ds));
-        CDMPT_TRY(grouped_gemm(b, gr));
-        for (int i = 0; i < G; ++i) {
-            if (b->sys[i].converged) continue;
-            const double nn = b->sys[i].N;
-            add_flops(b, sym_flops(b, b->sys[i].N) + 2.0 * nn * nn * nn);
+        if (k >= k_hp) {
+            CDMPT_TRY(residual_batch_hp(b, k, active));
+        } else {
+            CDMPT_TRY(grouped_gemm(b, gw));
+            CDMPT_TRY(run_ew(b, G_PAIR_LINCOMB, ds));
+            CDMPT_TRY(grouped_gemm(b, gr));
+            for (int i = 0; i < G; ++i) {
+                if (!active[i]) continue;
+                const double nn = b->sys[i].N;
+                add_flops(b, sym_flops(b, b->sys[i].N) + 2.0 * nn * nn * nn);
+            }
         }
         int it = 0;
         CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, 1e-3, skip, 2, &it, false, CDMPT_GEMM_TC_TF32));
         total += it;
-        CDMPT_TRY(run_ew(b, G_AXPBY, dz));
-        CDMPT_TRY(run_tiles(b, dsym, 1, grouped_symmetrize));
+        CDMPT_TRY(run_ew(b, G_PAIR_ADD, dz));
+        CDMPT_TRY(run_tiles(b, dsym, 1, grouped_pair_symmetrize));
     }
     *iters_out = total;
     return CDMPT_OK;
@@ -797,6 +864,11 @@ cdmpt_status occupations(cdmpt_batch* b, int n) {
         e.skip = b->inactive + i;
         e.s0 = B_TRZ;
         dt.push_back(e);
+        if (sy.Z[n].xl) {   // Tr of the pair's low part into the same slot
+            GrpEw l = e;
+            l.p0 = sy.Z[n].xl;
+            dt.push_back(l);
+        }
         e.s0 = B_ZZ;
         dd.push_back(e);
     }
@@ -831,7 +903,11 @@ cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
         if (D > 0) CDMPT_TRY(grab(b, D * blk * sizeof(double), (void**)&sy.H1));
         sy.Z.assign(n + 1, Mat());
         sy.W.assign(n, Mat());
-        for (int k = 0; k <= n; ++k) CDMPT_TRY(grab_mat(b, blk, &sy.Z[k], true));
+        for (int k = 0; k <= n; ++k) {
+            CDMPT_TRY(grab_mat(b, blk, &sy.Z[k], true));
+            if (b->opts.precision == CDMPT_MIXED_TF32)
+                CDMPT_TRY(grab(b, blk * sizeof(float), (void**)&sy.Z[k].xl));
+        }
         for (int k = 0; k < n; ++k) CDMPT_TRY(grab_mat(b, blk, &sy.W[k], true));
         CDMPT_TRY(grab_mat(b, big, &sy.R, false));
         CDMPT_TRY(grab_mat(b, big, &sy.P, true));
@@ -842,6 +918,19 @@ cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
         CDMPT_TRY(grab_mat(b, big, &sy.Z1a, true));
         CDMPT_TRY(grab_mat(b, big, &sy.Z1b, true));
         CDMPT_TRY(grab_mat(b, blk, &sy.Qmu, false));
+    }
+    if (b->opts.precision == CDMPT_MIXED_TF32) {
+        size_t mblk = 0;
+        int mN = 0;
+        for (const Sys& sy : b->sys) {
+            mblk = std::max(mblk, sy.blk);
+            mN = std::max(mN, sy.N);
+        }
+        CDMPT_TRY(grab(b, mblk * sizeof(float), (void**)&b->oz_wl));
+        for (auto& o : b->oz) {
+            for (int d = 0; d < kOzDigits; ++d) CDMPT_TRY(grab(b, mblk * 2, &o.s[d]));
+            CDMPT_TRY(grab(b, (size_t)mN * sizeof(int), (void**)&o.e));
+        }
     }
     b->n_alloc = n;
     b->have_H = false;
@@ -1048,50 +1137,90 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
     if (mixed) {
         const int min_pass = std::max(1, b->opts.refine_rounds);
         for (int i = 0; i < G; ++i) b->sys[i].converged = false;
-        bool all = false;
-        for (int pass = 0; pass < min_pass + 6 && !all; ++pass) {
-            for (int i = 0; i < G; ++i) inact[i] = b->sys[i].converged ? 1.0 : 0.0;
+        // first step of the FP64-class pass (the earliest over the systems): every step, or
+        // the steps whose spectral bound tanh(2^k atanh rho) exceeds 1/2
+        int k_hp = n;
+        if (b->opts.fp64_residual >= 0) {
+            k_hp = 0;
+            if (b->opts.fp64_residual == 0) {
+                k_hp = n;
+                for (int i = 0; i < G; ++i) {
+                    const Sys& sy = b->sys[i];
+                    const double a0 = std::atanh(
+                        std::min(sy.s2 * std::max(sy.gmax - sy.mu, sy.mu - sy.gmin), 0.999999));
+                    int k = 0;
+                    while (k < n && std::tanh(std::ldexp(a0, k)) <= 0.5) ++k;
+                    k_hp = std::min(k_hp, k);
+                }
+            }
+        }
+        b->st.fp64_residual_first_step = k_hp;
+        // Split-TF32 passes until every system has settled (its occupation within tolerance
+        // after a pass that did not follow a Newton step on mu); from then on every pass,
+        // including the Newton steps that follow, forms the residuals of steps k >= k_hp with
+        // Ozaki-sliced products, so that no occupation is measured on a trajectory carrying
+        // the split products' bias.
+        std::vector<char> shifted(G, 1);
+        bool all = false, hp_phase = false;
+        int hp_passes = 0;
+        for (int pass = 0; pass < min_pass + 12 && !all; ++pass) {
+            std::vector<char> active(G, 0);
+            for (int i = 0; i < G; ++i) {
+                active[i] = b->sys[i].converged ? 0 : 1;
+                inact[i] = active[i] ? 0.0 : 1.0;
+            }
             CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
                                            cudaMemcpyHostToDevice, st));
             int iters = 0;
-            cdmpt_status s = refine_batch(b, n, &iters);
+            cdmpt_status s = refine_batch(b, n, hp_phase ? k_hp : n, active, &iters);
             if (s != CDMPT_OK) return bfail(b, s);
             b->st.cg_iterations_refine += iters;
+            if (hp_phase) b->st.fp64_residual_passes += 1;
             s = occupations(b, n);
             if (s != CDMPT_OK) return bfail(b, s);
             all = true;
-            std::vector<GrpEw> reinit;
+            std::vector<char> reinit(G, 0);
             for (int i = 0; i < G; ++i) {
                 Sys& sy = b->sys[i];
                 if (sy.converged) continue;
                 const double trP = 0.5 * (sy.N + b->pinned[i * kSlots + B_TRZ]);
                 const double zz = b->pinned[i * kSlots + B_ZZ];
                 const double err = trP - sy.nocc;
-                // finish mu to 1e-9 N, or to the FP32 noise of the trace (about
-                // 1e-7 sqrt(N) for a refined trajectory) once the passes are done
+                // finish mu to 1e-9 N, or to 1e-7 sqrt(N) once the minimum passes are done
                 const double tol = b->opts.occ_tol > 0
                                        ? b->opts.occ_tol
                                        : std::max(1e-9 * sy.N, pass + 1 >= min_pass
                                                                    ? 1e-7 * std::sqrt((double)sy.N)
                                                                    : 0.0);
                 const bool occ_ok = std::fabs(err) <= tol;
-                if (occ_ok && pass + 1 >= min_pass) {
+                if (occ_ok && pass + 1 >= min_pass && (hp_phase || !shifted[i])) {
                     sy.converged = true;
                     continue;
                 }
                 all = false;
+                shifted[i] = 0;
                 if (!occ_ok) {   // Newton step on mu; Z_0 = -s2 (H0 - mu I) is rebuilt
                     const double slope = 0.25 * sy.beta * (sy.N - zz);
                     if (slope > 0) sy.mu -= err / slope;
-                    GrpEw e = ewd(sy.Z[0].x, nullptr, sy.Z[0].hi, sy.Z[0].lo);
-                    e.h = sy.H0;
-                    e.rows = sy.N; e.ld = sy.ld; e.N = sy.N;
-                    e.s0 = -sy.s2;
-                    e.s1 = sy.mu;
-                    reinit.push_back(e);
+                    reinit[i] = 1;
+                    shifted[i] = 1;
                 }
             }
-            if (!reinit.empty()) CDMPT_TRY(run_ew(b, G_INIT_Z, reinit));
+            bool any_re = false;
+            for (int i = 0; i < G; ++i) any_re = any_re || reinit[i];
+            if (any_re) {
+                std::vector<const double*> none_skip(G, nullptr);
+                CDMPT_TRY(init_z0_batch(b, none_skip, &reinit));
+            }
+            if (all && !hp_phase && k_hp < n) {
+                // every system settled on split-TF32 residuals: reopen all of them for the
+                // passes with FP64-class residuals on the late steps
+                hp_phase = true;
+                all = false;
+                for (int i = 0; i < G; ++i) b->sys[i].converged = false;
+            } else if (hp_phase && !all && ++hp_passes >= 4) {
+                break;
+            }
         }
         if (!all)
             return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
@@ -1232,8 +1361,32 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
                 dsym.push_back(y);
             }
-            CDMPT_TRY(grouped_gemm(b, gq));
-            for (int i = 0; i < G; ++i) add_flops(b, sym_flops(b, b->sys[i].N));
+            if (mixed) {
+                // I - Z_n^2 cancels for saturated levels: form it from the pair-stored Z_n with
+                // the Ozaki-sliced product, system by system
+                for (int i = 0; i < G; ++i) {
+                    Sys& sy = b->sys[i];
+                    for (auto& o : b->oz) o.ld = sy.ld;
+                    CDMPT_TRY(oz_slice(sy.Z[n].x, sy.Z[n].xl, sy.N, sy.N, sy.ld, b->oz[0], st));
+                    OzEpi q;
+                    q.D = sy.RHS.x;
+                    q.Dthi = sy.RHS.hi;
+                    q.Dtlo = sy.RHS.lo;
+                    q.ldd = sy.ld;
+                    q.alpha = -1.f;
+                    q.gamma = 1.f;
+                    CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[0], b->oz[0], q, st));
+                    if (b->cx.st) {
+                        const double f = 2.0 * sy.N * (double)sy.N * sy.N;
+                        b->cx.st->gemm_launches += 1;
+                        b->cx.st->gemm_flops += f;
+                        b->cx.st->tensor_flops += 10.0 * f;
+                    }
+                }
+            } else {
+                CDMPT_TRY(grouped_gemm(b, gq));
+                for (int i = 0; i < G; ++i) add_flops(b, sym_flops(b, b->sys[i].N));
+            }
             int it = 0;
             cdmpt_status s = cg_batch(b, cg, 1.0, -1.0, b->opts.cg_tol, none, 1, &it, true);
             if (s != CDMPT_OK) return bfail(b, s);
@@ -1302,12 +1455,18 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         Sys& sy = b->sys[i];
         const size_t e0 = (size_t)sy.N * sy.N;
         if (P0 && P0[i]) {
+            auto p0_out = [&](double* out) -> cdmpt_status {
+                if (sy.Z[n].xl)
+                    return pair::to_f64(out, sy.N, sy.Z[n].x, sy.Z[n].xl, sy.ld, sy.N, sy.N, 0.5,
+                                        0.5, st);
+                return Ew<float>::to_f64(out, sy.N, sy.Z[n].x, sy.ld, sy.N, sy.N, 0.5, 0.5, st);
+            };
             if (out_on_device) {
-                CDMPT_TRY(Ew<float>::to_f64(P0[i], sy.N, sy.Z[n].x, sy.ld, sy.N, sy.N, 0.5, 0.5, st));
+                CDMPT_TRY(p0_out(P0[i]));
             } else {
                 double* tmp = nullptr;
                 CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, e0 * sizeof(double), st));
-                CDMPT_TRY(Ew<float>::to_f64(tmp, sy.N, sy.Z[n].x, sy.ld, sy.N, sy.N, 0.5, 0.5, st));
+                CDMPT_TRY(p0_out(tmp));
                 CDMPT_CUDA_TRY(cudaMemcpyAsync(P0[i], tmp, e0 * sizeof(double),
                                                cudaMemcpyDeviceToHost, st));
                 CDMPT_CUDA_TRY(cudaFreeAsync(tmp, st));

@@ -4,8 +4,9 @@
 #include <algorithm>
 #include <string>
 
-#include "internal.cuh"
 #include "batch_kernels.cuh"
+#include "dd.cuh"
+#include "internal.cuh"
 
 namespace cdmpt {
 
@@ -51,7 +52,43 @@ __global__ void k_grouped(const GrpEw* __restrict__ desc) {
         if (d.sc[CG_RRNEW] <= d.sc[CG_THRESH]) return;
     }
     double acc = 0.0;
-    if constexpr (OP == G_INIT_Z || OP == G_DOT_H) {
+    if constexpr (OP == G_PAIR_INIT) {
+        const size_t total = (size_t)d.rows * d.ld;
+        for (size_t e = first; e < total; e += stride) {
+            const size_t r = e / d.ld;
+            const int j = (int)(e - r * d.ld);
+            double v = 0.0;
+            if (j < d.N) {
+                v = d.h[r * d.ld + j];
+                if ((size_t)j == r % (size_t)d.N) v -= d.s1;
+                v *= d.s0;
+            }
+            const float h = (float)v;
+            d.p0[e] = h;
+            d.p1[e] = (float)(v - (double)h);
+            if (d.p2) split1(h, d.p2, d.p3, e);
+        }
+    } else if constexpr (OP == G_PAIR_LINCOMB || OP == G_PAIR_ADD) {
+        const float a0 = (float)d.s0, a1 = (float)d.s1;
+        const size_t nv = (size_t)d.count / 4;
+        for (size_t v = first; v < nv; v += stride) {
+            const size_t i = v * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float h, l;
+                if constexpr (OP == G_PAIR_LINCOMB) {
+                    dd::add(__fmul_rn(a0, d.p1[i + k]), __fmul_rn(a0, d.p2[i + k]),
+                            __fmul_rn(a1, d.p3[i + k]), __fmul_rn(a1, d.p4[i + k]), h, l);
+                    d.p0[i + k] = __fadd_rn(h, l);
+                } else {
+                    dd::add1(d.p0[i + k], d.p1[i + k], d.p2[i + k], h, l);
+                    d.p0[i + k] = h;
+                    d.p1[i + k] = l;
+                    if (d.p3) split1(h, d.p3, d.p4, i + k);
+                }
+            }
+        }
+    } else if constexpr (OP == G_INIT_Z || OP == G_DOT_H) {
         const size_t total = (size_t)d.rows * d.ld;
         for (size_t e = first; e < total; e += stride) {
             const size_t r = e / d.ld;
@@ -188,6 +225,49 @@ __global__ void k_grouped_tiles(const GrpEw* __restrict__ desc, int max_blocks) 
                 }
             }
         }
+    } else if constexpr (OP == 2) {   // pair (p0, p1) symmetrised in double-float
+        if (bi > bj) return;
+        __shared__ float al[TT][TT + 1];
+        __shared__ float bl[TT][TT + 1];
+        for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+            int r = i0 + y, c = j0 + threadIdx.x;
+            bool in = r < N && c < N;
+            a[y][threadIdx.x] = in ? d.p0[base + (size_t)r * ld + c] : 0.f;
+            al[y][threadIdx.x] = in ? d.p1[base + (size_t)r * ld + c] : 0.f;
+            r = j0 + y;
+            c = i0 + threadIdx.x;
+            in = r < N && c < N;
+            b[y][threadIdx.x] = in ? d.p0[base + (size_t)r * ld + c] : 0.f;
+            bl[y][threadIdx.x] = in ? d.p1[base + (size_t)r * ld + c] : 0.f;
+        }
+        __syncthreads();
+        for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+            const int x = threadIdx.x;
+            float h1, l1, h2, l2;
+            dd::add(a[y][x], al[y][x], b[x][y], bl[x][y], h1, l1);
+            dd::add(b[y][x], bl[y][x], a[x][y], al[x][y], h2, l2);
+            h1 *= 0.5f;
+            l1 *= 0.5f;
+            h2 *= 0.5f;
+            l2 *= 0.5f;
+            int r = i0 + y, c = j0 + x;
+            if (r < N && c < N) {
+                const size_t i = base + (size_t)r * ld + c;
+                d.p0[i] = h1;
+                d.p1[i] = l1;
+                if (d.p2) split1(h1, d.p2, d.p3, i);
+            }
+            if (bi != bj) {
+                r = j0 + y;
+                c = i0 + x;
+                if (r < N && c < N) {
+                    const size_t i = base + (size_t)r * ld + c;
+                    d.p0[i] = h2;
+                    d.p1[i] = l2;
+                    if (d.p2) split1(h2, d.p2, d.p3, i);
+                }
+            }
+        }
     } else {                   // p0 = p1 + p1^T
         for (int y = threadIdx.y; y < TT; y += blockDim.y) {
             const int r = j0 + y, c = i0 + threadIdx.x;
@@ -275,6 +355,9 @@ cdmpt_status grouped_ew(int op, const GrpEw* dev_desc, int G, long long max_coun
         case G_ZERO: k_grouped<G_ZERO><<<grid, kT, 0, s>>>(dev_desc); break;
         case G_INIT_Z: k_grouped<G_INIT_Z><<<grid, kT, 0, s>>>(dev_desc); break;
         case G_DOT_H: k_grouped<G_DOT_H><<<grid, kT, 0, s>>>(dev_desc); break;
+        case G_PAIR_INIT: k_grouped<G_PAIR_INIT><<<grid, kT, 0, s>>>(dev_desc); break;
+        case G_PAIR_LINCOMB: k_grouped<G_PAIR_LINCOMB><<<grid, kT, 0, s>>>(dev_desc); break;
+        case G_PAIR_ADD: k_grouped<G_PAIR_ADD><<<grid, kT, 0, s>>>(dev_desc); break;
         default: set_error("grouped_ew: unknown op"); return CDMPT_ERR_ARG;
     }
     return check("grouped elementwise launch");
@@ -294,6 +377,14 @@ cdmpt_status grouped_transpose_add(const GrpEw* dev_desc, int G, int max_N, int 
     dim3 grid(nt, nt, G * max_blocks), block(TT, 8);
     k_grouped_tiles<1><<<grid, block, 0, s>>>(dev_desc, max_blocks);
     return check("grouped transpose-add launch");
+}
+
+cdmpt_status grouped_pair_symmetrize(const GrpEw* dev_desc, int G, int max_N, int max_blocks,
+                                     cudaStream_t s) {
+    const int nt = (max_N + TT - 1) / TT;
+    dim3 grid(nt, nt, G * max_blocks), block(TT, 8);
+    k_grouped_tiles<2><<<grid, block, 0, s>>>(dev_desc, max_blocks);
+    return check("grouped pair symmetrize launch");
 }
 
 cdmpt_status grouped_trace(const GrpEw* dev_desc, int G, int max_N, int max_blocks,

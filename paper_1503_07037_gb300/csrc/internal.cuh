@@ -120,6 +120,9 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
                          const Epilogue<float>& ep, const double* skip, cudaStream_t s,
                          const GemmScreen* screen = nullptr);
 bool tc_supported();   // device is sm_103 (tcgen05 kernels built for sm_103a)
+// One CTA waits on an mbarrier that nothing arrives on, through the kernels' bounded wait
+// with the given limit; returns CDMPT_ERR_TIMEOUT (and clears the error word) when it gave up.
+cdmpt_status bounded_wait_probe(double limit_ms, cudaStream_t s);
 // Two-SM variant (tcgen05.mma.cta_group::2, 256-row tiles per CTA pair);
 // X / Y are the hi operands (TF32) and Xl / Yl the lo operands (3xTF32).
 template <typename T>
@@ -180,6 +183,65 @@ struct Ew {
     static cdmpt_status dot_h(const T* A, const double* H, int N, int ld, int ldh,
                                  double* out, cudaStream_t s);
 };
+
+// Ozaki-sliced product of pair-stored matrices (gemm_oz.cu). An operand is nd = 4 or 5 BF16
+// digit arrays (rows x ld, row-major) and one power-of-two exponent per row, written by
+// oz_slice from a pair (xh, xl; xl may be null): x = 2^e sum_p s_p 2^(-7 - 8 p), p = 0 .. nd-1.
+struct OzOperand {
+    void* s[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int* e = nullptr;
+    int ld = 0;
+};
+// Epilogue of gemm_oz, in double-float arithmetic:
+//   D (+ Dl) = alpha X Y^T + b1 (c1h + c1l) + b2 (c2h + c2l) + gamma I,
+// with alpha, b1, b2 powers of two (exact scalings). D receives the FP32 rounding, Dl (if
+// given) the remainder, Dthi / Dtlo (if given) the TF32 split of D, and dot (if given)
+// += sum D^2. C terms and outputs share the leading dimensions ldc and ldd.
+struct OzEpi {
+    int M = 0, N = 0;
+    float* D = nullptr;
+    float* Dl = nullptr;
+    float* Dthi = nullptr;
+    float* Dtlo = nullptr;
+    int ldd = 0;
+    const float* c1h = nullptr;
+    const float* c1l = nullptr;
+    const float* c2h = nullptr;
+    const float* c2l = nullptr;
+    int ldc = 0;
+    float alpha = 1.f, b1 = 0.f, b2 = 0.f, gamma = 0.f;
+    double* dot = nullptr;
+    const int* ex = nullptr;   // set by gemm_oz from the operands
+    const int* ey = nullptr;
+};
+constexpr int kOzDigits = 5;   // digits of the refinement products (39 bits of the row maximum)
+cdmpt_status oz_slice(const float* xh, const float* xl, int rows, int cols, int ld,
+                      const OzOperand& out, cudaStream_t s, int nd = kOzDigits);
+// D = op(X Y^T) for X (M x K) and Y (N x K) given as nd digits each; K <= 32768.
+cdmpt_status gemm_oz(int M, int N, int K, const OzOperand& X, const OzOperand& Y,
+                     const OzEpi& ep, cudaStream_t s, int nd = kOzDigits);
+
+// Pair-stored FP32 matrices (value = hi + lo, double-float arithmetic; pair.cu). thi / tlo,
+// when given, receive the TF32 split of the new hi for the split-TF32 engine.
+namespace pair {
+// (hi, lo) = scale (H - shift I) per N x N block, rounded from FP64 to a pair
+cdmpt_status init(float* hi, float* lo, const double* H, int N, int ld, int ldh, int blocks,
+                  double scale, double shift, cudaStream_t s, float* thi = nullptr,
+                  float* tlo = nullptr);
+// out = FP32(a x + b y), x and y pairs, a and b powers of two (exact scalings) or zero
+cdmpt_status lincomb(float* out, double a, const float* xh, const float* xl, double b,
+                     const float* yh, const float* yl, size_t count, cudaStream_t s);
+// (hi, lo) += d without rounding the sum to FP32
+cdmpt_status add(float* hi, float* lo, const float* d, size_t count, cudaStream_t s,
+                 float* thi = nullptr, float* tlo = nullptr);
+cdmpt_status symmetrize(float* hi, float* lo, int N, int ld, int blocks, cudaStream_t s,
+                        float* thi = nullptr, float* tlo = nullptr);
+cdmpt_status add_diag(float* hi, float* lo, int N, int ld, int blocks, double shift,
+                      cudaStream_t s, float* thi = nullptr, float* tlo = nullptr);
+// out = a (hi + lo) + b_diag I in FP64
+cdmpt_status to_f64(double* out, int ldo, const float* hi, const float* lo, int ldi, int N,
+                    int rows, double a, double b_diag, cudaStream_t s);
+}  // namespace pair
 
 cdmpt_status split_tf32(const float* X, size_t count, float* hi, float* lo, cudaStream_t s);
 cdmpt_status cg_scalar_step(double* sc, cudaStream_t s);

@@ -62,13 +62,14 @@ Solver<T>::~Solver() {
 }
 
 template <typename T>
-cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
+cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt, bool pairs) {
     const int ld_new = (N + 31) / 32 * 32;
     const int rows_needed = std::max(1, D) * N;
+    pairs = pairs && sizeof(T) == 4 && ckpt == 0;
     seg_ = -1;
     // with checkpoints the trajectory views are laid out for exactly n steps
     if (N == N_ && D <= D_ && (ckpt == 0 ? n <= n_ : n == n_) && ckpt == ck_ && ld == ld_new &&
-        rows_cap_ >= rows_needed)
+        rows_cap_ >= rows_needed && pairs == pairs_)
         return CDMPT_OK;
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
@@ -76,6 +77,7 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     W_.clear();
     orders_ready_ = false;
     ck_ = ckpt;
+    pairs_ = pairs;
     N_ = N;
     D_ = D;
     n_ = n;
@@ -107,7 +109,10 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     Z_.resize(n + 1);
     W_.resize(n);
     if (ck_ == 0) {
-        for (int k = 0; k <= n; ++k) CDMPT_TRY(buf(blk_, &Z_[k], true));
+        for (int k = 0; k <= n; ++k) {
+            CDMPT_TRY(buf(blk_, &Z_[k], true));
+            if (pairs_) CDMPT_TRY(grab(blk_, &Z_[k].xl));
+        }
         for (int k = 0; k < n; ++k) CDMPT_TRY(buf(blk_, &W_[k], true));
     } else {
         std::vector<Buf<T>> zseg(std::max(0, ck_ - 1)), wseg(ck_);
@@ -134,6 +139,33 @@ cdmpt_status Solver<T>::reserve(int N, int D, int n, int ckpt) {
     CDMPT_TRY(buf(big, &Z1b_, true));
     CDMPT_TRY(buf(blk_, &Qmu_, false));
     CDMPT_TRY(buf(blk_, &Zh_, false));
+    wl_ = nullptr;
+    for (auto& o : oz_) o = OzOperand();
+    if (pairs_) {
+        // Ozaki digits of three N x N operands: kOzDigits BF16 arrays and N row exponents each
+        CDMPT_TRY(grab(blk_, &wl_));
+        for (auto& o : oz_) {
+            o.ld = ld;
+            for (int d = 0; d < kOzDigits; ++d) {
+                void* q = nullptr;
+                if (cudaMalloc(&q, blk_ * 2) != cudaSuccess) {
+                    cudaGetLastError();
+                    set_error("device allocation of the Ozaki digits failed");
+                    return CDMPT_ERR_OOM;
+                }
+                allocs_.push_back(q);
+                o.s[d] = q;
+            }
+            void* q = nullptr;
+            if (cudaMalloc(&q, (size_t)N * sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation of the Ozaki exponents failed");
+                return CDMPT_ERR_OOM;
+            }
+            allocs_.push_back(q);
+            o.e = (int*)q;
+        }
+    }
     tnx_ = tny_ = tnw_ = nullptr;
     wnorm_src_ = nullptr;
     tmask_ = nullptr;
@@ -421,6 +453,11 @@ template <typename T>
 cdmpt_status Solver<T>::init_z0(Context& cx, const double* H0, double mu, double s2, double rho,
                                 int engine) {
     if (!fdx_) {
+        if constexpr (sizeof(T) == 4) {
+            if (Z_[0].xl)   // pair storage: Z_0 to about 48 bits from the FP64 Hamiltonian
+                return pair::init(Z_[0].x, Z_[0].xl, H0, N_, ld, ld, 1, -s2, mu, cx.stream,
+                                  Z_[0].hi, Z_[0].lo);
+        }
         return Ew<T>::init_z(Z_[0].x, H0, N_, ld, ld, 1, -s2, mu, cx.stream, Z_[0].hi, Z_[0].lo);
     }
     std::vector<double> a;
@@ -443,14 +480,29 @@ cdmpt_status Solver<T>::init_z0(Context& cx, const double* H0, double mu, double
     CDMPT_CUDA_TRY(cudaMemsetAsync(hc->x, 0, blk_ * sizeof(T), cx.stream));
     if (hc->hi) CDMPT_CUDA_TRY(cudaMemsetAsync(hc->hi, 0, blk_ * sizeof(T), cx.stream));
     if (hc->lo) CDMPT_CUDA_TRY(cudaMemsetAsync(hc->lo, 0, blk_ * sizeof(T), cx.stream));
-    CDMPT_TRY(Ew<T>::add_diag(hc->x, N_, ld, 1, a[K], cx.stream, hc->hi, hc->lo));
+    // pair storage: Z_0 = Y + Y (h - I), the FP64 Y exactly as a pair and the small
+    // correction Y (h - I) = O(rho^2) Y from the products (h - I: the constant term dropped)
+    const bool pr = Z_[0].xl != nullptr;
+    CDMPT_TRY(Ew<T>::add_diag(hc->x, N_, ld, 1, (pr && K == 0) ? 0.0 : a[K], cx.stream, hc->hi,
+                              hc->lo));
     for (int k = K - 1; k >= 0; --k) {   // h <- U h + a_k I
         Epilogue<T> ep;
-        ep.gamma = a[k];
+        ep.gamma = (pr && k == 0) ? 0.0 : a[k];
         ep.Dhi = hn->hi;
         ep.Dlo = hn->lo;
         CDMPT_TRY(gemm(cx, N_, N_, N_, U.op(), hc->op(), hn->x, ep, nullptr, engine));
         std::swap(hc, hn);
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (pr) {
+            CDMPT_TRY(pair::init(Z_[0].x, Z_[0].xl, H0, N_, ld, ld, 1, -s2, mu, cx.stream));
+            if (K > 0) {
+                Epilogue<T> ep;   // E = Y (h - I)
+                CDMPT_TRY(gemm(cx, N_, N_, N_, Y.op(), hc->op(), S_.x, ep, nullptr, engine));
+                CDMPT_TRY(pair::add(Z_[0].x, Z_[0].xl, S_.x, blk_, cx.stream));
+            }
+            return pair::symmetrize(Z_[0].x, Z_[0].xl, N_, ld, 1, cx.stream, Z_[0].hi, Z_[0].lo);
+        }
     }
     Epilogue<T> ep;   // Z_0 = Y h
     ep.Dhi = Z_[0].hi;
@@ -668,6 +720,8 @@ cdmpt_status Solver<T>::step0(Context& cx, int k, int engine, double tol, int ma
     *hint = std::max(1, it);
     CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, Z_[k].x, blk_, 2.0, 1.0, nullptr, cx.stream));
     CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
+    // a sweep step leaves an FP32 iterate: the low part of a pair-stored one is zero
+    if (Z_[k + 1].xl) CDMPT_CUDA_TRY(cudaMemsetAsync(Z_[k + 1].xl, 0, blk_ * sizeof(T), cx.stream));
     return CDMPT_OK;
 }
 
@@ -708,35 +762,69 @@ cdmpt_status Solver<T>::need(Context& cx, int k) {
     return CDMPT_OK;
 }
 
-// One refinement pass over the stored trajectory (mixed precision): for each
-// step, accurate A_k from the refined Z_k, accurate residual of the stored
-// Z_{k+1}, one-pass TF32 CG iterations for the correction.
+// Z_k += d and symmetrise; a pair-stored Z_k takes the correction without rounding the sum
+// to FP32.
 template <typename T>
-cdmpt_status Solver<T>::refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
+cdmpt_status Solver<T>::correct(Context& cx, int k, const T* d) {
+    if constexpr (sizeof(T) == 4) {
+        if (Z_[k].xl) {
+            CDMPT_TRY(pair::add(Z_[k].x, Z_[k].xl, d, blk_, cx.stream));
+            return pair::symmetrize(Z_[k].x, Z_[k].xl, N_, ld, 1, cx.stream, Z_[k].hi, Z_[k].lo);
+        }
+    }
+    CDMPT_TRY(Ew<T>::axpby(Z_[k].x, d, blk_, 1.0, 1.0, nullptr, cx.stream));
+    return Ew<T>::symmetrize(Z_[k].x, N_, ld, 1, cx.stream, Z_[k].hi, Z_[k].lo);
+}
+
+// One refinement pass over the stored trajectory (mixed precision). For each step, with
+// Z_k already refined: the step matrix A_k = I + W_k from the refined Z_k and the residual
+// r = 2 Z_k - Z_{k+1} - Z_{k+1} W_k of the stored Z_{k+1} (Algorithm 1's per-step system in
+// the deviation form), then the correction d (I + W_k) = r by CG with one-pass TF32 products,
+// added to Z_{k+1}. Steps k < k_hp form W_k and r with split-TF32 products (with pair
+// storage the linear part 2 Z_k - Z_{k+1} comes from the pairs; both carry an error of
+// about 2^-22 ||Z_k||^2 relative to Z_k, small while ||Z_k|| is); steps k >= k_hp with the
+// Ozaki-sliced products of the pair-stored trajectory (FP64-class: about 2^-31, and free of
+// the truncation bias of FP32 tensor-core accumulation).
+template <typename T>
+cdmpt_status Solver<T>::refine(Context& cx, const cdmpt_opts& o, int n, int k_hp, int* cg_iters,
                                double* max_rel_res) {
     int total = 0;
     double worst = 0.0;
     for (int k = 0; k < n; ++k) {
-        {   // accurate W_k from the refined Z_k
-            Epilogue<T> ep;
-            ep.Dhi = W_[k].hi;
-            ep.Dlo = W_[k].lo;
-            ep.sym = true;
-            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr,
-                           CDMPT_GEMM_TC_3XTF32));
-        }
-        // accurate residual r = 2 Z_k - Z_{k+1} - Z_{k+1} W_k of the stored Z_{k+1}
-        CDMPT_TRY(Ew<T>::lincomb(S_.x, Z_[k].x, 2.0, Z_[k + 1].x, -1.0, blk_, cx.stream));
-        {   // full tiles: the stored Z_{k+1} differs from the exact one by an error that
-            // does not commute with W_k, so Z_{k+1} W_k is not symmetric and its upper
-            // triangle alone would change the correction at first order
-            Epilogue<T> ep;
-            ep.alpha = -1.0;
-            ep.beta = 1.0;
-            ep.C = S_.x;
-            ep.ldc = ld;
-            CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k + 1].op(), W_[k].op(), RHS_.x, ep, nullptr,
-                           CDMPT_GEMM_TC_3XTF32));
+        if (k >= k_hp) {
+            CDMPT_TRY(residual_hp(cx, k));
+        } else {
+            {   // W_k from the refined Z_k
+                Epilogue<T> ep;
+                ep.Dhi = W_[k].hi;
+                ep.Dlo = W_[k].lo;
+                ep.sym = true;
+                CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k].op(), Z_[k].op(), W_[k].x, ep, nullptr,
+                               CDMPT_GEMM_TC_3XTF32));
+            }
+            // linear part 2 Z_k - Z_{k+1}: it is small, of the size of Z_{k+1} W_k, so its
+            // FP32 rounding is at the level of the product's
+            if constexpr (sizeof(T) == 4) {
+                if (Z_[k].xl)
+                    CDMPT_TRY(pair::lincomb(S_.x, 2.0, Z_[k].x, Z_[k].xl, -1.0, Z_[k + 1].x,
+                                            Z_[k + 1].xl, blk_, cx.stream));
+                else
+                    CDMPT_TRY(Ew<T>::lincomb(S_.x, Z_[k].x, 2.0, Z_[k + 1].x, -1.0, blk_,
+                                             cx.stream));
+            } else {
+                CDMPT_TRY(Ew<T>::lincomb(S_.x, Z_[k].x, 2.0, Z_[k + 1].x, -1.0, blk_, cx.stream));
+            }
+            {   // full tiles: the stored Z_{k+1} differs from the exact one by an error that
+                // does not commute with W_k, so Z_{k+1} W_k is not symmetric and its upper
+                // triangle alone would change the correction at first order
+                Epilogue<T> ep;
+                ep.alpha = -1.0;
+                ep.beta = 1.0;
+                ep.C = S_.x;
+                ep.ldc = ld;
+                CDMPT_TRY(gemm(cx, N_, N_, N_, Z_[k + 1].op(), W_[k].op(), RHS_.x, ep, nullptr,
+                               CDMPT_GEMM_TC_3XTF32));
+            }
         }
         // correction d (I + W_k) = r with one-pass TF32 iterations
         CgArgs a;
@@ -757,18 +845,115 @@ cdmpt_status Solver<T>::refine(Context& cx, const cdmpt_opts& o, int n, int* cg_
         CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
         const double zz = cx.pinned[S_ZZ];
         if (zz > 0) worst = std::max(worst, std::sqrt(bb / (4.0 * zz)));
-        CDMPT_TRY(Ew<T>::axpby(Z_[k + 1].x, A1_.x, blk_, 1.0, 1.0, nullptr, cx.stream));
-        CDMPT_TRY(Ew<T>::symmetrize(Z_[k + 1].x, N_, ld, 1, cx.stream, Z_[k + 1].hi, Z_[k + 1].lo));
+        CDMPT_TRY(correct(cx, k + 1, A1_.x));
     }
     *cg_iters = total;
     *max_rel_res = worst;
     return CDMPT_OK;
 }
 
+// Z_0 += shift I (a Newton step on mu moves Z_0 = -s2 (H0 - mu I) by s2 dmu I)
+template <typename T>
+cdmpt_status Solver<T>::shift_z0(Context& cx, double shift) {
+    if constexpr (sizeof(T) == 4) {
+        if (Z_[0].xl)
+            return pair::add_diag(Z_[0].x, Z_[0].xl, N_, ld, 1, shift, cx.stream, Z_[0].hi,
+                                  Z_[0].lo);
+    }
+    return Ew<T>::add_diag(Z_[0].x, N_, ld, 1, shift, cx.stream, Z_[0].hi, Z_[0].lo);
+}
+
+// P0 = (I + Z_n) / 2 in FP64 (device array, leading dimension ldo)
+template <typename T>
+cdmpt_status Solver<T>::p0_out(Context& cx, double* out, int ldo) {
+    const int n = last_n_;
+    if constexpr (sizeof(T) == 4) {
+        if (Z_[n].xl)
+            return pair::to_f64(out, ldo, Z_[n].x, Z_[n].xl, ld, N_, N_, 0.5, 0.5, cx.stream);
+    }
+    return Ew<T>::to_f64(out, ldo, Z_[n].x, ld, N_, N_, 0.5, 0.5, cx.stream);
+}
+
+template <typename T>
+cdmpt_status Solver<T>::gemm_hp(Context& cx, const OzOperand& X, const OzOperand& Y,
+                                const OzEpi& ep) {
+    const double flops = 2.0 * N_ * (double)N_ * N_;
+    cudaEvent_t e1 = nullptr;
+    if (cx.profile) {
+        while (cx.ev.size() < 2 * (cx.ev_used + 1)) {
+            cudaEvent_t e;
+            CDMPT_CUDA_TRY(cudaEventCreate(&e));
+            cx.ev.push_back(e);
+        }
+        if (cx.ev_ok.size() < cx.ev_used + 1) {
+            cx.ev_ok.resize(cx.ev_used + 1);
+            cx.ev_engine.resize(cx.ev_used + 1);
+            cx.ev_flops.resize(cx.ev_used + 1);
+        }
+        cx.ev_ok[cx.ev_used] = 1;
+        cx.ev_engine[cx.ev_used] = CDMPT_GEMM_TC_OZAKI;
+        cx.ev_flops[cx.ev_used] = flops;
+        e1 = cx.ev[2 * cx.ev_used + 1];
+        CDMPT_CUDA_TRY(cudaEventRecord(cx.ev[2 * cx.ev_used], cx.stream));
+    }
+    CDMPT_TRY(gemm_oz(N_, N_, N_, X, Y, ep, cx.stream));
+    if (cx.profile) {
+        CDMPT_CUDA_TRY(cudaEventRecord(e1, cx.stream));
+        ++cx.ev_used;
+    }
+    if (cx.st) {
+        cx.st->gemm_launches += 1;
+        cx.st->gemm_flops += flops;
+        cx.st->tensor_flops += 10.0 * flops;   // ten BF16 digit products
+    }
+    return CDMPT_OK;
+}
+
+// W_k = Z_k Z_k and r = 2 Z_k - Z_{k+1} - Z_{k+1} W_k (into RHS_) from Ozaki-sliced products
+// of the pair-stored trajectory: the FP32 part and TF32 split of W_k replace the stored W_k, its
+// low part goes to wl_, and the linear part of r is formed in double-float in the epilogue.
+template <typename T>
+cdmpt_status Solver<T>::residual_hp(Context& cx, int k) {
+    if constexpr (sizeof(T) != 4) {
+        set_error("FP64-class residuals need the pair-stored FP32 trajectory");
+        return CDMPT_ERR_UNSUPPORTED;
+    } else {
+        if (!pairs_ || !Z_[k].xl) {
+            set_error("FP64-class residuals need the pair-stored FP32 trajectory");
+            return CDMPT_ERR_UNSUPPORTED;
+        }
+        CDMPT_TRY(oz_slice(Z_[k].x, Z_[k].xl, N_, N_, ld, oz_[0], cx.stream));
+        {
+            OzEpi ep;
+            ep.D = W_[k].x;
+            ep.Dl = wl_;
+            ep.Dthi = W_[k].hi;
+            ep.Dtlo = W_[k].lo;
+            ep.ldd = ld;
+            CDMPT_TRY(gemm_hp(cx, oz_[0], oz_[0], ep));
+        }
+        CDMPT_TRY(oz_slice(W_[k].x, wl_, N_, N_, ld, oz_[1], cx.stream));
+        CDMPT_TRY(oz_slice(Z_[k + 1].x, Z_[k + 1].xl, N_, N_, ld, oz_[2], cx.stream));
+        OzEpi ep;
+        ep.D = RHS_.x;
+        ep.ldd = ld;
+        ep.alpha = -1.f;
+        ep.b1 = 2.f;
+        ep.c1h = Z_[k].x;
+        ep.c1l = Z_[k].xl;
+        ep.b2 = -1.f;
+        ep.c2h = Z_[k + 1].x;
+        ep.c2l = Z_[k + 1].xl;
+        ep.ldc = ld;
+        return gemm_hp(cx, oz_[2], oz_[1], ep);
+    }
+}
+
 template <typename T>
 cdmpt_status Solver<T>::occupation(Context& cx, int n, double* trP, double* zz) {
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_TRZ, 0, 2 * sizeof(double), cx.stream));
     CDMPT_TRY(Ew<T>::trace(Z_[n].x, N_, ld, 1, sc_ + S_TRZ, cx.stream));
+    if (Z_[n].xl) CDMPT_TRY(Ew<T>::trace(Z_[n].xl, N_, ld, 1, sc_ + S_TRZ, cx.stream));
     CDMPT_TRY(Ew<T>::dot(Z_[n].x, Z_[n].x, blk_, sc_ + S_ZZ, nullptr, cx.stream));
     CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
     *trP = 0.5 * (N_ + cx.pinned[S_TRZ]);
@@ -785,15 +970,37 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
     const int acc = last_acc_;
     const cdmpt_opts& o = last_opts_;
     cdmpt_stats& st = *cx.st;
-    Epilogue<T> ep;
-    ep.alpha = -0.25 * beta;
-    ep.gamma = 0.25 * beta;
-    ep.Dhi = RHS_.hi;
-    ep.Dlo = RHS_.lo;
-    ep.sym = true;
-    CDMPT_TRY(gemm(cx, N, N, N, Z_[n].op(), Z_[n].op(), RHS_.x, ep, nullptr, acc));
+    // right side beta/4 (I - Z_n^2): for saturated levels 1 - z^2 cancels to a small value, so
+    // the pair-stored trajectory forms I - Z_n^2 with the Ozaki-sliced product (an FP32-class
+    // product's error, relative to the O(1) terms, would dominate Tr Q and hence mu1)
+    double rhs_scale = 1.0;
+    bool hp_rhs = false;
+    if constexpr (sizeof(T) == 4) {
+        if (pairs_ && Z_[n].xl) {
+            CDMPT_TRY(oz_slice(Z_[n].x, Z_[n].xl, N_, N_, ld, oz_[0], cx.stream));
+            OzEpi ep;
+            ep.D = RHS_.x;
+            ep.Dthi = RHS_.hi;
+            ep.Dtlo = RHS_.lo;
+            ep.ldd = ld;
+            ep.alpha = -1.f;
+            ep.gamma = 1.f;
+            CDMPT_TRY(gemm_hp(cx, oz_[0], oz_[0], ep));
+            rhs_scale = 0.25 * beta;
+            hp_rhs = true;
+        }
+    }
+    if (!hp_rhs) {
+        Epilogue<T> ep;
+        ep.alpha = -0.25 * beta;
+        ep.gamma = 0.25 * beta;
+        ep.Dhi = RHS_.hi;
+        ep.Dlo = RHS_.lo;
+        ep.sym = true;
+        CDMPT_TRY(gemm(cx, N, N, N, Z_[n].op(), Z_[n].op(), RHS_.x, ep, nullptr, acc));
+    }
     if (fdx_) {   // Z_0 = tanh(Y): dZ_0/dmu = s2 (I - Z_0^2), so Q = beta/4 (I - Z_n^2) = beta P0 (I - P0)
-        CDMPT_TRY(Ew<T>::axpby(Qmu_.x, RHS_.x, blk_, 1.0, 0.0, nullptr, cx.stream));
+        CDMPT_TRY(Ew<T>::axpby(Qmu_.x, RHS_.x, blk_, rhs_scale, 0.0, nullptr, cx.stream));
         st.cg_iterations_q = 0;
         q_valid_ = true;
         return CDMPT_OK;
@@ -803,7 +1010,9 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
     a.s = 1.0;
     a.t = -1.0;
     a.x0 = &RHS_;
+    a.x0_scale = rhs_scale;
     a.rhs = RHS_.x;
+    a.rhs_scale = rhs_scale;
     a.rows = N;
     a.tol = o.cg_tol;
     a.maxit = o.cg_maxit;
@@ -1304,10 +1513,11 @@ cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
     if (fdx_) {
         CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, sizeof(double), cx.stream));
         CDMPT_TRY(Ew<T>::trace(Z_[n].x, N, ld, 1, sc_ + S_FE, cx.stream));
+        if (Z_[n].xl) CDMPT_TRY(Ew<T>::trace(Z_[n].xl, N, ld, 1, sc_ + S_FE, cx.stream));
         CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
         if (omega) *omega = mu * 0.5 * (N + cx.pinned[S_FE]) + Te * logdet_1mp;
         if (grad && last_opts_.grand_canonical == 0) {   // P0 = (I + Z_n) / 2
-            CDMPT_TRY(Ew<T>::to_f64(grad, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
+            CDMPT_TRY(p0_out(cx, grad, N));
         } else if (grad) {
             double* G0 = nullptr;
             CDMPT_CUDA_TRY(cudaMallocAsync((void**)&G0, (size_t)N * N * sizeof(double),
@@ -1348,6 +1558,7 @@ cdmpt_status Solver<T>::free_energy(Context& cx, double* omega, double* grad) {
     // Tr P0 = (N + Tr Z_n)/2 and Tr[P0 R] = (Tr R + <Z_n, R>)/2
     CDMPT_CUDA_TRY(cudaMemsetAsync(sc_ + S_FE, 0, 3 * sizeof(double), cx.stream));
     CDMPT_TRY(Ew<T>::trace(Z_[n].x, N, ld, 1, sc_ + S_FE, cx.stream));
+    if (Z_[n].xl) CDMPT_TRY(Ew<T>::trace(Z_[n].xl, N, ld, 1, sc_ + S_FE, cx.stream));
     CDMPT_TRY(Ew<T>::trace(R.x, N, ld, 1, sc_ + S_FE + 1, cx.stream));
     CDMPT_TRY(Ew<T>::dot(Z_[n].x, R.x, blk_, sc_ + S_FE + 2, nullptr, cx.stream));
     CDMPT_TRY(read_scalars(cx, sc_, S_NSLOTS));
@@ -1394,7 +1605,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
         ck = o.ckpt_stride < 0 ? (int)std::ceil(std::sqrt((double)n) - 1e-9)
                                : std::min(o.ckpt_stride, n);
     }
-    CDMPT_TRY(reserve(N, D, n, ck));
+    CDMPT_TRY(reserve(N, D, n, ck, mixed));
     traj_valid_ = q_valid_ = false;
     fdx_ = o.fd_exact != 0;
     screen_tau_ = (sizeof(T) == 4 && tcnt_) ? (float)o.screen_tau : 0.f;
@@ -1478,26 +1689,59 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     // -------------------------------------------------- refinement (mixed)
     if (mixed) {
         const int min_pass = std::max(1, o.refine_rounds);
-        bool done = false;
-        for (int pass = 0; pass < min_pass + (bf16 ? 10 : 6) && !done; ++pass) {
+        // first step of the FP64-class pass: every step, or the steps whose spectral bound
+        // tanh(2^k atanh rho) exceeds 1/2 (before them the error of a split-TF32 residual,
+        // relative to Z_k, carries the factor ||W_k|| <= tanh(2^k atanh rho)^2)
+        int k_hp = n;
+        if (o.fp64_residual >= 0) {
+            k_hp = 0;
+            if (o.fp64_residual == 0) {
+                const double a0 = std::atanh(std::min(s2 * std::max(gmax - mu, mu - gmin), 0.999999));
+                while (k_hp < n && std::tanh(std::ldexp(a0, k_hp)) <= 0.5) ++k_hp;
+            }
+        }
+        st.fp64_residual_first_step = k_hp;
+        // split-TF32 passes until the step residuals settle; from then on (including the
+        // Newton steps that follow) every pass forms the residuals of steps k >= k_hp with
+        // Ozaki-sliced products, so that no occupation is measured on a trajectory carrying
+        // the split products' bias
+        bool done = false, hp_phase = false;
+        int hp_passes = 0;
+        for (int pass = 0; pass < min_pass + (bf16 ? 10 : 6) + 4 && !done; ++pass) {
             int iters = 0;
             double worst = 0.0;
-            CDMPT_TRY(refine(cx, o, n, &iters, &worst));
+            CDMPT_TRY(refine(cx, o, n, hp_phase ? k_hp : n, &iters, &worst));
             st.cg_iterations_refine += iters;
+            if (hp_phase) st.fp64_residual_passes += 1;
             CDMPT_TRY(occupation(cx, n, &trP, &zz));
             const double err = gc ? 0.0 : trP - nocc;
             st.trace_P0 = trP;
             st.occupation_error = std::fabs(err);
-            // finish mu to 1e-9 N, or to the FP32 noise of the trace (about 1e-7 sqrt(N)
-            // for a refined trajectory) once the minimum passes are done
+            // finish mu to 1e-9 N, or to 1e-7 sqrt(N) once the minimum passes are done
             const double tol_ref =
                 o.occ_tol > 0 ? occ_tol
                               : std::max(1e-9 * N, pass + 1 >= min_pass ? 1e-7 * std::sqrt((double)N)
                                                                          : 0.0);
             const bool occ_ok = std::fabs(err) <= tol_ref;
-            if (occ_ok && pass + 1 >= min_pass && worst < 1e-4) {
-                done = true;
-                break;
+            if (hp_phase) {
+                if (occ_ok) {
+                    done = true;
+                    break;
+                }
+                if (++hp_passes >= 4) break;
+            } else {
+                // the pass started from relative step residuals below 1e-6, so it left them
+                // at about 1e-9 or at the split-TF32 floor (or, after three extra passes,
+                // below 1e-4)
+                const bool settled = worst < 1e-6 || (pass + 1 >= min_pass + 3 && worst < 1e-4);
+                if (occ_ok && pass + 1 >= min_pass && settled) {
+                    if (k_hp >= n) {
+                        done = true;
+                        break;
+                    }
+                    hp_phase = true;
+                    continue;
+                }
             }
             if (!occ_ok) {   // Newton step on mu; Z_0 = -s2 (H - mu I) moves by s2 dmu I
                 const double slope = 0.25 * beta * (N - zz);
@@ -1506,8 +1750,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                 if (fdx_)   // Z_0 = tanh(Y) is not shifted by a multiple of I: rebuild it
                     CDMPT_TRY(init_z0(cx, H0, mu, s2, s2 * std::max(gmax - mu, mu - gmin), acc));
                 else
-                    CDMPT_TRY(Ew<T>::add_diag(Z_[0].x, N, ld, 1, s2 * dmu, cx.stream, Z_[0].hi,
-                                              Z_[0].lo));
+                    CDMPT_TRY(shift_z0(cx, s2 * dmu));
             }
         }
         if (!done) {
@@ -1654,11 +1897,11 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
 
     if (P0) {
         if (out_on_device) {
-            CDMPT_TRY(Ew<T>::to_f64(P0, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
+            CDMPT_TRY(p0_out(cx, P0, N));
         } else {
             double* tmp = nullptr;
             CDMPT_CUDA_TRY(cudaMallocAsync((void**)&tmp, (size_t)N * N * sizeof(double), cx.stream));
-            CDMPT_TRY(Ew<T>::to_f64(tmp, N, Z_[n].x, ld, N, N, 0.5, 0.5, cx.stream));
+            CDMPT_TRY(p0_out(cx, tmp, N));
             CDMPT_CUDA_TRY(cudaMemcpyAsync(P0, tmp, (size_t)N * N * sizeof(double),
                                            cudaMemcpyDeviceToHost, cx.stream));
             CDMPT_CUDA_TRY(cudaFreeAsync(tmp, cx.stream));

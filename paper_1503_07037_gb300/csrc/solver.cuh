@@ -34,6 +34,8 @@ struct Buf {
     T* x = nullptr;
     T* hi = nullptr;
     T* lo = nullptr;
+    // mixed-precision trajectory only: the low FP32 part of a pair, value = x + xl
+    T* xl = nullptr;
     Operand<T> op() const {
         Operand<T> o;
         o.x = x;
@@ -50,7 +52,8 @@ public:
     // (Re)allocate for N x N problems with D directions and n steps. ckpt > 0
     // keeps only every ckpt-th Z_k of the trajectory (plus Z_n and W_0); the
     // other steps are recomputed one segment at a time when they are needed.
-    cdmpt_status reserve(int N, int D, int n, int ckpt);
+    // pairs: the trajectory Z_0..Z_n is stored as FP32 pairs (mixed precision).
+    cdmpt_status reserve(int N, int D, int n, int ckpt, bool pairs = false);
     cdmpt_status solve(Context& cx, const double* H0, const double* H1, int N, int D,
                        double gmin, double gmax, double trH0, const cdmpt_opts& o, double beta,
                        double nocc, int n, double* P0, double* P1, double* mu_out,
@@ -174,8 +177,20 @@ private:
                         double* Pm, double* mu_out, double* omega, double* grad,
                         const double* H2 = nullptr, const double* H3 = nullptr,
                         const double* mu1s = nullptr);
-    cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int* cg_iters,
+    // One refinement pass; steps k >= k_hp form their residuals with Ozaki-sliced products.
+    cdmpt_status refine(Context& cx, const cdmpt_opts& o, int n, int k_hp, int* cg_iters,
                         double* max_rel_res);
+    // W_k and the residual of step k (into RHS_) from Ozaki-sliced products of the
+    // pair-stored trajectory (FP64-class residuals).
+    cdmpt_status residual_hp(Context& cx, int k);
+    // D = op(X Y^T) by gemm_oz, with the profile events and statistics of gemm()
+    cdmpt_status gemm_hp(Context& cx, const OzOperand& X, const OzOperand& Y, const OzEpi& ep);
+    // Z_k += d, symmetrised (pair storage: without rounding the sum to FP32)
+    cdmpt_status correct(Context& cx, int k, const T* d);
+    // Z_0 += shift I
+    cdmpt_status shift_z0(Context& cx, double shift);
+    // P0 = (I + Z_n)/2 of the last solve in FP64 (device, leading dimension ldo)
+    cdmpt_status p0_out(Context& cx, double* out, int ldo);
     cdmpt_status occupation(Context& cx, int n, double* trP, double* zz);
     cdmpt_status compute_q(Context& cx);
     cdmpt_status read_scalars(Context& cx, const double* dev, int count);
@@ -190,6 +205,9 @@ private:
     // ck_ - 1 Z and ck_ W segment buffers; seg_ is the segment they hold.
     std::vector<Buf<T>> Z_, W_;
     int ck_ = 0, seg_ = -1;
+    bool pairs_ = false;             // Z_k.xl allocated (mixed precision)
+    OzOperand oz_[3];                // digit operands of the Ozaki-sliced products (pairs_)
+    T* wl_ = nullptr;                // low part of the Ozaki-formed W_k (pairs_)
     int replay_iters_ = 0;           // CG iterations spent recomputing segments
     Buf<T> R_, P_, Q_;               // CG work (D' * N rows)
     Buf<T> S_, A1_, RHS_;            // response work

@@ -209,3 +209,75 @@ def test_gemm_symmetric_result(cuda, cdmpt_lib, engine, N):
     assert _rel(got, ref) < tol
     want = float(np.sum(got * E.astype(np.float32)))
     assert abs(float(dot.item()) - want) < 1e-5 * max(1.0, abs(want))
+
+
+def _pair(v):
+    """FP64 values stored as an FP32 pair (hi, lo); returns hi, lo and their exact FP64 sum."""
+    hi = v.astype(np.float32)
+    lo = (v - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo, hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def _pair_mat(rng, rows, cols, ld):
+    """Normal entries with row magnitudes spread over 2^-20 .. 2^20 (the per-row powers of two
+    of the slicing) and one all-zero row."""
+    v = np.zeros((rows, ld))
+    v[:, :cols] = rng.standard_normal((rows, cols))
+    v[:, :cols] *= np.exp2(rng.integers(-20, 21, size=rows))[:, None]
+    v[rows // 2, :] = 0.0
+    return _pair(v)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 128, 64), (300, 200, 130), (1024, 1024, 1024),
+                                   (777, 513, 2049), (2048, 2048, 4096)])
+def test_gemm_pair_matches_fp64(cuda, cdmpt_lib, M, N, K):
+    """Ozaki-sliced product of FP32 pairs against the FP64 product of the same values. Five
+    8-bit digits per row carry the row's values to 2^-39 of its power of two, so an element's
+    error is a sum of K such terms of random sign: it stays within 2^-35 sqrt(K) max|x_i.|
+    max|y_j.| (with four digits the observed maximum was 2^-29.6 sqrt(K)), and the whole
+    product within 3e-11 relative (Frobenius) - far below FP32 (6e-8 per operand), which no
+    FP32-accumulating product reaches."""
+    import torch
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    ld = (K + 7) // 8 * 8
+    Xh, Xl, X = _pair_mat(rng, M, K, ld)
+    Yh, Yl, Y = _pair_mat(rng, N, K, ld)
+    ldd = (N + 7) // 8 * 8
+    D = torch.zeros((M, ldd), dtype=torch.float32, device=cuda)
+    Dl = torch.zeros_like(D)
+    cdmpt_lib.gemm_pair(_t(Xh, cuda), _t(Xl, cuda), _t(Yh, cuda), _t(Yl, cuda), D, Dl, K=K)
+    torch.cuda.synchronize()
+    got = D.cpu().numpy()[:, :N].astype(np.float64) + Dl.cpu().numpy()[:, :N].astype(np.float64)
+    ref = X[:, :K] @ Y[:, :K].T
+    scale = np.abs(X[:, :K]).max(axis=1)[:, None] * np.abs(Y[:, :K]).max(axis=1)[None, :]
+    bound = 2.0 ** -35 * np.sqrt(K) * scale
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / np.maximum(bound, 1e-300)))
+    assert _rel(got, ref) < 3e-11, _rel(got, ref)
+    assert np.all(got[M // 2] == 0.0) and np.all(got[:, N // 2] == 0.0)
+
+
+def test_gemm_pair_step_residual(cuda, cdmpt_lib):
+    """The residual of one recursion step in correction form, R = 2 Z - Z' - Z' W with
+    W = Z Z and Z' = 2 Z (I + W)^-1, from pair-stored operands. R cancels to the rounding of
+    the pairs (about 2^-48 of |Z|), so the computed R shows the product's own error, which
+    must stay below 1e-11 |Z'| |W| (split-TF32 products leave about 1e-7)."""
+    import torch
+    rng = np.random.default_rng(11)
+    N = 1000
+    ld = 1008
+    A = rng.standard_normal((N, N)) / np.sqrt(N)
+    Z = 0.45 * (A + A.T)
+    Zh, Zl, Zp = _pair(np.pad(Z, ((0, 0), (0, ld - N))))
+    W = Zp[:, :N] @ Zp[:, :N].T
+    Wh, Wl, Wp = _pair(np.pad(W, ((0, 0), (0, ld - N))))
+    Zn = 2.0 * np.linalg.solve(np.eye(N) + Wp[:, :N], Zp[:, :N])
+    Zn = 0.5 * (Zn + Zn.T)
+    Znh, Znl, Znp = _pair(np.pad(Zn, ((0, 0), (0, ld - N))))
+    R = torch.zeros((N, ld), dtype=torch.float32, device=cuda)
+    t = lambda a: _t(a, cuda)
+    cdmpt_lib.gemm_pair(t(Znh), t(Znl), t(Wh), t(Wl), R, None, alpha=-1.0, b1=2.0,
+                        C1=(t(Zh), t(Zl)), b2=-1.0, C2=(t(Znh), t(Znl)), K=N)
+    torch.cuda.synchronize()
+    ref = 2.0 * Zp[:, :N] - Znp[:, :N] - Znp[:, :N] @ Wp[:, :N].T
+    err = np.abs(R.cpu().numpy()[:, :N].astype(np.float64) - ref).max()
+    assert err < 1e-11 * np.abs(Znp).max() * np.abs(Wp).sum(axis=1).max(), err

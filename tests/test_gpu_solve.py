@@ -2,12 +2,8 @@
 
 Parity reference: the oracle's recursion-exact function (kind="rec", same n).
 Bars (relative Frobenius norm): 1e-10 for FP64, 1e-5 for FP32, 1e-6 for mixed
-precision after refinement. The gap of the recursion to the exact Fermi-Dirac
-function is reported separately.
-
-Mixed precision at beta = 80 keeps the trajectory in FP32: plain float32 with
-exact (LU) step solves already leaves P1 at 1.1e-6 there (N = 4096, measured
-on the host), so that one case is held to 2e-6, the FP32 storage floor.
+precision after refinement, on every workload (mu1 and alpha within ten times the bar).
+The gap of the recursion to the exact Fermi-Dirac function is reported separately.
 """
 import numpy as np
 import pytest
@@ -81,8 +77,8 @@ def test_mixed_lattice_1000(cuda, cdmpt_lib, beta):
     p = syn.cubic_lattice((10, 10, 10), seed=1002, beta=beta, n=14, directions="xy")
     ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
     r = _run(cdmpt_lib, p, "mixed")
-    _check(r, ref, 2e-6, 2)
-    assert r["stats"]["cg_iterations_refine"] > 0
+    _check(r, ref, BAR["mixed"], 2)
+    assert r["stats"]["cg_iterations_refine"] > 0 and r["stats"]["fp64_residual_passes"] > 0
 
 
 @pytest.mark.parametrize("beta", [5.0, 20.0])
@@ -103,19 +99,13 @@ def test_mixed_bf16_cubic16_full_size(cuda, cdmpt_lib):
 
 
 def test_mixed_small_system(cuda, cdmpt_lib):
-    """Mixed precision on a small cluster (N = 96). The refined trace carries FP32 noise near
-    1e-9 relative, and the refinement must still finish. The levels lie within 0.14 kT of mu,
-    so P1 sits at the FP32 storage floor: FP32 with split products gives 2e-6 to 5.5e-6 here.
-    P0 is held to the mixed bar; P1 to max(mixed bar, 1.3 x the FP32 error of the same system)."""
+    """Mixed precision on a small cluster (N = 96) whose levels lie within 0.14 kT of mu, where
+    P1 is most sensitive to the trajectory and to mu: FP32 with split products gives 2e-6 to
+    5.5e-6 here, and a trajectory stored in FP32 left mixed precision there too. The
+    pair-stored trajectory with FP64-class residuals holds every output to the mixed bar."""
     p = syn.clusters(B=1, seed=6006, sizes=[96], beta=20.0, n=12)[0]
     ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    rm = _run(cdmpt_lib, p, "mixed")
-    rf = _run(cdmpt_lib, p, "fp32")
-    assert _rel(rm["P0"], ref["P0"]) < BAR["mixed"]
-    for d in range(p.H1.shape[0]):
-        ef = _rel(rf["P1"][d], ref["P1"][d])
-        em = _rel(rm["P1"][d], ref["P1"][d])
-        assert em < max(BAR["mixed"], 1.3 * ef), (d, em, ef)
+    _check(_run(cdmpt_lib, p, "mixed"), ref, BAR["mixed"], p.H1.shape[0])
 
 
 def test_tf32_single_pass_is_coarse(cuda, cdmpt_lib):
@@ -137,7 +127,7 @@ def test_fp32_cubic16_full_size(cuda, cdmpt_lib, beta):
     _check(r, ref, BAR["fp32"], 1)
 
 
-@pytest.mark.parametrize("beta,bar", [(5.0, 1e-6), (20.0, 1e-6), (80.0, 2e-6)])
+@pytest.mark.parametrize("beta,bar", [(5.0, 1e-6), (20.0, 1e-6), (80.0, 1e-6)])
 def test_mixed_cubic16_full_size(cuda, cdmpt_lib, beta, bar):
     """Mixed precision on the measured workload (N = 4096, n = 14)."""
     p = syn.cubic_lattice((16, 16, 16), seed=1002, beta=beta, n=14)
@@ -146,13 +136,10 @@ def test_mixed_cubic16_full_size(cuda, cdmpt_lib, beta, bar):
     _check(r, ref, bar, 1)
 
 
-@pytest.mark.parametrize("name,mixed_bar", [("cubic20_b20", 2e-6), ("banded8192", 1e-6)])
+@pytest.mark.parametrize("name,mixed_bar", [("cubic20_b20", 1e-6), ("banded8192", 1e-6)])
 def test_large_mixed_and_fp32(cuda, cdmpt_lib, name, mixed_bar):
     """The large workloads: 20^3 lattice (N = 8000) and N = 8192 banded, beta = 20, n = 14.
-    Mixed precision against its bar and FP32 against the FP32 bar, one oracle solve each.
-    On the 20^3 lattice the mixed P1 error (1.01e-6) sits at the FP32 storage floor: more
-    refinement rounds or a tighter CG tolerance leave it unchanged, and FP32 with split
-    products reaches 1.17e-6, so that case is held to 2e-6 like beta = 80 at N = 4096."""
+    Mixed precision against its bar and FP32 against the FP32 bar, one oracle solve each."""
     p = syn.workload(name)
     ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
     _check(_run(cdmpt_lib, p, "mixed"), ref, mixed_bar, 1)
