@@ -1,23 +1,27 @@
 """Throughput of canonical DMPT solves on GB300 (one JSON line on rank 0).
 
-Workload (one step): the 16 x 16 x 16 periodic simple-cubic tight-binding
-lattice (N = 4096, on-site N(0, 0.3^2), hopping -1 +- 10 %, seed 1002), dipole
-perturbation along x, N_occ = N/2, n = 14 recursion steps, solved canonically
-at beta = 5, 20 and 80: three full solves (occupation loop, first-order
-response, mu1, polarizability) per step.
+Workload (one step): the mixed-precision configuration, two systems solved canonically at
+beta = 20 with n = 14 recursion steps and one dipole perturbation each:
+  - the 20 x 20 x 20 periodic simple-cubic tight-binding lattice (N = 8000, on-site
+    N(0, 0.3^2), hopping -1 +- 10 %, seed 1003), dipole along x;
+  - a random symmetric banded matrix, N = 8192, bandwidth 64, entries N(0,1)/8 (seed 1004),
+    perturbation diag(i - (N-1)/2).
+A solve is the whole path: the occupation loop, the refinement, the first-order response,
+mu1 and the polarizability, with P0 and P1 written out.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
-                  [--impl ours|reference] [--no-compare] [--no-cpu-baseline]
+                  [--impl ours|reference] [--no-compare] [--no-cpu-baseline] [--no-extras]
 
-The timed precision defaults to mixed (TF32 sweeps, split-TF32 refinement and
-response); one step of FP32 with split-TF32 products and one with CUDA-core
-FFMA products are timed beside it ("modes"), and every mode's P0 and P1 are
-compared with the FP64 oracle at the three temperatures ("error").
+The timed precision defaults to mixed (TF32 sweeps; refinement of the pair-stored
+trajectory with split-TF32 and Ozaki-sliced FP64-class residuals; split-TF32 response).
+One step in FP32 with split-TF32 products is timed beside it ("fp32"), and both precisions'
+P0, P1, mu1 and alpha are compared with the FP64 oracle ("error"). Extras: the 16^3 lattice
+at beta 5, 20 and 80 (N = 4096), the 96-cluster batch, and one FP64 solve.
 
---impl reference times the FP64 CPU oracle (exact diagonalisation) on the
-host cores, one solve of the same workload per step.
-Under torchrun every rank solves its own copy (weak scaling, no collective on
-the data path); times are max-reduced over ranks.
+--impl reference times the FP64 CPU oracle (exact diagonalisation) on the host cores, one
+solve of the workload (alternating the two systems) per step.
+Under torchrun every rank solves its own copy (weak scaling, no collective on the data
+path); times are max-reduced over ranks.
 """
 from __future__ import annotations
 
@@ -36,14 +40,17 @@ if ROOT not in sys.path:
 
 METRIC = ("DMPT response solves/sec and tensor TFLOP/s vs peak, mixed vs FP32 at "
           "≤1e-6 err")
-BETAS = (5.0, 20.0, 80.0)
-LATTICE = (16, 16, 16)
-NSTEPS_REC = 14
-WORKLOAD = "cubic16x16x16 tight-binding, N=4096, D=1 (x dipole), n=14, beta in {5,20,80}"
-TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 tensor rate ratio
-# DRAM bytes (read + write) of one GEMM launch at N = 4096 from the ncu captures summarised in
-# profiles/ (per engine); None until the kernel's counters are re-taken after a change
-TRAFFIC = {2: None, 3: 995.9e6}   # per launch at N = 4096 (3xTF32 captured on the current kernel)
+C3 = ("cubic20_b20", "banded8192")
+WORKLOAD = ("mixed-precision config: 20x20x20 lattice (N=8000) and banded N=8192 (bandwidth 64), "
+            "beta 20, n 14, D=1 dipole; one step = one canonical solve of each")
+C2_BETAS = (5.0, 20.0, 80.0)
+ENGINE_NAMES = {1: "CUDA-core FFMA/DFMA", 2: "tcgen05 TF32", 3: "tcgen05 3xTF32",
+                4: "tcgen05 BF16", 5: "tcgen05 Ozaki BF16 digits"}
+# tensor-pipe products per algorithmic product of each engine
+PIPE_FACTOR = {2: 1.0, 3: 3.0, 4: 1.0, 5: 15.0}
+# DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/, by engine
+# and N; None until the kernel's counters are taken on the current code
+TRAFFIC = {}
 
 
 def dist_env():
@@ -134,33 +141,75 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
-def problems():
-    import synthetic
-    return [synthetic.cubic_lattice(LATTICE, seed=1002, beta=b, n=NSTEPS_REC) for b in BETAS]
+def measure_peaks(dev):
+    """TF32 and FP64 tensor-library rates of this GPU, measured the way the driver measures the
+    BF16 one: torch.matmul at 8192^3 (TF32, FP32 inputs) as the best of 10 and back to back for
+    3 s, and at 4096^3 in FP64 (best of 3), with CUDA events."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn((n, n), device=dev, dtype=torch.float32)
+        b = torch.randn((n, n), device=dev, dtype=torch.float32)
+        c = torch.empty_like(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        best = 1e30
+        for _ in range(10):
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["tf32_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        reps = max(1, int(3000.0 / best))
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        out["tf32_tflops_sustained"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b, c
+        n = 4096
+        a = torch.randn((n, n), device=dev, dtype=torch.float64)
+        b = torch.randn((n, n), device=dev, dtype=torch.float64)
+        c = torch.empty_like(a)
+        torch.matmul(a, b, out=c)
+        best = 1e30
+        for _ in range(3):
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["fp64_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b, c
+        torch.cuda.empty_cache()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = ("torch.matmul: TF32 8192^3 best of 10 and back to back for 3 s; FP64 4096^3 "
+                  "best of 3; CUDA events, in this run")
+    return out
 
 
 # --------------------------------------------------------------------------- oracle timing
 
-def time_oracle(sample_betas, cores_note=True):
-    """Times the FP64 oracle on this host: returns (solves/s, seconds, results)."""
+def oracle_solve(p, eig=None):
+    """The FP64 oracle's solve of problem p (recursion-exact function), and its wall time."""
     import oracle
-    import synthetic
-    res = {}
     t0 = time.perf_counter()
-    for b in sample_betas:
-        p = synthetic.cubic_lattice(LATTICE, seed=1002, beta=b, n=NSTEPS_REC)
-        res[b] = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-    dt = time.perf_counter() - t0
-    return len(sample_betas) / dt, dt, res
+    r = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=eig)
+    return r, time.perf_counter() - t0
 
 
 def time_oracle_one_core():
-    """The oracle's beta = 20 solve of a 16 x 16 x 8 lattice (N = 2048) on one host core, in a
-    child process whose BLAS pools are limited to one thread; scaled to the N = 4096 workload by
-    the N^3 cost of the eigendecomposition and the Daleckii-Krein products (x 8). A bounded sample:
-    about 10 s on one core."""
-    import subprocess
-    import sys
+    """The oracle's solve of the 16 x 16 x 8 lattice (N = 2048, beta 20) on one host core, in a
+    child process whose BLAS pools are limited to one thread; scaled to the workload's mean N
+    of 8096 by the N^3 cost of the eigendecomposition and the Daleckii-Krein products. A bounded
+    sample: about 10 s on one core."""
     code = ("import time, oracle, synthetic\n"
             "p = synthetic.cubic_lattice((16, 16, 8), seed=1002, beta=20.0, n=14)\n"
             "t = time.perf_counter()\n"
@@ -177,9 +226,10 @@ def time_oracle_one_core():
         dt = float(out.stdout.strip().splitlines()[-1])
     except Exception as e:   # a missing baseline must not fail the bench
         return {"unavailable": f"one-core oracle run failed: {e}"[:200]}
-    return {"value": 1.0 / (8.0 * dt), "unit": "solves/s", "cores": 1, "kind": "oracle",
+    scale = (8096.0 / 2048.0) ** 3
+    return {"value": 1.0 / (scale * dt), "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"beta=20 solve of the 16x16x8 lattice (N=2048) in {dt:.1f} s on one core, "
-                      f"scaled x8 (N^3) to N=4096"}
+                      f"scaled by (8096/2048)^3 to the workload's mean N"}
 
 
 def blas_threads():
@@ -193,13 +243,14 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-    betas = [BETAS[i % len(BETAS)] for i in range(args.warmup + args.steps)]
-    for b in betas[:args.warmup]:
-        time_oracle([b])
+    import synthetic
+    probs = [synthetic.workload(c) for c in C3]
+    seq = [probs[i % len(probs)] for i in range(args.warmup + args.steps)]
+    for p in seq[:args.warmup]:
+        oracle_solve(p)
     t0 = time.perf_counter()
-    for b in betas[args.warmup:]:
-        time_oracle([b])
+    for p in seq[args.warmup:]:
+        oracle_solve(p)
     dt = time.perf_counter() - t0
     value = args.steps / dt
     line = {
@@ -208,10 +259,10 @@ def run_reference(args):
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "fp64 exact diagonalisation (oracle)",
-                   "step": "one solve of the workload (cycling beta 5, 20, 80)"},
+                   "step": "one solve of one of the two systems (alternating)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": blas_threads(),
                          "kind": "oracle",
-                         "sample": "one beta per step: dsyevd N=4096, bisection on mu, "
+                         "sample": "one system per step: dsyevd N=8000 or 8192, bisection on mu, "
                                    "Daleckii-Krein P1, mu1, alpha"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -222,6 +273,22 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- our path
 
+def _errors(res, ref, D):
+    """Relative errors of one solve's outputs against the oracle: P0, P1 (Frobenius, worst
+    direction), mu1 and alpha (relative, worst direction)."""
+    import numpy as np
+
+    import oracle
+    e = {"P0": oracle.rel_frobenius(res["P0"], ref["P0"]),
+         "P1": max(oracle.rel_frobenius(res["P1"][d], ref["P1"][d]) for d in range(D)),
+         "mu1": max(abs(res["mu1"][d] - ref["mu1"][d]) / max(abs(ref["mu1"][d]), 1e-300)
+                    for d in range(D)),
+         "alpha": max(abs(res["alpha"][d] - ref["alpha"][d]) / abs(ref["alpha"][d])
+                      for d in range(D))}
+    e["max"] = max(e["P0"], e["P1"], e["alpha"])
+    return {k: float(v) for k, v in e.items()}
+
+
 def run_ours(args):
     import ctypes
 
@@ -229,6 +296,7 @@ def run_ours(args):
     import torch
 
     import paper_1503_07037_gb300 as pkg
+    import synthetic
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -247,53 +315,61 @@ def run_ours(args):
     def max_over_ranks(x):
         return reduce_max(pg, x, dev)
 
-    probs = problems()
-    N, D = probs[0].N, probs[0].D
     stream = torch.cuda.current_stream()
-    H0 = torch.from_numpy(probs[0].H0).to(dev)
-    H1 = torch.from_numpy(probs[0].H1).to(dev)
-    P0 = torch.empty((N, N), dtype=torch.float64, device=dev)
-    P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev)
-    mu = ctypes.c_double()
-    mu1 = np.zeros(D)
+    mpk = measure_peaks(dev)
+    pk = peaks()
+    probs = [synthetic.workload(c) for c in C3]
+    bufs = []
+    for p in probs:
+        N, D = p.N, p.D
+        bufs.append({"H0": torch.from_numpy(p.H0).to(dev), "H1": torch.from_numpy(p.H1).to(dev),
+                     "P0": torch.empty((N, N), dtype=torch.float64, device=dev),
+                     "P1": torch.empty((D, N, N), dtype=torch.float64, device=dev),
+                     "mu": ctypes.c_double(), "mu1": np.zeros(D)})
 
     def make(precision, engine="auto"):
-        h = pkg.Handle(precision=precision, engine=engine, profile=True, stream=stream)
-        h.set_H(H0, H1)                 # resident in HBM before any timed region
-        return h
+        hs = []
+        for p, b in zip(probs, bufs):
+            h = pkg.Handle(precision=precision, engine=engine, profile=True, stream=stream)
+            h.set_H(b["H0"], b["H1"])       # resident in HBM before any timed region
+            hs.append(h)
+        return hs
 
-    def step(h, stats_acc=None, outs=None):
-        for p in probs:
-            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0.data_ptr(), P1.data_ptr(),
-                          ctypes.addressof(mu), mu1.ctypes.data, 1)
+    def step(hs, stats_acc=None, outs=None):
+        for h, p, b in zip(hs, probs, bufs):
+            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, b["P0"].data_ptr(), b["P1"].data_ptr(),
+                          ctypes.addressof(b["mu"]), b["mu1"].ctypes.data, 1)
             if stats_acc is not None:
                 stats_acc.append(h.stats())
             if outs is not None:
-                outs.append((P0.cpu().numpy(), P1[0].cpu().numpy()))
+                outs.append({"P0": b["P0"].cpu().numpy(), "P1": b["P1"].cpu().numpy(),
+                             "mu1": b["mu1"].copy(), "alpha": h.polarizability()})
 
-    def timed_steps(h, k, stats_acc):
+    def timed_steps(hs, k, stats_acc):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
         ev0.record(stream)
         for _ in range(k):
-            step(h, stats_acc)
+            step(hs, stats_acc)
         ev1.record(stream)
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1)
 
-    h = make(args.precision)
+    hs = make(args.precision)
     for _ in range(args.warmup):
-        step(h)
+        step(hs)
     clocks = ClockSampler(local)
     clocks.start()
     st_all = []
-    ms = timed_steps(h, args.steps, st_all)
+    ms = timed_steps(hs, args.steps, st_all)
     clk = clocks.stop()
     ms = max_over_ranks(ms)
     barrier()
     solves = args.steps * len(probs) * world
     value = solves / (ms / 1000.0)
+    outs_main = []
+    step(hs, None, outs_main)
 
     # roofline of the dominant kernel: the GEMM engine with the most device time
     n_eng = len(st_all[0]["engine_ms"])
@@ -301,107 +377,108 @@ def run_ours(args):
     eng_n = [sum(s["engine_launches"][e] for s in st_all) for e in range(n_eng)]
     eng_fl = [sum(s["engine_flops"][e] for s in st_all) for e in range(n_eng)]
     dom = max(range(n_eng), key=lambda e: eng_ms[e])
-    names = {1: "CUDA-core FFMA/DFMA", 2: "tcgen05 TF32", 3: "tcgen05 3xTF32", 4: "tcgen05 BF16"}
     avg_s = eng_ms[dom] / 1000.0 / max(1, eng_n[dom])
-    # mean algorithmic flops per launch: 2 N^3 for a full product, N (N + 1) N for a symmetric
-    # one (upper-triangular tiles only)
+    # mean algorithmic flops per launch: 2 M N K for a full product, N (N + 1) N for a
+    # symmetric one (upper-triangular tiles only)
     per_launch = eng_fl[dom] / max(1, eng_n[dom])
     achieved = per_launch / avg_s / 1e12
-    pk = peaks()
-    if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None,
-                "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
+    if dom == 1:
+        peak, pnote = mpk["fp64_tflops"], "measured FP64 cuBLAS 4096^3 in this run"
+        roof = {"bound": "alu"}
+    elif dom == 5:
+        peak, pnote = pk["bf16_sustained"], f"{pk['source']} sustained bf16 (MEASURED_PEAKS.json)"
+        roof = {"bound": "tensor"}
     else:
-        peak_tf32 = pk["bf16_sustained"] * TF32_OVER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf32, "traffic": TRAFFIC.get(dom),
-                "kernel": f"k_gemm_tc ({names.get(dom)}), mean {per_launch:.3e} algorithmic flop "
-                          f"per launch (2 N^3 full, N^2 (N + 1) symmetric), mean "
-                          f"{avg_s * 1e3:.3f} ms over {eng_n[dom]} launches",
-                "peak_note": f"tf32 = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
-                             f"{TF32_OVER_BF16:.4f} (nominal 1.1/2.25) of measured",
-                "tensor_pipe_frac": achieved * (3 if dom == 3 else 1) / peak_tf32}
+        peak, pnote = mpk["tf32_tflops_sustained"], "measured sustained TF32 cuBLAS 8192^3 in this run"
+        roof = {"bound": "tensor"}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": TRAFFIC.get(dom),
+                 "kernel": f"{ENGINE_NAMES.get(dom)}: mean {per_launch:.3e} algorithmic flop per "
+                           f"launch (2 M N K full, N^2 (N + 1) symmetric), mean "
+                           f"{avg_s * 1e3:.3f} ms over {eng_n[dom]} launches",
+                 "peak_note": pnote + " (of measured)",
+                 "tensor_pipe_frac": achieved * PIPE_FACTOR.get(dom, 1.0) / peak})
     launches = sum(s["kernel_launches"] for s in st_all)
-    gemm_ms_total = sum(eng_ms)
+    engines = {}
+    for e in range(n_eng):
+        if not eng_n[e]:
+            continue
+        ach = eng_fl[e] / (eng_ms[e] / 1e3) / 1e12 if eng_ms[e] else None
+        pe = (mpk["fp64_tflops"] if e == 1 else pk["bf16_sustained"] if e in (4, 5)
+              else mpk["tf32_tflops_sustained"])
+        engines[ENGINE_NAMES.get(e, str(e))] = {
+            "ms_per_step": eng_ms[e] / args.steps, "launches_per_step": eng_n[e] / args.steps,
+            "algorithmic_tflops": ach, "frac_of_peak": ach / pe if ach else None,
+            "tensor_pipe_frac": ach * PIPE_FACTOR.get(e, 1.0) / pe if ach else None}
 
     # end to end through the public API with host buffers (pinned), copies inside the region
-    H0h = torch.from_numpy(probs[0].H0).pin_memory()
-    H1h = torch.from_numpy(probs[0].H1).pin_memory()
-    P0h = torch.empty((N, N), dtype=torch.float64).pin_memory()
-    P1h = torch.empty((D, N, N), dtype=torch.float64).pin_memory()
+    host = []
+    for p in probs:
+        host.append({"H0": torch.from_numpy(p.H0).pin_memory(),
+                     "H1": torch.from_numpy(p.H1).pin_memory(),
+                     "P0": torch.empty((p.N, p.N), dtype=torch.float64).pin_memory(),
+                     "P1": torch.empty((p.D, p.N, p.N), dtype=torch.float64).pin_memory(),
+                     "mu": ctypes.c_double(), "mu1": np.zeros(p.D)})
     ke = max(1, min(args.steps, 2))
     barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
-        pkg.set_H(h.h, N, H0h.data_ptr(), D, H1h.data_ptr(), 0)
-        for p in probs:
-            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, P0h.data_ptr(), P1h.data_ptr(),
-                          ctypes.addressof(mu), mu1.ctypes.data, 0)
+        for h, p, b in zip(hs, probs, host):
+            pkg.set_H(h.h, p.N, b["H0"].data_ptr(), p.D, b["H1"].data_ptr(), 0)
+            pkg.solve_raw(h.h, p.beta, p.nocc, p.n, b["P0"].data_ptr(), b["P1"].data_ptr(),
+                          ctypes.addressof(b["mu"]), b["mu1"].ctypes.data, 0)
     torch.cuda.synchronize()
     dte = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": ke * len(probs) * world / dte, "unit": "solves/s",
-           "h2d_bytes_per_step": (H0h.numel() + H1h.numel()) * 8,
-           "d2h_bytes_per_step": len(probs) * (P0h.numel() + P1h.numel()) * 8, "steps": ke}
-    h.set_H(H0, H1)
+           "h2d_bytes_per_step": sum((b["H0"].numel() + b["H1"].numel()) * 8 for b in host),
+           "d2h_bytes_per_step": sum((b["P0"].numel() + b["P1"].numel()) * 8 for b in host),
+           "steps": ke}
 
-    # the other precisions on the same workload (one step each), for "mixed vs FP32"
-    modes = {}
-    outs_by_mode = {}
-    if not args.no_compare:
-        for label, prec, eng in (("fp32_3xtf32", "fp32", "3xtf32"), ("fp32_ffma", "fp32", "simt"),
-                                 (args.precision, args.precision, "auto")):
-            hm = make(prec, eng) if label != args.precision else h
-            step(hm)            # warm-up (allocations)
-            stm = []
-            msm = timed_steps(hm, 1, stm)
-            outs = []
-            step(hm, None, outs)
-            outs_by_mode[label] = outs
-            modes[label] = {"solves_per_s": len(probs) / (msm / 1000.0), "ms_per_step": msm}
-            if hm is not h:
-                hm.close()
+    # FP32 (split-TF32 products) on the same workload, for "mixed vs FP32"
+    fp32 = None
+    outs_fp32 = []
+    if not args.no_compare and args.precision != "fp32":
+        hf = make("fp32")
+        step(hf)                    # warm-up (allocations)
+        stf = []
+        msf = max_over_ranks(timed_steps(hf, 1, stf))
+        step(hf, None, outs_fp32)
+        fp32 = {"solves_per_s": len(probs) * world / (msf / 1000.0), "ms_per_step": msf,
+                "speedup_of_timed_precision": value / (len(probs) * world / (msf / 1000.0))}
+        for h in hf:
+            h.close()
+    for h in hs:
+        h.close()
+    torch.cuda.empty_cache()
 
-    if "fp32_3xtf32" in modes and "fp32_ffma" in modes and args.precision in modes:
-        me = modes[args.precision]["solves_per_s"]
-        modes["speedup_vs_fp32_3xtf32"] = me / modes["fp32_3xtf32"]["solves_per_s"]
-        modes["speedup_vs_fp32_ffma"] = me / modes["fp32_ffma"]["solves_per_s"]
+    extras = {}
+    if not args.no_extras:
+        extras["cubic16_n4096"] = run_c2(pkg, args, barrier, max_over_ranks, world, rank)
+        if not args.no_batch:
+            extras["batched"] = run_batched(pkg, args, barrier, max_over_ranks, rank, world)
+        extras["fp64_n2048"] = run_fp64(pkg, mpk, rank)
+    if args.screen and rank == 0:
+        extras["screened_chain"] = run_screened(
+            pkg, sizes=[int(x) for x in args.screen_sizes.split(",") if x])
 
-    # batched workload: 96 disordered clusters, N_b ~ U{128..1536}, 3 directions, beta 20, n 12
-    batched = None
-    if not args.no_batch:
-        batched = run_batched(pkg, args, barrier, max_over_ranks, rank, world)
-
-    # the N = 8192 product chain: one mixed solve of the banded workload, per-engine rates
-    chain = None
-    if not args.no_chain:
-        chain = run_chain(pkg, pk)
-
-    # block-sparse screened products on the 1D chain (Sec. VI): dense against screened
-    screened = None
-    if not args.no_screen and rank == 0:
-        screened = run_screened(pkg, sizes=[int(x) for x in args.screen_sizes.split(",") if x])
-
-    cpu = None
-    cpu1 = None
-    err = None
+    cpu = cpu1 = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # bounded oracle sample: the beta = 20 solve of the workload, eigendecomposition included
-        import oracle
-        v, dt, res = time_oracle([20.0])
-        cpu = {"value": v, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"1 of the 3 solves of a step (beta=20, N=4096), {dt:.1f} s"}
+        refs, t_or = [], 0.0
+        for p in probs:
+            r, dt = oracle_solve(p)
+            refs.append(r)
+            t_or += dt
+        cpu = {"value": len(probs) / t_or, "unit": "solves/s", "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": f"one oracle solve of each system (dsyevd N=8000 and 8192, bisection on "
+                         f"mu, Daleckii-Krein P1, mu1, alpha) in {t_or:.1f} s"}
         cpu1 = time_oracle_one_core()
-        if outs_by_mode:
-            eig = np.linalg.eigh(probs[0].H0)
-            refs = {p.beta: oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=eig)
-                    for p in probs}
-            err = {"vs": "oracle, recursion-exact function (relative Frobenius)"}
-            for label, outs in outs_by_mode.items():
-                err[label] = {f"beta={p.beta:g}": {
-                    "P0": oracle.rel_frobenius(o[0], refs[p.beta]["P0"]),
-                    "P1": oracle.rel_frobenius(o[1], refs[p.beta]["P1"][0])}
-                    for p, o in zip(probs, outs)}
+        err = {"vs": "oracle, recursion-exact function: P0, P1 relative Frobenius; mu1, alpha "
+                     "relative; worst direction"}
+        for label, outs in ((args.precision, outs_main), ("fp32", outs_fp32)):
+            if outs:
+                err[label] = {c: _errors(o, r, p.D) for c, o, r, p in zip(C3, outs, refs, probs)}
+                err[label]["max"] = max(v["max"] for v in err[label].values())
 
     if rank == 0:
         s_last = st_all[-len(probs):]
@@ -409,15 +486,17 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "tf32+f32"}[args.precision],
+            "dtype": {"fp32": "f32 (3xtf32 products)", "fp64": "f64",
+                      "mixed": "tf32 + bf16-digit products, f32-pair storage"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "gemm": {"fp32": "tcgen05 3xTF32", "fp64": "CUDA-core DFMA",
-                                "mixed": "tcgen05 TF32 sweeps and response CG iterations, 3xTF32 "
-                                         "refinement, response right-hand sides and restarts"
-                                }[args.precision],
-                       "l2": "no flush: working set (trajectory of 29 N x N matrices plus "
-                             "their TF32 splits, 5.4 GiB) exceeds the 129 MB L2",
+                                "mixed": "tcgen05 TF32 sweeps and CG iterations; 3xTF32 "
+                                         "refinement of early steps, response right-hand sides "
+                                         "and restarts; Ozaki BF16-digit (FP64-class) residuals "
+                                         "of the late steps and of dP0/dmu"}[args.precision],
+                       "l2": "no flush: working set (trajectory of 29 N x N matrices as pairs "
+                             "with their TF32 splits, about 30 GiB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -425,70 +504,95 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
-            "modes": modes,
-            "batched": batched,
-            "chain_n8192": chain,
-            "screened_chain": screened,
+            "fp32": fp32,
             "error": err,
+            "peaks": {**mpk, "bf16_tflops": pk["bf16"], "bf16_tflops_sustained": pk["bf16_sustained"],
+                      "hbm_gbs": pk["hbm_gbs"], "bf16_hbm_source": pk["source"]},
+            "engines": engines,
+            "extras": extras,
             "detail": {
-                "gemm_share_of_step_time": gemm_ms_total / (ms / world) if ms else None,
-                "gemm_ms_per_engine": {names.get(e, e): eng_ms[e] / args.steps for e in range(n_eng)
-                                       if eng_n[e]},
+                "gemm_share_of_step_time": sum(eng_ms) / (ms / world) if ms else None,
                 "gemm_launches_per_step": sum(eng_n) / args.steps,
                 "algorithmic_tflop_per_step": sum(eng_fl) / args.steps / 1e12,
-                "per_beta": [{"beta": p.beta, "mu_iterations": s["mu_iterations"],
-                              "cg_sweeps": s["cg_iterations_sweeps"],
-                              "cg_refine": s["cg_iterations_refine"],
-                              "cg_response": s["cg_iterations_response"],
-                              "cg_q": s["cg_iterations_q"],
-                              "seconds": s["seconds"]} for p, s in zip(probs, s_last)],
+                "per_system": [{"system": c, "mu_iterations": s["mu_iterations"],
+                                "cg_sweeps": s["cg_iterations_sweeps"],
+                                "cg_refine": s["cg_iterations_refine"],
+                                "fp64_residual_passes": s["fp64_residual_passes"],
+                                "fp64_residual_first_step": s["fp64_residual_first_step"],
+                                "cg_response": s["cg_iterations_response"],
+                                "cg_q": s["cg_iterations_q"],
+                                "seconds": s["seconds"]} for c, s in zip(C3, s_last)],
             },
         }
         print(json.dumps(line), flush=True)
-    h.close()
     if pg:
         pg.destroy_process_group()
     return 0
 
 
-def run_chain(pkg, pk):
-    """GEMM chain at N = 8192: one mixed-precision solve of the banded workload (bandwidth 64,
-    beta 20, n 14) with every product timed; achieved rate per engine against the TF32 peak."""
+def run_c2(pkg, args, barrier, max_over_ranks, world, rank):
+    """The 16^3 lattice (N = 4096, n 14) at beta 5, 20 and 80: one step (three solves) in mixed
+    precision and in FP32, with every output against the oracle."""
+    import numpy as np
     import torch
 
     import synthetic
-    p = synthetic.workload("banded8192")
-    names = {1: "CUDA-core", 2: "tcgen05 TF32", 3: "tcgen05 3xTF32"}
-    peak = pk["bf16_sustained"] * TF32_OVER_BF16
-    with pkg.Handle(precision="mixed", profile=True) as h:
+    probs = [synthetic.cubic_lattice((16, 16, 16), seed=1002, beta=b, n=14) for b in C2_BETAS]
+    out = {"workload": "16x16x16 lattice, N=4096, n=14, D=1, beta 5, 20, 80; one step = 3 solves"}
+    res = {}
+    for prec in ("mixed", "fp32"):
+        with pkg.Handle(precision=prec) as h:
+            h.set_H(probs[0].H0, probs[0].H1)
+            for p in probs:
+                h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)   # warm-up
+            barrier()
+            t0 = time.perf_counter()
+            rs = []
+            for p in probs:
+                r = h.solve(p.beta, p.nocc, p.n)
+                torch.cuda.synchronize()
+                rs.append({"P0": r["P0"].cpu().numpy(), "P1": r["P1"].cpu().numpy(),
+                           "mu1": np.asarray(r["mu1"]), "alpha": h.polarizability()})
+            dt = max_over_ranks(time.perf_counter() - t0)
+        out[prec] = {"solves_per_s": len(probs) * world / dt}
+        res[prec] = rs
+    out["mixed_vs_fp32"] = out["mixed"]["solves_per_s"] / out["fp32"]["solves_per_s"]
+    if rank == 0 and not args.no_cpu_baseline:
+        eig = np.linalg.eigh(probs[0].H0)
+        refs = [oracle_solve(p, eig)[0] for p in probs]
+        for prec, rs in res.items():
+            out[prec]["error"] = {f"beta={p.beta:g}": _errors(r, ref, p.D)
+                                  for p, r, ref in zip(probs, rs, refs)}
+    return out
+
+
+def run_fp64(pkg, mpk, rank):
+    """One FP64 solve of the 16 x 16 x 8 lattice (N = 2048) at beta 20 (CUDA-core DFMA products),
+    with its rate against the measured FP64 library rate and its error against the oracle. (The
+    16^3 lattice takes 75 s per FP64 solve on this GPU; its parity is a GPU test.)"""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synthetic
+    p = synthetic.cubic_lattice((16, 16, 8), seed=1002, beta=20.0, n=14)
+    with pkg.Handle(precision="fp64", profile=True) as h:
         h.set_H(p.H0, p.H1)
-        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+        r = h.solve(p.beta, p.nocc, p.n)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         st = h.stats()
-    out = {"workload": "banded N=8192 (bandwidth 64, seed 1004), beta 20, n 14, mixed precision",
-           "solve_s": dt, "engines": {}}
-    tensor_fl = 0.0
-    gemm_s = 0.0
-    for e in (2, 3):
-        n_l = st["engine_launches"][e]
-        if not n_l:
-            continue
-        ms = st["engine_ms"][e]
-        fl = st["engine_flops"][e]
-        ach = fl / (ms / 1e3) / 1e12
-        tensor_fl += fl * (3 if e == 3 else 1)
-        gemm_s += ms / 1e3
-        out["engines"][names[e]] = {"launches": n_l, "ms": ms, "algorithmic_tflops": ach,
-                                    "frac_of_tf32_peak": ach / peak,
-                                    "tensor_pipe_frac": ach * (3 if e == 3 else 1) / peak}
-    out["tensor_pipe_frac_all_products"] = (tensor_fl / gemm_s / 1e12 / peak) if gemm_s else None
-    out["gemm_share_of_solve"] = gemm_s / dt if dt else None
-    out["peak_note"] = (f"tf32 peak = {pk['source']} sustained bf16 {pk['bf16_sustained']} x "
-                        f"{TF32_OVER_BF16:.4f}")
+        alpha = h.polarizability()
+    ach = st["engine_flops"][1] / (st["engine_ms"][1] / 1e3) / 1e12 if st["engine_ms"][1] else None
+    out = {"workload": "16x16x8 lattice, N=2048, beta 20, n 14, FP64", "solve_s": dt,
+           "gemm_tflops": ach, "fp64_peak_tflops": mpk["fp64_tflops"],
+           "frac_of_fp64_peak": ach / mpk["fp64_tflops"] if ach else None}
+    if rank == 0:
+        ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+        out["error"] = _errors({"P0": r["P0"].cpu().numpy(), "P1": r["P1"].cpu().numpy(),
+                                "mu1": np.asarray(r["mu1"]), "alpha": alpha}, ref, p.D)
     return out
 
 
@@ -623,19 +727,19 @@ def run_batched(pkg, args, barrier, max_over_ranks=lambda x: x, rank=0, world=1)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the N = 4096 lattice, batch and FP64 measurements")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched 96-cluster measurement")
-    ap.add_argument("--no-chain", action="store_true",
-                    help="skip the N = 8192 product-chain measurement")
-    ap.add_argument("--no-screen", action="store_true",
-                    help="skip the screened-product (block-sparse) chain measurement")
     ap.add_argument("--no-compare", action="store_true",
-                    help="skip the one-step runs of the other precisions")
+                    help="skip the FP32 step on the same workload")
+    ap.add_argument("--screen", action="store_true",
+                    help="add the screened-product (block-sparse) chain measurement")
     ap.add_argument("--screen-sizes", default="4096,8192,16384",
                     help="chain sizes of the screened-product measurement")
     ap.add_argument("--screened-only", action="store_true",

@@ -404,7 +404,10 @@ cdmpt_status cdmpt_spectral_bounds(const double* H, int N, int ldh, double* boun
  * kernels overlap on the GPU (different streams, or different host threads)
  * race on it and must be serialised by the caller. The first call on a
  * device looks up the array's device address; make that first call before
- * any stream capture begins. No call allocates or frees memory.
+ * any stream capture begins. The address is kept for the life of the process:
+ * after cudaDeviceReset (or any reset of the device's primary context) the
+ * library's module is reloaded elsewhere and this entry point must not be
+ * called again on that device. No call allocates or frees memory.
  * Errors: ERR_ARG (N < 1, N > 32768, ldh < N, NULL pointers), ERR_CUDA. */
 cdmpt_status cdmpt_spectral_bounds_noalloc(const double* H, int N, int ldh, double* bounds,
                                            void* stream);

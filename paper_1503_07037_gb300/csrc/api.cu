@@ -459,7 +459,7 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
                 ms += e;
                 ++timed;
                 const int eng = h->cx.ev_engine[i];
-                if (eng < 0 || eng > 4) continue;
+                if (eng < 0 || eng > 5) continue;
                 h->st.engine_ms[eng] += e;
                 h->st.engine_launches[eng] += 1;
                 h->st.engine_flops[eng] += h->cx.ev_flops[i];

@@ -38,17 +38,23 @@ def _solve(pkg, p, precision, tau):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_screening_is_exact_on_decoupled_chains(cuda, cdmpt_lib, precision):
-    blocks = [syn.chain_1d(128, 11 + i, 10.0, 12) for i in range(4)]
+@pytest.mark.parametrize("sizes", [(128, 128, 128, 128), (100, 156, 200, 54)])
+def test_screening_is_exact_on_decoupled_chains(cuda, cdmpt_lib, precision, sizes):
+    """Block-diagonal chains: every screened term is an exact zero, so the screened solve equals
+    the dense one bit for bit. The second block layout is not aligned to the 128 x 128 tiles and
+    N = 510 is not a multiple of 4: the tiles screened to nothing then include partial edge
+    tiles, whose epilogue takes the scalar tail, next to full ones (and the transposed placement
+    of the response's right-hand side)."""
+    blocks = [syn.chain_1d(nb, 11 + i, 10.0, 12) for i, nb in enumerate(sizes)]
     H0 = sl.block_diag(*[b.H0 for b in blocks])
     H1 = sl.block_diag(*[b.H1[0] for b in blocks])[None]
-    p = syn.Problem("four_chains_128", H0, H1, sum(b.nocc for b in blocks), 10.0, 12)
+    p = syn.Problem("four_chains", H0, H1, sum(b.nocc for b in blocks), 10.0, 12)
     dense = _solve(cdmpt_lib, p, precision, 0.0)
     scr = _solve(cdmpt_lib, p, precision, 1e-30)
     assert np.array_equal(dense["P0"], scr["P0"])
     assert np.array_equal(dense["P1"], scr["P1"])
     assert dense["examined"] == 0.0
-    assert 0.0 < scr["computed"] < 0.1 * scr["examined"]
+    assert 0.0 < scr["computed"] < (0.1 if sizes[0] == 128 else 0.5) * scr["examined"]
 
 
 @pytest.fixture(scope="module")
