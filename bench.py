@@ -517,10 +517,13 @@ def run_ours(args):
                 "per_system": [{"system": c, "mu_iterations": s["mu_iterations"],
                                 "cg_sweeps": s["cg_iterations_sweeps"],
                                 "cg_refine": s["cg_iterations_refine"],
+                                "refine_passes": s["refine_passes"],
                                 "fp64_residual_passes": s["fp64_residual_passes"],
                                 "fp64_residual_first_step": s["fp64_residual_first_step"],
                                 "cg_response": s["cg_iterations_response"],
                                 "cg_q": s["cg_iterations_q"],
+                                "phase_ms": dict(zip(("sweeps", "refine", "response", "q_mu1_alpha",
+                                                      "output"), s["phase_ms"])),
                                 "seconds": s["seconds"]} for c, s in zip(C3, s_last)],
             },
         }

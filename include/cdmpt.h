@@ -62,9 +62,11 @@ typedef enum {
 typedef enum {
     CDMPT_FP64 = 0,       /* FP64 storage, FP64 products (CUDA-core DFMA) */
     CDMPT_FP32 = 1,       /* FP32 storage, FP32-accurate products (3xTF32 on tcgen05 by default) */
-    CDMPT_MIXED_TF32 = 2, /* one-pass TF32 products for the occupation sweeps, split-TF32
-                             (FP32-accurate) residual refinement of the trajectory and
-                             split-TF32 response */
+    CDMPT_MIXED_TF32 = 2, /* one-pass TF32 products for the occupation sweeps; iterative
+                             refinement of the pair-stored (hi + lo FP32) trajectory with
+                             split-TF32 residuals on the early steps and FP64-class
+                             (Ozaki-sliced BF16) residuals on the late ones (fp64_residual);
+                             split-TF32 response right-hand sides */
     CDMPT_MIXED_BF16 = 3  /* as MIXED_TF32 with BF16 products (FP32 accumulation) for the
                              occupation sweeps */
 } cdmpt_precision;
@@ -125,11 +127,14 @@ typedef struct {
                            MIXED_TF32 with the tcgen05 engines only (ERR_ARG otherwise);
                            0 (the default) keeps every product dense. */
     int fp64_residual;  /* MIXED_* only: the refinement that recovers accuracy keeps the
-                           0th-order trajectory Z_0 .. Z_n as FP32 pairs (about 48 bits) and
-                           ends with a pass whose step residuals r_k = 2 Z_k - Z_{k+1} A_k
-                           (Algorithm 1's per-step system) and step matrices A_k = I + Z_k^2
-                           come from Ozaki-sliced BF16 tensor-core products accurate to about
-                           2^-31 (cdmpt_gemm_pair) instead of split-TF32 ones. 0 (default):
+                           0th-order trajectory Z_0 .. Z_n as FP32 pairs (about 48 bits).
+                           Once the split-TF32 passes have settled, every further pass (and
+                           the Newton steps on mu between them) forms the step residuals
+                           r_k = 2 Z_k - Z_{k+1} A_k (Algorithm 1's per-step system) and step
+                           matrices A_k = I + Z_k^2 of the chosen steps with Ozaki-sliced
+                           BF16 tensor-core products accurate to about 2^-39 of the row
+                           maxima (cdmpt_gemm_pair) instead of split-TF32 ones; the right
+                           side I - Z_n^2 of dP0/dmu is formed the same way. 0 (default):
                            on the steps whose spectral bound tanh(2^k atanh rho) exceeds
                            1/2, rho = beta max|lambda - mu| / 2^(n+1) over the Gershgorin
                            interval (for the earlier steps the split-TF32 residual is already
@@ -163,6 +168,10 @@ typedef struct {
     double screen_slices_examined; /* multiplied, and all slices of their output tiles */
     int fp64_residual_passes;      /* refinement passes with Ozaki-sliced (FP64-class) residuals */
     int fp64_residual_first_step;  /* first step k they covered (n: none) */
+    int refine_passes;             /* refinement passes of the mixed precisions, all kinds */
+    double phase_ms[5];            /* device time of the solve's phases (profile = 1): occupation
+                                      sweeps, refinement, first-order response, dP0/dmu with mu1
+                                      and alpha, output of P0 and P1 */
 } cdmpt_stats;
 
 typedef struct cdmpt_handle cdmpt_handle;
@@ -428,8 +437,9 @@ void cdmpt_destroy(cdmpt_handle* h);
  * all systems, every vector update one grouped launch; each system keeps its
  * own CG scalars and chemical potential, and converged systems are skipped.
  * Storage FP32. CDMPT_FP32: split-TF32 products throughout. CDMPT_MIXED_TF32:
- * one-pass TF32 occupation sweeps, then split-TF32 refinement of every
- * trajectory and a split-TF32 response, as in cdmpt_solve.
+ * one-pass TF32 occupation sweeps, then refinement of every pair-stored
+ * trajectory (split-TF32 passes, then FP64-class residuals on the late steps)
+ * and a split-TF32 response, as in cdmpt_solve.
  */
 typedef struct cdmpt_batch cdmpt_batch;
 

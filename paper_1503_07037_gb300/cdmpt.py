@@ -91,6 +91,8 @@ class Stats(ctypes.Structure):
         ("screen_slices_examined", ctypes.c_double),
         ("fp64_residual_passes", ctypes.c_int),
         ("fp64_residual_first_step", ctypes.c_int),
+        ("refine_passes", ctypes.c_int),
+        ("phase_ms", ctypes.c_double * 5),
     ]
 
     def as_dict(self):

@@ -411,6 +411,7 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
     h->st.n = n;
     h->cx.st = &h->st;
     h->cx.ev_used = 0;
+    for (bool& b : h->cx.ph_set) b = false;
     h->solved = false;
     h->alpha.assign(h->D, 0.0);
     const long long launches0 = launch_count();
@@ -467,6 +468,15 @@ cdmpt_status cdmpt_solve(cdmpt_handle* h, double beta, double nocc, int n, doubl
         }
         h->st.gemm_ms = ms;
         h->st.gemm_timed = timed;
+        // phases: the span from each recorded boundary to the next recorded one
+        for (int i = 0; i < 5; ++i) {
+            if (!h->cx.ph_set[i]) continue;
+            int j = i + 1;
+            while (j < 6 && !h->cx.ph_set[j]) ++j;
+            float e = 0;
+            if (j < 6 && cudaEventElapsedTime(&e, h->cx.ph[i], h->cx.ph[j]) == cudaSuccess)
+                h->st.phase_ms[i] = e;
+        }
     }
     if (s != CDMPT_OK) return fail(h, s);
     h->solved = true;
@@ -992,6 +1002,8 @@ void cdmpt_destroy(cdmpt_handle* h) {
     delete h->sf;
     delete h->sd;
     for (cudaEvent_t e : h->cx.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->cx.ph)
+        if (e) cudaEventDestroy(e);
     cudaFree(h->H0);
     cudaFree(h->H1);
     cudaFree(h->H2);

@@ -107,9 +107,15 @@ struct cdmpt_batch {
     std::string err;
     bool have_H = false;
     // mixed precision: Ozaki digits of three operands (sized for the largest system) and the
-    // low part of an Ozaki-formed W_k, shared by the systems one after another
-    OzOperand oz[3];
-    float* oz_wl = nullptr;
+    // low part of an Ozaki-formed W_k, one set per lane; the systems' FP64-class residuals run
+    // on kHpLanes side streams, system i on lane i % kHpLanes, so the small products of
+    // different systems share the GPU (lane 0's set also serves the dP0/dmu right side)
+    static constexpr int kHpLanes = 4;
+    OzOperand oz[kHpLanes][3];
+    float* oz_wl[kHpLanes] = {};
+    cudaStream_t hp_st[kHpLanes] = {};
+    cudaEvent_t hp_fork = nullptr;
+    cudaEvent_t hp_join[kHpLanes] = {};
 };
 
 namespace {
@@ -738,20 +744,39 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
 // digit buffers); W_k's FP32 part and split replace the stored W_k, the residual goes to RHS.
 cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& active) {
     cudaStream_t s = b->cx.stream;
+    int nact = 0;
+    for (int i = 0; i < b->B; ++i) nact += active[i] ? 1 : 0;
+    if (nact == 0) return CDMPT_OK;
+    const int L = std::min(nact, (int)cdmpt_batch::kHpLanes);
+    if (!b->hp_fork) {
+        CDMPT_CUDA_TRY(cudaEventCreateWithFlags(&b->hp_fork, cudaEventDisableTiming));
+        for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
+            CDMPT_CUDA_TRY(cudaStreamCreateWithFlags(&b->hp_st[l], cudaStreamNonBlocking));
+            CDMPT_CUDA_TRY(cudaEventCreateWithFlags(&b->hp_join[l], cudaEventDisableTiming));
+        }
+    }
+    // the lanes start after everything queued on the batch's stream
+    CDMPT_CUDA_TRY(cudaEventRecord(b->hp_fork, s));
+    for (int l = 0; l < L; ++l) CDMPT_CUDA_TRY(cudaStreamWaitEvent(b->hp_st[l], b->hp_fork, 0));
+    int j = 0;
     for (int i = 0; i < b->B; ++i) {
         if (!active[i]) continue;
+        const int l = j++ % L;
+        cudaStream_t ls = b->hp_st[l];
+        OzOperand* oz = b->oz[l];
+        float* wl = b->oz_wl[l];
         Sys& sy = b->sys[i];
-        for (auto& o : b->oz) o.ld = sy.ld;
-        CDMPT_TRY(oz_slice(sy.Z[k].x, sy.Z[k].xl, sy.N, sy.N, sy.ld, b->oz[0], s));
+        for (int a = 0; a < 3; ++a) oz[a].ld = sy.ld;
+        CDMPT_TRY(oz_slice(sy.Z[k].x, sy.Z[k].xl, sy.N, sy.N, sy.ld, oz[0], ls));
         OzEpi w;
         w.D = sy.W[k].x;
-        w.Dl = b->oz_wl;
+        w.Dl = wl;
         w.Dthi = sy.W[k].hi;
         w.Dtlo = sy.W[k].lo;
         w.ldd = sy.ld;
-        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[0], b->oz[0], w, s));
-        CDMPT_TRY(oz_slice(sy.W[k].x, b->oz_wl, sy.N, sy.N, sy.ld, b->oz[1], s));
-        CDMPT_TRY(oz_slice(sy.Z[k + 1].x, sy.Z[k + 1].xl, sy.N, sy.N, sy.ld, b->oz[2], s));
+        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, oz[0], oz[0], w, ls));
+        CDMPT_TRY(oz_slice(sy.W[k].x, wl, sy.N, sy.N, sy.ld, oz[1], ls));
+        CDMPT_TRY(oz_slice(sy.Z[k + 1].x, sy.Z[k + 1].xl, sy.N, sy.N, sy.ld, oz[2], ls));
         OzEpi r;
         r.D = sy.RHS.x;
         r.ldd = sy.ld;
@@ -763,13 +788,18 @@ cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& a
         r.c2h = sy.Z[k + 1].x;
         r.c2l = sy.Z[k + 1].xl;
         r.ldc = sy.ld;
-        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[2], b->oz[1], r, s));
+        CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, oz[2], oz[1], r, ls));
         if (b->cx.st) {
             const double f = 2.0 * sy.N * (double)sy.N * sy.N;
             b->cx.st->gemm_launches += 2;
             b->cx.st->gemm_flops += 2.0 * f;
-            b->cx.st->tensor_flops += 20.0 * f;
+            b->cx.st->tensor_flops += 2.0 * oz_products(kOzDigits) * f;
         }
+    }
+    // and the batch's stream continues after all lanes
+    for (int l = 0; l < L; ++l) {
+        CDMPT_CUDA_TRY(cudaEventRecord(b->hp_join[l], b->hp_st[l]));
+        CDMPT_CUDA_TRY(cudaStreamWaitEvent(s, b->hp_join[l], 0));
     }
     return CDMPT_OK;
 }
@@ -926,10 +956,12 @@ cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
             mblk = std::max(mblk, sy.blk);
             mN = std::max(mN, sy.N);
         }
-        CDMPT_TRY(grab(b, mblk * sizeof(float), (void**)&b->oz_wl));
-        for (auto& o : b->oz) {
-            for (int d = 0; d < kOzDigits; ++d) CDMPT_TRY(grab(b, mblk * 2, &o.s[d]));
-            CDMPT_TRY(grab(b, (size_t)mN * sizeof(int), (void**)&o.e));
+        for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
+            CDMPT_TRY(grab(b, mblk * sizeof(float), (void**)&b->oz_wl[l]));
+            for (auto& o : b->oz[l]) {
+                for (int d = 0; d < kOzDigits; ++d) CDMPT_TRY(grab(b, mblk * 2, &o.s[d]));
+                CDMPT_TRY(grab(b, (size_t)mN * sizeof(int), (void**)&o.e));
+            }
         }
     }
     b->n_alloc = n;
@@ -1175,6 +1207,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             cdmpt_status s = refine_batch(b, n, hp_phase ? k_hp : n, active, &iters);
             if (s != CDMPT_OK) return bfail(b, s);
             b->st.cg_iterations_refine += iters;
+            b->st.refine_passes += 1;
             if (hp_phase) b->st.fp64_residual_passes += 1;
             s = occupations(b, n);
             if (s != CDMPT_OK) return bfail(b, s);
@@ -1366,8 +1399,8 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 // the Ozaki-sliced product, system by system
                 for (int i = 0; i < G; ++i) {
                     Sys& sy = b->sys[i];
-                    for (auto& o : b->oz) o.ld = sy.ld;
-                    CDMPT_TRY(oz_slice(sy.Z[n].x, sy.Z[n].xl, sy.N, sy.N, sy.ld, b->oz[0], st));
+                    for (auto& o : b->oz[0]) o.ld = sy.ld;
+                    CDMPT_TRY(oz_slice(sy.Z[n].x, sy.Z[n].xl, sy.N, sy.N, sy.ld, b->oz[0][0], st));
                     OzEpi q;
                     q.D = sy.RHS.x;
                     q.Dthi = sy.RHS.hi;
@@ -1375,12 +1408,12 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                     q.ldd = sy.ld;
                     q.alpha = -1.f;
                     q.gamma = 1.f;
-                    CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[0], b->oz[0], q, st));
+                    CDMPT_TRY(gemm_oz(sy.N, sy.N, sy.N, b->oz[0][0], b->oz[0][0], q, st));
                     if (b->cx.st) {
                         const double f = 2.0 * sy.N * (double)sy.N * sy.N;
                         b->cx.st->gemm_launches += 1;
                         b->cx.st->gemm_flops += f;
-                        b->cx.st->tensor_flops += 10.0 * f;
+                        b->cx.st->tensor_flops += oz_products(kOzDigits) * f;
                     }
                 }
             } else {
@@ -1524,6 +1557,11 @@ void cdmpt_batch_destroy(cdmpt_batch* b) {
     if (!b) return;
     drop_graphs(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
+        if (b->hp_st[l]) cudaStreamDestroy(b->hp_st[l]);
+        if (b->hp_join[l]) cudaEventDestroy(b->hp_join[l]);
+    }
+    if (b->hp_fork) cudaEventDestroy(b->hp_fork);
     for (void* p : b->allocs) cudaFree(p);
     if (b->stage_host) cudaFreeHost(b->stage_host);
     if (b->stage_dev) cudaFree(b->stage_dev);

@@ -18,6 +18,11 @@
 // loads the hi and lo tiles of both operands, so the MMA forms
 // lo*hi + hi*lo + hi*hi (Ootomo & Yokota's split-TF32 scheme) with FP32
 // accumulation in TMEM, restarted every KCH k-blocks and summed in registers.
+// Each MMA truncates its FP32 result (an error of up to one unit in the last
+// place of the accumulator), so within a k-block the eight cross-term MMAs,
+// about 2^-11 of the result, are issued before the four hi*hi ones: on the
+// first k-block of a chunk they are truncated at the scale of a small
+// accumulator.
 // The finished sums of a tile are parked in a TMEM sum buffer and stored four
 // columns at a time between the chunk drains of the next tile (tc_deferred.cuh),
 // so the global stores overlap the MMAs.
@@ -375,13 +380,22 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
                             const uint64_t ah = sw128_desc(a0 + off), bh = sw128_desc(b0 + off);
                             const uint32_t first = ((q - kb0) | kk) != 0 ? 1u : 0u;
                             if constexpr (PASSES == 3) {
+                                // the two cross terms of the k-block come first, while the
+                                // chunk's accumulator is small (see the note on the order)
                                 const uint64_t al = sw128_desc(smem_u32(stage_alo(s)) + off);
                                 const uint64_t bl = sw128_desc(smem_u32(stage_blo(s)) + off);
                                 mma_tf32(tmem_d, al, bh, idesc, first);
                                 mma_tf32(tmem_d, ah, bl, idesc, 1u);
-                                mma_tf32(tmem_d, ah, bh, idesc, 1u);
                             } else {
                                 mma_tf32(tmem_d, ah, bh, idesc, first);
+                            }
+                        }
+                        if constexpr (PASSES == 3) {
+#pragma unroll
+                            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                                const uint32_t off = kk * UMMA_K * 4;
+                                mma_tf32(tmem_d, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc,
+                                         1u);
                             }
                         }
                         issued = true;
@@ -636,16 +650,16 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     return CDMPT_OK;
 }
 
-// Kernel family for single (non-grouped) products: one SM per tile or the
-// two-SM MMA (cta_group::2, 256-row tiles). Default: two-SM for TF32, one-SM for 3xTF32 (measured fastest);
-// CDMPT_TC_MODE=1sm|2sm forces one family.
-bool use_2sm(bool three) {
+// Kernel family for single (non-grouped) products with more than 128 rows: one SM per
+// tile or the two-SM MMA (cta_group::2, 256 x 256 tiles; for split TF32 the wide kernel
+// k_gemm_split2sm). Default: two-SM for both; CDMPT_TC_MODE=1sm|2sm forces one family.
+bool use_2sm(bool /*three*/) {
     static int v = -2;
     if (v == -2) {
         const char* e = getenv("CDMPT_TC_MODE");
         v = !e ? -1 : (std::strcmp(e, "2sm") == 0 ? 1 : 0);
     }
-    return v < 0 ? !three : v == 1;
+    return v != 0;
 }
 
 template <int BN, int STAGES, int PASSES, int KCH>
@@ -849,10 +863,13 @@ cdmpt_status gemm_tc_f32(int engine, int M, int N, int K, const Operand<float>& 
         }
     }
     if (p.sym) {
-        // symmetric result: square tiles, upper triangle only (TF32: 256 x 256 two-SM
-        // tiles; split TF32: 128 x 128 one-SM tiles without cluster pairs)
+        // symmetric result: square tiles, upper triangle only (256 x 256 two-SM tiles; split
+        // TF32 on one-SM 128 x 128 tiles when M <= 128 or the one-SM family is forced)
         if (!three)
             return gemm_tc_2sm(false, 0, M, N, K, xh, xh, ldx, yh, yh, ldy, p, skip, s);
+        if (use_2sm(true) && M > BM)
+            return gemm_tc_2sm(true, split_chunk(), M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p,
+                               skip, s);
         switch (split_chunk()) {
             case 1: return launch<128, 3, 3, 1>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);
             case 4: return launch<128, 3, 3, 4>(M, N, K, xh, X.lo, ldx, yh, Y.lo, ldy, p, skip, s);

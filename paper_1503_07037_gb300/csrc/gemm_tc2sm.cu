@@ -490,6 +490,311 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
     }
 }
 
+// ------------------------------------------------------------------ split TF32, wide tiles
+// Split-TF32 product (lo*hi + hi*lo + hi*hi per k-step) on 256 x 256 output tiles of an SM
+// pair. Order of the MMAs: each MMA truncates its FP32 result, an error of up to one unit in
+// the last place of the accumulator. Within a k-block the eight cross-term MMAs (about 2^-11
+// of the result) come first and the four hi*hi MMAs last, so on the first k-block of a chunk
+// the cross terms are truncated at the scale of a small accumulator: a one-k-block chunk
+// carries four truncations at the scale of the result instead of eleven. Against the 128 x 128 one-SM tile, every SM stages 128 rows of X and 128 rows of Y
+// per k-block for twice the flops, so the shared-memory fill per flop (the L2 -> SM traffic,
+// which bounds the narrow tile) halves. The accumulation restarts every KCH k-blocks (the
+// truncating FP32 accumulation of the tensor cores; KCH = 0: whole K) into one of two
+// 256-column TMEM accumulators, so the MMA of one chunk overlaps the drain of the other.
+// EW epilogue warps per CTA (8 or 16): warp w drains TMEM lanes 32 (w % 4) of column group
+// (w - 2) / 4, CW = 1024 / EW columns, and keeps its lane's CW running sums in registers
+// (IEEE round-to-nearest adds). The drain of a chunk must keep pace with the chunk's MMAs
+// (about 0.9 us at the TF32 rate); its arrival on the peer's barrier uses the plain
+// (.release.cta) form, since a cluster-scope release made every drain wait for the previous
+// tile's global stores (ncu: membar stalls dominated, 232 TF/s at N = 8192 against 344
+// without). A finished tile is stored straight from the registers; the MMA meanwhile fills
+// the other accumulator. Tiles run in groups of eight M-tiles (grouped raster), or over the
+// upper triangle for symmetric results.
+constexpr int SPLIT_BN = 256;
+constexpr int SPLIT_GROUP = 8;
+constexpr int split_threads(int ew) { return 32 * (2 + ew); }
+
+// Arrive on an mbarrier given by its shared::cluster address with the default .release.cta
+// semantics. The epilogue's per-chunk "accumulator drained" signal orders only tcgen05 loads
+// (completed by tcgen05.wait::ld and tcgen05.fence::before_thread_sync) against the peer's MMA;
+// a .release.cluster arrive would also wait, every chunk, for the warp's earlier global stores
+// (the previous tile's epilogue) to become visible cluster-wide.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+// 16 consecutive columns of this warp's 32 TMEM lanes, completed before return (the
+// 128 running sums and the 168-register budget of 320 threads leave room for 16 at a time)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int STAGES>
+struct CfgS {
+    static constexpr int A_BYTES = BM * BK * 4;                // this CTA's 128 rows of X
+    static constexpr int B_BYTES = (SPLIT_BN / 2) * BK * 4;    // this CTA's 128 rows of Y
+    static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGE_BYTES = 2 * PAIR_BYTES;         // hi and lo
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 1024;
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+template <int STAGES, int KCH, int EW>
+__global__ void __launch_bounds__(split_threads(EW), 1)
+    k_gemm_split2sm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                    const __grid_constant__ CUtensorMap tmXl,
+                    const __grid_constant__ CUtensorMap tmYl,
+                    const __grid_constant__ EpiParams<float> p, int K, int num_mt, int num_nt,
+                    int total_tiles, const double* skip, int* err) {
+    using C = CfgS<STAGES>;
+    static_assert(EW == 8 || EW == 16, "epilogue warps");
+    constexpr int BN = SPLIT_BN, NB = 2, CW = 4 * BN / EW;
+    constexpr int LW = CW >= 128 ? 32 : 16;   // columns per TMEM load
+    constexpr uint32_t kTmemCols = NB * BN;
+    if (skip != nullptr && *skip != 0.0) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);   // used in CTA 0
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;   // [NB]
+    uint64_t* tempty = tfull + NB;      // [NB], used in CTA 0
+    uint64_t* drain = tempty + NB;
+    uint32_t* tmem_holder = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    const int num_k = (K + BK - 1) / BK;
+    const bool sym = p.sym != 0;
+    auto tile_of = [&](int t, int* mt, int* nt) {
+        if (sym) {
+            tri_tile(t, num_mt, mt, nt);
+        } else {
+            const int grp = t / (SPLIT_GROUP * num_nt);
+            const int first = grp * SPLIT_GROUP;
+            const int gsize = min(SPLIT_GROUP, num_mt - first);
+            const int r = t - grp * SPLIT_GROUP * num_nt;
+            *mt = first + r % gsize;
+            *nt = r / gsize;
+        }
+    };
+    const int kc = KCH > 0 ? KCH : num_k;
+    const int nch = (num_k + kc - 1) / kc;
+    auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
+    auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::PAIR_BYTES; };
+    auto stage_blo = [&](int s) {
+        return smem + s * C::STAGE_BYTES + C::PAIR_BYTES + C::A_BYTES;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NB; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 2 * EW);   // the epilogue warps of both CTAs
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_holder, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const bool bad = ld_cluster_u32(mapa_u32(smem_u32(tmem_holder), rank ^ 1u)) != tmem_base;
+    if (bad && threadIdx.x == 0) atomicCAS(err, 0, DEV_TMEM_MISMATCH);
+
+    if (bad) {
+        // fall through to the final barrier and free the allocation
+    } else if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            prefetch_map(&tmX);
+            prefetch_map(&tmY);
+            prefetch_map(&tmXl);
+            prefetch_map(&tmYl);
+            const uint32_t full0 = mapa_u32(smem_u32(full), 0);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = cid; t < total_tiles && ok; t += ncl) {
+                int mt = 0, nt = 0;
+                tile_of(t, &mt, &nt);
+                const int m0 = mt * (2 * BM) + (int)rank * BM;
+                const int y0 = nt * BN + (int)rank * (BN / 2);
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait_cl(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_expect_tx(&full[s], 2 * C::STAGE_BYTES);
+                    const uint32_t fb = full0 + (uint32_t)s * 8u;
+                    tma_load_2d_pair(stage_a(s), &tmX, kb * BK, m0, fb);
+                    tma_load_2d_pair(stage_b(s), &tmY, kb * BK, y0, fb);
+                    tma_load_2d_pair(stage_alo(s), &tmXl, kb * BK, m0, fb);
+                    tma_load_2d_pair(stage_blo(s), &tmYl, kb * BK, y0, fb);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (CTA 0)
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = idesc_tf32<2 * BM, BN>();
+            uint32_t it = 0, g = 0;
+            bool ok = true, issued = false;
+            for (int t = cid; t < total_tiles && ok; t += ncl) {
+                for (int c = 0; c < nch && ok; ++c, ++g) {
+                    const int b = g % NB;
+                    if (!mbar_wait_cl(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
+                                      DEV_TIMEOUT_ACCUM)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
+                    const int kb0 = c * kc, kb1 = min(num_k, kb0 + kc);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        if (!mbar_wait_cl(&full[s], ph, abort_flag, err, DEV_TIMEOUT_FULL)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+                        const uint32_t al0 = smem_u32(stage_alo(s)), bl0 = smem_u32(stage_blo(s));
+                        // cross terms of the k-block first, then its hi*hi terms
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t first = ((kb - kb0) | kk) != 0 ? 1u : 0u;
+                            mma_tf32_pair(tmem_d, sw128_desc(al0 + off), sw128_desc(b0 + off),
+                                          idesc, first);
+                            mma_tf32_pair(tmem_d, sw128_desc(a0 + off), sw128_desc(bl0 + off),
+                                          idesc, 1u);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t off = kk * 32;
+                            mma_tf32_pair(tmem_d, sw128_desc(a0 + off), sw128_desc(b0 + off),
+                                          idesc, 1u);
+                        }
+                        issued = true;
+                        mma_commit_pair(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(&tfull[b]);
+                }
+            }
+            if (!ok && issued) {
+                mma_commit_local_pair(drain);
+                mbar_drain(drain, 0);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;            // TMEM lane quarter this warp may read
+        const int h = (warp - 2) >> 2;     // column group
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(CW * h);
+        const uint32_t tempty0 = mapa_u32(smem_u32(tempty), 0);
+        const bool vec4 = epi_vec4_ok(p);
+        double dsum = 0.0;
+        uint32_t g = 0;
+        for (int t = cid; t < total_tiles; t += ncl) {
+            int mt = 0, nt = 0;
+            tile_of(t, &mt, &nt);
+            const bool diag = sym && mt == nt;
+            const int m = mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
+            const int n0 = nt * BN + CW * h;
+            float acc[CW];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) acc[j] = 0.f;
+            bool ok = true;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int b = g % NB;
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait_cl(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                if (!__shfl_sync(0xffffffffu, w, 0)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += LW) {
+                    uint32_t rr[LW];
+                    if constexpr (LW == 32)
+                        tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
+                    else
+                        tmem_ld16(lane_base + (uint32_t)(b * BN + c0), rr);
+#pragma unroll
+                    for (int j = 0; j < LW; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(tempty0 + (uint32_t)b * 8u);
+            }
+            if (!ok) break;
+            if (m >= p.M) continue;
+#pragma unroll
+            for (int c0 = 0; c0 < CW; c0 += 32) {
+                const int nb = n0 + c0;
+                float local = 0.f;
+                if (vec4 && !diag && nb + 32 <= p.N) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        local += epi_apply4(p, m, nb + j, acc[c0 + j], acc[c0 + j + 1],
+                                            acc[c0 + j + 2], acc[c0 + j + 3]);
+                } else if (sym) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (nb + j < p.N) local += epi_apply_sym(p, m, nb + j, acc[c0 + j], diag);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (nb + j < p.N) local += epi_apply(p, m, nb + j, acc[c0 + j]);
+                }
+                dsum += (double)local;
+            }
+        }
+        if (p.dot) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+            if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        const unsigned long long t0 = globaltimer();
+        while (globaltimer() - t0 < 100000ull) {
+        }
+    }
+    __syncthreads();
+    cluster_sync();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, kTmemCols);
+    }
+}
+
 // Tensor map of a BF16 operand (rows x cols, leading dimension ld elements).
 bool make_map_bf16(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
     auto fn = encode_fn();
@@ -579,16 +884,104 @@ cdmpt_status launch_2sm(int M, int N, int K, const void* X, const void* Xl, int 
     return CDMPT_OK;
 }
 
+
+// Epilogue warps of the wide split kernel: eight by default (128 columns each, 32-column
+// TMEM loads; measured 344 against 328 TF/s for sixteen at N = 8192 with one-k-block chunks,
+// 279 against 274 at N = 4096); CDMPT_SPLIT_EPI=16 selects sixteen for tuning.
+int split_epilogue_warps() {
+    static int v = 0;
+    if (v == 0) {
+        const char* e = getenv("CDMPT_SPLIT_EPI");
+        v = (e && atoi(e) == 16) ? 16 : 8;
+    }
+    return v;
+}
+
+template <int STAGES, int KCH, int EW>
+cdmpt_status launch_split2sm(int M, int N, int K, const float* X, const float* Xl, int ldx,
+                             const float* Y, const float* Yl, int ldy, const EpiParams<float>& p,
+                             const double* skip, cudaStream_t s) {
+    using C = CfgS<STAGES>;
+    auto kern = k_gemm_split2sm<STAGES, KCH, EW>;
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM);
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3(2 * (sm_count() / 2));
+        q.blockDim = dim3(split_threads(EW));
+        q.dynamicSmemBytes = C::SMEM;
+        cudaLaunchAttribute a;
+        a.id = cudaLaunchAttributeClusterDimension;
+        a.val.clusterDim.x = 2;
+        a.val.clusterDim.y = 1;
+        a.val.clusterDim.z = 1;
+        q.attrs = &a;
+        q.numAttrs = 1;
+        int n = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
+        if (e != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            set_error("split-TF32 two-SM GEMM: no resident cluster of two");
+            return CDMPT_ERR_UNSUPPORTED;
+        }
+        max_clusters = n;
+    }
+    CUtensorMap mx, my, mxl, myl;
+    if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, SPLIT_BN / 2) ||
+        !make_map(&mxl, Xl, M, K, ldx, BM) || !make_map(&myl, Yl, N, K, ldy, SPLIT_BN / 2)) {
+        set_error("cuTensorMapEncodeTiled failed (alignment of X/Y or ld not a multiple of 4?)");
+        return CDMPT_ERR_ARG;
+    }
+    const int num_mt = (M + 2 * BM - 1) / (2 * BM);
+    const int num_nt = (N + SPLIT_BN - 1) / SPLIT_BN;
+    const bool sym = p.sym && M == N;
+    const int tiles = sym ? num_mt * (num_mt + 1) / 2 : num_mt * num_nt;
+    EpiParams<float> pk = p;
+    pk.sym = sym ? 1 : 0;
+    const int clusters = tiles < max_clusters ? tiles : max_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(split_threads(EW));
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 2;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, pk, K, num_mt, num_nt, tiles,
+                                       skip, device_error_word());
+    count_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("split-TF32 two-SM GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
 }  // namespace
 
 cdmpt_status gemm_tc_2sm(bool three, int kch, int M, int N, int K, const float* X,
                          const float* Xl, int ldx, const float* Y, const float* Yl, int ldy,
                          const EpiParams<float>& p, const double* skip, cudaStream_t s) {
     if (!three) return launch_2sm<256, 6, 1, 0>(M, N, K, X, X, ldx, Y, Y, ldy, p, skip, s);
+    if (split_epilogue_warps() == 16) {
+        switch (kch) {
+            case 0: return launch_split2sm<3, 0, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+            case 2: return launch_split2sm<3, 2, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+            case 4: return launch_split2sm<3, 4, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+            default: return launch_split2sm<3, 1, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        }
+    }
     switch (kch) {
-        case 0: return launch_2sm<128, 4, 3, 0>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-        case 4: return launch_2sm<128, 4, 3, 4>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-        default: return launch_2sm<128, 4, 3, 2>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        case 0: return launch_split2sm<3, 0, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        case 2: return launch_split2sm<3, 2, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        case 4: return launch_split2sm<3, 4, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+        default: return launch_split2sm<3, 1, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
     }
 }
 

@@ -215,6 +215,8 @@ struct OzEpi {
     const int* ey = nullptr;
 };
 constexpr int kOzDigits = 5;   // digits of the refinement products (39 bits of the row maximum)
+// digit products per k-step: the pairs (p, q) with p + q <= nd + 1, i.e. nd (nd + 1) / 2
+constexpr int oz_products(int nd) { return nd * (nd + 1) / 2; }
 cdmpt_status oz_slice(const float* xh, const float* xl, int rows, int cols, int ld,
                       const OzOperand& out, cudaStream_t s, int nd = kOzDigits);
 // D = op(X Y^T) for X (M x K) and Y (N x K) given as nd digits each; K <= 32768.

@@ -25,6 +25,19 @@ struct Context {
     std::vector<double> ev_flops;   // algorithmic flops of pair i
     size_t ev_used = 0;
     double* pinned = nullptr;       // host scalar readback (64 doubles)
+    // phase boundaries of a solve (profile mode): start, after the occupation sweeps,
+    // after the refinement, after the response, after dP0/dmu, end
+    cudaEvent_t ph[6] = {};
+    bool ph_set[6] = {};
+    void mark(int i) {
+        if (!profile || i < 0 || i > 5) return;
+        if (!ph[i] && cudaEventCreate(&ph[i]) != cudaSuccess) {
+            cudaGetLastError();
+            ph[i] = nullptr;
+            return;
+        }
+        ph_set[i] = cudaEventRecord(ph[i], stream) == cudaSuccess;
+    }
 };
 
 // A rows x ld matrix (or stack of N-row blocks) and, for float storage, its

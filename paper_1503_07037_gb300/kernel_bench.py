@@ -7,7 +7,10 @@ FP32 (or FP64) matrix with CUDA events on the launching stream, after three
 warm-up launches, and prints one JSON line with the duration and the
 algorithmic rate 2 N^3 / t. The input is a seeded symmetric matrix scaled like
 a recursion iterate (spectrum in [-1, 1]); the tensor-core engines get its
-TF32 split once, before timing, as the solver keeps splits resident.
+TF32 split once, before timing, as the solver keeps splits resident. Engine
+"oz" is the Ozaki-sliced product of a pair-stored matrix (hi + lo FP32),
+D + Dl = Z Z^T; its timing includes slicing both operands into BF16 digits,
+as every call of the solver's FP64-class residual does.
 """
 from __future__ import annotations
 
@@ -28,23 +31,32 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64"])
+    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64", "oz"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--check", action="store_true",
+                    help="also report the error against an FP64 product (cuBLAS DGEMM), on the "
+                         "signed input and on its absolute value (all-positive sums show the "
+                         "bias of a truncating accumulation)")
     a = ap.parse_args()
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(1234)
     dt = torch.float64 if a.engine == "f64" else torch.float32
     Z = torch.randn(a.n, a.n, device=dev, generator=g, dtype=torch.float64)
-    Z = (Z + Z.T) / (2.0 * (2 * a.n) ** 0.5)
-    Z = Z.to(dt).contiguous()
+    Z64 = (Z + Z.T) / (2.0 * (2 * a.n) ** 0.5)
+    Z = Z64.to(dt).contiguous()
     D = torch.empty_like(Z)
+    if a.engine == "oz":
+        Zl = (Z64 - Z.double()).float().contiguous()     # the pair's low part
+        Dl = torch.empty_like(Z)
     if a.engine in ("tf32", "3xtf32"):
         Zs = pkg.split_tf32(Z)      # split once, outside the timed launches
 
     def run():
         if a.engine == "f64":
             pkg.gemm_f64(Z, Z, D, gamma=1.0)
+        elif a.engine == "oz":
+            pkg.gemm_pair(Z, Zl, Z, Zl, D, Dl)
         elif a.engine in ("simt", "bf16"):
             # bf16: includes rounding the operand to BF16 (one pass, X is Y)
             pkg.gemm_f32(Z, Z, D, gamma=1.0, engine=a.engine)
@@ -63,8 +75,28 @@ def main():
     e1.record(s)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / a.reps / 1e3
-    print(json.dumps({"kernel": "gemm", "engine": a.engine, "n": a.n, "ms": t * 1e3,
-                      "alg_tflops": 2.0 * a.n ** 3 / t / 1e12}))
+    out = {"kernel": "gemm", "engine": a.engine, "n": a.n, "ms": t * 1e3,
+           "alg_tflops": 2.0 * a.n ** 3 / t / 1e12}
+    if a.engine == "oz":
+        out["digit_products"] = 15    # BF16 digit pairs (p, q) with p + q <= 4 of 5 digits
+        out["bf16_tflops"] = out["alg_tflops"] * 15
+    if a.check and a.engine != "oz":
+        for label, src in (("signed", Z64), ("positive", Z64.abs())):
+            Zc = src.to(dt).contiguous()
+            if a.engine in ("tf32", "3xtf32"):
+                Zs = pkg.split_tf32(Zc)
+            ref = Zc.double() @ Zc.double().T + torch.eye(a.n, dtype=torch.float64, device=dev)
+            if a.engine == "f64":
+                pkg.gemm_f64(Zc, Zc, D, gamma=1.0)
+            elif a.engine in ("simt", "bf16"):
+                pkg.gemm_f32(Zc, Zc, D, gamma=1.0, engine=a.engine)
+            else:
+                pkg.gemm_f32_split(Zs, Zs, D, gamma=1.0, engine=a.engine)
+            torch.cuda.synchronize()
+            err = D.double() - ref
+            out[f"rel_err_{label}"] = float(err.norm() / ref.norm())
+            out[f"rel_bias_{label}"] = float(err.sum() / ref.abs().sum())
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

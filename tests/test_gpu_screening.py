@@ -5,8 +5,10 @@ whose Frobenius norms satisfy ||X_IK|| ||Y_JK|| <= screen_tau (a per-tile slice 
 before each launch; the tcgen05 kernel skips the masked slices in all its roles).
 
 References and bars:
-- Four decoupled 128-site chains (block-diagonal H0 and H1): every dropped term is an exact
-  zero, so the screened P0 and P1 equal the dense ones bit for bit.
+- Decoupled chains (block-diagonal H0 and H1): every dropped term is an exact zero, so the
+  screened P0 and P1 keep the exact zero pattern of the blocks and agree with the dense ones
+  within the precision's bar (the two run different tile shapes, so the CG scalars differ in
+  their last bits).
 - The 1D chain (N = 1024, beta 10, n 12) against the oracle: at tau = 1e-8 the screened
   error stays within 1.5 x the dense error + 20 tau (the dense mixed-precision error is near
   4e-9, so the screening's own error, about 12 tau, is what shows); at tau = 1e-6 and
@@ -40,19 +42,28 @@ def _solve(pkg, p, precision, tau):
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("sizes", [(128, 128, 128, 128), (100, 156, 200, 54)])
 def test_screening_is_exact_on_decoupled_chains(cuda, cdmpt_lib, precision, sizes):
-    """Block-diagonal chains: every screened term is an exact zero, so the screened solve equals
-    the dense one bit for bit. The second block layout is not aligned to the 128 x 128 tiles and
-    N = 510 is not a multiple of 4: the tiles screened to nothing then include partial edge
-    tiles, whose epilogue takes the scalar tail, next to full ones (and the transposed placement
-    of the response's right-hand side)."""
+    """Block-diagonal chains: every screened term is an exact zero. The second block layout is
+    not aligned to the 128 x 128 tiles and N = 510 is not a multiple of 4: the tiles screened to
+    nothing then include partial edge tiles, whose epilogue takes the scalar tail, next to full
+    ones (and the transposed placement of the response's right-hand side).
+
+    The screened products run on the one-SM 128 x 128 kernels (the mask's granularity), the
+    dense ones with more than 128 rows on the two-SM 256 x 256 kernels. Both form every product
+    element by the same accumulation, but the fused CG dot products add the same float
+    partial sums in other double groupings, so the CG scalars differ in their last bits and
+    the iterates in rounding. The check is therefore the exact zero pattern of the blocks in
+    both solves and agreement within the precision's bar (1e-5 FP32, 1e-6 mixed)."""
     blocks = [syn.chain_1d(nb, 11 + i, 10.0, 12) for i, nb in enumerate(sizes)]
     H0 = sl.block_diag(*[b.H0 for b in blocks])
     H1 = sl.block_diag(*[b.H1[0] for b in blocks])[None]
     p = syn.Problem("four_chains", H0, H1, sum(b.nocc for b in blocks), 10.0, 12)
     dense = _solve(cdmpt_lib, p, precision, 0.0)
     scr = _solve(cdmpt_lib, p, precision, 1e-30)
-    assert np.array_equal(dense["P0"], scr["P0"])
-    assert np.array_equal(dense["P1"], scr["P1"])
+    off = sl.block_diag(*[np.ones((nb, nb)) for nb in sizes]) == 0
+    bar = 1e-5 if precision == "fp32" else 1e-6
+    for k in ("P0", "P1"):
+        assert not dense[k][off].any() and not scr[k][off].any(), k
+        assert oracle.rel_frobenius(scr[k], dense[k]) < bar, k
     assert dense["examined"] == 0.0
     assert 0.0 < scr["computed"] < (0.1 if sizes[0] == 128 else 0.5) * scr["examined"]
 
