@@ -535,7 +535,8 @@ def run_ours(args):
 
 def run_c2(pkg, args, barrier, max_over_ranks, world, rank):
     """The 16^3 lattice (N = 4096, n 14) at beta 5, 20 and 80: one step (three solves) in mixed
-    precision and in FP32, with every output against the oracle."""
+    precision, in FP32 and in FP64 (tensor-core FP64 products), with every output against the
+    oracle."""
     import numpy as np
     import torch
 
@@ -543,7 +544,7 @@ def run_c2(pkg, args, barrier, max_over_ranks, world, rank):
     probs = [synthetic.cubic_lattice((16, 16, 16), seed=1002, beta=b, n=14) for b in C2_BETAS]
     out = {"workload": "16x16x16 lattice, N=4096, n=14, D=1, beta 5, 20, 80; one step = 3 solves"}
     res = {}
-    for prec in ("mixed", "fp32"):
+    for prec in ("mixed", "fp32", "fp64"):
         with pkg.Handle(precision=prec) as h:
             h.set_H(probs[0].H0, probs[0].H1)
             for p in probs:
@@ -570,32 +571,44 @@ def run_c2(pkg, args, barrier, max_over_ranks, world, rank):
 
 
 def run_fp64(pkg, mpk, rank):
-    """One FP64 solve of the 16 x 16 x 8 lattice (N = 2048) at beta 20 (CUDA-core DFMA products),
-    with its rate against the measured FP64 library rate and its error against the oracle. (The
-    16^3 lattice takes 75 s per FP64 solve on this GPU; its parity is a GPU test.)"""
+    """FP64 solves of the 16 x 16 x 8 lattice (N = 2048) at beta 20 with each FP64 product
+    engine: the tensor-core Ozaki engine (seven BF16 digits, the default) and CUDA-core DFMA,
+    with their product rates against the measured cuBLAS FP64 rate and their errors against
+    the oracle."""
     import numpy as np
     import torch
 
     import oracle
     import synthetic
     p = synthetic.cubic_lattice((16, 16, 8), seed=1002, beta=20.0, n=14)
-    with pkg.Handle(precision="fp64", profile=True) as h:
-        h.set_H(p.H0, p.H1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = h.solve(p.beta, p.nocc, p.n)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        st = h.stats()
-        alpha = h.polarizability()
-    ach = st["engine_flops"][1] / (st["engine_ms"][1] / 1e3) / 1e12 if st["engine_ms"][1] else None
-    out = {"workload": "16x16x8 lattice, N=2048, beta 20, n 14, FP64", "solve_s": dt,
-           "gemm_tflops": ach, "fp64_peak_tflops": mpk["fp64_tflops"],
-           "frac_of_fp64_peak": ach / mpk["fp64_tflops"] if ach else None}
-    if rank == 0:
-        ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
-        out["error"] = _errors({"P0": r["P0"].cpu().numpy(), "P1": r["P1"].cpu().numpy(),
-                                "mu1": np.asarray(r["mu1"]), "alpha": alpha}, ref, p.D)
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec") if rank == 0 else None
+    out = {"workload": "16x16x8 lattice, N=2048, beta 20, n 14, FP64",
+           "fp64_peak_tflops": mpk["fp64_tflops"]}
+    for engine, eng_id, label in (("auto", 5, "tensor_core_ozaki"), ("simt", 1, "cuda_core_dfma")):
+        with pkg.Handle(precision="fp64", engine=engine, profile=True) as h:
+            h.set_H(p.H0, p.H1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = h.solve(p.beta, p.nocc, p.n)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = h.stats()
+            alpha = h.polarizability()
+        ms = st["engine_ms"][eng_id]
+        ach = st["engine_flops"][eng_id] / (ms / 1e3) / 1e12 if ms else None
+        o = {"solve_s": dt, "gemm_ms": ms, "gemm_launches": st["engine_launches"][eng_id],
+             "gemm_tflops_fp64": ach,
+             "frac_of_fp64_peak": ach / mpk["fp64_tflops"] if ach else None}
+        if eng_id == 5 and ach:
+            o["bf16_digit_tflops"] = 28 * ach
+            o["frac_of_bf16_sustained"] = 28 * ach / peaks()["bf16_sustained"]
+        if ref is not None:
+            o["error"] = _errors({"P0": r["P0"].cpu().numpy(), "P1": r["P1"].cpu().numpy(),
+                                  "mu1": np.asarray(r["mu1"]), "alpha": alpha}, ref, p.D)
+        out[label] = o
+    if out["cuda_core_dfma"]["solve_s"]:
+        out["speedup_tensor_core_vs_dfma"] = (out["cuda_core_dfma"]["solve_s"] /
+                                              out["tensor_core_ozaki"]["solve_s"])
     return out
 
 

@@ -77,14 +77,17 @@ typedef enum {
     CDMPT_GEMM_TC_TF32 = 2,   /* tcgen05 kind::tf32, one pass, FP32 accumulate in TMEM */
     CDMPT_GEMM_TC_3XTF32 = 3, /* tcgen05 kind::tf32, hi/lo split, three passes */
     CDMPT_GEMM_TC_BF16 = 4,   /* tcgen05 kind::f16 on operands rounded to BF16, one pass */
-    CDMPT_GEMM_TC_OZAKI = 5   /* statistics only (not a gemm_engine choice): Ozaki-sliced BF16
-                                 products of pair-stored operands, the FP64-class refinement
-                                 residuals of the mixed precisions (cdmpt_gemm_pair) */
+    CDMPT_GEMM_TC_OZAKI = 5   /* Ozaki-sliced BF16 digit products on tcgen05: the FP64-class
+                                 refinement residuals of the mixed precisions (pair-stored
+                                 operands, cdmpt_gemm_pair; statistics only there), and every
+                                 product of the FP64 precision (seven digits, cdmpt_gemm_f64_tc;
+                                 the default for FP64 on sm_103) */
 } cdmpt_gemm_engine;
 
 typedef struct {
     int precision;      /* cdmpt_precision */
-    int gemm_engine;    /* cdmpt_gemm_engine for FP32 storage; ignored for FP64 */
+    int gemm_engine;    /* cdmpt_gemm_engine. FP64 storage: AUTO or TC_OZAKI (FP64 Ozaki
+                           products on the tensor cores) or SIMT (CUDA-core DFMA) */
     double cg_tol;      /* CG stop: ||R||_F <= cg_tol * ||RHS||_F; <= 0 selects the default */
     int cg_maxit;       /* CG iteration cap per solve */
     int refine_rounds;  /* residual-refinement rounds (MIXED_* only) */
@@ -325,13 +328,13 @@ cdmpt_status cdmpt_vjp_P0(cdmpt_handle* h, const double* G0, double* gradH0, int
  * directions H1_d (D x N x N FP64, host or device per on_device), answered on the
  * stored trajectory without a new solve (every order and direction shares the step
  * matrices T_k, Sec. II). P1_d (D x N x N, may be NULL) with mu1_d from Tr P1_d = 0,
- * and Omega^(2)_d = 1/2 Tr[H1_d P1_d] (Eq. Resp_0; alpha_d = -4 Omega^(2)_d), host
- * arrays of D doubles (may be NULL). In the non-orthogonal mode H1 is h1 and P1 is
- * D1.
+ * Omega^(2)_d = 1/2 Tr[H1_d P1_d] (Eq. Resp_0) and the polarizability
+ * alpha_d = -2 Tr[H1_d P1_d] = -4 Omega^(2)_d, host arrays of D doubles (each may
+ * be NULL). In the non-orthogonal mode H1 is h1 and P1 is D1.
  * Errors: ERR_ARG (no solve yet, D outside 1..16, H1 NULL), ERR_CG_MAXITER,
  * ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA. */
 cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,
-                             double* omega2, int on_device);
+                             double* omega2, double* alpha, int on_device);
 
 /* Second-order canonical response of the last solve, per direction d of H1:
  * P2_d = (1/2) d^2 P / d lambda_d^2 of P(H0 + lambda_d H1_d) (Algorithm 1, the
@@ -565,6 +568,23 @@ cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, c
                             const double* C, int ldc, double gamma, int diag_block,
                             int trans_block, double* dot, const double* E, int lde,
                             void* stream);
+
+/* The same product, arguments and semantics as cdmpt_gemm_f64 (trans_block = -1 is accepted
+ * and computes every element), on the tensor cores by the error-free slicing of Ozaki et al.
+ * (integer-accumulation form of Mukunoki, Ozaki, Ogita, Imamura, ISC 2020): each row of X and
+ * Y is scaled by a power of two and cut into seven signed 8-bit digits (55 bits of the row's
+ * largest element), the 28 digit products with weight at least 2^-48 run as BF16 tcgen05 MMAs
+ * with FP32 accumulation, exact (integer) for the four leading weight groups, and the sums are
+ * combined in FP64. Error: within about 2^-47 of |X_i| |Y_j| row maxima times K, against FP64
+ * rounding of the exact product (tests: relative error below 1e-13 on random inputs). The
+ * CUDA-core FP64 rate of this part is about 1.2 TFLOP/s; this path runs the FP64 precision's
+ * products. Needs sm_103, K <= 16384; digits go to stream-ordered scratch of
+ * 14 (M + Ncols) roundup(K, 8) bytes. Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA. */
+cdmpt_status cdmpt_gemm_f64_tc(int M, int Ncols, int K, const double* X, int ldx,
+                               const double* Y, int ldy, double* D, int ldd, double alpha,
+                               double beta, const double* C, int ldc, double gamma,
+                               int diag_block, int trans_block, double* dot, const double* E,
+                               int lde, void* stream);
 
 #ifdef __cplusplus
 }

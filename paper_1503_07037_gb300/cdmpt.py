@@ -114,7 +114,7 @@ EXPORTS = ["cdmpt_version", "cdmpt_default_opts", "cdmpt_create", "cdmpt_set_opt
            "cdmpt_response3", "cdmpt_free_energy", "cdmpt_set_overlap",
            "cdmpt_get_overlap_info", "cdmpt_scc_solve", "cdmpt_response1",
            "cdmpt_set_H_orders", "cdmpt_scc_solve2", "cdmpt_gemm_pair",
-           "cdmpt_check_bounded_wait"]
+           "cdmpt_check_bounded_wait", "cdmpt_gemm_f64_tc"]
 
 
 def lib() -> ctypes.CDLL:
@@ -140,12 +140,13 @@ def lib() -> ctypes.CDLL:
         "cdmpt_destroy": (V, [P]),
         "cdmpt_gemm_f32": (I, [I, I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_gemm_f64": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
+        "cdmpt_gemm_f64_tc": (I, [I, I, I, P, I, P, I, P, I, D, D, P, I, D, I, I, P, P, I, P]),
         "cdmpt_spectral_bounds": (I, [P, I, I, P, P]),
         "cdmpt_spectral_bounds_noalloc": (I, [P, I, I, P, P]),
         "cdmpt_vjp_P0": (I, [P, P, P, I]),
         "cdmpt_response2": (I, [P, P, P, P, P, P, I]),
         "cdmpt_response3": (I, [P, P, P, P, I]),
-        "cdmpt_response1": (I, [P, I, P, P, P, P, I]),
+        "cdmpt_response1": (I, [P, I, P, P, P, P, P, I]),
         "cdmpt_set_H_orders": (I, [P, P, P, I]),
         "cdmpt_free_energy": (I, [P, P, P, I]),
         "cdmpt_set_overlap": (I, [P, I, P, I]),
@@ -310,12 +311,14 @@ def check_bounded_wait(limit_ms=2.0, stream=None) -> int:
 
 
 def gemm_f64(X, Y, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, diag_block=0, trans_block=0,
-             dot=None, E=None, M=None, Ncols=None, K=None, stream=None):
-    """FP64 counterpart of gemm_f32 (CUDA cores)."""
+             dot=None, E=None, M=None, Ncols=None, K=None, stream=None, engine="simt"):
+    """FP64 counterpart of gemm_f32: engine "simt" (cdmpt_gemm_f64, CUDA cores) or "tc"
+    (cdmpt_gemm_f64_tc, the seven-digit Ozaki product on the tensor cores)."""
     M = X.shape[0] if M is None else M
     K = X.shape[1] if K is None else K
     Ncols = Y.shape[0] if Ncols is None else Ncols
-    _check(lib().cdmpt_gemm_f64(M, Ncols, K, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+    fn = lib().cdmpt_gemm_f64_tc if engine == "tc" else lib().cdmpt_gemm_f64
+    _check(fn(M, Ncols, K, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
                                 _ptr(D), D.stride(0), float(alpha), float(beta), _ptr(C),
                                 C.stride(0) if C is not None else 0, float(gamma), diag_block,
                                 trans_block, _ptr(dot), _ptr(E),
@@ -494,9 +497,10 @@ class Handle:
         P1 = torch.empty((D, N, N), dtype=torch.float64, device=dev) if want_P1 else None
         mu1 = np.zeros(D)
         om2 = np.zeros(D)
+        alpha = np.zeros(D)
         _check(lib().cdmpt_response1(self.h, D, ptr_in, _ptr(P1), mu1.ctypes.data,
-                                     om2.ctypes.data, on_in), self.h)
-        return {"P1": P1, "mu1": mu1, "omega2": om2, "alpha": -4.0 * om2}
+                                     om2.ctypes.data, alpha.ctypes.data, on_in), self.h)
+        return {"P1": P1, "mu1": mu1, "omega2": om2, "alpha": alpha}
 
     def response2(self, weights=None, want_P2=True, want_grad=True, device="cuda"):
         """Second-order canonical response of the last solve: dict(P2 (D, N, N), mu2 (D,),

@@ -120,7 +120,9 @@ cdmpt_status ov_map(cdmpt_handle* h, const double* src, double* dst, int blocks,
 
 bool valid_opts(const cdmpt_opts* o) {
     if (o->precision < CDMPT_FP64 || o->precision > CDMPT_MIXED_BF16) return false;
-    if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_BF16) return false;
+    if (o->gemm_engine < CDMPT_GEMM_AUTO || o->gemm_engine > CDMPT_GEMM_TC_OZAKI) return false;
+    // the Ozaki engine is a choice of the FP64 precision only
+    if (o->gemm_engine == CDMPT_GEMM_TC_OZAKI && o->precision != CDMPT_FP64) return false;
     if (o->cg_maxit < 1 || o->mu_maxit < 1 || o->refine_rounds < 0) return false;
     if (o->grand_canonical && !o->have_mu_guess) return false;
     if (o->ckpt_stride < -1) return false;
@@ -841,7 +843,7 @@ cdmpt_status cdmpt_scc_solve(cdmpt_handle* h, const cdmpt_scc_model* m, int N, c
 }
 
 cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P1, double* mu1,
-                             double* omega2, int on_device) {
+                             double* omega2, double* alpha, int on_device) {
     if (!h) return CDMPT_ERR_ARG;
     if (!h->solved)
         return fail_msg(h, CDMPT_ERR_ARG, "response1: no completed solve on this handle");
@@ -896,6 +898,7 @@ cdmpt_status cdmpt_response1(cdmpt_handle* h, int D, const double* H1, double* P
     for (int d = 0; d < D; ++d) {
         if (mu1) mu1[d] = m1[d];
         if (omega2) omega2[d] = om[d];
+        if (alpha) alpha[d] = -4.0 * om[d];   // alpha_d = -2 Tr[H1_d P1_d] = -4 Omega^(2)_d
     }
     return CDMPT_OK;
 }
@@ -1157,6 +1160,58 @@ cdmpt_status cdmpt_gemm_f64(int M, int Ncols, int K, const double* X, int ldx, c
     ep.lde = lde;
     return gemm_simt<double>(M, Ncols, K, X, ldx, Y, ldy, D, ldd, ep, nullptr,
                              (cudaStream_t)stream);
+}
+
+cdmpt_status cdmpt_gemm_f64_tc(int M, int Ncols, int K, const double* X, int ldx,
+                               const double* Y, int ldy, double* D, int ldd, double alpha,
+                               double beta, const double* C, int ldc, double gamma,
+                               int diag_block, int trans_block, double* dot, const double* E,
+                               int lde, void* stream) {
+    if (M < 0 || Ncols < 0 || K < 1 || K > 16384 || !X || !Y || !D || ldx < K || ldy < K ||
+        ldd < (trans_block > 0 ? trans_block : Ncols) || (beta != 0.0 && !C)) {
+        set_error("gemm_f64_tc: bad arguments (1 <= K <= 16384, ld >= K)");
+        return CDMPT_ERR_ARG;
+    }
+    if (trans_block > 0 && (Ncols != trans_block || M % trans_block)) {
+        set_error("gemm_f64_tc: trans_block needs Ncols == trans_block and M a multiple of it");
+        return CDMPT_ERR_ARG;
+    }
+    if (M == 0 || Ncols == 0) return CDMPT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ldq = (K + 7) / 8 * 8;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t dx = up((size_t)M * ldq * 2), dy = up((size_t)Ncols * ldq * 2);
+    const size_t ex = up((size_t)M * 4), ey = up((size_t)Ncols * 4);
+    char* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, 7 * dx + 7 * dy + ex + ey, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("gemm_f64_tc: scratch allocation failed");
+        return CDMPT_ERR_OOM;
+    }
+    Oz64Operand ox, oy;
+    for (int d = 0; d < 7; ++d) {
+        ox.s[d] = buf + d * dx;
+        oy.s[d] = buf + 7 * dx + d * dy;
+    }
+    ox.e = (int*)(buf + 7 * dx + 7 * dy);
+    oy.e = (int*)(buf + 7 * dx + 7 * dy + ex);
+    ox.ld = oy.ld = ldq;
+    Epilogue<double> ep;
+    ep.alpha = alpha;
+    ep.beta = beta;
+    ep.C = C;
+    ep.ldc = ldc;
+    ep.gamma = gamma;
+    ep.diag_block = diag_block;
+    ep.trans_block = trans_block > 0 ? trans_block : 0;
+    ep.dot = dot;
+    ep.E = E;
+    ep.lde = lde;
+    cdmpt_status st = oz64_slice(X, M, K, ldx, ox, nullptr, s);
+    if (st == CDMPT_OK) st = oz64_slice(Y, Ncols, K, ldy, oy, nullptr, s);
+    if (st == CDMPT_OK) st = gemm_oz64(M, Ncols, K, ox, oy, D, ldd, ep, nullptr, s);
+    cudaFreeAsync(buf, s);
+    return st;
 }
 
 }  // extern "C"

@@ -1181,7 +1181,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                     const double a0 = std::atanh(
                         std::min(sy.s2 * std::max(sy.gmax - sy.mu, sy.mu - sy.gmin), 0.999999));
                     int k = 0;
-                    while (k < n && std::tanh(std::ldexp(a0, k)) <= 0.5) ++k;
+                    while (k < n && std::tanh(std::ldexp(a0, k)) <= hp_bound()) ++k;
                     k_hp = std::min(k_hp, k);
                 }
             }
@@ -1245,9 +1245,11 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 std::vector<const double*> none_skip(G, nullptr);
                 CDMPT_TRY(init_z0_batch(b, none_skip, &reinit));
             }
-            if (all && !hp_phase && k_hp < n) {
-                // every system settled on split-TF32 residuals: reopen all of them for the
-                // passes with FP64-class residuals on the late steps
+            if (!hp_phase && k_hp < n && (all || refine_early_hp())) {
+                // every system settled on split-TF32 residuals (or, by default, the first
+                // split pass is done: it took the sweeps' residuals from about 1e-4 to 1e-7):
+                // reopen all of them for the passes with FP64-class residuals on the late
+                // steps; the Newton steps just taken precede the first of them
                 hp_phase = true;
                 all = false;
                 for (int i = 0; i < G; ++i) b->sys[i].converged = false;

@@ -120,9 +120,11 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t caddr) {
     return v;
 }
 
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
-                 : "memory");
+// Arrival on the peer's barrier with the plain (.release.cta) form: the drained-accumulator
+// signals order tcgen05 loads (completed by tcgen05.wait::ld and fenced before the thread
+// sync); a cluster-scope release would also wait for the warp's earlier global stores.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 __device__ __forceinline__ bool try_wait_cl(uint64_t* bar, uint32_t parity) {
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(tempty0);
+                if (lane == 0) mbar_arrive_remote(tempty0);
             }
             if (!ok) break;
             int w = 1;
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(tfin_empty0);
+            if (lane == 0) mbar_arrive_remote(tfin_empty0);
         }
         if (p.dot) {
 #pragma unroll

@@ -217,6 +217,31 @@ struct OzEpi {
 constexpr int kOzDigits = 5;   // digits of the refinement products (39 bits of the row maximum)
 // digit products per k-step: the pairs (p, q) with p + q <= nd + 1, i.e. nd (nd + 1) / 2
 constexpr int oz_products(int nd) { return nd * (nd + 1) / 2; }
+// Settings of the mixed-precision refinement shared by the single and the batched solve
+// (environment overrides read once; see solver.cu): the split-residual level at which the
+// FP64-class passes start, whether they start before the occupation has settled, and the
+// spectral bound above which a step's residual is FP64-class.
+double refine_settle();
+bool refine_early_hp();
+double hp_bound();
+
+// Digits of an FP64 operand for the FP64 Ozaki engine: seven BF16 digit arrays (rows x ld)
+// and the rows' powers of two.
+struct Oz64Operand {
+    void* s[7] = {};
+    int* e = nullptr;
+    int ld = 0;
+};
+// One warp per row: digits of x (rows x cols, leading dimension ld) into out (out.ld >= cols,
+// zeros in the padding). Does nothing while *skip != 0 (skip may be null).
+cdmpt_status oz64_slice(const double* x, int rows, int cols, int ld, const Oz64Operand& out,
+                        const double* skip, cudaStream_t s);
+// D = alpha X Y^T + beta C + gamma I_blocks in FP64 from the digits of X (M x K) and Y (N x K),
+// K <= 16384; full tiles (ep.sym is ignored), transposed placement and fused dot as the other
+// engines. Does nothing while *skip != 0.
+cdmpt_status gemm_oz64(int M, int N, int K, const Oz64Operand& X, const Oz64Operand& Y,
+                       double* D, int ldd, const Epilogue<double>& ep, const double* skip,
+                       cudaStream_t s);
 cdmpt_status oz_slice(const float* xh, const float* xl, int rows, int cols, int ld,
                       const OzOperand& out, cudaStream_t s, int nd = kOzDigits);
 // D = op(X Y^T) for X (M x K) and Y (N x K) given as nd digits each; K <= 32768.

@@ -221,6 +221,11 @@ private:
     bool pairs_ = false;             // Z_k.xl allocated (mixed precision)
     OzOperand oz_[3];                // digit operands of the Ozaki-sliced products (pairs_)
     T* wl_ = nullptr;                // low part of the Ozaki-formed W_k (pairs_)
+    // FP64 storage on the tensor cores: digits of a product's left (up to D N rows) and
+    // right (N rows) operand, allocated at the first product of that engine
+    Oz64Operand ox64_, oy64_;
+    bool oz64_ready_ = false;
+    cdmpt_status oz64_prepare();
     int replay_iters_ = 0;           // CG iterations spent recomputing segments
     Buf<T> R_, P_, Q_;               // CG work (D' * N rows)
     Buf<T> S_, A1_, RHS_;            // response work

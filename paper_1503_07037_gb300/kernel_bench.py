@@ -10,7 +10,10 @@ a recursion iterate (spectrum in [-1, 1]); the tensor-core engines get its
 TF32 split once, before timing, as the solver keeps splits resident. Engine
 "oz" is the Ozaki-sliced product of a pair-stored matrix (hi + lo FP32),
 D + Dl = Z Z^T; its timing includes slicing both operands into BF16 digits,
-as every call of the solver's FP64-class residual does.
+as every call of the solver's FP64-class residual does. "f64tc" is the FP64
+product on the tensor cores (seven BF16 digits per element), slicing
+included; "f64" the CUDA-core DFMA product. --check adds the error against a
+cuBLAS FP64 product, on the signed input and on its absolute value.
 """
 from __future__ import annotations
 
@@ -31,7 +34,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64", "oz"])
+    ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64", "f64tc", "oz"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--check", action="store_true",
@@ -41,7 +44,7 @@ def main():
     a = ap.parse_args()
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(1234)
-    dt = torch.float64 if a.engine == "f64" else torch.float32
+    dt = torch.float64 if a.engine in ("f64", "f64tc") else torch.float32
     Z = torch.randn(a.n, a.n, device=dev, generator=g, dtype=torch.float64)
     Z64 = (Z + Z.T) / (2.0 * (2 * a.n) ** 0.5)
     Z = Z64.to(dt).contiguous()
@@ -53,8 +56,8 @@ def main():
         Zs = pkg.split_tf32(Z)      # split once, outside the timed launches
 
     def run():
-        if a.engine == "f64":
-            pkg.gemm_f64(Z, Z, D, gamma=1.0)
+        if a.engine in ("f64", "f64tc"):
+            pkg.gemm_f64(Z, Z, D, gamma=1.0, engine="tc" if a.engine == "f64tc" else "simt")
         elif a.engine == "oz":
             pkg.gemm_pair(Z, Zl, Z, Zl, D, Dl)
         elif a.engine in ("simt", "bf16"):
@@ -77,17 +80,18 @@ def main():
     t = e0.elapsed_time(e1) / a.reps / 1e3
     out = {"kernel": "gemm", "engine": a.engine, "n": a.n, "ms": t * 1e3,
            "alg_tflops": 2.0 * a.n ** 3 / t / 1e12}
-    if a.engine == "oz":
-        out["digit_products"] = 15    # BF16 digit pairs (p, q) with p + q <= 4 of 5 digits
-        out["bf16_tflops"] = out["alg_tflops"] * 15
+    if a.engine in ("oz", "f64tc"):
+        # BF16 digit pairs: p + q <= 4 of 5 digits (pairs), p + q <= 6 of 7 digits (FP64)
+        out["digit_products"] = 15 if a.engine == "oz" else 28
+        out["bf16_tflops"] = out["alg_tflops"] * out["digit_products"]
     if a.check and a.engine != "oz":
         for label, src in (("signed", Z64), ("positive", Z64.abs())):
             Zc = src.to(dt).contiguous()
             if a.engine in ("tf32", "3xtf32"):
                 Zs = pkg.split_tf32(Zc)
             ref = Zc.double() @ Zc.double().T + torch.eye(a.n, dtype=torch.float64, device=dev)
-            if a.engine == "f64":
-                pkg.gemm_f64(Zc, Zc, D, gamma=1.0)
+            if a.engine in ("f64", "f64tc"):
+                pkg.gemm_f64(Zc, Zc, D, gamma=1.0, engine="tc" if a.engine == "f64tc" else "simt")
             elif a.engine in ("simt", "bf16"):
                 pkg.gemm_f32(Zc, Zc, D, gamma=1.0, engine=a.engine)
             else:

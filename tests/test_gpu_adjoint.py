@@ -66,6 +66,52 @@ def test_adjoint_fp64_central_differences_20_directions(cuda, cdmpt_lib):
     assert max(errs) < 1e-6, max(errs)
 
 
+def test_fp64_differentiation_workload_central_differences(cuda, cdmpt_lib):
+    """The differentiation workload in FP64 (16 x 16 x 8 lattice, N = 2048, beta = 20, n = 16,
+    sqrt(n) checkpoints): the gradients of the polarizability alpha = -2 Tr(P1 H1) and of the
+    free energy Omega, through torch.autograd, against central differences (h = 1e-4) along
+    20 random symmetric directions, and the free-energy gradient against the oracle's P0
+    (dOmega/dH0 = P0, App. B)."""
+    import torch
+    p = syn.workload("cubic16x16x8")
+    dev = torch.device("cuda")
+    H0 = torch.from_numpy(p.H0).to(dev)
+    H1 = torch.from_numpy(p.H1).to(dev)
+    rng = np.random.default_rng(17)
+    h = 1e-4
+    with cdmpt_lib.Handle(precision="fp64", ckpt_stride=-1) as hd:
+        X = H0.clone().requires_grad_(True)
+        a = cdmpt_lib.Polarizability.apply(X, H1, p.beta, p.nocc, p.n, hd)
+        a.sum().backward()
+        ga = X.grad.cpu().numpy()
+        Y = H0.clone().requires_grad_(True)
+        om = cdmpt_lib.FreeEnergy.apply(Y, p.beta, p.nocc, p.n, hd)
+        om.backward()
+        gw = Y.grad.cpu().numpy()
+
+        def alpha(H):
+            hd.set_H(H, p.H1)
+            hd.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+            return float(np.sum(hd.polarizability()))
+
+        def omega(H):
+            hd.set_H(H, None)
+            hd.solve(p.beta, p.nocc, p.n, want_P0=False, want_P1=False)
+            return hd.free_energy(want_grad=False)["omega"]
+
+        ea, ew = [], []
+        for _ in range(20):
+            E = _sym(rng, p.N, 0.05)
+            fa = (alpha(p.H0 + h * E) - alpha(p.H0 - h * E)) / (2 * h)
+            fw = (omega(p.H0 + h * E) - omega(p.H0 - h * E)) / (2 * h)
+            ea.append(abs(fa - np.sum(ga * E)) / max(1e-12, abs(fa)))
+            ew.append(abs(fw - np.sum(gw * E)) / max(1e-12, abs(fw)))
+    assert max(ea) < 1e-5, max(ea)
+    assert max(ew) < 1e-6, max(ew)
+    ref = oracle.solve(p.H0, None, p.beta, p.nocc, n=p.n, kind="rec")
+    assert oracle.rel_frobenius(gw, ref["P0"]) < 1e-10
+
+
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 def test_adjoint_float_lattice_2048(cuda, cdmpt_lib, precision):
     """The differentiation workload: 16 x 16 x 8 lattice (N = 2048), beta = 20, n = 16."""

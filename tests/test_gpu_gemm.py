@@ -117,6 +117,63 @@ def test_gemm_f64(cuda, cdmpt_lib):
     assert abs(dot.item() - np.sum(got * got)) < 1e-12 * np.sum(got * got)
 
 
+@pytest.mark.parametrize("M,N,K", [(100, 70, 90), (300, 200, 130), (1024, 1024, 1024),
+                                   (777, 513, 2049)])
+def test_gemm_f64_tensor_core_matches_fp64(cuda, cdmpt_lib, M, N, K):
+    """FP64 Ozaki product (seven BF16 digits per element, cdmpt_gemm_f64_tc) against NumPy's
+    FP64 product: rows spread over 2^-30 .. 2^30 (the per-row powers of two of the slicing),
+    one all-zero row, ragged M, N and K (partial tiles, a K tail beyond the last 32-block)."""
+    import torch
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    X = _mat(rng, M, K, dtype=np.float64) * np.exp2(rng.integers(-30, 31, size=M))[:, None]
+    Y = _mat(rng, N, K, dtype=np.float64) * np.exp2(rng.integers(-30, 31, size=N))[:, None]
+    X[M // 3] = 0.0
+    C = _mat(rng, M, N, dtype=np.float64)
+    D = torch.zeros((M, N), dtype=torch.float64, device=cuda)
+    dot = torch.zeros(1, dtype=torch.float64, device=cuda)
+    cdmpt_lib.gemm_f64(_t(X, cuda), _t(Y, cuda), D, alpha=0.5, beta=-1.0, C=_t(C, cuda),
+                       gamma=3.0, dot=dot, engine="tc")
+    torch.cuda.synchronize()
+    P = X @ Y.T
+    ref = 0.5 * P - C
+    ref[np.arange(min(M, N)), np.arange(min(M, N))] += 3.0
+    got = D.cpu().numpy()
+    # elementwise against the scale of the terms (row and column maxima of |X| |Y|^T)
+    scale = 0.5 * np.abs(X).max(axis=1)[:, None] * np.abs(Y).max(axis=1)[None, :] * K
+    assert np.all(np.abs(got - ref) <= 2.0 ** -44 * scale + 4e-16 * np.abs(ref) + 1e-300)
+    assert _rel(got, ref) < 1e-13
+    assert abs(dot.item() - np.sum(got * got)) < 1e-12 * np.sum(got * got)
+
+
+def test_gemm_f64_tensor_core_epilogue(cuda, cdmpt_lib):
+    """alpha, beta C, gamma on block diagonals, transposed block placement and the fused dot
+    with E on the FP64 tensor-core engine."""
+    import torch
+    rng = np.random.default_rng(11)
+    Nb, blocks = 160, 2
+    M, N, K = Nb * blocks, Nb, Nb
+    X = _mat(rng, M, K, dtype=np.float64)
+    Y = _mat(rng, N, K, dtype=np.float64)
+    C = _mat(rng, M, N, dtype=np.float64)
+    E = _mat(rng, M, N, dtype=np.float64)
+    alpha, beta, gamma = -1.25, 2.0, 0.75
+    acc = X @ Y.T
+    for trans in (0, Nb):
+        ref = np.empty((M, N))
+        for b in range(blocks):
+            blk = alpha * acc[b * Nb:(b + 1) * Nb] + gamma * np.eye(Nb)
+            ref[b * Nb:(b + 1) * Nb] = (blk.T if trans else blk) + beta * C[b * Nb:(b + 1) * Nb]
+        D = torch.zeros((M, N), dtype=torch.float64, device=cuda)
+        dot = torch.zeros(1, dtype=torch.float64, device=cuda)
+        cdmpt_lib.gemm_f64(_t(X, cuda), _t(Y, cuda), D, alpha=alpha, beta=beta, C=_t(C, cuda),
+                           gamma=gamma, diag_block=Nb, trans_block=trans, dot=dot, E=_t(E, cuda),
+                           engine="tc")
+        torch.cuda.synchronize()
+        got = D.cpu().numpy()
+        assert _rel(got, ref) < 1e-13, trans
+        assert abs(dot.item() - np.sum(got * E)) < 1e-12 * np.sum(np.abs(got * E))
+
+
 def test_gemm_rejects_misaligned_ld(cuda, cdmpt_lib):
     import torch
     X = torch.zeros((64, 66), dtype=torch.float32, device=cuda)

@@ -127,6 +127,18 @@ def test_fp32_cubic16_full_size(cuda, cdmpt_lib, beta):
     _check(r, ref, BAR["fp32"], 1)
 
 
+@pytest.mark.parametrize("beta", [5.0, 20.0, 80.0])
+def test_fp64_cubic16_full_size(cuda, cdmpt_lib, beta):
+    """FP64 on the measured lattice (16^3, N = 4096, n = 14) at each temperature against the
+    1e-10 bar. The products run on the tensor cores (seven-digit Ozaki engine, the FP64
+    default on sm_103), which the statistics must show."""
+    p = syn.cubic_lattice((16, 16, 16), seed=1002, beta=beta, n=14)
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec", eig=_eig_cubic16())
+    r = _run(cdmpt_lib, p, "fp64", profile=True)
+    _check(r, ref, BAR["fp64"], 1)
+    assert r["stats"]["engine_launches"][5] > 0 and r["stats"]["engine_launches"][1] == 0
+
+
 @pytest.mark.parametrize("beta,bar", [(5.0, 1e-6), (20.0, 1e-6), (80.0, 1e-6)])
 def test_mixed_cubic16_full_size(cuda, cdmpt_lib, beta, bar):
     """Mixed precision on the measured workload (N = 4096, n = 14)."""
