@@ -108,7 +108,7 @@ def test_fp64_differentiation_workload_central_differences(cuda, cdmpt_lib):
             ew.append(abs(fw - np.sum(gw * E)) / max(1e-12, abs(fw)))
     assert max(ea) < 1e-5, max(ea)
     assert max(ew) < 1e-6, max(ew)
-    ref = oracle.solve(p.H0, None, p.beta, p.nocc, n=p.n, kind="rec")
+    ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
     assert oracle.rel_frobenius(gw, ref["P0"]) < 1e-10
 
 

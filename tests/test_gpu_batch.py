@@ -113,3 +113,22 @@ def test_batch_mixed_precision_matches_oracle(cuda, cdmpt_lib):
             ea = abs(float(r["alpha"][i][d]) - ref["alpha"][d]) / abs(ref["alpha"][d])
             assert ea < 1e-6, (i, d, ea)
     b.close()
+
+
+@pytest.mark.parametrize("precision,bar", [("mixed", 1e-6), ("fp32", 1e-5)])
+def test_batch_largest_cluster_sizes(cuda, cdmpt_lib, precision, bar):
+    """The top of the batched workload's size range (N_b up to 1536, the largest size the
+    96-cluster draw allows) next to small ragged systems: every system's P0 and P1 (three
+    directions) against the oracle at the precision's bar."""
+    probs = syn.clusters(B=4, seed=7005, sizes=[1536, 1031, 777, 128], n=12)
+    b = cdmpt_lib.Batch([p.N for p in probs], 3, precision=precision)
+    b.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
+    r = b.solve([p.beta for p in probs], [p.nocc for p in probs], 12)
+    for i, p in enumerate(probs):
+        ref = oracle.solve(p.H0, p.H1, p.beta, p.nocc, n=p.n, kind="rec")
+        e0 = oracle.rel_frobenius(r["P0"][i].cpu().numpy(), ref["P0"])
+        assert e0 < bar, (i, e0)
+        for d in range(3):
+            e1 = oracle.rel_frobenius(r["P1"][i][d].cpu().numpy(), ref["P1"][d])
+            assert e1 < bar, (i, d, e1)
+    b.close()
