@@ -202,8 +202,10 @@ __global__ void k_cg_scalar_step(double* sc) {
     }
 }
 
-__global__ void k_cg_scalar_init(double* sc, double tol2, double tol2_r0) {
-    const double thresh = fmax(tol2 * sc[CG_BB], tol2_r0 * sc[CG_RR]);
+__global__ void k_cg_scalar_init(double* sc, double tol2, double tol2_r0, const double* ref,
+                                 double tol2_ref) {
+    double thresh = fmax(tol2 * sc[CG_BB], tol2_r0 * sc[CG_RR]);
+    if (ref) thresh = fmax(thresh, tol2_ref * *ref);
     sc[CG_THRESH] = thresh;
     sc[CG_RR0] = sc[CG_RR];
     sc[CG_ITERS] = 0.0;
@@ -729,8 +731,9 @@ cdmpt_status cg_scalar_step(double* sc, cudaStream_t s) {
     return CDMPT_OK;
 }
 
-cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s) {
-    k_cg_scalar_init<<<1, 1, 0, s>>>(sc, tol2, tol2_r0);
+cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s,
+                            const double* ref, double tol2_ref) {
+    k_cg_scalar_init<<<1, 1, 0, s>>>(sc, tol2, tol2_r0, ref, tol2_ref);
     LAUNCH_CHECK();
     return CDMPT_OK;
 }

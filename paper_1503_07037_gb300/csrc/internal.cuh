@@ -273,7 +273,10 @@ cdmpt_status to_f64(double* out, int ldo, const float* hi, const float* lo, int 
 cdmpt_status split_tf32(const float* X, size_t count, float* hi, float* lo, cudaStream_t s);
 cdmpt_status cg_scalar_step(double* sc, cudaStream_t s);
 // threshold = max(tol2 * <B,B>, tol2_r0 * <R0,R0>)
-cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s);
+// Starts a CG solve's scalars: stop once <R,R> <= max(tol2 <RHS,RHS>, tol2_r0 <R0,R0>,
+// tol2_ref *ref) (ref: a device scalar, or null).
+cdmpt_status cg_scalar_init(double* sc, double tol2, double tol2_r0, cudaStream_t s,
+                            const double* ref = nullptr, double tol2_ref = 0.0);
 cdmpt_status gershgorin(const double* H, int N, int ld, double* out2, cudaStream_t s);
 cdmpt_status gershgorin_noalloc(const double* H, int N, int ld, double* out2, cudaStream_t s);
 // Count of kernel launches issued by this thread (for statistics).

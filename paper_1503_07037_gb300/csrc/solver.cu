@@ -49,6 +49,7 @@ enum Slot {
     S_TRZ = 8,      // Tr Z_n
     S_ZZ = 9,       // ||Z_n||_F^2
     S_TRQ = 10,     // Tr Q
+    S_REF = 11,     // ||ref||_F^2 of the running CG solve's absolute tolerance
     S_TRZ1 = 16,    // Tr Z1_d (d < 16)
     S_ALPHA = 32,   // sum P1_d * H1_d (d < 16)
     S_FE = 48,      // free energy and Omega terms: traces and dots (5 slots)
@@ -422,7 +423,7 @@ cdmpt_status Solver<T>::gemm(Context& cx, int M, int Nc, int K, const Operand<T>
 // iterations launched after convergence return at once.
 template <typename T>
 cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
-                           double* rel_res0) {
+                           double* rel_res0, bool* met_tol) {
     const size_t count = (size_t)a.rows * ld;
     double* sc = sc_;
     const int init_engine = engine_of(cx, a.init_engine);
@@ -461,8 +462,14 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
         CDMPT_TRY(Ew<T>::dot(R_.x, R_.x, count, sc + CG_RR, nullptr, cx.stream));
     }
     CDMPT_TRY(Ew<T>::dot(a.rhs, a.rhs, count, sc + CG_BB, nullptr, cx.stream));
+    const bool use_ref = a.ref != nullptr && a.tol_ref > 0.0;
+    if (use_ref) {
+        CDMPT_CUDA_TRY(cudaMemsetAsync(sc + S_REF, 0, sizeof(double), cx.stream));
+        CDMPT_TRY(Ew<T>::dot(a.ref, a.ref, count, sc + S_REF, nullptr, cx.stream));
+    }
     CDMPT_TRY(cg_scalar_init(sc, a.tol * a.tol * a.rhs_scale * a.rhs_scale, a.tol_r0 * a.tol_r0,
-                             cx.stream));
+                             cx.stream, use_ref ? sc + S_REF : nullptr,
+                             a.tol_ref * a.tol_ref * a.ref_scale * a.ref_scale));
     // the split of the direction P: both halves for the split-TF32 iterations, hi alone for
     // one-pass TF32, none for the engines that read P itself
     T* p_hi = (iter_engine == CDMPT_GEMM_TC_3XTF32 || iter_engine == CDMPT_GEMM_TC_TF32) ? P_.hi
@@ -490,7 +497,7 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
             CDMPT_TRY(Ew<T>::cg_direction(P_.x, R_.x, count, sc, cx.stream, p_hi, p_lo));
             CDMPT_TRY(cg_scalar_step(sc, cx.stream));
         }
-        CDMPT_TRY(read_scalars(cx, sc, CG_NSLOTS));
+        CDMPT_TRY(read_scalars(cx, sc, S_REF + 1));
         const int now = (int)cx.pinned[CG_ITERS];
         const int ran = now - iters;
         iters = now;
@@ -523,6 +530,16 @@ cdmpt_status Solver<T>::cg(Context& cx, T* X, const CgArgs& a, int* iters_out,
     if (rel_res0) {
         const double bb = cx.pinned[CG_BB] * a.rhs_scale * a.rhs_scale;
         *rel_res0 = bb > 0 ? std::sqrt(cx.pinned[CG_RR0] / bb) : 0.0;
+    }
+    if (met_tol) {
+        // the final residual meets the tolerance of the solve itself (relative to the right
+        // side or the absolute reference), not only the tol_r0 reduction of this call
+        const double bb = cx.pinned[CG_BB] * a.rhs_scale * a.rhs_scale;
+        double lim = a.tol * a.tol * bb;
+        if (use_ref)
+            lim = std::max(lim, a.tol_ref * a.tol_ref * a.ref_scale * a.ref_scale *
+                                    cx.pinned[S_REF]);
+        *met_tol = cx.pinned[CG_RR] <= lim;
     }
     return CDMPT_OK;
 }
@@ -811,6 +828,15 @@ cdmpt_status Solver<T>::step0(Context& cx, int k, int engine, double tol, int ma
     a.maxit = maxit;
     a.init_engine = a.iter_engine = engine;
     a.hint = *hint;
+    // accurate solves (FP32, FP64): tolerance relative to the new iterate Z_{k+1} = 2 Z_k + d
+    // as well: in the early steps the right side -2 Z_k W_k is far below Z_k, and its own
+    // relative tolerance would solve d to digits that Z_{k+1} cannot hold. The one-pass sweeps
+    // of the mixed precisions keep theirs: their traces steer mu before the refinement.
+    if (tol <= 1e-6) {
+        a.ref = Z_[k].x;
+        a.ref_scale = 2.0;
+        a.tol_ref = tol;
+    }
     // mirrored CG products only in the one-pass sweeps that are refined afterwards:
     // the iterates drift from commuting with W_k at rounding level, and the mirrored
     // operator is then not self-adjoint (measured: FP32-mode P1 errors doubled)
@@ -1932,6 +1958,13 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             a.maxit = o.cg_maxit;
             a.init_engine = a.iter_engine = acc;
             a.hint = hint;
+            // the correction d1 needs the tolerance relative to the new iterate
+            // Z1_{k+1} = 2 Z1_k + d1, not to its own right side: in the early steps that side
+            // is of the size of W_k Z1_k, far below Z1_k, and a tolerance relative to it
+            // would ask for digits the stored response never keeps
+            a.ref = Z1->x;
+            a.ref_scale = 2.0;
+            a.tol_ref = o.cg_tol;
             int it = 0;
             if (mixed && response_ir()) {
                 // mixed-precision iterative refinement of the step's system: one-pass TF32
@@ -1947,12 +1980,13 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
                     }
                     int itc = 0;
                     double rel0 = 0.0;
-                    CDMPT_TRY(cg(cx, Z1n->x, a, &itc, &rel0));
+                    bool met = false;
+                    CDMPT_TRY(cg(cx, Z1n->x, a, &itc, &rel0, &met));
                     it += itc;
                     a.hint = std::max(1, itc);
                     // done when the accurate residual already met the tolerance, or when this
                     // cycle's three digits reached it
-                    if (itc == 0 || rel0 * a.tol_r0 <= o.cg_tol) break;
+                    if (itc == 0 || met || rel0 * a.tol_r0 <= o.cg_tol) break;
                 }
             } else {
                 CDMPT_TRY(cg(cx, Z1n->x, a, &it, nullptr));

@@ -142,6 +142,11 @@ private:
         int init_engine = 0;            // engine of the initial residual (0: context default)
         int iter_engine = 0;            // engine of the iterations
         int hint = 1;                   // iterations expected (first chunk size)
+        // or ||R|| <= tol_ref ref_scale ||ref|| (ref: rows x ld, the same shape as X; null:
+        // none): an absolute tolerance on the scale of the quantity the solve updates
+        const T* ref = nullptr;
+        double ref_scale = 1.0;
+        double tol_ref = 0.0;
         // symmetric iterates: rhs and x0 symmetric and commuting with W (every
         // 0th-order solve), so each product is computed on upper-triangular tiles
         bool sym = false;
@@ -149,7 +154,8 @@ private:
     cdmpt_status gemm(Context& cx, int M, int Nc, int K, const Operand<T>& X,
                       const Operand<T>& Y, T* D, const Epilogue<T>& ep, const double* skip,
                       int engine_override = 0);
-    cdmpt_status cg(Context& cx, T* X, const CgArgs& a, int* iters_out, double* rel_res0);
+    cdmpt_status cg(Context& cx, T* X, const CgArgs& a, int* iters_out, double* rel_res0,
+                    bool* met_tol = nullptr);
     cdmpt_status sweep(Context& cx, const double* H0, double mu, double s2, const cdmpt_opts& o,
                        int n, int engine, double tol, int* cg_iters);
     // One 0th-order step: W_k = Z_k^2 (unless make_w is false) and, if solve,
