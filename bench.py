@@ -688,7 +688,7 @@ def run_batched(pkg, args, barrier, max_over_ranks=lambda x: x, rank=0, world=1)
            "ranks": world, "systems_on_rank0": len(probs)}
     results = {}
     for prec in ("fp32", "mixed"):
-        bt = pkg.Batch(sizes, 3, precision=prec)
+        bt = pkg.Batch(sizes, 3, precision=prec, profile=1)
         bt.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
         bt.solve(betas, noccs, 12)                 # warm-up (descriptor and map caches)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -704,10 +704,14 @@ def run_batched(pkg, args, barrier, max_over_ranks=lambda x: x, rank=0, world=1)
                      "cg_sweeps": st["cg_iterations_sweeps"],
                      "cg_refine": st["cg_iterations_refine"],
                      "kernel_launches": st["kernel_launches"],
+                     "phase_ms": dict(zip(("sweeps", "refine", "response", "q_mu1_alpha",
+                                           "output"), st["phase_ms"])),
                      "algorithmic_tflops": st["gemm_flops"] / (ms / 1e3) / 1e12,
                      "tuning": bt.tuning()}
         results[prec] = r
         bt.close()
+    if getattr(args, "batched_only", False):
+        return out
     # the same systems solved one at a time through the single-system path
     t0 = time.perf_counter()
     with pkg.Handle(precision="fp32") as h:
@@ -765,11 +769,20 @@ def main():
                     help="add the screened-product (block-sparse) chain measurement")
     ap.add_argument("--screen-sizes", default="4096,8192,16384",
                     help="chain sizes of the screened-product measurement")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the lockstep batches (FP32 and mixed) of the 96-cluster "
+                         "workload (one JSON line, no one-at-a-time comparison)")
     ap.add_argument("--screened-only", action="store_true",
                     help="run only the screened-product chain measurement (one JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched_only:
+        import paper_1503_07037_gb300 as pkg
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_batched(pkg, args, torch.cuda.synchronize)), flush=True)
+        return 0
     if args.screened_only:
         import paper_1503_07037_gb300 as pkg
         sizes = [int(x) for x in args.screen_sizes.split(",") if x]

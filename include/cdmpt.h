@@ -60,7 +60,8 @@ typedef enum {
 } cdmpt_status;
 
 typedef enum {
-    CDMPT_FP64 = 0,       /* FP64 storage, FP64 products (CUDA-core DFMA) */
+    CDMPT_FP64 = 0,       /* FP64 storage, FP64 products (tensor-core Ozaki slicing into seven
+                             BF16 digits on sm_103, or CUDA-core DFMA with CDMPT_GEMM_SIMT) */
     CDMPT_FP32 = 1,       /* FP32 storage, FP32-accurate products (3xTF32 on tcgen05 by default) */
     CDMPT_MIXED_TF32 = 2, /* one-pass TF32 products for the occupation sweeps; iterative
                              refinement of the pair-stored (hi + lo FP32) trajectory with
@@ -540,14 +541,17 @@ cdmpt_status cdmpt_gemm_f32_split(int engine, int M, int Ncols, int K, const flo
  * of 8 elements, 16-byte aligned), C1/C2/D/Dl share ldc and ldd. Xl, Yl, C1h, C1l, C2h, C2l
  * and Dl may be NULL (a NULL low part is zero; a NULL C term is skipped; Dl NULL: D only).
  * alpha, b1 and b2 must be powers of two or zero, so every scaling is exact. The error of
- * D + Dl is about 2^-39 of max_k |x_ik| max_k |y_jk| times sqrt(K). K <= 32768. The digits
- * of both operands (10 (M + Ncols) ld bytes plus one int per row) are allocated and freed
- * stream-ordered on the stream. Errors: ERR_ARG, ERR_UNSUPPORTED (not an sm_103 device),
- * ERR_OOM, ERR_CUDA. */
+ * D + Dl is about 2^-39 of max_k |x_ik| max_k |y_jk| times sqrt(K). K <= 32768. sym != 0
+ * with Y the same arrays as X (Yh == Xh, Yl == Xl, Ncols == M) and symmetric C terms: only
+ * the output tiles that meet the upper triangle are computed and every element with n >= m
+ * is written at (m, n) and (n, m) (the products W = X X^T and I - X X^T of the mixed
+ * refinement); otherwise sym is ignored. The digits of both operands (10 (M + Ncols) ld
+ * bytes plus one int per row; once when Y is X) are allocated and freed stream-ordered on
+ * the stream. Errors: ERR_ARG, ERR_UNSUPPORTED (not an sm_103 device), ERR_OOM, ERR_CUDA. */
 cdmpt_status cdmpt_gemm_pair(int M, int Ncols, int K, const float* Xh, const float* Xl, int ldx,
                              const float* Yh, const float* Yl, int ldy, float* D, float* Dl,
                              int ldd, double alpha, double b1, const float* C1h, const float* C1l,
-                             double b2, const float* C2h, const float* C2l, int ldc,
+                             double b2, const float* C2h, const float* C2l, int ldc, int sym,
                              void* stream);
 
 /* Check of the failure detection of the device waits (Sec. II of the paper names loss of

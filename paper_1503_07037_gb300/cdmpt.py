@@ -165,7 +165,7 @@ def lib() -> ctypes.CDLL:
         "cdmpt_split_tf32": (I, [P, ctypes.c_size_t, P, P, P]),
         "cdmpt_gemm_f32_split": (I, [I, I, I, I, P, P, I, P, P, I, P, I, D, D, P, I, D, I, I, P, P, I,
                                      P]),
-        "cdmpt_gemm_pair": (I, [I, I, I, P, P, I, P, P, I, P, P, I, D, D, P, P, D, P, P, I, P]),
+        "cdmpt_gemm_pair": (I, [I, I, I, P, P, I, P, P, I, P, P, I, D, D, P, P, D, P, P, I, I, P]),
         "cdmpt_check_bounded_wait": (I, [D, P]),
     }
     for name, (res, args) in sig.items():
@@ -291,18 +291,19 @@ def gemm_f32_split(Xs, Ys, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, engine="3x
 
 
 def gemm_pair(Xh, Xl, Yh, Yl, D, Dl=None, alpha=1.0, b1=0.0, C1=(None, None), b2=0.0,
-              C2=(None, None), K=None, stream=None):
+              C2=(None, None), K=None, sym=False, stream=None):
     """Ozaki-sliced product of pair-stored FP32 matrices (cdmpt_gemm_pair):
     D (+ Dl) = alpha (Xh + Xl)(Yh + Yl)^T + b1 C1 + b2 C2 with C1, C2 given as (hi, lo)
     pairs. All tensors are float32 CUDA tensors with row strides that are multiples of 8;
-    any low part may be None. alpha, b1, b2 are powers of two or zero."""
+    any low part may be None. alpha, b1, b2 are powers of two or zero. sym: Y is X and the
+    result symmetric, computed on the upper-triangle tiles and mirrored."""
     M, Ncols = Xh.shape[0], Yh.shape[0]
     K = Xh.shape[1] if K is None else K
     ldc = C1[0].stride(0) if C1[0] is not None else (C2[0].stride(0) if C2[0] is not None else D.stride(0))
     _check(lib().cdmpt_gemm_pair(M, Ncols, K, _ptr(Xh), _ptr(Xl), Xh.stride(0), _ptr(Yh), _ptr(Yl),
                                  Yh.stride(0), _ptr(D), _ptr(Dl), D.stride(0), float(alpha),
                                  float(b1), _ptr(C1[0]), _ptr(C1[1]), float(b2), _ptr(C2[0]),
-                                 _ptr(C2[1]), ldc, _stream_ptr(stream)))
+                                 _ptr(C2[1]), ldc, 1 if sym else 0, _stream_ptr(stream)))
 
 
 def check_bounded_wait(limit_ms=2.0, stream=None) -> int:

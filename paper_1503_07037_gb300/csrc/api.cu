@@ -1228,7 +1228,7 @@ extern "C" cdmpt_status cdmpt_gemm_pair(int M, int Ncols, int K, const float* Xh
                                         int ldx, const float* Yh, const float* Yl, int ldy,
                                         float* D, float* Dl, int ldd, double alpha, double b1,
                                         const float* C1h, const float* C1l, double b2,
-                                        const float* C2h, const float* C2l, int ldc,
+                                        const float* C2h, const float* C2l, int ldc, int sym,
                                         void* stream) {
     using namespace cdmpt;
     if (M < 0 || Ncols < 0 || K < 1 || K > 32768 || !Xh || !Yh || !D || ldx < K || ldy < K ||
@@ -1260,8 +1260,11 @@ extern "C" cdmpt_status cdmpt_gemm_pair(int M, int Ncols, int K, const float* Xh
     ox.ld = ldx;
     oy.ld = ldy;
     cdmpt_status st = oz_slice(Xh, Xl, M, K, ldx, ox, s);
-    if (st == CDMPT_OK) st = oz_slice(Yh, Yl, Ncols, K, ldy, oy, s);
+    const bool same = Xh == Yh && Xl == Yl && M == Ncols && ldx == ldy;
+    if (st == CDMPT_OK && !same) st = oz_slice(Yh, Yl, Ncols, K, ldy, oy, s);
+    if (same) oy = ox;   // one set of digits for both operands (the symmetric mode needs it)
     OzEpi ep;
+    ep.sym = (sym && M == Ncols && Xh == Yh && Xl == Yl) ? 1 : 0;
     ep.D = D;
     ep.Dl = Dl;
     ep.ldd = ldd;

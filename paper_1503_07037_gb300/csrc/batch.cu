@@ -455,6 +455,10 @@ struct BCg {
     const float* rhs;
     const Mat* W;
     int rows;
+    // absolute tolerance on the scale of the updated quantity: stop also once
+    // ||R|| <= tol_ref ref_scale ||ref|| (ref: rows x ld like X; null: none)
+    const float* ref = nullptr;
+    double ref_scale = 1.0;
 };
 
 // sym: every system's iterates are symmetric (0th-order solves), so the
@@ -465,10 +469,28 @@ struct BCg {
 cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, double t, double tol,
                       const std::vector<const double*>& skip, int hint, int* iters,
                       bool sym = false, int engine = kEngine, int init_engine = -1,
-                      double tol_r0 = 0.0, double* rel0 = nullptr) {
+                      double tol_r0 = 0.0, double* rel0 = nullptr, double tol_ref = 0.0,
+                      bool* met_all = nullptr) {
     if (init_engine < 0) init_engine = engine;
     const int G = b->B;
     CDMPT_TRY(zero_slots(b, 0, CG_NSLOTS));
+    bool use_ref = tol_ref > 0.0;
+    for (const BCg& c : a) use_ref = use_ref && c.ref != nullptr;
+    if (use_ref) {   // ||ref||^2 of every system into its reference slot
+        CDMPT_TRY(zero_slots(b, kCgRefSlot, 1));
+        std::vector<GrpEw> dref;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            GrpEw q = ewd((float*)a[i].ref, (float*)a[i].ref);
+            q.rows = a[i].rows; q.ld = sy.ld; q.N = sy.N;
+            q.count = (long long)a[i].rows * sy.ld;
+            q.sc = sy.sc;
+            q.s0 = kCgRefSlot;
+            q.skip = skip[i];
+            dref.push_back(q);
+        }
+        CDMPT_TRY(run_ew(b, G_DOT, dref));
+    }
     std::vector<GrpEw> dx, dr, drr, dbb, dp;
     std::vector<GemmSpec> g0;
     for (int i = 0; i < G; ++i) {
@@ -549,6 +571,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
             di[i].sc = b->sys[i].sc;
             di[i].s0 = tol * tol;
             di[i].s1 = tol_r0 * tol_r0;
+            di[i].s2 = use_ref ? tol_ref * tol_ref * a[i].ref_scale * a[i].ref_scale : 0.0;
             di[i].skip = skip[i];
         }
         const GrpEw* dev = nullptr;
@@ -640,6 +663,21 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
                 if (bb > 0) worst = std::max(worst, std::sqrt(b->pinned[i * kSlots + CG_RR0] / bb));
             }
             if (rel0) *rel0 = worst;
+            if (met_all) {
+                // every system's final residual meets the solve's own tolerance (relative to
+                // its right side or the absolute reference), not only the tol_r0 reduction
+                bool met = true;
+                for (int i = 0; i < G; ++i) {
+                    if (skip[i] && b->sys[i].converged) continue;   // skipped system
+                    const double* q = b->pinned + (size_t)i * kSlots;
+                    double lim = tol * tol * q[CG_BB];
+                    if (use_ref)
+                        lim = std::max(lim, tol_ref * tol_ref * a[i].ref_scale * a[i].ref_scale *
+                                                q[kCgRefSlot]);
+                    met = met && q[CG_RR] <= lim;
+                }
+                *met_all = met;
+            }
             return CDMPT_OK;
         }
         if (done_iters >= b->opts.cg_maxit) {
@@ -704,6 +742,8 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
             r.skip = skip[i];
             gr.push_back(r);
             cg[i] = BCg{sy.Z[k + 1].x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
+            cg[i].ref = sy.Z[k].x;     // accurate sweeps: also relative to 2 Z_k (as cdmpt_solve)
+            cg[i].ref_scale = 2.0;
             GrpEw z = ewd(sy.Z[k + 1].x, sy.Z[k].x);   // Z_{k+1} = 2 Z_k + d
             z.rows = sy.N; z.ld = sy.ld; z.N = sy.N; z.count = (long long)sy.N * sy.ld;
             z.s0 = 2.0;
@@ -727,8 +767,10 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
         for (int i = 0; i < G; ++i)
             if (!b->sys[i].converged) add_flops(b, 2.0 * sym_flops(b, b->sys[i].N), engine);
         int it = 0;
-        // mirrored CG products only in the one-pass sweeps of mixed precision (refined later)
-        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, tol, skip, hint, &it, engine != kEngine, engine));
+        // mirrored CG products only in the one-pass sweeps of mixed precision (refined later);
+        // the accurate sweeps (tol <= 1e-6) also stop relative to the new iterate
+        CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, tol, skip, hint, &it, engine != kEngine, engine, -1,
+                           0.0, nullptr, tol <= 1e-6 ? tol : 0.0));
         total += it;
         hint = std::max(1, it);
         CDMPT_TRY(run_ew(b, G_AXPBY, dz));
@@ -769,6 +811,7 @@ cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& a
         for (int a = 0; a < 3; ++a) oz[a].ld = sy.ld;
         CDMPT_TRY(oz_slice(sy.Z[k].x, sy.Z[k].xl, sy.N, sy.N, sy.ld, oz[0], ls));
         OzEpi w;
+        w.sym = 1;   // W_k = Z_k Z_k: upper-triangle tiles, mirrored
         w.D = sy.W[k].x;
         w.Dl = wl;
         w.Dthi = sy.W[k].hi;
@@ -1016,6 +1059,7 @@ cdmpt_status cdmpt_batch_create(const cdmpt_opts* opts, int B, const int* N, int
         b->sys[i].blk = (size_t)N[i] * b->sys[i].ld;
     }
     b->cx.stream = (cudaStream_t)b->opts.stream;
+    b->cx.profile = b->opts.profile != 0;   // phase boundaries of the solve (statistics)
     b->slot_bytes = std::max<size_t>(64 * 1024, (size_t)B * 16 * sizeof(GrpEw));
     b->slot_bytes = std::max<size_t>(b->slot_bytes, (size_t)B * D * sizeof(GrpEw) + 1024);
     b->slot_bytes = std::max<size_t>(b->slot_bytes, (size_t)B * sizeof(GemmProblem) + 1024);
@@ -1102,6 +1146,8 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
     const bool mixed = b->opts.precision == CDMPT_MIXED_TF32;
     const int sweep_engine = mixed ? (int)CDMPT_GEMM_TC_TF32 : kEngine;
     const double sweep_tol = mixed ? 1e-4 : b->opts.cg_tol;
+    for (bool& f : b->cx.ph_set) f = false;
+    b->cx.mark(0);
     // -------------------------------------------------- occupation loops, in lockstep
     int sweeps = 0;
     for (; sweeps < b->opts.mu_maxit; ++sweeps) {
@@ -1165,6 +1211,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         if (!b->sys[i].converged)
             return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
                              "batch: occupation of system " + std::to_string(i) + " not reached");
+    b->cx.mark(1);
     // -------------------------------------------------- refinement (mixed), in lockstep
     if (mixed) {
         const int min_pass = std::max(1, b->opts.refine_rounds);
@@ -1268,6 +1315,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                                    cudaMemcpyHostToDevice, st));
     std::vector<const double*> none(G, nullptr);
 
+    b->cx.mark(2);
     // -------------------------------------------------- response (all systems, D directions)
     if (D > 0) {
         std::vector<GrpEw> d;
@@ -1317,6 +1365,8 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 r2.skip = nullptr;
                 g2.push_back(r2);
                 cg[i] = BCg{Z1n->x, nullptr, sy.RHS.x, &sy.W[k], rows};
+                cg[i].ref = Z1->x;     // tolerance also relative to 2 Z1_k (as cdmpt_solve)
+                cg[i].ref_scale = 2.0;
                 GrpEw z = ewd(Z1n->x, Z1->x);
                 z.rows = rows; z.ld = sy.ld; z.N = sy.N; z.count = (long long)rows * sy.ld;
                 z.s0 = 2.0;
@@ -1358,14 +1408,16 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                     }
                     int itc = 0;
                     double r0 = 0.0;
+                    bool met = false;
                     s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, h, &itc, false,
-                                 CDMPT_GEMM_TC_TF32, kEngine, 1e-3, &r0);
+                                 CDMPT_GEMM_TC_TF32, kEngine, 1e-3, &r0, b->opts.cg_tol, &met);
                     it += itc;
                     h = std::max(1, itc);
-                    if (itc == 0 || r0 * 1e-3 <= b->opts.cg_tol) break;
+                    if (itc == 0 || met || r0 * 1e-3 <= b->opts.cg_tol) break;
                 }
             } else {
-                s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it);
+                s = cg_batch(b, cg, 1.0, 1.0, b->opts.cg_tol, none, hint, &it, false, kEngine, -1,
+                             0.0, nullptr, b->opts.cg_tol);
             }
             if (s != CDMPT_OK) return bfail(b, s);
             total += it;
@@ -1374,6 +1426,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             CDMPT_TRY(run_tiles(b, dsym, D, grouped_symmetrize));
         }
         b->st.cg_iterations_response = total;
+        b->cx.mark(3);
         // Q' = (I - Z_n^2)(I - W_0)^-1; dP0/dmu = beta/4 Q'
         {
             std::vector<GemmSpec> gq;
@@ -1404,6 +1457,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                     for (auto& o : b->oz[0]) o.ld = sy.ld;
                     CDMPT_TRY(oz_slice(sy.Z[n].x, sy.Z[n].xl, sy.N, sy.N, sy.ld, b->oz[0][0], st));
                     OzEpi q;
+                    q.sym = 1;   // I - Z_n Z_n: upper-triangle tiles, mirrored
                     q.D = sy.RHS.x;
                     q.Dthi = sy.RHS.hi;
                     q.Dtlo = sy.RHS.lo;
@@ -1485,6 +1539,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             for (int dd = 0; dd < D; ++dd)
                 if (alpha) alpha[i * D + dd] = -b->pinned[i * kSlots + B_ALPHA + dd];
     }
+    b->cx.mark(4);
     // -------------------------------------------------- outputs
     for (int i = 0; i < G; ++i) {
         Sys& sy = b->sys[i];
@@ -1522,9 +1577,18 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
             }
         }
     }
+    b->cx.mark(5);
     CDMPT_CUDA_TRY(cudaStreamSynchronize(st));
     b->st.kernel_launches = (int)(launch_count() - launches0);
     b->st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < 5 && b->cx.profile; ++i) {
+        if (!b->cx.ph_set[i]) continue;
+        int j = i + 1;
+        while (j < 6 && !b->cx.ph_set[j]) ++j;
+        float e = 0;
+        if (j < 6 && cudaEventElapsedTime(&e, b->cx.ph[i], b->cx.ph[j]) == cudaSuccess)
+            b->st.phase_ms[i] = e;
+    }
     b->st.n = n;
     b->st.D = D;
     b->st.N = G;
@@ -1559,6 +1623,8 @@ void cdmpt_batch_destroy(cdmpt_batch* b) {
     if (!b) return;
     drop_graphs(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaEvent_t e : b->cx.ph)
+        if (e) cudaEventDestroy(e);
     for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
         if (b->hp_st[l]) cudaStreamDestroy(b->hp_st[l]);
         if (b->hp_join[l]) cudaEventDestroy(b->hp_join[l]);

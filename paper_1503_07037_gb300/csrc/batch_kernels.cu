@@ -302,7 +302,8 @@ __global__ void k_grouped_cg_init(const GrpEw* __restrict__ desc, int G) {
     if (g >= G) return;
     const GrpEw d = desc[g];
     double* sc = d.sc;
-    const double thresh = fmax(d.s0 * sc[CG_BB], d.s1 * sc[CG_RR]);
+    double thresh = fmax(d.s0 * sc[CG_BB], d.s1 * sc[CG_RR]);
+    if (d.s2 > 0.0) thresh = fmax(thresh, d.s2 * sc[kCgRefSlot]);
     sc[CG_THRESH] = thresh;
     sc[CG_RR0] = sc[CG_RR];
     sc[CG_ITERS] = 0.0;

@@ -22,7 +22,11 @@ struct GrpEw {
     int N, ld, rows;
     double s0, s1;        // op coefficients
     const double* skip;   // system skipped while *skip != 0 (may be null)
+    double s2;            // CG init: tolerance^2 on the reference norm in slot kCgRefSlot (0: none)
 };
+
+// Per-system scalar slot that holds ||ref||^2 of a CG solve's absolute tolerance.
+constexpr int kCgRefSlot = 11;
 
 enum GrpOp {
     G_AXPBY = 0,      // p0 = s0 p1 + s1 p0, split to (p2, p3) when given

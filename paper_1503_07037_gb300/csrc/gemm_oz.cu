@@ -236,6 +236,30 @@ __device__ __forceinline__ float scale2(float x, int sh) {
 }
 
 
+// Output tile t of the launch: M-fastest over all tiles, or, for a symmetric result, over
+// the tiles that meet the upper triangle only (column tile nt holds the row tiles mt with
+// 256 mt <= the tile's last column).
+__host__ __device__ __forceinline__ int oz_sym_count(int nt, int num_mt, int bn) {
+    const int c = (nt * bn + bn - 1) / (2 * BM) + 1;
+    return c < num_mt ? c : num_mt;
+}
+__device__ __forceinline__ void oz_tile(int t, int num_mt, int bn, bool sym, int* mt, int* nt) {
+    if (!sym) {
+        *mt = t % num_mt;
+        *nt = t / num_mt;
+        return;
+    }
+    int j = 0;
+    while (true) {
+        const int c = oz_sym_count(j, num_mt, bn);
+        if (t < c) break;
+        t -= c;
+        ++j;
+    }
+    *mt = t;
+    *nt = j;
+}
+
 template <int ND>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_gemm_oz(const __grid_constant__ OzMaps<ND> maps, const __grid_constant__ OzEpi p, int K,
@@ -298,7 +322,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             for (int t = cid; t < total_tiles && ok; t += ncl) {
-                const int mt = t % num_mt, nt = t / num_mt;
+                int mt = 0, nt = 0;
+                oz_tile(t, num_mt, BN, p.sym != 0, &mt, &nt);
                 const int m0 = mt * (2 * BM) + (int)rank * BM;
                 const int y0 = nt * BN + (int)rank * (BN / 2);
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
@@ -401,7 +426,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         uint32_t gc = 0, tc = 0;
         double dsum = 0.0;
         for (int t = cid; t < total_tiles; t += ncl, ++tc) {
-            const int mt = t % num_mt, nt = t / num_mt;
+            int mt = 0, nt = 0;
+            oz_tile(t, num_mt, BN, p.sym != 0, &mt, &nt);
             const int m = mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
             const int n0 = nt * BN + CW * h;
             int G[NX][CW];
@@ -463,7 +489,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int n = n0 + c0 + j;
-                        if (n < p.N) {
+                        if (n < p.N && !(p.sym && n < m)) {
                             // exact integer part of the exact groups, then the float tail of the
                             // whole-K groups, in units of the last exact group's weight
                             long long I = 0;
@@ -491,15 +517,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             if (p.gamma != 0.f && n == m) dd::add1(dh, dl, p.gamma, dh, dl);
                             float o, ol;
                             dd::fast_two_sum(dh, dl, o, ol);
+                            // symmetric result: the mirror (n, m) too (the lanes hold
+                            // consecutive rows m, so these stores coalesce)
+                            const bool mir = p.sym && n > m;
+                            const size_t mirror = (size_t)n * p.ldd + m;
                             p.D[rowd + n] = o;
-                            if (p.Dl) p.Dl[rowd + n] = ol;
+                            if (mir) p.D[mirror] = o;
+                            if (p.Dl) {
+                                p.Dl[rowd + n] = ol;
+                                if (mir) p.Dl[mirror] = ol;
+                            }
                             if (p.Dthi) {
                                 float th, tl;
                                 dd::tf32_split(o, th, tl);
                                 p.Dthi[rowd + n] = th;
-                                if (p.Dtlo) p.Dtlo[rowd + n] = tl;
+                                if (mir) p.Dthi[mirror] = th;
+                                if (p.Dtlo) {
+                                    p.Dtlo[rowd + n] = tl;
+                                    if (mir) p.Dtlo[mirror] = tl;
+                                }
                             }
-                            local = __fmaf_rn(o, o, local);
+                            local = __fmaf_rn(mir ? 2.f * o : o, o, local);
                         }
                     }
                     dsum += (double)local;
@@ -630,7 +668,13 @@ cdmpt_status launch_oz(int M, int N, int K, const OzOperand& X, const OzOperand&
     p.ex = X.e;
     p.ey = Y.e;
     const int num_mt = (M + 2 * BM - 1) / (2 * BM);
-    const int tiles = num_mt * ((N + C::BN - 1) / C::BN);
+    const int num_nt = (N + C::BN - 1) / C::BN;
+    p.sym = (ep.sym && M == N && X.s[0] == Y.s[0]) ? 1 : 0;
+    int tiles = 0;
+    if (p.sym)
+        for (int j = 0; j < num_nt; ++j) tiles += oz_sym_count(j, num_mt, C::BN);
+    else
+        tiles = num_mt * num_nt;
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters);

@@ -213,6 +213,9 @@ struct OzEpi {
     double* dot = nullptr;
     const int* ex = nullptr;   // set by gemm_oz from the operands
     const int* ey = nullptr;
+    // symmetric result (X is Y, M = N, the C terms symmetric): only the tiles that meet the
+    // upper triangle are computed, each element n >= m written at (m, n) and (n, m)
+    int sym = 0;
 };
 constexpr int kOzDigits = 5;   // digits of the refinement products (39 bits of the row maximum)
 // digit products per k-step: the pairs (p, q) with p + q <= nd + 1, i.e. nd (nd + 1) / 2

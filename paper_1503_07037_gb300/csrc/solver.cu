@@ -1004,7 +1004,9 @@ cdmpt_status Solver<T>::p0_out(Context& cx, double* out, int ldo) {
 template <typename T>
 cdmpt_status Solver<T>::gemm_hp(Context& cx, const OzOperand& X, const OzOperand& Y,
                                 const OzEpi& ep) {
-    const double flops = 2.0 * N_ * (double)N_ * N_;
+    // a symmetric result computes the tiles of the upper triangle: N (N + 1) N, as for the
+    // symmetric TF32 products
+    const double flops = ep.sym ? (double)N_ * (N_ + 1) * N_ : 2.0 * N_ * (double)N_ * N_;
     cudaEvent_t e1 = nullptr;
     if (cx.profile) {
         while (cx.ev.size() < 2 * (cx.ev_used + 1)) {
@@ -1052,6 +1054,7 @@ cdmpt_status Solver<T>::residual_hp(Context& cx, int k) {
         CDMPT_TRY(oz_slice(Z_[k].x, Z_[k].xl, N_, N_, ld, oz_[0], cx.stream));
         {
             OzEpi ep;
+            ep.sym = 1;   // W_k = Z_k Z_k: upper-triangle tiles, mirrored
             ep.D = W_[k].x;
             ep.Dl = wl_;
             ep.Dthi = W_[k].hi;
@@ -1106,6 +1109,7 @@ cdmpt_status Solver<T>::compute_q(Context& cx) {
         if (pairs_ && Z_[n].xl) {
             CDMPT_TRY(oz_slice(Z_[n].x, Z_[n].xl, N_, N_, ld, oz_[0], cx.stream));
             OzEpi ep;
+            ep.sym = 1;   // I - Z_n Z_n: upper-triangle tiles, mirrored
             ep.D = RHS_.x;
             ep.Dthi = RHS_.hi;
             ep.Dtlo = RHS_.lo;

@@ -338,3 +338,32 @@ def test_gemm_pair_step_residual(cuda, cdmpt_lib):
     ref = 2.0 * Zp[:, :N] - Znp[:, :N] - Znp[:, :N] @ Wp[:, :N].T
     err = np.abs(R.cpu().numpy()[:, :N].astype(np.float64) - ref).max()
     assert err < 1e-11 * np.abs(Znp).max() * np.abs(Wp).sum(axis=1).max(), err
+
+
+@pytest.mark.parametrize("N", [300, 1024, 1100])
+def test_gemm_pair_symmetric_result(cuda, cdmpt_lib, N):
+    """sym = 1 (Y is X): only the output tiles that meet the upper triangle are computed and
+    mirrored. The result W = X X^T - I (the right side I - Z_n^2 of dP0/dmu, negated) and its
+    TF32 split must equal the full product's (the same element sums, written twice) and be
+    exactly symmetric, for N not a multiple of the 256 x 96 tiles."""
+    import torch
+    rng = np.random.default_rng(N)
+    ld = (N + 7) // 8 * 8
+    A = rng.standard_normal((N, N)) / np.sqrt(N)
+    Zh, Zl, Zp = _pair(np.pad(0.5 * (A + A.T), ((0, 0), (0, ld - N))))
+    t = lambda a: _t(a, cuda)
+    outs = []
+    for sym in (False, True):
+        D = torch.zeros((N, ld), dtype=torch.float32, device=cuda)
+        Dl = torch.zeros_like(D)
+        Xh, Xl = t(Zh), t(Zl)
+        cdmpt_lib.gemm_pair(Xh, Xl, Xh, Xl, D, Dl, K=N, sym=sym)
+        torch.cuda.synchronize()
+        outs.append((D.cpu().numpy()[:, :N], Dl.cpu().numpy()[:, :N]))
+    (Df, Dlf), (Ds, Dls) = outs
+    assert np.array_equal(Ds, Ds.T) and np.array_equal(Dls, Dls.T)
+    up = np.triu_indices(N)
+    assert np.array_equal(Ds[up], Df[up]) and np.array_equal(Dls[up], Dlf[up])
+    ref = Zp[:, :N] @ Zp[:, :N].T
+    got = Ds.astype(np.float64) + Dls.astype(np.float64)
+    assert _rel(got, ref) < 3e-11
