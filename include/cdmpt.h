@@ -470,13 +470,15 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
 cdmpt_status cdmpt_batch_get_stats(const cdmpt_batch* b, cdmpt_stats* st);
 
 /* Tile autotuner and graph report of a batch. tile_n: the grouped kernel's
- * tile width chosen by timing each candidate (128 and 64 columns, the same
- * accumulation and so the same rounding) on the batch's first product over all
- * systems; 0 before the first solve. ms[0], ms[1]: the measured time per
- * launch of the 128- and 64-column candidates (0 if not timed). graphs: 1 when
+ * tile width chosen by timing each candidate on the batch's first product over
+ * all systems; 0 before the first solve. The candidates are 128 x 128 and
+ * 128 x 64 tiles on one SM, and 256 x 256 tiles on a cluster of two SMs for
+ * the split-TF32 products (one-pass TF32 products then take 128 x 128 tiles);
+ * all three accumulate the same k-chunks, so results agree to FP32 rounding. ms: an array of 3 that receives the measured time per launch
+ * of the 128-, 64- and 256-column candidates (0 if not timed). graphs: 1 when
  * the CG iterations replay a captured CUDA graph (CDMPT_BATCH_GRAPH=0 turns
- * capture off; CDMPT_BATCH_TILE=64|128 fixes the tile width). Any pointer may
- * be NULL. Errors: ERR_ARG (b NULL). */
+ * capture off; CDMPT_BATCH_TILE=64|128|256 fixes the tile width). Any pointer
+ * may be NULL. Errors: ERR_ARG (b NULL). */
 cdmpt_status cdmpt_batch_get_tuning(const cdmpt_batch* b, int* tile_n, double* ms, int* graphs);
 
 /* Last error of the batch ("" if none). */

@@ -670,12 +670,12 @@ class Batch:
     def tuning(self):
         """The tile autotuner's choice and timings, and whether CG iterations replay a graph."""
         tn = ctypes.c_int(0)
-        ms = np.zeros(2)
+        ms = np.zeros(3)
         gr = ctypes.c_int(0)
         self._check(lib().cdmpt_batch_get_tuning(self.h, ctypes.addressof(tn), ms.ctypes.data,
                                                  ctypes.addressof(gr)))
         return {"tile_n": tn.value, "ms_128": float(ms[0]), "ms_64": float(ms[1]),
-                "graphs": bool(gr.value)}
+                "ms_256": float(ms[2]), "graphs": bool(gr.value)}
 
     def stats(self):
         s = Stats()

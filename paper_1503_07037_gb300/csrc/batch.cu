@@ -64,6 +64,7 @@ struct Sys {
     double gmin = 0, gmax = 0, trH0 = 0;
     // host-side state of the current solve
     double beta = 0, nocc = 0, s2 = 0, mu = 0, lo = 0, hi = 0;
+    double e_lo = 0, e_hi = 0;   // occupation errors at lo and hi once a sweep set them
     bool converged = false;
 };
 
@@ -93,7 +94,7 @@ struct cdmpt_batch {
     double* pinned = nullptr;     // scalar readback, B x kSlots
     // tile autotuner: chosen tile width (0 = not tuned yet) and the timings
     int tile_bn = 0;
-    double tune_ms[2] = {0.0, 0.0};   // per launch, tile widths 128 and 64
+    double tune_ms[3] = {0.0, 0.0, 0.0};   // per launch, tile widths 128, 64 and 256
     // CUDA graph of one CG iteration: dedicated descriptors, graphs by shape
     GemmProblem* it_gemm = nullptr;   // B problems
     GrpEw* it_ew = nullptr;           // 3 B: update, direction, scalar step
@@ -189,7 +190,9 @@ cdmpt_status quad_of(cdmpt_batch* b, const Mat* X, int rows, const Mat* Y, int N
         return CDMPT_ERR_OOM;
     }
     CUtensorMap m[4];
-    const int bn = b->tile_bn;
+    // the wide two-SM kernel (tile width 256) loads boxes of 128 rows of both operands, as
+    // does the one-pass 128-column kernel that shares these maps
+    const int bn = b->tile_bn == 256 ? 128 : b->tile_bn;
     if (!tc_encode_operand(&m[0], X->hi, rows, N, ld, false, kEngine, bn) ||
         !tc_encode_operand(&m[1], Y->hi, N, N, ld, true, kEngine, bn) ||
         !tc_encode_operand(&m[2], X->lo, rows, N, ld, false, kEngine, bn) ||
@@ -226,10 +229,10 @@ void add_flops(cdmpt_batch* b, double f, int engine = kEngine) {
 }
 
 // Flops of one symmetric N x N x N product: the upper-triangular tiles only
-// when the grouped kernel's tiles are square (tile width 128), else all.
+// when the grouped kernel's tiles are square (tile width 128 or 256), else all.
 double sym_flops(const cdmpt_batch* b, int N) {
     const double n = N;
-    return b->tile_bn == 128 || b->tile_bn == 0 ? n * (n + 1) * n : 2.0 * n * n * n;
+    return b->tile_bn != 64 ? n * (n + 1) * n : 2.0 * n * n * n;
 }
 
 struct GemmSpec {
@@ -258,15 +261,32 @@ EpiParams<float> epi(float* D, int M, int N, int ld, float alpha = 1.f, float be
     return p;
 }
 
-// Problem descriptors of one grouped product (tensor maps resolved and uploaded).
+// Problem descriptors of one grouped product (tensor maps resolved and uploaded). Tiles
+// are 128 x tile_bn, except at tile width 256: 256 x 256 for split-TF32 products (the
+// wide two-SM kernel) and 128 x 128 for one-pass TF32 products.
 cdmpt_status prepare_grouped(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
-                             std::vector<GemmProblem>* probs, int* tiles_out) {
+                             std::vector<GemmProblem>* probs, int* tiles_out,
+                             int engine = kEngine) {
     std::vector<int> quad;
     probs->clear();
     probs->reserve(specs.size());
     int tiles = 0;
-    const int bm = tc_tile_m(), bn = b->tile_bn > 0 ? b->tile_bn : tc_tile_n(kEngine);
-    for (const GemmSpec& g : specs) {
+    int bm = tc_tile_m(), bn = b->tile_bn > 0 ? b->tile_bn : tc_tile_n(kEngine);
+    if (bn == 256) {
+        if (engine == kEngine)
+            bm = 256;
+        else
+            bn = 128;
+    }
+    // tiles are numbered problem by problem and CTAs stride over them: the largest K
+    // first, so that each stride takes tiles of about the same length and the last
+    // ones to finish are the shortest (longest-processing-time order)
+    std::vector<int> order(specs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return specs[x].p.N > specs[y].p.N; });
+    for (int oi : order) {
+        const GemmSpec& g = specs[oi];
         const int N = g.p.N;
         int q = 0;
         CDMPT_TRY(quad_of(b, g.X, g.rows, g.Y, N, g.p.ldd, &q));
@@ -297,7 +317,7 @@ cdmpt_status grouped_gemm(cdmpt_batch* b, const std::vector<GemmSpec>& specs,
                           int engine = kEngine) {
     std::vector<GemmProblem> probs;
     int tiles = 0;
-    CDMPT_TRY(prepare_grouped(b, specs, &probs, &tiles));
+    CDMPT_TRY(prepare_grouped(b, specs, &probs, &tiles, engine));
     if (probs.empty()) return CDMPT_OK;
     const GemmProblem* dev = nullptr;
     CDMPT_TRY(stage(b, probs, &dev));
@@ -315,12 +335,12 @@ void clear_maps(cdmpt_batch* b) {
 // idempotent) and keeps the fastest. CDMPT_BATCH_TILE=64|128 fixes the choice.
 cdmpt_status tune_tiles(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
     const char* env = getenv("CDMPT_BATCH_TILE");
-    if (env && (atoi(env) == 64 || atoi(env) == 128)) {
+    if (env && (atoi(env) == 64 || atoi(env) == 128 || atoi(env) == 256)) {
         clear_maps(b);
         b->tile_bn = atoi(env);
         return CDMPT_OK;
     }
-    const int cand[2] = {128, 64};
+    const int cand[3] = {128, 64, 256};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CDMPT_CUDA_TRY(cudaEventCreate(&e0));
     CDMPT_CUDA_TRY(cudaEventCreate(&e1));
@@ -329,7 +349,7 @@ cdmpt_status tune_tiles(cdmpt_batch* b, const std::vector<GemmSpec>& specs) {
     int best = 128;
     double best_ms = 1e300;
     cdmpt_status st = CDMPT_OK;
-    for (int c = 0; c < 2 && st == CDMPT_OK; ++c) {
+    for (int c = 0; c < 3 && st == CDMPT_OK; ++c) {
         clear_maps(b);
         b->tile_bn = cand[c];
         st = grouped_gemm(b, specs);   // warm-up (kernel attributes, maps)
@@ -614,7 +634,7 @@ cdmpt_status cg_batch(cdmpt_batch* b, const std::vector<BCg>& a, double s, doubl
     if (b->graphs) {
         std::vector<GemmProblem> probs;
         int tiles = 0;
-        CDMPT_TRY(prepare_grouped(b, gi, &probs, &tiles));
+        CDMPT_TRY(prepare_grouped(b, gi, &probs, &tiles, engine));
         long long maxc = 0;
         for (const GrpEw& e : du) maxc = std::max(maxc, (long long)e.rows * e.ld);
         std::vector<GrpEw> ew(du);
@@ -1140,6 +1160,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
         sy.lo = sy.gmin - pad;
         sy.hi = sy.gmax + pad;
         sy.mu = std::min(std::max(sy.trH0 / sy.N, sy.lo + 1e-3 * pad), sy.hi - 1e-3 * pad);
+        sy.e_lo = sy.e_hi = 0.0;
         sy.converged = false;
     }
     // mixed precision: one-pass TF32 sweeps, then split-TF32 refinement (as in cdmpt_solve)
@@ -1195,10 +1216,17 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 continue;
             }
             all = false;
-            if (err > 0) sy.hi = sy.mu; else sy.lo = sy.mu;
+            if (err > 0) {
+                sy.hi = sy.mu;
+                sy.e_hi = err;
+            } else {
+                sy.lo = sy.mu;
+                sy.e_lo = err;
+            }
             const double slope = 0.25 * sy.beta * (sy.N - zz);
-            double mnew = slope > 0 ? sy.mu - err / slope : 0.5 * (sy.lo + sy.hi);
-            if (!(mnew > sy.lo && mnew < sy.hi)) mnew = 0.5 * (sy.lo + sy.hi);
+            double mnew = slope > 0 ? sy.mu - err / slope : sy.lo - 1.0;
+            if (!(mnew > sy.lo && mnew < sy.hi))
+                mnew = next_mu_outside_newton(sy.lo, sy.hi, sy.e_lo, sy.e_hi);
             sy.mu = mnew;
         }
         if (all) {
@@ -1614,6 +1642,7 @@ cdmpt_status cdmpt_batch_get_tuning(const cdmpt_batch* b, int* tile_n, double* m
     if (ms) {
         ms[0] = b->tune_ms[0];
         ms[1] = b->tune_ms[1];
+        ms[2] = b->tune_ms[2];
     }
     if (graphs) *graphs = (b->graphs && !b->it_graphs.empty()) ? 1 : 0;
     return CDMPT_OK;

@@ -10,9 +10,11 @@
 //   warp 1      TMEM allocator and single-thread tcgen05.mma issuer
 //               (kind::tf32, M = 128, N = BN, K = 8 per instruction) into
 //               one of two TMEM accumulators (2 x BN columns);
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //               lanes 32 (w % 4) ...), alpha/beta/gamma, transposed
-//               placement, fused Frobenius dot, global stores;
+//               placement, fused Frobenius dot, global stores in 32 x 32
+//               blocks through a per-warp shared-memory transpose
+//               (tc_store.cuh), so that every access is a row segment;
 // For 3xTF32 the operands arrive already split in HBM (hi = rna_tf32(x),
 // lo = rna_tf32(x - hi), written once by the kernel that produced x) and TMA
 // loads the hi and lo tiles of both operands, so the MMA forms
@@ -23,9 +25,11 @@
 // about 2^-11 of the result, are issued before the four hi*hi ones: on the
 // first k-block of a chunk they are truncated at the scale of a small
 // accumulator.
-// The finished sums of a tile are parked in a TMEM sum buffer and stored four
-// columns at a time between the chunk drains of the next tile (tc_deferred.cuh),
-// so the global stores overlap the MMAs.
+// Warps 2..5 sum the chunks of a tile and park the finished sums in a TMEM sum
+// buffer; warps 6..9 store the parked tile while the chunk warps drain the next
+// tile's chunks, so the global stores overlap the MMAs. With the whole K in one
+// accumulator (one pass, or KCH = 0) all eight warps drain it, two per TMEM lane
+// quarter, each taking half of the columns.
 //
 // Block-norm screening (single launches with a GemmProblem::mask): k-slice kb of
 // an output tile is skipped when the product of the Frobenius norms of its X and Y
@@ -51,7 +55,7 @@
 #include "epilogue.cuh"
 #include "gemm_problem.cuh"
 #include "internal.cuh"
-#include "tc_deferred.cuh"
+#include "tc_store.cuh"
 #include "tc_ptx.cuh"
 
 namespace cdmpt {
@@ -77,6 +81,10 @@ int split_chunk() {
 }
 
 
+// Threads of the kernel: producer and MMA warps, eight warps that drain the accumulators and,
+// in the chunked engine, four store warps.
+constexpr int tc_threads(int kch) { return kch > 0 ? 448 : 320; }
+
 template <int BN, int STAGES, int PASSES>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 4;
@@ -84,10 +92,12 @@ struct Cfg {
     static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
     // one pass: the A and B tiles; three passes: their hi and lo tiles
     static constexpr int STAGE_BYTES = PAIR_BYTES * (PASSES == 3 ? 2 : 1);
-    static constexpr int BAR_BYTES = 256;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+    // mbarriers (256 bytes), then the grouped launches' tile cache (kTileCache entries)
+    static constexpr int BAR_BYTES = 1024;
+    // eight epilogue warps, each with a transpose buffer (tc_store.cuh)
+    static constexpr int XPOSE_BYTES = 8 * kXposeWords * 4;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + XPOSE_BYTES + 1024;
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int THREADS = 192;
     static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(TMEM_COLS <= 512, "TMEM");
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
@@ -110,25 +120,44 @@ struct TileRef {
 // its maps from global memory. A problem whose skip flag is set (its CG has
 // converged) contributes no work; every role sees the same flags, so all roles
 // walk the same sequence of tiles.
+// Problem of launch-wide tile t: binary search over tile_begin.
+__device__ __forceinline__ int find_problem(int t, const GemmProblem* groups, int G) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (groups[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tiles of a grouped launch whose problem, K and skip flag each CTA looks up once, in
+// parallel, when it starts (entry i: the CTA's i-th tile): the MMA issuer then starts a
+// tile without a chain of dependent global loads. Later tiles use find_problem.
+constexpr int kTileCache = 96;
+
 template <bool GROUPED>
 __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
                                             const GemmProblem* groups, int G,
                                             const CUtensorMap* sx, const CUtensorMap* sy,
-                                            const CUtensorMap* sxl, const CUtensorMap* syl) {
+                                            const CUtensorMap* sxl, const CUtensorMap* syl,
+                                            const int2* cached = nullptr) {
     TileRef r;
     const GemmProblem* pr;
     if constexpr (GROUPED) {
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (groups[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        if (cached) {   // {problem, num_k or -1 when skipped}
+            const int2 e = *cached;
+            pr = &groups[e.x];
+            r.skip = e.y < 0;
+            r.num_k = e.y < 0 ? 0 : e.y;
+        } else {
+            pr = &groups[find_problem(t, groups, G)];
+            r.skip = pr->skip != nullptr && *pr->skip != 0.0;
+            r.num_k = (pr->K + BK - 1) / BK;
         }
-        pr = &groups[lo];
         r.mx = pr->maps;
         r.my = pr->maps + 1;
         r.mxl = pr->maps + 2;
         r.myl = pr->maps + 3;
-        r.skip = pr->skip != nullptr && *pr->skip != 0.0;
     } else {
         pr = &single;
         r.mx = sx;
@@ -136,12 +165,12 @@ __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
         r.mxl = sxl;
         r.myl = syl;
         r.skip = false;
+        r.num_k = (pr->K + BK - 1) / BK;
     }
     const int lt = t - pr->tile_begin;
     r.pr = pr;
     r.m0 = (lt % pr->num_mt) * BM;
     r.n0 = 0;   // set by the caller, which knows BN
-    r.num_k = (pr->K + BK - 1) / BK;
     return r;
 }
 
@@ -150,13 +179,14 @@ __device__ __forceinline__ TileRef tile_ref(int t, const GemmProblem& single,
 // the lanes need not own rows: warps take rows and lanes 16-byte column groups, so every
 // store is coalesced (the mirror gets its own row-major pass, C and E being symmetric). With
 // transposed placement the lanes take rows instead, which the placement turns into
-// consecutive columns. Returns the D * E contribution of the lane's elements.
+// consecutive columns. Warp q of nq takes every nq-th row (column). Returns the D * E
+// contribution of the lane's elements.
 template <int BN>
 __device__ double epi_fill_zero_tile(const EpiParams<float>& p, int m0, int n0, bool diag, int q,
-                                     int lane) {
+                                     int nq, int lane) {
     double dsum = 0.0;
     if (p.trans_block > 0) {
-        for (int j = q; j < BN && n0 + j < p.N; j += 4)
+        for (int j = q; j < BN && n0 + j < p.N; j += nq)
             for (int i = lane; i < BM && m0 + i < p.M; i += 32)
                 dsum += (double)epi_apply(p, m0 + i, n0 + j, 0.f);
         return dsum;
@@ -165,7 +195,7 @@ __device__ double epi_fill_zero_tile(const EpiParams<float>& p, int m0, int n0, 
     f.sym = 0;
     const bool vec4 = epi_vec4_ok(f);
     auto pass = [&](int r0, int c0, int rows, int cols) {
-        for (int i = q; i < rows && r0 + i < f.M; i += 4) {
+        for (int i = q; i < rows && r0 + i < f.M; i += nq) {
             const int m = r0 + i;
             for (int c = lane * 4; c < cols; c += 128) {
                 const int n = c0 + c;
@@ -185,7 +215,7 @@ __device__ double epi_fill_zero_tile(const EpiParams<float>& p, int m0, int n0, 
 
 // Every CTA loads its own A and B tiles (no cluster, no multicast).
 template <int BN, int STAGES, int PASSES, int KCH, bool GROUPED, bool SCREEN = false>
-__global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
+__global__ void __launch_bounds__(tc_threads(KCH), 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
               const __grid_constant__ GemmProblem single, const GemmProblem* groups, int G,
@@ -203,13 +233,18 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     uint64_t* tfull = empty + STAGES;   // [NB]
     uint64_t* tempty = tfull + 3;       // [NB]
     uint64_t* drain = tempty + 3;       // [1]
-    uint32_t* tmem_holder = (uint32_t*)(drain + 1);
+    uint64_t* parked = drain + 1;       // chunked engine: a finished tile is in the sum buffer
+    uint64_t* pfree = parked + 1;       // ... and has been read by the store warps
+    uint32_t* tmem_holder = (uint32_t*)(pfree + 1);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // symmetric results (p.sym, square tiles) enumerate the upper-triangular tiles only
+    const int2* tcache = (const int2*)(smem + STAGES * C::STAGE_BYTES + 256);
     auto tile = [&](int t) {
-        TileRef r = tile_ref<GROUPED>(t, single, groups, G, &tmX, &tmY, &tmXl, &tmYl);
+        const int li = (t - (int)blockIdx.x) / (int)gridDim.x;
+        TileRef r = tile_ref<GROUPED>(t, single, groups, G, &tmX, &tmY, &tmXl, &tmYl,
+                                      GROUPED && li < kTileCache ? tcache + li : nullptr);
         const int lt = t - r.pr->tile_begin;
         r.diag = false;
         if (BN == BM && r.pr->p.sym) {
@@ -262,9 +297,11 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
         }
         for (int a = 0; a < NB; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);   // one arrival per epilogue warp
+            mbar_init(&tempty[a], 8);   // one arrival per draining warp
         }
         mbar_init(drain, 1);
+        mbar_init(parked, 8);   // the eight chunk warps
+        mbar_init(pfree, 4);    // the four store warps
         *abort_flag = 0;
         fence_barrier_init();
         fence_proxy_async();
@@ -273,6 +310,21 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
     constexpr uint32_t kTmemCols = KCH > 0 ? 4 * BN : C::TMEM_COLS;
     static_assert(kTmemCols <= 512, "TMEM columns");
     if (warp == 1) tmem_alloc(tmem_holder, kTmemCols);
+    if constexpr (GROUPED) {
+        // the tile cache: one lookup per thread, all in parallel
+        int2* fill = (int2*)(smem + STAGES * C::STAGE_BYTES + 256);
+        for (int i = (int)threadIdx.x; i < kTileCache; i += (int)blockDim.x) {
+            const int t = t_first + i * t_step;
+            int2 e = make_int2(0, -1);
+            if (t < total_tiles) {
+                const int g = find_problem(t, groups, G);
+                const GemmProblem* pr = &groups[g];
+                const bool sk = pr->skip != nullptr && *pr->skip != 0.0;
+                e = make_int2(g, sk ? -1 : (pr->K + BK - 1) / BK);
+            }
+            fill[i] = e;
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -417,156 +469,150 @@ __global__ void __launch_bounds__(Cfg<BN, STAGES, PASSES>::THREADS, 1)
             }
         }
     } else {
-        // ------------------------------------------------ epilogue
+        // ------------------------------------------------ epilogue (warps 2 .. 9, 10 .. 13)
+        const int ew = warp - 2;
         const int q = warp & 3;     // TMEM lane quarter this warp may read
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        float* xbuf = (float*)(smem + STAGES * C::STAGE_BYTES + C::BAR_BYTES) + (ew & 7) * kXposeWords;
         double dsum = 0.0;
-        uint32_t g = 0;
-        PendingTile<BN> pend;   // chunked engine: finished tile parked in TMEM columns NB BN ..
-        auto finish_pending = [&]() {
+        // each problem of a grouped launch has its own dot target: flush per tile
+        auto flush_tile_dot = [&](double* dot) {
             if constexpr (GROUPED) {
-                // each problem has its own dot target: flush per tile
-                if (pend.p->dot) {
+                if (dot) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-                    if (lane == 0 && dsum != 0.0) atomicAdd(pend.p->dot, dsum);
+                    if (lane == 0 && dsum != 0.0) atomicAdd(dot, dsum);
                 }
                 dsum = 0.0;
             }
-            pend.p = nullptr;
         };
-        for (int t = t_first; t < total_tiles; t += t_step) {
-            const TileRef r = tile(t);
-            if (r.skip) continue;
-            const EpiParams<float> p = r.pr->p;
-            const bool vec4 = epi_vec4_ok(p);
-            const int m = r.m0 + 32 * q + lane;
+        // computed k-slices of a tile, the same count as the MMA issuer's (from lane 0)
+        auto active_of = [&](const TileRef& r) {
             int na = r.num_k;
-            if constexpr (screen) {   // the same count as the MMA issuer's, from lane 0
+            if constexpr (screen) {
                 if (lane == 0) na = count_active(r);
                 na = __shfl_sync(0xffffffffu, na, 0);
             }
-            int kc = 0;
-            const int nch = (screen && na == 0) ? 0 : chunks(na, &kc);
-            bool ok = true;
-            if constexpr (KCH > 0) {
-                // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
-                float acc[BN];
-#pragma unroll
-                for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-                for (int c = 0; c < nch; ++c, ++g) {
-                    const int b = g % NB;
-                    int w = 1;
-                    if (lane == 0)
-                        w = mbar_wait(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-                    w = __shfl_sync(0xffffffffu, w, 0);
-                    if (!w) {
-                        ok = false;
-                        break;
+            return na;
+        };
+        auto wait_bar = [&](uint64_t* bar, uint32_t parity, int code) {
+            int w = 1;
+            if (lane == 0) w = mbar_wait(bar, parity, abort_flag, err, code);
+            return __shfl_sync(0xffffffffu, w, 0) != 0;
+        };
+        if constexpr (KCH > 0) {
+            if (ew < 8) {
+                // chunk warps, two per lane quarter, each with half of the columns: sum the
+                // short TMEM partial sums of a tile in registers (IEEE round-to-nearest) and
+                // park the finished sums in the sum buffer (TMEM columns NB BN ..)
+                constexpr int HW = BN / 2;
+                const int col0 = (ew >> 2) * HW;
+                uint32_t g = 0, j = 0;
+                for (int t = t_first; t < total_tiles; t += t_step) {
+                    const TileRef r = tile(t);
+                    if (r.skip) continue;
+                    const int na = active_of(r);
+                    if (screen && na == 0) {   // every slice screened out: no TMEM, no barrier
+                        dsum += epi_fill_zero_tile<BN>(r.pr->p, r.m0, r.n0, r.diag, ew, 8, lane);
+                        flush_tile_dot(r.pr->p.dot);
+                        continue;
                     }
+                    int kc = 0;
+                    const int nch = chunks(na, &kc);
+                    float acc[HW];
+#pragma unroll
+                    for (int i = 0; i < HW; ++i) acc[i] = 0.f;
+                    bool ok = true;
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        const int b = g % NB;
+                        if (!wait_bar(&tfull[b], (g / NB) & 1, DEV_TIMEOUT_ACCUM)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll
+                        for (int c0 = 0; c0 < HW; c0 += 32) {
+                            uint32_t rr[32];
+                            tmem_ld32(lane_base + (uint32_t)(b * BN + col0 + c0), rr);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) acc[c0 + i] += __uint_as_float(rr[i]);
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[b]);
+                    }
+                    if (!ok) break;
+                    // the store warps must have read the previous parked tile
+                    if (!wait_bar(pfree, (j & 1) ^ 1, DEV_TIMEOUT_ACCUM)) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int c0 = 0; c0 < BN; c0 += 64) {
-                        uint32_t rr[64];
-                        tmem_ld64(lane_base + (uint32_t)(b * BN + c0), rr);
+                    for (int c0 = 0; c0 < HW; c0 += 32)
+                        tmem_st32(lane_base + (uint32_t)(NB * BN + col0 + c0), acc + c0);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(parked);
+                    ++j;
+                }
+            } else {
+                // store warps, one per lane quarter: the epilogue of each parked tile in
+                // 32 x 32 blocks through the transpose buffer, then the sum buffer goes back
+                uint32_t j = 0;
+                for (int t = t_first; t < total_tiles; t += t_step) {
+                    const TileRef r = tile(t);
+                    if (r.skip) continue;
+                    if (screen && active_of(r) == 0) continue;   // written by the chunk warps
+                    const EpiParams<float> p = r.pr->p;
+                    if (!wait_bar(parked, j & 1, DEV_TIMEOUT_ACCUM)) break;
+                    tc_fence_after();
+#pragma unroll 1
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t rr[32];
+                        tmem_ld32(lane_base + (uint32_t)(NB * BN + c0), rr);
+                        float a[32];
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
+                        for (int i = 0; i < 32; ++i) a[i] = __uint_as_float(rr[i]);
+                        dsum += (double)epi_block32(p, r.m0 + 32 * q, r.n0 + c0, r.diag, a, xbuf,
+                                                    lane);
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[b]);
-                    // a share of the previous tile's stores, spread over this tile's chunks
-                    if (pend.p) {
-                        const int left = BN / 4 - pend.next;
-                        if (pend.drain((left + (nch - c) - 1) / (nch - c), dsum)) finish_pending();
-                    }
+                    if (lane == 0) mbar_arrive(pfree);
+                    ++j;
+                    flush_tile_dot(p.dot);
                 }
-                if (!ok) break;
-                if (pend.p) {
-                    pend.drain(BN / 4, dsum);
-                    finish_pending();
-                }
-                if (screen && nch == 0)
-                    dsum += epi_fill_zero_tile<BN>(r.pr->p, r.m0, r.n0, r.diag, q, lane);
-                else
-                    pend.park(&r.pr->p, lane_base + (uint32_t)(NB * BN), m, r.n0, r.diag, acc);
-            } else {
-                (void)nch;
-                if constexpr (screen) {
-                    if (nch == 0) {   // every slice screened out: no TMEM, no barrier
-                        dsum += epi_fill_zero_tile<BN>(p, r.m0, r.n0, r.diag, q, lane);
-                        continue;
-                    }
+            }
+        } else {
+            // the whole K in one accumulator: eight warps drain it, two per lane quarter,
+            // each taking half of the columns
+            const int h = ew >> 2;
+            uint32_t g = 0;
+            for (int t = t_first; t < total_tiles; t += t_step) {
+                const TileRef r = tile(t);
+                if (r.skip) continue;
+                const EpiParams<float> p = r.pr->p;
+                if (screen && active_of(r) == 0) {   // every slice screened out
+                    dsum += epi_fill_zero_tile<BN>(p, r.m0, r.n0, r.diag, ew, 8, lane);
+                    flush_tile_dot(p.dot);
+                    continue;
                 }
                 const int b = g & 1;
-                int w = 1;
-                if (lane == 0)
-                    w = mbar_wait(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-                w = __shfl_sync(0xffffffffu, w, 0);
-                if (!w) break;
+                if (!wait_bar(&tfull[b], (g >> 1) & 1, DEV_TIMEOUT_ACCUM)) break;
                 tc_fence_after();
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
+                for (int c0 = h * (BN / 2); c0 < (h + 1) * (BN / 2); c0 += 32) {
                     uint32_t rr[32];
                     tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
-                    if (m < p.M && p.sym) {
-                        float local = 0.f;
-                        const int nb = r.n0 + c0;
-                        if (vec4 && !r.diag && nb + 32 <= p.N) {
+                    float a[32];
 #pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
-                                                    __uint_as_float(rr[j + 1]),
-                                                    __uint_as_float(rr[j + 2]),
-                                                    __uint_as_float(rr[j + 3]));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int n = nb + j;
-                                if (n < p.N)
-                                    local += epi_apply_sym(p, m, n, __uint_as_float(rr[j]), r.diag);
-                            }
-                        }
-                        dsum += (double)local;
-                    } else if (m < p.M) {
-                        float local = 0.f;
-                        const int nb = r.n0 + c0;
-                        if (vec4 && nb + 32 <= p.N) {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
-                                                    __uint_as_float(rr[j + 1]),
-                                                    __uint_as_float(rr[j + 2]),
-                                                    __uint_as_float(rr[j + 3]));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int n = nb + j;
-                                if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
-                            }
-                        }
-                        dsum += (double)local;
-                    }
+                    for (int i = 0; i < 32; ++i) a[i] = __uint_as_float(rr[i]);
+                    dsum += (double)epi_block32(p, r.m0 + 32 * q, r.n0 + c0, r.diag, a, xbuf, lane);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
                 ++g;
-            }
-            if constexpr (GROUPED && KCH == 0) {
-                // each problem has its own dot target: flush per tile
-                if (p.dot) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-                    if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
-                }
-                dsum = 0.0;
-            }
-        }
-        if constexpr (KCH > 0) {
-            if (pend.p) {
-                pend.drain(BN / 4, dsum);
-                finish_pending();
+                flush_tile_dot(p.dot);
             }
         }
         if constexpr (!GROUPED) {
@@ -639,7 +685,7 @@ cdmpt_status launch(int M, int N, int K, const float* X, const float* Xl, int ld
     pr.p.sym = sym ? 1 : 0;
     const int tiles = sym ? pr.num_mt * (pr.num_mt + 1) / 2 : pr.num_mt * ((N + BN - 1) / BN);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_tc<BN, STAGES, PASSES, KCH, false, SCREEN><<<grid, C::THREADS, C::SMEM, s>>>(
+    k_gemm_tc<BN, STAGES, PASSES, KCH, false, SCREEN><<<grid, tc_threads(KCH), C::SMEM, s>>>(
         mx, my, mxl, myl, pr, nullptr, 1, tiles, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -674,7 +720,7 @@ cdmpt_status launch_grouped(const GemmProblem* problems, int G, int total_tiles,
     GemmProblem none;
     std::memset(&none, 0, sizeof(none));
     const int grid = total_tiles < sm_count() ? total_tiles : sm_count();
-    k_gemm_tc<BN, STAGES, PASSES, KCH, true><<<grid, C::THREADS, C::SMEM, s>>>(
+    k_gemm_tc<BN, STAGES, PASSES, KCH, true><<<grid, tc_threads(KCH), C::SMEM, s>>>(
         dummy, dummy, dummy, dummy, none, problems, G, total_tiles, device_error_word());
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -738,10 +784,12 @@ cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int
     if (engine == CDMPT_GEMM_TC_TF32) {
         // one pass over the hi arrays; 128- and 64-column tiles share the tensor maps
         // of the split-TF32 engine with the same tile width (batched mixed precision)
-        if (bn == 128) return launch_grouped<128, 6, 1, 0>(problems, G, total_tiles, s);
+        if (bn == 128 || bn == 256) return launch_grouped<128, 6, 1, 0>(problems, G, total_tiles, s);
         if (bn == 64) return launch_grouped<64, 8, 1, 0>(problems, G, total_tiles, s);
         return launch_grouped<256, 4, 1, 0>(problems, G, total_tiles, s);
     }
+    if (bn == 256)   // the wide two-SM split kernel
+        return gemm_split2sm_grouped(split_chunk(), problems, G, total_tiles, s);
     if (bn == 64)   // the same chunk as the 128-column kernel, so the same sums
         return split_chunk() == 2 ? launch_grouped<64, 4, 3, 2>(problems, G, total_tiles, s)
                                   : launch_grouped<64, 4, 3, 1>(problems, G, total_tiles, s);

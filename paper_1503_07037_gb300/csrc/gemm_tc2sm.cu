@@ -37,6 +37,7 @@
 #include <string>
 
 #include "epilogue.cuh"
+#include "gemm_problem.cuh"
 #include "internal.cuh"
 #include "tc_deferred.cuh"
 #include "tc_ptx.cuh"
@@ -546,19 +547,51 @@ struct CfgS {
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int STAGES, int KCH, int EW>
+// One output tile of the wide kernel: its problem's tensor maps, epilogue and K, and its
+// position. Single launches take the kernel's own maps and parameters; grouped launches (the
+// batched solve: one launch over the products of all systems) find the problem by binary search
+// over the problems' first tiles.
+struct WideTile {
+    const CUtensorMap* mx;
+    const CUtensorMap* my;
+    const CUtensorMap* mxl;
+    const CUtensorMap* myl;
+    const EpiParams<float>* p;
+    int mt, nt, num_k;
+    bool sym, skip;
+    int g;   // problem index (0 for single launches)
+};
+
+// Tile t of a problem with num_mt x num_nt tiles: the upper triangle for symmetric results,
+// else groups of SPLIT_GROUP M-tiles (grouped raster).
+__device__ __forceinline__ void wide_tile_pos(int t, int num_mt, int num_nt, bool sym, int* mt,
+                                              int* nt) {
+    if (sym) {
+        tri_tile(t, num_mt, mt, nt);
+    } else {
+        const int grp = t / (SPLIT_GROUP * num_nt);
+        const int first = grp * SPLIT_GROUP;
+        const int gsize = min(SPLIT_GROUP, num_mt - first);
+        const int r = t - grp * SPLIT_GROUP * num_nt;
+        *mt = first + r % gsize;
+        *nt = r / gsize;
+    }
+}
+
+template <int STAGES, int KCH, int EW, bool GROUPED>
 __global__ void __launch_bounds__(split_threads(EW), 1)
     k_gemm_split2sm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                     const __grid_constant__ CUtensorMap tmXl,
                     const __grid_constant__ CUtensorMap tmYl,
                     const __grid_constant__ EpiParams<float> p, int K, int num_mt, int num_nt,
-                    int total_tiles, const double* skip, int* err) {
+                    int total_tiles, const double* skip, int* err, const GemmProblem* groups,
+                    int G) {
     using C = CfgS<STAGES>;
     static_assert(EW == 8 || EW == 16, "epilogue warps");
     constexpr int BN = SPLIT_BN, NB = 2, CW = 4 * BN / EW;
     constexpr int LW = CW >= 128 ? 32 : 16;   // columns per TMEM load
     constexpr uint32_t kTmemCols = NB * BN;
-    if (skip != nullptr && *skip != 0.0) return;
+    if (!GROUPED && skip != nullptr && *skip != 0.0) return;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -573,22 +606,44 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
-    const int num_k = (K + BK - 1) / BK;
-    const bool sym = p.sym != 0;
-    auto tile_of = [&](int t, int* mt, int* nt) {
-        if (sym) {
-            tri_tile(t, num_mt, mt, nt);
+    auto tile = [&](int t) {
+        WideTile w;
+        if constexpr (GROUPED) {
+            int lo = 0, hi = G - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (groups[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+            }
+            const GemmProblem* pr = &groups[lo];
+            w.g = lo;
+            w.mx = pr->maps;
+            w.my = pr->maps + 1;
+            w.mxl = pr->maps + 2;
+            w.myl = pr->maps + 3;
+            w.p = &pr->p;
+            w.sym = pr->p.sym != 0;
+            w.num_k = (pr->K + BK - 1) / BK;
+            w.skip = pr->skip != nullptr && *pr->skip != 0.0;
+            wide_tile_pos(t - pr->tile_begin, pr->num_mt, (pr->p.N + BN - 1) / BN, w.sym, &w.mt,
+                          &w.nt);
         } else {
-            const int grp = t / (SPLIT_GROUP * num_nt);
-            const int first = grp * SPLIT_GROUP;
-            const int gsize = min(SPLIT_GROUP, num_mt - first);
-            const int r = t - grp * SPLIT_GROUP * num_nt;
-            *mt = first + r % gsize;
-            *nt = r / gsize;
+            w.g = 0;
+            w.mx = &tmX;
+            w.my = &tmY;
+            w.mxl = &tmXl;
+            w.myl = &tmYl;
+            w.p = &p;
+            w.sym = p.sym != 0;
+            w.num_k = (K + BK - 1) / BK;
+            w.skip = false;
+            wide_tile_pos(t, num_mt, num_nt, w.sym, &w.mt, &w.nt);
         }
+        return w;
     };
-    const int kc = KCH > 0 ? KCH : num_k;
-    const int nch = (num_k + kc - 1) / kc;
+    auto chunks = [&](int num_k, int* kc) {
+        *kc = KCH > 0 ? KCH : num_k;
+        return (num_k + *kc - 1) / *kc;
+    };
     auto stage_a = [&](int s) { return smem + s * C::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * C::STAGE_BYTES + C::A_BYTES; };
     auto stage_alo = [&](int s) { return smem + s * C::STAGE_BYTES + C::PAIR_BYTES; };
@@ -623,19 +678,31 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
     } else if (warp == 0) {
         // ------------------------------------------------ TMA producer (both CTAs)
         if (lane == 0) {
-            prefetch_map(&tmX);
-            prefetch_map(&tmY);
-            prefetch_map(&tmXl);
-            prefetch_map(&tmYl);
+            if constexpr (!GROUPED) {
+                prefetch_map(&tmX);
+                prefetch_map(&tmY);
+                prefetch_map(&tmXl);
+                prefetch_map(&tmYl);
+            }
             const uint32_t full0 = mapa_u32(smem_u32(full), 0);
             uint32_t it = 0;
             bool ok = true;
+            int last = -1;
             for (int t = cid; t < total_tiles && ok; t += ncl) {
-                int mt = 0, nt = 0;
-                tile_of(t, &mt, &nt);
-                const int m0 = mt * (2 * BM) + (int)rank * BM;
-                const int y0 = nt * BN + (int)rank * (BN / 2);
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                const WideTile w = tile(t);
+                if (w.skip) continue;
+                if constexpr (GROUPED) {
+                    if (w.g != last) {   // maps written by the host: fence before first use
+                        acquire_map(w.mx);
+                        acquire_map(w.my);
+                        acquire_map(w.mxl);
+                        acquire_map(w.myl);
+                        last = w.g;
+                    }
+                }
+                const int m0 = w.mt * (2 * BM) + (int)rank * BM;
+                const int y0 = w.nt * BN + (int)rank * (BN / 2);
+                for (int kb = 0; kb < w.num_k; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!mbar_wait_cl(&empty[s], ph ^ 1, abort_flag, err, DEV_TIMEOUT_EMPTY)) {
@@ -644,10 +711,10 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
                     }
                     if (rank == 0) mbar_expect_tx(&full[s], 2 * C::STAGE_BYTES);
                     const uint32_t fb = full0 + (uint32_t)s * 8u;
-                    tma_load_2d_pair(stage_a(s), &tmX, kb * BK, m0, fb);
-                    tma_load_2d_pair(stage_b(s), &tmY, kb * BK, y0, fb);
-                    tma_load_2d_pair(stage_alo(s), &tmXl, kb * BK, m0, fb);
-                    tma_load_2d_pair(stage_blo(s), &tmYl, kb * BK, y0, fb);
+                    tma_load_2d_pair(stage_a(s), w.mx, kb * BK, m0, fb);
+                    tma_load_2d_pair(stage_b(s), w.my, kb * BK, y0, fb);
+                    tma_load_2d_pair(stage_alo(s), w.mxl, kb * BK, m0, fb);
+                    tma_load_2d_pair(stage_blo(s), w.myl, kb * BK, y0, fb);
                 }
             }
         }
@@ -658,6 +725,10 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
             uint32_t it = 0, g = 0;
             bool ok = true, issued = false;
             for (int t = cid; t < total_tiles && ok; t += ncl) {
+                const WideTile w = tile(t);
+                if (w.skip) continue;
+                int kc = 0;
+                const int nch = chunks(w.num_k, &kc);
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int b = g % NB;
                     if (!mbar_wait_cl(&tempty[b], ((g / NB) & 1) ^ 1, abort_flag, err,
@@ -667,7 +738,7 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
                     }
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
-                    const int kb0 = c * kc, kb1 = min(num_k, kb0 + kc);
+                    const int kb0 = c * kc, kb1 = min(w.num_k, kb0 + kc);
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
@@ -712,25 +783,28 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
         const int h = (warp - 2) >> 2;     // column group
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(CW * h);
         const uint32_t tempty0 = mapa_u32(smem_u32(tempty), 0);
-        const bool vec4 = epi_vec4_ok(p);
         double dsum = 0.0;
         uint32_t g = 0;
         for (int t = cid; t < total_tiles; t += ncl) {
-            int mt = 0, nt = 0;
-            tile_of(t, &mt, &nt);
-            const bool diag = sym && mt == nt;
-            const int m = mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
-            const int n0 = nt * BN + CW * h;
+            const WideTile w = tile(t);
+            if (w.skip) continue;
+            const EpiParams<float>& P = *w.p;
+            const bool vec4 = epi_vec4_ok(P);
+            const bool diag = w.sym && w.mt == w.nt;
+            const int m = w.mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
+            const int n0 = w.nt * BN + CW * h;
+            int kc = 0;
+            const int nch = chunks(w.num_k, &kc);
             float acc[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) acc[j] = 0.f;
             bool ok = true;
             for (int c = 0; c < nch; ++c, ++g) {
                 const int b = g % NB;
-                int w = 1;
+                int wt = 1;
                 if (lane == 0)
-                    w = mbar_wait_cl(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-                if (!__shfl_sync(0xffffffffu, w, 0)) {
+                    wt = mbar_wait_cl(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+                if (!__shfl_sync(0xffffffffu, wt, 0)) {
                     ok = false;
                     break;
                 }
@@ -750,32 +824,44 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
                 if (lane == 0) mbar_arrive_remote(tempty0 + (uint32_t)b * 8u);
             }
             if (!ok) break;
-            if (m >= p.M) continue;
+            if (m < P.M) {
 #pragma unroll
-            for (int c0 = 0; c0 < CW; c0 += 32) {
-                const int nb = n0 + c0;
-                float local = 0.f;
-                if (vec4 && !diag && nb + 32 <= p.N) {
+                for (int c0 = 0; c0 < CW; c0 += 32) {
+                    const int nb = n0 + c0;
+                    float local = 0.f;
+                    if (vec4 && !diag && nb + 32 <= P.N) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        local += epi_apply4(p, m, nb + j, acc[c0 + j], acc[c0 + j + 1],
-                                            acc[c0 + j + 2], acc[c0 + j + 3]);
-                } else if (sym) {
+                        for (int j = 0; j < 32; j += 4)
+                            local += epi_apply4(P, m, nb + j, acc[c0 + j], acc[c0 + j + 1],
+                                                acc[c0 + j + 2], acc[c0 + j + 3]);
+                    } else if (w.sym) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (nb + j < p.N) local += epi_apply_sym(p, m, nb + j, acc[c0 + j], diag);
-                } else {
+                        for (int j = 0; j < 32; ++j)
+                            if (nb + j < P.N) local += epi_apply_sym(P, m, nb + j, acc[c0 + j], diag);
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (nb + j < p.N) local += epi_apply(p, m, nb + j, acc[c0 + j]);
+                        for (int j = 0; j < 32; ++j)
+                            if (nb + j < P.N) local += epi_apply(P, m, nb + j, acc[c0 + j]);
+                    }
+                    dsum += (double)local;
                 }
-                dsum += (double)local;
+            }
+            if constexpr (GROUPED) {
+                // each problem has its own dot target: flush per tile
+                if (P.dot) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                    if (lane == 0 && dsum != 0.0) atomicAdd(P.dot, dsum);
+                }
+                dsum = 0.0;
             }
         }
-        if (p.dot) {
+        if constexpr (!GROUPED) {
+            if (p.dot) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-            if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                if (lane == 0 && dsum != 0.0) atomicAdd(p.dot, dsum);
+            }
         }
     }
 
@@ -897,12 +983,12 @@ int split_epilogue_warps() {
     return v;
 }
 
-template <int STAGES, int KCH, int EW>
-cdmpt_status launch_split2sm(int M, int N, int K, const float* X, const float* Xl, int ldx,
-                             const float* Y, const float* Yl, int ldy, const EpiParams<float>& p,
-                             const double* skip, cudaStream_t s) {
+// Resident clusters of two of an instantiation of the wide kernel (0 with the error set when
+// none fits), queried once per instantiation.
+template <int STAGES, int KCH, int EW, bool GROUPED>
+int split2sm_clusters() {
     using C = CfgS<STAGES>;
-    auto kern = k_gemm_split2sm<STAGES, KCH, EW>;
+    auto kern = k_gemm_split2sm<STAGES, KCH, EW, GROUPED>;
     static int max_clusters = 0;
     if (max_clusters == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -923,10 +1009,49 @@ cdmpt_status launch_split2sm(int M, int N, int K, const float* X, const float* X
         if (e != cudaSuccess || n < 1) {
             cudaGetLastError();
             set_error("split-TF32 two-SM GEMM: no resident cluster of two");
-            return CDMPT_ERR_UNSUPPORTED;
+            return 0;
         }
         max_clusters = n;
     }
+    return max_clusters;
+}
+
+template <int STAGES, int KCH, int EW, bool GROUPED>
+cdmpt_status launch_wide(int clusters, const CUtensorMap& mx, const CUtensorMap& my,
+                         const CUtensorMap& mxl, const CUtensorMap& myl, const EpiParams<float>& p,
+                         int K, int num_mt, int num_nt, int tiles, const double* skip,
+                         const GemmProblem* groups, int G, cudaStream_t s) {
+    using C = CfgS<STAGES>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(split_threads(EW));
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 2;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_gemm_split2sm<STAGES, KCH, EW, GROUPED>, mx, my, mxl,
+                                       myl, p, K, num_mt, num_nt, tiles, skip,
+                                       device_error_word(), groups, G);
+    count_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("split-TF32 two-SM GEMM launch: ") + cudaGetErrorString(e));
+        return CDMPT_ERR_CUDA;
+    }
+    return CDMPT_OK;
+}
+
+template <int STAGES, int KCH, int EW>
+cdmpt_status launch_split2sm(int M, int N, int K, const float* X, const float* Xl, int ldx,
+                             const float* Y, const float* Yl, int ldy, const EpiParams<float>& p,
+                             const double* skip, cudaStream_t s) {
+    const int max_clusters = split2sm_clusters<STAGES, KCH, EW, false>();
+    if (max_clusters == 0) return CDMPT_ERR_UNSUPPORTED;
     CUtensorMap mx, my, mxl, myl;
     if (!make_map(&mx, X, M, K, ldx, BM) || !make_map(&my, Y, N, K, ldy, SPLIT_BN / 2) ||
         !make_map(&mxl, Xl, M, K, ldx, BM) || !make_map(&myl, Yl, N, K, ldy, SPLIT_BN / 2)) {
@@ -940,27 +1065,24 @@ cdmpt_status launch_split2sm(int M, int N, int K, const float* X, const float* X
     EpiParams<float> pk = p;
     pk.sym = sym ? 1 : 0;
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * clusters);
-    cfg.blockDim = dim3(split_threads(EW));
-    cfg.dynamicSmemBytes = C::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute a;
-    a.id = cudaLaunchAttributeClusterDimension;
-    a.val.clusterDim.x = 2;
-    a.val.clusterDim.y = 1;
-    a.val.clusterDim.z = 1;
-    cfg.attrs = &a;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mx, my, mxl, myl, pk, K, num_mt, num_nt, tiles,
-                                       skip, device_error_word());
-    count_launch();
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error(std::string("split-TF32 two-SM GEMM launch: ") + cudaGetErrorString(e));
-        return CDMPT_ERR_CUDA;
-    }
-    return CDMPT_OK;
+    return launch_wide<STAGES, KCH, EW, false>(clusters, mx, my, mxl, myl, pk, K, num_mt, num_nt,
+                                               tiles, skip, nullptr, 0, s);
+}
+
+// Grouped launch over the problems of a batch (tiles numbered problem by problem, tensor maps
+// in device memory, boxes of 128 rows for both operands).
+template <int STAGES, int KCH, int EW>
+cdmpt_status launch_split2sm_grouped(const GemmProblem* problems, int G, int total_tiles,
+                                     cudaStream_t s) {
+    const int max_clusters = split2sm_clusters<STAGES, KCH, EW, true>();
+    if (max_clusters == 0) return CDMPT_ERR_UNSUPPORTED;
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    EpiParams<float> none;
+    std::memset(&none, 0, sizeof(none));
+    const int clusters = total_tiles < max_clusters ? total_tiles : max_clusters;
+    return launch_wide<STAGES, KCH, EW, true>(clusters, dummy, dummy, dummy, dummy, none, 0, 0, 0,
+                                              total_tiles, nullptr, problems, G, s);
 }
 
 }  // namespace
@@ -982,6 +1104,17 @@ cdmpt_status gemm_tc_2sm(bool three, int kch, int M, int N, int K, const float* 
         case 2: return launch_split2sm<3, 2, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
         case 4: return launch_split2sm<3, 4, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
         default: return launch_split2sm<3, 1, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
+    }
+}
+
+cdmpt_status gemm_split2sm_grouped(int kch, const GemmProblem* problems, int G,
+                                   int total_tiles, cudaStream_t s) {
+    if (G <= 0 || total_tiles <= 0) return CDMPT_OK;
+    switch (kch) {
+        case 0: return launch_split2sm_grouped<3, 0, 8>(problems, G, total_tiles, s);
+        case 2: return launch_split2sm_grouped<3, 2, 8>(problems, G, total_tiles, s);
+        case 4: return launch_split2sm_grouped<3, 4, 8>(problems, G, total_tiles, s);
+        default: return launch_split2sm_grouped<3, 1, 8>(problems, G, total_tiles, s);
     }
 }
 

@@ -148,6 +148,11 @@ int tc_tile_m();
 // encoded with the same bn (tc_encode_operand).
 cdmpt_status gemm_tc_grouped(int engine, const GemmProblem* problems, int G, int total_tiles,
                              cudaStream_t s, int bn = 0);
+// bn = 256 with the split engine: the grouped wide kernel, 256 x 256 two-SM tiles (problems'
+// num_mt in 256-row tiles, tensor maps with 128-row boxes for both operands; kch as in
+// gemm_tc_2sm).
+cdmpt_status gemm_split2sm_grouped(int kch, const GemmProblem* problems, int G,
+                                   int total_tiles, cudaStream_t s);
 
 // Elementwise / reduction launchers (T = float or double). "count" is the
 // number of elements of a contiguous rows x ld block; padding columns hold 0.
@@ -227,6 +232,8 @@ constexpr int oz_products(int nd) { return nd * (nd + 1) / 2; }
 double refine_settle();
 bool refine_early_hp();
 double hp_bound();
+// mu step of the occupation loops when Newton's step leaves the bracket (see solver.cu)
+double next_mu_outside_newton(double lo, double hi, double e_lo, double e_hi);
 
 // Digits of an FP64 operand for the FP64 Ozaki engine: seven BF16 digit arrays (rows x ld)
 // and the rows' powers of two.

@@ -212,6 +212,21 @@ cdmpt_status Solver<T>::read_scalars(Context& cx, const double* dev, int count) 
     return check_device_error(cx.stream);
 }
 
+// The mu step of the occupation loop when Newton's step (Eq. NewtRaphs: slope beta Tr[P (I -
+// P)], exact only as n -> infinity) leaves the bracket [lo, hi]: false position between the
+// bracket's ends once sweeps have measured both occupation errors (e_lo < 0 < e_hi), else
+// bisection. Where mu sits in a gap of the spectrum the slope nearly vanishes, Newton leaves
+// the bracket, and bisection alone would halve a bracket of several hoppings each sweep.
+double next_mu_outside_newton(double lo, double hi, double e_lo, double e_hi) {
+    if (e_lo < 0.0 && e_hi > 0.0) {
+        const double m = lo - e_lo * (hi - lo) / (e_hi - e_lo);
+        // stay away from the ends, where false position stalls
+        const double w = hi - lo;
+        if (m > lo + 0.05 * w && m < hi - 0.05 * w) return m;
+    }
+    return 0.5 * (lo + hi);
+}
+
 // FP64 storage: products on the tensor cores by the FP64 Ozaki engine (seven BF16 digits)
 // unless CUDA-core DFMA is asked for; CDMPT_FP64_ENGINE=simt forces DFMA for comparison.
 static bool fp64_on_tc() {
@@ -1786,6 +1801,7 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
     cx.mark(0);
     bool converged = false;
     double trP = 0, zz = 0;
+    double e_lo = 0.0, e_hi = 0.0;   // occupation errors at lo and hi once a sweep set them
     for (int it = 0; it < o.mu_maxit; ++it) {
         int iters = 0;
         CDMPT_TRY(sweep(cx, H0, mu, s2, o, n, fast, sweep_tol, &iters));
@@ -1801,13 +1817,17 @@ cdmpt_status Solver<T>::solve(Context& cx, const double* H0, const double* H1, i
             converged = true;
             break;
         }
-        if (err > 0)
+        if (err > 0) {
             hi = mu;
-        else
+            e_hi = err;
+        } else {
             lo = mu;
+            e_lo = err;
+        }
         const double slope = 0.25 * beta * (N - zz);
-        double mu_new = slope > 0 ? mu - err / slope : 0.5 * (lo + hi);
-        if (!(mu_new > lo && mu_new < hi)) mu_new = 0.5 * (lo + hi);
+        double mu_new = slope > 0 ? mu - err / slope : lo - 1.0;
+        if (!(mu_new > lo && mu_new < hi))
+            mu_new = next_mu_outside_newton(lo, hi, e_lo, e_hi);
         if (mu_new == mu) break;
         mu = mu_new;
     }
