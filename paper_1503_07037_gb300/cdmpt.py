@@ -275,8 +275,9 @@ def split_tf32(X, hi=None, lo=None, stream=None):
 
 
 def gemm_f32_split(Xs, Ys, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, engine="3xtf32", M=None,
-                   Ncols=None, K=None, stream=None):
-    """gemm_f32 on pre-split operands Xs = (hi, lo), Ys = (hi, lo)."""
+                   Ncols=None, K=None, dot=None, E=None, stream=None):
+    """gemm_f32 on pre-split operands Xs = (hi, lo), Ys = (hi, lo); dot (a float64 CUDA
+    tensor) receives += sum(D * E), or sum(D * D) without E."""
     Xh, Xl = Xs
     Yh, Yl = Ys
     M = Xh.shape[0] if M is None else M
@@ -287,7 +288,8 @@ def gemm_f32_split(Xs, Ys, D, alpha=1.0, beta=0.0, C=None, gamma=0.0, engine="3x
                                       _ptr(Yh), _ptr(Yl), Yh.stride(0), _ptr(D), D.stride(0),
                                       float(alpha), float(beta), _ptr(C),
                                       C.stride(0) if C is not None else 0, float(gamma), 0, 0,
-                                      None, None, 0, _stream_ptr(stream)))
+                                      _ptr(dot), _ptr(E), E.stride(0) if E is not None else 0,
+                                      _stream_ptr(stream)))
 
 
 def gemm_pair(Xh, Xl, Yh, Yl, D, Dl=None, alpha=1.0, b1=0.0, C1=(None, None), b2=0.0,

@@ -10,7 +10,7 @@
 // the Y tile instead of all of it: per flop it receives fewer bytes, so the
 // same shared memory holds more k-blocks of lookahead.
 //
-// Roles per CTA (192 threads):
+// Roles per CTA (320 threads):
 //   warp 0      TMA producer in both CTAs, each loading its own halves. The
 //               copies of both CTAs complete on CTA 0's full barrier (the
 //               .cta_group::2 form of the copy may signal the peer's barrier),
@@ -18,10 +18,13 @@
 //   warp 1      collective TMEM allocation of the pair; in CTA 0, lane 0
 //               issues the MMAs and commits them to the empty and
 //               accumulator-full barriers of both CTAs (multicast);
-//   warps 2..5  epilogue of this CTA's 128 rows (as in k_gemm_tc, including
-//               the deferred stores of the chunked engine); after draining an
-//               accumulator each warp arrives on CTA 0's accumulator-empty
-//               barrier, which counts 8 warps.
+//   warps 2..9  epilogue of this CTA's 128 rows, two warps per TMEM lane
+//               quarter, each with half of the columns, stored in 32 x 32
+//               blocks through a shared-memory transpose (tc_store.cuh); after
+//               draining an accumulator each warp arrives on CTA 0's
+//               accumulator-empty barrier, which counts the 16 warps of the
+//               pair. The whole K goes into one of two accumulators, so one
+//               tile's stores overlap the next tile's MMAs.
 // All tcgen05 instructions of the kernel use .cta_group::2.
 //
 // Every mbarrier wait is bounded by %globaltimer. On timeout the waiting
@@ -39,7 +42,7 @@
 #include "epilogue.cuh"
 #include "gemm_problem.cuh"
 #include "internal.cuh"
-#include "tc_deferred.cuh"
+#include "tc_store.cuh"
 #include "tc_ptx.cuh"
 
 namespace cdmpt {
@@ -55,9 +58,11 @@ struct Cfg2 {
     static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
     static constexpr int STAGE_BYTES = PAIR_BYTES * (PASSES == 3 ? 2 : 1);
     static constexpr int BAR_BYTES = 256;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
-    static constexpr int THREADS = 192;
-    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "BN");
+    // eight epilogue warps, each with a transpose buffer (tc_store.cuh)
+    static constexpr int XPOSE_BYTES = 8 * kXposeWords * 4;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + XPOSE_BYTES + 1024;
+    static constexpr int THREADS = 320;
+    static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte alignment of tiles");
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert((2 * STAGES + 8) * 8 + 8 <= BAR_BYTES, "barrier area");
@@ -67,6 +72,15 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t saddr, uint32_t rank) {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
     return r;
+}
+
+// Arrive on an mbarrier given by its shared::cluster address with the default .release.cta
+// semantics. The epilogue's per-chunk "accumulator drained" signal orders only tcgen05 loads
+// (completed by tcgen05.wait::ld and tcgen05.fence::before_thread_sync) against the peer's MMA;
+// a .release.cluster arrive would also wait, every chunk, for the warp's earlier global stores
+// (the previous tile's epilogue) to become visible cluster-wide.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t caddr) {
@@ -189,6 +203,7 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
                  const double* skip, int* err) {
     using C = Cfg2<BN, STAGES, PASSES>;
     // two accumulators; the chunked engine adds a sum buffer (power-of-two allocation)
+    static_assert(KCH == 0, "the whole K in one of two accumulators");
     constexpr uint32_t kTmemCols = KCH > 0 ? 4 * BN : 2 * BN;
     static_assert(kTmemCols <= 512, "TMEM columns");
     // both CTAs of a pair read the same flag, so both return or neither does
@@ -241,7 +256,7 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
         }
         for (int a = 0; a < NB; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 8);
+            mbar_init(&tempty[a], 16);   // the eight epilogue warps of both CTAs
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -352,120 +367,44 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
             }
         }
     } else {
-        // ------------------------------------------------ epilogue (both CTAs)
+        // ------------------------------------------------ epilogue (both CTAs, warps 2 .. 9)
+        // two warps per TMEM lane quarter, each with half of the tile's columns, stored in
+        // 32 x 32 blocks through its transpose buffer
+        const int ew = warp - 2;
         const int q = warp & 3;     // TMEM lane quarter this warp may read
+        const int h = ew >> 2;      // column half
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         const uint32_t tempty0 = mapa_u32(smem_u32(tempty), 0);   // CTA 0's tempty[0]
-        const bool vec4 = epi_vec4_ok(p);
+        float* xbuf = (float*)(smem + STAGES * C::STAGE_BYTES + C::BAR_BYTES) + ew * kXposeWords;
         double dsum = 0.0;
         uint32_t g = 0;
-        PendingTile<BN> pend;   // chunked engine: finished tile parked in TMEM columns NB BN ..
         for (int t = cid; t < total_tiles; t += ncl) {
             int mt = 0, nt = 0;
             tile_of(t, &mt, &nt);
             const bool diag = sym && mt == nt;
-            const int m = mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
-            const int n0 = nt * BN;
-            int kc = 0;
-            const int nch = chunks(&kc);
-            bool ok = true;
-            auto wait_full = [&](int b) {
-                int w = 1;
-                if (lane == 0)
-                    w = mbar_wait_cl(&tfull[b], (g / NB) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
-                return __shfl_sync(0xffffffffu, w, 0) != 0;
-            };
-            auto release = [&](int b) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)b * 8u);
-            };
-            if constexpr (KCH > 0) {
-                // sum the short TMEM partial sums in registers (IEEE round-to-nearest)
-                float acc[BN];
-#pragma unroll
-                for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-                for (int c = 0; c < nch; ++c, ++g) {
-                    const int b = g % NB;
-                    if (!wait_full(b)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-#pragma unroll
-                    for (int c0 = 0; c0 < BN; c0 += 64) {
-                        uint32_t rr[64];
-                        tmem_ld64(lane_base + (uint32_t)(b * BN + c0), rr);
-#pragma unroll
-                        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(rr[j]);
-                    }
-                    release(b);
-                    // a share of the previous tile's stores, spread over this tile's chunks
-                    if (pend.p) {
-                        const int left = BN / 4 - pend.next;
-                        if (pend.drain((left + (nch - c) - 1) / (nch - c), dsum)) pend.p = nullptr;
-                    }
-                }
-                if (!ok) break;
-                if (pend.p) {
-                    pend.drain(BN / 4, dsum);
-                    pend.p = nullptr;
-                }
-                pend.park(&p, lane_base + (uint32_t)(NB * BN), m, n0, diag, acc);
-            } else {
-                (void)nch;
-                const int b = g & 1;
-                if (!wait_full(b)) break;
-                tc_fence_after();
+            const int m0 = mt * (2 * BM) + (int)rank * BM + 32 * q;
+            const int col0 = h * (BN / 2);
+            const int b = g & 1;
+            int w = 1;
+            if (lane == 0)
+                w = mbar_wait_cl(&tfull[b], (g >> 1) & 1, abort_flag, err, DEV_TIMEOUT_ACCUM);
+            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+            tc_fence_after();
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
-                    uint32_t rr[32];
-                    tmem_ld32(lane_base + (uint32_t)(b * BN + c0), rr);
-                    if (m < p.M && sym) {
-                        float local = 0.f;
-                        const int nb = n0 + c0;
-                        if (vec4 && !diag && nb + 32 <= p.N) {
+            for (int c0 = 0; c0 < BN / 2; c0 += 32) {
+                uint32_t rr[32];
+                tmem_ld32(lane_base + (uint32_t)(b * BN + col0 + c0), rr);
+                float a[32];
 #pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
-                                                    __uint_as_float(rr[j + 1]),
-                                                    __uint_as_float(rr[j + 2]),
-                                                    __uint_as_float(rr[j + 3]));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int n = nb + j;
-                                if (n < p.N)
-                                    local += epi_apply_sym(p, m, n, __uint_as_float(rr[j]), diag);
-                            }
-                        }
-                        dsum += (double)local;
-                    } else if (m < p.M) {
-                        float local = 0.f;
-                        const int nb = n0 + c0;
-                        if (vec4 && nb + 32 <= p.N) {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                local += epi_apply4(p, m, nb + j, __uint_as_float(rr[j]),
-                                                    __uint_as_float(rr[j + 1]),
-                                                    __uint_as_float(rr[j + 2]),
-                                                    __uint_as_float(rr[j + 3]));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int n = nb + j;
-                                if (n < p.N) local += epi_apply(p, m, n, __uint_as_float(rr[j]));
-                            }
-                        }
-                        dsum += (double)local;
-                    }
-                }
-                release(b);
-                ++g;
+                for (int j = 0; j < 32; ++j) a[j] = __uint_as_float(rr[j]);
+                dsum += (double)epi_block32(p, m0, nt * BN + col0 + c0, diag, a, xbuf, lane);
             }
-        }
-        if constexpr (KCH > 0) {
-            if (pend.p) pend.drain(BN / 4, dsum);
+            // the loads are complete (tcgen05.wait::ld); the plain arrive orders them before
+            // the peer's next MMA without waiting for this tile's global stores
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_remote(tempty0 + (uint32_t)b * 8u);
+            ++g;
         }
         if (p.dot) {
 #pragma unroll
@@ -515,15 +454,6 @@ constexpr int SPLIT_BN = 256;
 constexpr int SPLIT_GROUP = 8;
 constexpr int split_threads(int ew) { return 32 * (2 + ew); }
 
-// Arrive on an mbarrier given by its shared::cluster address with the default .release.cta
-// semantics. The epilogue's per-chunk "accumulator drained" signal orders only tcgen05 loads
-// (completed by tcgen05.wait::ld and tcgen05.fence::before_thread_sync) against the peer's MMA;
-// a .release.cluster arrive would also wait, every chunk, for the warp's earlier global stores
-// (the previous tile's epilogue) to become visible cluster-wide.
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
-    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
-}
-
 // 16 consecutive columns of this warp's 32 TMEM lanes, completed before return (the
 // 128 running sums and the 168-register budget of 320 threads leave room for 16 at a time)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -543,7 +473,10 @@ struct CfgS {
     static constexpr int B_BYTES = (SPLIT_BN / 2) * BK * 4;    // this CTA's 128 rows of Y
     static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;
     static constexpr int STAGE_BYTES = 2 * PAIR_BYTES;         // hi and lo
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 1024;
+    static constexpr int BAR_BYTES = 256;
+    // eight epilogue warps, each with a transpose buffer (tc_store.cuh)
+    static constexpr int XPOSE_BYTES = 8 * kXposeWords * 4;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + XPOSE_BYTES + 1024;
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -587,7 +520,7 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
                     int total_tiles, const double* skip, int* err, const GemmProblem* groups,
                     int G) {
     using C = CfgS<STAGES>;
-    static_assert(EW == 8 || EW == 16, "epilogue warps");
+    static_assert(EW == 8, "epilogue warps");
     constexpr int BN = SPLIT_BN, NB = 2, CW = 4 * BN / EW;
     constexpr int LW = CW >= 128 ? 32 : 16;   // columns per TMEM load
     constexpr uint32_t kTmemCols = NB * BN;
@@ -783,13 +716,14 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
         const int h = (warp - 2) >> 2;     // column group
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(CW * h);
         const uint32_t tempty0 = mapa_u32(smem_u32(tempty), 0);
+        float* xbuf = (float*)(smem + STAGES * C::STAGE_BYTES + C::BAR_BYTES) +
+                      (warp - 2) * kXposeWords;
         double dsum = 0.0;
         uint32_t g = 0;
         for (int t = cid; t < total_tiles; t += ncl) {
             const WideTile w = tile(t);
             if (w.skip) continue;
-            const EpiParams<float>& P = *w.p;
-            const bool vec4 = epi_vec4_ok(P);
+            const EpiParams<float>& P = *w.p;   // kernel parameter or problem descriptor
             const bool diag = w.sym && w.mt == w.nt;
             const int m = w.mt * (2 * BM) + (int)rank * BM + 32 * q + lane;
             const int n0 = w.nt * BN + CW * h;
@@ -824,27 +758,12 @@ __global__ void __launch_bounds__(split_threads(EW), 1)
                 if (lane == 0) mbar_arrive_remote(tempty0 + (uint32_t)b * 8u);
             }
             if (!ok) break;
-            if (m < P.M) {
 #pragma unroll
-                for (int c0 = 0; c0 < CW; c0 += 32) {
-                    const int nb = n0 + c0;
-                    float local = 0.f;
-                    if (vec4 && !diag && nb + 32 <= P.N) {
+            for (int c0 = 0; c0 < CW; c0 += 32) {
+                float a[32];
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            local += epi_apply4(P, m, nb + j, acc[c0 + j], acc[c0 + j + 1],
-                                                acc[c0 + j + 2], acc[c0 + j + 3]);
-                    } else if (w.sym) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (nb + j < P.N) local += epi_apply_sym(P, m, nb + j, acc[c0 + j], diag);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (nb + j < P.N) local += epi_apply(P, m, nb + j, acc[c0 + j]);
-                    }
-                    dsum += (double)local;
-                }
+                for (int j = 0; j < 32; ++j) a[j] = acc[c0 + j];
+                dsum += (double)epi_block32(P, m - lane, n0 + c0, diag, a, xbuf, lane);
             }
             if constexpr (GROUPED) {
                 // each problem has its own dot target: flush per tile
@@ -971,17 +890,6 @@ cdmpt_status launch_2sm(int M, int N, int K, const void* X, const void* Xl, int 
 }
 
 
-// Epilogue warps of the wide split kernel: eight by default (128 columns each, 32-column
-// TMEM loads; measured 344 against 328 TF/s for sixteen at N = 8192 with one-k-block chunks,
-// 279 against 274 at N = 4096); CDMPT_SPLIT_EPI=16 selects sixteen for tuning.
-int split_epilogue_warps() {
-    static int v = 0;
-    if (v == 0) {
-        const char* e = getenv("CDMPT_SPLIT_EPI");
-        v = (e && atoi(e) == 16) ? 16 : 8;
-    }
-    return v;
-}
 
 // Resident clusters of two of an instantiation of the wide kernel (0 with the error set when
 // none fits), queried once per instantiation.
@@ -1091,14 +999,6 @@ cdmpt_status gemm_tc_2sm(bool three, int kch, int M, int N, int K, const float* 
                          const float* Xl, int ldx, const float* Y, const float* Yl, int ldy,
                          const EpiParams<float>& p, const double* skip, cudaStream_t s) {
     if (!three) return launch_2sm<256, 6, 1, 0>(M, N, K, X, X, ldx, Y, Y, ldy, p, skip, s);
-    if (split_epilogue_warps() == 16) {
-        switch (kch) {
-            case 0: return launch_split2sm<3, 0, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-            case 2: return launch_split2sm<3, 2, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-            case 4: return launch_split2sm<3, 4, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-            default: return launch_split2sm<3, 1, 16>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
-        }
-    }
     switch (kch) {
         case 0: return launch_split2sm<3, 0, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);
         case 2: return launch_split2sm<3, 2, 8>(M, N, K, X, Xl, ldx, Y, Yl, ldy, p, skip, s);

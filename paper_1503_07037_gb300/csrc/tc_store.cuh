@@ -47,16 +47,23 @@ template <bool SYM, bool SPLIT>
 __device__ __forceinline__ float epi_block32_plain(const EpiParams<float>& p, int m0, int n,
                                                    bool diag, float* S, int lane) {
     constexpr int RB = 8;   // rows whose loads are issued together
+    // every field the loops use, read once (p may live in global memory, where the
+    // stores below could alias it)
+    const int M = p.M, N = p.N;
+    const size_t ldd = (size_t)p.ldd, ldc = (size_t)p.ldc, lde = (size_t)p.lde;
+    float* const D = p.D;
+    float* const Dhi = p.Dhi;
+    float* const Dlo = p.Dlo;
     const int c = n + lane;
-    const bool col_ok = c < p.N;
+    const bool col_ok = c < N;
     const float alpha = p.alpha, beta = p.beta, gamma = p.gamma;
     const bool has_c = beta != 0.f, has_g = gamma != 0.f, has_dot = p.dot != nullptr;
     const bool has_e = has_dot && p.E != nullptr;
     const int db = p.diag_block;
     int mm = has_g ? m0 % db : -1;   // (m0 + r) % diag_block, advanced row by row
-    const size_t o0 = (size_t)m0 * p.ldd + c;
-    const float* Cp = has_c ? p.C + (size_t)m0 * p.ldc + c : nullptr;
-    const float* Ep = has_e ? p.E + (size_t)m0 * p.lde + c : nullptr;
+    const size_t o0 = (size_t)m0 * ldd + c;
+    const float* Cp = has_c ? p.C + (size_t)m0 * ldc + c : nullptr;
+    const float* Ep = has_e ? p.E + (size_t)m0 * lde + c : nullptr;
     float local = 0.f;
 #pragma unroll 1
     for (int r0 = 0; r0 < 32; r0 += RB) {
@@ -64,27 +71,27 @@ __device__ __forceinline__ float epi_block32_plain(const EpiParams<float>& p, in
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int m = m0 + r0 + i;
-            const bool ok = col_ok && m < p.M && !(diag && c < m);
-            cv[i] = (ok && has_c) ? Cp[(size_t)(r0 + i) * p.ldc] : 0.f;
-            ev[i] = (ok && has_e) ? Ep[(size_t)(r0 + i) * p.lde] : 0.f;
+            const bool ok = col_ok && m < M && !(diag && c < m);
+            cv[i] = (ok && has_c) ? Cp[(size_t)(r0 + i) * ldc] : 0.f;
+            ev[i] = (ok && has_e) ? Ep[(size_t)(r0 + i) * lde] : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int m = m0 + r0 + i;
-            const bool ok = col_ok && m < p.M && !(diag && c < m);
+            const bool ok = col_ok && m < M && !(diag && c < m);
             float v = alpha * S[(r0 + i) * 33 + lane];
             v = has_c ? fmaf(beta, cv[i], v) : v;
             v = (has_g && mm == c) ? v + gamma : v;
             mm = (mm + 1 == db) ? 0 : mm + 1;
             if constexpr (SYM) S[(r0 + i) * 33 + lane] = v;
-            const size_t o = o0 + (size_t)(r0 + i) * p.ldd;
-            if (ok) p.D[o] = v;
+            const size_t o = o0 + (size_t)(r0 + i) * ldd;
+            if (ok) D[o] = v;
             if constexpr (SPLIT) {
                 float h, l;
                 split_tf32(v, h, l);
                 if (ok) {
-                    p.Dhi[o] = h;
-                    p.Dlo[o] = l;
+                    Dhi[o] = h;
+                    Dlo[o] = l;
                 }
             }
             const float d = v * (has_e ? ev[i] : v);
@@ -96,21 +103,21 @@ __device__ __forceinline__ float epi_block32_plain(const EpiParams<float>& p, in
         // the mirrored block: lane l on row m0 + l again, column n + j goes to row n + j
         __syncwarp();
         const int m = m0 + lane;
-        const bool row_ok = m < p.M;
-        const size_t q0 = (size_t)n * p.ldd + m;
+        const bool row_ok = m < M;
+        const size_t q0 = (size_t)n * ldd + m;
 #pragma unroll 8
         for (int j = 0; j < 32; ++j) {
             const int cj = n + j;
-            const bool ok = row_ok && cj < p.N && cj != m && !(diag && cj < m);
+            const bool ok = row_ok && cj < N && cj != m && !(diag && cj < m);
             const float w = S[lane * 33 + j];
-            const size_t o = q0 + (size_t)j * p.ldd;
-            if (ok) p.D[o] = w;
+            const size_t o = q0 + (size_t)j * ldd;
+            if (ok) D[o] = w;
             if constexpr (SPLIT) {
                 float h, l;
                 split_tf32(w, h, l);
                 if (ok) {
-                    p.Dhi[o] = h;
-                    p.Dlo[o] = l;
+                    Dhi[o] = h;
+                    Dlo[o] = l;
                 }
             }
         }

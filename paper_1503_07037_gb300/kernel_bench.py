@@ -37,6 +37,9 @@ def main():
     ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64", "f64tc", "oz"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--epi", default="plain", choices=["plain", "cdot"],
+                    help="epilogue of the tf32/3xtf32 products: D = X Y^T + I (plain), or "
+                         "D = X Y^T + C with the dot sum(D * E) (cdot, as in the CG updates)")
     ap.add_argument("--check", action="store_true",
                     help="also report the error against an FP64 product (cuBLAS DGEMM), on the "
                          "signed input and on its absolute value (all-positive sums show the "
@@ -54,6 +57,7 @@ def main():
         Dl = torch.empty_like(Z)
     if a.engine in ("tf32", "3xtf32"):
         Zs = pkg.split_tf32(Z)      # split once, outside the timed launches
+        dsum = torch.zeros(1, device=dev, dtype=torch.float64)
 
     def run():
         if a.engine in ("f64", "f64tc"):
@@ -63,6 +67,8 @@ def main():
         elif a.engine in ("simt", "bf16"):
             # bf16: includes rounding the operand to BF16 (one pass, X is Y)
             pkg.gemm_f32(Z, Z, D, gamma=1.0, engine=a.engine)
+        elif a.epi == "cdot":
+            pkg.gemm_f32_split(Zs, Zs, D, beta=1.0, C=Z, dot=dsum, E=Z, engine=a.engine)
         else:
             pkg.gemm_f32_split(Zs, Zs, D, gamma=1.0, engine=a.engine)
 
@@ -80,6 +86,8 @@ def main():
     t = e0.elapsed_time(e1) / a.reps / 1e3
     out = {"kernel": "gemm", "engine": a.engine, "n": a.n, "ms": t * 1e3,
            "alg_tflops": 2.0 * a.n ** 3 / t / 1e12}
+    if a.engine in ("tf32", "3xtf32"):
+        out["epi"] = a.epi
     if a.engine in ("oz", "f64tc"):
         # BF16 digit pairs: p + q <= 4 of 5 digits (pairs), p + q <= 6 of 7 digits (FP64)
         out["digit_products"] = 15 if a.engine == "oz" else 28
