@@ -51,7 +51,7 @@ PIPE_FACTOR = {2: 1.0, 3: 3.0, 4: 1.0, 5: 15.0}
 # DRAM bytes (read + write) of one launch and its algorithmic flops, from the ncu captures
 # summarised in profiles/ (engine 3: k_gemm_split2sm, D = Z Z^T + I at N = 8192); the roofline
 # scales it to the mean launch of the step by algorithmic flops
-TRAFFIC = {3: (4328539392 + 274094592, 2.0 * 8192.0 ** 3)}
+TRAFFIC = {3: (3849249024 + 271198464, 2.0 * 8192.0 ** 3)}
 
 
 def dist_env():

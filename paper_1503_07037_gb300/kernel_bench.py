@@ -14,6 +14,13 @@ as every call of the solver's FP64-class residual does. "f64tc" is the FP64
 product on the tensor cores (seven BF16 digits per element), slicing
 included; "f64" the CUDA-core DFMA product. --check adds the error against a
 cuBLAS FP64 product, on the signed input and on its absolute value.
+
+  python -m paper_1503_07037_gb300.kernel_bench --batch 16 [--precision fp32]
+
+instead solves one lockstep batch of the first B clusters of the batched workload (N_b drawn
+from {128..1536}, seed 1005, D = 3) and prints the tile autotuner's per-launch times of its
+first grouped product (W = Z^2 over all systems) for each tile width, with the solve's time:
+the grouped tcgen05 products at a size a profiler capture can hold.
 """
 from __future__ import annotations
 
@@ -27,6 +34,26 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def run_batch(pkg, a):
+    import torch
+
+    import synthetic
+    probs = synthetic.clusters(B=a.batch, seed=1005, beta=20.0, n=12)
+    b = pkg.Batch([p.N for p in probs], 3, precision=a.precision)
+    b.set_H([p.H0 for p in probs], [p.H1 for p in probs], 12)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.solve([p.beta for p in probs], [p.nocc for p in probs], 12)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"kernel": "grouped", "clusters": a.batch, "precision": a.precision,
+           "sum_N3": float(sum(float(p.N) ** 3 for p in probs)),
+           "solve_ms_first": e0.elapsed_time(e1), "tuning": b.tuning()}
+    b.close()
+    print(json.dumps(out))
+
+
 def main():
     import torch
 
@@ -37,6 +64,10 @@ def main():
     ap.add_argument("--engine", default="tf32", choices=["simt", "tf32", "3xtf32", "bf16", "f64", "f64tc", "oz"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="solve a lockstep batch of this many clusters instead (see above)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="precision of the --batch solve")
     ap.add_argument("--epi", default="plain", choices=["plain", "cdot"],
                     help="epilogue of the tf32/3xtf32 products: D = X Y^T + I (plain), or "
                          "D = X Y^T + C with the dot sum(D * E) (cdot, as in the CG updates)")
@@ -45,6 +76,8 @@ def main():
                          "signed input and on its absolute value (all-positive sums show the "
                          "bias of a truncating accumulation)")
     a = ap.parse_args()
+    if a.batch > 0:
+        return run_batch(pkg, a)
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(1234)
     dt = torch.float64 if a.engine in ("f64", "f64tc") else torch.float32
