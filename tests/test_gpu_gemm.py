@@ -46,14 +46,17 @@ def test_gemm_f32_plain(cuda, cdmpt_lib, engine, M, N, K):
 
 
 @pytest.mark.parametrize("engine", ["simt", "3xtf32", "tf32"])
-def test_gemm_f32_epilogue(cuda, cdmpt_lib, engine):
-    """alpha, beta C, gamma on block diagonals, transposed block placement and the fused dot."""
+@pytest.mark.parametrize("Nb", [160, 150])
+def test_gemm_f32_epilogue(cuda, cdmpt_lib, engine, Nb):
+    """alpha, beta C, gamma on block diagonals, transposed block placement and the fused dot.
+    Nb = 150: the diagonal blocks start inside the epilogue's 32-row store blocks."""
     import torch
     rng = np.random.default_rng(5)
-    Nb, blocks = 160, 2
+    blocks = 2
     M, N, K = Nb * blocks, Nb, Nb
-    X = _mat(rng, M, K)
-    Y = _mat(rng, N, K)
+    ldk = (K + 3) // 4 * 4      # operand rows 16-byte aligned (zero padding adds nothing)
+    X = _mat(rng, M, K, ld=ldk)
+    Y = _mat(rng, N, K, ld=ldk)
     C = _mat(rng, M, N)
     E = _mat(rng, M, N)
     alpha, beta, gamma = -1.25, 2.0, 0.75

@@ -45,8 +45,9 @@ def _solve(pkg, p, precision, tau):
 def test_screening_is_exact_on_decoupled_chains(cuda, cdmpt_lib, precision, sizes):
     """Block-diagonal chains: every screened term is an exact zero. The second block layout is
     not aligned to the 128 x 128 tiles and N = 510 is not a multiple of 4: the tiles screened to
-    nothing then include partial edge tiles, whose epilogue takes the scalar tail, next to full
-    ones (and the transposed placement of the response's right-hand side).
+    nothing then include partial edge tiles, whose epilogue masks the elements outside the
+    matrix, next to full ones (and the transposed placement of the response's right-hand
+    side).
 
     The screened products run on the one-SM 128 x 128 kernels (the mask's granularity), the
     dense ones with more than 128 rows on the two-SM 256 x 256 kernels. Both form every product
