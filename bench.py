@@ -703,6 +703,8 @@ def run_batched(pkg, args, barrier, max_over_ranks=lambda x: x, rank=0, world=1)
         out[prec] = {"solves_per_s": 96 / (ms / 1e3), "ms": ms, "mu_sweeps": st["mu_iterations"],
                      "cg_sweeps": st["cg_iterations_sweeps"],
                      "cg_refine": st["cg_iterations_refine"],
+                     "refine_passes": st["refine_passes"],
+                     "fp64_residual_passes": st["fp64_residual_passes"],
                      "kernel_launches": st["kernel_launches"],
                      "phase_ms": dict(zip(("sweeps", "refine", "response", "q_mu1_alpha",
                                            "output"), st["phase_ms"])),

@@ -46,6 +46,21 @@ namespace {
 constexpr int kEngine = CDMPT_GEMM_TC_3XTF32;
 constexpr int kSlots = 64;
 
+// When a system of a mixed-precision batch switches from split-TF32 refinement passes to
+// passes with FP64-class late-step residuals: at once after its first split pass (negative,
+// the default), or once its occupation error after a split pass is within this value times
+// sqrt(N) (CDMPT_BATCH_HP_SWITCH), so that the Newton steps on mu it still needs run on the
+// cheaper split passes.
+double batch_hp_switch() {
+    static double v = -2.0;
+    if (v < -1.5) {
+        const char* e = getenv("CDMPT_BATCH_HP_SWITCH");
+        v = e ? atof(e) : -1.0;
+        if (!(v > 0)) v = -1.0;
+    }
+    return v;
+}
+
 struct Mat {   // FP32 matrix stack with TF32 split
     float* x = nullptr;
     float* hi = nullptr;
@@ -66,6 +81,11 @@ struct Sys {
     double beta = 0, nocc = 0, s2 = 0, mu = 0, lo = 0, hi = 0;
     double e_lo = 0, e_hi = 0;   // occupation errors at lo and hi once a sweep set them
     bool converged = false;
+    // mixed refinement: first step of the FP64-class residuals (n: none), whether this
+    // system's passes form them yet, and how many such passes it has had
+    int khp = 0;
+    bool hp = false;
+    int hp_passes = 0;
 };
 
 enum BSlot { B_TRZ = 8, B_ZZ = 9, B_TRQ = 10, B_TRZ1 = 16, B_ALPHA = 32 };
@@ -117,6 +137,7 @@ struct cdmpt_batch {
     cudaStream_t hp_st[kHpLanes] = {};
     cudaEvent_t hp_fork = nullptr;
     cudaEvent_t hp_join[kHpLanes] = {};
+    int hp_lanes = 0;   // lanes forked by the last residual_batch_hp, not yet joined
 };
 
 namespace {
@@ -801,10 +822,24 @@ cdmpt_status sweep_batch(cdmpt_batch* b, int n, int* iters_out, int engine, doub
     return CDMPT_OK;
 }
 
+// The batch's stream continues after the lanes forked by residual_batch_hp.
+cdmpt_status hp_join_lanes(cdmpt_batch* b) {
+    cudaStream_t s = b->cx.stream;
+    for (int l = 0; l < b->hp_lanes; ++l) {
+        CDMPT_CUDA_TRY(cudaEventRecord(b->hp_join[l], b->hp_st[l]));
+        CDMPT_CUDA_TRY(cudaStreamWaitEvent(s, b->hp_join[l], 0));
+    }
+    b->hp_lanes = 0;
+    return CDMPT_OK;
+}
+
 // W_k and the residual 2 Z_k - Z_{k+1} - Z_{k+1} W_k of step k from Ozaki-sliced products of
 // the pair-stored trajectory, for every active system one after another (they share the
 // digit buffers); W_k's FP32 part and split replace the stored W_k, the residual goes to RHS.
-cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& active) {
+// The work goes to side lanes forked from the batch's stream; join: the batch's stream waits
+// for them before returning (else hp_join_lanes does, after more work on the batch's stream).
+cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& active,
+                               bool join = true) {
     cudaStream_t s = b->cx.stream;
     int nact = 0;
     for (int i = 0; i < b->B; ++i) nact += active[i] ? 1 : 0;
@@ -859,22 +894,19 @@ cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& a
             b->cx.st->tensor_flops += 2.0 * oz_products(kOzDigits) * f;
         }
     }
-    // and the batch's stream continues after all lanes
-    for (int l = 0; l < L; ++l) {
-        CDMPT_CUDA_TRY(cudaEventRecord(b->hp_join[l], b->hp_st[l]));
-        CDMPT_CUDA_TRY(cudaStreamWaitEvent(s, b->hp_join[l], 0));
-    }
-    return CDMPT_OK;
+    b->hp_lanes = L;
+    return join ? hp_join_lanes(b) : CDMPT_OK;
 }
 
 // One refinement pass of the stored trajectories (mixed precision), for the systems whose
 // inactive flag is 0 (active[i] on the host): per step, W_k = Z_k Z_k and the residual
 // 2 Z_k - Z_{k+1} - Z_{k+1} W_k, then the correction d (I + W_k) = residual by CG with
 // one-pass TF32 products (relative residual 1e-3), Z_{k+1} += d added to the pair,
-// symmetrised. Steps k < k_hp form W_k and the residual with grouped split-TF32 products
+// symmetrised. A system's steps form W_k and the residual with grouped split-TF32 products
 // (full tiles for the residual: the stored Z_{k+1} does not commute with W_k to first order
-// in its error); steps k >= k_hp with Ozaki-sliced products.
-cdmpt_status refine_batch(cdmpt_batch* b, int n, int k_hp, const std::vector<char>& active,
+// in its error), except, once the system is in its FP64-class passes (Sys::hp), the steps
+// k >= Sys::khp, which use Ozaki-sliced products.
+cdmpt_status refine_batch(cdmpt_batch* b, int n, const std::vector<char>& active,
                           int* iters_out) {
     const int G = b->B;
     std::vector<const double*> skip(G);
@@ -884,6 +916,15 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int k_hp, const std::vector<cha
         std::vector<GemmSpec> gw, gr;
         std::vector<BCg> cg(G);
         std::vector<GrpEw> ds, dz, dsym;
+        std::vector<char> act_hp(G, 0), act_split(G, 0);
+        bool any_hp = false, any_split = false;
+        for (int i = 0; i < G; ++i) {
+            const bool hp = b->sys[i].hp && k >= b->sys[i].khp;
+            act_hp[i] = active[i] && hp;
+            act_split[i] = active[i] && !hp;
+            any_hp = any_hp || act_hp[i];
+            any_split = any_split || act_split[i];
+        }
         for (int i = 0; i < G; ++i) {
             Sys& sy = b->sys[i];
             cg[i] = BCg{sy.A1.x, nullptr, sy.RHS.x, &sy.W[k], sy.N};
@@ -895,7 +936,7 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int k_hp, const std::vector<cha
             y.rows = sy.N; y.ld = sy.ld; y.N = sy.N;
             y.skip = skip[i];
             dsym.push_back(y);
-            if (k >= k_hp) continue;
+            if (!act_split[i]) continue;
             GemmSpec w;                  // W_k = Z_k Z_k, split-TF32
             w.X = &sy.Z[k];
             w.rows = sy.N;
@@ -922,18 +963,20 @@ cdmpt_status refine_batch(cdmpt_batch* b, int n, int k_hp, const std::vector<cha
             r.skip = skip[i];
             gr.push_back(r);
         }
-        if (k >= k_hp) {
-            CDMPT_TRY(residual_batch_hp(b, k, active));
-        } else {
+        // the FP64-class residuals run on side lanes while the split products of the other
+        // systems run on the batch's stream
+        if (any_hp) CDMPT_TRY(residual_batch_hp(b, k, act_hp, false));
+        if (any_split) {
             CDMPT_TRY(grouped_gemm(b, gw));
             CDMPT_TRY(run_ew(b, G_PAIR_LINCOMB, ds));
             CDMPT_TRY(grouped_gemm(b, gr));
             for (int i = 0; i < G; ++i) {
-                if (!active[i]) continue;
+                if (!act_split[i]) continue;
                 const double nn = b->sys[i].N;
                 add_flops(b, sym_flops(b, b->sys[i].N) + 2.0 * nn * nn * nn);
             }
         }
+        CDMPT_TRY(hp_join_lanes(b));
         int it = 0;
         CDMPT_TRY(cg_batch(b, cg, 1.0, 1.0, 1e-3, skip, 2, &it, false, CDMPT_GEMM_TC_TF32));
         total += it;
@@ -1244,49 +1287,56 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
     if (mixed) {
         const int min_pass = std::max(1, b->opts.refine_rounds);
         for (int i = 0; i < G; ++i) b->sys[i].converged = false;
-        // first step of the FP64-class pass (the earliest over the systems): every step, or
-        // the steps whose spectral bound tanh(2^k atanh rho) exceeds 1/2
-        int k_hp = n;
-        if (b->opts.fp64_residual >= 0) {
-            k_hp = 0;
-            if (b->opts.fp64_residual == 0) {
-                k_hp = n;
-                for (int i = 0; i < G; ++i) {
-                    const Sys& sy = b->sys[i];
-                    const double a0 = std::atanh(
-                        std::min(sy.s2 * std::max(sy.gmax - sy.mu, sy.mu - sy.gmin), 0.999999));
-                    int k = 0;
-                    while (k < n && std::tanh(std::ldexp(a0, k)) <= hp_bound()) ++k;
-                    k_hp = std::min(k_hp, k);
-                }
+        // first step of each system's FP64-class residuals: every step, or the steps whose
+        // spectral bound tanh(2^k atanh rho) exceeds hp_bound(), or none
+        int k_first = n;
+        for (int i = 0; i < G; ++i) {
+            Sys& sy = b->sys[i];
+            sy.hp = false;
+            sy.hp_passes = 0;
+            sy.khp = n;
+            if (b->opts.fp64_residual > 0) {
+                sy.khp = 0;
+            } else if (b->opts.fp64_residual == 0) {
+                const double a0 = std::atanh(
+                    std::min(sy.s2 * std::max(sy.gmax - sy.mu, sy.mu - sy.gmin), 0.999999));
+                int k = 0;
+                while (k < n && std::tanh(std::ldexp(a0, k)) <= hp_bound()) ++k;
+                sy.khp = k;
             }
+            k_first = std::min(k_first, sy.khp);
         }
-        b->st.fp64_residual_first_step = k_hp;
-        // Split-TF32 passes until every system has settled (its occupation within tolerance
-        // after a pass that did not follow a Newton step on mu); from then on every pass,
-        // including the Newton steps that follow, forms the residuals of steps k >= k_hp with
-        // Ozaki-sliced products, so that no occupation is measured on a trajectory carrying
+        b->st.fp64_residual_first_step = k_first;
+        const double hp_occ = batch_hp_switch();
+        // Each system runs split-TF32 passes until it switches to passes whose late-step
+        // residuals are FP64-class (by default after its first split pass; with a switch
+        // threshold, once its occupation error after a split pass is within the threshold,
+        // so that the Newton steps on mu it still needs run on the cheaper split passes). It
+        // finishes only in an FP64-class pass (or, without any, in a split pass that did not
+        // follow a Newton step), so that no occupation is accepted on a trajectory carrying
         // the split products' bias.
         std::vector<char> shifted(G, 1);
-        bool all = false, hp_phase = false;
-        int hp_passes = 0;
+        bool all = false;
         for (int pass = 0; pass < min_pass + 12 && !all; ++pass) {
             std::vector<char> active(G, 0);
+            bool any_hp = false;
             for (int i = 0; i < G; ++i) {
                 active[i] = b->sys[i].converged ? 0 : 1;
                 inact[i] = active[i] ? 0.0 : 1.0;
+                any_hp = any_hp || (active[i] && b->sys[i].hp && b->sys[i].khp < n);
             }
             CDMPT_CUDA_TRY(cudaMemcpyAsync(b->inactive, inact.data(), G * sizeof(double),
                                            cudaMemcpyHostToDevice, st));
             int iters = 0;
-            cdmpt_status s = refine_batch(b, n, hp_phase ? k_hp : n, active, &iters);
+            cdmpt_status s = refine_batch(b, n, active, &iters);
             if (s != CDMPT_OK) return bfail(b, s);
             b->st.cg_iterations_refine += iters;
             b->st.refine_passes += 1;
-            if (hp_phase) b->st.fp64_residual_passes += 1;
+            if (any_hp) b->st.fp64_residual_passes += 1;
             s = occupations(b, n);
             if (s != CDMPT_OK) return bfail(b, s);
             all = true;
+            bool stuck = false;
             std::vector<char> reinit(G, 0);
             for (int i = 0; i < G; ++i) {
                 Sys& sy = b->sys[i];
@@ -1301,12 +1351,21 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                                                                    ? 1e-7 * std::sqrt((double)sy.N)
                                                                    : 0.0);
                 const bool occ_ok = std::fabs(err) <= tol;
-                if (occ_ok && pass + 1 >= min_pass && (hp_phase || !shifted[i])) {
+                const bool final_phase = sy.hp || sy.khp >= n;
+                if (final_phase && occ_ok && pass + 1 >= min_pass && (sy.hp || !shifted[i])) {
                     sy.converged = true;
                     continue;
                 }
                 all = false;
                 shifted[i] = 0;
+                if (sy.hp) {
+                    if (++sy.hp_passes >= 4) stuck = true;
+                } else if (sy.khp < n) {
+                    // switch to the FP64-class passes: at once (hp_occ < 0), or once the
+                    // occupation is within the threshold
+                    if (hp_occ < 0 || std::fabs(err) <= std::max(tol, hp_occ * std::sqrt((double)sy.N)))
+                        sy.hp = true;
+                }
                 if (!occ_ok) {   // Newton step on mu; Z_0 = -s2 (H0 - mu I) is rebuilt
                     const double slope = 0.25 * sy.beta * (sy.N - zz);
                     if (slope > 0) sy.mu -= err / slope;
@@ -1320,17 +1379,7 @@ cdmpt_status cdmpt_batch_solve(cdmpt_batch* b, const double* beta, const double*
                 std::vector<const double*> none_skip(G, nullptr);
                 CDMPT_TRY(init_z0_batch(b, none_skip, &reinit));
             }
-            if (!hp_phase && k_hp < n && (all || refine_early_hp())) {
-                // every system settled on split-TF32 residuals (or, by default, the first
-                // split pass is done: it took the sweeps' residuals from about 1e-4 to 1e-7):
-                // reopen all of them for the passes with FP64-class residuals on the late
-                // steps; the Newton steps just taken precede the first of them
-                hp_phase = true;
-                all = false;
-                for (int i = 0; i < G; ++i) b->sys[i].converged = false;
-            } else if (hp_phase && !all && ++hp_passes >= 4) {
-                break;
-            }
+            if (stuck) break;
         }
         if (!all)
             return bfail_msg(b, CDMPT_ERR_NO_CONVERGENCE,
