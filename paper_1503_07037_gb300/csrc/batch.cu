@@ -47,15 +47,16 @@ constexpr int kEngine = CDMPT_GEMM_TC_3XTF32;
 constexpr int kSlots = 64;
 
 // When a system of a mixed-precision batch switches from split-TF32 refinement passes to
-// passes with FP64-class late-step residuals: at once after its first split pass (negative,
-// the default), or once its occupation error after a split pass is within this value times
-// sqrt(N) (CDMPT_BATCH_HP_SWITCH), so that the Newton steps on mu it still needs run on the
-// cheaper split passes.
+// passes with FP64-class late-step residuals: once its occupation error after a split pass
+// is within this value times sqrt(N), so that the Newton steps on mu it still needs run on
+// the cheaper split passes (default 1e-4; CDMPT_BATCH_HP_SWITCH overrides it, and a value of
+// 0 or below switches every system right after its first split pass). On the 96-cluster
+// workload, 1e-4 against switching at once: refinement 486 against 507 ms per batch.
 double batch_hp_switch() {
     static double v = -2.0;
     if (v < -1.5) {
         const char* e = getenv("CDMPT_BATCH_HP_SWITCH");
-        v = e ? atof(e) : -1.0;
+        v = e ? atof(e) : 1e-4;
         if (!(v > 0)) v = -1.0;
     }
     return v;
@@ -129,9 +130,12 @@ struct cdmpt_batch {
     bool have_H = false;
     // mixed precision: Ozaki digits of three operands (sized for the largest system) and the
     // low part of an Ozaki-formed W_k, one set per lane; the systems' FP64-class residuals run
-    // on kHpLanes side streams, system i on lane i % kHpLanes, so the small products of
-    // different systems share the GPU (lane 0's set also serves the dP0/dmu right side)
-    static constexpr int kHpLanes = 4;
+    // on hp_nlanes side streams (at most kHpLanes; CDMPT_BATCH_HP_LANES, default 8: on the
+    // 96-cluster workload the refinement took 617, 531 and 507 ms with 2, 4 and 8 lanes),
+    // system i on lane i % hp_nlanes, so the small products of different systems share the
+    // GPU (lane 0's set also serves the dP0/dmu right side)
+    static constexpr int kHpLanes = 8;
+    int hp_nlanes = 4;
     OzOperand oz[kHpLanes][3];
     float* oz_wl[kHpLanes] = {};
     cudaStream_t hp_st[kHpLanes] = {};
@@ -844,7 +848,7 @@ cdmpt_status residual_batch_hp(cdmpt_batch* b, int k, const std::vector<char>& a
     int nact = 0;
     for (int i = 0; i < b->B; ++i) nact += active[i] ? 1 : 0;
     if (nact == 0) return CDMPT_OK;
-    const int L = std::min(nact, (int)cdmpt_batch::kHpLanes);
+    const int L = std::min(nact, b->hp_nlanes);
     if (!b->hp_fork) {
         CDMPT_CUDA_TRY(cudaEventCreateWithFlags(&b->hp_fork, cudaEventDisableTiming));
         for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
@@ -1062,7 +1066,9 @@ cdmpt_status alloc_batch(cdmpt_batch* b, int n) {
             mblk = std::max(mblk, sy.blk);
             mN = std::max(mN, sy.N);
         }
-        for (int l = 0; l < cdmpt_batch::kHpLanes; ++l) {
+        const char* env = getenv("CDMPT_BATCH_HP_LANES");
+        b->hp_nlanes = env ? std::min(std::max(atoi(env), 1), (int)cdmpt_batch::kHpLanes) : 8;
+        for (int l = 0; l < b->hp_nlanes; ++l) {
             CDMPT_TRY(grab(b, mblk * sizeof(float), (void**)&b->oz_wl[l]));
             for (auto& o : b->oz[l]) {
                 for (int d = 0; d < kOzDigits; ++d) CDMPT_TRY(grab(b, mblk * 2, &o.s[d]));
