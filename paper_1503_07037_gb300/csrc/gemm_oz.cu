@@ -477,6 +477,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tmem_wait_st();
             const bool row_ok = m < p.M;
             const int ex = row_ok ? p.ex[m] : 0;
+            // every field the loop uses, read once: the stores below may alias p's memory
+            // for all the compiler knows, which would make it reload them after each store
+            const int PN = p.N, ldc = p.ldc, ldd = p.ldd;
+            const bool sym = p.sym != 0;
+            const float alpha = p.alpha, b1 = p.b1, b2 = p.b2, gamma = p.gamma;
+            const float* c1h = p.c1h;
+            const float* c1l = p.c1l;
+            const float* c2h = p.c2h;
+            const float* c2l = p.c2l;
+            const int* ey = p.ey;
+            float* const Dp = p.D;
+            float* const Dlp = p.Dl;
+            float* const Dth = p.Dthi;
+            float* const Dtl = p.Dtlo;
 #pragma unroll 1
             for (int c0 = 0; c0 < CW; c0 += 8) {
                 uint32_t r[ND][8];
@@ -484,12 +498,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 for (int g = 0; g < ND; ++g) ld8(lane_base + (uint32_t)(g * BN + c0), r[g]);
                 tmem_ld_wait();
                 if (row_ok) {
-                    const size_t rowc = (size_t)m * p.ldc, rowd = (size_t)m * p.ldd;
+                    const size_t rowc = (size_t)m * ldc, rowd = (size_t)m * ldd;
+                    // the chunk's loads first (column exponents and C terms), then its
+                    // arithmetic and stores: one memory latency per chunk, not per element
+                    int eyv[8];
+                    float ch1[8], cl1[8], ch2[8], cl2[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int n = n0 + c0 + j;
+                        const bool ok = n < PN && !(sym && n < m);
+                        eyv[j] = ok ? ey[n] : 0;
+                        ch1[j] = (ok && c1h) ? c1h[rowc + n] : 0.f;
+                        cl1[j] = (ok && c1l) ? c1l[rowc + n] : 0.f;
+                        ch2[j] = (ok && c2h) ? c2h[rowc + n] : 0.f;
+                        cl2[j] = (ok && c2l) ? c2l[rowc + n] : 0.f;
+                    }
                     float local = 0.f;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int n = n0 + c0 + j;
-                        if (n < p.N && !(p.sym && n < m)) {
+                        if (n < PN && !(sym && n < m)) {
                             // exact integer part of the exact groups, then the float tail of the
                             // whole-K groups, in units of the last exact group's weight
                             long long I = 0;
@@ -499,42 +527,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             float vl = (float)(I - (long long)vh);
                             vl = __fadd_rn(vl, __fadd_rn(__uint_as_float(r[NX][j]) * (1.f / 256.f),
                                                          __uint_as_float(r[NX + 1][j]) * (1.f / 65536.f)));
-                            const int sh = ex + p.ey[n] - 14 - 8 * (NX - 1);
+                            const int sh = ex + eyv[j] - 14 - 8 * (NX - 1);
                             vh = scale2(vh, sh);
                             vl = scale2(vl, sh);
                             // D = alpha X Y^T + b1 C1 + b2 C2 + gamma I in double-float
-                            float dh = __fmul_rn(p.alpha, vh), dl = __fmul_rn(p.alpha, vl);
-                            if (p.c1h) {
-                                const float ch = __fmul_rn(p.b1, p.c1h[rowc + n]);
-                                const float cl = p.c1l ? __fmul_rn(p.b1, p.c1l[rowc + n]) : 0.f;
+                            float dh = __fmul_rn(alpha, vh), dl = __fmul_rn(alpha, vl);
+                            if (c1h) {
+                                const float ch = __fmul_rn(b1, ch1[j]);
+                                const float cl = c1l ? __fmul_rn(b1, cl1[j]) : 0.f;
                                 dd::add(dh, dl, ch, cl, dh, dl);
                             }
-                            if (p.c2h) {
-                                const float ch = __fmul_rn(p.b2, p.c2h[rowc + n]);
-                                const float cl = p.c2l ? __fmul_rn(p.b2, p.c2l[rowc + n]) : 0.f;
+                            if (c2h) {
+                                const float ch = __fmul_rn(b2, ch2[j]);
+                                const float cl = c2l ? __fmul_rn(b2, cl2[j]) : 0.f;
                                 dd::add(dh, dl, ch, cl, dh, dl);
                             }
-                            if (p.gamma != 0.f && n == m) dd::add1(dh, dl, p.gamma, dh, dl);
+                            if (gamma != 0.f && n == m) dd::add1(dh, dl, gamma, dh, dl);
                             float o, ol;
                             dd::fast_two_sum(dh, dl, o, ol);
                             // symmetric result: the mirror (n, m) too (the lanes hold
                             // consecutive rows m, so these stores coalesce)
-                            const bool mir = p.sym && n > m;
-                            const size_t mirror = (size_t)n * p.ldd + m;
-                            p.D[rowd + n] = o;
-                            if (mir) p.D[mirror] = o;
-                            if (p.Dl) {
-                                p.Dl[rowd + n] = ol;
-                                if (mir) p.Dl[mirror] = ol;
+                            const bool mir = sym && n > m;
+                            const size_t mirror = (size_t)n * ldd + m;
+                            Dp[rowd + n] = o;
+                            if (mir) Dp[mirror] = o;
+                            if (Dlp) {
+                                Dlp[rowd + n] = ol;
+                                if (mir) Dlp[mirror] = ol;
                             }
-                            if (p.Dthi) {
+                            if (Dth) {
                                 float th, tl;
                                 dd::tf32_split(o, th, tl);
-                                p.Dthi[rowd + n] = th;
-                                if (mir) p.Dthi[mirror] = th;
-                                if (p.Dtlo) {
-                                    p.Dtlo[rowd + n] = tl;
-                                    if (mir) p.Dtlo[mirror] = tl;
+                                Dth[rowd + n] = th;
+                                if (mir) Dth[mirror] = th;
+                                if (Dtl) {
+                                    Dtl[rowd + n] = tl;
+                                    if (mir) Dtl[mirror] = tl;
                                 }
                             }
                             local = __fmaf_rn(mir ? 2.f * o : o, o, local);
