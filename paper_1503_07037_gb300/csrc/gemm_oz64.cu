@@ -439,6 +439,20 @@ __global__ void __launch_bounds__(Z_THREADS, 1)
                 for (int g = 0; g < Z_NG; ++g) ld8(lane_base + (uint32_t)(g * Z_BN + c0), r[g]);
                 tmem_ld_wait();
                 if (row_ok) {
+                    // the chunk's loads first (column exponents, C and E), then the arithmetic
+                    // of epi_apply and the stores: one memory latency per chunk, not per element
+                    int eyv[8];
+                    double cv[8], ev[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int n = n0 + c0 + j;
+                        const bool ok = n < p.N;
+                        size_t rr, cc;
+                        epi_position(p, m, n, rr, cc);
+                        eyv[j] = ok ? ey_[n] : 0;
+                        cv[j] = (ok && p.beta != 0.0) ? p.C[rr * p.ldc + cc] : 0.0;
+                        ev[j] = (ok && p.dot && p.E) ? p.E[rr * p.lde + cc] : 0.0;
+                    }
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int n = n0 + c0 + j;
@@ -450,9 +464,15 @@ __global__ void __launch_bounds__(Z_THREADS, 1)
                                 (double)__uint_as_float(r[Z_NX][j]) * (1.0 / 256.0) +
                                 (double)__uint_as_float(r[Z_NX + 1][j]) * (1.0 / 65536.0) +
                                 (double)__uint_as_float(r[Z_NX + 2][j]) * (1.0 / 16777216.0);
-                            const double v =
-                                ldexp((double)I + tail, ex + ey_[n] - 14 - 8 * (Z_NX - 1));
-                            dsum += epi_apply<double>(p, m, n, v);
+                            const double acc =
+                                ldexp((double)I + tail, ex + eyv[j] - 14 - 8 * (Z_NX - 1));
+                            size_t rr, cc;
+                            epi_position(p, m, n, rr, cc);
+                            double v = p.alpha * acc;
+                            if (p.beta != 0.0) v = fma(p.beta, cv[j], v);
+                            if (p.gamma != 0.0 && (m % p.diag_block) == n) v += p.gamma;
+                            p.D[rr * p.ldd + cc] = v;
+                            if (p.dot) dsum += v * (p.E ? ev[j] : v);
                         }
                     }
                 }
