@@ -443,7 +443,12 @@ void cdmpt_destroy(cdmpt_handle* h);
  * Storage FP32. CDMPT_FP32: split-TF32 products throughout. CDMPT_MIXED_TF32:
  * one-pass TF32 occupation sweeps, then refinement of every pair-stored
  * trajectory (split-TF32 passes, then FP64-class residuals on the late steps)
- * and a split-TF32 response, as in cdmpt_solve.
+ * and a split-TF32 response, as in cdmpt_solve. In the refinement each system
+ * switches to the FP64-class passes by itself, once its occupation error after
+ * a split pass is within 1e-4 sqrt(N_b) (environment CDMPT_BATCH_HP_SWITCH; 0
+ * switches after the first split pass), and finishes only in such a pass; the
+ * FP64-class products of different systems run on CDMPT_BATCH_HP_LANES side
+ * streams (default 8, at most 8).
  */
 typedef struct cdmpt_batch cdmpt_batch;
 
