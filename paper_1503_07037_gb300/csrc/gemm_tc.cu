@@ -25,11 +25,11 @@
 // about 2^-11 of the result, are issued before the four hi*hi ones: on the
 // first k-block of a chunk they are truncated at the scale of a small
 // accumulator.
-// Warps 2..5 sum the chunks of a tile and park the finished sums in a TMEM sum
-// buffer; warps 6..9 store the parked tile while the chunk warps drain the next
+// Warps 2..9 (two per TMEM lane quarter, each with half of the columns) sum the
+// chunks of a tile and park the finished sums in a TMEM sum buffer; warps 10..13
+// (one per quarter) store the parked tile while the chunk warps drain the next
 // tile's chunks, so the global stores overlap the MMAs. With the whole K in one
-// accumulator (one pass, or KCH = 0) all eight warps drain it, two per TMEM lane
-// quarter, each taking half of the columns.
+// accumulator (one pass, or KCH = 0) warps 2..9 drain it and store it themselves.
 //
 // Block-norm screening (single launches with a GemmProblem::mask): k-slice kb of
 // an output tile is skipped when the product of the Frobenius norms of its X and Y

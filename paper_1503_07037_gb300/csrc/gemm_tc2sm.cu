@@ -441,14 +441,14 @@ __global__ void __launch_bounds__(Cfg2<BN, STAGES, PASSES>::THREADS, 1)
 // which bounds the narrow tile) halves. The accumulation restarts every KCH k-blocks (the
 // truncating FP32 accumulation of the tensor cores; KCH = 0: whole K) into one of two
 // 256-column TMEM accumulators, so the MMA of one chunk overlaps the drain of the other.
-// EW epilogue warps per CTA (8 or 16): warp w drains TMEM lanes 32 (w % 4) of column group
+// EW = 8 epilogue warps per CTA: warp w drains TMEM lanes 32 (w % 4) of column group
 // (w - 2) / 4, CW = 1024 / EW columns, and keeps its lane's CW running sums in registers
 // (IEEE round-to-nearest adds). The drain of a chunk must keep pace with the chunk's MMAs
 // (about 0.9 us at the TF32 rate); its arrival on the peer's barrier uses the plain
 // (.release.cta) form, since a cluster-scope release made every drain wait for the previous
 // tile's global stores (ncu: membar stalls dominated, 232 TF/s at N = 8192 against 344
-// without). A finished tile is stored straight from the registers; the MMA meanwhile fills
-// the other accumulator. Tiles run in groups of eight M-tiles (grouped raster), or over the
+// without). A finished tile is stored from the registers in 32 x 32 blocks through the warp's
+// shared-memory transpose buffer (tc_store.cuh); the MMA meanwhile fills the other accumulator. Tiles run in groups of eight M-tiles (grouped raster), or over the
 // upper triangle for symmetric results.
 constexpr int SPLIT_BN = 256;
 constexpr int SPLIT_GROUP = 8;
